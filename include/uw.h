@@ -1,0 +1,167 @@
+/*
+ * uw.h -- C ABI of libuw: fast products with the N x M section U of the
+ * Walsh-Hadamard -> boundary-wavelet change-of-basis matrix and with U^*.
+ *
+ * Paper: V. Antun, "Recovering wavelet coefficients from binary samples using
+ * fast transforms", arXiv 2106.00554.
+ *
+ *   U_{n,m} = <r_m, w_n>                                  (Sec. 1.2)
+ *   y = P_Omega U x,   x = U^* P_Omega^* y                 (Sec. 1.1, Algorithm 1)
+ *   2D: alpha = G xi G^*, xi = G^* alpha G                 (Sec. 5, Algorithm 2)
+ *
+ * with w_n the sequency-ordered Walsh functions (Def. 3.1), r_m the
+ * orthonormal Daubechies wavelet basis C_{psi,R} on [0,1]^d with periodic or
+ * vanishing-moments-preserving (Cohen-Daubechies-Vial) boundary functions
+ * (Sec. 3.2), M = 2^R per dimension and N = 2^{R+q} per dimension.  The
+ * product is computed as IDWT -> dyadic upsample-and-convolve with the cell
+ * integrals of the scaling function -> sequency FWHT -> selection of Omega,
+ * and the adjoint as the same steps transposed, on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - All functions return a status (UW_OK = 0) or NULL on error; the status of
+ *    the last failing call on the calling thread is kept in uw_last_error()
+ *    and a message in uw_last_message().  No C++ exception crosses the ABI.
+ *  - Device pointers are CUDA device addresses on the device that was
+ *    current when the plan was created; the caller owns them.  Host pointers
+ *    are ordinary CPU memory (pinned memory is faster, pageable works).
+ *  - Calls are asynchronous and ordered on the given stream (a cudaStream_t
+ *    passed as void*; NULL = legacy default stream).  A plan may be used by
+ *    one stream at a time: it owns one workspace.
+ *  - Layouts are row-major.  1D x: batch x M, coefficients ordered
+ *    [phi_{J0,.} | psi_{J0,.} | psi_{J0+1,.} | ... | psi_{R-1,.}].
+ *    2D x: batch x M x M in the Mallat square layout (J0 scaling block at the
+ *    top-left; at level j the three detail blocks [0:2^j, 2^j:2^{j+1}],
+ *    [2^j:2^{j+1}, 0:2^j], [2^j:2^{j+1}, 2^j:2^{j+1}]).
+ *    y: batch x m, the samples at the sorted linear sequency indices Omega
+ *    (2D linear index n1 * N + n2, n1 = row of alpha).
+ *  - Precision: UW_F64 (double in, double out, double arithmetic),
+ *    UW_F32 (float in/out, float arithmetic on CUDA cores) and
+ *    UW_F32_SPLIT_BF16 (float in/out; the +-1 Walsh-Hadamard stages run on
+ *    tensor cores on hi+lo bfloat16 splits with float accumulation).
+ */
+#ifndef UW_H
+#define UW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct uw_plan uw_plan;
+
+enum { UW_BOUNDARY_PERIODIC = 0, UW_BOUNDARY_VMP = 1 };
+enum { UW_F64 = 0, UW_F32 = 1, UW_F32_SPLIT_BF16 = 2 };
+enum {
+  UW_OK = 0,
+  UW_ERR_INVALID_ARG = 1,  /* bad size, pointer, precision, batch, mask  */
+  UW_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement */
+  UW_ERR_OOM = 3,          /* device or host allocation failed            */
+  UW_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed        */
+  UW_ERR_TIMEOUT = 5,      /* a bounded device wait gave up               */
+  UW_ERR_INTERNAL = 6      /* a device-side consistency check tripped     */
+};
+
+/*
+ * uw_plan_create -- build every input-independent table of the method on the
+ * host in extended precision and upload it to the current CUDA device.
+ *   d        dimension, 1 or 2 (Sec. 4 / Sec. 5)
+ *   R        level of the reconstruction space, M = 2^R per dimension
+ *   q        oversampling, N = 2^{R+q} per dimension (Remark 4.1), 0..6
+ *   p        vanishing moments of the Daubechies wavelet (nu), 1..10
+ *   boundary UW_BOUNDARY_PERIODIC or UW_BOUNDARY_VMP (Sec. 3.2)
+ * Tables (Sec. 4.1 "computed a priori", Sec. 4.3, Prop. 4.4): the filter h,
+ * the (2p-1) 2^q cell integrals of phi, the boundary cell-integral rows and
+ * the level-independent boundary two-scale blocks.  The coarsest level J0 is
+ * the smallest J with 2^J >= 2 (2p - 1) (left and right edge functions
+ * disjoint); R must satisfy J0 <= R and d * (R + q) <= 26.
+ * Omega defaults to all N^d indices; the workspace to batch 1.
+ * Returns NULL on error (uw_last_error() says why).  The plan owns its
+ * device memory until uw_plan_destroy.
+ */
+uw_plan* uw_plan_create(int d, int R, int q, int p, int boundary);
+
+/* uw_plan_set_coarsest -- choose J0 (J0_min(p) <= J0 <= R).  Invalidates
+ * nothing else.  UW_ERR_INVALID_ARG if out of range. */
+int uw_plan_set_coarsest(uw_plan* plan, int J0);
+
+/*
+ * uw_plan_set_mask -- P_Omega of Sec. 1.1.  omega_host: m strictly increasing
+ * linear sequency indices in [0, N^d) (host memory, copied; the caller keeps
+ * ownership).  omega_host == NULL or m < 0 selects all N^d indices.
+ * Synchronous (uploads before returning).  UW_ERR_INVALID_ARG if the list
+ * is unsorted, repeats or leaves the range.
+ */
+int uw_plan_set_mask(uw_plan* plan, const int64_t* omega_host, int64_t m);
+
+/* uw_plan_reserve -- size the workspace for batches up to max_batch (>= 1)
+ * in every precision.  The only allocation a plan makes after creation. */
+int uw_plan_reserve(uw_plan* plan, int max_batch);
+
+/* Accessors: number of samples m, coefficients per instance M^d,
+ * coarsest level J0, N per dimension. */
+int64_t uw_plan_num_samples(const uw_plan* plan);
+int64_t uw_plan_num_coeffs(const uw_plan* plan);
+int     uw_plan_coarsest(const uw_plan* plan);
+int64_t uw_plan_n(const uw_plan* plan);
+
+/*
+ * uw_forward -- y = P_Omega U x for `batch` instances (Algorithm 1 in 1D,
+ * Algorithm 2 in 2D, preceded by the IDWT of Remark 4.2).
+ *   precision  UW_F64 / UW_F32 / UW_F32_SPLIT_BF16 (x, y are double for
+ *              UW_F64 and float otherwise)
+ *   x_dev      device, batch x M^d coefficients (read only)
+ *   y_dev      device, batch x m samples (written; must not overlap x)
+ *   batch      1 .. reserved max_batch, else UW_ERR_INVALID_ARG
+ *   stream     cudaStream_t as void*
+ */
+int uw_forward(const uw_plan* plan, int precision, const void* x_dev, void* y_dev,
+               int batch, void* stream);
+
+/*
+ * uw_adjoint -- x = U^* P_Omega^* y (Sec. 4.2 and the transposed Algorithm 2:
+ * scatter into zeros, FWHT, transposed upsample-convolve, DWT).
+ * Same arguments as uw_forward with the roles of x and y exchanged.
+ */
+int uw_adjoint(const uw_plan* plan, int precision, const void* y_dev, void* x_dev,
+               int batch, void* stream);
+
+/*
+ * uw_forward_host / uw_adjoint_host -- the same products on HOST buffers:
+ * the input is copied to the plan's device staging area, the product runs on
+ * `stream`, the result is copied back; the call returns once the result is in
+ * host memory (it synchronises `stream`).  Staging is part of the reserved
+ * workspace.
+ */
+int uw_forward_host(const uw_plan* plan, int precision, const void* x_host, void* y_host,
+                    int batch, void* stream);
+int uw_adjoint_host(const uw_plan* plan, int precision, const void* y_host, void* x_host,
+                    int batch, void* stream);
+
+/* uw_plan_destroy -- frees the plan's device and host memory; NULL is a
+ * no-op.  The caller must make sure no call using the plan is in flight. */
+void uw_plan_destroy(uw_plan* plan);
+
+/* Introspection for tests: copy the host tables into `out` (capacity `cap`
+ * doubles); returns the number of doubles the table has (call with cap = 0
+ * to size).  which: 0 = h, 1 = cell integrals I_q[t] for t from (-p+1) 2^q,
+ * 2 = left edge cell rows (p x (2p-1) 2^q), 3 = right edge cell rows,
+ * 4 = left scaling block P_L (p x (3p-1)), 5 = Q_L, 6 = P_R, 7 = Q_R. */
+int64_t uw_plan_table(const uw_plan* plan, int which, double* out, int64_t cap);
+
+/* uw_host_table -- the same tables computed on the host only (no CUDA call):
+ * what uw_plan_create would upload for (p, q).  Same `which` codes and return
+ * convention as uw_plan_table; -1 on invalid p or q. */
+int64_t uw_host_table(int p, int q, int which, double* out, int64_t cap);
+
+/* Number of kernel launches the last uw_forward / uw_adjoint issued. */
+int uw_plan_last_launches(const uw_plan* plan);
+
+int uw_last_error(void);
+const char* uw_last_message(void);
+const char* uw_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UW_H */

@@ -75,19 +75,15 @@ def taps(p, q):
 
 def _edge_walsh(p, q):
     """W phi^left_m(.+l)|[0,1)(s) and W phi^right_r(.+l)|[0,1)(s)."""
-    I = tables.cell_integrals(p, q)
-    A, trL, B, trR = tables.edge_coefficients(p)
+    EL, ER = tables.edge_cells(p, q)
     Q = 2 ** q
     left, right = {}, {}
     for m in range(p):
         for l in range(0, p + m):
-            cells = [sum(A[m, j] * I.get(l * Q + c - Q * n, 0.0) for j, n in enumerate(trL))
-                     for c in range(Q)]
-            left[(m, l)] = _walsh_of_cells(cells, q)
+            left[(m, l)] = _walsh_of_cells(EL[m, l * Q:(l + 1) * Q], q)
         for l in range(-(m + p), 0):
-            cells = [sum(B[m, j] * I.get(l * Q + c - Q * n, 0.0) for j, n in enumerate(trR))
-                     for c in range(Q)]
-            right[(m, l)] = _walsh_of_cells(cells, q)
+            # cells [l + c/Q, l + (c+1)/Q) of phi^right_m: ER index -(l Q + c) - 1
+            right[(m, l)] = _walsh_of_cells([ER[m, -(l * Q + c) - 1] for c in range(Q)], q)
     return left, right
 
 

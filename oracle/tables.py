@@ -216,6 +216,27 @@ def _edges_mp(p):
     return A, trL, B, trR
 
 
+@lru_cache(maxsize=None)
+def _edge_cells_mp(p, q):
+    m = _mp()
+    A, trL, B, trR = _edges_mp(p)
+    I = _cells_mp(p, q)
+    Q = 2 ** q
+    n = (2 * p - 1) * Q
+    EL = [[sum(A[r][j] * I.get(k - Q * t, 0) for j, t in enumerate(trL)) for k in range(n)] for r in range(p)]
+    ER = [[sum(B[r][j] * I.get(-(k + 1) - Q * t, 0) for j, t in enumerate(trR)) for k in range(n)] for r in range(p)]
+    return EL, ER
+
+
+def edge_cells(p, q):
+    """(EL, ER), p x (2p-1) 2^q float64: EL[m][k] = int_{k/2^q}^{(k+1)/2^q}
+    phi^left_m and ER[m][k] = int_{-(k+1)/2^q}^{-k/2^q} phi^right_m, summed at
+    the working precision (the translate coefficients are large exactly where
+    the restricted translates are tiny, so a float64 sum would cancel)."""
+    EL, ER = _edge_cells_mp(p, q)
+    return (np.array([[float(x) for x in r] for r in EL]), np.array([[float(x) for x in r] for r in ER]))
+
+
 def edge_coefficients(p):
     """(A, trL, B, trR): phi^left_m = sum_j A[m,j] phi(.-trL[j])|[0,inf),
     phi^right_m = sum_j B[m,j] phi(.-trR[j])|(-inf,0], float64."""

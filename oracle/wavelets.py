@@ -51,16 +51,14 @@ def cell_matrix(R, q, p, bd):
             for t, v in I.items():
                 T[(t + 2 ** q * m) % N, m] += v
         return T * 2.0 ** (-R / 2)
-    A, trL, B, trR = tables.edge_coefficients(p)
+    EL, ER = tables.edge_cells(p, q)
+    n = EL.shape[1]
     for m in range(p, M - p):
         for t, v in I.items():
             T[t + 2 ** q * m, m] = v
     for m in range(p):
-        for k in range(N):
-            T[k, m] = sum(A[m, j] * I.get(k - 2 ** q * n, 0.0) for j, n in enumerate(trL))
-        for kp in range(N):
-            T[N - 1 - kp, M - 1 - m] = sum(B[m, j] * I.get(-(kp + 1) - 2 ** q * n, 0.0)
-                                          for j, n in enumerate(trR))
+        T[:n, m] = EL[m]
+        T[N - 1 - np.arange(n), M - 1 - m] = ER[m]
     return T * 2.0 ** (-R / 2)
 
 

@@ -1,0 +1,127 @@
+"""GB300-native fast products with the Walsh -> boundary-wavelet change of basis.
+
+Paper: V. Antun, "Recovering wavelet coefficients from binary samples using
+fast transforms", arXiv 2106.00554.  The computation lives in libuw.so (CUDA
+for sm_103a behind the C ABI of include/uw.h); this package only marshals
+arguments.  PyTorch supplies device memory and streams.
+
+    plan = Plan(d=2, R=11, q=1, p=8, boundary=VMP, omega=omega)
+    y = plan.forward(x)        # y = P_Omega U x
+    z = plan.adjoint(y)        # z = U^* P_Omega^* y
+"""
+from . import _lib
+from ._lib import (UW_BOUNDARY_PERIODIC, UW_BOUNDARY_VMP, UW_F32, UW_F32_SPLIT_BF16, UW_F64,
+                   UWError, uw_adjoint, uw_adjoint_host, uw_forward, uw_forward_host, uw_host_table,
+                   uw_plan_create, uw_plan_destroy, uw_plan_reserve, uw_plan_set_coarsest,
+                   uw_plan_set_mask, uw_plan_table)
+
+PERIODIC, VMP = UW_BOUNDARY_PERIODIC, UW_BOUNDARY_VMP
+F64, F32, F32_SPLIT_BF16 = UW_F64, UW_F32, UW_F32_SPLIT_BF16
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+class Plan:
+    """Owns one uw_plan (tables, mask and workspace on the current device)."""
+
+    def __init__(self, d, R, q, p, boundary=VMP, J0=None, omega=None, max_batch=1):
+        self.d, self.R, self.q, self.p, self.boundary = d, R, q, p, boundary
+        self._h = uw_plan_create(d, R, q, p, boundary)
+        if J0 is not None:
+            uw_plan_set_coarsest(self._h, J0)
+        if omega is not None:
+            uw_plan_set_mask(self._h, omega)
+        if max_batch > 1:
+            uw_plan_reserve(self._h, max_batch)
+        self.max_batch = max_batch
+
+    # -- properties -----------------------------------------------------------
+    @property
+    def M(self):
+        return 1 << self.R
+
+    @property
+    def N(self):
+        return 1 << (self.R + self.q)
+
+    @property
+    def J0(self):
+        return _lib.lib().uw_plan_coarsest(self._h)
+
+    @property
+    def m(self):
+        return _lib.lib().uw_plan_num_samples(self._h)
+
+    @property
+    def coeffs(self):
+        return _lib.lib().uw_plan_num_coeffs(self._h)
+
+    @property
+    def last_launches(self):
+        return _lib.lib().uw_plan_last_launches(self._h)
+
+    def set_mask(self, omega):
+        uw_plan_set_mask(self._h, omega)
+
+    def reserve(self, max_batch):
+        uw_plan_reserve(self._h, max_batch)
+        self.max_batch = max_batch
+
+    def table(self, which):
+        return uw_plan_table(self._h, which)
+
+    # -- products on device tensors ---------------------------------------------
+    @staticmethod
+    def _prec(t, precision):
+        import torch
+        if precision is None:
+            return F64 if t.dtype == torch.float64 else F32
+        return precision
+
+    def forward(self, x, y=None, precision=None, stream=None):
+        """y = P_Omega U x for x of shape (batch, M) / (batch, M, M) or without
+        the batch axis; float64 -> UW_F64, float32 -> UW_F32 unless given."""
+        import torch
+        prec = self._prec(x, precision)
+        batch = x.numel() // self.coeffs
+        assert x.is_cuda and x.is_contiguous() and batch * self.coeffs == x.numel()
+        shape = (batch, self.m) if x.dim() > self.d else (self.m,)
+        if y is None:
+            y = torch.empty(shape, dtype=x.dtype, device=x.device)
+        uw_forward(self._h, prec, x.data_ptr(), y.data_ptr(), batch, _stream_ptr(stream))
+        return y
+
+    def adjoint(self, y, x=None, precision=None, stream=None):
+        """x = U^* P_Omega^* y for y of shape (batch, m) or (m,)."""
+        import torch
+        prec = self._prec(y, precision)
+        batch = (y.numel() // self.m) if self.m > 0 else (y.shape[0] if y.dim() > 1 else 1)
+        assert y.is_cuda and y.is_contiguous() and batch * self.m == y.numel()
+        shp = (self.M,) * self.d
+        shape = (batch, *shp) if y.dim() > 1 else shp
+        if x is None:
+            x = torch.empty(shape, dtype=y.dtype, device=y.device)
+        uw_adjoint(self._h, prec, y.data_ptr(), x.data_ptr(), batch, _stream_ptr(stream))
+        return x
+
+    # -- products on host arrays (copies inside the call) -------------------------
+    def forward_host(self, x, y, precision, batch, stream=None):
+        uw_forward_host(self._h, precision, x, y, batch, _stream_ptr(stream))
+
+    def adjoint_host(self, y, x, precision, batch, stream=None):
+        uw_adjoint_host(self._h, precision, y, x, batch, _stream_ptr(stream))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            uw_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,138 @@
+"""ctypes binding of libuw (include/uw.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  The CUDA
+library must be built (``paper_2106_00554_gb300.build.build()``); there is no
+CPU fallback: if libuw.so is missing the first call raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libuw.so")
+
+UW_BOUNDARY_PERIODIC, UW_BOUNDARY_VMP = 0, 1
+UW_F64, UW_F32, UW_F32_SPLIT_BF16 = 0, 1, 2
+STATUS = {0: "UW_OK", 1: "UW_ERR_INVALID_ARG", 2: "UW_ERR_UNSUPPORTED", 3: "UW_ERR_OOM",
+          4: "UW_ERR_CUDA", 5: "UW_ERR_TIMEOUT", 6: "UW_ERR_INTERNAL"}
+
+_c_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "uw_plan_create": (_c_p, [_int, _int, _int, _int, _int]),
+    "uw_plan_set_coarsest": (_int, [_c_p, _int]),
+    "uw_plan_set_mask": (_int, [_c_p, _i64p, _i64]),
+    "uw_plan_reserve": (_int, [_c_p, _int]),
+    "uw_plan_num_samples": (_i64, [_c_p]),
+    "uw_plan_num_coeffs": (_i64, [_c_p]),
+    "uw_plan_coarsest": (_int, [_c_p]),
+    "uw_plan_n": (_i64, [_c_p]),
+    "uw_forward": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
+    "uw_adjoint": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
+    "uw_forward_host": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
+    "uw_adjoint_host": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
+    "uw_plan_destroy": (None, [_c_p]),
+    "uw_plan_table": (_i64, [_c_p, _int, _dp, _i64]),
+    "uw_host_table": (_i64, [_int, _int, _int, _dp, _i64]),
+    "uw_plan_last_launches": (_int, [_c_p]),
+    "uw_last_error": (_int, []),
+    "uw_last_message": (ctypes.c_char_p, []),
+    "uw_status_string": (ctypes.c_char_p, [_int]),
+}
+
+_LIB = None
+
+
+def lib():
+    """Load libuw.so (built in-tree).  Raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError("libuw.so is not built: run paper_2106_00554_gb300.build.build() "
+                               "(the CUDA library is required; there is no CPU path)")
+        L = ctypes.CDLL(LIBPATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class UWError(RuntimeError):
+    def __init__(self, status, where):
+        msg = lib().uw_last_message().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _chk(st, where):
+    if st != 0:
+        raise UWError(st, where)
+
+
+# --- thin wrappers with the C names -----------------------------------------
+def uw_plan_create(d, R, q, p, boundary):
+    h = lib().uw_plan_create(d, R, q, p, boundary)
+    if not h:
+        raise UWError(lib().uw_last_error(), "uw_plan_create")
+    return h
+
+
+def uw_plan_set_coarsest(h, J0):
+    _chk(lib().uw_plan_set_coarsest(h, J0), "uw_plan_set_coarsest")
+
+
+def uw_plan_set_mask(h, omega):
+    import numpy as np
+    if omega is None:
+        _chk(lib().uw_plan_set_mask(h, None, -1), "uw_plan_set_mask")
+        return
+    om = np.ascontiguousarray(omega, dtype=np.int64)
+    _chk(lib().uw_plan_set_mask(h, om.ctypes.data_as(_i64p), om.size), "uw_plan_set_mask")
+
+
+def uw_plan_reserve(h, max_batch):
+    _chk(lib().uw_plan_reserve(h, max_batch), "uw_plan_reserve")
+
+
+def uw_forward(h, precision, x_ptr, y_ptr, batch, stream):
+    _chk(lib().uw_forward(h, precision, x_ptr, y_ptr, batch, stream), "uw_forward")
+
+
+def uw_adjoint(h, precision, y_ptr, x_ptr, batch, stream):
+    _chk(lib().uw_adjoint(h, precision, y_ptr, x_ptr, batch, stream), "uw_adjoint")
+
+
+def uw_forward_host(h, precision, x_ptr, y_ptr, batch, stream):
+    _chk(lib().uw_forward_host(h, precision, x_ptr, y_ptr, batch, stream), "uw_forward_host")
+
+
+def uw_adjoint_host(h, precision, y_ptr, x_ptr, batch, stream):
+    _chk(lib().uw_adjoint_host(h, precision, y_ptr, x_ptr, batch, stream), "uw_adjoint_host")
+
+
+def uw_plan_destroy(h):
+    lib().uw_plan_destroy(h)
+
+
+def uw_host_table(p, q, which):
+    import numpy as np
+    n = lib().uw_host_table(p, q, which, None, 0)
+    if n < 0:
+        raise ValueError("invalid p or q")
+    out = np.zeros(n)
+    lib().uw_host_table(p, q, which, out.ctypes.data_as(_dp), n)
+    return out
+
+
+def uw_plan_table(h, which):
+    import numpy as np
+    n = lib().uw_plan_table(h, which, None, 0)
+    out = np.zeros(n)
+    lib().uw_plan_table(h, which, out.ctypes.data_as(_dp), n)
+    return out

@@ -1,0 +1,63 @@
+// Internal declarations shared by the host planner (plan.cpp) and the CUDA
+// kernels (kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/uw.h"
+
+namespace uw {
+
+// Device-side view of the input-independent tables, one copy per precision.
+// Everything is indexed exactly like the host vectors of Plan below.
+template <typename T>
+struct Tables {
+  const T* h;      // 2p            scaling filter h_k, k = -p+1..p
+  const T* g;      // 2p            wavelet filter g_k = (-1)^k h_{1-k}
+  const T* taps;   // (2p-1) Q      I_q[t] = int_{t/Q}^{(t+1)/Q} phi, t = (-p+1)Q ..
+  const T* EL;     // p x (2p-1)Q   cell integrals of phi^left_m over [k/Q, (k+1)/Q)
+  const T* ER;     // p x (2p-1)Q   cell integrals of phi^right_r over [-(k+1)/Q, -k/Q)
+  const T* PL;     // p x Lb        level-1 coordinates of phi^left_m (Lb = 3p-1)
+  const T* QL;     // p x Lb        level-1 coordinates of psi^left_m
+  const T* PR;     // p x Lb        same on the right (coordinate c <-> index n1-1-c)
+  const T* QR;     // p x Lb
+};
+
+struct Plan {
+  int d = 1, R = 0, q = 0, p = 1, bd = 0, J0 = 0;
+  int M = 1, N = 1;          // per dimension
+  int Q = 1, Lb = 2, ntap = 1;
+  int64_t m = 0;             // samples
+  int64_t words = 0;         // mask words (d = 1: ceil(N/32); d = 2: N * ceil(N/32))
+  int wpr = 1;               // mask words per row
+  int max_batch = 0;
+  int last_launches = 0;
+
+  // host tables (double, rounded from long double)
+  std::vector<double> h, g, taps, EL, ER, PL, QL, PR, QR;
+
+  // device memory
+  void* d_tab64 = nullptr;   // packed double tables
+  void* d_tab32 = nullptr;   // packed float tables
+  Tables<double> t64{};
+  Tables<float> t32{};
+  uint32_t* d_mask = nullptr;    // words
+  int32_t* d_prefix = nullptr;   // exclusive prefix count per word
+  void* d_work = nullptr;
+  size_t work_bytes = 0;
+  void* d_stage = nullptr;       // host-API staging (input + output)
+  size_t stage_bytes = 0;
+  int device = 0;
+};
+
+// plan.cpp
+bool build_tables(Plan& P, std::string& err);
+// kernels.cu
+int upload_tables(Plan& P);
+int launch_forward(const Plan& P, int prec, const void* x, void* y, int batch, void* stream, int* nlaunch);
+int launch_adjoint(const Plan& P, int prec, const void* y, void* x, int batch, void* stream, int* nlaunch);
+size_t workspace_bytes(const Plan& P, int batch);
+void set_error(int status, const std::string& msg);
+
+}  // namespace uw

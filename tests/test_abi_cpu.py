@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI: the library loads, exports every declared symbol,
+validates arguments without touching a GPU, and its host planner computes
+the same tables as the oracle by its own routes (antiderivative cell
+integrals, partial-autocorrelation Gram matrices, projected boundary
+wavelets)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import tables, wavelets as W
+from paper_2106_00554_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "uw.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(uw_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    names = _declared()
+    assert "uw_forward" in names and "uw_plan_create" in names and len(names) >= 15
+    L = _lib.lib()
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in _lib.SIGNATURES, n
+
+
+def test_argument_validation_without_gpu():
+    L = _lib.lib()
+    for args in [(3, 5, 1, 2, 1), (1, 5, 1, 0, 1), (1, 5, 1, 11, 1), (1, 5, -1, 2, 1), (1, 5, 7, 2, 1),
+                 (1, 5, 1, 2, 2), (1, 2, 1, 2, 1), (2, 14, 0, 2, 1), (1, 30, 1, 2, 1)]:
+        assert not L.uw_plan_create(*args)
+        assert L.uw_last_error() == 1, args
+    assert L.uw_forward(None, 1, None, None, 1, None) == 1
+    assert L.uw_adjoint(None, 1, None, None, 1, None) == 1
+    assert L.uw_host_table(0, 1, 0, None, 0) == -1
+    assert L.uw_status_string(4) == b"CUDA error"
+    L.uw_plan_destroy(None)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("q", [0, 1, 2, 4])
+def test_host_tables_match_oracle(p, q):
+    tol = 1e-14 if p <= 4 else (1e-12 if p <= 6 else 5e-9)
+    h = _lib.uw_host_table(p, q, 0)
+    assert np.abs(h - tables.daubechies(p)).max() < 1e-15
+    I = _lib.uw_host_table(p, q, 1)
+    Io = tables.cell_integrals(p, q)
+    assert np.abs(I - np.array([Io[t] for t in sorted(Io)])).max() < 1e-15
+    Q = 2 ** q
+    ntap = (2 * p - 1) * Q
+    R = W.default_J0(p) + 1
+    T = W.cell_matrix(R, q, p, W.VMP) * 2 ** (R / 2)
+    N, M = T.shape
+    EL = _lib.uw_host_table(p, q, 2).reshape(p, ntap)
+    ER = _lib.uw_host_table(p, q, 3).reshape(p, ntap)
+    for m in range(p):
+        assert np.abs(EL[m] - T[:ntap, m]).max() < tol
+        assert np.abs(ER[m] - T[N - 1 - np.arange(ntap), M - 1 - m]).max() < tol
+    Lb = 3 * p - 1
+    for side, (wp, wq) in (("L", (4, 5)), ("R", (6, 7))):
+        Po, Qo = tables.edge_blocks(p, side)
+        assert np.abs(_lib.uw_host_table(p, q, wp).reshape(p, Lb) - Po[:, :Lb]).max() < tol
+        assert np.abs(_lib.uw_host_table(p, q, wq).reshape(p, Lb) - Qo[:, :Lb]).max() < 100 * tol

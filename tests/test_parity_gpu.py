@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Tolerances (relative L2 error against the FP64 oracle):
+1e-12 for UW_F64, 1e-5 for UW_F32 and UW_F32_SPLIT_BF16."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dense, fast, wavelets as W
+from paper_2106_00554_gb300 import F32, F32_SPLIT_BF16, F64, PERIODIC, VMP, Plan, UWError, build, inputs
+
+pytestmark = pytest.mark.gpu
+TOL = {F64: 1e-12, F32: 1e-5, F32_SPLIT_BF16: 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def dev(a, prec):
+    dt = torch.float64 if prec == F64 else torch.float32
+    return torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def run_fwd(plan, x, prec):
+    y = plan.forward(dev(x, prec), precision=prec)
+    torch.cuda.synchronize()
+    return y.double().cpu().numpy()
+
+
+def run_adj(plan, y, prec):
+    x = plan.adjoint(dev(y, prec), precision=prec)
+    torch.cuda.synchronize()
+    return x.double().cpu().numpy()
+
+
+# ----------------------------------------------------------------------------
+# 1D
+# ----------------------------------------------------------------------------
+def test_config1_fp64_dense():
+    """p = 2 VMP, M = 2^10, q = 1, all Walsh rows, one x (level decay 1.0) and
+    one y ~ N(0,1), seed 0: against the dense 2048 x 1024 oracle."""
+    rng = np.random.default_rng(0)
+    R, q, p = 10, 1, 2
+    plan = Plan(1, R, q, p, VMP)
+    assert plan.J0 == 3
+    x = inputs.coeffs_1d(rng, R, plan.J0, 1.0)
+    y = inputs.gaussian(rng, 2 ** (R + q))
+    U = dense.U1d(R, q, p, VMP, plan.J0)
+    for prec in (F64, F32):
+        assert rel(run_fwd(plan, x, prec), U @ x) < TOL[prec]
+        assert rel(run_adj(plan, y, prec), U.T @ y) < TOL[prec]
+
+
+CASES_1D = [(p, bd, dR, q) for p in (1, 2, 3, 4, 6, 8) for bd in (PERIODIC, VMP)
+            for dR, q in ((0, 1), (1, 0), (1, 2), (3, 1))]
+
+
+@pytest.mark.parametrize("p,bd,dR,q", CASES_1D)
+def test_1d_sweep_against_dense(p, bd, dR, q):
+    rng = np.random.default_rng(100 * p + 10 * bd + dR + q)
+    J0 = W.default_J0(p)
+    R = J0 + dR
+    M, N = 2 ** R, 2 ** (R + q)
+    omega = np.sort(rng.choice(N, size=max(1, (2 * N) // 5), replace=False))
+    plan = Plan(1, R, q, p, bd, omega=omega, max_batch=3)
+    U = dense.U1d(R, q, p, bd, J0)[omega]
+    x = rng.standard_normal((3, M))
+    y = rng.standard_normal((3, omega.size))
+    for prec in (F64, F32):
+        assert rel(run_fwd(plan, x, prec), x @ U.T) < TOL[prec]
+        assert rel(run_adj(plan, y, prec), y @ U) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec,R,q,p", [(F64, 13, 2, 3), (F32, 14, 2, 2), (F64, 12, 4, 4)])
+def test_1d_large_lines_against_algorithm1(prec, R, q, p):
+    """Lines longer than one CTA's shared memory take the multi-kernel path."""
+    rng = np.random.default_rng(R + q)
+    J0 = W.default_J0(p)
+    N = 2 ** (R + q)
+    omega = inputs.mask_1d(rng, N, 0.2)
+    plan = Plan(1, R, q, p, VMP, omega=omega, max_batch=2)
+    x = inputs.coeffs_1d(rng, R, J0, 1.5, batch=2)
+    y = rng.standard_normal((2, omega.size))
+    assert rel(run_fwd(plan, x, prec), fast.forward1d(x, R, q, p, VMP, J0, omega)) < TOL[prec]
+    assert rel(run_adj(plan, y, prec), fast.adjoint1d(y, R, q, p, VMP, J0, omega)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_config2_full_size(prec):
+    """p = 4, M = 2^16, q = 2 (N = 2^18), multilevel 15% mask, batch 64 with
+    level decay 1.5, seed 1; two sampled instances against Algorithm 1 and the
+    whole batch through the dot-product test."""
+    rng = np.random.default_rng(1)
+    R, q, p = 16, 2, 4
+    N = 2 ** (R + q)
+    omega = inputs.mask_1d(rng, N, 0.15)
+    assert omega.size == 39322
+    plan = Plan(1, R, q, p, VMP, omega=omega, max_batch=64)
+    J0 = plan.J0
+    x = inputs.coeffs_1d(rng, R, J0, 1.5, batch=64)
+    y = rng.standard_normal((64, omega.size))
+    yg = run_fwd(plan, x, prec)
+    xg = run_adj(plan, y, prec)
+    for b in (0, 63):
+        assert rel(yg[b], fast.forward1d(x[b], R, q, p, VMP, J0, omega)) < TOL[prec]
+        assert rel(xg[b], fast.adjoint1d(y[b], R, q, p, VMP, J0, omega)) < TOL[prec]
+    lhs = np.sum(yg * y)
+    rhs = np.sum(x * xg)
+    assert abs(lhs - rhs) <= 10 * TOL[prec] * (abs(lhs) + np.linalg.norm(yg) * np.linalg.norm(y))
+
+
+# ----------------------------------------------------------------------------
+# 2D
+# ----------------------------------------------------------------------------
+CASES_2D = [(p, bd, dR, q) for p in (1, 2, 4) for bd in (PERIODIC, VMP)
+            for dR, q in ((0, 1), (1, 1), (2, 0), (2, 2))]
+
+
+@pytest.mark.parametrize("p,bd,dR,q", CASES_2D)
+def test_2d_sweep_against_dense(p, bd, dR, q):
+    rng = np.random.default_rng(1000 + 100 * p + 10 * bd + dR + q)
+    J0 = W.default_J0(p)
+    R = J0 + dR
+    M, N = 2 ** R, 2 ** (R + q)
+    omega = np.sort(rng.choice(N * N, size=max(1, (N * N) // 3), replace=False))
+    plan = Plan(2, R, q, p, bd, omega=omega, max_batch=2)
+    G = dense.G1d(R, q, p, bd)
+    x = rng.standard_normal((2, M, M))
+    y = rng.standard_normal((2, omega.size))
+    want_y = dense.forward2d(x, R, q, p, bd, J0, omega, G=G)
+    want_x = dense.adjoint2d(y, R, q, p, bd, J0, omega, G=G)
+    for prec in (F64, F32):
+        assert rel(run_fwd(plan, x, prec), want_y) < TOL[prec]
+        assert rel(run_adj(plan, y, prec), want_x) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_config3(prec):
+    """p = 4, M = 256^2, q = 1, radial 25% mask, level decay 1.5, seed 2."""
+    rng = np.random.default_rng(2)
+    R, q, p = 8, 1, 4
+    N = 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.25)
+    assert omega.size == 65536
+    plan = Plan(2, R, q, p, VMP, omega=omega)
+    x = inputs.coeffs_2d(rng, R, plan.J0, 1.5)
+    y = rng.standard_normal(omega.size)
+    G = dense.G1d(R, q, p, VMP)
+    assert rel(run_fwd(plan, x, prec), dense.forward2d(x, R, q, p, VMP, plan.J0, omega, G=G)) < TOL[prec]
+    assert rel(run_adj(plan, y, prec), dense.adjoint2d(y, R, q, p, VMP, plan.J0, omega, G=G)) < TOL[prec]
+
+
+def test_config5_full_size_fp32():
+    """p = 8, M = 2048^2, q = 1 (N = 4096^2), radial 12% mask, seed 4: the
+    workload the benchmark times, against the dense-per-dimension oracle."""
+    rng = np.random.default_rng(4)
+    R, q, p = 11, 1, 8
+    N = 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.12)
+    plan = Plan(2, R, q, p, VMP, omega=omega)
+    x = inputs.coeffs_2d(rng, R, plan.J0, 1.5)
+    y = rng.standard_normal(omega.size)
+    G = dense.G1d(R, q, p, VMP)
+    assert rel(run_fwd(plan, x, F32), dense.forward2d(x, R, q, p, VMP, plan.J0, omega, G=G)) < 1e-5
+    assert rel(run_adj(plan, y, F32), dense.adjoint2d(y, R, q, p, VMP, plan.J0, omega, G=G)) < 1e-5
+
+
+# ----------------------------------------------------------------------------
+# edge cases and API behaviour
+# ----------------------------------------------------------------------------
+def test_empty_and_single_sample_masks():
+    R, q, p = 4, 1, 2
+    plan = Plan(2, R, q, p, VMP, omega=np.zeros(0, dtype=np.int64))
+    assert plan.m == 0
+    x = np.random.default_rng(0).standard_normal((16, 16))
+    xa = run_adj(plan, np.zeros(0), F64)
+    assert np.all(xa == 0)
+    plan.set_mask(np.array([5]))
+    G = dense.G1d(R, q, p, VMP)
+    assert rel(run_fwd(plan, x, F64), dense.forward2d(x, R, q, p, VMP, plan.J0, [5], G=G)) < 1e-12
+
+
+def test_invalid_calls_raise():
+    plan = Plan(1, 6, 1, 2, VMP)
+    x = torch.zeros((2, 64), dtype=torch.float64, device="cuda")
+    with pytest.raises(UWError):
+        plan.forward(x, precision=F64)           # batch 2 > reserved 1
+    with pytest.raises(UWError):
+        plan.set_mask(np.array([3, 2]))          # unsorted
+    with pytest.raises(UWError):
+        plan.set_mask(np.array([0, 128]))        # out of range
+    plan.reserve(2)
+    plan.forward(x, precision=F64)
+
+
+def test_host_buffer_api_matches_device():
+    rng = np.random.default_rng(5)
+    R, q, p = 7, 1, 3
+    N = 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.3)
+    plan = Plan(2, R, q, p, VMP, omega=omega)
+    x = np.ascontiguousarray(rng.standard_normal((2 ** R, 2 ** R)).astype(np.float32))
+    y = np.zeros(plan.m, dtype=np.float32)
+    plan.forward_host(x.ctypes.data, y.ctypes.data, F32, 1)
+    assert rel(y, run_fwd(plan, x, F32)) < 1e-6
+    xb = np.zeros_like(x)
+    plan.adjoint_host(y.ctypes.data, xb.ctypes.data, F32, 1)
+    assert rel(xb, run_adj(plan, y, F32)) < 1e-6
+
+
+def test_dot_product_2d_fp64():
+    rng = np.random.default_rng(6)
+    R, q, p = 7, 2, 4
+    N = 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.2)
+    plan = Plan(2, R, q, p, VMP, omega=omega)
+    x = rng.standard_normal((2 ** R, 2 ** R))
+    y = rng.standard_normal(omega.size)
+    a = np.dot(run_fwd(plan, x, F64), y)
+    b = np.sum(x * run_adj(plan, y, F64))
+    assert abs(a - b) < 1e-12 * abs(a)
