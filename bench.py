@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Throughput of the 2D Walsh -> boundary-wavelet products on GB300.
+
+Metric: (U x + U^* y) pairs per second at N = 4096^2 (Daubechies p = 8 with
+vanishing-moments-preserving boundaries, M = 2048^2, q = 1, radial
+multilevel sampling of 12% of the Walsh coefficients, seed 4).  One step is
+one forward product and one adjoint product (the whole path: IDWT,
+upsample-convolve, FWHT, selection, and the transposed chain).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|split_bf16|f64]
+    python bench.py --impl reference      # the CPU oracle on the host cores
+
+Under torchrun every rank runs its own replica on its own GPU (the product is
+independent per instance: weak scaling, no collective on the data path); the
+timed region is bracketed by a barrier and a device synchronisation, and the
+slowest rank sets the time.  Prints one JSON line on rank 0.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+R, Q, P, FRAC, SEED = 11, 1, 8, 0.12, 4
+METRIC = "2D U·x+U*·y pairs/s at N=4096²; split-BF16 TC vs FP32; % of HBM roofline"
+WORKLOAD = ("2D Daubechies p=8 VMP, M=2048^2 -> N=4096^2 (R=11, q=1), radial multilevel 12% mask "
+            "(m=2013266), x level-decaying alpha=1.5, y ~ N(0,1), seed 4")
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2106_00554_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    if not e:
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# the CPU oracle (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+def oracle_pair_rate(lines=64):
+    """Time the oracle's Algorithm 2 on a bounded sample of the workload and
+    scale to one full pair: the Mallat IDWT and DWT on the full 2048^2 array,
+    and Algorithm 1 (sum_l D_l H_l plus Prop. 4.4 edges) forward and adjoint
+    on `lines` lines of each pass; a full pair applies Algorithm 1 to
+    M + N lines in each direction.  Single thread (BLAS pinned to 1)."""
+    code = f"""
+import time, json, numpy as np
+from oracle import fast, wavelets as W
+from paper_2106_00554_gb300 import inputs
+R, q, p = {R}, {Q}, {P}
+M, N = 2 ** R, 2 ** (R + q)
+J0 = W.default_J0(p)
+rng = np.random.default_rng({SEED})
+x = inputs.coeffs_2d(rng, R, J0, 1.5)
+fast.alg1_forward(np.zeros((1, M)), R, q, p, W.VMP)       # build the oracle tables first
+t0 = time.perf_counter(); S = fast.idwt2d(x, J0, p, W.VMP); t_idwt = time.perf_counter() - t0
+t0 = time.perf_counter(); fast.dwt2d(S, J0, p, W.VMP); t_dwt = time.perf_counter() - t0
+L = {lines}
+xi = rng.standard_normal((L, M)); al = rng.standard_normal((L, N))
+t0 = time.perf_counter(); fast.alg1_forward(xi, R, q, p, W.VMP); t_f = (time.perf_counter() - t0) / L
+t0 = time.perf_counter(); fast.alg1_adjoint(al, R, q, p, W.VMP); t_a = (time.perf_counter() - t0) / L
+pair = t_idwt + t_dwt + (M + N) * (t_f + t_a)
+print(json.dumps({{"pair_s": pair, "idwt_s": t_idwt, "dwt_s": t_dwt, "line_fwd_s": t_f, "line_adj_s": t_a}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    t0 = time.perf_counter()
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+    wall = time.perf_counter() - t0
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": 1.0 / d["pair_s"], "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle Algorithm 2 at N=4096^2: full 2048^2 Mallat IDWT + DWT, Algorithm 1 "
+                       f"forward and adjoint timed on {lines} lines each and scaled to the M+N=6144 "
+                       f"lines of one pair; single thread; {wall:.1f} s of CPU work"),
+            "detail": d}
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(max(1, args.steps)):
+        steps.append(oracle_pair_rate(lines=16))
+        if len(steps) >= 3:
+            break
+    v = statistics.median(s["value"] for s in steps)
+    cb = dict(steps[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": len(steps), "warmup": 0, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "f64 (CPU oracle)"},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the CUDA path
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local, world = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2106_00554_gb300 import F32, F32_SPLIT_BF16, F64, VMP, Plan, _lib, build, inputs
+    build.build()
+    prec = {"f32": F32, "split_bf16": F32_SPLIT_BF16, "f64": F64}[args.precision]
+    dt = torch.float64 if prec == F64 else torch.float32
+    esize = 8 if prec == F64 else 4
+
+    rng = np.random.default_rng(SEED)
+    N = 2 ** (R + Q)
+    omega = inputs.mask_2d(rng, N, FRAC)
+    plan = Plan(2, R, Q, P, VMP, omega=omega)
+    x_np = inputs.coeffs_2d(rng, R, plan.J0, 1.5)
+    y_np = rng.standard_normal(omega.size)
+    x = torch.tensor(x_np, dtype=dt, device="cuda")
+    yin = torch.tensor(y_np, dtype=dt, device="cuda")
+    y = torch.empty(plan.m, dtype=dt, device="cuda")
+    xo = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.forward(x, y, precision=prec)
+        plan.adjoint(yin, xo, precision=prec)
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    _lib.uw_plan_profile(plan._h, True)
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    for k in range(args.steps):
+        starts[k].record(stream)
+        plan.forward(x, y, precision=prec)
+        launches += plan.last_launches
+        plan.adjoint(yin, xo, precision=prec)
+        launches += plan.last_launches
+        ends[k].record(stream)
+        flush.fill_(k)                   # L2 flush between timed steps (not timed)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    prof = _lib.uw_plan_profile_read(plan._h)
+    _lib.uw_plan_profile(plan._h, False)
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(per)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = args.steps * world / (total_ms / 1000.0)
+
+    # end to end through the host-buffer entry points (copies inside)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.tensor(x_np, dtype=dt).pin_memory()
+        yh = torch.empty(plan.m, dtype=dt).pin_memory()
+        yinh = torch.tensor(y_np, dtype=dt).pin_memory()
+        xoh = torch.empty_like(xh).pin_memory()
+        ke = max(3, min(args.steps, 200))
+        for _ in range(3):
+            plan.forward_host(xh.data_ptr(), yh.data_ptr(), prec, 1)
+            plan.adjoint_host(yinh.data_ptr(), xoh.data_ptr(), prec, 1)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            plan.forward_host(xh.data_ptr(), yh.data_ptr(), prec, 1)
+            plan.adjoint_host(yinh.data_ptr(), xoh.data_ptr(), prec, 1)
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        nbx = plan.coeffs * esize
+        nby = plan.m * esize
+        e2e = {"value": ke * world / te, "unit": "pairs/s", "h2d_bytes_per_step": nbx + nby,
+               "d2h_bytes_per_step": nby + nbx, "steps": ke}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (live event timings of this run)
+    peak, peak_kind = peaks()
+    dom = max(prof, key=lambda e: e["total_ms"])
+    avg_ms = dom["total_ms"] / max(1, dom["launches"])
+    achieved = dom["bytes_per_launch"] / (avg_ms / 1000.0) / 1e9
+    traffic = ncu_traffic(dom["name"])
+    kernels = {e["name"]: {"launches": e["launches"], "avg_us": 1000.0 * e["total_ms"] / max(1, e["launches"]),
+                           "share": e["total_ms"] / sum(z["total_ms"] for z in prof),
+                           "GBps": e["bytes_per_launch"] / (e["total_ms"] / max(1, e["launches"]) / 1000) / 1e9}
+               for e in prof}
+    words = N * ((N + 31) // 32)
+    comp = 2 * (plan.coeffs * esize + plan.m * esize + 8 * words)      # both directions
+    twopass = comp + 2 * 2 * (2 ** R) * N * esize
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {F32: "f32", F32_SPLIT_BF16: "bf16 hi+lo split, f32 accumulate", F64: "f64"}[prec],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "batch": 1,
+                   "l2": "flushed between timed steps by a 256 MiB device write outside the event pair",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s"},
+        "pipeline_roofline": {"compulsory_bytes_per_pair": comp, "two_pass_bytes_per_pair": twopass,
+                              "frac_compulsory": value * comp / 1e9 / peak,
+                              "frac_two_pass": value * twopass / 1e9 / peak},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        cb = oracle_pair_rate(lines=32)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=os.environ.get("UW_BENCH_PRECISION", "f32"),
+                    choices=["f32", "split_bf16", "f64"])
+    ap.add_argument("--R", type=int, default=R,
+                    help="level per dimension (default 11 = the benchmark workload; smaller only for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    globals()["R"] = args.R
+    if args.R != 11:
+        globals()["WORKLOAD"] = WORKLOAD.replace("M=2048^2 -> N=4096^2 (R=11, q=1)",
+                                                 f"M={2 ** args.R}^2 -> N={2 ** (args.R + 1)}^2 (R={args.R}, q=1)")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

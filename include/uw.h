@@ -154,6 +154,20 @@ int64_t uw_plan_table(const uw_plan* plan, int which, double* out, int64_t cap);
  * convention as uw_plan_table; -1 on invalid p or q. */
 int64_t uw_host_table(int p, int q, int which, double* out, int64_t cap);
 
+/* uw_plan_profile -- enable (1) or disable (0) per-kernel timing: while
+ * enabled every launch of the plan is bracketed by two CUDA events recorded
+ * on the launching stream (no extra synchronisation).  Enabling resets the
+ * totals.  Not part of the paper: measurement support. */
+int uw_plan_profile(uw_plan* plan, int enable);
+
+/* uw_plan_profile_read -- synchronises the recorded events and reports
+ * entry i: kernel name (NUL-terminated, at most cap bytes), total device time
+ * in ms, number of launches, and the algorithmic bytes of one launch (each
+ * input read once, each output written once).  Returns the number of entries
+ * (call with i = -1 to size); 0 if profiling was never enabled. */
+int uw_plan_profile_read(uw_plan* plan, int i, char* name, int cap, double* total_ms,
+                         int64_t* launches, double* bytes_per_launch);
+
 /* Number of kernel launches the last uw_forward / uw_adjoint issued. */
 int uw_plan_last_launches(const uw_plan* plan);
 

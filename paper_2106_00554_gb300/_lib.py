@@ -39,6 +39,8 @@ SIGNATURES = {
     "uw_plan_table": (_i64, [_c_p, _int, _dp, _i64]),
     "uw_host_table": (_i64, [_int, _int, _int, _dp, _i64]),
     "uw_plan_last_launches": (_int, [_c_p]),
+    "uw_plan_profile": (_int, [_c_p, _int]),
+    "uw_plan_profile_read": (_int, [_c_p, _int, ctypes.c_char_p, _int, _dp, _i64p, _dp]),
     "uw_last_error": (_int, []),
     "uw_last_message": (ctypes.c_char_p, []),
     "uw_status_string": (ctypes.c_char_p, [_int]),
@@ -135,4 +137,24 @@ def uw_plan_table(h, which):
     n = lib().uw_plan_table(h, which, None, 0)
     out = np.zeros(n)
     lib().uw_plan_table(h, which, out.ctypes.data_as(_dp), n)
+    return out
+
+
+def uw_plan_profile(h, enable):
+    _chk(lib().uw_plan_profile(h, 1 if enable else 0), "uw_plan_profile")
+
+
+def uw_plan_profile_read(h):
+    """list of dicts {name, total_ms, launches, bytes_per_launch}"""
+    L = lib()
+    n = L.uw_plan_profile_read(h, -1, None, 0, None, None, None)
+    out = []
+    for i in range(n):
+        buf = ctypes.create_string_buffer(128)
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        by = ctypes.c_double()
+        L.uw_plan_profile_read(h, i, buf, 128, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(by))
+        out.append({"name": buf.value.decode(), "total_ms": ms.value, "launches": cnt.value,
+                    "bytes_per_launch": by.value})
     return out

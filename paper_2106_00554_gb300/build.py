@@ -33,8 +33,8 @@ def sources():
 
 def build(force=False, verbose=False, extra=()):
     srcs = sources()
-    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(CSRC, "uw_internal.h"),
-                                                          os.path.join(HERE, "..", "include", "uw.h")])
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    newest = max(os.path.getmtime(s) for s in srcs + deps + [os.path.join(HERE, "..", "include", "uw.h")])
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= newest:
         return OUT
     nvcc = _nvcc()

@@ -20,262 +20,17 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
 #include "uw_internal.h"
 
+#include "line_common.cuh"
+
 namespace uw {
-
-// ---------------------------------------------------------------------------
-// small device helpers
-// ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
-__host__ __device__ __forceinline__ int padlen(int n) { return n + (n >> 4) + 1; }
-
-__device__ __forceinline__ int seqrow(int n, int L) {
-  return L == 0 ? 0 : (int)(__brev((unsigned)(n ^ (n >> 1))) >> (32 - L));
-}
-
-template <typename T>
-struct SmemTables {  // tables staged in shared memory for one CTA
-  T* h; T* g; T* taps; T* EL; T* ER; T* PL; T* QL; T* PR; T* QR;
-};
-
-struct Geo {  // geometry of one plan, passed by value
-  int p, q, Q, R, M, N, L, bd, ntap, Lb;
-};
-
-template <typename T>
-__device__ int stage_tables(const Tables<T>& t, const Geo& G, T* base, SmemTables<T>& s, int tid, int nthr) {
-  int off = 0;
-  auto take = [&](T*& dst, const T* src, int n) {
-    dst = base + off;
-    for (int i = tid; i < n; i += nthr) dst[i] = src[i];
-    off += n;
-  };
-  take(s.h, t.h, 2 * G.p);
-  take(s.g, t.g, 2 * G.p);
-  take(s.taps, t.taps, G.ntap);
-  take(s.EL, t.EL, G.p * G.ntap);
-  take(s.ER, t.ER, G.p * G.ntap);
-  take(s.PL, t.PL, G.p * G.Lb);
-  take(s.QL, t.QL, G.p * G.Lb);
-  take(s.PR, t.PR, G.p * G.Lb);
-  take(s.QR, t.QR, G.p * G.Lb);
-  return off;
-}
-
-__host__ __device__ inline int table_count(const Geo& G) {
-  return 4 * G.p + G.ntap + 2 * G.p * G.ntap + 4 * G.p * G.Lb;
-}
-
-// Accessors: plain array, or padded shared-memory array.
-template <typename T>
-struct Plain {
-  const T* a;
-  __device__ __forceinline__ T operator[](int i) const { return a[i]; }
-};
-template <typename T>
-struct Padded {
-  const T* a;
-  __device__ __forceinline__ T operator[](int i) const { return a[padi(i)]; }
-};
-template <typename T>
-struct Strided {
-  const T* a;
-  int64_t s;
-  __device__ __forceinline__ T operator[](int i) const { return a[(int64_t)i * s]; }
-};
-
-// ---------------------------------------------------------------------------
-// one synthesis output (level j -> j+1): s_{j+1}[k] from lo = s_j, hi = d_j
-// (Sec. 3.2: interior phi_{j,m} = sum_l h_l phi_{j+1,2m+l}, psi with g; the
-// p edge functions at each side through the level-independent blocks).
-// ---------------------------------------------------------------------------
-template <typename T, typename AL, typename AH, typename TB>
-__device__ __forceinline__ T syn_one(int k, int n0, const AL& lo, const AH& hi, const TB& t, const Geo& G) {
-  const int p = G.p, n1 = 2 * n0;
-  T acc = 0;
-  if (G.bd == UW_BOUNDARY_PERIODIC) {
-    for (int l = -p + 1; l <= p; ++l) {
-      int km = k - l;
-      km %= n1;
-      if (km < 0) km += n1;
-      if (km & 1) continue;
-      int m = km >> 1;
-      acc += t.h[l + p - 1] * lo[m] + t.g[l + p - 1] * hi[m];
-    }
-    return acc;
-  }
-  int mlo = max(p, (k - p + 1) >> 1);       // ceil((k - p) / 2): k - 2m <= p
-  int mhi = min(n0 - p - 1, (k + p - 1) >> 1);
-  for (int m = mlo; m <= mhi; ++m) {
-    int l = k - 2 * m;
-    acc += t.h[l + p - 1] * lo[m] + t.g[l + p - 1] * hi[m];
-  }
-  if (k < G.Lb)
-    for (int m = 0; m < p; ++m) acc += t.PL[m * G.Lb + k] * lo[m] + t.QL[m * G.Lb + k] * hi[m];
-  int c = n1 - 1 - k;
-  if (c < G.Lb)
-    for (int r = 0; r < p; ++r) acc += t.PR[r * G.Lb + c] * lo[n0 - 1 - r] + t.QR[r * G.Lb + c] * hi[n0 - 1 - r];
-  return acc;
-}
-
-// one analysis output pair (level j+1 -> j): lo[m], hi[m] from s (length n1)
-template <typename T, typename AS, typename TB>
-__device__ __forceinline__ void ana_one(int m, int n0, const AS& s, const TB& t, const Geo& G, T& lo, T& hi) {
-  const int p = G.p, n1 = 2 * n0;
-  T a = 0, b = 0;
-  if (G.bd == UW_BOUNDARY_PERIODIC) {
-    for (int l = -p + 1; l <= p; ++l) {
-      int k = (2 * m + l) % n1;
-      if (k < 0) k += n1;
-      T v = s[k];
-      a += t.h[l + p - 1] * v;
-      b += t.g[l + p - 1] * v;
-    }
-  } else if (m < p) {
-    for (int c = 0; c < G.Lb; ++c) {
-      T v = s[c];
-      a += t.PL[m * G.Lb + c] * v;
-      b += t.QL[m * G.Lb + c] * v;
-    }
-  } else if (m >= n0 - p) {
-    int r = n0 - 1 - m;
-    for (int c = 0; c < G.Lb; ++c) {
-      T v = s[n1 - 1 - c];
-      a += t.PR[r * G.Lb + c] * v;
-      b += t.QR[r * G.Lb + c] * v;
-    }
-  } else {
-    for (int l = -p + 1; l <= p; ++l) {
-      T v = s[2 * m + l];
-      a += t.h[l + p - 1] * v;
-      b += t.g[l + p - 1] * v;
-    }
-  }
-  lo = a;
-  hi = b;
-}
-
-// one output of T (upsample by Q = 2^q, convolve with the cell integrals):
-// v[k] = 2^{-R/2} (sum_{m interior} s[m] I_q[k - Q m] + edge rows)
-template <typename T, typename AS, typename TB>
-__device__ __forceinline__ T up_one(int k, const AS& s, const TB& t, const Geo& G) {
-  const int p = G.p, Q = G.Q, M = G.M, N = G.N;
-  T acc = 0;
-  const int mbase = (k >> G.q) + (p - 1);
-  const int t0 = k - mbase * Q + (p - 1) * Q;  // index into taps for j = 0
-  for (int j = 0; j < 2 * p - 1; ++j) {
-    int m = mbase - j;
-    T tap = t.taps[t0 + j * Q];
-    if (G.bd == UW_BOUNDARY_PERIODIC) {
-      int mm = m % M;
-      if (mm < 0) mm += M;
-      acc += tap * s[mm];
-    } else if (m >= p && m <= M - p - 1) {
-      acc += tap * s[m];
-    }
-  }
-  if (G.bd == UW_BOUNDARY_VMP) {
-    if (k < G.ntap)
-      for (int m = 0; m < p; ++m) acc += t.EL[m * G.ntap + k] * s[m];
-    int kk = N - 1 - k;
-    if (kk < G.ntap)
-      for (int r = 0; r < p; ++r) acc += t.ER[r * G.ntap + kk] * s[M - 1 - r];
-  }
-  return acc;
-}
-
-// one output of T^T: s[m] = 2^{-R/2} sum_k T[k, m] v[k]
-template <typename T, typename AV, typename TB>
-__device__ __forceinline__ T upT_one(int m, const AV& v, const TB& t, const Geo& G) {
-  const int p = G.p, Q = G.Q, M = G.M, N = G.N;
-  T acc = 0;
-  const int tmin = (-p + 1) * Q;
-  if (G.bd == UW_BOUNDARY_PERIODIC) {
-    for (int i = 0; i < G.ntap; ++i) {
-      int k = (Q * m + tmin + i) % N;
-      if (k < 0) k += N;
-      acc += t.taps[i] * v[k];
-    }
-  } else if (m < p) {
-    for (int k = 0; k < G.ntap; ++k) acc += t.EL[m * G.ntap + k] * v[k];
-  } else if (m >= M - p) {
-    int r = M - 1 - m;
-    for (int kk = 0; kk < G.ntap; ++kk) acc += t.ER[r * G.ntap + kk] * v[N - 1 - kk];
-  } else {
-    const int k0 = Q * m + tmin;
-    for (int i = 0; i < G.ntap; ++i) acc += t.taps[i] * v[k0 + i];
-  }
-  return acc;
-}
-
-// ---------------------------------------------------------------------------
-// natural-order Walsh-Hadamard transform of a padded shared-memory line of
-// length 2^L: radix-16 pencils in registers, one shared-memory round trip per
-// 4 bits (pad of 1 word per 16 keeps the three access strides conflict-free).
-// ---------------------------------------------------------------------------
-template <typename T, int RAD>
-__device__ __forceinline__ void fwht_pass(T* v, int L, int done, int tid, int nthr) {
-  const int N = 1 << L;
-  const int stride = 1 << done;
-  const int npencil = N / RAD;
-  for (int pc = tid; pc < npencil; pc += nthr) {
-    int lowp = pc & (stride - 1);
-    int highp = pc >> done;
-    int base = lowp + highp * stride * RAD;
-    T a[RAD];
-#pragma unroll
-    for (int i = 0; i < RAD; ++i) a[i] = v[padi(base + i * stride)];
-#pragma unroll
-    for (int hh = 1; hh < RAD; hh <<= 1)
-#pragma unroll
-      for (int i = 0; i < RAD; ++i)
-        if (!(i & hh)) {
-          T x = a[i], y = a[i + hh];
-          a[i] = x + y;
-          a[i + hh] = x - y;
-        }
-#pragma unroll
-    for (int i = 0; i < RAD; ++i) v[padi(base + i * stride)] = a[i];
-  }
-}
-
-template <typename T>
-__device__ void fwht_smem(T* v, int L, int tid, int nthr) {
-  int done = 0;
-  while (done < L) {
-    int r = min(4, L - done);
-    if (r == 4) fwht_pass<T, 16>(v, L, done, tid, nthr);
-    else if (r == 3) fwht_pass<T, 8>(v, L, done, tid, nthr);
-    else if (r == 2) fwht_pass<T, 4>(v, L, done, tid, nthr);
-    else fwht_pass<T, 2>(v, L, done, tid, nthr);
-    __syncthreads();
-    done += r;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Fused line operators (one line per CTA, whole line in shared memory).
-// ---------------------------------------------------------------------------
-struct LineIO {
-  // input / output addressing
-  int64_t in_stride;     // elements between consecutive input lines
-  int64_t out_stride;    // elements between consecutive output lines
-  int lines;             // lines per batch instance
-  int64_t in_batch;      // elements between batch instances (input)
-  int64_t out_batch;     // elements between batch instances (output)
-  int seq_rows;          // 1: line index is a sequency row n1; the data row is r(n1)
-  int mode;              // forward: 0 store natural, 1 gather; adjoint: 0 load natural, 1 scatter
-  int jlev;              // forward: first synthesis level; adjoint: last analysis level
-  const uint32_t* mask;
-  const int32_t* prefix;
-  int wpr;               // mask words per row
-  int64_t m;             // samples per instance
-  int mask_rows;         // 1 for d = 1 (all lines use row 0), else = lines
-};
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_line_fwd(const T* __restrict__ in, T* __restrict__ out,
@@ -625,6 +380,66 @@ __global__ void k_transpose(const T* __restrict__ in, T* __restrict__ out, int r
   }
 }
 
+// All small coarse levels of the 2D Mallat IDWT / DWT in one CTA: the n x n
+// top-left block (n <= 128 for FP32) stays in shared memory across levels; one
+// level is a row pass and a column pass of the per-output formulas.
+//   forward: levels jfrom .. jto-1 (block 2^jfrom -> 2^jto), in place in buf
+//   adjoint: levels jto-1 .. jfrom
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_small(T* buf, int64_t ld, int64_t bstride, int jfrom, int jto,
+                                                       int fwd, Tables<T> tab, Geo G) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<T> st;
+  const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  const int n = 1 << jto;
+  T* A = sm + off;          // n x n, row stride n + 1
+  T* Bf = A + n * (n + 1);
+  const int ls = n + 1;
+  T* g = buf + blockIdx.x * bstride;
+  for (int i = tid; i < n * n; i += nthr) A[(i / n) * ls + i % n] = g[(int64_t)(i / n) * ld + i % n];
+  __syncthreads();
+  for (int it = 0; it < jto - jfrom; ++it) {
+    const int j = fwd ? jfrom + it : jto - 1 - it;
+    const int n0 = 1 << j, n1 = 2 * n0;
+    if (fwd) {
+      for (int i = tid; i < n1 * n1; i += nthr) {      // rows: Bf[r][k]
+        int r = i / n1, kk = i % n1;
+        Plain<T> lo{A + r * ls}, hi{A + r * ls + n0};
+        Bf[r * ls + kk] = syn_one<T>(kk, n0, lo, hi, st, G);
+      }
+      __syncthreads();
+      for (int i = tid; i < n1 * n1; i += nthr) {      // columns: A[k][c]
+        int c = i % n1, kk = i / n1;
+        Strided<T> lo{Bf + c, ls}, hi{Bf + n0 * ls + c, ls};
+        A[kk * ls + c] = syn_one<T>(kk, n0, lo, hi, st, G);
+      }
+      __syncthreads();
+    } else {
+      for (int i = tid; i < n1 * n0; i += nthr) {      // columns: Bf[m][c], Bf[n0+m][c]
+        int c = i % n1, mm = i / n1;
+        Strided<T> s{A + c, ls};
+        T lo, hi;
+        ana_one<T>(mm, n0, s, st, G, lo, hi);
+        Bf[mm * ls + c] = lo;
+        Bf[(n0 + mm) * ls + c] = hi;
+      }
+      __syncthreads();
+      for (int i = tid; i < n1 * n0; i += nthr) {      // rows: A[r][m], A[r][n0+m]
+        int r = i / n0, mm = i % n0;
+        Plain<T> s{Bf + r * ls};
+        T lo, hi;
+        ana_one<T>(mm, n0, s, st, G, lo, hi);
+        A[r * ls + mm] = lo;
+        A[r * ls + n0 + mm] = hi;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < n * n; i += nthr) g[(int64_t)(i / n) * ld + i % n] = A[(i / n) * ls + i % n];
+}
+
 template <typename T>
 __global__ void k_copy_block(const T* __restrict__ in, int64_t ldin, int64_t in_batch, T* __restrict__ out,
                              int64_t ldout, int64_t out_batch, int rows, int cols, int batch) {
@@ -659,6 +474,17 @@ static const size_t kSmemMax = 200 * 1024;
 
 template <typename T>
 static bool line_fits(const Plan& P) { return line_smem<T>(P) <= kSmemMax; }
+
+// largest level whose 2^j x 2^j block (two copies) fits one CTA's shared memory
+template <typename T>
+static int small_top() { return sizeof(T) == 4 ? 7 : 6; }
+
+template <typename T>
+static size_t coarse_smem(const Plan& P, int jto) {
+  Geo G = geo_of(P);
+  const size_t n = (size_t)1 << jto;
+  return sizeof(T) * ((size_t)table_count(G) + 2 * n * (n + 1));
+}
 
 template <typename T>
 static void set_table_ptrs(Tables<T>& t, const T* base, const std::vector<const std::vector<double>*>& parts) {
@@ -709,14 +535,82 @@ size_t workspace_bytes(const Plan& P, int batch) {
   return e * (xs + a + vt + v) + 1024;
 }
 
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  struct Rec { int id; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::map<std::string, int> ids;
+  std::vector<std::string> names;
+  std::vector<double> ms, bytes;
+  std::vector<int64_t> cnt;
+  cudaEvent_t get() {
+    if (next == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[next++];
+  }
+  void collect() {
+    for (auto& r : pending) {
+      float t = 0;
+      cudaEventSynchronize(r.b);
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.id] += t;
+      cnt[r.id] += 1;
+    }
+    pending.clear();
+    next = 0;
+  }
+};
+
+void profiler_free(Plan& P) {
+  if (!P.prof) return;
+  for (auto e : P.prof->pool) cudaEventDestroy(e);
+  delete P.prof;
+  P.prof = nullptr;
+}
+
 struct Launcher {
   cudaStream_t s;
   int count = 0;
   cudaError_t err = cudaSuccess;
+  Profiler* prof = nullptr;
+  Profiler::Rec cur{};
+  bool armed = false;
+  // call before each kernel launch: name and algorithmic bytes of the launch
+  void pre(const char* name, double bytes) {
+    armed = false;
+    if (!prof || !prof->on) return;
+    auto it = prof->ids.find(name);
+    int id;
+    if (it == prof->ids.end()) {
+      id = (int)prof->names.size();
+      prof->ids[name] = id;
+      prof->names.push_back(name);
+      prof->ms.push_back(0);
+      prof->bytes.push_back(0);
+      prof->cnt.push_back(0);
+    } else {
+      id = it->second;
+    }
+    prof->bytes[id] = bytes;
+    cur = {id, prof->get(), prof->get()};
+    cudaEventRecord(cur.a, s);
+    armed = true;
+  }
   void check() {
     ++count;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess && err == cudaSuccess) err = e;
+    if (armed) {
+      cudaEventRecord(cur.b, s);
+      prof->pending.push_back(cur);
+      if (prof->pending.size() > 4000) prof->collect();
+      armed = false;
+    }
   }
 };
 
@@ -737,32 +631,69 @@ static cudaError_t set_smem(const void* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+static bool getenv_flag(const char* name) {
+  const char* v = getenv(name);
+  return v && v[0] && v[0] != '0';
+}
+
 static int line_threads(int N) { return N >= 4096 ? 256 : (N >= 1024 ? 128 : 64); }
+
+// One launch of the line operator: the register-blocked FP32 kernels where
+// they apply, the generic kernels otherwise.
+template <typename T>
+static void launch_line(bool fwd, const Plan& P, const Geo& G, const T* in, T* out, const LineIO& io, int nblocks,
+                        Launcher& L) {
+  size_t sm = line_smem<T>(P);
+  if (fwd) {
+    set_smem<T>((const void*)k_line_fwd<T>, sm);
+    k_line_fwd<T><<<nblocks, line_threads(P.N), sm, L.s>>>(in, out, tabs<T>(P), G, io);
+  } else {
+    set_smem<T>((const void*)k_line_adj<T>, sm);
+    k_line_adj<T><<<nblocks, line_threads(P.N), sm, L.s>>>(in, out, tabs<T>(P), G, io);
+  }
+}
+
+template <>
+void launch_line<float>(bool fwd, const Plan& P, const Geo& G, const float* in, float* out, const LineIO& io,
+                        int nblocks, Launcher& L) {
+  if (line2_eligible(P) && !getenv_flag("UW_GENERIC_LINES")) {
+    line2_launch(fwd, P, G, in, out, io, nblocks, L.s);
+    return;
+  }
+  size_t sm = line_smem<float>(P);
+  if (fwd) {
+    set_smem<float>((const void*)k_line_fwd<float>, sm);
+    k_line_fwd<float><<<nblocks, line_threads(P.N), sm, L.s>>>(in, out, tabs<float>(P), G, io);
+  } else {
+    set_smem<float>((const void*)k_line_adj<float>, sm);
+    k_line_adj<float><<<nblocks, line_threads(P.N), sm, L.s>>>(in, out, tabs<float>(P), G, io);
+  }
+}
 
 // 1D, the whole line in shared memory.
 template <typename T>
 static void fwd1d_smem(const Plan& P, const T* x, T* y, int batch, Launcher& L) {
+  const double e = sizeof(T);
   Geo G = geo_of(P);
   LineIO io{};
   io.in_stride = P.M; io.out_stride = P.N; io.lines = 1; io.in_batch = P.M; io.out_batch = P.m;
   io.seq_rows = 0; io.mode = 1; io.jlev = P.J0; io.mask = P.d_mask; io.prefix = P.d_prefix;
   io.wpr = P.wpr; io.m = P.m; io.mask_rows = 1;
-  size_t sm = line_smem<T>(P);
-  set_smem<T>((const void*)k_line_fwd<T>, sm);
-  k_line_fwd<T><<<batch, line_threads(P.N), sm, L.s>>>(x, y, tabs<T>(P), G, io);
+  L.pre("line_fwd_1d", e * ((double)batch * (P.M + P.m)) + 8.0 * P.words);
+  launch_line<T>(true, P, G, x, y, io, batch, L);
   L.check();
 }
 
 template <typename T>
 static void adj1d_smem(const Plan& P, const T* y, T* x, int batch, Launcher& L) {
+  const double e = sizeof(T);
   Geo G = geo_of(P);
   LineIO io{};
   io.in_stride = P.N; io.out_stride = P.M; io.lines = 1; io.in_batch = P.m; io.out_batch = P.M;
   io.seq_rows = 0; io.mode = 1; io.jlev = P.J0; io.mask = P.d_mask; io.prefix = P.d_prefix;
   io.wpr = P.wpr; io.m = P.m; io.mask_rows = 1;
-  size_t sm = line_smem<T>(P);
-  set_smem<T>((const void*)k_line_adj<T>, sm);
-  k_line_adj<T><<<batch, line_threads(P.N), sm, L.s>>>(y, x, tabs<T>(P), G, io);
+  L.pre("line_adj_1d", e * ((double)batch * (P.M + P.m)) + 8.0 * P.words);
+  launch_line<T>(false, P, G, y, x, io, batch, L);
   L.check();
 }
 
@@ -772,12 +703,14 @@ static void fwht_big(T* v, int L, int batch, Launcher& Lc) {
   int L2 = std::min(L, 12), L1 = L - L2;
   size_t sm2 = sizeof(T) * padlen(1 << L2);
   set_smem<T>((const void*)k_fwht_seg<T>, sm2);
+  Lc.pre("fwht_seg", 2.0 * sizeof(T) * (double)batch * (double)(1LL << L));
   k_fwht_seg<T><<<(int64_t)batch << L1, 256, sm2, Lc.s>>>(v, L2);
   Lc.check();
   if (L1 > 0) {
     const int COLS = 8;
     size_t sm1 = sizeof(T) * COLS * padlen(1 << L1);
     set_smem<T>((const void*)k_fwht_cols<T, COLS>, sm1);
+    Lc.pre("fwht_cols", 2.0 * sizeof(T) * (double)batch * (double)(1LL << L));
     k_fwht_cols<T, COLS><<<batch * ((1 << L2) / COLS), 256, sm1, Lc.s>>>(v, L1, L2);
     Lc.check();
   }
@@ -785,6 +718,7 @@ static void fwht_big(T* v, int L, int batch, Launcher& Lc) {
 
 template <typename T>
 static void fwd1d_big(const Plan& P, const T* x, T* y, int batch, T* work, Launcher& L) {
+  const double e = sizeof(T);
   Geo G = geo_of(P);
   const int M = P.M, N = P.N;
   T* sA = work;
@@ -795,37 +729,46 @@ static void fwd1d_big(const Plan& P, const T* x, T* y, int batch, T* work, Launc
     int n0 = 1 << j;
     LineGeom gi{M, 1, M, 1, 0}, go{M, 1, M, 1, 0};
     // lo from sA (synthesised so far), hi = details of x at [n0, 2n0): copied in sA
+    L.pre("syn_level_1d", e * 4.0 * batch * n0);
     k_syn_level<T><<<grid_for((int64_t)batch * 2 * n0), 256, 0, L.s>>>(sA, sB, n0, tabs<T>(P), G, gi, go, batch);
     L.check();
     // keep the untouched details of higher levels: copy the new prefix back
+    L.pre("copy_prefix_1d", e * 4.0 * batch * n0);
     k_copy_block<T><<<grid_for((int64_t)batch * 2 * n0), 256, 0, L.s>>>(sB, M, M, sA, M, M, 1, 2 * n0, batch);
     L.check();
   }
+  L.pre("upconv_1d", e * (double)batch * (M + N));
   k_up<T><<<grid_for((int64_t)batch * N), 256, 0, L.s>>>(sA, v, tabs<T>(P), G, batch);
   L.check();
   fwht_big<T>(v, G.L, batch, L);
+  L.pre("gather_1d", e * 2.0 * batch * P.m + 8.0 * P.words);
   k_gather<T><<<grid_for((int64_t)batch * P.words), 256, 0, L.s>>>(v, y, P.d_mask, P.d_prefix, P.words, G.L, N, P.m, batch);
   L.check();
 }
 
 template <typename T>
 static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launcher& L) {
+  const double e = sizeof(T);
   Geo G = geo_of(P);
   const int M = P.M, N = P.N;
   T* sA = work;
   T* sB = sA + (size_t)batch * M;
   T* v = sB + (size_t)batch * M;
   cudaMemsetAsync(v, 0, sizeof(T) * (size_t)batch * N, L.s);
+  L.pre("scatter_1d", e * 2.0 * batch * P.m + 8.0 * P.words);
   k_scatter<T><<<grid_for((int64_t)batch * P.words), 256, 0, L.s>>>(y, v, P.d_mask, P.d_prefix, P.words, G.L, N, P.m, batch);
   L.check();
   fwht_big<T>(v, G.L, batch, L);
+  L.pre("upconvT_1d", e * (double)batch * (M + N));
   k_upT<T><<<grid_for((int64_t)batch * M), 256, 0, L.s>>>(v, sA, tabs<T>(P), G, batch);
   L.check();
   for (int j = P.R - 1; j >= P.J0; --j) {
     int n0 = 1 << j;
     LineGeom gi{M, 1, M, 1, 0}, go{M, 1, M, 1, 0};
+    L.pre("ana_level_1d", e * 4.0 * batch * n0);
     k_ana_level<T><<<grid_for((int64_t)batch * n0), 256, 0, L.s>>>(sA, sB, n0, tabs<T>(P), G, gi, go, batch);
     L.check();
+    L.pre("copy_prefix_1d", e * 4.0 * batch * n0);
     k_copy_block<T><<<grid_for((int64_t)batch * 2 * n0), 256, 0, L.s>>>(sB, M, M, sA, M, M, 1, 2 * n0, batch);
     L.check();
   }
@@ -835,6 +778,7 @@ static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launc
 // 2D (Algorithm 2 with the Mallat IDWT in front).
 template <typename T>
 static void fwd2d(const Plan& P, const T* x, T* y, int batch, T* work, Launcher& L) {
+  const double e = sizeof(T);
   Geo G = geo_of(P);
   const int M = P.M, N = P.N, Mh = M / 2;
   const int64_t MM = (int64_t)M * M;
@@ -845,43 +789,60 @@ static void fwd2d(const Plan& P, const T* x, T* y, int batch, T* work, Launcher&
   T* V = VT + (size_t)batch * M * N;
   const bool coarse = (P.R - 1 > P.J0);
   if (coarse) {
+    L.pre("copy_coarse_in", e * 2.0 * batch * Mh * Mh);
     k_copy_block<T><<<grid_for((int64_t)batch * Mh * Mh), 256, 0, L.s>>>(x, M, MM, XS, Mh, (int64_t)Mh * Mh, Mh, Mh, batch);
     L.check();
-    for (int j = P.J0; j < P.R - 1; ++j) {
+    // small levels in one CTA per instance, larger ones level by level
+    const int jsm = std::min(P.R - 1, small_top<T>());
+    int j = P.J0;
+    if (jsm > P.J0) {
+      size_t sm = coarse_smem<T>(P, jsm);
+      set_smem<T>((const void*)k_coarse_small<T>, sm);
+      L.pre("idwt2d_small", e * 4.0 * batch * (double)(1 << jsm) * (1 << jsm));
+      k_coarse_small<T><<<batch, 1024, sm, L.s>>>(XS, Mh, (int64_t)Mh * Mh, P.J0, jsm, 1, tabs<T>(P), G);
+      L.check();
+      j = jsm;
+    }
+    for (; j < P.R - 1; ++j) {
       int n0 = 1 << j, n1 = 2 * n0;
       LineGeom rows{Mh, 1, (int64_t)Mh * Mh, n1, 0};
+      L.pre("idwt2d_rows", e * 2.0 * batch * n1 * n1);
       k_syn_level<T><<<grid_for((int64_t)batch * n1 * n1), 256, 0, L.s>>>(XS, XS2, n0, tabs<T>(P), G, rows, rows, batch);
       L.check();
       LineGeom cols{1, Mh, (int64_t)Mh * Mh, n1, 1};
+      L.pre("idwt2d_cols", e * 2.0 * batch * n1 * n1);
       k_syn_level<T><<<grid_for((int64_t)batch * n1 * n1), 256, 0, L.s>>>(XS2, XS, n0, tabs<T>(P), G, cols, cols, batch);
       L.check();
     }
   }
   dim3 tb(32, 8);
   dim3 tg((M + 31) / 32, (M + 31) / 32, batch);
+  L.pre("transpose_in", e * 2.0 * batch * MM);
   k_transpose<T><<<tg, tb, 0, L.s>>>(x, XT, M, M, MM, MM, coarse ? XS : nullptr, (int64_t)Mh * Mh, nullptr,
                                      Mh, Mh, Mh);
   L.check();
   LineIO io{};
   io.in_stride = M; io.out_stride = N; io.lines = M; io.in_batch = MM; io.out_batch = (int64_t)M * N;
   io.seq_rows = 0; io.mode = 0; io.jlev = std::max(P.R - 1, P.J0);
-  size_t sm = line_smem<T>(P);
-  set_smem<T>((const void*)k_line_fwd<T>, sm);
-  k_line_fwd<T><<<batch * M, line_threads(N), sm, L.s>>>(XT, VT, tabs<T>(P), G, io);
+  L.pre("line_fwd_dim1", e * (double)batch * (MM + (double)M * N));
+  launch_line<T>(true, P, G, XT, VT, io, batch * M, L);
   L.check();
   dim3 tg2((N + 31) / 32, (M + 31) / 32, batch);
+  L.pre("transpose_mid_fwd", e * 2.0 * batch * M * N);
   k_transpose<T><<<tg2, tb, 0, L.s>>>(VT, V, M, N, (int64_t)M * N, (int64_t)M * N, nullptr, 0, nullptr, 0, 0, 1);
   L.check();
   LineIO io2{};
   io2.in_stride = M; io2.lines = N; io2.in_batch = (int64_t)N * M; io2.out_batch = P.m;
   io2.seq_rows = 1; io2.mode = 1; io2.jlev = io.jlev; io2.mask = P.d_mask; io2.prefix = P.d_prefix;
   io2.wpr = P.wpr; io2.m = P.m; io2.mask_rows = N;
-  k_line_fwd<T><<<batch * N, line_threads(N), sm, L.s>>>(V, y, tabs<T>(P), G, io2);
+  L.pre("line_fwd_dim2_gather", e * (double)batch * ((double)N * M + P.m) + 8.0 * P.words);
+  launch_line<T>(true, P, G, V, y, io2, batch * N, L);
   L.check();
 }
 
 template <typename T>
 static void adj2d(const Plan& P, const T* y, T* x, int batch, T* work, Launcher& L) {
+  const double e = sizeof(T);
   Geo G = geo_of(P);
   const int M = P.M, N = P.N, Mh = M / 2;
   const int64_t MM = (int64_t)M * M;
@@ -892,36 +853,50 @@ static void adj2d(const Plan& P, const T* y, T* x, int batch, T* work, Launcher&
   T* Qm = QT + (size_t)batch * M * N;
   const bool coarse = (P.R - 1 > P.J0);
   const int jl = std::max(P.R - 1, P.J0);
-  size_t sm = line_smem<T>(P);
-  set_smem<T>((const void*)k_line_adj<T>, sm);
   LineIO io{};
   io.out_stride = M; io.lines = N; io.out_batch = (int64_t)N * M; io.seq_rows = 1; io.mode = 1; io.jlev = jl;
   io.mask = P.d_mask; io.prefix = P.d_prefix; io.wpr = P.wpr; io.m = P.m; io.mask_rows = N;
-  k_line_adj<T><<<batch * N, line_threads(N), sm, L.s>>>(y, Qm, tabs<T>(P), G, io);
+  L.pre("line_adj_dim2_scatter", e * (double)batch * ((double)N * M + P.m) + 8.0 * P.words);
+  launch_line<T>(false, P, G, y, Qm, io, batch * N, L);
   L.check();
   dim3 tb(32, 8);
   dim3 tg((M + 31) / 32, (N + 31) / 32, batch);
+  L.pre("transpose_mid_adj", e * 2.0 * batch * M * N);
   k_transpose<T><<<tg, tb, 0, L.s>>>(Qm, QT, N, M, (int64_t)N * M, (int64_t)N * M, nullptr, 0, nullptr, 0, 0, 1);
   L.check();
   LineIO io2{};
   io2.in_stride = N; io2.out_stride = M; io2.lines = M; io2.in_batch = (int64_t)M * N; io2.out_batch = MM;
   io2.seq_rows = 0; io2.mode = 0; io2.jlev = jl;
-  k_line_adj<T><<<batch * M, line_threads(N), sm, L.s>>>(QT, XT, tabs<T>(P), G, io2);
+  L.pre("line_adj_dim1", e * (double)batch * (MM + (double)M * N));
+  launch_line<T>(false, P, G, QT, XT, io2, batch * M, L);
   L.check();
   dim3 tg2((M + 31) / 32, (M + 31) / 32, batch);
+  L.pre("transpose_out", e * 2.0 * batch * MM);
   k_transpose<T><<<tg2, tb, 0, L.s>>>(XT, x, M, M, MM, MM, nullptr, (int64_t)Mh * Mh, coarse ? XS : nullptr,
                                       Mh, Mh, Mh);
   L.check();
   if (coarse) {
-    for (int j = P.R - 2; j >= P.J0; --j) {
+    const int jsm = std::min(P.R - 1, small_top<T>());
+    const int jstop = jsm > P.J0 ? jsm : P.J0;
+    for (int j = P.R - 2; j >= jstop; --j) {
       int n0 = 1 << j, n1 = 2 * n0;
       LineGeom cols{1, Mh, (int64_t)Mh * Mh, n1, 1};
+      L.pre("dwt2d_cols", e * 2.0 * batch * n1 * n1);
       k_ana_level<T><<<grid_for((int64_t)batch * n1 * n0), 256, 0, L.s>>>(XS, XS2, n0, tabs<T>(P), G, cols, cols, batch);
       L.check();
       LineGeom rows{Mh, 1, (int64_t)Mh * Mh, n1, 0};
+      L.pre("dwt2d_rows", e * 2.0 * batch * n1 * n1);
       k_ana_level<T><<<grid_for((int64_t)batch * n1 * n0), 256, 0, L.s>>>(XS2, XS, n0, tabs<T>(P), G, rows, rows, batch);
       L.check();
     }
+    if (jsm > P.J0) {
+      size_t sm = coarse_smem<T>(P, jsm);
+      set_smem<T>((const void*)k_coarse_small<T>, sm);
+      L.pre("dwt2d_small", e * 4.0 * batch * (double)(1 << jsm) * (1 << jsm));
+      k_coarse_small<T><<<batch, 1024, sm, L.s>>>(XS, Mh, (int64_t)Mh * Mh, P.J0, jsm, 0, tabs<T>(P), G);
+      L.check();
+    }
+    L.pre("copy_coarse_out", e * 2.0 * batch * Mh * Mh);
     k_copy_block<T><<<grid_for((int64_t)batch * Mh * Mh), 256, 0, L.s>>>(XS, Mh, (int64_t)Mh * Mh, x, M, MM, Mh, Mh, batch);
     L.check();
   }
@@ -931,6 +906,7 @@ template <typename T>
 static int run(const Plan& P, bool fwd, const void* in, void* out, int batch, cudaStream_t s, int* nl) {
   Launcher L;
   L.s = s;
+  L.prof = P.prof;
   T* work = (T*)P.d_work;
   if (P.d == 1) {
     if (line_fits<T>(P)) {
@@ -979,7 +955,9 @@ int launch_adjoint(const Plan& P, int prec, const void* y, void* x, int batch, v
 // ===========================================================================
 struct uw_plan : public uw::Plan {};
 
-static int check_call(const uw_plan* P, int prec, const void* a, const void* b, int batch) {
+// x_ptr: the coefficient side, y_ptr: the sample side (may be NULL when the
+// plan samples nothing, m == 0)
+static int check_call(const uw_plan* P, int prec, const void* x_ptr, const void* y_ptr, int batch) {
   if (!P) { uw::set_error(UW_ERR_INVALID_ARG, "null plan"); return UW_ERR_INVALID_ARG; }
   if (prec != UW_F64 && prec != UW_F32 && prec != UW_F32_SPLIT_BF16) {
     uw::set_error(UW_ERR_INVALID_ARG, "unknown precision");
@@ -989,7 +967,7 @@ static int check_call(const uw_plan* P, int prec, const void* a, const void* b, 
     uw::set_error(UW_ERR_INVALID_ARG, "batch must be in 1..reserved max_batch");
     return UW_ERR_INVALID_ARG;
   }
-  if (!a || !b) { uw::set_error(UW_ERR_INVALID_ARG, "null buffer"); return UW_ERR_INVALID_ARG; }
+  if (!x_ptr || (!y_ptr && P->m > 0)) { uw::set_error(UW_ERR_INVALID_ARG, "null buffer"); return UW_ERR_INVALID_ARG; }
   return UW_OK;
 }
 
@@ -1005,7 +983,7 @@ int uw_forward(const uw_plan* P, int prec, const void* x, void* y, int batch, vo
 }
 
 int uw_adjoint(const uw_plan* P, int prec, const void* y, void* x, int batch, void* stream) {
-  int st = check_call(P, prec, y, x, batch);
+  int st = check_call(P, prec, x, y, batch);
   if (st != UW_OK) return st;
   int nl = 0;
   st = uw::launch_adjoint(*P, prec, y, x, batch, stream, &nl);
@@ -1014,7 +992,7 @@ int uw_adjoint(const uw_plan* P, int prec, const void* y, void* x, int batch, vo
 }
 
 static int host_call(const uw_plan* P, int prec, bool fwd, const void* in, void* out, int batch, void* stream) {
-  int st = check_call(P, prec, in, out, batch);
+  int st = fwd ? check_call(P, prec, in, out, batch) : check_call(P, prec, out, in, batch);
   if (st != UW_OK) return st;
   const size_t e = prec == UW_F64 ? sizeof(double) : sizeof(float);
   const int64_t coeffs = P->d == 1 ? (int64_t)P->M : (int64_t)P->M * P->M;
@@ -1044,6 +1022,43 @@ int uw_forward_host(const uw_plan* P, int prec, const void* x, void* y, int batc
 
 int uw_adjoint_host(const uw_plan* P, int prec, const void* y, void* x, int batch, void* stream) {
   return host_call(P, prec, false, y, x, batch, stream);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int uw_plan_profile(uw_plan* P, int enable) {
+  if (!P) { uw::set_error(UW_ERR_INVALID_ARG, "null plan"); return UW_ERR_INVALID_ARG; }
+  if (!enable) {
+    if (P->prof) P->prof->on = false;
+    return UW_OK;
+  }
+  if (!P->prof) P->prof = new uw::Profiler();
+  P->prof->collect();
+  auto& f = *P->prof;
+  std::fill(f.ms.begin(), f.ms.end(), 0.0);
+  std::fill(f.cnt.begin(), f.cnt.end(), 0);
+  f.on = true;
+  return UW_OK;
+}
+
+int uw_plan_profile_read(uw_plan* P, int i, char* name, int cap, double* total_ms, int64_t* launches,
+                         double* bytes_per_launch) {
+  if (!P || !P->prof) return 0;
+  auto& f = *P->prof;
+  f.collect();
+  int n = (int)f.names.size();
+  if (i < 0 || i >= n) return n;
+  if (name && cap > 0) {
+    size_t k = std::min((size_t)cap - 1, f.names[i].size());
+    std::memcpy(name, f.names[i].data(), k);
+    name[k] = 0;
+  }
+  if (total_ms) *total_ms = f.ms[i];
+  if (launches) *launches = f.cnt[i];
+  if (bytes_per_launch) *bytes_per_launch = f.bytes[i];
+  return n;
 }
 
 }  // extern "C"

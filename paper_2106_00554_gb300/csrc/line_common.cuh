@@ -1,0 +1,282 @@
+// Device helpers shared by the CUDA translation units of libuw: index
+// helpers, table staging, and the per-output formulas of one synthesis /
+// analysis level, of T and T^T, and the shared-memory Walsh-Hadamard passes.
+// Paper: V. Antun, arXiv 2106.00554 (Sec. 3.1 FWHT, Sec. 3.2 DWT, Sec. 4.1 T).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "uw_internal.h"
+
+namespace uw {
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int padlen(int n) { return n + (n >> 4) + 1; }
+
+__device__ __forceinline__ int seqrow(int n, int L) {
+  return L == 0 ? 0 : (int)(__brev((unsigned)(n ^ (n >> 1))) >> (32 - L));
+}
+
+template <typename T>
+struct SmemTables {  // tables staged in shared memory for one CTA
+  T* h; T* g; T* taps; T* EL; T* ER; T* PL; T* QL; T* PR; T* QR;
+};
+
+struct Geo {  // geometry of one plan, passed by value
+  int p, q, Q, R, M, N, L, bd, ntap, Lb;
+};
+
+__host__ __device__ inline int table_count(const Geo& G) {
+  return 4 * G.p + G.ntap + 2 * G.p * G.ntap + 4 * G.p * G.Lb;
+}
+
+// Copy the tables into shared memory.  The host packs them contiguously in
+// this order starting at t.h, so one batched loop moves them (every thread
+// issues its loads before its stores).
+template <typename T>
+__device__ int stage_tables(const Tables<T>& t, const Geo& G, T* base, SmemTables<T>& s, int tid, int nthr) {
+  const int n = table_count(G);
+  constexpr int K = 8;
+  for (int i0 = 0; i0 < n; i0 += K * nthr) {
+    T a[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      int i = i0 + k * nthr + tid;
+      a[k] = i < n ? t.h[i] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      int i = i0 + k * nthr + tid;
+      if (i < n) base[i] = a[k];
+    }
+  }
+  s.h = base;
+  s.g = s.h + 2 * G.p;
+  s.taps = s.g + 2 * G.p;
+  s.EL = s.taps + G.ntap;
+  s.ER = s.EL + G.p * G.ntap;
+  s.PL = s.ER + G.p * G.ntap;
+  s.QL = s.PL + G.p * G.Lb;
+  s.PR = s.QL + G.p * G.Lb;
+  s.QR = s.PR + G.p * G.Lb;
+  return n;
+}
+
+
+// Accessors: plain array, or padded shared-memory array.
+template <typename T>
+struct Plain {
+  const T* a;
+  __device__ __forceinline__ T operator[](int i) const { return a[i]; }
+};
+template <typename T>
+struct Padded {
+  const T* a;
+  __device__ __forceinline__ T operator[](int i) const { return a[padi(i)]; }
+};
+template <typename T>
+struct Strided {
+  const T* a;
+  int64_t s;
+  __device__ __forceinline__ T operator[](int i) const { return a[(int64_t)i * s]; }
+};
+
+// ---------------------------------------------------------------------------
+// one synthesis output (level j -> j+1): s_{j+1}[k] from lo = s_j, hi = d_j
+// (Sec. 3.2: interior phi_{j,m} = sum_l h_l phi_{j+1,2m+l}, psi with g; the
+// p edge functions at each side through the level-independent blocks).
+// ---------------------------------------------------------------------------
+template <typename T, typename AL, typename AH, typename TB>
+__device__ __forceinline__ T syn_one(int k, int n0, const AL& lo, const AH& hi, const TB& t, const Geo& G) {
+  const int p = G.p, n1 = 2 * n0;
+  T acc = 0;
+  if (G.bd == UW_BOUNDARY_PERIODIC) {
+    for (int l = -p + 1; l <= p; ++l) {
+      int km = k - l;
+      km %= n1;
+      if (km < 0) km += n1;
+      if (km & 1) continue;
+      int m = km >> 1;
+      acc += t.h[l + p - 1] * lo[m] + t.g[l + p - 1] * hi[m];
+    }
+    return acc;
+  }
+  int mlo = max(p, (k - p + 1) >> 1);       // ceil((k - p) / 2): k - 2m <= p
+  int mhi = min(n0 - p - 1, (k + p - 1) >> 1);
+  for (int m = mlo; m <= mhi; ++m) {
+    int l = k - 2 * m;
+    acc += t.h[l + p - 1] * lo[m] + t.g[l + p - 1] * hi[m];
+  }
+  if (k < G.Lb)
+    for (int m = 0; m < p; ++m) acc += t.PL[m * G.Lb + k] * lo[m] + t.QL[m * G.Lb + k] * hi[m];
+  int c = n1 - 1 - k;
+  if (c < G.Lb)
+    for (int r = 0; r < p; ++r) acc += t.PR[r * G.Lb + c] * lo[n0 - 1 - r] + t.QR[r * G.Lb + c] * hi[n0 - 1 - r];
+  return acc;
+}
+
+// one analysis output pair (level j+1 -> j): lo[m], hi[m] from s (length n1)
+template <typename T, typename AS, typename TB>
+__device__ __forceinline__ void ana_one(int m, int n0, const AS& s, const TB& t, const Geo& G, T& lo, T& hi) {
+  const int p = G.p, n1 = 2 * n0;
+  T a = 0, b = 0;
+  if (G.bd == UW_BOUNDARY_PERIODIC) {
+    for (int l = -p + 1; l <= p; ++l) {
+      int k = (2 * m + l) % n1;
+      if (k < 0) k += n1;
+      T v = s[k];
+      a += t.h[l + p - 1] * v;
+      b += t.g[l + p - 1] * v;
+    }
+  } else if (m < p) {
+    for (int c = 0; c < G.Lb; ++c) {
+      T v = s[c];
+      a += t.PL[m * G.Lb + c] * v;
+      b += t.QL[m * G.Lb + c] * v;
+    }
+  } else if (m >= n0 - p) {
+    int r = n0 - 1 - m;
+    for (int c = 0; c < G.Lb; ++c) {
+      T v = s[n1 - 1 - c];
+      a += t.PR[r * G.Lb + c] * v;
+      b += t.QR[r * G.Lb + c] * v;
+    }
+  } else {
+    for (int l = -p + 1; l <= p; ++l) {
+      T v = s[2 * m + l];
+      a += t.h[l + p - 1] * v;
+      b += t.g[l + p - 1] * v;
+    }
+  }
+  lo = a;
+  hi = b;
+}
+
+// one output of T (upsample by Q = 2^q, convolve with the cell integrals):
+// v[k] = 2^{-R/2} (sum_{m interior} s[m] I_q[k - Q m] + edge rows)
+template <typename T, typename AS, typename TB>
+__device__ __forceinline__ T up_one(int k, const AS& s, const TB& t, const Geo& G) {
+  const int p = G.p, Q = G.Q, M = G.M, N = G.N;
+  T acc = 0;
+  const int mbase = (k >> G.q) + (p - 1);
+  const int t0 = k - mbase * Q + (p - 1) * Q;  // index into taps for j = 0
+  for (int j = 0; j < 2 * p - 1; ++j) {
+    int m = mbase - j;
+    T tap = t.taps[t0 + j * Q];
+    if (G.bd == UW_BOUNDARY_PERIODIC) {
+      int mm = m % M;
+      if (mm < 0) mm += M;
+      acc += tap * s[mm];
+    } else if (m >= p && m <= M - p - 1) {
+      acc += tap * s[m];
+    }
+  }
+  if (G.bd == UW_BOUNDARY_VMP) {
+    if (k < G.ntap)
+      for (int m = 0; m < p; ++m) acc += t.EL[m * G.ntap + k] * s[m];
+    int kk = N - 1 - k;
+    if (kk < G.ntap)
+      for (int r = 0; r < p; ++r) acc += t.ER[r * G.ntap + kk] * s[M - 1 - r];
+  }
+  return acc;
+}
+
+// one output of T^T: s[m] = 2^{-R/2} sum_k T[k, m] v[k]
+template <typename T, typename AV, typename TB>
+__device__ __forceinline__ T upT_one(int m, const AV& v, const TB& t, const Geo& G) {
+  const int p = G.p, Q = G.Q, M = G.M, N = G.N;
+  T acc = 0;
+  const int tmin = (-p + 1) * Q;
+  if (G.bd == UW_BOUNDARY_PERIODIC) {
+    for (int i = 0; i < G.ntap; ++i) {
+      int k = (Q * m + tmin + i) % N;
+      if (k < 0) k += N;
+      acc += t.taps[i] * v[k];
+    }
+  } else if (m < p) {
+    for (int k = 0; k < G.ntap; ++k) acc += t.EL[m * G.ntap + k] * v[k];
+  } else if (m >= M - p) {
+    int r = M - 1 - m;
+    for (int kk = 0; kk < G.ntap; ++kk) acc += t.ER[r * G.ntap + kk] * v[N - 1 - kk];
+  } else {
+    const int k0 = Q * m + tmin;
+    for (int i = 0; i < G.ntap; ++i) acc += t.taps[i] * v[k0 + i];
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// natural-order Walsh-Hadamard transform of a padded shared-memory line of
+// length 2^L: radix-16 pencils in registers, one shared-memory round trip per
+// 4 bits (pad of 1 word per 16 keeps the three access strides conflict-free).
+// ---------------------------------------------------------------------------
+template <typename T, int RAD>
+__device__ __forceinline__ void fwht_pass(T* v, int L, int done, int tid, int nthr) {
+  const int N = 1 << L;
+  const int stride = 1 << done;
+  const int npencil = N / RAD;
+  for (int pc = tid; pc < npencil; pc += nthr) {
+    int lowp = pc & (stride - 1);
+    int highp = pc >> done;
+    int base = lowp + highp * stride * RAD;
+    T a[RAD];
+#pragma unroll
+    for (int i = 0; i < RAD; ++i) a[i] = v[padi(base + i * stride)];
+#pragma unroll
+    for (int hh = 1; hh < RAD; hh <<= 1)
+#pragma unroll
+      for (int i = 0; i < RAD; ++i)
+        if (!(i & hh)) {
+          T x = a[i], y = a[i + hh];
+          a[i] = x + y;
+          a[i + hh] = x - y;
+        }
+#pragma unroll
+    for (int i = 0; i < RAD; ++i) v[padi(base + i * stride)] = a[i];
+  }
+}
+
+template <typename T>
+__device__ void fwht_smem(T* v, int L, int tid, int nthr) {
+  int done = 0;
+  while (done < L) {
+    int r = min(4, L - done);
+    if (r == 4) fwht_pass<T, 16>(v, L, done, tid, nthr);
+    else if (r == 3) fwht_pass<T, 8>(v, L, done, tid, nthr);
+    else if (r == 2) fwht_pass<T, 4>(v, L, done, tid, nthr);
+    else fwht_pass<T, 2>(v, L, done, tid, nthr);
+    __syncthreads();
+    done += r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused line operators (one line per CTA, whole line in shared memory).
+// ---------------------------------------------------------------------------
+struct LineIO {
+  // input / output addressing
+  int64_t in_stride;     // elements between consecutive input lines
+  int64_t out_stride;    // elements between consecutive output lines
+  int lines;             // lines per batch instance
+  int64_t in_batch;      // elements between batch instances (input)
+  int64_t out_batch;     // elements between batch instances (output)
+  int seq_rows;          // 1: line index is a sequency row n1; the data row is r(n1)
+  int mode;              // forward: 0 store natural, 1 gather; adjoint: 0 load natural, 1 scatter
+  int jlev;              // forward: first synthesis level; adjoint: last analysis level
+  const uint32_t* mask;
+  const int32_t* prefix;
+  int wpr;               // mask words per row
+  int64_t m;             // samples per instance
+  int mask_rows;         // 1 for d = 1 (all lines use row 0), else = lines
+};
+
+// kernels_line.cu: register-blocked FP32 line operators
+bool line2_eligible(const Plan& P);
+cudaError_t line2_launch(bool fwd, const Plan& P, const Geo& G, const float* in, float* out, const LineIO& io,
+                         int nblocks, cudaStream_t s);
+
+}  // namespace uw

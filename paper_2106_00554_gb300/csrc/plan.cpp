@@ -146,24 +146,27 @@ static std::vector<LD> daubechies(int p) {
 }
 
 // ---------------------------------------------------------------------------
-// Cell integrals I_q[t] through the antiderivative Phi(x) = int_{-inf}^x phi:
-// Phi(x) = (1/sqrt2) sum_k h_k Phi(2x - k), Phi = 0 left of the support and 1
-// right of it; solve at the integers, refine to the dyadics of level q, then
-// I_q[t] = Phi((t+1)/2^q) - Phi(t/2^q).
+// Cell integrals I_q[t] through antiderivatives of phi: the lower one
+// Phi(x) = int_{-inf}^x phi and the upper one Psi(x) = int_x^inf phi both satisfy
+// X(x) = (1/sqrt2) sum_k h_k X(2x - k) (Phi = 0 left of the support and 1 right
+// of it, Psi the other way round).  Solve at the integers, refine to the
+// dyadics of level q, then take I_q[t] = Phi((t+1)/2^q) - Phi(t/2^q) on the
+// left half of the support and Psi(t/2^q) - Psi((t+1)/2^q) on the right half:
+// each difference is formed where its antiderivative is small, so the tiny
+// cells at both ends keep their relative accuracy.
 // ---------------------------------------------------------------------------
-static std::vector<LD> cell_integrals(const std::vector<LD>& h, int p, int q) {
+static std::map<long, LD> antiderivative(const std::vector<LD>& h, int p, int q, bool upper) {
   auto H = [&](int k) -> LD { int i = k + p - 1; return (i >= 0 && i < 2 * p) ? h[i] : 0; };
   const LD is2 = 1 / std::sqrt((LD)2);
-  // unknowns Phi(n), n = -p+2 .. p-1
+  const LD left_val = upper ? 1 : 0, right_val = upper ? 0 : 1;
   int lo = -p + 2, hi = p - 1, n = std::max(0, hi - lo + 1);
-  std::map<long, LD> phi0;  // level-0 values keyed by integer
-  auto known0 = [&](long x, bool& isk) -> LD {
-    isk = true;
-    if (x <= -p + 1) return 0;
-    if (x >= p) return 1;
-    isk = false;
-    return 0;
+  auto val = [&](const std::map<long, LD>& m, long i, long S) -> LD {
+    if (i <= (-p + 1) * S) return left_val;
+    if (i >= p * S) return right_val;
+    auto it = m.find(i);
+    return it == m.end() ? 0 : it->second;
   };
+  std::map<long, LD> cur;
   if (n > 0) {
     std::vector<LD> A((size_t)n * n, 0), b(n, 0), x;
     for (int r = 0; r < n; ++r) {
@@ -171,51 +174,51 @@ static std::vector<LD> cell_integrals(const std::vector<LD>& h, int p, int q) {
       A[(size_t)r * n + r] += 1;
       for (int k = -p + 1; k <= p; ++k) {
         long arg = 2L * nn - k;
-        bool isk;
-        LD v = known0(arg, isk);
-        if (isk) b[r] += is2 * H(k) * v;
+        if (arg <= -p + 1 || arg >= p) b[r] += is2 * H(k) * (arg <= -p + 1 ? left_val : right_val);
         else A[(size_t)r * n + (arg - lo)] -= is2 * H(k);
       }
     }
     solve(A, b, n, x);
-    for (int r = 0; r < n; ++r) phi0[lo + r] = x[r];
+    for (int r = 0; r < n; ++r) cur[lo + r] = x[r];
   }
-  // level j values Phi(i / 2^j), i in [(-p+1) 2^j, p 2^j]
-  auto val = [&](const std::map<long, LD>& m, long i, long j_scale_lo, long j_scale_hi) -> LD {
-    if (i <= j_scale_lo) return 0;
-    if (i >= j_scale_hi) return 1;
-    auto it = m.find(i);
-    return it == m.end() ? 0 : it->second;
-  };
-  std::map<long, LD> cur = phi0;
   long S = 1;
   for (int j = 1; j <= q; ++j) {
     std::map<long, LD> nxt;
     long S2 = S * 2;
     for (long i = (-p + 1) * S2; i <= p * S2; ++i) {
-      // Phi(i/S2) = (1/sqrt2) sum_k h_k Phi(i/S - k)  with i/S = 2 * (i/S2)
+      // X(i/S2) = (1/sqrt2) sum_k h_k X(i/S - k)
       LD s = 0;
-      for (int k = -p + 1; k <= p; ++k) s += H(k) * val(cur, i - k * S, (-p + 1) * S, p * S);
+      for (int k = -p + 1; k <= p; ++k) s += H(k) * val(cur, i - k * S, S);
       nxt[i] = is2 * s;
     }
     cur.swap(nxt);
     S = S2;
   }
+  // complete the table with the boundary values
+  for (long i = (-p + 1) * S; i <= p * S; ++i) cur[i] = val(cur, i, S);
+  return cur;
+}
+
+static std::vector<LD> cell_integrals(const std::vector<LD>& h, int p, int q) {
+  std::map<long, LD> Phi = antiderivative(h, p, q, false), Psi = antiderivative(h, p, q, true);
+  const long S = 1L << q;
   std::vector<LD> I;
-  for (long t = (-p + 1) * S; t <= p * S - 1; ++t)
-    I.push_back(val(cur, t + 1, (-p + 1) * S, p * S) - val(cur, t, (-p + 1) * S, p * S));
+  for (long t = (-p + 1) * S; t <= p * S - 1; ++t) {
+    // the support [-p+1, p] has its centre at 1/2, i.e. at t + 1/2 = S/2
+    if (2 * t + 1 < S) I.push_back(Phi[t + 1] - Phi[t]);
+    else I.push_back(Psi[t] - Psi[t + 1]);
+  }
   return I;
 }
 
 // ---------------------------------------------------------------------------
 // Restricted Gram matrices through partial autocorrelations at integers:
-//   F_d(y)  = int_{-inf}^y phi(u) phi(u-d) du,   Fb_d(y) = int_y^inf phi(u) phi(u-d) du.
-// Both satisfy X_d(y) = sum_{k,l} h_k h_l X_{2d+l-k}(2y-k) (substitute
-// phi(u) = sqrt2 sum_k h_k phi(2u-k)), with the boundary values 0 / delta_{d0}
-// on either side of the common support [max(-p+1,d-p+1), min(p,d+p)]
-// exchanged.  Then int_{-inf}^0 phi(x-a) phi(x-b) dx = F_{b-a}(-a) and
-// int_0^inf phi(x-a) phi(x-b) dx = Fb_{b-a}(-a): tiny overlaps come straight out
-// of a solve and are never formed as 1 - (1 - tiny).
+//   Fb_d(y) = int_y^inf phi(u) phi(u-d) du
+// satisfies Fb_d(y) = sum_{k,l} h_k h_l Fb_{2d+l-k}(2y-k) (substitute
+// phi(u) = sqrt2 sum_k h_k phi(2u-k)), with Fb = delta_{d0} left of the common
+// support [max(-p+1,d-p+1), min(p,d+p)] and 0 right of it.  Then
+//   int_0^inf  phi(x-a) phi(x-b) dx = Fb_{b-a}(-a),
+//   int_-inf^0 phi(x-a) phi(x-b) dx = delta_ab - Fb_{b-a}(-a).
 // ---------------------------------------------------------------------------
 struct Gram {
   int p;
@@ -229,8 +232,11 @@ struct Gram {
     auto it = X.find({d, (int)y});
     return it == X.end() ? 0 : it->second;
   }
+  // Only the upper integrals Fb are used: solved directly they keep relative
+  // accuracy down to the smallest overlaps (F loses it in the upper part of
+  // the support), and the lower integral is delta_{d0} - Fb.
   LD left(int a, int b) const { return lookup(Fb, p, b - a, -a, true); }
-  LD right(int a, int b) const { return lookup(F, p, b - a, -a, false); }
+  LD right(int a, int b) const { return (a == b ? 1 : 0) - lookup(Fb, p, b - a, -a, true); }
 };
 
 static bool solve_autocorr(const std::vector<LD>& h, int p, bool upper, std::map<std::pair<int, int>, LD>& X) {
@@ -269,7 +275,7 @@ static bool solve_autocorr(const std::vector<LD>& h, int p, bool upper, std::map
 
 static bool build_gram(const std::vector<LD>& h, int p, Gram& G) {
   G.p = p;
-  return solve_autocorr(h, p, false, G.F) && solve_autocorr(h, p, true, G.Fb);
+  return solve_autocorr(h, p, true, G.Fb);
 }
 
 // ---------------------------------------------------------------------------
@@ -287,9 +293,15 @@ static std::vector<std::vector<LD>> edge_fns(int p, const std::vector<int>& tr,
     std::vector<LD> v(n);
     LD mx = 0;
     for (int j = 0; j < n; ++j) {
+      // Lagrange polynomial of node m (left: nodes 0..p-1) or -m-1 (right:
+      // nodes -1..-p): it vanishes on the nodes beyond m, so L_0..L_m span the
+      // functions supported in [0, p+m] (resp. [-m-p, 0])
+      const int node = left ? m : -m - 1;
       LD prod = 1;
-      if (left) for (int k = m + 1; k <= p - 1; ++k) prod *= (LD)(tr[j] - k);
-      else for (int k = -p; k <= -m - 2; ++k) prod *= (LD)(tr[j] - k);
+      for (int i = 0; i < p; ++i) {
+        const int nk = left ? i : -i - 1;
+        if (nk != node) prod *= (LD)(tr[j] - nk) / (LD)(node - nk);
+      }
       v[j] = prod;
       mx = std::max(mx, std::fabs(prod));
     }
@@ -688,6 +700,7 @@ int64_t uw_host_table(int p, int q, int which, double* out, int64_t cap) {
 
 void uw_plan_destroy(uw_plan* P) {
   if (!P) return;
+  uw::profiler_free(*P);
   cudaFree(P->d_tab64);
   cudaFree(P->d_tab32);
   cudaFree(P->d_mask);

@@ -24,6 +24,12 @@ struct Tables {
   const T* QR;     // p x Lb
 };
 
+// Per-kernel timing with CUDA events recorded on the launching stream around
+// every launch (only while enabled): total time, launch count and the
+// algorithmic bytes one launch must move (inputs read once, outputs written
+// once).
+struct Profiler;
+
 struct Plan {
   int d = 1, R = 0, q = 0, p = 1, bd = 0, J0 = 0;
   int M = 1, N = 1;          // per dimension
@@ -49,6 +55,7 @@ struct Plan {
   void* d_stage = nullptr;       // host-API staging (input + output)
   size_t stage_bytes = 0;
   int device = 0;
+  Profiler* prof = nullptr;
 };
 
 // plan.cpp
@@ -59,5 +66,6 @@ int launch_forward(const Plan& P, int prec, const void* x, void* y, int batch, v
 int launch_adjoint(const Plan& P, int prec, const void* y, void* x, int batch, void* stream, int* nlaunch);
 size_t workspace_bytes(const Plan& P, int batch);
 void set_error(int status, const std::string& msg);
+void profiler_free(Plan& P);
 
 }  // namespace uw

@@ -145,6 +145,34 @@ def test_2d_sweep_against_dense(p, bd, dR, q):
         assert rel(run_adj(plan, y, prec), want_x) < TOL[prec]
 
 
+@pytest.mark.parametrize("generic", [False, True])
+@pytest.mark.parametrize("p,bd,dR,q", [(2, VMP, 2, 1), (4, PERIODIC, 3, 2), (8, VMP, 4, 1), (3, VMP, 4, 1)])
+def test_fp32_line_kernels_both_implementations(monkeypatch, generic, p, bd, dR, q):
+    """The register-blocked FP32 line kernels and the generic ones (selected
+    with UW_GENERIC_LINES=1) both match the oracle, 1D and 2D."""
+    if generic:
+        monkeypatch.setenv("UW_GENERIC_LINES", "1")
+    rng = np.random.default_rng(7 * p + q)
+    J0 = W.default_J0(p)
+    R = J0 + dR
+    M, N = 2 ** R, 2 ** (R + q)
+    om1 = inputs.mask_1d(rng, N, 0.3)
+    plan1 = Plan(1, R, q, p, bd, omega=om1, max_batch=2)
+    x1 = inputs.coeffs_1d(rng, R, J0, 1.0, batch=2)
+    y1 = rng.standard_normal((2, om1.size))
+    assert rel(run_fwd(plan1, x1, F32), fast.forward1d(x1, R, q, p, bd, J0, om1)) < 1e-5
+    assert rel(run_adj(plan1, y1, F32), fast.adjoint1d(y1, R, q, p, bd, J0, om1)) < 1e-5
+    if R > 9:
+        return
+    om2 = inputs.mask_2d(rng, N, 0.2)
+    plan2 = Plan(2, R, q, p, bd, omega=om2)
+    x2 = inputs.coeffs_2d(rng, R, J0, 1.5)
+    y2 = rng.standard_normal(om2.size)
+    G = dense.G1d(R, q, p, bd)
+    assert rel(run_fwd(plan2, x2, F32), dense.forward2d(x2, R, q, p, bd, J0, om2, G=G)) < 1e-5
+    assert rel(run_adj(plan2, y2, F32), dense.adjoint2d(y2, R, q, p, bd, J0, om2, G=G)) < 1e-5
+
+
 @pytest.mark.parametrize("prec", [F64, F32])
 def test_config3(prec):
     """p = 4, M = 256^2, q = 1, radial 25% mask, level decay 1.5, seed 2."""
