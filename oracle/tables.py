@@ -10,6 +10,7 @@ Conventions (Sec. 3.2): supp(phi) = supp(psi) = [-p+1, p]; the scaling filter
 h_k lives on k = -p+1..p and phi(x) = sqrt(2) sum_k h_k phi(2x - k); the
 wavelet filter is g_k = (-1)^k h_{1-k}.
 """
+from fractions import Fraction
 from functools import lru_cache
 from math import comb
 
@@ -181,11 +182,17 @@ def gram_right_mp(p, a, b):
 # n = -p..p-2, nodes -1, -2, ..: supp phi^right_m = [-m-p, 0].
 # ----------------------------------------------------------------------------
 def _lagrange(nodes, i, x):
-    v = 1
+    """Lagrange basis polynomial of nodes[i] at x, in exact rationals (the
+    polynomial weights must be exact: rounding them moves the edge space)."""
+    v = Fraction(1)
     for k in nodes:
         if k != nodes[i]:
-            v = v * (x - k) / (nodes[i] - k)
+            v = v * Fraction(x - k, nodes[i] - k)
     return v
+
+
+def _mpq(fr):
+    return _mp().mpf(fr.numerator) / fr.denominator
 
 
 def _gs(vectors, G):
@@ -208,11 +215,11 @@ def _edges_mp(p):
     trL = list(range(-p + 1, p))
     GL = [[gram_left_mp(p, a, b) for b in trL] for a in trL]
     nodesL = list(range(0, p))
-    A = _gs([[m.mpf(_lagrange(nodesL, i, n)) for n in trL] for i in range(p)], GL)
+    A = _gs([[_mpq(_lagrange(nodesL, i, n)) for n in trL] for i in range(p)], GL)
     trR = list(range(-p, p - 1))
     GR = [[gram_right_mp(p, a, b) for b in trR] for a in trR]
     nodesR = [-(i + 1) for i in range(p)]
-    B = _gs([[m.mpf(_lagrange(nodesR, i, n)) for n in trR] for i in range(p)], GR)
+    B = _gs([[_mpq(_lagrange(nodesR, i, n)) for n in trR] for i in range(p)], GR)
     return A, trL, B, trR
 
 

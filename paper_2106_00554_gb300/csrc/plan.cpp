@@ -69,6 +69,25 @@ static bool solve(std::vector<LD> A, std::vector<LD> b, int n, std::vector<LD>& 
   return true;
 }
 
+// Compensated dot product (Ogita, Rump, Oishi, "Accurate sum and dot
+// product", 2005, Algorithm Dot2): every product is split exactly with an FMA
+// and every addition with TwoSum, so the result is as accurate as a plain sum
+// in twice the working precision.  The edge-space sums pair large polynomial
+// coefficients with tiny restricted overlaps and cancel heavily.
+struct Dot2 {
+  LD s = 0, c = 0;
+  void add(LD a, LD b) {
+    const LD p = a * b;
+    const LD ep = std::fma(a, b, -p);
+    const LD t = s + p;
+    const LD z = t - s;
+    const LD es = (s - (t - z)) + (p - z);
+    s = t;
+    c += ep + es;
+  }
+  LD get() const { return s + c; }
+};
+
 // ---------------------------------------------------------------------------
 // Daubechies extremal-phase filter: roots of P(y) = sum_{k<p} C(p-1+k,k) y^k
 // by Durand-Kerner iteration polished with Newton steps; each root y gives the
@@ -307,10 +326,14 @@ static std::vector<std::vector<LD>> edge_fns(int p, const std::vector<int>& tr,
     }
     for (auto& e : v) e /= mx;
     auto dot = [&](const std::vector<LD>& a, const std::vector<LD>& b) {
-      LD s = 0;
-      for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) s += a[i] * Gm[i][j] * b[j];
-      return s;
+      Dot2 outer;
+      for (int i = 0; i < n; ++i) {
+        Dot2 inner;
+        for (int j = 0; j < n; ++j) inner.add(Gm[i][j], b[j]);
+        outer.add(a[i], inner.s);  // keep the inner sum as the pair (s, c)
+        outer.add(a[i], inner.c);
+      }
+      return outer.get();
     };
     for (int pass = 0; pass < 2; ++pass)
       for (auto& u : out) {
@@ -348,18 +371,24 @@ static void side_blocks(int p, bool left, const std::vector<LD>& h, const Gram& 
   std::vector<std::vector<LD>> rows;
   // level-0 edge scaling functions
   for (int m = 0; m < p; ++m) {
-    std::map<int, LD> c;
+    std::map<int, Dot2> cacc;
     for (size_t j = 0; j < tr.size(); ++j)
       for (int k = -p + 1; k <= p; ++k) {
         int i = 2 * tr[j] + k;
-        if (keep(i)) c[i] += E[m][j] * H(k);
+        if (keep(i)) cacc[i].add(E[m][j], H(k));
       }
+    std::map<int, LD> c;
+    for (auto& kv : cacc) c[kv.first] = kv.second.get();
     std::vector<LD> v(W, 0);
     for (int mp = 0; mp < p; ++mp) {
-      LD s = 0;
-      for (auto& kv : c)
-        for (size_t j2 = 0; j2 < tr.size(); ++j2) s += kv.second * Gf(kv.first, tr[j2]) * E[mp][j2];
-      v[mp] = s;
+      Dot2 outer;
+      for (auto& kv : c) {
+        Dot2 inner;
+        for (size_t j2 = 0; j2 < tr.size(); ++j2) inner.add(Gf(kv.first, tr[j2]), E[mp][j2]);
+        outer.add(kv.second, inner.s);
+        outer.add(kv.second, inner.c);
+      }
+      v[mp] = outer.get();
     }
     for (auto& kv : c)
       if (coord(kv.first) >= p) v[coord(kv.first)] += kv.second;
@@ -499,11 +528,11 @@ bool build_tables(Plan& P, std::string& err) {
   P.ER.assign((size_t)p * P.ntap, 0);
   for (int m = 0; m < p; ++m)
     for (int k = 0; k < P.ntap; ++k) {
-      LD sl = 0, sr = 0;
-      for (size_t j = 0; j < trL.size(); ++j) sl += A[m][j] * Iq((long)k - (long)Q * trL[j]);
-      for (size_t j = 0; j < trR.size(); ++j) sr += B[m][j] * Iq(-(long)(k + 1) - (long)Q * trR[j]);
-      P.EL[(size_t)m * P.ntap + k] = (double)sl;
-      P.ER[(size_t)m * P.ntap + k] = (double)sr;
+      Dot2 sl, sr;
+      for (size_t j = 0; j < trL.size(); ++j) sl.add(A[m][j], Iq((long)k - (long)Q * trL[j]));
+      for (size_t j = 0; j < trR.size(); ++j) sr.add(B[m][j], Iq(-(long)(k + 1) - (long)Q * trR[j]));
+      P.EL[(size_t)m * P.ntap + k] = (double)sl.get();
+      P.ER[(size_t)m * P.ntap + k] = (double)sr.get();
     }
   std::vector<LD> pl, ql, pr, qr;
   side_blocks(p, true, h, G, A, trL, pl, ql, P.Lb);
