@@ -16,10 +16,12 @@
 // w_n(k/N) = (-1)^{sum_j (n^(j) xor n^(j+1)) k^(L+1-j)} = (-1)^{popcount(r(n) & k)},
 // r(n) = bitreverse_L(n xor (n >> 1)).  So the natural-order (Hadamard) FWHT
 // output at index r(n) is the sequency coefficient n, and (d) reads it there.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -380,6 +382,249 @@ __global__ void k_transpose(const T* __restrict__ in, T* __restrict__ out, int r
   }
 }
 
+// ---------------------------------------------------------------------------
+// One coarse Mallat level, both directions of the separable step fused in one
+// kernel: a CTA stages the input window it needs (with the halo of the
+// filters, and the boundary rows of the VMP blocks) in shared memory, runs the
+// row pass and the column pass there, and writes its output tile.
+// ---------------------------------------------------------------------------
+// window accessor: global index g -> window slot (modular for periodic)
+template <typename T>
+struct Win {
+  const T* a;
+  int start, len, stride, n, per;
+  __device__ __forceinline__ T operator[](int g) const {
+    int w = g - start;
+    if (per) {
+      w %= n;
+      if (w < 0) w += n;
+    }
+    return (w >= 0 && w < len) ? a[w * stride] : T(0);
+  }
+};
+
+// index range [lo, hi) of level-j coefficients that outputs [a, b) of level
+// j+1 depend on (interior taps, and the VMP boundary blocks near the edges);
+// periodic ranges may start below 0 and are read modulo n0
+__host__ __device__ __forceinline__ void syn_dep(int a, int b, int n0, const Geo& G, int& lo, int& hi) {
+  const int p = G.p, n1 = 2 * n0;
+  lo = (a - p) >> 1;        // floor((a - p) / 2)
+  hi = ((b - 1 + p - 1) >> 1) + 1;
+  if (G.bd == UW_BOUNDARY_PERIODIC) {
+    if (hi - lo > n0) { lo = 0; hi = n0; }
+    return;
+  }
+  if (a < G.Lb || lo < 0) lo = 0;
+  if (b > n1 - G.Lb || hi > n0) hi = n0;
+}
+
+// analysis: outputs m in [a, b) of level j need level-(j+1) samples [lo, hi)
+__host__ __device__ __forceinline__ void ana_dep(int a, int b, int n0, const Geo& G, int& lo, int& hi) {
+  const int p = G.p, n1 = 2 * n0;
+  lo = 2 * a - p + 1;
+  hi = 2 * (b - 1) + p + 1;
+  if (G.bd == UW_BOUNDARY_PERIODIC) {
+    if (hi - lo > n1) { lo = 0; hi = n1; }
+    return;
+  }
+  if (a < p || lo < 0) lo = 0;
+  if (b > n0 - p || hi > n1) hi = n1;
+}
+
+constexpr int kTile = 64;
+
+// synthesis level j -> j+1 on the n1 x n1 block [[LL, D1], [D2, D3]]:
+// LL from llsrc (leading dim ldll), details from x; output S_{j+1} to dst
+template <typename T>
+__global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc, int64_t ldll, int64_t llb,
+                                                     const T* __restrict__ x, int M, T* __restrict__ dst, int64_t lddst,
+                                                     int64_t dstb, int j, Tables<T> tab, Geo G) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<T> st;
+  const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  const int n0 = 1 << j, n1 = 2 * n0;
+  const int TS = min(kTile, n1);
+  const int tiles = n1 / TS;
+  const int r0 = (blockIdx.x / tiles) * TS, c0 = (blockIdx.x % tiles) * TS;
+  const int64_t b = blockIdx.y;
+  const bool per = G.bd == UW_BOUNDARY_PERIODIC;
+  int dr0, dr1, dc0, dc1;
+  syn_dep(r0, r0 + TS, n0, G, dr0, dr1);
+  syn_dep(c0, c0 + TS, n0, G, dc0, dc1);
+  const int nr = dr1 - dr0, nc = dc1 - dc0;
+  // window of the four subbands: W[q][i][m], q = 0 LL, 1 D1, 2 D2, 3 D3
+  T* W = sm + off;
+  T* H = W + 4 * nr * nc;  // row-synthesised: H[half][i][c], half 0 = top rows, 1 = bottom rows
+  const T* xb = x + b * (int64_t)M * M;
+  const T* lb = llsrc + b * llb;
+  for (int e = tid; e < 4 * nr * nc; e += nthr) {
+    const int q = e / (nr * nc), rem = e % (nr * nc), i = rem / nc, m = rem % nc;
+    int gi = dr0 + i, gm = dc0 + m;
+    if (per) { gi &= n0 - 1; gm &= n0 - 1; }
+    T val;
+    if (q == 0) val = lb[(int64_t)gi * ldll + gm];
+    else if (q == 1) val = xb[(int64_t)gi * M + n0 + gm];
+    else if (q == 2) val = xb[(int64_t)(n0 + gi) * M + gm];
+    else val = xb[(int64_t)(n0 + gi) * M + n0 + gm];
+    W[e] = val;
+  }
+  __syncthreads();
+  // rows: for each window row i (top: LL|D1, bottom: D2|D3), outputs c in tile
+  for (int e = tid; e < 2 * nr * TS; e += nthr) {
+    const int half = e / (nr * TS), rem = e % (nr * TS), i = rem / TS, cc = rem % TS;
+    const T* lo = W + (half == 0 ? 0 : 2) * nr * nc + i * nc;
+    const T* hi = W + (half == 0 ? 1 : 3) * nr * nc + i * nc;
+    Win<T> wl{lo, dc0, nc, 1, n0, per}, wh{hi, dc0, nc, 1, n0, per};
+    H[e] = syn_one<T>(c0 + cc, n0, wl, wh, st, G);
+  }
+  __syncthreads();
+  // columns: outputs r in tile from the top (lo) and bottom (hi) H rows
+  for (int e = tid; e < TS * TS; e += nthr) {
+    const int rr = e / TS, cc = e % TS;
+    Win<T> wl{H + cc, dr0, nr, TS, n0, per}, wh{H + nr * TS + cc, dr0, nr, TS, n0, per};
+    dst[b * dstb + (int64_t)(r0 + rr) * lddst + c0 + cc] = syn_one<T>(r0 + rr, n0, wl, wh, st, G);
+  }
+}
+
+// analysis level j+1 -> j of the n1 x n1 block src (leading dim ldsrc): the
+// low-pass block to lldst (or to x when lldst is null), details to x
+template <typename T>
+__global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, int64_t ldsrc, int64_t srcb,
+                                                     T* __restrict__ x, int M, T* __restrict__ lldst, int64_t ldll,
+                                                     int64_t llb, int j, Tables<T> tab, Geo G) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<T> st;
+  const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  const int n0 = 1 << j, n1 = 2 * n0;
+  const int TS = min(kTile / 2, n0);  // output coefficients per dimension and quadrant
+  const int tiles = n0 / TS;
+  const int m0 = (blockIdx.x / tiles) * TS, k0 = (blockIdx.x % tiles) * TS;
+  const int64_t b = blockIdx.y;
+  const bool per = G.bd == UW_BOUNDARY_PERIODIC;
+  int sr0, sr1, sc0, sc1;
+  ana_dep(m0, m0 + TS, n0, G, sr0, sr1);
+  ana_dep(k0, k0 + TS, n0, G, sc0, sc1);
+  const int nr = sr1 - sr0, nc = sc1 - sc0;
+  T* S = sm + off;            // S[i][c] window of the level-(j+1) block
+  T* H = S + nr * nc;         // H[half][m][c]: column analysis, half 0 = low, 1 = high
+  const T* sb = src + b * srcb;
+  for (int e = tid; e < nr * nc; e += nthr) {
+    const int i = e / nc, c = e % nc;
+    int gi = sr0 + i, gc = sc0 + c;
+    if (per) { gi &= n1 - 1; gc &= n1 - 1; }
+    S[e] = sb[(int64_t)gi * ldsrc + gc];
+  }
+  __syncthreads();
+  // columns: for each window column c, low/high outputs m in [m0, m0 + TS)
+  for (int e = tid; e < TS * nc; e += nthr) {
+    const int mm = e / nc, c = e % nc;
+    Win<T> s{S + c, sr0, nr, nc, n1, per};
+    T lo, hi;
+    ana_one<T>(m0 + mm, n0, s, st, G, lo, hi);
+    H[mm * nc + c] = lo;
+    H[(TS + mm) * nc + c] = hi;
+  }
+  __syncthreads();
+  // rows: each H row -> low/high outputs k in [k0, k0 + TS)
+  T* xb = x + b * (int64_t)M * M;
+  for (int e = tid; e < 2 * TS * TS; e += nthr) {
+    const int row = e / TS, kk = e % TS;      // row < TS: low rows, else high rows
+    Win<T> s{H + row * nc, sc0, nc, 1, n1, per};
+    T lo, hi;
+    ana_one<T>(k0 + kk, n0, s, st, G, lo, hi);
+    const int mm = row < TS ? m0 + row : m0 + row - TS;
+    if (row < TS) {
+      if (lldst) lldst[b * llb + (int64_t)mm * ldll + k0 + kk] = lo;
+      else xb[(int64_t)mm * M + k0 + kk] = lo;
+      xb[(int64_t)mm * M + n0 + k0 + kk] = hi;
+    } else {
+      xb[(int64_t)(n0 + mm) * M + k0 + kk] = lo;
+      xb[(int64_t)(n0 + mm) * M + n0 + k0 + kk] = hi;
+    }
+  }
+}
+
+// All coarse levels of the 2D Mallat IDWT (forward) or DWT (adjoint) in one
+// cooperative launch: each level is a row pass and a column pass of the
+// per-output formulas spread over the whole grid, separated by grid-wide
+// barriers.  The detail blocks are read from (forward) or written to (adjoint)
+// the caller's coefficient array directly; XS holds the running low-pass
+// block (leading dimension Mh), XS2 the half-synthesised one.
+//   forward: levels jfrom .. jto-1, the LL block of level jfrom read from x
+//   adjoint: levels jto-1 .. jfrom, the LL block of level jfrom written to x
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_coop(const T* __restrict__ xin, T* xout, T* XS, T* XS2, int M,
+                                                     int Mh, int jfrom, int jto, int fwd, int batch, Tables<T> tab,
+                                                     Geo G) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  SmemTables<T> st;
+  stage_tables(tab, G, sm, st, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+  const int64_t MM = (int64_t)M * M, HH = (int64_t)Mh * Mh;
+  for (int it = 0; it < jto - jfrom; ++it) {
+    const int j = fwd ? jfrom + it : jto - 1 - it;
+    const int n0 = 1 << j, n1 = 2 * n0;
+    const int64_t tot = (int64_t)batch * n1 * n1, toth = (int64_t)batch * n1 * n0;
+    if (fwd) {
+      for (int64_t i = gt; i < tot; i += gs) {            // rows -> XS2
+        const int kk = (int)(i % n1);
+        const int64_t rr = i / n1;
+        const int r = (int)(rr % n1);
+        const int64_t b = rr / n1;
+        const T* xr = xin + b * MM + (int64_t)r * M;
+        const T* lop = (r < n0) ? ((j == jfrom) ? xr : XS + b * HH + (int64_t)r * Mh) : xr;
+        Plain<T> lo{lop}, hi{xr + n0};
+        XS2[b * HH + (int64_t)r * Mh + kk] = syn_one<T>(kk, n0, lo, hi, st, G);
+      }
+      grid.sync();
+      for (int64_t i = gt; i < tot; i += gs) {            // columns -> XS
+        const int c = (int)(i % n1);
+        const int64_t rr = i / n1;
+        const int kk = (int)(rr % n1);
+        const int64_t b = rr / n1;
+        Strided<T> lo{XS2 + b * HH + c, Mh}, hi{XS2 + b * HH + (int64_t)n0 * Mh + c, Mh};
+        XS[b * HH + (int64_t)kk * Mh + c] = syn_one<T>(kk, n0, lo, hi, st, G);
+      }
+      grid.sync();
+    } else {
+      for (int64_t i = gt; i < toth; i += gs) {           // columns of XS -> XS2
+        const int c = (int)(i % n1);
+        const int64_t rr = i / n1;
+        const int mm = (int)(rr % n0);
+        const int64_t b = rr / n0;
+        Strided<T> s{XS + b * HH + c, Mh};
+        T lo, hi;
+        ana_one<T>(mm, n0, s, st, G, lo, hi);
+        XS2[b * HH + (int64_t)mm * Mh + c] = lo;
+        XS2[b * HH + (int64_t)(n0 + mm) * Mh + c] = hi;
+      }
+      grid.sync();
+      for (int64_t i = gt; i < toth; i += gs) {           // rows of XS2 -> XS / x
+        const int mm = (int)(i % n0);
+        const int64_t rr = i / n0;
+        const int r = (int)(rr % n1);
+        const int64_t b = rr / n1;
+        Plain<T> s{XS2 + b * HH + (int64_t)r * Mh};
+        T lo, hi;
+        ana_one<T>(mm, n0, s, st, G, lo, hi);
+        T* xr = xout + b * MM + (int64_t)r * M;
+        if (r < n0 && j > jfrom) XS[b * HH + (int64_t)r * Mh + mm] = lo;
+        else xr[mm] = lo;
+        xr[n0 + mm] = hi;
+      }
+      grid.sync();
+    }
+  }
+}
+
 // All small coarse levels of the 2D Mallat IDWT / DWT in one CTA: the n x n
 // top-left block (n <= 128 for FP32) stays in shared memory across levels; one
 // level is a row pass and a column pass of the per-output formulas.
@@ -440,6 +685,50 @@ __global__ void __launch_bounds__(1024) k_coarse_small(T* buf, int64_t ld, int64
   for (int i = tid; i < n * n; i += nthr) g[(int64_t)(i / n) * ld + i % n] = A[(i / n) * ls + i % n];
 }
 
+// FP32 transpose with 64 x 64 tiles and 16-byte global accesses; rows,
+// cols, br and bc are multiples of 64, so a tile is entirely inside or
+// outside the spliced block (same semantics as k_transpose).
+__global__ void __launch_bounds__(256) k_transpose64(const float* __restrict__ in, float* __restrict__ out, int rows,
+                                                     int cols, int64_t in_batch, int64_t out_batch,
+                                                     const float* __restrict__ alt, int64_t alt_batch,
+                                                     float* __restrict__ altout, int br, int bc, int ldalt) {
+  __shared__ float tile[64][65];
+  const int64_t b = blockIdx.z;
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int t = threadIdx.x, c4 = t & 15, rw = t >> 4;
+  const bool from_alt = alt && r0 < br && c0 < bc;
+  float4 v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + rw + 16 * i;
+    const float* src = from_alt ? alt + b * alt_batch + (int64_t)r * ldalt + c0
+                                : in + b * in_batch + (int64_t)r * cols + c0;
+    v[i] = __ldg(reinterpret_cast<const float4*>(src) + c4);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = rw + 16 * i;
+    tile[r][4 * c4 + 0] = v[i].x;
+    tile[r][4 * c4 + 1] = v[i].y;
+    tile[r][4 * c4 + 2] = v[i].z;
+    tile[r][4 * c4 + 3] = v[i].w;
+  }
+  __syncthreads();
+  const bool to_alt = altout && c0 < br && r0 < bc;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int orow = rw + 16 * i;  // output row c0 + orow, columns r0 + 4 c4 ..
+    float4 w;
+    w.x = tile[4 * c4 + 0][orow];
+    w.y = tile[4 * c4 + 1][orow];
+    w.z = tile[4 * c4 + 2][orow];
+    w.w = tile[4 * c4 + 3][orow];
+    float* dst = to_alt ? altout + b * alt_batch + (int64_t)(c0 + orow) * ldalt + r0
+                        : out + b * out_batch + (int64_t)(c0 + orow) * rows + r0;
+    reinterpret_cast<float4*>(dst)[c4] = w;
+  }
+}
+
 template <typename T>
 __global__ void k_copy_block(const T* __restrict__ in, int64_t ldin, int64_t in_batch, T* __restrict__ out,
                              int64_t ldout, int64_t out_batch, int rows, int cols, int batch) {
@@ -477,7 +766,7 @@ static bool line_fits(const Plan& P) { return line_smem<T>(P) <= kSmemMax; }
 
 // largest level whose 2^j x 2^j block (two copies) fits one CTA's shared memory
 template <typename T>
-static int small_top() { return sizeof(T) == 4 ? 7 : 6; }
+static int small_top() { return 6; }
 
 template <typename T>
 static size_t coarse_smem(const Plan& P, int jto) {
@@ -670,6 +959,112 @@ void launch_line<float>(bool fwd, const Plan& P, const Geo& G, const float* in, 
   }
 }
 
+template <typename T>
+static void launch_coarse(const Plan& P, const Geo& G, const T* xin, T* xout, T* XS, T* XS2, int batch, bool fwd,
+                          Launcher& L) {
+  const size_t sm = sizeof(T) * (size_t)table_count(G);
+  set_smem<T>((const void*)k_coarse_coop<T>, sm);
+  int per_sm = 0, nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_coop<T>, 256, sm);
+  const int64_t work = (int64_t)batch * (P.M / 2) * (P.M / 2);
+  int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * nsm, (work + 255) / 256));
+  int M = P.M, Mh = P.M / 2, jfrom = P.J0, jto = P.R - 1, f = fwd ? 1 : 0;
+  Tables<T> tb = tabs<T>(P);
+  Geo g = G;
+  void* args[] = {(void*)&xin, (void*)&xout, (void*)&XS, (void*)&XS2, &M, &Mh, &jfrom, &jto, &f, &batch, &tb, &g};
+  cudaLaunchCooperativeKernel((const void*)k_coarse_coop<T>, dim3(grid), dim3(256), args, sm, L.s);
+  L.check();
+}
+
+// coarse levels J0 .. R-2 of the 2D Mallat transform, one fused kernel per
+// level.  forward: S_{J0} and the details from x, S_{R-1} ends in XS;
+// adjoint: S_{R-1} from XS, the low-pass block and details of every level
+// end in x.  XS and XS2 (Mh x Mh per instance) alternate as level buffers.
+static int coarse_tile_extent(const Geo& G, int j, bool syn) {
+  const int n0 = 1 << j, n1 = 2 * n0;
+  const int TS = syn ? std::min(kTile, n1) : std::min(kTile / 2, n0);
+  const int span = syn ? n1 : n0;
+  int worst = 0;
+  for (int a = 0; a < span; a += TS) {
+    int lo, hi;
+    if (syn) syn_dep(a, a + TS, n0, G, lo, hi);
+    else ana_dep(a, a + TS, n0, G, lo, hi);
+    worst = std::max(worst, hi - lo);
+  }
+  return worst;
+}
+
+template <typename T>
+static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xout, T* XS, T* XS2, int batch,
+                                 bool fwd, Launcher& L) {
+  const int M = P.M, Mh = M / 2;
+  const int nl = P.R - 1 - P.J0;
+  const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
+  const size_t tabn = (size_t)table_count(G);
+  for (int it = 0; it < nl; ++it) {
+    const int j = fwd ? P.J0 + it : P.R - 2 - it;
+    const int n0 = 1 << j, n1 = 2 * n0;
+    const int w = coarse_tile_extent(G, j, fwd);
+    if (fwd) {
+      const int TS = std::min(kTile, n1), tiles = n1 / TS;
+      const size_t sm = sizeof(T) * (tabn + 4 * (size_t)w * w + 2 * (size_t)w * TS);
+      const T* src = it == 0 ? x : ((nl - it) % 2 == 0 ? XS : XS2);
+      const int64_t ld = it == 0 ? M : Mh, sb = it == 0 ? MM : HH;
+      T* dst = (nl - 1 - it) % 2 == 0 ? XS : XS2;
+      char name[32];
+      snprintf(name, sizeof name, "idwt2d_level_j%d", j);
+      L.pre(name, sizeof(T) * (double)batch * (4.0 * n0 * n0 + (double)n1 * n1));
+      set_smem<T>((const void*)k_syn2d_level<T>, sm);
+      k_syn2d_level<T><<<dim3(tiles * tiles, batch), 256, sm, L.s>>>(src, ld, sb, x, M, dst, Mh, HH, j, tabs<T>(P), G);
+    } else {
+      const int TS = std::min(kTile / 2, n0), tiles = n0 / TS;
+      const size_t sm = sizeof(T) * (tabn + (size_t)w * w + 2 * (size_t)TS * w);
+      const T* src = it % 2 == 0 ? XS : XS2;
+      T* dst = it == nl - 1 ? nullptr : (it % 2 == 0 ? XS2 : XS);
+      char name[32];
+      snprintf(name, sizeof name, "dwt2d_level_j%d", j);
+      L.pre(name, sizeof(T) * (double)batch * (4.0 * n0 * n0 + (double)n1 * n1));
+      set_smem<T>((const void*)k_ana2d_level<T>, sm);
+      k_ana2d_level<T><<<dim3(tiles * tiles, batch), 256, sm, L.s>>>(src, Mh, HH, xout, M, dst, Mh, HH, j, tabs<T>(P),
+                                                                     G);
+    }
+    L.check();
+  }
+}
+
+// transpose dispatcher: the 64 x 64 FP32 kernel where shapes allow
+template <typename T>
+static void launch_transpose(const T* in, T* out, int rows, int cols, int64_t in_batch, int64_t out_batch,
+                             const T* alt, int64_t alt_batch, T* altout, int br, int bc, int ldalt, int batch,
+                             Launcher& L) {
+  dim3 tb(32, 8);
+  dim3 tg((cols + 31) / 32, (rows + 31) / 32, batch);
+  k_transpose<T><<<tg, tb, 0, L.s>>>(in, out, rows, cols, in_batch, out_batch, alt, alt_batch, altout, br, bc, ldalt);
+}
+
+template <>
+void launch_transpose<float>(const float* in, float* out, int rows, int cols, int64_t in_batch, int64_t out_batch,
+                             const float* alt, int64_t alt_batch, float* altout, int br, int bc, int ldalt, int batch,
+                             Launcher& L) {
+  // 16-byte vector accesses: every base pointer and every stride must keep
+  // 16-byte alignment, otherwise the scalar kernel runs
+  auto al16 = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+  const bool ok = rows % 64 == 0 && cols % 64 == 0 && br % 64 == 0 && bc % 64 == 0 && ldalt % 4 == 0 &&
+                  in_batch % 4 == 0 && out_batch % 4 == 0 && alt_batch % 4 == 0 && al16(in) && al16(out) &&
+                  (!alt || al16(alt)) && (!altout || al16(altout));
+  if (!ok) {
+    dim3 tb(32, 8);
+    dim3 tg((cols + 31) / 32, (rows + 31) / 32, batch);
+    k_transpose<float><<<tg, tb, 0, L.s>>>(in, out, rows, cols, in_batch, out_batch, alt, alt_batch, altout, br, bc,
+                                           ldalt);
+    return;
+  }
+  dim3 tg(cols / 64, rows / 64, batch);
+  k_transpose64<<<tg, 256, 0, L.s>>>(in, out, rows, cols, in_batch, out_batch, alt, alt_batch, altout, br, bc, ldalt);
+}
+
 // 1D, the whole line in shared memory.
 template <typename T>
 static void fwd1d_smem(const Plan& P, const T* x, T* y, int batch, Launcher& L) {
@@ -789,37 +1184,10 @@ static void fwd2d(const Plan& P, const T* x, T* y, int batch, T* work, Launcher&
   T* V = VT + (size_t)batch * M * N;
   const bool coarse = (P.R - 1 > P.J0);
   if (coarse) {
-    L.pre("copy_coarse_in", e * 2.0 * batch * Mh * Mh);
-    k_copy_block<T><<<grid_for((int64_t)batch * Mh * Mh), 256, 0, L.s>>>(x, M, MM, XS, Mh, (int64_t)Mh * Mh, Mh, Mh, batch);
-    L.check();
-    // small levels in one CTA per instance, larger ones level by level
-    const int jsm = std::min(P.R - 1, small_top<T>());
-    int j = P.J0;
-    if (jsm > P.J0) {
-      size_t sm = coarse_smem<T>(P, jsm);
-      set_smem<T>((const void*)k_coarse_small<T>, sm);
-      L.pre("idwt2d_small", e * 4.0 * batch * (double)(1 << jsm) * (1 << jsm));
-      k_coarse_small<T><<<batch, 1024, sm, L.s>>>(XS, Mh, (int64_t)Mh * Mh, P.J0, jsm, 1, tabs<T>(P), G);
-      L.check();
-      j = jsm;
-    }
-    for (; j < P.R - 1; ++j) {
-      int n0 = 1 << j, n1 = 2 * n0;
-      LineGeom rows{Mh, 1, (int64_t)Mh * Mh, n1, 0};
-      L.pre("idwt2d_rows", e * 2.0 * batch * n1 * n1);
-      k_syn_level<T><<<grid_for((int64_t)batch * n1 * n1), 256, 0, L.s>>>(XS, XS2, n0, tabs<T>(P), G, rows, rows, batch);
-      L.check();
-      LineGeom cols{1, Mh, (int64_t)Mh * Mh, n1, 1};
-      L.pre("idwt2d_cols", e * 2.0 * batch * n1 * n1);
-      k_syn_level<T><<<grid_for((int64_t)batch * n1 * n1), 256, 0, L.s>>>(XS2, XS, n0, tabs<T>(P), G, cols, cols, batch);
-      L.check();
-    }
+    launch_coarse_levels<T>(P, G, x, nullptr, XS, XS2, batch, true, L);
   }
-  dim3 tb(32, 8);
-  dim3 tg((M + 31) / 32, (M + 31) / 32, batch);
   L.pre("transpose_in", e * 2.0 * batch * MM);
-  k_transpose<T><<<tg, tb, 0, L.s>>>(x, XT, M, M, MM, MM, coarse ? XS : nullptr, (int64_t)Mh * Mh, nullptr,
-                                     Mh, Mh, Mh);
+  launch_transpose<T>(x, XT, M, M, MM, MM, coarse ? XS : nullptr, (int64_t)Mh * Mh, nullptr, Mh, Mh, Mh, batch, L);
   L.check();
   LineIO io{};
   io.in_stride = M; io.out_stride = N; io.lines = M; io.in_batch = MM; io.out_batch = (int64_t)M * N;
@@ -827,9 +1195,8 @@ static void fwd2d(const Plan& P, const T* x, T* y, int batch, T* work, Launcher&
   L.pre("line_fwd_dim1", e * (double)batch * (MM + (double)M * N));
   launch_line<T>(true, P, G, XT, VT, io, batch * M, L);
   L.check();
-  dim3 tg2((N + 31) / 32, (M + 31) / 32, batch);
   L.pre("transpose_mid_fwd", e * 2.0 * batch * M * N);
-  k_transpose<T><<<tg2, tb, 0, L.s>>>(VT, V, M, N, (int64_t)M * N, (int64_t)M * N, nullptr, 0, nullptr, 0, 0, 1);
+  launch_transpose<T>(VT, V, M, N, (int64_t)M * N, (int64_t)M * N, nullptr, 0, nullptr, 0, 0, 4, batch, L);
   L.check();
   LineIO io2{};
   io2.in_stride = M; io2.lines = N; io2.in_batch = (int64_t)N * M; io2.out_batch = P.m;
@@ -859,10 +1226,8 @@ static void adj2d(const Plan& P, const T* y, T* x, int batch, T* work, Launcher&
   L.pre("line_adj_dim2_scatter", e * (double)batch * ((double)N * M + P.m) + 8.0 * P.words);
   launch_line<T>(false, P, G, y, Qm, io, batch * N, L);
   L.check();
-  dim3 tb(32, 8);
-  dim3 tg((M + 31) / 32, (N + 31) / 32, batch);
   L.pre("transpose_mid_adj", e * 2.0 * batch * M * N);
-  k_transpose<T><<<tg, tb, 0, L.s>>>(Qm, QT, N, M, (int64_t)N * M, (int64_t)N * M, nullptr, 0, nullptr, 0, 0, 1);
+  launch_transpose<T>(Qm, QT, N, M, (int64_t)N * M, (int64_t)N * M, nullptr, 0, nullptr, 0, 0, 4, batch, L);
   L.check();
   LineIO io2{};
   io2.in_stride = N; io2.out_stride = M; io2.lines = M; io2.in_batch = (int64_t)M * N; io2.out_batch = MM;
@@ -870,35 +1235,11 @@ static void adj2d(const Plan& P, const T* y, T* x, int batch, T* work, Launcher&
   L.pre("line_adj_dim1", e * (double)batch * (MM + (double)M * N));
   launch_line<T>(false, P, G, QT, XT, io2, batch * M, L);
   L.check();
-  dim3 tg2((M + 31) / 32, (M + 31) / 32, batch);
   L.pre("transpose_out", e * 2.0 * batch * MM);
-  k_transpose<T><<<tg2, tb, 0, L.s>>>(XT, x, M, M, MM, MM, nullptr, (int64_t)Mh * Mh, coarse ? XS : nullptr,
-                                      Mh, Mh, Mh);
+  launch_transpose<T>(XT, x, M, M, MM, MM, nullptr, (int64_t)Mh * Mh, coarse ? XS : nullptr, Mh, Mh, Mh, batch, L);
   L.check();
   if (coarse) {
-    const int jsm = std::min(P.R - 1, small_top<T>());
-    const int jstop = jsm > P.J0 ? jsm : P.J0;
-    for (int j = P.R - 2; j >= jstop; --j) {
-      int n0 = 1 << j, n1 = 2 * n0;
-      LineGeom cols{1, Mh, (int64_t)Mh * Mh, n1, 1};
-      L.pre("dwt2d_cols", e * 2.0 * batch * n1 * n1);
-      k_ana_level<T><<<grid_for((int64_t)batch * n1 * n0), 256, 0, L.s>>>(XS, XS2, n0, tabs<T>(P), G, cols, cols, batch);
-      L.check();
-      LineGeom rows{Mh, 1, (int64_t)Mh * Mh, n1, 0};
-      L.pre("dwt2d_rows", e * 2.0 * batch * n1 * n1);
-      k_ana_level<T><<<grid_for((int64_t)batch * n1 * n0), 256, 0, L.s>>>(XS2, XS, n0, tabs<T>(P), G, rows, rows, batch);
-      L.check();
-    }
-    if (jsm > P.J0) {
-      size_t sm = coarse_smem<T>(P, jsm);
-      set_smem<T>((const void*)k_coarse_small<T>, sm);
-      L.pre("dwt2d_small", e * 4.0 * batch * (double)(1 << jsm) * (1 << jsm));
-      k_coarse_small<T><<<batch, 1024, sm, L.s>>>(XS, Mh, (int64_t)Mh * Mh, P.J0, jsm, 0, tabs<T>(P), G);
-      L.check();
-    }
-    L.pre("copy_coarse_out", e * 2.0 * batch * Mh * Mh);
-    k_copy_block<T><<<grid_for((int64_t)batch * Mh * Mh), 256, 0, L.s>>>(XS, Mh, (int64_t)Mh * Mh, x, M, MM, Mh, Mh, batch);
-    L.check();
+    launch_coarse_levels<T>(P, G, nullptr, x, XS, XS2, batch, false, L);
   }
 }
 
@@ -998,9 +1339,11 @@ static int host_call(const uw_plan* P, int prec, bool fwd, const void* in, void*
   const int64_t coeffs = P->d == 1 ? (int64_t)P->M : (int64_t)P->M * P->M;
   const size_t nin = (size_t)batch * (size_t)(fwd ? coeffs : P->m);
   const size_t nout = (size_t)batch * (size_t)(fwd ? P->m : coeffs);
+  // input at the start of the staging area, output at the next 256-byte
+  // boundary after the largest possible input
+  auto up256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
   char* din = (char*)P->d_stage;
-  char* dout = din + (size_t)batch * (size_t)coeffs * sizeof(double);
-  if (!fwd) dout = din + (size_t)batch * (size_t)P->m * sizeof(double);
+  char* dout = din + up256((size_t)batch * (size_t)(fwd ? coeffs : P->m) * sizeof(double));
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemcpyAsync(din, in, nin * e, cudaMemcpyHostToDevice, s) != cudaSuccess) {
     uw::set_error(UW_ERR_CUDA, "host-to-device copy failed");

@@ -81,6 +81,44 @@ __device__ __forceinline__ void load_line(const float* __restrict__ src, float* 
   for (int i = 0; i < K; ++i) dst[p32(tid + i * nthr)] = a[i];
 }
 
+// position of the (r+1)-th set bit of x (0 <= r < popc(x)), branch-free
+__device__ __forceinline__ int select_bit(unsigned x, int r) {
+  int pos = 0, c;
+  c = __popc(x & 0xFFFFu); if (r >= c) { r -= c; x >>= 16; pos += 16; }
+  c = __popc(x & 0xFFu);   if (r >= c) { r -= c; x >>= 8;  pos += 8; }
+  c = __popc(x & 0xFu);    if (r >= c) { r -= c; x >>= 4;  pos += 4; }
+  c = __popc(x & 0x3u);    if (r >= c) { r -= c; x >>= 2;  pos += 2; }
+  c = x & 1u;              if (r >= c) { pos += 1; }
+  return pos;
+}
+
+// The sampled sequency indices of one mask row, one sample per thread: the
+// row's words and word prefixes are staged in shared memory, a binary search
+// finds the word of sample j and select_bit its bit.  Returns the row's first
+// packed position r0 and its sample count; fills smask / spre.
+__device__ __forceinline__ void stage_row(const LineIO& io, int mrow, int rows, uint32_t* smask, int* spre,
+                                          int64_t& r0, int& cnt, int tid, int nthr) {
+  const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
+  const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
+  r0 = pf[0];
+  const int64_t r1 = (mrow + 1 < rows) ? (int64_t)io.prefix[(int64_t)(mrow + 1) * io.wpr] : io.m;
+  cnt = (int)(r1 - r0);
+  for (int w = tid; w < io.wpr; w += nthr) {
+    smask[w] = mk[w];
+    spre[w] = (int)(pf[w] - r0);
+  }
+}
+
+__device__ __forceinline__ int sample_index(const uint32_t* smask, const int* spre, int wpr, int j) {
+  int lo = 0, hi = wpr - 1;  // last word with spre[w] <= j
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (spre[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo * 32 + select_bit(smask[lo], j - spre[lo]);
+}
+
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
@@ -95,7 +133,10 @@ __global__ void __launch_bounds__(512) k_line2_fwd(const float* __restrict__ in,
   float* sIn = sm + off;
   float* sS = sIn + p32len(G.M);
   float* v = sS + p32len(G.M);
+  uint32_t* smask = reinterpret_cast<uint32_t*>(v + padlen(G.N));
+  int* spre = reinterpret_cast<int*>(smask + io.wpr);
   const int M = G.M, N = G.N, p = G.p;
+  const bool per = G.bd == UW_BOUNDARY_PERIODIC;
   const int line = blockIdx.x % io.lines;
   const int64_t b = blockIdx.x / io.lines;
   const int drow = io.seq_rows ? seqrow(line, G.L) : line;
@@ -103,12 +144,12 @@ __global__ void __launch_bounds__(512) k_line2_fwd(const float* __restrict__ in,
   load_line<16 / Q>(src, sIn, M, tid, nthr);
   __syncthreads();
 
-  // (a) synthesis: levels jlev .. R-2 per output, level R-1 register-blocked
+  // (a) synthesis: levels jlev .. R-2 per output (1D only), level R-1 blocked
   const int nlev = G.R - io.jlev;
   if (nlev == 0) {
     for (int k = tid; k < M; k += nthr) sS[p32(k)] = sIn[p32(k)];
   } else {
-    const int g = nlev - 1;  // per-output levels; their last output lands in v
+    const int g = nlev - 1;
     float* lo_buf = sIn;
     float* outb = (g & 1) ? v : sS;
     for (int j = io.jlev; j < G.R - 1; ++j) {
@@ -120,33 +161,45 @@ __global__ void __launch_bounds__(512) k_line2_fwd(const float* __restrict__ in,
       outb = (outb == v) ? sS : v;
     }
     const int n0 = M / 2;
-    Pad32<float> lo{lo_buf, 0}, hi{sIn, n0};
-    constexpr int B = 8 / Q;                 // output pairs per thread
+    constexpr int B = 8 / Q;  // output pairs per thread
     const int i0 = tid * B;
-    const bool fast = (G.bd == UW_BOUNDARY_PERIODIC)
-                          ? (i0 - PM / 2 >= 0 && i0 + B - 1 + PM / 2 <= n0 - 1)
-                          : (i0 - PM / 2 >= p && i0 + B - 1 + PM / 2 <= n0 - p - 1 && 2 * i0 >= G.Lb &&
-                             2 * (i0 + B) - 1 <= M - 1 - G.Lb);
-    if (fast) {
-      float wl[B + PM], wh[B + PM];
+    // interior formula on a masked (VMP) or wrapped (periodic) window
+    float wl[B + PM], wh[B + PM];
 #pragma unroll
-      for (int w = 0; w < B + PM; ++w) {
-        wl[w] = lo[i0 - PM / 2 + w];
-        wh[w] = hi[i0 - PM / 2 + w];
-      }
-#pragma unroll
-      for (int bb = 0; bb < B; ++bb)
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          float acc = 0.f;
-#pragma unroll
-          for (int d = -PM / 2; d <= PM / 2; ++d)
-            acc += ft.hp[f][d + PM / 2] * wl[bb - d + PM / 2] + ft.gp[f][d + PM / 2] * wh[bb - d + PM / 2];
-          sS[p32(2 * (i0 + bb) + f)] = acc;
-        }
-    } else {
-      for (int kk = 2 * i0; kk < 2 * (i0 + B); ++kk) sS[p32(kk)] = syn_one<float>(kk, n0, lo, hi, st, G);
+    for (int w = 0; w < B + PM; ++w) {
+      int m = i0 - PM / 2 + w;
+      bool ok = per || (m >= p && m <= n0 - p - 1);
+      int mi = per ? (m & (n0 - 1)) : m;
+      wl[w] = ok ? lo_buf[p32(mi)] : 0.f;
+      wh[w] = ok ? sIn[p32(n0 + mi)] : 0.f;
     }
+    float acc[2 * B];
+#pragma unroll
+    for (int bb = 0; bb < B; ++bb)
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        float a = 0.f;
+#pragma unroll
+        for (int d = -PM / 2; d <= PM / 2; ++d)
+          a += ft.hp[f][d + PM / 2] * wl[bb - d + PM / 2] + ft.gp[f][d + PM / 2] * wh[bb - d + PM / 2];
+        acc[2 * bb + f] = a;
+      }
+    // boundary blocks of the VMP synthesis (Sec. 3.2)
+    if (!per && (2 * i0 < G.Lb || 2 * (i0 + B) > M - G.Lb)) {
+#pragma unroll
+      for (int u = 0; u < 2 * B; ++u) {
+        const int k = 2 * i0 + u;
+        if (k < G.Lb)
+          for (int mm = 0; mm < p; ++mm)
+            acc[u] += st.PL[mm * G.Lb + k] * lo_buf[p32(mm)] + st.QL[mm * G.Lb + k] * sIn[p32(n0 + mm)];
+        const int c = M - 1 - k;
+        if (c < G.Lb)
+          for (int r = 0; r < p; ++r)
+            acc[u] += st.PR[r * G.Lb + c] * lo_buf[p32(n0 - 1 - r)] + st.QR[r * G.Lb + c] * sIn[p32(2 * n0 - 1 - r)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2 * B; ++u) sS[p32(2 * i0 + u)] = acc[u];
   }
   __syncthreads();
 
@@ -156,52 +209,53 @@ __global__ void __launch_bounds__(512) k_line2_fwd(const float* __restrict__ in,
     constexpr int BI = 16 / Q;
     const int k0 = 16 * tid;
     const int i0 = k0 / Q;
-    Pad32<float> s{sS, 0};
-    const bool fast = (G.bd == UW_BOUNDARY_PERIODIC)
-                          ? (i0 - PM + 1 >= 0 && i0 + BI + PM - 2 <= M - 1)
-                          : (i0 - PM + 1 >= p && i0 + BI + PM - 2 <= M - p - 1 && k0 >= G.ntap &&
-                             k0 + 15 <= N - 1 - G.ntap);
-    float a[16];
-    if (fast) {
-      float ws[BI + 2 * PM - 2];
+    float ws[BI + 2 * PM - 2];
 #pragma unroll
-      for (int w = 0; w < BI + 2 * PM - 2; ++w) ws[w] = s[i0 - PM + 1 + w];
+    for (int w = 0; w < BI + 2 * PM - 2; ++w) {
+      int m = i0 - PM + 1 + w;
+      bool ok = per || (m >= p && m <= M - p - 1);
+      ws[w] = ok ? sS[p32(per ? (m & (M - 1)) : m)] : 0.f;
+    }
+    float a[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      float acc = 0.f;
+#pragma unroll
+      for (int d = -(PM - 1); d <= PM - 1; ++d) acc += ft.tp[u % Q][d + PM - 1] * ws[u / Q - d + PM - 1];
+      a[u] = acc;
+    }
+    // boundary rows of T (cell integrals of the VMP edge functions)
+    if (!per && (k0 < G.ntap || k0 + 16 > N - G.ntap)) {
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        float acc = 0.f;
-#pragma unroll
-        for (int d = -(PM - 1); d <= PM - 1; ++d) acc += ft.tp[u % Q][d + PM - 1] * ws[u / Q - d + PM - 1];
-        a[u] = sc * acc;
+        const int k = k0 + u;
+        if (k < G.ntap)
+          for (int mm = 0; mm < p; ++mm) a[u] += st.EL[mm * G.ntap + k] * sS[p32(mm)];
+        const int kk = N - 1 - k;
+        if (kk < G.ntap)
+          for (int r = 0; r < p; ++r) a[u] += st.ER[r * G.ntap + kk] * sS[p32(M - 1 - r)];
       }
-    } else {
-#pragma unroll
-      for (int u = 0; u < 16; ++u) a[u] = sc * up_one<float>(k0 + u, s, st, G);
     }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) a[u] *= sc;
     fwht16(a);
 #pragma unroll
     for (int u = 0; u < 16; ++u) v[padi(k0 + u)] = a[u];
   }
-  __syncthreads();
-  fwht_from(v, G.L, 4, tid, nthr);
-
-  // (d) store natural order, or gather the sampled sequency indices
-  if (io.mode == 0) {
+  if (io.mode == 1) {
+    int64_t r0;
+    int cnt;
+    stage_row(io, io.mask_rows == 1 ? 0 : line, io.mask_rows, smask, spre, r0, cnt, tid, nthr);
+    __syncthreads();
+    fwht_from(v, G.L, 4, tid, nthr);
+    // (d) gather: one sample per thread, coalesced writes of y
+    float* y = out + b * io.m + r0;
+    for (int j = tid; j < cnt; j += nthr) y[j] = v[padi(seqrow(sample_index(smask, spre, io.wpr, j), G.L))];
+  } else {
+    __syncthreads();
+    fwht_from(v, G.L, 4, tid, nthr);
     float* dst = out + b * io.out_batch + (int64_t)line * io.out_stride;
     for (int k = tid; k < N; k += nthr) dst[k] = v[padi(k)];
-  } else {
-    const int mrow = io.mask_rows == 1 ? 0 : line;
-    const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
-    const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
-    float* y = out + b * io.m;
-    for (int w = tid; w < io.wpr; w += nthr) {
-      uint32_t bits = mk[w];
-      int64_t pos = pf[w];
-      while (bits) {
-        int bb = __ffs(bits) - 1;
-        bits &= bits - 1;
-        y[pos++] = v[padi(seqrow(w * 32 + bb, G.L))];
-      }
-    }
   }
 }
 
@@ -219,7 +273,10 @@ __global__ void __launch_bounds__(512) k_line2_adj(const float* __restrict__ in,
   float* sIn = sm + off;
   float* sS = sIn + p32len(G.M);
   float* v = sS + p32len(G.M);
+  uint32_t* smask = reinterpret_cast<uint32_t*>(v + padlen(G.N));
+  int* spre = reinterpret_cast<int*>(smask + io.wpr);
   const int M = G.M, N = G.N, p = G.p;
+  const bool per = G.bd == UW_BOUNDARY_PERIODIC;
   const int line = blockIdx.x % io.lines;
   const int64_t b = blockIdx.x / io.lines;
   if (io.mode == 0) {
@@ -230,31 +287,18 @@ __global__ void __launch_bounds__(512) k_line2_adj(const float* __restrict__ in,
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[padi(tid + i * nthr)] = a[i];
   } else {
+    // scatter: one sample per thread, coalesced reads of y
+    int64_t r0;
+    int cnt;
+    stage_row(io, io.mask_rows == 1 ? 0 : line, io.mask_rows, smask, spre, r0, cnt, tid, nthr);
     for (int k = tid; k < padlen(N); k += nthr) v[k] = 0.f;
     __syncthreads();
-    const int mrow = io.mask_rows == 1 ? 0 : line;
-    const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
-    const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
-    const float* y = in + b * io.m;
-    for (int w = tid; w < io.wpr; w += nthr) {
-      const uint32_t bits = mk[w];
-      const int64_t pos = pf[w];
-      // the word's samples are contiguous in y: issue all loads, then store
-#pragma unroll
-      for (int g8 = 0; g8 < 32; g8 += 8) {
-        float val[8];
-#pragma unroll
-        for (int bp = 0; bp < 8; ++bp)
-          val[bp] = ((bits >> (g8 + bp)) & 1u) ? __ldg(y + pos + __popc(bits & ((1u << (g8 + bp)) - 1u))) : 0.f;
-#pragma unroll
-        for (int bp = 0; bp < 8; ++bp)
-          if ((bits >> (g8 + bp)) & 1u) v[padi(seqrow(w * 32 + g8 + bp, G.L))] = val[bp];
-      }
-    }
+    const float* y = in + b * io.m + r0;
+    for (int j = tid; j < cnt; j += nthr) v[padi(seqrow(sample_index(smask, spre, io.wpr, j), G.L))] = __ldg(y + j);
   }
   __syncthreads();
-  // the Hadamard stages commute: bits 4.. in shared memory, bits 0..3 last in
-  // registers
+  // the Hadamard stages commute: bits 4.. in shared memory, bits 0..3 in
+  // registers right before T^T
   fwht_from(v, G.L, 4, tid, nthr);
   {
     float a[16];
@@ -273,27 +317,43 @@ __global__ void __launch_bounds__(512) k_line2_adj(const float* __restrict__ in,
     constexpr int BM = 16 / Q;
     constexpr int W = Q * (BM + 2 * PM - 2);
     const int m0 = tid * BM;
-    const bool fast = (G.bd == UW_BOUNDARY_PERIODIC)
-                          ? (m0 - PM + 1 >= 0 && m0 + BM + PM - 2 <= M - 1)
-                          : (m0 >= p && m0 + BM - 1 <= M - p - 1 && m0 - PM + 1 >= 0 && m0 + BM + PM - 2 <= M - 1);
-    if (fast) {
-      float wv[W];
-      const int base = Q * (m0 - PM + 1);
+    const int base = Q * (m0 - PM + 1);
+    float wv[W];
 #pragma unroll
-      for (int w = 0; w < W; ++w) wv[w] = v[padi(base + w)];
+    for (int w = 0; w < W; ++w) {
+      int k = base + w;
+      bool ok = per || (k >= 0 && k < N);
+      wv[w] = ok ? v[padi(per ? (k & (N - 1)) : k)] : 0.f;
+    }
+    float acc[BM];
+#pragma unroll
+    for (int bb = 0; bb < BM; ++bb) {
+      float a = 0.f;
+#pragma unroll
+      for (int d = -(PM - 1); d <= PM - 1; ++d)
+#pragma unroll
+        for (int f = 0; f < Q; ++f) a += ft.tp[f][d + PM - 1] * wv[Q * (bb + d + PM - 1) + f];
+      acc[bb] = a;
+    }
+    // VMP edge columns: the transposed boundary rows replace the interior sum
+    if (!per && (m0 < p || m0 + BM > M - p)) {
 #pragma unroll
       for (int bb = 0; bb < BM; ++bb) {
-        float acc = 0.f;
-#pragma unroll
-        for (int d = -(PM - 1); d <= PM - 1; ++d)
-#pragma unroll
-          for (int f = 0; f < Q; ++f) acc += ft.tp[f][d + PM - 1] * wv[Q * (bb + d + PM - 1) + f];
-        sS[p32(m0 + bb)] = sc * acc;
+        const int m = m0 + bb;
+        if (m < p) {
+          float a = 0.f;
+          for (int k = 0; k < G.ntap; ++k) a += st.EL[m * G.ntap + k] * v[padi(k)];
+          acc[bb] = a;
+        } else if (m >= M - p) {
+          const int r = M - 1 - m;
+          float a = 0.f;
+          for (int kk = 0; kk < G.ntap; ++kk) a += st.ER[r * G.ntap + kk] * v[padi(N - 1 - kk)];
+          acc[bb] = a;
+        }
       }
-    } else {
-      Padded<float> vv{v};
-      for (int m = m0; m < m0 + BM; ++m) sS[p32(m)] = sc * upT_one<float>(m, vv, st, G);
     }
+#pragma unroll
+    for (int bb = 0; bb < BM; ++bb) sS[p32(m0 + bb)] = sc * acc[bb];
   }
   __syncthreads();
 
@@ -306,39 +366,62 @@ __global__ void __launch_bounds__(512) k_line2_adj(const float* __restrict__ in,
     float* lo_out = (nlev == 1) ? sIn : v;
     constexpr int BA = 8 / Q;
     const int m0 = tid * BA;
-    Pad32<float> s{sS, 0};
-    const bool fast = (G.bd == UW_BOUNDARY_PERIODIC)
-                          ? (m0 - PM / 2 >= 0 && m0 + BA - 1 + PM / 2 <= n0 - 1)
-                          : (m0 >= p && m0 + BA - 1 <= n0 - p - 1 && m0 - PM / 2 >= 0 &&
-                             m0 + BA - 1 + PM / 2 <= n0 - 1);
-    if (fast) {
-      float ws[2 * (BA + PM)];
+    float ws[2 * (BA + PM)];
 #pragma unroll
-      for (int w = 0; w < 2 * (BA + PM); ++w) ws[w] = s[2 * (m0 - PM / 2) + w];
+    for (int w = 0; w < 2 * (BA + PM); ++w) {
+      int k = 2 * (m0 - PM / 2) + w;
+      bool ok = per || (k >= 0 && k < M);
+      ws[w] = ok ? sS[p32(per ? (k & (M - 1)) : k)] : 0.f;
+    }
+    float alo[BA], ahi[BA];
+#pragma unroll
+    for (int bb = 0; bb < BA; ++bb) {
+      float lo = 0.f, hi = 0.f;
+#pragma unroll
+      for (int d = -PM / 2; d <= PM / 2; ++d)
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          float x = ws[2 * (bb + d + PM / 2) + f];
+          lo += ft.hp[f][d + PM / 2] * x;
+          hi += ft.gp[f][d + PM / 2] * x;
+        }
+      alo[bb] = lo;
+      ahi[bb] = hi;
+    }
+    // VMP boundary blocks (transposed)
+    if (!per && (m0 < p || m0 + BA > n0 - p)) {
 #pragma unroll
       for (int bb = 0; bb < BA; ++bb) {
-        float lo = 0.f, hi = 0.f;
-#pragma unroll
-        for (int d = -PM / 2; d <= PM / 2; ++d)
-#pragma unroll
-          for (int f = 0; f < 2; ++f) {
-            float x = ws[2 * (bb + d + PM / 2) + f];
-            lo += ft.hp[f][d + PM / 2] * x;
-            hi += ft.gp[f][d + PM / 2] * x;
+        const int mm = m0 + bb;
+        if (mm < p) {
+          float lo = 0.f, hi = 0.f;
+          for (int c = 0; c < G.Lb; ++c) {
+            float x = sS[p32(c)];
+            lo += st.PL[mm * G.Lb + c] * x;
+            hi += st.QL[mm * G.Lb + c] * x;
           }
-        lo_out[p32(m0 + bb)] = lo;
-        sIn[p32(n0 + m0 + bb)] = hi;
-      }
-    } else {
-      for (int m = m0; m < m0 + BA; ++m) {
-        float lo, hi;
-        ana_one<float>(m, n0, s, st, G, lo, hi);
-        lo_out[p32(m)] = lo;
-        sIn[p32(n0 + m)] = hi;
+          alo[bb] = lo;
+          ahi[bb] = hi;
+        } else if (mm >= n0 - p) {
+          const int r = n0 - 1 - mm;
+          float lo = 0.f, hi = 0.f;
+          for (int c = 0; c < G.Lb; ++c) {
+            float x = sS[p32(M - 1 - c)];
+            lo += st.PR[r * G.Lb + c] * x;
+            hi += st.QR[r * G.Lb + c] * x;
+          }
+          alo[bb] = lo;
+          ahi[bb] = hi;
+        }
       }
     }
+#pragma unroll
+    for (int bb = 0; bb < BA; ++bb) {
+      lo_out[p32(m0 + bb)] = alo[bb];
+      sIn[p32(n0 + m0 + bb)] = ahi[bb];
+    }
     __syncthreads();
-    // remaining levels: scratch buffers alternate v, sS; the last writes sIn
+    // remaining levels (1D): scratch buffers alternate v, sS; the last writes sIn
     float* cur = v;
     for (int j = G.R - 2; j >= io.jlev; --j) {
       const int h0 = 1 << j;
@@ -387,7 +470,8 @@ static FastTaps<PM, Q> make_taps(const Plan& P) {
 static size_t line2_smem(const Plan& P) {
   Geo G;
   G.p = P.p; G.ntap = P.ntap; G.Lb = P.Lb;
-  return sizeof(float) * ((size_t)table_count(G) + 2 * (size_t)p32len(P.M) + (size_t)padlen(P.N));
+  return sizeof(float) * ((size_t)table_count(G) + 2 * (size_t)p32len(P.M) + (size_t)padlen(P.N)) +
+         2 * sizeof(int) * (size_t)P.wpr + 16;
 }
 
 bool line2_eligible(const Plan& P) {

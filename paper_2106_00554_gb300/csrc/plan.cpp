@@ -673,7 +673,7 @@ int uw_plan_reserve(uw_plan* P, int max_batch) {
   if (!P || max_batch < 1) return fail(UW_ERR_INVALID_ARG, "null plan or max_batch < 1");
   size_t wb = uw::workspace_bytes(*P, max_batch);
   int64_t coeffs = P->d == 1 ? (int64_t)P->M : (int64_t)P->M * P->M;
-  size_t sb = (size_t)max_batch * (size_t)(coeffs + P->m) * sizeof(double);
+  size_t sb = (size_t)max_batch * (size_t)(coeffs + P->m) * sizeof(double) + 512;
   void* w = nullptr;
   void* s = nullptr;
   if (wb && cudaMalloc(&w, wb) != cudaSuccess) { cudaGetLastError(); return fail(UW_ERR_OOM, "workspace allocation failed"); }
