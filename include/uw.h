@@ -127,6 +127,36 @@ int uw_adjoint(const uw_plan* plan, int precision, const void* y_dev, void* x_de
                int batch, void* stream);
 
 /*
+ * uw_forward_noalloc -- the same product as uw_forward for a 2D plan, with
+ * its intermediate arrays in a fixed 8 MiB scratch array that the library
+ * holds in device memory from the moment it is loaded on a device, instead
+ * of the plan's reserved workspace.  The paper has no counterpart: this is a
+ * service for callers that must not allocate device memory at call time or
+ * grow a plan's workspace for a larger batch -- e.g. code whose device memory
+ * is handed out entirely by its own pool, where a cudaMalloc would fail or
+ * fragment that pool.  The call itself makes no allocation of any kind.
+ *   precision  UW_F64 or UW_F32 (UW_F32_SPLIT_BF16: UW_ERR_UNSUPPORTED)
+ *   x_dev      device, batch x M^2 coefficients (read only)
+ *   y_dev      device, batch x m samples (written; must not overlap x)
+ *   batch      >= 1, not limited by the reserved max_batch but by the scratch:
+ *              batch x (2 (M/2)^2 + M^2 + 2 M N) elements of the precision
+ *              must fit in 8 MiB (e.g. M = 256, N = 512 in FP32: batch <= 5;
+ *              M = 512, N = 1024 in FP32: batch 1), else UW_ERR_INVALID_ARG
+ *              and nothing is launched
+ *   stream     cudaStream_t as void*
+ * Errors: UW_ERR_UNSUPPORTED for 1D plans; UW_ERR_CUDA if the scratch's
+ * device address cannot be found (looked up once per device, on the device
+ * that is current at the call).
+ * All calls on one device share the one scratch array: two calls whose
+ * kernels can overlap (different streams, or different host threads without
+ * ordering) race on it and give wrong results; order them on one stream.
+ * The first call on each device does the one-time address lookup, which may
+ * load the library's GPU code: make it before any stream capture begins.
+ */
+int uw_forward_noalloc(const uw_plan* plan, int precision, const void* x_dev, void* y_dev,
+                       int batch, void* stream);
+
+/*
  * uw_forward_host / uw_adjoint_host -- the same products on HOST buffers:
  * the input is copied to the plan's device staging area, the product runs on
  * `stream`, the result is copied back; the call returns once the result is in

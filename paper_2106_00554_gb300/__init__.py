@@ -11,7 +11,8 @@ arguments.  PyTorch supplies device memory and streams.
 """
 from . import _lib
 from ._lib import (UW_BOUNDARY_PERIODIC, UW_BOUNDARY_VMP, UW_F32, UW_F32_SPLIT_BF16, UW_F64,
-                   UWError, uw_adjoint, uw_adjoint_host, uw_forward, uw_forward_host, uw_host_table,
+                   UWError, uw_adjoint, uw_adjoint_host, uw_forward, uw_forward_host, uw_forward_noalloc,
+                   uw_host_table,
                    uw_plan_create, uw_plan_destroy, uw_plan_reserve, uw_plan_set_coarsest,
                    uw_plan_set_mask, uw_plan_table)
 
@@ -93,6 +94,16 @@ class Plan:
         if y is None:
             y = torch.empty(shape, dtype=x.dtype, device=x.device)
         uw_forward(self._h, prec, x.data_ptr(), y.data_ptr(), batch, _stream_ptr(stream))
+        return y
+
+    def forward_noalloc(self, x, y, precision=None, stream=None):
+        """uw_forward_noalloc: the 2D forward product into the caller's y with
+        the library's fixed scratch (no device allocation in the call)."""
+        prec = self._prec(x, precision)
+        batch = x.numel() // self.coeffs
+        assert x.is_cuda and x.is_contiguous() and batch * self.coeffs == x.numel()
+        assert y.is_cuda and y.is_contiguous() and y.numel() == batch * self.m and y.dtype == x.dtype
+        uw_forward_noalloc(self._h, prec, x.data_ptr(), y.data_ptr(), batch, _stream_ptr(stream))
         return y
 
     def adjoint(self, y, x=None, precision=None, stream=None):

@@ -33,6 +33,7 @@ SIGNATURES = {
     "uw_plan_n": (_i64, [_c_p]),
     "uw_forward": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
     "uw_adjoint": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
+    "uw_forward_noalloc": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
     "uw_forward_host": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
     "uw_adjoint_host": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
     "uw_plan_destroy": (None, [_c_p]),
@@ -108,6 +109,10 @@ def uw_forward(h, precision, x_ptr, y_ptr, batch, stream):
 
 def uw_adjoint(h, precision, y_ptr, x_ptr, batch, stream):
     _chk(lib().uw_adjoint(h, precision, y_ptr, x_ptr, batch, stream), "uw_adjoint")
+
+
+def uw_forward_noalloc(h, precision, x_ptr, y_ptr, batch, stream):
+    _chk(lib().uw_forward_noalloc(h, precision, x_ptr, y_ptr, batch, stream), "uw_forward_noalloc")
 
 
 def uw_forward_host(h, precision, x_ptr, y_ptr, batch, stream):

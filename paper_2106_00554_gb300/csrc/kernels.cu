@@ -25,6 +25,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -810,18 +811,25 @@ int upload_tables(Plan& P) {
   return UW_OK;
 }
 
+size_t work2d_elems(const Plan& P, int batch);
+
 size_t workspace_bytes(const Plan& P, int batch) {
   const size_t M = P.M, N = P.N, B = batch, e = sizeof(double);
   if (P.d == 1) {
     if (line_fits<double>(P) && line_fits<float>(P)) return 256;
     return e * B * (2 * M + N) + 256;
   }
-  const size_t Mh = M / 2;
-  size_t xs = 2 * B * Mh * Mh;
+  return e * work2d_elems(P, batch) + 1024;
+}
+
+// elements of scratch the 2D path (fwd2d / adj2d) uses for `batch` instances
+size_t work2d_elems(const Plan& P, int batch) {
+  const size_t M = P.M, N = P.N, B = batch, Mh = M / 2;
+  size_t xs = 2 * B * Mh * Mh;   // XS, XS2: coarse level buffers
   size_t a = B * M * M;          // XT / X'T
   size_t vt = B * M * N;         // VT / QT
   size_t v = B * N * M;          // V / Q
-  return e * (xs + a + vt + v) + 1024;
+  return xs + a + vt + v;
 }
 
 struct Profiler {
@@ -1291,6 +1299,82 @@ int launch_adjoint(const Plan& P, int prec, const void* y, void* x, int batch, v
 
 }  // namespace uw
 
+// ---------------------------------------------------------------------------
+// Fixed scratch for uw_forward_noalloc: a file-scope device array that exists
+// from the moment the library's module is loaded on a device, so the call
+// needs no allocator.  Every element the 2D path reads from it is written
+// earlier in the same call, so nothing in it has to start at zero.
+// ---------------------------------------------------------------------------
+static constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace uw {
+
+// device address of g_noalloc_scratch on the current device, looked up once
+// per device (the first call on a device should come before any stream
+// capture: the lookup may load the library's module)
+static int noalloc_scratch(void** out) {
+  static std::mutex mu;
+  static void* addr[128] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+    cudaGetLastError();
+    set_error(UW_ERR_CUDA, "no usable current CUDA device");
+    return UW_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* a = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+    if (e != cudaSuccess || !a) {
+      cudaGetLastError();
+      set_error(UW_ERR_CUDA, std::string("cudaGetSymbolAddress of the fixed scratch failed: ") + cudaGetErrorString(e));
+      return UW_ERR_CUDA;
+    }
+    addr[dev] = a;
+  }
+  *out = addr[dev];
+  return UW_OK;
+}
+
+int launch_forward_noalloc(const Plan& P, int prec, const void* x, void* y, int batch, void* stream, int* nl) {
+  if (P.d != 2) {
+    set_error(UW_ERR_UNSUPPORTED, "uw_forward_noalloc serves 2D plans only");
+    return UW_ERR_UNSUPPORTED;
+  }
+  if (prec != UW_F64 && prec != UW_F32) {
+    set_error(UW_ERR_UNSUPPORTED, "uw_forward_noalloc supports UW_F64 and UW_F32");
+    return UW_ERR_UNSUPPORTED;
+  }
+  const size_t e = prec == UW_F64 ? sizeof(double) : sizeof(float);
+  const size_t need = e * work2d_elems(P, batch);
+  if (need > kNoAllocScratchBytes) {
+    set_error(UW_ERR_INVALID_ARG, "request needs " + std::to_string(need) + " bytes of scratch; the fixed scratch holds " +
+                                      std::to_string(kNoAllocScratchBytes));
+    return UW_ERR_INVALID_ARG;
+  }
+  if ((prec == UW_F64 && !line_fits<double>(P)) || (prec == UW_F32 && !line_fits<float>(P))) {
+    set_error(UW_ERR_UNSUPPORTED, "2D lines longer than one CTA's shared memory are not implemented");
+    return UW_ERR_UNSUPPORTED;
+  }
+  void* work = nullptr;
+  int st = noalloc_scratch(&work);
+  if (st != UW_OK) return st;
+  Launcher L;
+  L.s = (cudaStream_t)stream;
+  L.prof = nullptr;  // the profiler's event pool may grow; keep this call free of it
+  if (prec == UW_F64) fwd2d<double>(P, (const double*)x, (double*)y, batch, (double*)work, L);
+  else fwd2d<float>(P, (const float*)x, (float*)y, batch, (float*)work, L);
+  if (nl) *nl = L.count;
+  if (L.err != cudaSuccess) {
+    set_error(UW_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(L.err));
+    return UW_ERR_CUDA;
+  }
+  return UW_OK;
+}
+
+}  // namespace uw
+
 // ===========================================================================
 // C ABI: forward / adjoint
 // ===========================================================================
@@ -1328,6 +1412,20 @@ int uw_adjoint(const uw_plan* P, int prec, const void* y, void* x, int batch, vo
   if (st != UW_OK) return st;
   int nl = 0;
   st = uw::launch_adjoint(*P, prec, y, x, batch, stream, &nl);
+  const_cast<uw_plan*>(P)->last_launches = nl;
+  return st;
+}
+
+int uw_forward_noalloc(const uw_plan* P, int prec, const void* x, void* y, int batch, void* stream) {
+  if (!P) { uw::set_error(UW_ERR_INVALID_ARG, "null plan"); return UW_ERR_INVALID_ARG; }
+  if (prec != UW_F64 && prec != UW_F32 && prec != UW_F32_SPLIT_BF16) {
+    uw::set_error(UW_ERR_INVALID_ARG, "unknown precision");
+    return UW_ERR_INVALID_ARG;
+  }
+  if (batch < 1) { uw::set_error(UW_ERR_INVALID_ARG, "batch must be >= 1"); return UW_ERR_INVALID_ARG; }
+  if (!x || (!y && P->m > 0)) { uw::set_error(UW_ERR_INVALID_ARG, "null buffer"); return UW_ERR_INVALID_ARG; }
+  int nl = 0;
+  int st = uw::launch_forward_noalloc(*P, prec, x, y, batch, stream, &nl);
   const_cast<uw_plan*>(P)->last_launches = nl;
   return st;
 }
