@@ -232,9 +232,35 @@ def run_ours(args):
         flush.fill_(1)
     torch.cuda.synchronize()
 
+    # the step as one CUDA graph (launch-bound otherwise: ~20 small launches per
+    # pair); eager launches if the capture is refused
+    graph, graph_error = None, None
+    if not args.eager:
+        try:
+            side = torch.cuda.Stream()
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                step()
+            stream.wait_stream(side)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                plan.forward(x, y, precision=prec)
+                plan.adjoint(yin, xo, precision=prec)
+            for _ in range(3):
+                graph.replay()
+            torch.cuda.synchronize()
+        except Exception as e:  # noqa: BLE001 - reported in the JSON line
+            graph = None
+            graph_error = f"{type(e).__name__}: {e}"[:200]
+    plan.forward(x, y, precision=prec)
+    n_fwd = plan.last_launches
+    plan.adjoint(yin, xo, precision=prec)
+    n_adj = plan.last_launches
+    torch.cuda.synchronize()
+
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    _lib.uw_plan_profile(plan._h, True)
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
@@ -244,18 +270,17 @@ def run_ours(args):
     launches = 0
     for k in range(args.steps):
         starts[k].record(stream)
-        plan.forward(x, y, precision=prec)
-        launches += plan.last_launches
-        plan.adjoint(yin, xo, precision=prec)
-        launches += plan.last_launches
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+        launches += n_fwd + n_adj
         ends[k].record(stream)
         flush.fill_(k)                   # L2 flush between timed steps (not timed)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = clk.stop()
-    prof = _lib.uw_plan_profile_read(plan._h)
-    _lib.uw_plan_profile(plan._h, False)
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(per)
     if dist:
@@ -263,6 +288,17 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = args.steps * world / (total_ms / 1000.0)
+
+    # per-kernel device times: the same step launched eagerly with the
+    # library's event profiler on (events on the launching stream)
+    kp = max(3, min(args.steps, 300))
+    _lib.uw_plan_profile(plan._h, True)
+    for k in range(kp):
+        step()
+        flush.fill_(k)
+    torch.cuda.synchronize()
+    prof = [e for e in _lib.uw_plan_profile_read(plan._h) if e["launches"] > 0]
+    _lib.uw_plan_profile(plan._h, False)
 
     # end to end through the host-buffer entry points (copies inside)
     e2e = None
@@ -317,6 +353,9 @@ def run_ours(args):
         "dtype": {F32: "f32", F32_SPLIT_BF16: "bf16 hi+lo split, f32 accumulate", F64: "f64"}[prec],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "batch": 1,
+                   "launch": "cuda graph of the pair" if graph is not None else
+                   ("eager" if args.eager else f"eager (graph capture failed: {graph_error})"),
+                   "kernel_times": f"event profiler over {kp} further eager steps",
                    "l2": "flushed between timed steps by a 256 MiB device write outside the event pair",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
@@ -343,6 +382,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--eager", action="store_true", help="launch the timed steps without a CUDA graph")
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

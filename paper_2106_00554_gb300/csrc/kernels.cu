@@ -26,7 +26,9 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "uw_internal.h"
@@ -389,18 +391,18 @@ __global__ void k_transpose(const T* __restrict__ in, T* __restrict__ out, int r
 // filters, and the boundary rows of the VMP blocks) in shared memory, runs the
 // row pass and the column pass there, and writes its output tile.
 // ---------------------------------------------------------------------------
-// window accessor: global index g -> window slot (modular for periodic)
+// window accessor: global index g -> window slot.  The window covers every
+// index the per-output formulas read (the dependency ranges below), so no
+// bounds check is needed; `wrap` (periodic windows that cross the end of the
+// level) maps g modulo the power-of-two length with a mask.
 template <typename T>
 struct Win {
   const T* a;
-  int start, len, stride, n, per;
+  int start, stride, mask, wrap;
   __device__ __forceinline__ T operator[](int g) const {
     int w = g - start;
-    if (per) {
-      w %= n;
-      if (w < 0) w += n;
-    }
-    return (w >= 0 && w < len) ? a[w * stride] : T(0);
+    if (wrap) w &= mask;
+    return a[w * stride];
   }
 };
 
@@ -415,8 +417,16 @@ __host__ __device__ __forceinline__ void syn_dep(int a, int b, int n0, const Geo
     if (hi - lo > n0) { lo = 0; hi = n0; }
     return;
   }
-  if (a < G.Lb || lo < 0) lo = 0;
-  if (b > n1 - G.Lb || hi > n0) hi = n0;
+  if (lo < 0) lo = 0;
+  if (hi > n0) hi = n0;
+  if (a < G.Lb) {  // left boundary block reads the p edge coefficients
+    lo = 0;
+    if (hi < p) hi = p;
+  }
+  if (b > n1 - G.Lb) {  // right boundary block
+    hi = n0;
+    if (lo > n0 - p) lo = n0 - p;
+  }
 }
 
 // analysis: outputs m in [a, b) of level j need level-(j+1) samples [lo, hi)
@@ -428,25 +438,108 @@ __host__ __device__ __forceinline__ void ana_dep(int a, int b, int n0, const Geo
     if (hi - lo > n1) { lo = 0; hi = n1; }
     return;
   }
-  if (a < p || lo < 0) lo = 0;
-  if (b > n0 - p || hi > n1) hi = n1;
+  if (lo < 0) lo = 0;
+  if (hi > n1) hi = n1;
+  if (a < p) {  // left boundary rows read the first Lb samples
+    lo = 0;
+    if (hi < G.Lb) hi = G.Lb;
+  }
+  if (b > n0 - p) {  // right boundary rows read the last Lb samples
+    hi = n1;
+    if (lo > n1 - G.Lb) lo = n1 - G.Lb;
+  }
 }
 
-constexpr int kTile = 64;
+// Copy a rows x cols window into shared memory (row-major, leading dim
+// cols): warps take 8 rows at a time, lanes take columns, and all 16 loads of
+// a lane are issued before its stores so their latencies overlap.  addr(r, c)
+// is the global address of window element (r, c).
+template <typename T, typename Addr>
+__device__ __forceinline__ void gather_window(T* dst, int rows, int cols, const Addr& addr) {
+  constexpr int RB = 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r0 = warp * RB; r0 < rows; r0 += nw * RB)
+    for (int c0 = 0; c0 < cols; c0 += 64) {
+      T v[RB][2];
+#pragma unroll
+      for (int a = 0; a < RB; ++a)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = r0 + a, c = c0 + lane + 32 * h;
+          v[a][h] = (r < rows && c < cols) ? __ldg(addr(r, c)) : T(0);
+        }
+#pragma unroll
+      for (int a = 0; a < RB; ++a)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = r0 + a, c = c0 + lane + 32 * h;
+          if (r < rows && c < cols) dst[r * cols + c] = v[a][h];
+        }
+    }
+}
+
+// Interior formulas with the filter length P known at compile time (P = 0:
+// the runtime p, loops not unrolled).  Synthesis: s[k] = sum over the p
+// indices m with k - 2m in [-p+1, p] of h_{k-2m} lo[m] + g_{k-2m} hi[m];
+// analysis: lo[m] = sum_l h_l s[2m+l], hi[m] = sum_l g_l s[2m+l]
+// (Sec. 3.2, two-scale relations of the interior functions).
+template <typename T, int P, typename AL, typename AH>
+__device__ __forceinline__ T syn_interior(int k, int p_rt, const AL& lo, const AH& hi, const T* h, const T* g) {
+  const int p = P ? P : p_rt;
+  const int m0 = (k - p + 1) >> 1;
+  const int l0 = k - 2 * m0 + p - 1;  // filter index of m0
+  T acc = 0;
+#pragma unroll
+  for (int t = 0; t < (P ? P : 1); ++t) {
+    if (!P) break;
+    acc += h[l0 - 2 * t] * lo[m0 + t] + g[l0 - 2 * t] * hi[m0 + t];
+  }
+  if (!P)
+    for (int t = 0; t < p; ++t) acc += h[l0 - 2 * t] * lo[m0 + t] + g[l0 - 2 * t] * hi[m0 + t];
+  return acc;
+}
+
+template <typename T, int P, typename AS>
+__device__ __forceinline__ void ana_interior(int m, int p_rt, const AS& s, const T* h, const T* g, T& lo, T& hi) {
+  const int p = P ? P : p_rt;
+  const int k0 = 2 * m - p + 1;
+  T a = 0, b = 0;
+#pragma unroll
+  for (int l = 0; l < (P ? 2 * P : 1); ++l) {
+    if (!P) break;
+    const T v = s[k0 + l];
+    a += h[l] * v;
+    b += g[l] * v;
+  }
+  if (!P)
+    for (int l = 0; l < 2 * p; ++l) {
+      const T v = s[k0 + l];
+      a += h[l] * v;
+      b += g[l] * v;
+    }
+  lo = a;
+  hi = b;
+}
+
+// tile edges: synthesis tiles of level-(j+1) samples, analysis tiles of
+// level-j coefficients per quadrant; small levels take small tiles so every
+// level launches at least 64 CTAs per instance (and the analysis column pass
+// maps a window of at most 64 columns to lanes)
+__host__ __device__ inline int syn_tile(int n1) { return n1 >= 512 ? 32 : (n1 >= 128 ? n1 / 8 : (n1 >= 64 ? 8 : n1)); }
+__host__ __device__ inline int ana_tile(int n0) { return n0 >= 64 ? 16 : (n0 >= 32 ? 8 : n0); }
 
 // synthesis level j -> j+1 on the n1 x n1 block [[LL, D1], [D2, D3]]:
 // LL from llsrc (leading dim ldll), details from x; output S_{j+1} to dst
-template <typename T>
+template <typename T, int P>
 __global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc, int64_t ldll, int64_t llb,
                                                      const T* __restrict__ x, int M, T* __restrict__ dst, int64_t lddst,
-                                                     int64_t dstb, int j, Tables<T> tab, Geo G) {
+                                                     int64_t dstb, int j, int TS, Tables<T> tab, Geo G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
   const int off = stage_tables(tab, G, sm, st, tid, nthr);
   const int n0 = 1 << j, n1 = 2 * n0;
-  const int TS = min(kTile, n1);
   const int tiles = n1 / TS;
   const int r0 = (blockIdx.x / tiles) * TS, c0 = (blockIdx.x % tiles) * TS;
   const int64_t b = blockIdx.y;
@@ -455,54 +548,59 @@ __global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc
   syn_dep(r0, r0 + TS, n0, G, dr0, dr1);
   syn_dep(c0, c0 + TS, n0, G, dc0, dc1);
   const int nr = dr1 - dr0, nc = dc1 - dc0;
+  const int wrapr = per, wrapc = per;  // periodic reads go through the power-of-two mask
   // window of the four subbands: W[q][i][m], q = 0 LL, 1 D1, 2 D2, 3 D3
   T* W = sm + off;
   T* H = W + 4 * nr * nc;  // row-synthesised: H[half][i][c], half 0 = top rows, 1 = bottom rows
   const T* xb = x + b * (int64_t)M * M;
   const T* lb = llsrc + b * llb;
-  for (int e = tid; e < 4 * nr * nc; e += nthr) {
-    const int q = e / (nr * nc), rem = e % (nr * nc), i = rem / nc, m = rem % nc;
-    int gi = dr0 + i, gm = dc0 + m;
-    if (per) { gi &= n0 - 1; gm &= n0 - 1; }
-    T val;
-    if (q == 0) val = lb[(int64_t)gi * ldll + gm];
-    else if (q == 1) val = xb[(int64_t)gi * M + n0 + gm];
-    else if (q == 2) val = xb[(int64_t)(n0 + gi) * M + gm];
-    else val = xb[(int64_t)(n0 + gi) * M + n0 + gm];
-    W[e] = val;
+  {
+    const int msk = per ? n0 - 1 : -1;
+    auto addr = [&](int r, int m) -> const T* {  // window row r = q * nr + i
+      const int q = r >= 2 * nr ? (r >= 3 * nr ? 3 : 2) : (r >= nr ? 1 : 0);
+      const int gi = (dr0 + r - q * nr) & msk, gm = (dc0 + m) & msk;
+      if (q == 0) return lb + (int64_t)gi * ldll + gm;
+      return xb + (int64_t)((q >= 2 ? n0 : 0) + gi) * M + (q & 1 ? n0 : 0) + gm;
+    };
+    gather_window<T>(W, 4 * nr, nc, addr);
   }
   __syncthreads();
   // rows: for each window row i (top: LL|D1, bottom: D2|D3), outputs c in tile
+  const int lg = __ffs(TS) - 1;
   for (int e = tid; e < 2 * nr * TS; e += nthr) {
-    const int half = e / (nr * TS), rem = e % (nr * TS), i = rem / TS, cc = rem % TS;
+    const int half = e >= nr * TS ? 1 : 0, rem = e - half * nr * TS, i = rem >> lg, cc = rem & (TS - 1);
     const T* lo = W + (half == 0 ? 0 : 2) * nr * nc + i * nc;
     const T* hi = W + (half == 0 ? 1 : 3) * nr * nc + i * nc;
-    Win<T> wl{lo, dc0, nc, 1, n0, per}, wh{hi, dc0, nc, 1, n0, per};
-    H[e] = syn_one<T>(c0 + cc, n0, wl, wh, st, G);
+    Win<T> wl{lo, dc0, 1, n0 - 1, wrapc}, wh{hi, dc0, 1, n0 - 1, wrapc};
+    const int kk = c0 + cc;
+    H[e] = (per || (kk >= G.Lb && kk < n1 - G.Lb)) ? syn_interior<T, P>(kk, G.p, wl, wh, st.h, st.g)
+                                                   : syn_one<T>(kk, n0, wl, wh, st, G);
   }
   __syncthreads();
   // columns: outputs r in tile from the top (lo) and bottom (hi) H rows
   for (int e = tid; e < TS * TS; e += nthr) {
-    const int rr = e / TS, cc = e % TS;
-    Win<T> wl{H + cc, dr0, nr, TS, n0, per}, wh{H + nr * TS + cc, dr0, nr, TS, n0, per};
-    dst[b * dstb + (int64_t)(r0 + rr) * lddst + c0 + cc] = syn_one<T>(r0 + rr, n0, wl, wh, st, G);
+    const int rr = e >> lg, cc = e & (TS - 1);
+    Win<T> wl{H + cc, dr0, TS, n0 - 1, wrapr}, wh{H + nr * TS + cc, dr0, TS, n0 - 1, wrapr};
+    const int kr = r0 + rr;
+    dst[b * dstb + (int64_t)kr * lddst + c0 + cc] = (per || (kr >= G.Lb && kr < n1 - G.Lb))
+                                                        ? syn_interior<T, P>(kr, G.p, wl, wh, st.h, st.g)
+                                                        : syn_one<T>(kr, n0, wl, wh, st, G);
   }
 }
 
 // analysis level j+1 -> j of the n1 x n1 block src (leading dim ldsrc): the
 // low-pass block to lldst (or to x when lldst is null), details to x
-template <typename T>
+template <typename T, int P>
 __global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, int64_t ldsrc, int64_t srcb,
                                                      T* __restrict__ x, int M, T* __restrict__ lldst, int64_t ldll,
-                                                     int64_t llb, int j, Tables<T> tab, Geo G) {
+                                                     int64_t llb, int j, int TS, Tables<T> tab, Geo G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
   const int off = stage_tables(tab, G, sm, st, tid, nthr);
   const int n0 = 1 << j, n1 = 2 * n0;
-  const int TS = min(kTile / 2, n0);  // output coefficients per dimension and quadrant
-  const int tiles = n0 / TS;
+  const int tiles = n0 / TS;  // TS: output coefficients per dimension and quadrant
   const int m0 = (blockIdx.x / tiles) * TS, k0 = (blockIdx.x % tiles) * TS;
   const int64_t b = blockIdx.y;
   const bool per = G.bd == UW_BOUNDARY_PERIODIC;
@@ -510,33 +608,42 @@ __global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, 
   ana_dep(m0, m0 + TS, n0, G, sr0, sr1);
   ana_dep(k0, k0 + TS, n0, G, sc0, sc1);
   const int nr = sr1 - sr0, nc = sc1 - sc0;
+  const int wrapr = per, wrapc = per;
   T* S = sm + off;            // S[i][c] window of the level-(j+1) block
   T* H = S + nr * nc;         // H[half][m][c]: column analysis, half 0 = low, 1 = high
   const T* sb = src + b * srcb;
-  for (int e = tid; e < nr * nc; e += nthr) {
-    const int i = e / nc, c = e % nc;
-    int gi = sr0 + i, gc = sc0 + c;
-    if (per) { gi &= n1 - 1; gc &= n1 - 1; }
-    S[e] = sb[(int64_t)gi * ldsrc + gc];
+  {
+    const int msk = per ? n1 - 1 : -1;
+    auto addr = [&](int i, int c) -> const T* {
+      return sb + (int64_t)((sr0 + i) & msk) * ldsrc + ((sc0 + c) & msk);
+    };
+    gather_window<T>(S, nr, nc, addr);
   }
   __syncthreads();
-  // columns: for each window column c, low/high outputs m in [m0, m0 + TS)
-  for (int e = tid; e < TS * nc; e += nthr) {
-    const int mm = e / nc, c = e % nc;
-    Win<T> s{S + c, sr0, nr, nc, n1, per};
+  // columns: for each window column c (< 64 by the tile size), low/high
+  // outputs m in [m0, m0 + TS)
+  for (int e = tid; e < TS * 64; e += nthr) {
+    const int mm = e >> 6, c = e & 63;
+    if (c >= nc) continue;
+    Win<T> s{S + c, sr0, nc, n1 - 1, wrapr};
     T lo, hi;
-    ana_one<T>(m0 + mm, n0, s, st, G, lo, hi);
+    const int m = m0 + mm;
+    if (per || (m >= G.p && m < n0 - G.p)) ana_interior<T, P>(m, G.p, s, st.h, st.g, lo, hi);
+    else ana_one<T>(m, n0, s, st, G, lo, hi);
     H[mm * nc + c] = lo;
     H[(TS + mm) * nc + c] = hi;
   }
   __syncthreads();
   // rows: each H row -> low/high outputs k in [k0, k0 + TS)
   T* xb = x + b * (int64_t)M * M;
+  const int lg = __ffs(TS) - 1;
   for (int e = tid; e < 2 * TS * TS; e += nthr) {
-    const int row = e / TS, kk = e % TS;      // row < TS: low rows, else high rows
-    Win<T> s{H + row * nc, sc0, nc, 1, n1, per};
+    const int row = e >> lg, kk = e & (TS - 1);  // row < TS: low rows, else high rows
+    Win<T> s{H + row * nc, sc0, 1, n1 - 1, wrapc};
     T lo, hi;
-    ana_one<T>(k0 + kk, n0, s, st, G, lo, hi);
+    const int m = k0 + kk;
+    if (per || (m >= G.p && m < n0 - G.p)) ana_interior<T, P>(m, G.p, s, st.h, st.g, lo, hi);
+    else ana_one<T>(m, n0, s, st, G, lo, hi);
     const int mm = row < TS ? m0 + row : m0 + row - TS;
     if (row < TS) {
       if (lldst) lldst[b * llb + (int64_t)mm * ldll + k0 + kk] = lo;
@@ -808,6 +915,19 @@ int upload_tables(Plan& P) {
   }
   set_table_ptrs(P.t64, (const double*)P.d_tab64, parts);
   set_table_ptrs(P.t32, (const float*)P.d_tab32, parts);
+  std::vector<uint32_t> tcw;
+  build_tc(P, tcw);
+  if (P.tc.ok) {
+    if (cudaMalloc(&P.d_tc, tcw.size() * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error(UW_ERR_OOM, "tensor-core table allocation failed");
+      return UW_ERR_OOM;
+    }
+    if (cudaMemcpy(P.d_tc, tcw.data(), tcw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error(UW_ERR_CUDA, "tensor-core table upload failed");
+      return UW_ERR_CUDA;
+    }
+  }
   return UW_OK;
 }
 
@@ -872,6 +992,7 @@ void profiler_free(Plan& P) {
 
 struct Launcher {
   cudaStream_t s;
+  bool split = false;      // UW_F32_SPLIT_BF16: line operators on the tensor cores where eligible
   int count = 0;
   cudaError_t err = cudaSuccess;
   Profiler* prof = nullptr;
@@ -898,6 +1019,26 @@ struct Launcher {
     cudaEventRecord(cur.a, s);
     armed = true;
   }
+  // rename the armed launch (same bytes), e.g. when a line operator takes
+  // the tensor-core kernel
+  void retag(const std::string& name) {
+    if (!armed) return;
+    const double bytes = prof->bytes[cur.id];
+    auto it = prof->ids.find(name);
+    int id;
+    if (it == prof->ids.end()) {
+      id = (int)prof->names.size();
+      prof->ids[name] = id;
+      prof->names.push_back(name);
+      prof->ms.push_back(0);
+      prof->bytes.push_back(0);
+      prof->cnt.push_back(0);
+    } else {
+      id = it->second;
+    }
+    prof->bytes[id] = bytes;
+    cur.id = id;
+  }
   void check() {
     ++count;
     cudaError_t e = cudaGetLastError();
@@ -923,9 +1064,25 @@ const Tables<double>& tabs<double>(const Plan& P) { return P.t64; }
 template <>
 const Tables<float>& tabs<float>(const Plan& P) { return P.t32; }
 
+// raise a kernel's dynamic shared-memory limit to the device maximum, once
+// per kernel and device (the launch itself passes the bytes it uses)
+cudaError_t set_smem_limit(const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, fn})) return cudaSuccess;
+  int mx = 0;
+  cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) done.insert({dev, fn});
+  return e;
+}
+
 template <typename T>
-static cudaError_t set_smem(const void* fn, size_t bytes) {
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+static cudaError_t set_smem(const void* fn, size_t) {
+  return set_smem_limit(fn);
 }
 
 static bool getenv_flag(const char* name) {
@@ -953,6 +1110,11 @@ static void launch_line(bool fwd, const Plan& P, const Geo& G, const T* in, T* o
 template <>
 void launch_line<float>(bool fwd, const Plan& P, const Geo& G, const float* in, float* out, const LineIO& io,
                         int nblocks, Launcher& L) {
+  if (L.split && tc_eligible(P, io, in, out, fwd)) {
+    if (L.armed) L.retag(P.prof->names[L.cur.id] + "_tc");
+    tc_launch(fwd, P, in, out, io, nblocks, L.s);
+    return;
+  }
   if (line2_eligible(P) && !getenv_flag("UW_GENERIC_LINES")) {
     line2_launch(fwd, P, G, in, out, io, nblocks, L.s);
     return;
@@ -990,9 +1152,31 @@ static void launch_coarse(const Plan& P, const Geo& G, const T* xin, T* xout, T*
 // level.  forward: S_{J0} and the details from x, S_{R-1} ends in XS;
 // adjoint: S_{R-1} from XS, the low-pass block and details of every level
 // end in x.  XS and XS2 (Mh x Mh per instance) alternate as level buffers.
+// filter length as a compile-time constant for the FP32 coarse kernels
+// (p = 1..10); FP64 runs the runtime-p variant (P = 0)
+template <typename T, typename F>
+static void coarse_dispatch(int p, F&& f) {
+  if constexpr (sizeof(T) == 8) {
+    f(std::integral_constant<int, 0>{});
+  } else {
+  switch (p) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 9: f(std::integral_constant<int, 9>{}); break;
+    default: f(std::integral_constant<int, 10>{}); break;
+  }
+  }
+}
+
 static int coarse_tile_extent(const Geo& G, int j, bool syn) {
   const int n0 = 1 << j, n1 = 2 * n0;
-  const int TS = syn ? std::min(kTile, n1) : std::min(kTile / 2, n0);
+  const int TS = syn ? syn_tile(n1) : ana_tile(n0);
   const int span = syn ? n1 : n0;
   int worst = 0;
   for (int a = 0; a < span; a += TS) {
@@ -1015,8 +1199,13 @@ static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xou
     const int j = fwd ? P.J0 + it : P.R - 2 - it;
     const int n0 = 1 << j, n1 = 2 * n0;
     const int w = coarse_tile_extent(G, j, fwd);
+    if (!fwd && w > 64) {  // the analysis column pass maps window columns to 64 lanes
+      L.err = cudaErrorInvalidConfiguration;
+      return;
+    }
     if (fwd) {
-      const int TS = std::min(kTile, n1), tiles = n1 / TS;
+      const int TS = syn_tile(n1), tiles = n1 / TS;
+      const int thr = TS >= 32 ? 256 : 128;
       const size_t sm = sizeof(T) * (tabn + 4 * (size_t)w * w + 2 * (size_t)w * TS);
       const T* src = it == 0 ? x : ((nl - it) % 2 == 0 ? XS : XS2);
       const int64_t ld = it == 0 ? M : Mh, sb = it == 0 ? MM : HH;
@@ -1024,19 +1213,27 @@ static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xou
       char name[32];
       snprintf(name, sizeof name, "idwt2d_level_j%d", j);
       L.pre(name, sizeof(T) * (double)batch * (4.0 * n0 * n0 + (double)n1 * n1));
-      set_smem<T>((const void*)k_syn2d_level<T>, sm);
-      k_syn2d_level<T><<<dim3(tiles * tiles, batch), 256, sm, L.s>>>(src, ld, sb, x, M, dst, Mh, HH, j, tabs<T>(P), G);
+      coarse_dispatch<T>(G.p, [&](auto pc) {
+        constexpr int PP = decltype(pc)::value;
+        set_smem_limit((const void*)k_syn2d_level<T, PP>);
+        k_syn2d_level<T, PP><<<dim3(tiles * tiles, batch), thr, sm, L.s>>>(src, ld, sb, x, M, dst, Mh, HH, j, TS,
+                                                                          tabs<T>(P), G);
+      });
     } else {
-      const int TS = std::min(kTile / 2, n0), tiles = n0 / TS;
+      const int TS = ana_tile(n0), tiles = n0 / TS;
+      const int thr = TS >= 16 ? 256 : 128;
       const size_t sm = sizeof(T) * (tabn + (size_t)w * w + 2 * (size_t)TS * w);
       const T* src = it % 2 == 0 ? XS : XS2;
       T* dst = it == nl - 1 ? nullptr : (it % 2 == 0 ? XS2 : XS);
       char name[32];
       snprintf(name, sizeof name, "dwt2d_level_j%d", j);
       L.pre(name, sizeof(T) * (double)batch * (4.0 * n0 * n0 + (double)n1 * n1));
-      set_smem<T>((const void*)k_ana2d_level<T>, sm);
-      k_ana2d_level<T><<<dim3(tiles * tiles, batch), 256, sm, L.s>>>(src, Mh, HH, xout, M, dst, Mh, HH, j, tabs<T>(P),
-                                                                     G);
+      coarse_dispatch<T>(G.p, [&](auto pc) {
+        constexpr int PP = decltype(pc)::value;
+        set_smem_limit((const void*)k_ana2d_level<T, PP>);
+        k_ana2d_level<T, PP><<<dim3(tiles * tiles, batch), thr, sm, L.s>>>(src, Mh, HH, xout, M, dst, Mh, HH, j, TS,
+                                                                          tabs<T>(P), G);
+      });
     }
     L.check();
   }
@@ -1252,9 +1449,11 @@ static void adj2d(const Plan& P, const T* y, T* x, int batch, T* work, Launcher&
 }
 
 template <typename T>
-static int run(const Plan& P, bool fwd, const void* in, void* out, int batch, cudaStream_t s, int* nl) {
+static int run(const Plan& P, bool fwd, const void* in, void* out, int batch, cudaStream_t s, int* nl,
+               bool split = false) {
   Launcher L;
   L.s = s;
+  L.split = split;
   L.prof = P.prof;
   T* work = (T*)P.d_work;
   if (P.d == 1) {
@@ -1284,17 +1483,13 @@ static int run(const Plan& P, bool fwd, const void* in, void* out, int batch, cu
 int launch_forward(const Plan& P, int prec, const void* x, void* y, int batch, void* stream, int* nl) {
   cudaStream_t s = (cudaStream_t)stream;
   if (prec == UW_F64) return run<double>(P, true, x, y, batch, s, nl);
-  if (prec == UW_F32) return run<float>(P, true, x, y, batch, s, nl);
-  set_error(UW_ERR_UNSUPPORTED, "split-bf16 tensor-core path is not built");
-  return UW_ERR_UNSUPPORTED;
+  return run<float>(P, true, x, y, batch, s, nl, prec == UW_F32_SPLIT_BF16);
 }
 
 int launch_adjoint(const Plan& P, int prec, const void* y, void* x, int batch, void* stream, int* nl) {
   cudaStream_t s = (cudaStream_t)stream;
   if (prec == UW_F64) return run<double>(P, false, y, x, batch, s, nl);
-  if (prec == UW_F32) return run<float>(P, false, y, x, batch, s, nl);
-  set_error(UW_ERR_UNSUPPORTED, "split-bf16 tensor-core path is not built");
-  return UW_ERR_UNSUPPORTED;
+  return run<float>(P, false, y, x, batch, s, nl, prec == UW_F32_SPLIT_BF16);
 }
 
 }  // namespace uw

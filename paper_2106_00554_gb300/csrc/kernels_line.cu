@@ -81,44 +81,6 @@ __device__ __forceinline__ void load_line(const float* __restrict__ src, float* 
   for (int i = 0; i < K; ++i) dst[p32(tid + i * nthr)] = a[i];
 }
 
-// position of the (r+1)-th set bit of x (0 <= r < popc(x)), branch-free
-__device__ __forceinline__ int select_bit(unsigned x, int r) {
-  int pos = 0, c;
-  c = __popc(x & 0xFFFFu); if (r >= c) { r -= c; x >>= 16; pos += 16; }
-  c = __popc(x & 0xFFu);   if (r >= c) { r -= c; x >>= 8;  pos += 8; }
-  c = __popc(x & 0xFu);    if (r >= c) { r -= c; x >>= 4;  pos += 4; }
-  c = __popc(x & 0x3u);    if (r >= c) { r -= c; x >>= 2;  pos += 2; }
-  c = x & 1u;              if (r >= c) { pos += 1; }
-  return pos;
-}
-
-// The sampled sequency indices of one mask row, one sample per thread: the
-// row's words and word prefixes are staged in shared memory, a binary search
-// finds the word of sample j and select_bit its bit.  Returns the row's first
-// packed position r0 and its sample count; fills smask / spre.
-__device__ __forceinline__ void stage_row(const LineIO& io, int mrow, int rows, uint32_t* smask, int* spre,
-                                          int64_t& r0, int& cnt, int tid, int nthr) {
-  const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
-  const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
-  r0 = pf[0];
-  const int64_t r1 = (mrow + 1 < rows) ? (int64_t)io.prefix[(int64_t)(mrow + 1) * io.wpr] : io.m;
-  cnt = (int)(r1 - r0);
-  for (int w = tid; w < io.wpr; w += nthr) {
-    smask[w] = mk[w];
-    spre[w] = (int)(pf[w] - r0);
-  }
-}
-
-__device__ __forceinline__ int sample_index(const uint32_t* smask, const int* spre, int wpr, int j) {
-  int lo = 0, hi = wpr - 1;  // last word with spre[w] <= j
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (spre[mid] <= j) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo * 32 + select_bit(smask[lo], j - spre[lo]);
-}
-
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
@@ -484,10 +446,10 @@ static cudaError_t go(bool fwd, const Plan& P, const Geo& G, const float* in, fl
   FastTaps<PM, Q> ft = make_taps<PM, Q>(P);
   size_t sm = line2_smem(P);
   if (fwd) {
-    cudaFuncSetAttribute((const void*)k_line2_fwd<PM, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set_smem_limit((const void*)k_line2_fwd<PM, Q>);
     k_line2_fwd<PM, Q><<<nblocks, P.N / 16, sm, s>>>(in, out, P.t32, G, io, ft);
   } else {
-    cudaFuncSetAttribute((const void*)k_line2_adj<PM, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set_smem_limit((const void*)k_line2_adj<PM, Q>);
     k_line2_adj<PM, Q><<<nblocks, P.N / 16, sm, s>>>(in, out, P.t32, G, io, ft);
   }
   return cudaGetLastError();

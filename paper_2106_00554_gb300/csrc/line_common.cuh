@@ -274,6 +274,52 @@ struct LineIO {
   int mask_rows;         // 1 for d = 1 (all lines use row 0), else = lines
 };
 
+// position of the (r+1)-th set bit of x (0 <= r < popc(x)), branch-free
+__device__ __forceinline__ int select_bit(unsigned x, int r) {
+  int pos = 0, c;
+  c = __popc(x & 0xFFFFu); if (r >= c) { r -= c; x >>= 16; pos += 16; }
+  c = __popc(x & 0xFFu);   if (r >= c) { r -= c; x >>= 8;  pos += 8; }
+  c = __popc(x & 0xFu);    if (r >= c) { r -= c; x >>= 4;  pos += 4; }
+  c = __popc(x & 0x3u);    if (r >= c) { r -= c; x >>= 2;  pos += 2; }
+  c = x & 1u;              if (r >= c) { pos += 1; }
+  return pos;
+}
+
+// The sampled sequency indices of one mask row, one sample per thread: the
+// row's words and word prefixes are staged in shared memory, a binary search
+// finds the word of sample j and select_bit its bit.  Returns the row's first
+// packed position r0 and its sample count; fills smask / spre.
+__device__ __forceinline__ void stage_row(const LineIO& io, int mrow, int rows, uint32_t* smask, int* spre,
+                                          int64_t& r0, int& cnt, int tid, int nthr) {
+  const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
+  const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
+  r0 = pf[0];
+  const int64_t r1 = (mrow + 1 < rows) ? (int64_t)io.prefix[(int64_t)(mrow + 1) * io.wpr] : io.m;
+  cnt = (int)(r1 - r0);
+  for (int w = tid; w < io.wpr; w += nthr) {
+    smask[w] = mk[w];
+    spre[w] = (int)(pf[w] - r0);
+  }
+}
+
+__device__ __forceinline__ int sample_index(const uint32_t* smask, const int* spre, int wpr, int j) {
+  int lo = 0, hi = wpr - 1;  // last word with spre[w] <= j
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (spre[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo * 32 + select_bit(smask[lo], j - spre[lo]);
+}
+
+// raise a kernel's dynamic shared-memory limit to the device maximum (once)
+cudaError_t set_smem_limit(const void* fn);
+
+// kernels_tc.cu: split-BF16 tensor-core line operators (last level only)
+bool tc_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd);
+cudaError_t tc_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
+                      cudaStream_t s);
+
 // kernels_line.cu: register-blocked FP32 line operators
 bool line2_eligible(const Plan& P);
 cudaError_t line2_launch(bool fwd, const Plan& P, const Geo& G, const float* in, float* out, const LineIO& io,

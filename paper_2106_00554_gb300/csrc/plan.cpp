@@ -736,6 +736,7 @@ void uw_plan_destroy(uw_plan* P) {
   cudaFree(P->d_prefix);
   cudaFree(P->d_work);
   cudaFree(P->d_stage);
+  cudaFree(P->d_tc);
   delete P;
 }
 

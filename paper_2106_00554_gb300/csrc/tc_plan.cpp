@@ -1,0 +1,341 @@
+// Host construction (FP64) of the block matrices of the split-BF16
+// tensor-core line operators (kernels_tc.cu).
+//
+// The last synthesis level, the upsample-convolve T (Sec. 4.1 cell integrals)
+// and the first four Walsh-Hadamard stages (Sec. 3.1, natural order, bits 0-3)
+// are one linear map from a window of lo / hi coefficients to 16 consecutive
+// outputs.  Away from the VMP boundaries it is the same matrix for every
+// block (the interior two-scale and tap formulas are shift invariant), so the
+// device applies it as a GEMM against im2col windows.  The adjoint applies the
+// transposed map (Sec. 4.2) per block of 8 lo and 8 hi outputs.  Blocks that
+// touch a VMP boundary function use dense matrices built here from the exact
+// line operator (the formulas of Sec. 3.2 and 4.1 applied to unit vectors).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "uw_internal.h"
+
+namespace uw {
+namespace {
+
+int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+int ceildiv(int a, int b) { return -floordiv(-a, b); }
+int up16(int a) { return (a + 15) / 16 * 16; }
+int up32(int a) { return (a + 31) / 32 * 32; }
+int hsign(int a, int b) { return (__builtin_popcount((unsigned)(a & b)) & 1) ? -1 : 1; }
+
+uint16_t bf16_rn(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+  return (uint16_t)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+float bf16_f(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+uint32_t fbits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+
+// The exact last-level line operator of one plan in FP64: the per-output
+// formulas of the GPU FP64 path (synthesis with the boundary blocks, T with
+// the boundary rows, their transposes), whole lines at a time.
+struct Exact {
+  const Plan& P;
+  int p, Q, n0, M, N, Lb, ntap, tmin;
+  double sc;
+  bool per;
+  explicit Exact(const Plan& pl)
+      : P(pl), p(pl.p), Q(pl.Q), n0(pl.M / 2), M(pl.M), N(pl.N), Lb(pl.Lb), ntap(pl.ntap), tmin(-(pl.p - 1) * pl.Q),
+        sc(std::exp2(-0.5 * pl.R)), per(pl.bd == UW_BOUNDARY_PERIODIC) {}
+  static int wrap(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  void syn(const std::vector<double>& lo, const std::vector<double>& hi, std::vector<double>& s) const {
+    s.assign(M, 0.0);
+    for (int k = 0; k < M; ++k) {
+      double acc = 0;
+      if (per) {
+        for (int l = -p + 1; l <= p; ++l) {
+          int km = wrap(k - l, M);
+          if (km & 1) continue;
+          acc += P.h[l + p - 1] * lo[km >> 1] + P.g[l + p - 1] * hi[km >> 1];
+        }
+      } else {
+        int mlo = std::max(p, ceildiv(k - p, 2)), mhi = std::min(n0 - p - 1, floordiv(k + p - 1, 2));
+        for (int m = mlo; m <= mhi; ++m) acc += P.h[k - 2 * m + p - 1] * lo[m] + P.g[k - 2 * m + p - 1] * hi[m];
+        if (k < Lb)
+          for (int m = 0; m < p; ++m) acc += P.PL[m * Lb + k] * lo[m] + P.QL[m * Lb + k] * hi[m];
+        int c = M - 1 - k;
+        if (c < Lb)
+          for (int r = 0; r < p; ++r) acc += P.PR[r * Lb + c] * lo[n0 - 1 - r] + P.QR[r * Lb + c] * hi[n0 - 1 - r];
+      }
+      s[k] = acc;
+    }
+  }
+  void up(const std::vector<double>& s, std::vector<double>& v) const {
+    v.assign(N, 0.0);
+    for (int k = 0; k < N; ++k) {
+      double acc = 0;
+      for (int m = ceildiv(k - (p * Q - 1), Q); m <= floordiv(k - tmin, Q); ++m) {
+        double tap = P.taps[k - Q * m - tmin];
+        if (per) acc += tap * s[wrap(m, M)];
+        else if (m >= p && m <= M - p - 1) acc += tap * s[m];
+      }
+      if (!per) {
+        if (k < ntap)
+          for (int m = 0; m < p; ++m) acc += P.EL[m * ntap + k] * s[m];
+        int kk = N - 1 - k;
+        if (kk < ntap)
+          for (int r = 0; r < p; ++r) acc += P.ER[r * ntap + kk] * s[M - 1 - r];
+      }
+      v[k] = sc * acc;
+    }
+  }
+  void upT(const std::vector<double>& v, std::vector<double>& s) const {
+    s.assign(M, 0.0);
+    for (int m = 0; m < M; ++m) {
+      double acc = 0;
+      if (per) {
+        for (int i = 0; i < ntap; ++i) acc += P.taps[i] * v[wrap(Q * m + tmin + i, N)];
+      } else if (m < p) {
+        for (int k = 0; k < ntap; ++k) acc += P.EL[m * ntap + k] * v[k];
+      } else if (m >= M - p) {
+        int r = M - 1 - m;
+        for (int kk = 0; kk < ntap; ++kk) acc += P.ER[r * ntap + kk] * v[N - 1 - kk];
+      } else {
+        for (int i = 0; i < ntap; ++i) acc += P.taps[i] * v[Q * m + tmin + i];
+      }
+      s[m] = sc * acc;
+    }
+  }
+  void ana(const std::vector<double>& s, std::vector<double>& lo, std::vector<double>& hi) const {
+    lo.assign(n0, 0.0);
+    hi.assign(n0, 0.0);
+    for (int m = 0; m < n0; ++m) {
+      double a = 0, b = 0;
+      if (per) {
+        for (int l = -p + 1; l <= p; ++l) {
+          double v = s[wrap(2 * m + l, M)];
+          a += P.h[l + p - 1] * v;
+          b += P.g[l + p - 1] * v;
+        }
+      } else if (m < p) {
+        for (int c = 0; c < Lb; ++c) {
+          a += P.PL[m * Lb + c] * s[c];
+          b += P.QL[m * Lb + c] * s[c];
+        }
+      } else if (m >= n0 - p) {
+        int r = n0 - 1 - m;
+        for (int c = 0; c < Lb; ++c) {
+          a += P.PR[r * Lb + c] * s[M - 1 - c];
+          b += P.QR[r * Lb + c] * s[M - 1 - c];
+        }
+      } else {
+        for (int l = -p + 1; l <= p; ++l) {
+          a += P.h[l + p - 1] * s[2 * m + l];
+          b += P.g[l + p - 1] * s[2 * m + l];
+        }
+      }
+      lo[m] = a;
+      hi[m] = b;
+    }
+  }
+  // interior entry of the line matrix: d v[k] / d lo[i] (hi = false) or
+  // d v[k] / d hi[i] (hi = true), any integers k, i (shift invariant)
+  double interior(int k, int i, bool hi) const {
+    double acc = 0;
+    for (int m = ceildiv(k - (p * Q - 1), Q); m <= floordiv(k - tmin, Q); ++m) {
+      int l = m - 2 * i;
+      if (l < -p + 1 || l > p) continue;
+      acc += P.taps[k - Q * m - tmin] * (hi ? P.g[l + p - 1] : P.h[l + p - 1]);
+    }
+    return sc * acc;
+  }
+};
+
+// A (16 x 16 KS, row major, double) -> fragment-ordered BF16 parts of the
+// m16n8k16 A operand, A = A1 + A2 + A3 + O(2^-27 |A|) (each part the BF16
+// rounding of what the previous ones leave): per k-step and lane the words
+// a0..a3 of A1, then of A2, then of A3; a register holds columns (2t, 2t+1)
+// of row g (a0), g+8 (a1), and the same with columns + 8 (a2, a3); the lower
+// 16 bits hold the lower column.
+void pack_a(const std::vector<double>& A, int KS, std::vector<uint32_t>& w) {
+  const int K = 16 * KS;
+  for (int ks = 0; ks < KS; ++ks)
+    for (int lane = 0; lane < 32; ++lane) {
+      const int g = lane >> 2, t = lane & 3;
+      const int rows[4] = {g, g + 8, g, g + 8};
+      const int cols[4] = {2 * t, 2 * t, 2 * t + 8, 2 * t + 8};
+      uint32_t part[3][4];
+      for (int r = 0; r < 4; ++r) {
+        uint16_t b[3][2];
+        for (int e = 0; e < 2; ++e) {
+          double rest = A[(size_t)rows[r] * K + 16 * ks + cols[r] + e];
+          for (int s = 0; s < 3; ++s) {
+            b[s][e] = bf16_rn((float)rest);
+            rest -= (double)bf16_f(b[s][e]);
+          }
+        }
+        for (int s = 0; s < 3; ++s) part[s][r] = (uint32_t)b[s][0] | ((uint32_t)b[s][1] << 16);
+      }
+      for (int s = 0; s < 3; ++s)
+        for (int r = 0; r < 4; ++r) w.push_back(part[s][r]);
+    }
+}
+
+}  // namespace
+
+void build_tc(Plan& P, std::vector<uint32_t>& words) {
+  words.clear();
+  TcGeo& G = P.tc;
+  G = TcGeo{};
+  const int p = P.p, Q = P.Q, N = P.N, M = P.M, n0 = M / 2;
+  int L = 0;
+  while ((1 << L) < N) ++L;
+  if ((Q != 2 && Q != 4) || L < 9 || L > 13 || p > 10) return;
+  const bool per = P.bd == UW_BOUNDARY_PERIODIC;
+  const int tmin = -(p - 1) * Q, tmax = p * Q - 1;
+  Exact X(P);
+
+  // forward window (block n = 0): coefficients [imin, imax] reach its outputs
+  const int S0 = ceildiv(-tmax, Q), S1 = floordiv(15 - tmin, Q);
+  const int imin = ceildiv(S0 - p, 2), imax = floordiv(S1 + p - 1, 2);
+  G.bs = 8 / Q;
+  G.W0 = -imin + ((-imin) & 1);                // even, so 32-bit pairs stay aligned
+  G.lw = imax + G.W0 + 1;
+  G.lw += G.lw & 1;
+  G.KS = (2 * G.lw + 15) / 16;
+  G.HL = 16;
+  G.HR = 16;
+  if (G.W0 > G.HL || G.lw - G.W0 - G.bs > G.HR || G.KS > 3) return;
+  const int nb = N / 16;
+
+  // adjoint window (block c = 0: outputs lo / hi [0, 8))
+  const int kmin = Q * (-p + 1) + tmin, kmax = Q * (14 + p) + tmax;
+  G.W1 = up16(-kmin);
+  G.KSA = (kmax + G.W1 + 16) / 16;
+  G.HLa = up32(G.W1);
+  G.HRa = up32(std::max(0, 16 * G.KSA - 16 * Q - G.W1));
+  if (G.KSA > 16) return;
+  const int nbA = n0 / 8;
+
+  // boundary blocks (VMP): a forward block is interior when every coefficient
+  // and every s value it reads is an interior one; an adjoint block when its
+  // outputs are interior coefficients
+  if (!per) {
+    auto fwd_interior = [&](int n) {
+      const int a = G.bs * n + imin, b = G.bs * n + imax;
+      const int s0 = 16 * n / Q + S0, s1 = 16 * n / Q + S1;
+      return a >= p && b <= n0 - p - 1 && s0 >= P.Lb && s1 <= M - 1 - P.Lb && 16 * n >= P.ntap &&
+             16 * n + 15 <= N - 1 - P.ntap;
+    };
+    int lo = 0;
+    while (lo < nb && !fwd_interior(lo)) ++lo;
+    int hi = nb - 1;
+    while (hi >= 0 && !fwd_interior(hi)) --hi;
+    if (lo > hi) return;
+    for (int n = lo; n <= hi; ++n)
+      if (!fwd_interior(n)) return;
+    G.EBl = lo;
+    G.EBr = nb - 1 - hi;
+    const int reach_l = std::max(G.bs * (G.EBl - 1) + imax, p - 1) + 1;
+    const int reach_r = n0 - std::min(G.bs * (nb - G.EBr) + imin, n0 - p);
+    G.Xl = std::min(n0, std::max(reach_l, reach_r));
+    G.EAl = (p + 7) / 8;
+    G.EAr = (p + 7) / 8;
+    if (G.EAl + G.EAr >= nbA) return;
+    const int smax = std::max(2 * (8 * G.EAl - 1) + p, P.Lb - 1);
+    G.Wl = std::min(N, up16(std::max(Q * smax + tmax, P.ntap - 1) + 1));
+  }
+
+  // interior block matrices
+  const int K = 16 * G.KS, KA = 16 * G.KSA;
+  std::vector<double> Araw(16 * K, 0.0), A(16 * K, 0.0);
+  for (int r = 0; r < 16; ++r)
+    for (int c = 0; c < 2 * G.lw; ++c) {
+      const bool hi = c >= G.lw;
+      Araw[r * K + c] = X.interior(r, (c % G.lw) - G.W0, hi);
+    }
+  for (int r = 0; r < 16; ++r)
+    for (int c = 0; c < K; ++c) {
+      double a = 0;
+      for (int rr = 0; rr < 16; ++rr) a += hsign(r, rr) * Araw[rr * K + c];
+      A[r * K + c] = a;
+    }
+  std::vector<double> Braw(16 * KA, 0.0), B(16 * KA, 0.0);
+  for (int o = 0; o < 16; ++o)
+    for (int kk = 0; kk < KA; ++kk) Braw[o * KA + kk] = X.interior(kk - G.W1, o & 7, o >= 8);
+  for (int o = 0; o < 16; ++o)
+    for (int kk = 0; kk < KA; ++kk) {
+      const int j = kk / 16, r = kk % 16;
+      double a = 0;
+      for (int rr = 0; rr < 16; ++rr) a += Braw[o * KA + 16 * j + rr] * hsign(rr, r);
+      B[o * KA + kk] = a;
+    }
+
+  G.oAf = (int64_t)words.size();
+  pack_a(A, G.KS, words);
+  G.oAa = (int64_t)words.size();
+  pack_a(B, G.KSA, words);
+
+  // boundary matrices, stored input-major: E[c * rows + o]
+  if (!per) {
+    std::vector<double> lo(n0), hi(n0), s, v, u(N);
+    auto fwd_edge = [&](bool left) {
+      const int EB = left ? G.EBl : G.EBr, rows = 16 * EB;
+      for (int c = 0; c < 2 * G.Xl; ++c) {
+        std::fill(lo.begin(), lo.end(), 0.0);
+        std::fill(hi.begin(), hi.end(), 0.0);
+        const int i = (c % G.Xl) + (left ? 0 : n0 - G.Xl);
+        (c < G.Xl ? lo : hi)[i] = 1.0;
+        X.syn(lo, hi, s);
+        X.up(s, v);
+        for (int o = 0; o < rows; ++o) {
+          const int blk = (left ? 0 : nb - EB) + o / 16, r = o % 16;
+          double a = 0;
+          for (int rr = 0; rr < 16; ++rr) a += hsign(r, rr) * v[16 * blk + rr];
+          words.push_back(fbits((float)a));
+        }
+      }
+    };
+    G.oEfl = (int64_t)words.size();
+    fwd_edge(true);
+    G.oEfr = (int64_t)words.size();
+    fwd_edge(false);
+    auto adj_edge = [&](bool left) {
+      const int EA = left ? G.EAl : G.EAr, rows = 16 * EA;
+      for (int kk = 0; kk < G.Wl; ++kk) {
+        std::fill(u.begin(), u.end(), 0.0);
+        const int k = left ? kk : N - G.Wl + kk;
+        u[k] = 1.0;
+        std::vector<double> vv(N, 0.0);
+        const int blk = k / 16;
+        for (int r = 0; r < 16; ++r) vv[16 * blk + r] = hsign(r, k % 16);
+        X.upT(vv, s);
+        X.ana(s, lo, hi);
+        for (int o = 0; o < rows; ++o) {
+          const int c = (left ? 0 : nbA - EA) + o / 16, r = o % 16;
+          words.push_back(fbits((float)(r < 8 ? lo[8 * c + r] : hi[8 * c + r - 8])));
+        }
+      }
+    };
+    G.oEal = (int64_t)words.size();
+    adj_edge(true);
+    G.oEar = (int64_t)words.size();
+    adj_edge(false);
+  }
+  G.words = (int64_t)words.size();
+  G.ok = 1;
+}
+
+}  // namespace uw

@@ -30,6 +30,25 @@ struct Tables {
 // once).
 struct Profiler;
 
+// Geometry of the tensor-core (split-BF16) line operators of one plan (see
+// tc_plan.cpp).  Forward: 16 consecutive outputs of H16 (T Syn) per block,
+// from the lo / hi coefficients [bs n - W0, bs n - W0 + lw); adjoint: 8 lo and
+// 8 hi outputs per block c from the partially transformed samples
+// [16 Q c - W1, 16 Q c - W1 + 16 KSA).  Blocks next to a VMP boundary use
+// small dense matrices instead (EBl / EBr forward, EAl / EAr adjoint blocks).
+struct TcGeo {
+  int ok = 0;
+  int KS = 0, KSA = 0;      // k-steps (of 16) of the forward / adjoint block matrices
+  int W0 = 0, lw = 0, bs = 0;
+  int W1 = 0;
+  int EBl = 0, EBr = 0, Xl = 0;   // forward edge blocks; inputs per side (lo and hi each)
+  int EAl = 0, EAr = 0, Wl = 0;   // adjoint edge blocks; inputs per side
+  int HL = 0, HR = 0;       // forward halo (coefficients) left / right
+  int HLa = 0, HRa = 0;     // adjoint halo (samples) left / right
+  // word offsets into the device buffer d_tc
+  int64_t oAf = 0, oAa = 0, oEfl = 0, oEfr = 0, oEal = 0, oEar = 0, words = 0;
+};
+
 struct Plan {
   int d = 1, R = 0, q = 0, p = 1, bd = 0, J0 = 0;
   int M = 1, N = 1;          // per dimension
@@ -56,10 +75,15 @@ struct Plan {
   size_t stage_bytes = 0;
   int device = 0;
   Profiler* prof = nullptr;
+  TcGeo tc;                      // split-BF16 line operators (tc.ok = 0: not eligible)
+  void* d_tc = nullptr;
 };
 
 // plan.cpp
 bool build_tables(Plan& P, std::string& err);
+// tc_plan.cpp: block matrices of the tensor-core line operators (host, FP64);
+// fills P.tc and the packed words to upload (empty if not eligible)
+void build_tc(Plan& P, std::vector<uint32_t>& words);
 // kernels.cu
 int upload_tables(Plan& P);
 int launch_forward(const Plan& P, int prec, const void* x, void* y, int batch, void* stream, int* nlaunch);

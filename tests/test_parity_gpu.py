@@ -145,6 +145,26 @@ def test_2d_sweep_against_dense(p, bd, dR, q):
         assert rel(run_adj(plan, y, prec), want_x) < TOL[prec]
 
 
+@pytest.mark.parametrize("p,bd,R,q", [(5, VMP, 8, 1), (6, PERIODIC, 8, 1), (7, VMP, 7, 2), (8, VMP, 9, 1),
+                                       (9, PERIODIC, 9, 1), (10, VMP, 9, 1), (10, PERIODIC, 8, 1)])
+def test_2d_coarse_levels_long_filters(p, bd, R, q):
+    """Several coarse 2D levels with long filters: the per-level kernels'
+    small tiles (8 and 16 samples) meet the boundary blocks of both edges."""
+    rng = np.random.default_rng(2000 + 10 * p + bd)
+    J0 = W.default_J0(p)
+    M, N = 2 ** R, 2 ** (R + q)
+    omega = np.sort(rng.choice(N * N, size=(N * N) // 5, replace=False))
+    plan = Plan(2, R, q, p, bd, omega=omega)
+    G = dense.G1d(R, q, p, bd)
+    x = inputs.coeffs_2d(rng, R, J0, 1.0)
+    y = rng.standard_normal(omega.size)
+    want_y = dense.forward2d(x, R, q, p, bd, J0, omega, G=G)
+    want_x = dense.adjoint2d(y, R, q, p, bd, J0, omega, G=G)
+    for prec in (F64, F32):
+        assert rel(run_fwd(plan, x, prec), want_y) < TOL[prec]
+        assert rel(run_adj(plan, y, prec), want_x) < TOL[prec]
+
+
 @pytest.mark.parametrize("generic", [False, True])
 @pytest.mark.parametrize("p,bd,dR,q", [(2, VMP, 2, 1), (4, PERIODIC, 3, 2), (8, VMP, 4, 1), (3, VMP, 4, 1)])
 def test_fp32_line_kernels_both_implementations(monkeypatch, generic, p, bd, dR, q):
@@ -173,7 +193,7 @@ def test_fp32_line_kernels_both_implementations(monkeypatch, generic, p, bd, dR,
     assert rel(run_adj(plan2, y2, F32), dense.adjoint2d(y2, R, q, p, bd, J0, om2, G=G)) < 1e-5
 
 
-@pytest.mark.parametrize("prec", [F64, F32])
+@pytest.mark.parametrize("prec", [F64, F32, F32_SPLIT_BF16])
 def test_config3(prec):
     """p = 4, M = 256^2, q = 1, radial 25% mask, level decay 1.5, seed 2."""
     rng = np.random.default_rng(2)
@@ -187,6 +207,75 @@ def test_config3(prec):
     G = dense.G1d(R, q, p, VMP)
     assert rel(run_fwd(plan, x, prec), dense.forward2d(x, R, q, p, VMP, plan.J0, omega, G=G)) < TOL[prec]
     assert rel(run_adj(plan, y, prec), dense.adjoint2d(y, R, q, p, VMP, plan.J0, omega, G=G)) < TOL[prec]
+
+
+SPLIT_CASES = [(1, PERIODIC, 8, 1), (2, VMP, 8, 1), (3, VMP, 8, 2), (4, PERIODIC, 9, 1), (5, VMP, 9, 1),
+               (6, VMP, 8, 2), (8, VMP, 9, 1), (8, PERIODIC, 9, 2), (9, PERIODIC, 9, 2), (10, VMP, 9, 1),
+               (10, VMP, 8, 2)]
+
+
+def _kernel_names(plan):
+    from paper_2106_00554_gb300 import _lib
+    return [e["name"] for e in _lib.uw_plan_profile_read(plan._h)]
+
+
+@pytest.mark.parametrize("p,bd,R,q", SPLIT_CASES)
+def test_split_bf16_tensor_core_lines(p, bd, R, q):
+    """UW_F32_SPLIT_BF16: the tensor-core line operators (block GEMM of the
+    last level, T and bits 0-3; exact +-1 MMA for bits 4-7) against the dense
+    oracle, both boundary types, q = 1 and 2, batch 2."""
+    from paper_2106_00554_gb300 import _lib
+    rng = np.random.default_rng(3000 + 10 * p + bd + q)
+    J0 = W.default_J0(p)
+    M, N = 2 ** R, 2 ** (R + q)
+    omega = np.sort(rng.choice(N * N, size=(N * N) // 4, replace=False))
+    plan = Plan(2, R, q, p, bd, omega=omega, max_batch=2)
+    G = dense.G1d(R, q, p, bd)
+    x = np.stack([inputs.coeffs_2d(rng, R, J0, 1.0) for _ in range(2)])
+    y = rng.standard_normal((2, omega.size))
+    want_y = dense.forward2d(x, R, q, p, bd, J0, omega, G=G)
+    want_x = dense.adjoint2d(y, R, q, p, bd, J0, omega, G=G)
+    _lib.uw_plan_profile(plan._h, True)
+    got_y = run_fwd(plan, x, F32_SPLIT_BF16)
+    got_x = run_adj(plan, y, F32_SPLIT_BF16)
+    names = _kernel_names(plan)
+    _lib.uw_plan_profile(plan._h, False)
+    assert rel(got_y, want_y) < TOL[F32_SPLIT_BF16]
+    assert rel(got_x, want_x) < TOL[F32_SPLIT_BF16]
+    assert sum(n.endswith("_tc") for n in names) == 4, names
+
+
+def test_split_bf16_small_lines_use_fp32_kernels():
+    """Lines shorter than 512 samples are not served by the tensor-core
+    kernels; the split precision then runs the FP32 line kernels."""
+    from paper_2106_00554_gb300 import _lib
+    rng = np.random.default_rng(7)
+    R, q, p = 6, 1, 2
+    N = 2 ** (R + q)
+    omega = np.sort(rng.choice(N * N, size=N * N // 3, replace=False))
+    plan = Plan(2, R, q, p, VMP, omega=omega)
+    x = rng.standard_normal((2 ** R, 2 ** R))
+    _lib.uw_plan_profile(plan._h, True)
+    got = run_fwd(plan, x, F32_SPLIT_BF16)
+    names = _kernel_names(plan)
+    assert not any(n.endswith("_tc") for n in names)
+    want = dense.forward2d(x, R, q, p, VMP, plan.J0, omega)
+    assert rel(got, want) < 1e-5
+
+
+def test_config5_full_size_split_bf16():
+    """The benchmark workload (p = 8, M = 2048^2, q = 1, 12% radial mask,
+    seed 4) on the split-BF16 tensor-core path against the oracle."""
+    rng = np.random.default_rng(4)
+    R, q, p = 11, 1, 8
+    N = 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.12)
+    plan = Plan(2, R, q, p, VMP, omega=omega)
+    x = inputs.coeffs_2d(rng, R, plan.J0, 1.5)
+    y = rng.standard_normal(omega.size)
+    G = dense.G1d(R, q, p, VMP)
+    assert rel(run_fwd(plan, x, F32_SPLIT_BF16), dense.forward2d(x, R, q, p, VMP, plan.J0, omega, G=G)) < 1e-5
+    assert rel(run_adj(plan, y, F32_SPLIT_BF16), dense.adjoint2d(y, R, q, p, VMP, plan.J0, omega, G=G)) < 1e-5
 
 
 def test_config5_full_size_fp32():
