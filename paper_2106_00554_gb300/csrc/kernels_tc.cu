@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "line_common.cuh"
 
@@ -30,14 +31,14 @@ namespace uw {
 struct TcArgs {
   const uint32_t* Af;   // forward block matrix fragments (KS x 32 lanes x 8 words)
   const uint32_t* Aa;   // adjoint block matrix fragments (KSA x 32 x 8)
-  const float* Efl;     // forward boundary matrices, input-major
-  const float* Efr;
-  const float* Eal;     // adjoint boundary matrices, input-major
-  const float* Ear;
+  const float* Ef;      // forward boundary matrix: 16 (EBl + EBr) rows of stride SF
+  const float* Ea;      // adjoint boundary matrix: 16 (EAl + EAr) rows of stride SA
   int n0, M, N, L, per, nb, nbA;
   int W0, lw, bs, EBl, EBr, Xl;
   int W1, KSA, EAl, EAr, Wl, Q;
   int HL, HR, HLa, HRa;
+  int SF, SA;
+  int efs, eas;         // 1: the boundary matrix is staged in shared memory
 };
 
 // FP32 sample buffer: 8 words of padding per 32 keep the stage-2 fragment
@@ -70,17 +71,84 @@ __device__ __forceinline__ void split3(float x0, float x1, uint32_t& p1, uint32_
   p3 = c;
 }
 
-// the six part products of order <= 2: d += (A1 + A2 + A3)(B1 + B2 + B3)
-__device__ __forceinline__ void mma_split(float (&d)[4], const uint32_t (&a1)[4], const uint32_t (&a2)[4],
-                                          const uint32_t (&a3)[4], const uint32_t (&b)[3][2]) {
-  mma_bf16(d, a3, b[0][0], b[0][1]);
-  mma_bf16(d, a2, b[1][0], b[1][1]);
-  mma_bf16(d, a1, b[2][0], b[2][1]);
+// the six part products of order <= 2 of (A1 + A2 + A3)(B1 + B2 + B3): the
+// three leading ones into d, the three small ones into e (two independent
+// accumulation chains; the caller adds them)
+__device__ __forceinline__ void mma_split(float (&d)[4], float (&e)[4], const uint32_t (&a1)[4],
+                                          const uint32_t (&a2)[4], const uint32_t (&a3)[4],
+                                          const uint32_t (&b)[3][2]) {
+  mma_bf16(e, a3, b[0][0], b[0][1]);
   mma_bf16(d, a2, b[0][0], b[0][1]);
+  mma_bf16(e, a2, b[1][0], b[1][1]);
   mma_bf16(d, a1, b[1][0], b[1][1]);
+  mma_bf16(e, a1, b[2][0], b[2][1]);
   mma_bf16(d, a1, b[0][0], b[0][1]);
 }
 
+// asynchronous global -> shared copies (no register staging); completion is
+// awaited with cp.async.wait_group
+__device__ __forceinline__ void cp16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp4(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// The mask row of line l (words and raw prefix counts, plus the next row's
+// first prefix) copied asynchronously; r1 of the last row is the sample count.
+__device__ __forceinline__ void issue_row(const LineIO& io, int mrow, uint32_t* smask, int* spraw, int tid, int nt) {
+  const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
+  const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
+  for (int w4 = tid; w4 < io.wpr / 4; w4 += nt) {
+    cp16(smask + 4 * w4, mk + 4 * w4);
+    cp16(spraw + 4 * w4, pf + 4 * w4);
+  }
+  if (tid == 0 && mrow + 1 < io.mask_rows) cp4(spraw + io.wpr, pf + io.wpr);
+}
+
+// sample j (absolute packed position) of a staged row: the last word w with
+// spraw[w] <= j, then the bit of rank j - spraw[w] in that word
+__device__ __forceinline__ int sample_index_raw(const uint32_t* smask, const int* spraw, int wpr, int j) {
+  int lo = 0, hi = wpr - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (spraw[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo * 32 + select_bit(smask[lo], j - spraw[lo]);
+}
+
+// One dot product per boundary row: w row-major weights (stride ld, nin a
+// multiple of 4), x the matching inputs; gsz threads per row, each taking
+// float4 chunks part, part + gsz, ..., reduced with shuffles.  sink(o, v)
+// receives row o from the first thread of its group.
+template <typename XPTR, typename SINK>
+__device__ __forceinline__ void row_dots(const float* w, int ld, int rows, int nin, int gsz, const XPTR& xrow,
+                                         const SINK& sink, int tid, int nt) {
+  const int nq = nin / 4;
+  for (int ob = 0; ob < rows; ob += nt / gsz) {
+    const int o = ob + tid / gsz, part = tid % gsz;
+    float acc0 = 0.f, acc1 = 0.f;
+    if (o < rows) {
+      const float4* e = reinterpret_cast<const float4*>(w + (size_t)o * ld);
+      const float4* x = reinterpret_cast<const float4*>(xrow(o));
+      for (int c4 = part; c4 < nq; c4 += gsz) {
+        const float4 ev = e[c4], xv = x[c4];
+        acc0 = fmaf(ev.x, xv.x, acc0);
+        acc1 = fmaf(ev.y, xv.y, acc1);
+        acc0 = fmaf(ev.z, xv.z, acc0);
+        acc1 = fmaf(ev.w, xv.w, acc1);
+      }
+    }
+    float acc = acc0 + acc1;
+    for (int off = gsz >> 1; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (o < rows && part == 0) sink(o, acc);
+  }
+}
 
 // rows r0, r0 + 1 of H16 at column c as a BF16 pair (exact +-1)
 __device__ __forceinline__ uint32_t hpair(int r0, int c) {
@@ -89,13 +157,14 @@ __device__ __forceinline__ uint32_t hpair(int r0, int c) {
   return a | (b << 16);
 }
 
-// Walsh-Hadamard transform over bits 8..L-1 of the padded line: thread
-// `low` (< 256) owns the pencil low + 256 j
+// Walsh-Hadamard transform over bits 8..L-1 of the padded line: pencil
+// `low` (< 256) holds low + 256 j, at pv(low) + 320 j
 template <int R>
 __device__ __forceinline__ void wht_pencil(float* sV, int low) {
+  float* v = sV + pv(low);
   float a[R];
 #pragma unroll
-  for (int j = 0; j < R; ++j) a[j] = sV[pv(low + 256 * j)];
+  for (int j = 0; j < R; ++j) a[j] = v[320 * j];
 #pragma unroll
   for (int h = 1; h < R; h <<= 1)
 #pragma unroll
@@ -106,41 +175,52 @@ __device__ __forceinline__ void wht_pencil(float* sV, int low) {
         a[j + h] = x - y;
       }
 #pragma unroll
-  for (int j = 0; j < R; ++j) sV[pv(low + 256 * j)] = a[j];
+  for (int j = 0; j < R; ++j) v[320 * j] = a[j];
 }
 
-__device__ __forceinline__ void fwht_high(float* sV, int ng, int tid) {
-  switch (ng) {
-    case 2: wht_pencil<2>(sV, tid); break;
-    case 4: wht_pencil<4>(sV, tid); break;
-    case 8: wht_pencil<8>(sV, tid); break;
-    case 16: wht_pencil<16>(sV, tid); break;
-    default: wht_pencil<32>(sV, tid); break;
+__device__ __forceinline__ void fwht_high(float* sV, int ng, int tid, int nt) {
+  for (int low = tid; low < 256; low += nt) {
+    switch (ng) {
+      case 2: wht_pencil<2>(sV, low); break;
+      case 4: wht_pencil<4>(sV, low); break;
+      case 8: wht_pencil<8>(sV, low); break;
+      case 16: wht_pencil<16>(sV, low); break;
+      default: wht_pencil<32>(sV, low); break;
+    }
   }
 }
 
 __device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
 // ---------------------------------------------------------------------------
-// forward: 256 threads, persistent over lines
+// forward: 256 threads, persistent over lines; the next line's coefficients
+// (and mask row) are copied into shared memory while the current one runs
 // ---------------------------------------------------------------------------
-template <int KS>
-__global__ void __launch_bounds__(256, 2) k_tc_fwd(const float* __restrict__ in, float* __restrict__ out, TcArgs a,
+template <int KS, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_tc_fwd(const float* __restrict__ in, float* __restrict__ out, TcArgs a,
                                                    LineIO io, int total) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int n0 = a.n0, N = a.N, ng = N >> 8;
+  const int n0 = a.n0, N = a.N, M = a.M, ng = N >> 8;
   const int clen = a.HL + n0 + a.HR;
+  const int wst = io.mode == 1 ? io.wpr + 4 : 0;     // staged mask words / prefixes per buffer
   float* sV = reinterpret_cast<float*>(smem_raw);
   uint4* sA = reinterpret_cast<uint4*>(sV + pvlen(N));            // KS x 32 lanes x 3 parts
-  float* sEdge = reinterpret_cast<float*>(sA + KS * 96);
-  // coefficient parts: cp[3 * half + part], half 0 = lo (scaling), 1 = hi (detail)
-  uint16_t* cp0 = reinterpret_cast<uint16_t*>(sEdge + 16 * (a.EBl + a.EBr) + 4);
-  uint32_t* smask = reinterpret_cast<uint32_t*>(cp0 + 6 * clen + 8);
-  int* spre = reinterpret_cast<int*>(smask + io.wpr);
+  float* sIn = reinterpret_cast<float*>(sA + KS * 96);            // 2 x M staged coefficients
+  float* sEdge = sIn + 2 * M;
+  uint32_t* smask = reinterpret_cast<uint32_t*>(sEdge + 16 * (a.EBl + a.EBr) + 4);   // 2 x wst
+  int* spraw = reinterpret_cast<int*>(smask + 2 * wst);                               // 2 x wst
+  // coefficient parts: cp0[(3 * half + part) * clen + i], half 0 = lo, 1 = hi
+  uint16_t* cp0 = reinterpret_cast<uint16_t*>(spraw + 2 * wst);
+  // boundary matrix, staged when it fits (a.efs), else read from global memory
+  const int Rf = 16 * (a.EBl + a.EBr);
+  float* sEfs = reinterpret_cast<float*>(cp0 + ((6 * clen + 8 + 7) & ~7));
+  const float* Ef = a.efs ? sEfs : a.Ef;
+  if (a.efs)
+    for (int i = tid; i < Rf * a.SF / 4; i += NT) reinterpret_cast<float4*>(sEfs)[i] = reinterpret_cast<const float4*>(a.Ef)[i];
 
-  for (int i = tid; i < KS * 96; i += 256) sA[i] = reinterpret_cast<const uint4*>(a.Af)[i];
+  for (int i = tid; i < KS * 96; i += NT) sA[i] = reinterpret_cast<const uint4*>(a.Af)[i];
   uint32_t Hb[2][2];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
@@ -149,18 +229,34 @@ __global__ void __launch_bounds__(256, 2) k_tc_fwd(const float* __restrict__ in,
   }
   // VMP halos stay zero (only boundary blocks, whose results are replaced,
   // read them)
-  for (int i = tid; i < clen; i += 256)
+  for (int i = tid; i < clen; i += NT)
     if (i < a.HL || i >= a.HL + n0)
       for (int c = 0; c < 6; ++c) cp0[c * clen + i] = 0;
 
-  for (int line = blockIdx.x; line < total; line += gridDim.x) {
-    const int l = line % io.lines;
-    const int64_t b = line / io.lines;
+  auto issue = [&](int ln, int bi) {
+    const int l = ln % io.lines;
+    const int64_t b = ln / io.lines;
     const int drow = io.seq_rows ? seqrow(l, a.L) : l;
     const float* src = in + b * io.in_batch + (int64_t)drow * io.in_stride;
-    // (1) load the coefficient line, split into BF16 parts (with periodic halos)
-    for (int e4 = tid; e4 < a.M / 4; e4 += 256) {
-      const float4 x = __ldg(reinterpret_cast<const float4*>(src) + e4);
+    float* dst = sIn + bi * M;
+    for (int e4 = tid; e4 < M / 4; e4 += NT) cp16(dst + 4 * e4, src + 4 * e4);
+    if (io.mode == 1) issue_row(io, io.mask_rows == 1 ? 0 : l, smask + bi * wst, spraw + bi * wst, tid, NT);
+  };
+  if ((int)blockIdx.x < total) issue(blockIdx.x, 0);
+  cp_commit();
+
+  int buf = 0;
+  for (int line = blockIdx.x; line < total; line += gridDim.x, buf ^= 1) {
+    if (line + (int)gridDim.x < total) issue(line + gridDim.x, buf ^ 1);
+    cp_commit();
+    cp_wait1();
+    __syncthreads();
+    const int l = line % io.lines;
+    const int64_t b = line / io.lines;
+    const float* xin = sIn + buf * M;
+    // (1) split the staged line into BF16 parts (with periodic halos)
+    for (int e4 = tid; e4 < M / 4; e4 += NT) {
+      const float4 x = *reinterpret_cast<const float4*>(xin + 4 * e4);
       const int i = 4 * e4;
       const int half = i >= n0;
       const int ii = i - (half ? n0 : 0);
@@ -178,31 +274,44 @@ __global__ void __launch_bounds__(256, 2) k_tc_fwd(const float* __restrict__ in,
         }
       }
     }
-    // (2) VMP boundary blocks in FP32 from the line itself
+    // (2) VMP boundary blocks in FP32 from the staged line
     if (!a.per) {
-      for (int o = tid; o < 16 * (a.EBl + a.EBr); o += 256) {
-        const bool left = o < 16 * a.EBl;
-        const int oo = left ? o : o - 16 * a.EBl, rows = 16 * (left ? a.EBl : a.EBr);
-        const float* E = left ? a.Efl : a.Efr;
-        const int base = left ? 0 : n0 - a.Xl;
-        float acc = 0.f;
-        for (int c = 0; c < 2 * a.Xl; ++c) {
-          const float x = __ldg(src + (c < a.Xl ? base + c : n0 + base + c - a.Xl));
-          acc = fmaf(__ldg(E + c * rows + oo), x, acc);
+      // row o: 16 (EBl + EBr) rows, two threads each (the lo and the hi
+      // weights); the window starts at 0 (left rows) or n0 - Xl (right rows)
+      const int nl = 16 * a.EBl, X4 = a.Xl;
+      auto xrow = [&](int o2) {
+        const int o = o2 >> 1, part = o2 & 1;
+        return xin + (o < nl ? 0 : n0 - X4) + part * n0;
+      };
+      auto wrow = [&](int o2) { return Ef + (size_t)(o2 >> 1) * a.SF + (o2 & 1) * X4; };
+      for (int ob = 0; ob < 2 * Rf; ob += NT) {
+        const int o2 = ob + tid;
+        float acc0 = 0.f, acc1 = 0.f;
+        if (o2 < 2 * Rf) {
+          const float4* e = reinterpret_cast<const float4*>(wrow(o2));
+          const float4* x = reinterpret_cast<const float4*>(xrow(o2));
+          for (int c4 = 0; c4 < X4 / 4; ++c4) {
+            const float4 ev = e[c4], xv = x[c4];
+            acc0 = fmaf(ev.x, xv.x, acc0);
+            acc1 = fmaf(ev.y, xv.y, acc1);
+            acc0 = fmaf(ev.z, xv.z, acc0);
+            acc1 = fmaf(ev.w, xv.w, acc1);
+          }
         }
-        sEdge[o] = acc;
+        float acc = acc0 + acc1;
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (o2 < 2 * Rf && !(o2 & 1)) sEdge[o2 >> 1] = acc;
       }
     }
-    int64_t r0 = 0;
-    int cnt = 0;
-    if (io.mode == 1) stage_row(io, io.mask_rows == 1 ? 0 : l, io.mask_rows, smask, spre, r0, cnt, tid, 256);
     __syncthreads();
 
     // (3) stages 1 and 2, one group of 16 blocks (256 outputs) per warp step
-    for (int grp = warp; grp < ng; grp += 8) {
-      float c[2][4];
+    for (int grp = warp; grp < ng; grp += NT / 32) {
+      float c[2][4], cs[2][4];
 #pragma unroll
-      for (int j = 0; j < 2; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) c[j][r] = cs[j][r] = 0.f;
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) {
         uint32_t A1[4], A2[4], A3[4];
@@ -230,9 +339,13 @@ __global__ void __launch_bounds__(256, 2) k_tc_fwd(const float* __restrict__ in,
               bq[pt][hh] = ok ? v : 0u;
             }
           }
-          mma_split(c[j], A1, A2, A3, bq);
+          mma_split(c[j], cs[j], A1, A2, A3, bq);
         }
       }
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) c[j][r] += cs[j][r];
       if (!a.per) {
 #pragma unroll
         for (int j = 0; j < 2; ++j)
@@ -259,92 +372,162 @@ __global__ void __launch_bounds__(256, 2) k_tc_fwd(const float* __restrict__ in,
         mma_bf16(d, q[2], Hb[j][0], Hb[j][1]);
         mma_bf16(d, q[1], Hb[j][0], Hb[j][1]);
         mma_bf16(d, q[0], Hb[j][0], Hb[j][1]);
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int kidx = 16 * (16 * grp + 8 * j + 2 * t + e) + g;
-          sV[pv(kidx)] = d[e];
-          sV[pv(kidx + 8)] = d[2 + e];
-        }
+        // natural index 16 (16 grp + 8 j + 2 t + e) + g (+8) sits at
+        // pv = 320 grp + 160 j + 40 t + 16 e + g (+8)
+        float* v = sV + 320 * grp + 160 * j + 40 * t + g;
+        v[0] = d[0];
+        v[16] = d[1];
+        v[8] = d[2];
+        v[24] = d[3];
       }
     }
     __syncthreads();
     // (4) bits 8..L-1
-    fwht_high(sV, ng, tid);
+    fwht_high(sV, ng, tid, NT);
     __syncthreads();
     // (5) store the natural-order line or gather the samples
     if (io.mode == 1) {
-      float* y = out + b * io.m + r0;
-      for (int j = tid; j < cnt; j += 256) y[j] = sV[pv(seqrow(sample_index(smask, spre, io.wpr, j), a.L))];
+      const uint32_t* mk = smask + buf * wst;
+      const int* pr = spraw + buf * wst;
+      const int mrow = io.mask_rows == 1 ? 0 : l;
+      const int r0 = pr[0];
+      const int r1 = mrow + 1 < io.mask_rows ? pr[io.wpr] : (int)io.m;
+      float* y = out + b * io.m;
+      for (int j = r0 + tid; j < r1; j += NT) y[j] = sV[pv(seqrow(sample_index_raw(mk, pr, io.wpr, j), a.L))];
     } else {
       float4* dst = reinterpret_cast<float4*>(out + b * io.out_batch + (int64_t)l * io.out_stride);
-      for (int k4 = tid; k4 < N / 4; k4 += 256) dst[k4] = *reinterpret_cast<const float4*>(sV + pv(4 * k4));
+      const float* v = sV + pv(4 * tid);
+      for (int k4 = tid, o = 0; k4 < N / 4; k4 += NT, o += 5 * NT) dst[k4] = *reinterpret_cast<const float4*>(v + o);
     }
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// adjoint: 256 threads, persistent over lines
+// adjoint: 256 threads, persistent over lines; the next line's samples (a
+// natural-order line, or the packed samples and the mask row) are copied into
+// shared memory while the current one runs
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 2) k_tc_adj(const float* __restrict__ in, float* __restrict__ out, TcArgs a,
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict__ in, float* __restrict__ out, TcArgs a,
                                                    LineIO io, int total) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int n0 = a.n0, N = a.N, ng = N >> 8;
   const int ulen = a.HLa + N + a.HRa;              // BF16 elements per part
-  const int uwords = pw(ulen / 2) + 4;
-  float* sV = reinterpret_cast<float*>(smem_raw);
-  uint4* sA = reinterpret_cast<uint4*>(sV + pvlen(N));   // KSA x 32 lanes x 3 parts
-  uint32_t* u0 = reinterpret_cast<uint32_t*>(sA + a.KSA * 96);   // 3 parts of uwords each
-  uint32_t* smask = u0 + 3 * uwords;
-  int* spre = reinterpret_cast<int*>(smask + io.wpr);
+  const int uwords = (pw(ulen / 2) + 4 + 3) & ~3;   // multiple of 4: later arrays stay 16-byte aligned
+  const bool scat = io.mode == 1;
+  const int wst = scat ? io.wpr + 4 : 0;
+  const int vst = pvlen(N);
+  // mode 0: two sample buffers sV[2][vst] (the staged line is transformed in
+  // place); mode 1: one sV, staged packed samples sY[2][N] and mask rows
+  float* sV0 = reinterpret_cast<float*>(smem_raw);
+  uint4* sA = reinterpret_cast<uint4*>(sV0 + (scat ? 1 : 2) * vst);   // KSA x 32 lanes x 3 parts
+  uint32_t* u0 = reinterpret_cast<uint32_t*>(sA + a.KSA * 96);        // 3 parts of uwords each
+  uint32_t* smask = u0 + 3 * uwords;                                   // 2 x wst
+  int* spraw = reinterpret_cast<int*>(smask + 2 * wst);                // 2 x wst
+  float* sY = reinterpret_cast<float*>(spraw + 2 * wst);               // 2 x N (mode 1)
+  // FP32 copies of the samples the boundary rows read (after bits 4..L-1):
+  // [0, Wl) and [N - Wl, N); the boundary matrix, staged when it fits
+  float* sUe = sY + (scat ? 2 * N : 0);
+  const int Ra = 16 * (a.EAl + a.EAr);
+  float* sEas = sUe + 2 * a.Wl;
+  const float* Ea = a.eas ? sEas : a.Ea;
+  if (a.eas)
+    for (int i = tid; i < Ra * a.SA / 4; i += NT) reinterpret_cast<float4*>(sEas)[i] = reinterpret_cast<const float4*>(a.Ea)[i];
 
-  for (int i = tid; i < a.KSA * 96; i += 256) sA[i] = reinterpret_cast<const uint4*>(a.Aa)[i];
+  for (int i = tid; i < a.KSA * 96; i += NT) sA[i] = reinterpret_cast<const uint4*>(a.Aa)[i];
   uint32_t Hb[2][2];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     Hb[j][0] = hpair(2 * t, g + 8 * j);
     Hb[j][1] = hpair(2 * t + 8, g + 8 * j);
   }
-  for (int w = tid; w < 3 * uwords; w += 256) u0[w] = 0u;   // halos (VMP) start and stay zero
+  for (int w = tid; w < 3 * uwords; w += NT) u0[w] = 0u;   // halos (VMP) start and stay zero
   uint16_t* u16 = reinterpret_cast<uint16_t*>(u0);
   auto uidx = [&](int e) {  // element e in [-HLa, N + HRa) -> 16-bit slot of part 0
     const int x = e + a.HLa;
     return 2 * pw(x >> 1) + (x & 1);
   };
+
+  // staging: mode 0 copies the natural-order line into sV[bi]; mode 1 first
+  // the mask row (issue_pre), later the packed samples (issue_y)
+  auto issue_pre = [&](int ln, int bi) {
+    const int l = ln % io.lines;
+    const int64_t b = ln / io.lines;
+    if (!scat) {
+      const float* src = in + b * io.in_batch + (int64_t)l * io.in_stride;
+      float* dst = sV0 + bi * vst;
+      float* d0 = dst + pv(4 * tid);
+      for (int k4 = tid, o = 0; k4 < N / 4; k4 += NT, o += 5 * NT) cp16(d0 + o, src + 4 * k4);
+    } else {
+      issue_row(io, io.mask_rows == 1 ? 0 : l, smask + bi * wst, spraw + bi * wst, tid, NT);
+    }
+  };
+  auto row_range = [&](int ln, int& r0, int& r1) {
+    const int mrow = io.mask_rows == 1 ? 0 : ln % io.lines;
+    r0 = __ldg(io.prefix + (int64_t)mrow * io.wpr);
+    r1 = mrow + 1 < io.mask_rows ? __ldg(io.prefix + (int64_t)(mrow + 1) * io.wpr) : (int)io.m;
+  };
+  auto issue_y = [&](int ln, int bi, int r0, int r1) {
+    const float* y = in + (ln / io.lines) * io.m;
+    float* dst = sY + bi * N;
+    for (int j = r0 + tid; j < r1; j += NT) cp4(dst + (j - r0), y + j);
+  };
+  if ((int)blockIdx.x < total) {
+    issue_pre(blockIdx.x, 0);
+    if (scat) {
+      int r0, r1;
+      row_range(blockIdx.x, r0, r1);
+      issue_y(blockIdx.x, 0, r0, r1);
+    }
+  }
+  cp_commit();
   __syncthreads();
 
-  for (int line = blockIdx.x; line < total; line += gridDim.x) {
+  int buf = 0;
+  for (int line = blockIdx.x; line < total; line += gridDim.x, buf ^= 1) {
+    const int nxt = line + gridDim.x;
+    int nr0 = 0, nr1 = 0;
+    if (nxt < total) {
+      issue_pre(nxt, buf ^ 1);
+      if (scat) row_range(nxt, nr0, nr1);      // used after stage 2
+    }
+    cp_commit();
+    cp_wait1();
+    __syncthreads();
     const int l = line % io.lines;
     const int64_t b = line / io.lines;
-    // (1) input: natural-order samples, or scatter of the sampled indices
-    if (io.mode == 0) {
-      const float4* src = reinterpret_cast<const float4*>(in + b * io.in_batch + (int64_t)l * io.in_stride);
-      for (int k4 = tid; k4 < N / 4; k4 += 256) *reinterpret_cast<float4*>(sV + pv(4 * k4)) = __ldg(src + k4);
-    } else {
-      int64_t r0;
-      int cnt;
-      stage_row(io, io.mask_rows == 1 ? 0 : l, io.mask_rows, smask, spre, r0, cnt, tid, 256);
-      for (int k = tid; k < pvlen(N); k += 256) sV[k] = 0.f;
+    float* sV = sV0 + (scat ? 0 : buf * vst);
+    // (1) mode 1: scatter the staged samples into zeros
+    if (scat) {
+      const uint32_t* mk = smask + buf * wst;
+      const int* pr = spraw + buf * wst;
+      const int mrow = io.mask_rows == 1 ? 0 : l;
+      const int r0 = pr[0];
+      const int r1 = mrow + 1 < io.mask_rows ? pr[io.wpr] : (int)io.m;
+      for (int k = tid; k < vst; k += NT) sV[k] = 0.f;
       __syncthreads();
-      const float* y = in + b * io.m + r0;
-      for (int j = tid; j < cnt; j += 256) sV[pv(seqrow(sample_index(smask, spre, io.wpr, j), a.L))] = __ldg(y + j);
+      const float* ys = sY + buf * N;
+      for (int j = r0 + tid; j < r1; j += NT) sV[pv(seqrow(sample_index_raw(mk, pr, io.wpr, j), a.L))] = ys[j - r0];
+      __syncthreads();
     }
-    __syncthreads();
     // (2) bits 8..L-1 (the Hadamard stages commute)
-    fwht_high(sV, ng, tid);
+    fwht_high(sV, ng, tid, NT);
     __syncthreads();
     // (3) bits 4-7 on the tensor cores; the result, split into BF16 parts,
     // is the im2col source of stage 1
-    for (int grp = warp; grp < ng; grp += 8) {
+    for (int grp = warp; grp < ng; grp += NT / 32) {
       const int k0 = 256 * grp;
+      // element (row r, block n) of the group at pv(k0 + 16 n + r) =
+      // 320 grp + 40 (n / 2) + 16 (n % 2) + r for n < 16, r < 16
+      const float* v = sV + 320 * grp + 40 * t + g;
       uint32_t q[3][4];
-      split3(sV[pv(k0 + 16 * (2 * t) + g)], sV[pv(k0 + 16 * (2 * t + 1) + g)], q[0][0], q[1][0], q[2][0]);
-      split3(sV[pv(k0 + 16 * (2 * t) + g + 8)], sV[pv(k0 + 16 * (2 * t + 1) + g + 8)], q[0][1], q[1][1], q[2][1]);
-      split3(sV[pv(k0 + 16 * (2 * t + 8) + g)], sV[pv(k0 + 16 * (2 * t + 9) + g)], q[0][2], q[1][2], q[2][2]);
-      split3(sV[pv(k0 + 16 * (2 * t + 8) + g + 8)], sV[pv(k0 + 16 * (2 * t + 9) + g + 8)], q[0][3], q[1][3],
-             q[2][3]);
+      split3(v[0], v[16], q[0][0], q[1][0], q[2][0]);
+      split3(v[8], v[24], q[0][1], q[1][1], q[2][1]);
+      split3(v[160], v[176], q[0][2], q[1][2], q[2][2]);
+      split3(v[168], v[184], q[0][3], q[1][3], q[2][3]);
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         float d[4] = {0.f, 0.f, 0.f, 0.f};
@@ -354,6 +537,10 @@ __global__ void __launch_bounds__(256, 2) k_tc_adj(const float* __restrict__ in,
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) {
           const int kidx = k0 + 16 * (8 * j + 2 * t + (qq & 1)) + g + (qq >> 1) * 8;
+          if (!a.per) {
+            if (kidx < a.Wl) sUe[kidx] = d[qq];
+            else if (kidx >= N - a.Wl) sUe[kidx - (N - 2 * a.Wl)] = d[qq];
+          }
           uint32_t w1, w2, w3;
           split3(d[qq], 0.f, w1, w2, w3);
           const uint16_t v1 = (uint16_t)(w1 & 0xffffu), v2 = (uint16_t)(w2 & 0xffffu), v3 = (uint16_t)(w3 & 0xffffu);
@@ -379,29 +566,27 @@ __global__ void __launch_bounds__(256, 2) k_tc_adj(const float* __restrict__ in,
       }
     }
     __syncthreads();
+    // the next line's packed samples (its row range was read above)
+    if (scat && nxt < total) issue_y(nxt, buf ^ 1, nr0, nr1);
+    cp_commit();
     const int drow = io.seq_rows ? seqrow(l, a.L) : l;
     float* dst = out + b * io.out_batch + (int64_t)drow * io.out_stride;
     // (4) VMP boundary blocks in FP32 (samples rebuilt from their parts)
     if (!a.per) {
-      for (int o = tid; o < 16 * (a.EAl + a.EAr); o += 256) {
-        const bool left = o < 16 * a.EAl;
-        const int oo = left ? o : o - 16 * a.EAl, rows = 16 * (left ? a.EAl : a.EAr);
-        const float* E = left ? a.Eal : a.Ear;
-        const int kb = left ? 0 : N - a.Wl;
-        float acc = 0.f;
-        for (int kk = 0; kk < a.Wl; ++kk) {
-          const int s = uidx(kb + kk);
-          const float u = __uint_as_float((uint32_t)u16[s] << 16) + __uint_as_float((uint32_t)u16[2 * uwords + s] << 16) +
-                          __uint_as_float((uint32_t)u16[4 * uwords + s] << 16);
-          acc = fmaf(__ldg(E + kk * rows + oo), u, acc);
-        }
+      const int nl = 16 * a.EAl;
+      const int q = NT / Ra, gsz = q >= 8 ? 8 : (q >= 4 ? 4 : (q >= 2 ? 2 : 1));
+      auto xrow = [&](int o) { return sUe + (o < nl ? 0 : a.Wl); };
+      auto sink = [&](int o, float v) {
+        const bool left = o < nl;
+        const int oo = left ? o : o - nl;
         const int c = (left ? 0 : a.nbA - a.EAr) + oo / 16, r = oo % 16;
-        dst[r < 8 ? 8 * c + r : n0 + 8 * c + r - 8] = acc;
-      }
+        dst[r < 8 ? 8 * c + r : n0 + 8 * c + r - 8] = v;
+      };
+      row_dots(Ea, a.SA, Ra, a.Wl, gsz, xrow, sink, tid, NT);
     }
     // (5) stage 1: 8 lo and 8 hi outputs per block, 8 blocks per n-tile
-    for (int tile = warp; tile < a.nbA / 8; tile += 8) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int tile = warp; tile < a.nbA / 8; tile += NT / 32) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
       const int base = 16 * a.Q * (8 * tile + g) - a.W1 + a.HLa;   // element offset, even
       for (int ks = 0; ks < a.KSA; ++ks) {
         const uint4 x1 = sA[(ks * 32 + lane) * 3], x2 = sA[(ks * 32 + lane) * 3 + 1], x3 = sA[(ks * 32 + lane) * 3 + 2];
@@ -415,14 +600,14 @@ __global__ void __launch_bounds__(256, 2) k_tc_adj(const float* __restrict__ in,
           bq[pt][0] = u0[pt * uwords + s0];
           bq[pt][1] = u0[pt * uwords + s1];
         }
-        mma_split(c, A1, A2, A3, bq);
+        mma_split(c, cs, A1, A2, A3, bq);
       }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int cb = 8 * tile + 2 * t + e;
         if (a.per || (cb >= a.EAl && cb < a.nbA - a.EAr)) {
-          dst[8 * cb + g] = c[e];
-          dst[n0 + 8 * cb + g] = c[2 + e];
+          dst[8 * cb + g] = c[e] + cs[e];
+          dst[n0 + 8 * cb + g] = c[2 + e] + cs[2 + e];
         }
       }
     }
@@ -433,16 +618,23 @@ __global__ void __launch_bounds__(256, 2) k_tc_adj(const float* __restrict__ in,
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// boundary matrices up to this size are staged in shared memory
+static const size_t kEdgeStage = 32 * 1024;
+static size_t tc_efs_bytes(const Plan& P) { return sizeof(float) * 16 * (P.tc.EBl + P.tc.EBr) * (size_t)P.tc.SF; }
+static size_t tc_eas_bytes(const Plan& P) { return sizeof(float) * 16 * (P.tc.EAl + P.tc.EAr) * (size_t)P.tc.SA; }
+
 static TcArgs tc_args(const Plan& P) {
   const TcGeo& G = P.tc;
   const uint32_t* w = (const uint32_t*)P.d_tc;
   TcArgs a{};
   a.Af = w + G.oAf;
   a.Aa = w + G.oAa;
-  a.Efl = (const float*)(w + G.oEfl);
-  a.Efr = (const float*)(w + G.oEfr);
-  a.Eal = (const float*)(w + G.oEal);
-  a.Ear = (const float*)(w + G.oEar);
+  a.Ef = (const float*)(w + G.oEf);
+  a.Ea = (const float*)(w + G.oEa);
+  a.SF = G.SF;
+  a.SA = G.SA;
+  a.efs = tc_efs_bytes(P) <= kEdgeStage;
+  a.eas = tc_eas_bytes(P) <= kEdgeStage;
   a.n0 = P.M / 2; a.M = P.M; a.N = P.N;
   int L = 0;
   while ((1 << L) < P.N) ++L;
@@ -455,18 +647,24 @@ static TcArgs tc_args(const Plan& P) {
   return a;
 }
 
-static size_t tc_fwd_smem(const Plan& P) {
+static size_t tc_fwd_smem(const Plan& P, bool gather) {
   const TcGeo& G = P.tc;
   const size_t clen = (size_t)G.HL + P.M / 2 + G.HR;
-  return sizeof(float) * pvlen(P.N) + (size_t)G.KS * 96 * 16 + sizeof(float) * (16 * (G.EBl + G.EBr) + 4) +
-         6 * clen * sizeof(uint16_t) + 16 + 2 * sizeof(uint32_t) * P.wpr + 16;
+  const size_t wst = gather ? (size_t)P.wpr + 4 : 0;
+  const size_t ef = tc_efs_bytes(P) <= kEdgeStage ? tc_efs_bytes(P) : 0;
+  return sizeof(float) * pvlen(P.N) + (size_t)G.KS * 96 * 16 + sizeof(float) * 2 * P.M +
+         sizeof(float) * (16 * (G.EBl + G.EBr) + 4) + 2 * 2 * wst * 4 + ((6 * clen + 8 + 7) & ~(size_t)7) * 2 + ef +
+         16;
 }
 
-static size_t tc_adj_smem(const Plan& P) {
+static size_t tc_adj_smem(const Plan& P, bool scatter) {
   const TcGeo& G = P.tc;
   const int ulen = G.HLa + P.N + G.HRa;
-  const size_t uwords = (size_t)((ulen / 2) + 4 * ((ulen / 2) >> 4)) + 4;
-  return sizeof(float) * pvlen(P.N) + (size_t)G.KSA * 96 * 16 + 3 * uwords * 4 + 2 * sizeof(uint32_t) * P.wpr + 16;
+  const size_t uwords = ((size_t)((ulen / 2) + 4 * ((ulen / 2) >> 4)) + 4 + 3) & ~(size_t)3;
+  const size_t wst = scatter ? (size_t)P.wpr + 4 : 0;
+  const size_t ea = tc_eas_bytes(P) <= kEdgeStage ? tc_eas_bytes(P) : 0;
+  return sizeof(float) * pvlen(P.N) * (scatter ? 1 : 2) + (size_t)G.KSA * 96 * 16 + 3 * uwords * 4 + 2 * 2 * wst * 4 +
+         (scatter ? sizeof(float) * 2 * P.N : 0) + sizeof(float) * 2 * G.Wl + ea + 16;
 }
 
 bool tc_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd) {
@@ -475,48 +673,49 @@ bool tc_eligible(const Plan& P, const LineIO& io, const void* in, const void* ou
   if (fwd) {
     if (!al16(in) || io.in_stride % 4 || io.in_batch % 4) return false;
     if (io.mode == 0 && (!al16(out) || io.out_stride % 4 || io.out_batch % 4)) return false;
-    return tc_fwd_smem(P) <= 110 * 1024;
+    return tc_fwd_smem(P, io.mode == 1) <= 112 * 1024;
   }
   if (io.mode == 0 && (!al16(in) || io.in_stride % 4 || io.in_batch % 4)) return false;
-  return tc_adj_smem(P) <= 110 * 1024;
+  return tc_adj_smem(P, io.mode == 1) <= 112 * 1024;
 }
 
 template <typename K>
-static int persistent_grid(K kernel, size_t smem, int total) {
+static int persistent_grid(K kernel, int nt, size_t smem, int total) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, nt, smem);
   return std::max(1, std::min(total, std::max(per, 1) * nsm));
+}
+
+template <int NT>
+static void tc_go(bool fwd, const Plan& P, const TcArgs& a, const float* in, float* out, const LineIO& io, int total,
+                  cudaStream_t s) {
+  if (fwd) {
+    const size_t sm = tc_fwd_smem(P, io.mode == 1);
+    auto go = [&](auto kern) {
+      set_smem_limit((const void*)kern);
+      kern<<<persistent_grid(kern, NT, sm, total), NT, sm, s>>>(in, out, a, io, total);
+    };
+    if (P.tc.KS == 1) go(k_tc_fwd<1, NT>);
+    else if (P.tc.KS == 2) go(k_tc_fwd<2, NT>);
+    else go(k_tc_fwd<3, NT>);
+  } else {
+    const size_t sm = tc_adj_smem(P, io.mode == 1);
+    set_smem_limit((const void*)k_tc_adj<NT>);
+    k_tc_adj<NT><<<persistent_grid(k_tc_adj<NT>, NT, sm, total), NT, sm, s>>>(in, out, a, io, total);
+  }
 }
 
 cudaError_t tc_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
                       cudaStream_t s) {
-  TcArgs a = tc_args(P);
-  if (fwd) {
-    const size_t sm = tc_fwd_smem(P);
-    switch (P.tc.KS) {
-      case 1: {
-        set_smem_limit((const void*)k_tc_fwd<1>);
-        k_tc_fwd<1><<<persistent_grid(k_tc_fwd<1>, sm, total), 256, sm, s>>>(in, out, a, io, total);
-        break;
-      }
-      case 2: {
-        set_smem_limit((const void*)k_tc_fwd<2>);
-        k_tc_fwd<2><<<persistent_grid(k_tc_fwd<2>, sm, total), 256, sm, s>>>(in, out, a, io, total);
-        break;
-      }
-      default: {
-        set_smem_limit((const void*)k_tc_fwd<3>);
-        k_tc_fwd<3><<<persistent_grid(k_tc_fwd<3>, sm, total), 256, sm, s>>>(in, out, a, io, total);
-        break;
-      }
-    }
-  } else {
-    const size_t sm = tc_adj_smem(P);
-    set_smem_limit((const void*)k_tc_adj);
-    k_tc_adj<<<persistent_grid(k_tc_adj, sm, total), 256, sm, s>>>(in, out, a, io, total);
-  }
+  const TcArgs a = tc_args(P);
+  static const int nt = [] {
+    const char* e = std::getenv("UW_TC_THREADS");
+    return (e && std::atoi(e) == 128) ? 128 : 256;
+  }();
+  if (nt == 256) tc_go<256>(fwd, P, a, in, out, io, total, s);
+  else tc_go<128>(fwd, P, a, in, out, io, total, s);
   return cudaGetLastError();
 }
 

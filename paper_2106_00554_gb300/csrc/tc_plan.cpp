@@ -251,11 +251,13 @@ void build_tc(Plan& P, std::vector<uint32_t>& words) {
     const int reach_l = std::max(G.bs * (G.EBl - 1) + imax, p - 1) + 1;
     const int reach_r = n0 - std::min(G.bs * (nb - G.EBr) + imin, n0 - p);
     G.Xl = std::min(n0, std::max(reach_l, reach_r));
+    if ((G.Xl + 3) / 4 * 4 > n0) return;
     G.EAl = (p + 7) / 8;
     G.EAr = (p + 7) / 8;
     if (G.EAl + G.EAr >= nbA) return;
     const int smax = std::max(2 * (8 * G.EAl - 1) + p, P.Lb - 1);
-    G.Wl = std::min(N, up16(std::max(Q * smax + tmax, P.ntap - 1) + 1));
+    G.Wl = up16(std::max(Q * smax + tmax, P.ntap - 1) + 1);
+    if (2 * G.Wl > N) return;
   }
 
   // interior block matrices
@@ -291,48 +293,61 @@ void build_tc(Plan& P, std::vector<uint32_t>& words) {
   // boundary matrices, stored input-major: E[c * rows + o]
   if (!per) {
     std::vector<double> lo(n0), hi(n0), s, v, u(N);
-    auto fwd_edge = [&](bool left) {
-      const int EB = left ? G.EBl : G.EBr, rows = 16 * EB;
-      for (int c = 0; c < 2 * G.Xl; ++c) {
+    // forward: rows (left blocks, then right blocks) of 16 outputs; a row
+    // holds X4 lo then X4 hi coefficient weights (window [0, X4) on the left,
+    // [n0 - X4, n0) on the right), padded to the stride SF
+    const int X4 = (G.Xl + 3) / 4 * 4;
+    G.Xl = X4;
+    G.SF = 2 * X4 + 4;
+    const int Rf = 16 * (G.EBl + G.EBr);
+    std::vector<double> Ef((size_t)Rf * G.SF, 0.0);
+    for (int side = 0; side < 2; ++side) {
+      const bool left = side == 0;
+      const int EB = left ? G.EBl : G.EBr, row0 = left ? 0 : 16 * G.EBl;
+      for (int c = 0; c < 2 * X4; ++c) {
         std::fill(lo.begin(), lo.end(), 0.0);
         std::fill(hi.begin(), hi.end(), 0.0);
-        const int i = (c % G.Xl) + (left ? 0 : n0 - G.Xl);
-        (c < G.Xl ? lo : hi)[i] = 1.0;
+        const int i = (c % X4) + (left ? 0 : n0 - X4);
+        (c < X4 ? lo : hi)[i] = 1.0;
         X.syn(lo, hi, s);
         X.up(s, v);
-        for (int o = 0; o < rows; ++o) {
+        for (int o = 0; o < 16 * EB; ++o) {
           const int blk = (left ? 0 : nb - EB) + o / 16, r = o % 16;
           double a = 0;
           for (int rr = 0; rr < 16; ++rr) a += hsign(r, rr) * v[16 * blk + rr];
-          words.push_back(fbits((float)a));
+          Ef[(size_t)(row0 + o) * G.SF + c] = a;
         }
       }
-    };
-    G.oEfl = (int64_t)words.size();
-    fwd_edge(true);
-    G.oEfr = (int64_t)words.size();
-    fwd_edge(false);
-    auto adj_edge = [&](bool left) {
-      const int EA = left ? G.EAl : G.EAr, rows = 16 * EA;
+    }
+    while (words.size() % 4) words.push_back(0);   // 16-byte aligned rows on the device
+    G.oEf = (int64_t)words.size();
+    for (double e : Ef) words.push_back(fbits((float)e));
+    // adjoint: rows (left blocks, then right blocks) of 8 lo and 8 hi
+    // outputs; a row holds the weights of the samples [0, Wl) on the left,
+    // [N - Wl, N) on the right (before the bits 0-3 transform), stride SA
+    G.SA = G.Wl + 4;
+    const int Ra = 16 * (G.EAl + G.EAr);
+    std::vector<double> Ea((size_t)Ra * G.SA, 0.0);
+    for (int side = 0; side < 2; ++side) {
+      const bool left = side == 0;
+      const int EA = left ? G.EAl : G.EAr, row0 = left ? 0 : 16 * G.EAl;
       for (int kk = 0; kk < G.Wl; ++kk) {
         std::fill(u.begin(), u.end(), 0.0);
-        const int k = left ? kk : N - G.Wl + kk;
-        u[k] = 1.0;
+        const int kq = left ? kk : N - G.Wl + kk;
         std::vector<double> vv(N, 0.0);
-        const int blk = k / 16;
-        for (int r = 0; r < 16; ++r) vv[16 * blk + r] = hsign(r, k % 16);
+        const int blk = kq / 16;
+        for (int r = 0; r < 16; ++r) vv[16 * blk + r] = hsign(r, kq % 16);
         X.upT(vv, s);
         X.ana(s, lo, hi);
-        for (int o = 0; o < rows; ++o) {
+        for (int o = 0; o < 16 * EA; ++o) {
           const int c = (left ? 0 : nbA - EA) + o / 16, r = o % 16;
-          words.push_back(fbits((float)(r < 8 ? lo[8 * c + r] : hi[8 * c + r - 8])));
+          Ea[(size_t)(row0 + o) * G.SA + kk] = r < 8 ? lo[8 * c + r] : hi[8 * c + r - 8];
         }
       }
-    };
-    G.oEal = (int64_t)words.size();
-    adj_edge(true);
-    G.oEar = (int64_t)words.size();
-    adj_edge(false);
+    }
+    while (words.size() % 4) words.push_back(0);
+    G.oEa = (int64_t)words.size();
+    for (double e : Ea) words.push_back(fbits((float)e));
   }
   G.words = (int64_t)words.size();
   G.ok = 1;

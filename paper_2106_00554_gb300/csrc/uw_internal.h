@@ -41,12 +41,13 @@ struct TcGeo {
   int KS = 0, KSA = 0;      // k-steps (of 16) of the forward / adjoint block matrices
   int W0 = 0, lw = 0, bs = 0;
   int W1 = 0;
-  int EBl = 0, EBr = 0, Xl = 0;   // forward edge blocks; inputs per side (lo and hi each)
-  int EAl = 0, EAr = 0, Wl = 0;   // adjoint edge blocks; inputs per side
+  int EBl = 0, EBr = 0, Xl = 0;   // forward edge blocks; inputs per side (lo and hi each, multiple of 4)
+  int EAl = 0, EAr = 0, Wl = 0;   // adjoint edge blocks; inputs per side (multiple of 16)
+  int SF = 0, SA = 0;       // row strides of the forward / adjoint edge matrices
   int HL = 0, HR = 0;       // forward halo (coefficients) left / right
   int HLa = 0, HRa = 0;     // adjoint halo (samples) left / right
   // word offsets into the device buffer d_tc
-  int64_t oAf = 0, oAa = 0, oEfl = 0, oEfr = 0, oEal = 0, oEar = 0, words = 0;
+  int64_t oAf = 0, oAa = 0, oEf = 0, oEa = 0, words = 0;
 };
 
 struct Plan {
