@@ -16,7 +16,6 @@
 // w_n(k/N) = (-1)^{sum_j (n^(j) xor n^(j+1)) k^(L+1-j)} = (-1)^{popcount(r(n) & k)},
 // r(n) = bitreverse_L(n xor (n >> 1)).  So the natural-order (Hadamard) FWHT
 // output at index r(n) is the sequency coefficient n, and (d) reads it there.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,6 +44,8 @@ __global__ void __launch_bounds__(256) k_line_fwd(const T* __restrict__ in, T* _
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
   int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
   T* s0 = sm + off;
   T* s1 = s0 + G.M;
   T* v = s1 + G.M;
@@ -110,6 +111,8 @@ __global__ void __launch_bounds__(256) k_line_adj(const T* __restrict__ in, T* _
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
   int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
   T* s0 = sm + off;
   T* s1 = s0 + G.M;
   T* v = s1 + G.M;
@@ -363,6 +366,8 @@ __global__ void k_transpose(const T* __restrict__ in, T* __restrict__ out, int r
                             int64_t in_batch, int64_t out_batch, const T* __restrict__ alt, int64_t alt_batch,
                             T* __restrict__ altout, int br, int bc, int ldalt) {
   __shared__ T tile[32][33];
+  pdl_trigger();
+  pdl_wait();
   const int64_t b = blockIdx.z;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -539,6 +544,8 @@ __global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
   const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
   const int n0 = 1 << j, n1 = 2 * n0;
   const int tiles = n1 / TS;
   const int r0 = (blockIdx.x / tiles) * TS, c0 = (blockIdx.x % tiles) * TS;
@@ -599,6 +606,8 @@ __global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, 
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
   const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
   const int n0 = 1 << j, n1 = 2 * n0;
   const int tiles = n0 / TS;  // TS: output coefficients per dimension and quadrant
   const int m0 = (blockIdx.x / tiles) * TS, k0 = (blockIdx.x % tiles) * TS;
@@ -656,143 +665,6 @@ __global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, 
   }
 }
 
-// All coarse levels of the 2D Mallat IDWT (forward) or DWT (adjoint) in one
-// cooperative launch: each level is a row pass and a column pass of the
-// per-output formulas spread over the whole grid, separated by grid-wide
-// barriers.  The detail blocks are read from (forward) or written to (adjoint)
-// the caller's coefficient array directly; XS holds the running low-pass
-// block (leading dimension Mh), XS2 the half-synthesised one.
-//   forward: levels jfrom .. jto-1, the LL block of level jfrom read from x
-//   adjoint: levels jto-1 .. jfrom, the LL block of level jfrom written to x
-template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_coop(const T* __restrict__ xin, T* xout, T* XS, T* XS2, int M,
-                                                     int Mh, int jfrom, int jto, int fwd, int batch, Tables<T> tab,
-                                                     Geo G) {
-  namespace cg = cooperative_groups;
-  cg::grid_group grid = cg::this_grid();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  SmemTables<T> st;
-  stage_tables(tab, G, sm, st, threadIdx.x, blockDim.x);
-  __syncthreads();
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
-  const int64_t MM = (int64_t)M * M, HH = (int64_t)Mh * Mh;
-  for (int it = 0; it < jto - jfrom; ++it) {
-    const int j = fwd ? jfrom + it : jto - 1 - it;
-    const int n0 = 1 << j, n1 = 2 * n0;
-    const int64_t tot = (int64_t)batch * n1 * n1, toth = (int64_t)batch * n1 * n0;
-    if (fwd) {
-      for (int64_t i = gt; i < tot; i += gs) {            // rows -> XS2
-        const int kk = (int)(i % n1);
-        const int64_t rr = i / n1;
-        const int r = (int)(rr % n1);
-        const int64_t b = rr / n1;
-        const T* xr = xin + b * MM + (int64_t)r * M;
-        const T* lop = (r < n0) ? ((j == jfrom) ? xr : XS + b * HH + (int64_t)r * Mh) : xr;
-        Plain<T> lo{lop}, hi{xr + n0};
-        XS2[b * HH + (int64_t)r * Mh + kk] = syn_one<T>(kk, n0, lo, hi, st, G);
-      }
-      grid.sync();
-      for (int64_t i = gt; i < tot; i += gs) {            // columns -> XS
-        const int c = (int)(i % n1);
-        const int64_t rr = i / n1;
-        const int kk = (int)(rr % n1);
-        const int64_t b = rr / n1;
-        Strided<T> lo{XS2 + b * HH + c, Mh}, hi{XS2 + b * HH + (int64_t)n0 * Mh + c, Mh};
-        XS[b * HH + (int64_t)kk * Mh + c] = syn_one<T>(kk, n0, lo, hi, st, G);
-      }
-      grid.sync();
-    } else {
-      for (int64_t i = gt; i < toth; i += gs) {           // columns of XS -> XS2
-        const int c = (int)(i % n1);
-        const int64_t rr = i / n1;
-        const int mm = (int)(rr % n0);
-        const int64_t b = rr / n0;
-        Strided<T> s{XS + b * HH + c, Mh};
-        T lo, hi;
-        ana_one<T>(mm, n0, s, st, G, lo, hi);
-        XS2[b * HH + (int64_t)mm * Mh + c] = lo;
-        XS2[b * HH + (int64_t)(n0 + mm) * Mh + c] = hi;
-      }
-      grid.sync();
-      for (int64_t i = gt; i < toth; i += gs) {           // rows of XS2 -> XS / x
-        const int mm = (int)(i % n0);
-        const int64_t rr = i / n0;
-        const int r = (int)(rr % n1);
-        const int64_t b = rr / n1;
-        Plain<T> s{XS2 + b * HH + (int64_t)r * Mh};
-        T lo, hi;
-        ana_one<T>(mm, n0, s, st, G, lo, hi);
-        T* xr = xout + b * MM + (int64_t)r * M;
-        if (r < n0 && j > jfrom) XS[b * HH + (int64_t)r * Mh + mm] = lo;
-        else xr[mm] = lo;
-        xr[n0 + mm] = hi;
-      }
-      grid.sync();
-    }
-  }
-}
-
-// All small coarse levels of the 2D Mallat IDWT / DWT in one CTA: the n x n
-// top-left block (n <= 128 for FP32) stays in shared memory across levels; one
-// level is a row pass and a column pass of the per-output formulas.
-//   forward: levels jfrom .. jto-1 (block 2^jfrom -> 2^jto), in place in buf
-//   adjoint: levels jto-1 .. jfrom
-template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse_small(T* buf, int64_t ld, int64_t bstride, int jfrom, int jto,
-                                                       int fwd, Tables<T> tab, Geo G) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  SmemTables<T> st;
-  const int off = stage_tables(tab, G, sm, st, tid, nthr);
-  const int n = 1 << jto;
-  T* A = sm + off;          // n x n, row stride n + 1
-  T* Bf = A + n * (n + 1);
-  const int ls = n + 1;
-  T* g = buf + blockIdx.x * bstride;
-  for (int i = tid; i < n * n; i += nthr) A[(i / n) * ls + i % n] = g[(int64_t)(i / n) * ld + i % n];
-  __syncthreads();
-  for (int it = 0; it < jto - jfrom; ++it) {
-    const int j = fwd ? jfrom + it : jto - 1 - it;
-    const int n0 = 1 << j, n1 = 2 * n0;
-    if (fwd) {
-      for (int i = tid; i < n1 * n1; i += nthr) {      // rows: Bf[r][k]
-        int r = i / n1, kk = i % n1;
-        Plain<T> lo{A + r * ls}, hi{A + r * ls + n0};
-        Bf[r * ls + kk] = syn_one<T>(kk, n0, lo, hi, st, G);
-      }
-      __syncthreads();
-      for (int i = tid; i < n1 * n1; i += nthr) {      // columns: A[k][c]
-        int c = i % n1, kk = i / n1;
-        Strided<T> lo{Bf + c, ls}, hi{Bf + n0 * ls + c, ls};
-        A[kk * ls + c] = syn_one<T>(kk, n0, lo, hi, st, G);
-      }
-      __syncthreads();
-    } else {
-      for (int i = tid; i < n1 * n0; i += nthr) {      // columns: Bf[m][c], Bf[n0+m][c]
-        int c = i % n1, mm = i / n1;
-        Strided<T> s{A + c, ls};
-        T lo, hi;
-        ana_one<T>(mm, n0, s, st, G, lo, hi);
-        Bf[mm * ls + c] = lo;
-        Bf[(n0 + mm) * ls + c] = hi;
-      }
-      __syncthreads();
-      for (int i = tid; i < n1 * n0; i += nthr) {      // rows: A[r][m], A[r][n0+m]
-        int r = i / n0, mm = i % n0;
-        Plain<T> s{Bf + r * ls};
-        T lo, hi;
-        ana_one<T>(mm, n0, s, st, G, lo, hi);
-        A[r * ls + mm] = lo;
-        A[r * ls + n0 + mm] = hi;
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = tid; i < n * n; i += nthr) g[(int64_t)(i / n) * ld + i % n] = A[(i / n) * ls + i % n];
-}
-
 // FP32 transpose with 64 x 64 tiles and 16-byte global accesses; rows,
 // cols, br and bc are multiples of 64, so a tile is entirely inside or
 // outside the spliced block (same semantics as k_transpose).
@@ -801,6 +673,8 @@ __global__ void __launch_bounds__(256) k_transpose64(const float* __restrict__ i
                                                      const float* __restrict__ alt, int64_t alt_batch,
                                                      float* __restrict__ altout, int br, int bc, int ldalt) {
   __shared__ float tile[64][65];
+  pdl_trigger();
+  pdl_wait();
   const int64_t b = blockIdx.z;
   const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
   const int t = threadIdx.x, c4 = t & 15, rw = t >> 4;
@@ -873,16 +747,6 @@ template <typename T>
 static bool line_fits(const Plan& P) { return line_smem<T>(P) <= kSmemMax; }
 
 // largest level whose 2^j x 2^j block (two copies) fits one CTA's shared memory
-template <typename T>
-static int small_top() { return 6; }
-
-template <typename T>
-static size_t coarse_smem(const Plan& P, int jto) {
-  Geo G = geo_of(P);
-  const size_t n = (size_t)1 << jto;
-  return sizeof(T) * ((size_t)table_count(G) + 2 * n * (n + 1));
-}
-
 template <typename T>
 static void set_table_ptrs(Tables<T>& t, const T* base, const std::vector<const std::vector<double>*>& parts) {
   const T** slots[9] = {&t.h, &t.g, &t.taps, &t.EL, &t.ER, &t.PL, &t.QL, &t.PR, &t.QR};
@@ -1019,6 +883,10 @@ struct Launcher {
     cudaEventRecord(cur.a, s);
     armed = true;
   }
+  // record the status of a cudaLaunchKernelEx launch
+  void note(cudaError_t e) {
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  }
   // rename the armed launch (same bytes), e.g. when a line operator takes
   // the tensor-core kernel
   void retag(const std::string& name) {
@@ -1100,10 +968,10 @@ static void launch_line(bool fwd, const Plan& P, const Geo& G, const T* in, T* o
   size_t sm = line_smem<T>(P);
   if (fwd) {
     set_smem<T>((const void*)k_line_fwd<T>, sm);
-    k_line_fwd<T><<<nblocks, line_threads(P.N), sm, L.s>>>(in, out, tabs<T>(P), G, io);
+    L.note(launch_pdl(k_line_fwd<T>, dim3(nblocks), dim3(line_threads(P.N)), sm, L.s, in, out, tabs<T>(P), G, io));
   } else {
     set_smem<T>((const void*)k_line_adj<T>, sm);
-    k_line_adj<T><<<nblocks, line_threads(P.N), sm, L.s>>>(in, out, tabs<T>(P), G, io);
+    L.note(launch_pdl(k_line_adj<T>, dim3(nblocks), dim3(line_threads(P.N)), sm, L.s, in, out, tabs<T>(P), G, io));
   }
 }
 
@@ -1112,40 +980,23 @@ void launch_line<float>(bool fwd, const Plan& P, const Geo& G, const float* in, 
                         int nblocks, Launcher& L) {
   if (L.split && tc_eligible(P, io, in, out, fwd)) {
     if (L.armed) L.retag(P.prof->names[L.cur.id] + "_tc");
-    tc_launch(fwd, P, in, out, io, nblocks, L.s);
+    L.note(tc_launch(fwd, P, in, out, io, nblocks, L.s));
     return;
   }
   if (line2_eligible(P) && !getenv_flag("UW_GENERIC_LINES")) {
-    line2_launch(fwd, P, G, in, out, io, nblocks, L.s);
+    L.note(line2_launch(fwd, P, G, in, out, io, nblocks, L.s));
     return;
   }
   size_t sm = line_smem<float>(P);
   if (fwd) {
     set_smem<float>((const void*)k_line_fwd<float>, sm);
-    k_line_fwd<float><<<nblocks, line_threads(P.N), sm, L.s>>>(in, out, tabs<float>(P), G, io);
+    L.note(launch_pdl(k_line_fwd<float>, dim3(nblocks), dim3(line_threads(P.N)), sm, L.s, in, out, tabs<float>(P), G,
+                      io));
   } else {
     set_smem<float>((const void*)k_line_adj<float>, sm);
-    k_line_adj<float><<<nblocks, line_threads(P.N), sm, L.s>>>(in, out, tabs<float>(P), G, io);
+    L.note(launch_pdl(k_line_adj<float>, dim3(nblocks), dim3(line_threads(P.N)), sm, L.s, in, out, tabs<float>(P), G,
+                      io));
   }
-}
-
-template <typename T>
-static void launch_coarse(const Plan& P, const Geo& G, const T* xin, T* xout, T* XS, T* XS2, int batch, bool fwd,
-                          Launcher& L) {
-  const size_t sm = sizeof(T) * (size_t)table_count(G);
-  set_smem<T>((const void*)k_coarse_coop<T>, sm);
-  int per_sm = 0, nsm = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_coop<T>, 256, sm);
-  const int64_t work = (int64_t)batch * (P.M / 2) * (P.M / 2);
-  int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * nsm, (work + 255) / 256));
-  int M = P.M, Mh = P.M / 2, jfrom = P.J0, jto = P.R - 1, f = fwd ? 1 : 0;
-  Tables<T> tb = tabs<T>(P);
-  Geo g = G;
-  void* args[] = {(void*)&xin, (void*)&xout, (void*)&XS, (void*)&XS2, &M, &Mh, &jfrom, &jto, &f, &batch, &tb, &g};
-  cudaLaunchCooperativeKernel((const void*)k_coarse_coop<T>, dim3(grid), dim3(256), args, sm, L.s);
-  L.check();
 }
 
 // coarse levels J0 .. R-2 of the 2D Mallat transform, one fused kernel per
@@ -1216,8 +1067,8 @@ static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xou
       coarse_dispatch<T>(G.p, [&](auto pc) {
         constexpr int PP = decltype(pc)::value;
         set_smem_limit((const void*)k_syn2d_level<T, PP>);
-        k_syn2d_level<T, PP><<<dim3(tiles * tiles, batch), thr, sm, L.s>>>(src, ld, sb, x, M, dst, Mh, HH, j, TS,
-                                                                          tabs<T>(P), G);
+        L.note(launch_pdl(k_syn2d_level<T, PP>, dim3(tiles * tiles, batch), dim3(thr), sm, L.s, src, ld, sb, x, M,
+                          dst, (int64_t)Mh, HH, j, TS, tabs<T>(P), G));
       });
     } else {
       const int TS = ana_tile(n0), tiles = n0 / TS;
@@ -1231,8 +1082,8 @@ static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xou
       coarse_dispatch<T>(G.p, [&](auto pc) {
         constexpr int PP = decltype(pc)::value;
         set_smem_limit((const void*)k_ana2d_level<T, PP>);
-        k_ana2d_level<T, PP><<<dim3(tiles * tiles, batch), thr, sm, L.s>>>(src, Mh, HH, xout, M, dst, Mh, HH, j, TS,
-                                                                          tabs<T>(P), G);
+        L.note(launch_pdl(k_ana2d_level<T, PP>, dim3(tiles * tiles, batch), dim3(thr), sm, L.s, src, (int64_t)Mh, HH,
+                          xout, M, dst, (int64_t)Mh, HH, j, TS, tabs<T>(P), G));
       });
     }
     L.check();
@@ -1246,7 +1097,8 @@ static void launch_transpose(const T* in, T* out, int rows, int cols, int64_t in
                              Launcher& L) {
   dim3 tb(32, 8);
   dim3 tg((cols + 31) / 32, (rows + 31) / 32, batch);
-  k_transpose<T><<<tg, tb, 0, L.s>>>(in, out, rows, cols, in_batch, out_batch, alt, alt_batch, altout, br, bc, ldalt);
+  L.note(launch_pdl(k_transpose<T>, tg, tb, 0, L.s, in, out, rows, cols, in_batch, out_batch, alt, alt_batch, altout,
+                    br, bc, ldalt));
 }
 
 template <>
@@ -1262,12 +1114,13 @@ void launch_transpose<float>(const float* in, float* out, int rows, int cols, in
   if (!ok) {
     dim3 tb(32, 8);
     dim3 tg((cols + 31) / 32, (rows + 31) / 32, batch);
-    k_transpose<float><<<tg, tb, 0, L.s>>>(in, out, rows, cols, in_batch, out_batch, alt, alt_batch, altout, br, bc,
-                                           ldalt);
+    L.note(launch_pdl(k_transpose<float>, tg, tb, 0, L.s, in, out, rows, cols, in_batch, out_batch, alt, alt_batch,
+                      altout, br, bc, ldalt));
     return;
   }
   dim3 tg(cols / 64, rows / 64, batch);
-  k_transpose64<<<tg, 256, 0, L.s>>>(in, out, rows, cols, in_batch, out_batch, alt, alt_batch, altout, br, bc, ldalt);
+  L.note(launch_pdl(k_transpose64, tg, dim3(256), 0, L.s, in, out, rows, cols, in_batch, out_batch, alt, alt_batch,
+                    altout, br, bc, ldalt));
 }
 
 // 1D, the whole line in shared memory.

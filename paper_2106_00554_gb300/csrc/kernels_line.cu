@@ -92,6 +92,8 @@ __global__ void __launch_bounds__(512) k_line2_fwd(const float* __restrict__ in,
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<float> st;
   const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
   float* sIn = sm + off;
   float* sS = sIn + p32len(G.M);
   float* v = sS + p32len(G.M);
@@ -232,6 +234,8 @@ __global__ void __launch_bounds__(512) k_line2_adj(const float* __restrict__ in,
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<float> st;
   const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
   float* sIn = sm + off;
   float* sS = sIn + p32len(G.M);
   float* v = sS + p32len(G.M);
@@ -447,10 +451,10 @@ static cudaError_t go(bool fwd, const Plan& P, const Geo& G, const float* in, fl
   size_t sm = line2_smem(P);
   if (fwd) {
     set_smem_limit((const void*)k_line2_fwd<PM, Q>);
-    k_line2_fwd<PM, Q><<<nblocks, P.N / 16, sm, s>>>(in, out, P.t32, G, io, ft);
+    return launch_pdl(k_line2_fwd<PM, Q>, dim3(nblocks), dim3(P.N / 16), sm, s, in, out, P.t32, G, io, ft);
   } else {
     set_smem_limit((const void*)k_line2_adj<PM, Q>);
-    k_line2_adj<PM, Q><<<nblocks, P.N / 16, sm, s>>>(in, out, P.t32, G, io, ft);
+    return launch_pdl(k_line2_adj<PM, Q>, dim3(nblocks), dim3(P.N / 16), sm, s, in, out, P.t32, G, io, ft);
   }
   return cudaGetLastError();
 }

@@ -110,18 +110,6 @@ __device__ __forceinline__ void issue_row(const LineIO& io, int mrow, uint32_t* 
   if (tid == 0 && mrow + 1 < io.mask_rows) cp4(spraw + io.wpr, pf + io.wpr);
 }
 
-// sample j (absolute packed position) of a staged row: the last word w with
-// spraw[w] <= j, then the bit of rank j - spraw[w] in that word
-__device__ __forceinline__ int sample_index_raw(const uint32_t* smask, const int* spraw, int wpr, int j) {
-  int lo = 0, hi = wpr - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (spraw[mid] <= j) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo * 32 + select_bit(smask[lo], j - spraw[lo]);
-}
-
 // One dot product per boundary row: w row-major weights (stride ld, nin a
 // multiple of 4), x the matching inputs; gsz threads per row, each taking
 // float4 chunks part, part + gsz, ..., reduced with shuffles.  sink(o, v)
@@ -242,6 +230,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_fwd(const float* __restrict
     for (int e4 = tid; e4 < M / 4; e4 += NT) cp16(dst + 4 * e4, src + 4 * e4);
     if (io.mode == 1) issue_row(io, io.mask_rows == 1 ? 0 : l, smask + bi * wst, spraw + bi * wst, tid, NT);
   };
+  pdl_trigger();
+  pdl_wait();
   if ((int)blockIdx.x < total) issue(blockIdx.x, 0);
   cp_commit();
 
@@ -306,6 +296,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_fwd(const float* __restrict
     __syncthreads();
 
     // (3) stages 1 and 2, one group of 16 blocks (256 outputs) per warp step
+    const int hoff = 3 * clen - 8 * KS;   // from a lo column to the hi coefficient parts
     for (int grp = warp; grp < ng; grp += NT / 32) {
       float c[2][4], cs[2][4];
 #pragma unroll
@@ -324,20 +315,17 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_fwd(const float* __restrict
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          const int base = a.bs * (16 * grp + 8 * j + g) - a.W0 + a.HL;
+          // window column kk = 16 ks + 2 t + 8 hh (< 2 lw = 16 KS): the lo
+          // coefficients for kk < lw = 8 KS, the hi ones after
+          const uint16_t* Cb = cp0 + a.bs * (16 * grp + 8 * j + g) - a.W0 + a.HL + 2 * t;
           uint32_t bq[3][2];
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
-            const int kk0 = 16 * ks + 2 * t + 8 * hh;
-            const bool ok = kk0 < 2 * a.lw;   // zero columns of the block matrix past 2 lw
-            const int kk = ok ? kk0 : 0;
-            const int half = kk >= a.lw;
-            const uint16_t* C = cp0 + 3 * half * clen + base + (half ? kk - a.lw : kk);
+            constexpr int LW = 8 * KS;
+            const int kk = 16 * ks + 8 * hh;
+            const uint16_t* C = kk < LW ? Cb + kk : Cb + hoff + kk;
 #pragma unroll
-            for (int pt = 0; pt < 3; ++pt) {
-              const uint32_t v = ld32(C + pt * clen);
-              bq[pt][hh] = ok ? v : 0u;
-            }
+            for (int pt = 0; pt < 3; ++pt) bq[pt][hh] = ld32(C + pt * clen);
           }
           mma_split(c[j], cs[j], A1, A2, A3, bq);
         }
@@ -390,10 +378,20 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_fwd(const float* __restrict
       const uint32_t* mk = smask + buf * wst;
       const int* pr = spraw + buf * wst;
       const int mrow = io.mask_rows == 1 ? 0 : l;
-      const int r0 = pr[0];
-      const int r1 = mrow + 1 < io.mask_rows ? pr[io.wpr] : (int)io.m;
       float* y = out + b * io.m;
-      for (int j = r0 + tid; j < r1; j += NT) y[j] = sV[pv(seqrow(sample_index_raw(mk, pr, io.wpr, j), a.L))];
+      // half-word parallel: thread hw walks the set bits of 16 mask bits
+      for (int hw = tid; hw < 2 * io.wpr; hw += NT) {
+        const uint32_t wd = mk[hw >> 1];
+        uint32_t bits = (hw & 1) ? wd >> 16 : wd & 0xffffu;
+        int pos = pr[hw >> 1] + ((hw & 1) ? __popc(wd & 0xffffu) : 0);
+        const int kb = 16 * hw;
+        while (bits) {
+          const int bit = __ffs(bits) - 1;
+          bits &= bits - 1;
+          y[pos++] = sV[pv(seqrow(kb + bit, a.L))];
+        }
+      }
+      (void)mrow;
     } else {
       float4* dst = reinterpret_cast<float4*>(out + b * io.out_batch + (int64_t)l * io.out_stride);
       const float* v = sV + pv(4 * tid);
@@ -475,6 +473,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict
     float* dst = sY + bi * N;
     for (int j = r0 + tid; j < r1; j += NT) cp4(dst + (j - r0), y + j);
   };
+  pdl_trigger();
+  pdl_wait();
   if ((int)blockIdx.x < total) {
     issue_pre(blockIdx.x, 0);
     if (scat) {
@@ -510,7 +510,18 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict
       for (int k = tid; k < vst; k += NT) sV[k] = 0.f;
       __syncthreads();
       const float* ys = sY + buf * N;
-      for (int j = r0 + tid; j < r1; j += NT) sV[pv(seqrow(sample_index_raw(mk, pr, io.wpr, j), a.L))] = ys[j - r0];
+      for (int hw = tid; hw < 2 * io.wpr; hw += NT) {
+        const uint32_t wd = mk[hw >> 1];
+        uint32_t bits = (hw & 1) ? wd >> 16 : wd & 0xffffu;
+        int pos = pr[hw >> 1] - r0 + ((hw & 1) ? __popc(wd & 0xffffu) : 0);
+        const int kb = 16 * hw;
+        while (bits) {
+          const int bit = __ffs(bits) - 1;
+          bits &= bits - 1;
+          sV[pv(seqrow(kb + bit, a.L))] = ys[pos++];
+        }
+      }
+      (void)r1;
       __syncthreads();
     }
     // (2) bits 8..L-1 (the Hadamard stages commute)
@@ -587,18 +598,20 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict
     // (5) stage 1: 8 lo and 8 hi outputs per block, 8 blocks per n-tile
     for (int tile = warp; tile < a.nbA / 8; tile += NT / 32) {
       float c[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
-      const int base = 16 * a.Q * (8 * tile + g) - a.W1 + a.HLa;   // element offset, even
+      // window start 16 Q c - W1 + HLa = 16 Q c elements = 8 Q c words, a
+      // multiple of 16 words: the padded word of 8 Q c + 8 ks + t is
+      // 10 Q c + 8 ks + 4 (ks / 2) + t, and + 4 for the next 8 elements
+      const uint32_t* ub = u0 + 10 * a.Q * (8 * tile + g) + t;
       for (int ks = 0; ks < a.KSA; ++ks) {
         const uint4 x1 = sA[(ks * 32 + lane) * 3], x2 = sA[(ks * 32 + lane) * 3 + 1], x3 = sA[(ks * 32 + lane) * 3 + 2];
         const uint32_t A1[4] = {x1.x, x1.y, x1.z, x1.w}, A2[4] = {x2.x, x2.y, x2.z, x2.w},
                        A3[4] = {x3.x, x3.y, x3.z, x3.w};
-        const int w0 = (base + 16 * ks + 2 * t) >> 1;
-        const int s0 = pw(w0), s1 = pw(w0 + 4);
+        const int s0 = 8 * ks + 4 * (ks >> 1), s1 = s0 + 4;
         uint32_t bq[3][2];
 #pragma unroll
         for (int pt = 0; pt < 3; ++pt) {
-          bq[pt][0] = u0[pt * uwords + s0];
-          bq[pt][1] = u0[pt * uwords + s1];
+          bq[pt][0] = ub[pt * uwords + s0];
+          bq[pt][1] = ub[pt * uwords + s1];
         }
         mma_split(c, cs, A1, A2, A3, bq);
       }
@@ -689,22 +702,22 @@ static int persistent_grid(K kernel, int nt, size_t smem, int total) {
 }
 
 template <int NT>
-static void tc_go(bool fwd, const Plan& P, const TcArgs& a, const float* in, float* out, const LineIO& io, int total,
-                  cudaStream_t s) {
+static cudaError_t tc_go(bool fwd, const Plan& P, const TcArgs& a, const float* in, float* out, const LineIO& io,
+                         int total, cudaStream_t s) {
   if (fwd) {
     const size_t sm = tc_fwd_smem(P, io.mode == 1);
     auto go = [&](auto kern) {
       set_smem_limit((const void*)kern);
-      kern<<<persistent_grid(kern, NT, sm, total), NT, sm, s>>>(in, out, a, io, total);
+      return launch_pdl(kern, dim3(persistent_grid(kern, NT, sm, total)), dim3(NT), sm, s, in, out, a, io, total);
     };
-    if (P.tc.KS == 1) go(k_tc_fwd<1, NT>);
-    else if (P.tc.KS == 2) go(k_tc_fwd<2, NT>);
-    else go(k_tc_fwd<3, NT>);
-  } else {
-    const size_t sm = tc_adj_smem(P, io.mode == 1);
-    set_smem_limit((const void*)k_tc_adj<NT>);
-    k_tc_adj<NT><<<persistent_grid(k_tc_adj<NT>, NT, sm, total), NT, sm, s>>>(in, out, a, io, total);
+    if (P.tc.KS == 1) return go(k_tc_fwd<1, NT>);
+    if (P.tc.KS == 2) return go(k_tc_fwd<2, NT>);
+    return go(k_tc_fwd<3, NT>);
   }
+  const size_t sm = tc_adj_smem(P, io.mode == 1);
+  set_smem_limit((const void*)k_tc_adj<NT>);
+  return launch_pdl(k_tc_adj<NT>, dim3(persistent_grid(k_tc_adj<NT>, NT, sm, total)), dim3(NT), sm, s, in, out, a,
+                    io, total);
 }
 
 cudaError_t tc_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
@@ -714,9 +727,7 @@ cudaError_t tc_launch(bool fwd, const Plan& P, const float* in, float* out, cons
     const char* e = std::getenv("UW_TC_THREADS");
     return (e && std::atoi(e) == 128) ? 128 : 256;
   }();
-  if (nt == 256) tc_go<256>(fwd, P, a, in, out, io, total, s);
-  else tc_go<128>(fwd, P, a, in, out, io, total, s);
-  return cudaGetLastError();
+  return nt == 256 ? tc_go<256>(fwd, P, a, in, out, io, total, s) : tc_go<128>(fwd, P, a, in, out, io, total, s);
 }
 
 }  // namespace uw

@@ -312,6 +312,30 @@ __device__ __forceinline__ int sample_index(const uint32_t* smask, const int* sp
   return lo * 32 + select_bit(smask[lo], j - spre[lo]);
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while the previous kernel in the stream is still running; it stages its
+// constant tables, lets the next kernel launch (pdl_trigger), and waits for
+// the previous grid's completion and memory (pdl_wait) before it reads that
+// grid's output or writes any global memory.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // raise a kernel's dynamic shared-memory limit to the device maximum (once)
 cudaError_t set_smem_limit(const void* fn);
 

@@ -213,8 +213,8 @@ void build_tc(Plan& P, std::vector<uint32_t>& words) {
   G.bs = 8 / Q;
   G.W0 = -imin + ((-imin) & 1);                // even, so 32-bit pairs stay aligned
   G.lw = imax + G.W0 + 1;
-  G.lw += G.lw & 1;
   G.KS = (2 * G.lw + 15) / 16;
+  G.lw = 8 * G.KS;                             // window padded with zero weights: 2 lw = 16 KS
   G.HL = 16;
   G.HR = 16;
   if (G.W0 > G.HL || G.lw - G.W0 - G.bs > G.HR || G.KS > 3) return;
@@ -224,7 +224,7 @@ void build_tc(Plan& P, std::vector<uint32_t>& words) {
   const int kmin = Q * (-p + 1) + tmin, kmax = Q * (14 + p) + tmax;
   G.W1 = up16(-kmin);
   G.KSA = (kmax + G.W1 + 16) / 16;
-  G.HLa = up32(G.W1);
+  G.HLa = G.W1;                                // window starts are then multiples of 32 elements
   G.HRa = up32(std::max(0, 16 * G.KSA - 16 * Q - G.W1));
   if (G.KSA > 16) return;
   const int nbA = n0 / 8;
