@@ -395,8 +395,10 @@ def main():
     args = ap.parse_args()
     globals()["R"] = args.R
     if args.R != 11:
-        globals()["WORKLOAD"] = WORKLOAD.replace("M=2048^2 -> N=4096^2 (R=11, q=1)",
-                                                 f"M={2 ** args.R}^2 -> N={2 ** (args.R + 1)}^2 (R={args.R}, q=1)")
+        n = 2 ** (args.R + 1)
+        globals()["WORKLOAD"] = (WORKLOAD.replace("M=2048^2 -> N=4096^2 (R=11, q=1)",
+                                                  f"M={2 ** args.R}^2 -> N={n}^2 (R={args.R}, q=1)")
+                                 .replace("(m=2013266)", f"(m={int(round(FRAC * n * n))})"))
     if args.impl == "reference":
         run_reference(args)
     else:
