@@ -7,8 +7,11 @@ multilevel sampling of 12% of the Walsh coefficients, seed 4).  One step is
 one forward product and one adjoint product (the whole path: IDWT,
 upsample-convolve, FWHT, selection, and the transposed chain).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|split_bf16|f64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision split_bf16|f32|f64] [--compare f32]
     python bench.py --impl reference      # the CPU oracle on the host cores
+
+The headline precision is split-BF16 (tensor cores); the same pair is then
+timed in FP32 on CUDA cores and reported under "comparison".
 
 Under torchrun every rank runs its own replica on its own GPU (the product is
 independent per instance: weak scaling, no collective on the data path); the
@@ -170,22 +173,58 @@ print(json.dumps({{"pair_s": pair, "idwt_s": t_idwt, "dwt_s": t_dwt, "line_fwd_s
 
 
 def run_reference(args):
+    """The oracle on the host cores: one-time Mallat IDWT + DWT of the full
+    array, then per step Algorithm 1 forward and adjoint on a bounded number
+    of lines (sized so the whole run stays within a few minutes), each step
+    scaled to one full pair."""
     rank, _, world = env_rank()
     if rank != 0:
         return
-    steps = []
-    for _ in range(max(1, args.steps)):
-        steps.append(oracle_pair_rate(lines=16))
-        if len(steps) >= 3:
-            break
-    v = statistics.median(s["value"] for s in steps)
-    cb = dict(steps[0])
-    cb["value"] = v
+    total = args.steps + args.warmup
+    code = f"""
+import time, json, statistics, numpy as np
+from oracle import fast, wavelets as W
+from paper_2106_00554_gb300 import inputs
+R, q, p = {R}, {Q}, {P}
+M, N = 2 ** R, 2 ** (R + q)
+J0 = W.default_J0(p)
+rng = np.random.default_rng({SEED})
+x = inputs.coeffs_2d(rng, R, J0, 1.5)
+fast.alg1_forward(np.zeros((1, M)), R, q, p, W.VMP)
+t0 = time.perf_counter(); S = fast.idwt2d(x, J0, p, W.VMP); t_idwt = time.perf_counter() - t0
+t0 = time.perf_counter(); fast.dwt2d(S, J0, p, W.VMP); t_dwt = time.perf_counter() - t0
+budget = 120.0 / {total}
+t0 = time.perf_counter(); fast.alg1_forward(rng.standard_normal((1, M)), R, q, p, W.VMP)
+fast.alg1_adjoint(rng.standard_normal((1, N)), R, q, p, W.VMP); t1 = time.perf_counter() - t0
+L = max(1, min(32, int(budget / max(t1, 1e-6))))
+pairs = []
+for s in range({total}):
+    xi = rng.standard_normal((L, M)); al = rng.standard_normal((L, N))
+    t0 = time.perf_counter(); fast.alg1_forward(xi, R, q, p, W.VMP); tf = (time.perf_counter() - t0) / L
+    t0 = time.perf_counter(); fast.alg1_adjoint(al, R, q, p, W.VMP); ta = (time.perf_counter() - t0) / L
+    if s >= {args.warmup}:
+        pairs.append(t_idwt + t_dwt + (M + N) * (tf + ta))
+print(json.dumps({{"pair_s": statistics.median(pairs), "lines": L, "steps": len(pairs), "idwt_s": t_idwt,
+                  "dwt_s": t_dwt}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    t0 = time.perf_counter()
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+    wall = time.perf_counter() - t0
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    v = 1.0 / d["pair_s"]
+    sample = (f"oracle Algorithm 2 at N=4096^2: the full 2048^2 Mallat IDWT + DWT timed once "
+              f"({d['idwt_s'] + d['dwt_s']:.1f} s), then per step Algorithm 1 forward and adjoint on "
+              f"{d['lines']} line(s) each, scaled to the M+N=6144 lines of one pair; median over "
+              f"{d['steps']} steps; single thread; {wall:.1f} s wall")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
-            "steps": len(steps), "warmup": 0, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "f64 (CPU oracle)"},
-            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -206,9 +245,8 @@ def run_ours(args):
 
     from paper_2106_00554_gb300 import F32, F32_SPLIT_BF16, F64, VMP, Plan, _lib, build, inputs
     build.build()
-    prec = {"f32": F32, "split_bf16": F32_SPLIT_BF16, "f64": F64}[args.precision]
-    dt = torch.float64 if prec == F64 else torch.float32
-    esize = 8 if prec == F64 else 4
+    PREC = {"f32": F32, "split_bf16": F32_SPLIT_BF16, "f64": F64}
+    DTYPE = {F32: "f32", F32_SPLIT_BF16: "bf16 split (3 parts per operand), f32 accumulate", F64: "f64"}
 
     rng = np.random.default_rng(SEED)
     N = 2 ** (R + Q)
@@ -216,93 +254,104 @@ def run_ours(args):
     plan = Plan(2, R, Q, P, VMP, omega=omega)
     x_np = inputs.coeffs_2d(rng, R, plan.J0, 1.5)
     y_np = rng.standard_normal(omega.size)
-    x = torch.tensor(x_np, dtype=dt, device="cuda")
-    yin = torch.tensor(y_np, dtype=dt, device="cuda")
-    y = torch.empty(plan.m, dtype=dt, device="cuda")
-    xo = torch.empty_like(x)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        plan.forward(x, y, precision=prec)
-        plan.adjoint(yin, xo, precision=prec)
+    def measure(prec, sample_clocks):
+        dt = torch.float64 if prec == F64 else torch.float32
+        x = torch.tensor(x_np, dtype=dt, device="cuda")
+        yin = torch.tensor(y_np, dtype=dt, device="cuda")
+        y = torch.empty(plan.m, dtype=dt, device="cuda")
+        xo = torch.empty_like(x)
 
-    for _ in range(args.warmup):
-        step()
-        flush.fill_(1)
-    torch.cuda.synchronize()
+        def step():
+            plan.forward(x, y, precision=prec)
+            plan.adjoint(yin, xo, precision=prec)
 
-    # the step as one CUDA graph (launch-bound otherwise: ~20 small launches per
-    # pair); eager launches if the capture is refused
-    graph, graph_error = None, None
-    if not args.eager:
-        try:
-            side = torch.cuda.Stream()
-            side.wait_stream(stream)
-            with torch.cuda.stream(side):
-                step()
-            stream.wait_stream(side)
-            torch.cuda.synchronize()
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph):
-                plan.forward(x, y, precision=prec)
-                plan.adjoint(yin, xo, precision=prec)
-            for _ in range(3):
-                graph.replay()
-            torch.cuda.synchronize()
-        except Exception as e:  # noqa: BLE001 - reported in the JSON line
-            graph = None
-            graph_error = f"{type(e).__name__}: {e}"[:200]
-    plan.forward(x, y, precision=prec)
-    n_fwd = plan.last_launches
-    plan.adjoint(yin, xo, precision=prec)
-    n_adj = plan.last_launches
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clk = ClockSampler(local)
-    clk.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    launches = 0
-    for k in range(args.steps):
-        starts[k].record(stream)
-        if graph is not None:
-            graph.replay()
-        else:
+        for _ in range(args.warmup):
             step()
-        launches += n_fwd + n_adj
-        ends[k].record(stream)
-        flush.fill_(k)                   # L2 flush between timed steps (not timed)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = clk.stop()
-    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(per)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = args.steps * world / (total_ms / 1000.0)
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        # the pair as one CUDA graph (18 launches); eager if the capture is refused
+        graph, graph_error = None, None
+        if not args.eager:
+            try:
+                side = torch.cuda.Stream()
+                side.wait_stream(stream)
+                with torch.cuda.stream(side):
+                    step()
+                stream.wait_stream(side)
+                torch.cuda.synchronize()
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    step()
+                for _ in range(3):
+                    graph.replay()
+                torch.cuda.synchronize()
+            except Exception as e:  # noqa: BLE001 - reported in the JSON line
+                graph = None
+                graph_error = f"{type(e).__name__}: {e}"[:200]
+        plan.forward(x, y, precision=prec)
+        n_fwd = plan.last_launches
+        plan.adjoint(yin, xo, precision=prec)
+        n_adj = plan.last_launches
+        torch.cuda.synchronize()
 
-    # per-kernel device times: the same step launched eagerly with the
-    # library's event profiler on (events on the launching stream)
-    kp = max(3, min(args.steps, 300))
-    _lib.uw_plan_profile(plan._h, True)
-    for k in range(kp):
-        step()
-        flush.fill_(k)
-    torch.cuda.synchronize()
-    prof = [e for e in _lib.uw_plan_profile_read(plan._h) if e["launches"] > 0]
-    _lib.uw_plan_profile(plan._h, False)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.start()
+            time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches = 0
+        for k in range(args.steps):
+            starts[k].record(stream)
+            if graph is not None:
+                graph.replay()
+            else:
+                step()
+            launches += n_fwd + n_adj
+            ends[k].record(stream)
+            flush.fill_(k)                   # L2 flush between timed steps (not timed)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = clk.stop() if clk else None
+        total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        if dist:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        value = args.steps * world / (total_ms / 1000.0)
+        # per-kernel device times: the same pair launched eagerly with the
+        # library's event profiler on (events on the launching stream)
+        kp = max(3, min(args.steps, 300))
+        _lib.uw_plan_profile(plan._h, True)
+        for k in range(kp):
+            step()
+            flush.fill_(k)
+        torch.cuda.synchronize()
+        prof = [e for e in _lib.uw_plan_profile_read(plan._h) if e["launches"] > 0]
+        _lib.uw_plan_profile(plan._h, False)
+        launch = ("cuda graph of the pair" if graph is not None else
+                  ("eager" if args.eager else f"eager (graph capture failed: {graph_error})"))
+        return {"value": value, "ms": total_ms / args.steps, "prof": prof, "kp": kp, "launches": launches,
+                "clocks": clocks, "launch": launch}
+
+    prec = PREC[args.precision]
+    main_m = measure(prec, True)
+    comp_m = None
+    if args.compare and args.compare != args.precision:
+        comp_m = measure(PREC[args.compare], False)
+    esize = 8 if prec == F64 else 4
 
     # end to end through the host-buffer entry points (copies inside)
     e2e = None
     if not args.no_e2e:
+        dt = torch.float64 if prec == F64 else torch.float32
         xh = torch.tensor(x_np, dtype=dt).pin_memory()
         yh = torch.empty(plan.m, dtype=dt).pin_memory()
         yinh = torch.tensor(y_np, dtype=dt).pin_memory()
@@ -326,15 +375,17 @@ def run_ours(args):
         nbx = plan.coeffs * esize
         nby = plan.m * esize
         e2e = {"value": ke * world / te, "unit": "pairs/s", "h2d_bytes_per_step": nbx + nby,
-               "d2h_bytes_per_step": nby + nbx, "steps": ke}
+               "d2h_bytes_per_step": nby + nbx, "steps": ke,
+               "how": "uw_forward_host + uw_adjoint_host from pinned host buffers (copies and sync inside)"}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (live event timings of this run)
+    # roofline of the dominant kernel (event timings of this run)
     peak, peak_kind = peaks()
+    prof = main_m["prof"]
     dom = max(prof, key=lambda e: e["total_ms"])
     avg_ms = dom["total_ms"] / max(1, dom["launches"])
     achieved = dom["bytes_per_launch"] / (avg_ms / 1000.0) / 1e9
@@ -343,36 +394,38 @@ def run_ours(args):
                            "share": e["total_ms"] / sum(z["total_ms"] for z in prof),
                            "GBps": e["bytes_per_launch"] / (e["total_ms"] / max(1, e["launches"]) / 1000) / 1e9}
                for e in prof}
+    value = main_m["value"]
     words = N * ((N + 31) // 32)
     comp = 2 * (plan.coeffs * esize + plan.m * esize + 8 * words)      # both directions
     twopass = comp + 2 * 2 * (2 ** R) * N * esize
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": {F32: "f32", F32_SPLIT_BF16: "bf16 hi+lo split, f32 accumulate", F64: "f64"}[prec],
-        "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": main_m["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "batch": 1,
-                   "launch": "cuda graph of the pair" if graph is not None else
-                   ("eager" if args.eager else f"eager (graph capture failed: {graph_error})"),
-                   "kernel_times": f"event profiler over {kp} further eager steps",
+                   "launch": main_m["launch"],
+                   "kernel_times": f"library event profiler over {main_m['kp']} further eager pairs",
                    "l2": "flushed between timed steps by a 256 MiB device write outside the event pair",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                     else "fallback 6.8 TB/s"},
+                     "peak_kind": (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                                   else "fallback 6.8 TB/s")},
         "pipeline_roofline": {"compulsory_bytes_per_pair": comp, "two_pass_bytes_per_pair": twopass,
                               "frac_compulsory": value * comp / 1e9 / peak,
                               "frac_two_pass": value * twopass / 1e9 / peak},
         "kernels": kernels,
-        "gpu_launches": launches,
-        "clocks": clocks,
+        "gpu_launches": main_m["launches"],
+        "clocks": main_m["clocks"],
     }
+    if comp_m:
+        line["comparison"] = {"precision": args.compare, "dtype": DTYPE[PREC[args.compare]],
+                              "value": comp_m["value"], "unit": "pairs/s", "ms_per_step": comp_m["ms"],
+                              "launch": comp_m["launch"], "speedup_of_main": value / comp_m["value"]}
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
-        cb = oracle_pair_rate(lines=32)
+        cb = oracle_pair_rate(lines=128)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
     if dist:
@@ -383,10 +436,11 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--eager", action="store_true", help="launch the timed steps without a CUDA graph")
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("UW_BENCH_PRECISION", "f32"),
+    ap.add_argument("--compare", default="f32", help="second precision timed the same way ('' to skip)")
+    ap.add_argument("--precision", default=os.environ.get("UW_BENCH_PRECISION", "split_bf16"),
                     choices=["f32", "split_bf16", "f64"])
     ap.add_argument("--R", type=int, default=R,
                     help="level per dimension (default 11 = the benchmark workload; smaller only for profiling)")
