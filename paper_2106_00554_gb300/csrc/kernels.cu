@@ -943,8 +943,12 @@ cudaError_t set_smem_limit(const void* fn) {
   if (done.count({dev, fn})) return cudaSuccess;
   int mx = 0;
   cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e == cudaSuccess)   // the static shared memory of the kernel counts against the same limit
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
   if (e == cudaSuccess) done.insert({dev, fn});
+  else cudaGetLastError();   // leave no sticky status for the launch checks
   return e;
 }
 
