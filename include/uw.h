@@ -36,8 +36,12 @@
  *    (2D linear index n1 * N + n2, n1 = row of alpha).
  *  - Precision: UW_F64 (double in, double out, double arithmetic),
  *    UW_F32 (float in/out, float arithmetic on CUDA cores) and
- *    UW_F32_SPLIT_BF16 (float in/out; the +-1 Walsh-Hadamard stages run on
- *    tensor cores on hi+lo bfloat16 splits with float accumulation).
+ *    UW_F32_SPLIT_BF16 (float in/out; the last synthesis level, the
+ *    upsample-convolve and the Walsh-Hadamard stages of bits 0-7 of each line
+ *    run on the tensor cores with every operand split into three bfloat16
+ *    parts and float accumulation -- as accurate as UW_F32; lines shorter
+ *    than 512 samples and 1D plans with several levels per line take the
+ *    UW_F32 kernels).
  */
 #ifndef UW_H
 #define UW_H
@@ -167,6 +171,42 @@ int uw_forward_host(const uw_plan* plan, int precision, const void* x_host, void
                     int batch, void* stream);
 int uw_adjoint_host(const uw_plan* plan, int precision, const void* y_host, void* x_host,
                     int batch, void* stream);
+
+/*
+ * Solver kernels (element-wise, no plan): the pieces of an l1-regularised
+ * recovery  min_x 1/2 ||P_Omega U x - y||^2 + lam ||x||_1  (the
+ * compressive-sensing use of the products, Sec. 1.2 and Remark 4.2) that are
+ * not products with U: FISTA's proximal step with momentum, its
+ * vector-Jacobian product for back-propagation through the iterations, and
+ * FP64-accumulated inner products.  precision: UW_F32 or UW_F64 (every array
+ * of that type, device memory, n elements each); stream: cudaStream_t.
+ *
+ * uw_fista_step:  v = z - tau (G - B),  x1 = sign(v) max(|v| - tau lam, 0),
+ *                 z1 = x1 + beta (x1 - x0).
+ *   With G = U^* P_Omega^* P_Omega U z and B = U^* P_Omega^* y this is one
+ *   FISTA iteration with step tau (tau <= 1: ||P_Omega U|| <= 1) and
+ *   momentum beta.  x1, z1 must not overlap the inputs.
+ */
+int uw_fista_step(int precision, int64_t n, const void* z, const void* G, const void* B, const void* x0,
+                  double tau, double lam, double beta, void* x1, void* z1, void* stream);
+
+/*
+ * uw_fista_step_backward -- given gx1 = dL/dx1 and gz1 = dL/dz1 (either may
+ * be NULL: zero), writes dL/dz (gz), dL/dG (gG), dL/dB (gB) and dL/dx0 (gx0,
+ * skipped if NULL), and ADDS dL/dlam to the device double *glam (the caller
+ * zeroes it; accumulated in FP64).  On the active set |v| > tau lam the step
+ * passes w = gx1 + (1 + beta) gz1 to v; elsewhere nothing.
+ */
+int uw_fista_step_backward(int precision, int64_t n, const void* z, const void* G, const void* B, double tau,
+                           double lam, double beta, const void* gx1, const void* gz1, void* gz, void* gG,
+                           void* gB, void* gx0, double* glam, void* stream);
+
+/* uw_dot -- *out (device double) = sum_i a_i b_i accumulated in FP64. */
+int uw_dot(int precision, int64_t n, const void* a, const void* b, double* out, void* stream);
+
+/* uw_axpby -- out = alpha a + beta b (b may be NULL: out = alpha a). */
+int uw_axpby(int precision, int64_t n, double alpha, const void* a, double beta, const void* b, void* out,
+             void* stream);
 
 /* uw_plan_destroy -- frees the plan's device and host memory; NULL is a
  * no-op.  The caller must make sure no call using the plan is in flight. */

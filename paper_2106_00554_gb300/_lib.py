@@ -42,6 +42,12 @@ SIGNATURES = {
     "uw_plan_last_launches": (_int, [_c_p]),
     "uw_plan_profile": (_int, [_c_p, _int]),
     "uw_plan_profile_read": (_int, [_c_p, _int, ctypes.c_char_p, _int, _dp, _i64p, _dp]),
+    "uw_fista_step": (_int, [_int, _i64, _c_p, _c_p, _c_p, _c_p, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_double, _c_p, _c_p, _c_p]),
+    "uw_fista_step_backward": (_int, [_int, _i64, _c_p, _c_p, _c_p, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "uw_dot": (_int, [_int, _i64, _c_p, _c_p, _c_p, _c_p]),
+    "uw_axpby": (_int, [_int, _i64, ctypes.c_double, _c_p, ctypes.c_double, _c_p, _c_p, _c_p]),
     "uw_last_error": (_int, []),
     "uw_last_message": (ctypes.c_char_p, []),
     "uw_status_string": (ctypes.c_char_p, [_int]),
@@ -121,6 +127,23 @@ def uw_forward_host(h, precision, x_ptr, y_ptr, batch, stream):
 
 def uw_adjoint_host(h, precision, y_ptr, x_ptr, batch, stream):
     _chk(lib().uw_adjoint_host(h, precision, y_ptr, x_ptr, batch, stream), "uw_adjoint_host")
+
+
+def uw_fista_step(precision, n, z, G, B, x0, tau, lam, beta, x1, z1, stream):
+    _chk(lib().uw_fista_step(precision, n, z, G, B, x0, tau, lam, beta, x1, z1, stream), "uw_fista_step")
+
+
+def uw_fista_step_backward(precision, n, z, G, B, tau, lam, beta, gx1, gz1, gz, gG, gB, gx0, glam, stream):
+    _chk(lib().uw_fista_step_backward(precision, n, z, G, B, tau, lam, beta, gx1, gz1, gz, gG, gB, gx0, glam,
+                                      stream), "uw_fista_step_backward")
+
+
+def uw_dot(precision, n, a, b, out, stream):
+    _chk(lib().uw_dot(precision, n, a, b, out, stream), "uw_dot")
+
+
+def uw_axpby(precision, n, alpha, a, beta, b, out, stream):
+    _chk(lib().uw_axpby(precision, n, alpha, a, beta, b, out, stream), "uw_axpby")
 
 
 def uw_plan_destroy(h):
