@@ -443,12 +443,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict
     Hb[j][1] = hpair(2 * t + 8, g + 8 * j);
   }
   for (int w = tid; w < 3 * uwords; w += NT) u0[w] = 0u;   // halos (VMP) start and stay zero
-  uint16_t* u16 = reinterpret_cast<uint16_t*>(u0);
-  auto uidx = [&](int e) {  // element e in [-HLa, N + HRa) -> 16-bit slot of part 0
-    const int x = e + a.HLa;
-    return 2 * pw(x >> 1) + (x & 1);
-  };
-
   // staging: mode 0 copies the natural-order line into sV[bi]; mode 1 first
   // the mask row (issue_pre), later the packed samples (issue_y)
   auto issue_pre = [&](int ln, int bi) {
@@ -507,7 +501,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict
       const int mrow = io.mask_rows == 1 ? 0 : l;
       const int r0 = pr[0];
       const int r1 = mrow + 1 < io.mask_rows ? pr[io.wpr] : (int)io.m;
-      for (int k = tid; k < vst; k += NT) sV[k] = 0.f;
+      for (int k4 = tid; k4 < vst / 4; k4 += NT) reinterpret_cast<float4*>(sV)[k4] = make_float4(0.f, 0.f, 0.f, 0.f);
       __syncthreads();
       const float* ys = sY + buf * N;
       for (int hw = tid; hw < 2 * io.wpr; hw += NT) {
@@ -545,32 +539,45 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict
         mma_bf16(d, q[2], Hb[j][0], Hb[j][1]);
         mma_bf16(d, q[1], Hb[j][0], Hb[j][1]);
         mma_bf16(d, q[0], Hb[j][0], Hb[j][1]);
+        // pair rows (2i, 2i+1) across the lanes g, g^1 (lane ^ 4): the even
+        // lane keeps rows (g, g+1), the odd one rows (g+7, g+8) of its partner's
+        // numbering, so every store writes two adjacent elements
+        const bool odd = g & 1;
+        const float r0 = __shfl_xor_sync(0xffffffffu, odd ? d[0] : d[2], 4);
+        const float r1 = __shfl_xor_sync(0xffffffffu, odd ? d[1] : d[3], 4);
+        const int brow = odd ? g + 7 : g;
 #pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-          const int kidx = k0 + 16 * (8 * j + 2 * t + (qq & 1)) + g + (qq >> 1) * 8;
+        for (int e = 0; e < 2; ++e) {
+          const float lo = odd ? (e ? r1 : r0) : d[e];
+          const float hi = odd ? d[2 + e] : (e ? r1 : r0);
+          const int kidx = k0 + 16 * (8 * j + 2 * t + e) + brow;   // even
           if (!a.per) {
-            if (kidx < a.Wl) sUe[kidx] = d[qq];
-            else if (kidx >= N - a.Wl) sUe[kidx - (N - 2 * a.Wl)] = d[qq];
+            if (kidx < a.Wl) {
+              sUe[kidx] = lo;
+              sUe[kidx + 1] = hi;
+            } else if (kidx >= N - a.Wl) {
+              sUe[kidx - (N - 2 * a.Wl)] = lo;
+              sUe[kidx + 1 - (N - 2 * a.Wl)] = hi;
+            }
           }
           uint32_t w1, w2, w3;
-          split3(d[qq], 0.f, w1, w2, w3);
-          const uint16_t v1 = (uint16_t)(w1 & 0xffffu), v2 = (uint16_t)(w2 & 0xffffu), v3 = (uint16_t)(w3 & 0xffffu);
-          int s = uidx(kidx);
-          u16[s] = v1;
-          u16[2 * uwords + s] = v2;
-          u16[4 * uwords + s] = v3;
+          split3(lo, hi, w1, w2, w3);
+          int s = pw((kidx + a.HLa) >> 1);
+          u0[s] = w1;
+          u0[uwords + s] = w2;
+          u0[2 * uwords + s] = w3;
           if (a.per) {
             if (kidx < a.HRa) {
-              s = uidx(kidx + N);
-              u16[s] = v1;
-              u16[2 * uwords + s] = v2;
-              u16[4 * uwords + s] = v3;
+              s = pw((kidx + N + a.HLa) >> 1);
+              u0[s] = w1;
+              u0[uwords + s] = w2;
+              u0[2 * uwords + s] = w3;
             }
             if (kidx >= N - a.HLa) {
-              s = uidx(kidx - N);
-              u16[s] = v1;
-              u16[2 * uwords + s] = v2;
-              u16[4 * uwords + s] = v3;
+              s = pw((kidx - N + a.HLa) >> 1);
+              u0[s] = w1;
+              u0[uwords + s] = w2;
+              u0[2 * uwords + s] = w3;
             }
           }
         }
