@@ -1134,7 +1134,7 @@ static void fwd1d_smem(const Plan& P, const T* x, T* y, int batch, Launcher& L) 
   Geo G = geo_of(P);
   LineIO io{};
   io.in_stride = P.M; io.out_stride = P.N; io.lines = 1; io.in_batch = P.M; io.out_batch = P.m;
-  io.seq_rows = 0; io.mode = 1; io.jlev = P.J0; io.mask = P.d_mask; io.prefix = P.d_prefix;
+  io.seq_rows = 0; io.mode = 1; io.jlev = P.J0; io.mask = P.d_mask; io.prefix = P.d_prefix; io.pos = P.d_pos;
   io.wpr = P.wpr; io.m = P.m; io.mask_rows = 1;
   L.pre("line_fwd_1d", e * ((double)batch * (P.M + P.m)) + 8.0 * P.words);
   launch_line<T>(true, P, G, x, y, io, batch, L);
@@ -1147,7 +1147,7 @@ static void adj1d_smem(const Plan& P, const T* y, T* x, int batch, Launcher& L) 
   Geo G = geo_of(P);
   LineIO io{};
   io.in_stride = P.N; io.out_stride = P.M; io.lines = 1; io.in_batch = P.m; io.out_batch = P.M;
-  io.seq_rows = 0; io.mode = 1; io.jlev = P.J0; io.mask = P.d_mask; io.prefix = P.d_prefix;
+  io.seq_rows = 0; io.mode = 1; io.jlev = P.J0; io.mask = P.d_mask; io.prefix = P.d_prefix; io.pos = P.d_pos;
   io.wpr = P.wpr; io.m = P.m; io.mask_rows = 1;
   L.pre("line_adj_1d", e * ((double)batch * (P.M + P.m)) + 8.0 * P.words);
   launch_line<T>(false, P, G, y, x, io, batch, L);
@@ -1262,7 +1262,7 @@ static void fwd2d(const Plan& P, const T* x, T* y, int batch, T* work, Launcher&
   L.check();
   LineIO io2{};
   io2.in_stride = M; io2.lines = N; io2.in_batch = (int64_t)N * M; io2.out_batch = P.m;
-  io2.seq_rows = 1; io2.mode = 1; io2.jlev = io.jlev; io2.mask = P.d_mask; io2.prefix = P.d_prefix;
+  io2.seq_rows = 1; io2.mode = 1; io2.jlev = io.jlev; io2.mask = P.d_mask; io2.prefix = P.d_prefix; io2.pos = P.d_pos;
   io2.wpr = P.wpr; io2.m = P.m; io2.mask_rows = N;
   L.pre("line_fwd_dim2_gather", e * (double)batch * ((double)N * M + P.m) + 8.0 * P.words);
   launch_line<T>(true, P, G, V, y, io2, batch * N, L);
@@ -1284,7 +1284,7 @@ static void adj2d(const Plan& P, const T* y, T* x, int batch, T* work, Launcher&
   const int jl = std::max(P.R - 1, P.J0);
   LineIO io{};
   io.out_stride = M; io.lines = N; io.out_batch = (int64_t)N * M; io.seq_rows = 1; io.mode = 1; io.jlev = jl;
-  io.mask = P.d_mask; io.prefix = P.d_prefix; io.wpr = P.wpr; io.m = P.m; io.mask_rows = N;
+  io.mask = P.d_mask; io.prefix = P.d_prefix; io.pos = P.d_pos; io.wpr = P.wpr; io.m = P.m; io.mask_rows = N;
   L.pre("line_adj_dim2_scatter", e * (double)batch * ((double)N * M + P.m) + 8.0 * P.words);
   launch_line<T>(false, P, G, y, Qm, io, batch * N, L);
   L.check();

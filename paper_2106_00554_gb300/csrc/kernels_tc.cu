@@ -97,6 +97,7 @@ __device__ __forceinline__ void cp4(void* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_wait2() { asm volatile("cp.async.wait_group 2;\n" ::); }
 
 // The mask row of line l (words and raw prefix counts, plus the next row's
 // first prefix) copied asynchronously; r1 of the last row is the sample count.
@@ -180,6 +181,94 @@ __device__ __forceinline__ void fwht_high(float* sV, int ng, int tid, int nt) {
 
 __device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
+// Stages 1 and 2 of the forward operator for NG groups grp0, grp0 + gstep,
+// ...: the block GEMM (6 part products per k-step, two accumulation chains
+// per n-tile), the VMP boundary blocks replaced, bits 4-7 as an exact +-1
+// MMA, results to the padded FP32 line.
+template <int KS, int NG>
+__device__ __forceinline__ void fwd_stage12(int grp0, int gstep, const uint4* sA, const uint16_t* cp0, int clen,
+                                            int hoff, const TcArgs& a, int lane, int g, int t,
+                                            const uint32_t (&Hb)[2][2], const float* sEdge, float* sV) {
+  float c[NG][2][4], cs[NG][2][4];
+#pragma unroll
+  for (int gi = 0; gi < NG; ++gi)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) c[gi][j][r] = cs[gi][j][r] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    uint32_t A1[4], A2[4], A3[4];
+    {
+      const uint4 u1 = sA[(ks * 32 + lane) * 3], u2 = sA[(ks * 32 + lane) * 3 + 1], u3 = sA[(ks * 32 + lane) * 3 + 2];
+      A1[0] = u1.x; A1[1] = u1.y; A1[2] = u1.z; A1[3] = u1.w;
+      A2[0] = u2.x; A2[1] = u2.y; A2[2] = u2.z; A2[3] = u2.w;
+      A3[0] = u3.x; A3[1] = u3.y; A3[2] = u3.z; A3[3] = u3.w;
+    }
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        // window column kk = 16 ks + 2 t + 8 hh (< 2 lw = 16 KS): the lo
+        // coefficients for kk < lw = 8 KS, the hi ones after
+        const int grp = grp0 + gi * gstep;
+        const uint16_t* Cb = cp0 + a.bs * (16 * grp + 8 * j + g) - a.W0 + a.HL + 2 * t;
+        uint32_t bq[3][2];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          constexpr int LW = 8 * KS;
+          const int kk = 16 * ks + 8 * hh;
+          const uint16_t* C = kk < LW ? Cb + kk : Cb + hoff + kk;
+#pragma unroll
+          for (int pt = 0; pt < 3; ++pt) bq[pt][hh] = ld32(C + pt * clen);
+        }
+        mma_split(c[gi][j], cs[gi][j], A1, A2, A3, bq);
+      }
+  }
+#pragma unroll
+  for (int gi = 0; gi < NG; ++gi) {
+    const int grp = grp0 + gi * gstep;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) c[gi][j][r] += cs[gi][j][r];
+    if (!a.per) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int blk = 16 * grp + 8 * j + 2 * t + e;
+          int o = -1;
+          if (blk < a.EBl) o = 16 * blk;
+          else if (blk >= a.nb - a.EBr) o = 16 * (a.EBl + blk - (a.nb - a.EBr));
+          if (o >= 0) {
+            c[gi][j][e] = sEdge[o + g];
+            c[gi][j][2 + e] = sEdge[o + g + 8];
+          }
+        }
+    }
+    uint32_t q[3][4];
+    split3(c[gi][0][0], c[gi][0][1], q[0][0], q[1][0], q[2][0]);
+    split3(c[gi][0][2], c[gi][0][3], q[0][1], q[1][1], q[2][1]);
+    split3(c[gi][1][0], c[gi][1][1], q[0][2], q[1][2], q[2][2]);
+    split3(c[gi][1][2], c[gi][1][3], q[0][3], q[1][3], q[2][3]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16(d, q[2], Hb[j][0], Hb[j][1]);
+      mma_bf16(d, q[1], Hb[j][0], Hb[j][1]);
+      mma_bf16(d, q[0], Hb[j][0], Hb[j][1]);
+      // natural index 16 (16 grp + 8 j + 2 t + e) + g (+8) sits at
+      // pv = 320 grp + 160 j + 40 t + 16 e + g (+8)
+      float* v = sV + 320 * grp + 160 * j + 40 * t + g;
+      v[0] = d[0];
+      v[16] = d[1];
+      v[8] = d[2];
+      v[24] = d[3];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // forward: 256 threads, persistent over lines; the next line's coefficients
 // (and mask row) are copied into shared memory while the current one runs
@@ -195,12 +284,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_fwd(const float* __restrict
   const int wst = io.mode == 1 ? io.wpr + 4 : 0;     // staged mask words / prefixes per buffer
   float* sV = reinterpret_cast<float*>(smem_raw);
   uint4* sA = reinterpret_cast<uint4*>(sV + pvlen(N));            // KS x 32 lanes x 3 parts
-  float* sIn = reinterpret_cast<float*>(sA + KS * 96);            // 2 x M staged coefficients
-  float* sEdge = sIn + 2 * M;
-  uint32_t* smask = reinterpret_cast<uint32_t*>(sEdge + 16 * (a.EBl + a.EBr) + 4);   // 2 x wst
-  int* spraw = reinterpret_cast<int*>(smask + 2 * wst);                               // 2 x wst
+  // three staging buffers: the lines two and one ahead are in flight while
+  // the current one runs
+  float* sIn = reinterpret_cast<float*>(sA + KS * 96);            // 3 x M staged coefficients
+  float* sEdge = sIn + 3 * M;
+  uint32_t* smask = reinterpret_cast<uint32_t*>(sEdge + 16 * (a.EBl + a.EBr) + 4);   // 3 x wst
+  int* spraw = reinterpret_cast<int*>(smask + 3 * wst);                               // 3 x wst
   // coefficient parts: cp0[(3 * half + part) * clen + i], half 0 = lo, 1 = hi
-  uint16_t* cp0 = reinterpret_cast<uint16_t*>(spraw + 2 * wst);
+  uint16_t* cp0 = reinterpret_cast<uint16_t*>(spraw + 3 * wst);
   // boundary matrix, staged when it fits (a.efs), else read from global memory
   const int Rf = 16 * (a.EBl + a.EBr);
   float* sEfs = reinterpret_cast<float*>(cp0 + ((6 * clen + 8 + 7) & ~7));
@@ -234,16 +325,36 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_fwd(const float* __restrict
   pdl_wait();
   if ((int)blockIdx.x < total) issue(blockIdx.x, 0);
   cp_commit();
+  if ((int)(blockIdx.x + gridDim.x) < total) issue(blockIdx.x + gridDim.x, 1);
+  cp_commit();
 
   int buf = 0;
-  for (int line = blockIdx.x; line < total; line += gridDim.x, buf ^= 1) {
-    if (line + (int)gridDim.x < total) issue(line + gridDim.x, buf ^ 1);
+  for (int line = blockIdx.x; line < total; line += gridDim.x, buf = buf == 2 ? 0 : buf + 1) {
+    if (line + 2 * (int)gridDim.x < total) issue(line + 2 * gridDim.x, buf == 0 ? 2 : buf - 1);
     cp_commit();
-    cp_wait1();
+    cp_wait2();
     __syncthreads();
     const int l = line % io.lines;
     const int64_t b = line / io.lines;
     const float* xin = sIn + buf * M;
+    // this line's sample positions, fetched now and used by the gather
+    const uint16_t* posr = nullptr;
+    uint16_t ppre[4] = {0, 0, 0, 0};
+    int r0g = 0, r1g = 0;
+    if (io.mode == 1) {
+      const int* pr = spraw + buf * wst;
+      const int mrow = io.mask_rows == 1 ? 0 : l;
+      r0g = pr[0];
+      r1g = mrow + 1 < io.mask_rows ? pr[io.wpr] : (int)io.m;
+      if (io.pos) {
+        posr = io.pos;   // positions are per plan (shared by the batch)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = r0g + tid + u * NT;
+          if (j < r1g) ppre[u] = __ldg(posr + j);
+        }
+      }
+    }
     // (1) split the staged line into BF16 parts (with periodic halos)
     for (int e4 = tid; e4 < M / 4; e4 += NT) {
       const float4 x = *reinterpret_cast<const float4*>(xin + 4 * e4);
@@ -295,86 +406,30 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_fwd(const float* __restrict
     }
     __syncthreads();
 
-    // (3) stages 1 and 2, one group of 16 blocks (256 outputs) per warp step
+    // (3) stages 1 and 2: groups of 16 blocks (256 outputs), NG of them per
+    // warp step with their k-steps interleaved (independent MMA chains)
     const int hoff = 3 * clen - 8 * KS;   // from a lo column to the hi coefficient parts
-    for (int grp = warp; grp < ng; grp += NT / 32) {
-      float c[2][4], cs[2][4];
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) c[j][r] = cs[j][r] = 0.f;
-#pragma unroll
-      for (int ks = 0; ks < KS; ++ks) {
-        uint32_t A1[4], A2[4], A3[4];
-        {
-          const uint4 u1 = sA[(ks * 32 + lane) * 3], u2 = sA[(ks * 32 + lane) * 3 + 1],
-                      u3 = sA[(ks * 32 + lane) * 3 + 2];
-          A1[0] = u1.x; A1[1] = u1.y; A1[2] = u1.z; A1[3] = u1.w;
-          A2[0] = u2.x; A2[1] = u2.y; A2[2] = u2.z; A2[3] = u2.w;
-          A3[0] = u3.x; A3[1] = u3.y; A3[2] = u3.z; A3[3] = u3.w;
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          // window column kk = 16 ks + 2 t + 8 hh (< 2 lw = 16 KS): the lo
-          // coefficients for kk < lw = 8 KS, the hi ones after
-          const uint16_t* Cb = cp0 + a.bs * (16 * grp + 8 * j + g) - a.W0 + a.HL + 2 * t;
-          uint32_t bq[3][2];
-#pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            constexpr int LW = 8 * KS;
-            const int kk = 16 * ks + 8 * hh;
-            const uint16_t* C = kk < LW ? Cb + kk : Cb + hoff + kk;
-#pragma unroll
-            for (int pt = 0; pt < 3; ++pt) bq[pt][hh] = ld32(C + pt * clen);
-          }
-          mma_split(c[j], cs[j], A1, A2, A3, bq);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) c[j][r] += cs[j][r];
-      if (!a.per) {
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int blk = 16 * grp + 8 * j + 2 * t + e;
-            int o = -1;
-            if (blk < a.EBl) o = 16 * blk;
-            else if (blk >= a.nb - a.EBr) o = 16 * (a.EBl + blk - (a.nb - a.EBr));
-            if (o >= 0) {
-              c[j][e] = sEdge[o + g];
-              c[j][2 + e] = sEdge[o + g + 8];
-            }
-          }
-      }
-      uint32_t q[3][4];
-      split3(c[0][0], c[0][1], q[0][0], q[1][0], q[2][0]);
-      split3(c[0][2], c[0][3], q[0][1], q[1][1], q[2][1]);
-      split3(c[1][0], c[1][1], q[0][2], q[1][2], q[2][2]);
-      split3(c[1][2], c[1][3], q[0][3], q[1][3], q[2][3]);
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_bf16(d, q[2], Hb[j][0], Hb[j][1]);
-        mma_bf16(d, q[1], Hb[j][0], Hb[j][1]);
-        mma_bf16(d, q[0], Hb[j][0], Hb[j][1]);
-        // natural index 16 (16 grp + 8 j + 2 t + e) + g (+8) sits at
-        // pv = 320 grp + 160 j + 40 t + 16 e + g (+8)
-        float* v = sV + 320 * grp + 160 * j + 40 * t + g;
-        v[0] = d[0];
-        v[16] = d[1];
-        v[8] = d[2];
-        v[24] = d[3];
-      }
+    if (ng >= 2 * (NT / 32)) {
+      for (int grp = warp; grp < ng; grp += 2 * (NT / 32))
+        fwd_stage12<KS, 2>(grp, NT / 32, sA, cp0, clen, hoff, a, lane, g, t, Hb, sEdge, sV);
+    } else {
+      for (int grp = warp; grp < ng; grp += NT / 32)
+        fwd_stage12<KS, 1>(grp, NT / 32, sA, cp0, clen, hoff, a, lane, g, t, Hb, sEdge, sV);
     }
     __syncthreads();
     // (4) bits 8..L-1
     fwht_high(sV, ng, tid, NT);
     __syncthreads();
     // (5) store the natural-order line or gather the samples
-    if (io.mode == 1) {
+    if (io.mode == 1 && posr) {
+      float* y = out + b * io.m;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = r0g + tid + u * NT;
+        if (j < r1g) y[j] = sV[pv(ppre[u])];
+      }
+      for (int j = r0g + tid + 4 * NT; j < r1g; j += NT) y[j] = sV[pv(__ldg(posr + j))];
+    } else if (io.mode == 1) {
       const uint32_t* mk = smask + buf * wst;
       const int* pr = spraw + buf * wst;
       const int mrow = io.mask_rows == 1 ? 0 : l;
@@ -425,10 +480,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict
   uint32_t* u0 = reinterpret_cast<uint32_t*>(sA + a.KSA * 96);        // 3 parts of uwords each
   uint32_t* smask = u0 + 3 * uwords;                                   // 2 x wst
   int* spraw = reinterpret_cast<int*>(smask + 2 * wst);                // 2 x wst
-  float* sY = reinterpret_cast<float*>(spraw + 2 * wst);               // 2 x N (mode 1)
+  // the packed samples of the next line and their natural positions (pairs
+  // of 16-bit values per word): one buffer each, refilled after stage 2 of
+  // the current line, whose scatter is then done
+  float* sY = reinterpret_cast<float*>(spraw + 2 * wst);               // N (mode 1)
+  const bool spos = scat && io.pos;
+  const int pst = N / 2 + 4;
+  uint32_t* sP = reinterpret_cast<uint32_t*>(sY + (scat ? N : 0));       // pst (when spos)
   // FP32 copies of the samples the boundary rows read (after bits 4..L-1):
   // [0, Wl) and [N - Wl, N); the boundary matrix, staged when it fits
-  float* sUe = sY + (scat ? 2 * N : 0);
+  float* sUe = reinterpret_cast<float*>(sP + (spos ? pst : 0));
   const int Ra = 16 * (a.EAl + a.EAr);
   float* sEas = sUe + 2 * a.Wl;
   const float* Ea = a.eas ? sEas : a.Ea;
@@ -464,8 +525,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict
   };
   auto issue_y = [&](int ln, int bi, int r0, int r1) {
     const float* y = in + (ln / io.lines) * io.m;
-    float* dst = sY + bi * N;
-    for (int j = r0 + tid; j < r1; j += NT) cp4(dst + (j - r0), y + j);
+    (void)bi;
+    for (int j = r0 + tid; j < r1; j += NT) cp4(sY + (j - r0), y + j);
+    if (spos) {   // the words holding positions r0 .. r1 - 1
+      const uint32_t* pw32 = reinterpret_cast<const uint32_t*>(io.pos);
+      for (int w = (r0 >> 1) + tid; w < ((r1 + 1) >> 1); w += NT) cp4(sP + (w - (r0 >> 1)), pw32 + w);
+    }
   };
   pdl_trigger();
   pdl_wait();
@@ -503,7 +568,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tc_adj(const float* __restrict
       const int r1 = mrow + 1 < io.mask_rows ? pr[io.wpr] : (int)io.m;
       for (int k4 = tid; k4 < vst / 4; k4 += NT) reinterpret_cast<float4*>(sV)[k4] = make_float4(0.f, 0.f, 0.f, 0.f);
       __syncthreads();
-      const float* ys = sY + buf * N;
+      const float* ys = sY;
+      if (spos) {
+        const uint16_t* ps = reinterpret_cast<const uint16_t*>(sP) + (r0 & 1);
+        for (int j = tid; j < r1 - r0; j += NT) sV[pv(ps[j])] = ys[j];
+      } else
       for (int hw = tid; hw < 2 * io.wpr; hw += NT) {
         const uint32_t wd = mk[hw >> 1];
         uint32_t bits = (hw & 1) ? wd >> 16 : wd & 0xffffu;
@@ -672,8 +741,8 @@ static size_t tc_fwd_smem(const Plan& P, bool gather) {
   const size_t clen = (size_t)G.HL + P.M / 2 + G.HR;
   const size_t wst = gather ? (size_t)P.wpr + 4 : 0;
   const size_t ef = tc_efs_bytes(P) <= kEdgeStage ? tc_efs_bytes(P) : 0;
-  return sizeof(float) * pvlen(P.N) + (size_t)G.KS * 96 * 16 + sizeof(float) * 2 * P.M +
-         sizeof(float) * (16 * (G.EBl + G.EBr) + 4) + 2 * 2 * wst * 4 + ((6 * clen + 8 + 7) & ~(size_t)7) * 2 + ef +
+  return sizeof(float) * pvlen(P.N) + (size_t)G.KS * 96 * 16 + sizeof(float) * 3 * P.M +
+         sizeof(float) * (16 * (G.EBl + G.EBr) + 4) + 3 * 2 * wst * 4 + ((6 * clen + 8 + 7) & ~(size_t)7) * 2 + ef +
          16;
 }
 
@@ -683,8 +752,9 @@ static size_t tc_adj_smem(const Plan& P, bool scatter) {
   const size_t uwords = ((size_t)((ulen / 2) + 4 * ((ulen / 2) >> 4)) + 4 + 3) & ~(size_t)3;
   const size_t wst = scatter ? (size_t)P.wpr + 4 : 0;
   const size_t ea = tc_eas_bytes(P) <= kEdgeStage ? tc_eas_bytes(P) : 0;
+  const size_t pstage = (scatter && P.d_pos) ? ((size_t)P.N / 2 + 4) * 4 : 0;
   return sizeof(float) * pvlen(P.N) * (scatter ? 1 : 2) + (size_t)G.KSA * 96 * 16 + 3 * uwords * 4 + 2 * 2 * wst * 4 +
-         (scatter ? sizeof(float) * 2 * P.N : 0) + sizeof(float) * 2 * G.Wl + ea + 16;
+         (scatter ? sizeof(float) * P.N : 0) + pstage + sizeof(float) * 2 * G.Wl + ea + 16;
 }
 
 bool tc_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd) {

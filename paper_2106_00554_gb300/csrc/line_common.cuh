@@ -272,6 +272,7 @@ struct LineIO {
   int wpr;               // mask words per row
   int64_t m;             // samples per instance
   int mask_rows;         // 1 for d = 1 (all lines use row 0), else = lines
+  const uint16_t* pos;   // per sample: natural FWHT position in its row (or null)
 };
 
 // position of the (r+1)-th set bit of x (0 <= r < popc(x)), branch-free

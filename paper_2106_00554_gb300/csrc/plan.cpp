@@ -592,11 +592,42 @@ static int upload_mask(uw_plan* P, const int64_t* omega, int64_t m) {
     acc += __builtin_popcount(mask[w]);
   }
   if (acc != m) return fail(UW_ERR_INTERNAL, "mask count mismatch");
+  // natural-order position of every sample, in packed order: the sequency
+  // index n of a row reads the FWHT output at bitrev_L(n xor (n >> 1))
+  std::vector<uint16_t> pos;
+  if (N <= 65536) {
+    int L = 0;
+    while ((int64_t(1) << L) < N) ++L;
+    std::vector<uint16_t> seqpos((size_t)N);
+    for (int64_t n = 0; n < N; ++n) {
+      uint32_t gry = (uint32_t)(n ^ (n >> 1)), rev = 0;
+      for (int b = 0; b < L; ++b) rev |= ((gry >> b) & 1u) << (L - 1 - b);
+      seqpos[(size_t)n] = (uint16_t)rev;
+    }
+    pos.reserve((size_t)m);
+    for (int64_t w = 0; w < words; ++w)
+      for (uint32_t bits = mask[w]; bits; bits &= bits - 1)
+        pos.push_back(seqpos[(size_t)((w % wpr) * 32 + __builtin_ctz(bits))]);
+  }
+  uint16_t* dpos = nullptr;
+  if (!pos.empty()) {
+    pos.push_back(0);   // padding: positions are also read in 32-bit pairs
+    pos.push_back(0);
+    if (cudaMalloc(&dpos, pos.size() * sizeof(uint16_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(UW_ERR_OOM, "sample position allocation failed");
+    }
+    if (cudaMemcpy(dpos, pos.data(), pos.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(dpos);
+      return fail(UW_ERR_CUDA, "sample position upload failed");
+    }
+  }
   uint32_t* dm = nullptr;
   int32_t* dp = nullptr;
   if (cudaMalloc(&dm, words * sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&dp, words * sizeof(int32_t)) != cudaSuccess) {
     cudaFree(dm);
+    cudaFree(dpos);
     cudaGetLastError();
     return fail(UW_ERR_OOM, "mask allocation failed");
   }
@@ -604,12 +635,15 @@ static int upload_mask(uw_plan* P, const int64_t* omega, int64_t m) {
       cudaMemcpy(dp, pre.data(), words * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(dm);
     cudaFree(dp);
+    cudaFree(dpos);
     return fail(UW_ERR_CUDA, "mask upload failed");
   }
   cudaFree(P->d_mask);
   cudaFree(P->d_prefix);
+  cudaFree(P->d_pos);
   P->d_mask = dm;
   P->d_prefix = dp;
+  P->d_pos = dpos;
   P->m = m;
   P->words = words;
   P->wpr = wpr;
@@ -737,6 +771,7 @@ void uw_plan_destroy(uw_plan* P) {
   cudaFree(P->d_work);
   cudaFree(P->d_stage);
   cudaFree(P->d_tc);
+  cudaFree(P->d_pos);
   delete P;
 }
 

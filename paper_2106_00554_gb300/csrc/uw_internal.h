@@ -70,6 +70,7 @@ struct Plan {
   Tables<float> t32{};
   uint32_t* d_mask = nullptr;    // words
   int32_t* d_prefix = nullptr;   // exclusive prefix count per word
+  uint16_t* d_pos = nullptr;     // per sample (packed order): its natural FWHT position in the row (N <= 65536)
   void* d_work = nullptr;
   size_t work_bytes = 0;
   void* d_stage = nullptr;       // host-API staging (input + output)

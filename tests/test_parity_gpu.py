@@ -274,8 +274,12 @@ def test_config5_full_size_split_bf16():
     x = inputs.coeffs_2d(rng, R, plan.J0, 1.5)
     y = rng.standard_normal(omega.size)
     G = dense.G1d(R, q, p, VMP)
+    from paper_2106_00554_gb300 import _lib
+    _lib.uw_plan_profile(plan._h, True)
     assert rel(run_fwd(plan, x, F32_SPLIT_BF16), dense.forward2d(x, R, q, p, VMP, plan.J0, omega, G=G)) < 1e-5
     assert rel(run_adj(plan, y, F32_SPLIT_BF16), dense.adjoint2d(y, R, q, p, VMP, plan.J0, omega, G=G)) < 1e-5
+    # all four line passes of the benchmark workload run on the tensor cores
+    assert sum(n.endswith("_tc") for n in _kernel_names(plan)) == 4
 
 
 def test_config5_full_size_fp32():
