@@ -526,12 +526,31 @@ __device__ __forceinline__ void ana_interior(int m, int p_rt, const AS& s, const
   hi = b;
 }
 
+// The coarse kernels stage only the filters h and g (4p values) in shared
+// memory; the boundary blocks PL, QL, PR, QR are read through L1 by the tiles
+// that touch a VMP boundary.  Returns the number of staged values.
+template <typename T>
+__device__ __forceinline__ int stage_filters(const Tables<T>& t, const Geo& G, T* base, SmemTables<T>& s, int tid,
+                                             int nthr) {
+  const int n = 4 * G.p;
+  for (int i = tid; i < n; i += nthr) base[i] = t.h[i];   // h and g are contiguous in the packed tables
+  s.h = base;
+  s.g = base + 2 * G.p;
+  s.taps = nullptr;
+  s.EL = s.ER = nullptr;
+  s.PL = const_cast<T*>(t.PL);
+  s.QL = const_cast<T*>(t.QL);
+  s.PR = const_cast<T*>(t.PR);
+  s.QR = const_cast<T*>(t.QR);
+  return (n + 3) & ~3;
+}
+
 // tile edges: synthesis tiles of level-(j+1) samples, analysis tiles of
 // level-j coefficients per quadrant; small levels take small tiles so every
 // level launches at least 64 CTAs per instance (and the analysis column pass
 // maps a window of at most 64 columns to lanes)
-__host__ __device__ inline int syn_tile(int n1) { return n1 >= 512 ? 32 : (n1 >= 128 ? n1 / 8 : (n1 >= 64 ? 8 : n1)); }
-__host__ __device__ inline int ana_tile(int n0) { return n0 >= 64 ? 16 : (n0 >= 32 ? 8 : n0); }
+__host__ __device__ inline int syn_tile(int n1) { return n1 >= 512 ? 32 : (n1 >= 256 ? 16 : (n1 >= 8 ? 8 : n1)); }
+__host__ __device__ inline int ana_tile(int n0) { return n0 >= 128 ? 16 : (n0 >= 8 ? 8 : n0); }
 
 // synthesis level j -> j+1 on the n1 x n1 block [[LL, D1], [D2, D3]]:
 // LL from llsrc (leading dim ldll), details from x; output S_{j+1} to dst
@@ -543,7 +562,7 @@ __global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
-  const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  const int off = stage_filters(tab, G, sm, st, tid, nthr);
   pdl_trigger();
   pdl_wait();
   const int n0 = 1 << j, n1 = 2 * n0;
@@ -605,7 +624,7 @@ __global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, 
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
-  const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  const int off = stage_filters(tab, G, sm, st, tid, nthr);
   pdl_trigger();
   pdl_wait();
   const int n0 = 1 << j, n1 = 2 * n0;
@@ -1049,7 +1068,6 @@ static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xou
   const int M = P.M, Mh = M / 2;
   const int nl = P.R - 1 - P.J0;
   const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
-  const size_t tabn = (size_t)table_count(G);
   for (int it = 0; it < nl; ++it) {
     const int j = fwd ? P.J0 + it : P.R - 2 - it;
     const int n0 = 1 << j, n1 = 2 * n0;
@@ -1061,7 +1079,7 @@ static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xou
     if (fwd) {
       const int TS = syn_tile(n1), tiles = n1 / TS;
       const int thr = TS >= 32 ? 256 : 128;
-      const size_t sm = sizeof(T) * (tabn + 4 * (size_t)w * w + 2 * (size_t)w * TS);
+      const size_t sm = sizeof(T) * (((size_t)4 * G.p + 3) / 4 * 4 + 4 * (size_t)w * w + 2 * (size_t)w * TS);
       const T* src = it == 0 ? x : ((nl - it) % 2 == 0 ? XS : XS2);
       const int64_t ld = it == 0 ? M : Mh, sb = it == 0 ? MM : HH;
       T* dst = (nl - 1 - it) % 2 == 0 ? XS : XS2;
@@ -1077,7 +1095,7 @@ static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xou
     } else {
       const int TS = ana_tile(n0), tiles = n0 / TS;
       const int thr = TS >= 16 ? 256 : 128;
-      const size_t sm = sizeof(T) * (tabn + (size_t)w * w + 2 * (size_t)TS * w);
+      const size_t sm = sizeof(T) * (((size_t)4 * G.p + 3) / 4 * 4 + (size_t)w * w + 2 * (size_t)TS * w);
       const T* src = it % 2 == 0 ? XS : XS2;
       T* dst = it == nl - 1 ? nullptr : (it % 2 == 0 ? XS2 : XS);
       char name[32];
