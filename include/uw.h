@@ -238,6 +238,20 @@ int uw_plan_profile(uw_plan* plan, int enable);
 int uw_plan_profile_read(uw_plan* plan, int i, char* name, int cap, double* total_ms,
                          int64_t* launches, double* bytes_per_launch);
 
+/*
+ * uw_plan_device_status -- waits for the device (cudaDeviceSynchronize on the
+ * plan's device) and reports whether a bounded device-side wait of the plan
+ * gave up since the last query: the 2D products run all coarse wavelet levels
+ * in one cooperative launch whose CTAs meet at grid barriers between levels;
+ * each wait spins a bounded number of times (environment variable
+ * UW_BARRIER_SPIN_LIMIT, default 2^22 polls of about 64 ns) and then records
+ * the failure and returns.  Returns UW_OK, UW_ERR_TIMEOUT (the results of the
+ * calls since the last query are invalid; the barrier is reset for the next
+ * call) or UW_ERR_CUDA (a CUDA error surfaced while synchronising).  Not part
+ * of the paper: failure reporting of this implementation.
+ */
+int uw_plan_device_status(uw_plan* plan);
+
 /* Number of kernel launches the last uw_forward / uw_adjoint issued. */
 int uw_plan_last_launches(const uw_plan* plan);
 

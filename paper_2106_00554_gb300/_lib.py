@@ -40,6 +40,7 @@ SIGNATURES = {
     "uw_plan_table": (_i64, [_c_p, _int, _dp, _i64]),
     "uw_host_table": (_i64, [_int, _int, _int, _dp, _i64]),
     "uw_plan_last_launches": (_int, [_c_p]),
+    "uw_plan_device_status": (_int, [_c_p]),
     "uw_plan_profile": (_int, [_c_p, _int]),
     "uw_plan_profile_read": (_int, [_c_p, _int, ctypes.c_char_p, _int, _dp, _i64p, _dp]),
     "uw_fista_step": (_int, [_int, _i64, _c_p, _c_p, _c_p, _c_p, ctypes.c_double, ctypes.c_double,
@@ -144,6 +145,12 @@ def uw_dot(precision, n, a, b, out, stream):
 
 def uw_axpby(precision, n, alpha, a, beta, b, out, stream):
     _chk(lib().uw_axpby(precision, n, alpha, a, beta, b, out, stream), "uw_axpby")
+
+
+def uw_plan_device_status(h):
+    """UW_OK, or UW_ERR_TIMEOUT if a bounded device wait gave up since the
+    last query (synchronises the device); returns the status, does not raise."""
+    return lib().uw_plan_device_status(h)
 
 
 def uw_plan_destroy(h):

@@ -553,22 +553,16 @@ __host__ __device__ inline int syn_tile(int n1) { return n1 >= 512 ? 32 : (n1 >=
 __host__ __device__ inline int ana_tile(int n0) { return n0 >= 128 ? 16 : (n0 >= 8 ? 8 : n0); }
 
 // synthesis level j -> j+1 on the n1 x n1 block [[LL, D1], [D2, D3]]:
-// LL from llsrc (leading dim ldll), details from x; output S_{j+1} to dst
+// LL from llsrc (leading dim ldll), details from x; output S_{j+1} to dst.
+// One TS x TS output tile `tile` of instance b; W is the CTA's shared window.
 template <typename T, int P>
-__global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc, int64_t ldll, int64_t llb,
-                                                     const T* __restrict__ x, int M, T* __restrict__ dst, int64_t lddst,
-                                                     int64_t dstb, int j, int TS, Tables<T> tab, Geo G) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  SmemTables<T> st;
-  const int off = stage_filters(tab, G, sm, st, tid, nthr);
-  pdl_trigger();
-  pdl_wait();
+__device__ __forceinline__ void syn2d_tile(int tile, int64_t b, const T* __restrict__ llsrc, int64_t ldll,
+                                           int64_t llb, const T* __restrict__ x, int M, T* __restrict__ dst,
+                                           int64_t lddst, int64_t dstb, int j, int TS, const SmemTables<T>& st, T* W,
+                                           const Geo& G, int tid, int nthr) {
   const int n0 = 1 << j, n1 = 2 * n0;
   const int tiles = n1 / TS;
-  const int r0 = (blockIdx.x / tiles) * TS, c0 = (blockIdx.x % tiles) * TS;
-  const int64_t b = blockIdx.y;
+  const int r0 = (tile / tiles) * TS, c0 = (tile % tiles) * TS;
   const bool per = G.bd == UW_BOUNDARY_PERIODIC;
   int dr0, dr1, dc0, dc1;
   syn_dep(r0, r0 + TS, n0, G, dr0, dr1);
@@ -576,7 +570,6 @@ __global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc
   const int nr = dr1 - dr0, nc = dc1 - dc0;
   const int wrapr = per, wrapc = per;  // periodic reads go through the power-of-two mask
   // window of the four subbands: W[q][i][m], q = 0 LL, 1 D1, 2 D2, 3 D3
-  T* W = sm + off;
   T* H = W + 4 * nr * nc;  // row-synthesised: H[half][i][c], half 0 = top rows, 1 = bottom rows
   const T* xb = x + b * (int64_t)M * M;
   const T* lb = llsrc + b * llb;
@@ -614,12 +607,10 @@ __global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc
   }
 }
 
-// analysis level j+1 -> j of the n1 x n1 block src (leading dim ldsrc): the
-// low-pass block to lldst (or to x when lldst is null), details to x
 template <typename T, int P>
-__global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, int64_t ldsrc, int64_t srcb,
-                                                     T* __restrict__ x, int M, T* __restrict__ lldst, int64_t ldll,
-                                                     int64_t llb, int j, int TS, Tables<T> tab, Geo G) {
+__global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc, int64_t ldll, int64_t llb,
+                                                     const T* __restrict__ x, int M, T* __restrict__ dst, int64_t lddst,
+                                                     int64_t dstb, int j, int TS, Tables<T> tab, Geo G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -627,17 +618,26 @@ __global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, 
   const int off = stage_filters(tab, G, sm, st, tid, nthr);
   pdl_trigger();
   pdl_wait();
+  syn2d_tile<T, P>(blockIdx.x, blockIdx.y, llsrc, ldll, llb, x, M, dst, lddst, dstb, j, TS, st, sm + off, G, tid, nthr);
+}
+
+// analysis level j+1 -> j of the n1 x n1 block src (leading dim ldsrc): the
+// low-pass block to lldst (or to x when lldst is null), details to x.  One
+// tile of TS x TS coefficients per quadrant; S is the CTA's shared window.
+template <typename T, int P>
+__device__ __forceinline__ void ana2d_tile(int tile, int64_t b, const T* __restrict__ src, int64_t ldsrc,
+                                           int64_t srcb, T* __restrict__ x, int M, T* __restrict__ lldst,
+                                           int64_t ldll, int64_t llb, int j, int TS, const SmemTables<T>& st, T* S,
+                                           const Geo& G, int tid, int nthr) {
   const int n0 = 1 << j, n1 = 2 * n0;
   const int tiles = n0 / TS;  // TS: output coefficients per dimension and quadrant
-  const int m0 = (blockIdx.x / tiles) * TS, k0 = (blockIdx.x % tiles) * TS;
-  const int64_t b = blockIdx.y;
+  const int m0 = (tile / tiles) * TS, k0 = (tile % tiles) * TS;
   const bool per = G.bd == UW_BOUNDARY_PERIODIC;
   int sr0, sr1, sc0, sc1;
   ana_dep(m0, m0 + TS, n0, G, sr0, sr1);
   ana_dep(k0, k0 + TS, n0, G, sc0, sc1);
   const int nr = sr1 - sr0, nc = sc1 - sc0;
   const int wrapr = per, wrapc = per;
-  T* S = sm + off;            // S[i][c] window of the level-(j+1) block
   T* H = S + nr * nc;         // H[half][m][c]: column analysis, half 0 = low, 1 = high
   const T* sb = src + b * srcb;
   {
@@ -681,6 +681,133 @@ __global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, 
       xb[(int64_t)(n0 + mm) * M + k0 + kk] = lo;
       xb[(int64_t)(n0 + mm) * M + n0 + k0 + kk] = hi;
     }
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, int64_t ldsrc, int64_t srcb,
+                                                     T* __restrict__ x, int M, T* __restrict__ lldst, int64_t ldll,
+                                                     int64_t llb, int j, int TS, Tables<T> tab, Geo G) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<T> st;
+  const int off = stage_filters(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
+  ana2d_tile<T, P>(blockIdx.x, blockIdx.y, src, ldsrc, srcb, x, M, lldst, ldll, llb, j, TS, st, sm + off, G, tid, nthr);
+}
+
+// ---------------------------------------------------------------------------
+// All coarse 2D levels in one cooperative launch: the CTAs of the grid (all
+// resident at once) take the tiles of a level in turn and meet at a grid
+// barrier before the next level, whose tiles read what every CTA wrote.
+// The barrier spins a bounded number of times; a CTA that gives up records
+// the failure in the barrier's error word and returns (uw_plan_device_status
+// reports it as UW_ERR_TIMEOUT).
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+  unsigned int count;   // CTAs arrived at the current barrier
+  unsigned int gen;     // barriers completed (wraps)
+  unsigned int err;     // set when a wait gave up
+  unsigned int pad;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// returns false (in every thread of the CTA) if the wait gave up
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int nblocks, unsigned int limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g = ld_acquire_u32(&bar->gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+    if (arrived == nblocks) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      unsigned int it = 0;
+      while (ld_acquire_u32(&bar->gen) == g) {
+        if (++it > limit) {
+          atomicExch(&bar->err, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// level buffers of the forward synthesis: level it (j = J0 + it) reads
+// S_j (x itself for it = 0) and writes S_{j+1}; S_{R-1} ends in XS
+template <typename T>
+struct CoarseIO {
+  const T* x;    // forward input (Mallat layout)
+  T* xout;       // adjoint output (Mallat layout)
+  T* XS;
+  T* XS2;
+  int M, J0, nl, batch;
+};
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_syn2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, GridBarrier* bar,
+                                                      unsigned int limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<T> st;
+  const int off = stage_filters(tab, G, sm, st, tid, nthr);
+  const int M = io.M, Mh = M / 2;
+  const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
+  for (int it = 0; it < io.nl; ++it) {
+    const int j = io.J0 + it, n1 = 2 << j;
+    const int TS = syn_tile(n1), tiles = (n1 / TS) * (n1 / TS);
+    const T* src = it == 0 ? io.x : ((io.nl - it) % 2 == 0 ? io.XS : io.XS2);
+    const int64_t ld = it == 0 ? M : Mh, sb = it == 0 ? MM : HH;
+    T* dst = (io.nl - 1 - it) % 2 == 0 ? io.XS : io.XS2;
+    for (int t = blockIdx.x; t < tiles * io.batch; t += gridDim.x) {
+      __syncthreads();   // the previous tile's windows are no longer read
+      syn2d_tile<T, P>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, TS, st, sm + off, G, tid,
+                       nthr);
+    }
+    if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, limit)) return;
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_ana2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, GridBarrier* bar,
+                                                      unsigned int limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<T> st;
+  const int off = stage_filters(tab, G, sm, st, tid, nthr);
+  const int M = io.M, Mh = M / 2;
+  const int64_t HH = (int64_t)Mh * Mh;
+  const int R = io.J0 + io.nl + 1;
+  for (int it = 0; it < io.nl; ++it) {
+    const int j = R - 2 - it, n0 = 1 << j;
+    const int TS = ana_tile(n0), tiles = (n0 / TS) * (n0 / TS);
+    const T* src = it % 2 == 0 ? io.XS : io.XS2;
+    T* dst = it == io.nl - 1 ? nullptr : (it % 2 == 0 ? io.XS2 : io.XS);
+    for (int t = blockIdx.x; t < tiles * io.batch; t += gridDim.x) {
+      __syncthreads();
+      ana2d_tile<T, P>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, TS, st,
+                       sm + off, G, tid, nthr);
+    }
+    if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, limit)) return;
   }
 }
 
@@ -808,6 +935,28 @@ int upload_tables(Plan& P) {
     }
     if (cudaMemcpy(P.d_tc, tcw.data(), tcw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
       set_error(UW_ERR_CUDA, "tensor-core table upload failed");
+      return UW_ERR_CUDA;
+    }
+  }
+  if (cudaMalloc(&P.d_sync, sizeof(GridBarrier)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error(UW_ERR_OOM, "barrier allocation failed");
+    return UW_ERR_OOM;
+  }
+  if (cudaMemset(P.d_sync, 0, sizeof(GridBarrier)) != cudaSuccess) {
+    set_error(UW_ERR_CUDA, "barrier initialisation failed");
+    return UW_ERR_CUDA;
+  }
+  std::vector<float> f32w;
+  build_f32(P, f32w);
+  if (P.f32.ok && !f32w.empty()) {
+    if (cudaMalloc(&P.d_f32, f32w.size() * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error(UW_ERR_OOM, "edge-correction table allocation failed");
+      return UW_ERR_OOM;
+    }
+    if (cudaMemcpy(P.d_f32, f32w.data(), f32w.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error(UW_ERR_CUDA, "edge-correction table upload failed");
       return UW_ERR_CUDA;
     }
   }
@@ -1006,6 +1155,11 @@ void launch_line<float>(bool fwd, const Plan& P, const Geo& G, const float* in, 
     L.note(tc_launch(fwd, P, in, out, io, nblocks, L.s));
     return;
   }
+  if (!L.split && f32_eligible(P, io, in, out, fwd) && !getenv_flag("UW_GENERIC_LINES")) {
+    if (L.armed) L.retag(P.prof->names[L.cur.id] + "_f32");
+    L.note(f32_launch(fwd, P, in, out, io, nblocks, L.s));
+    return;
+  }
   if (line2_eligible(P) && !getenv_flag("UW_GENERIC_LINES")) {
     L.note(line2_launch(fwd, P, G, in, out, io, nblocks, L.s));
     return;
@@ -1062,9 +1216,75 @@ static int coarse_tile_extent(const Geo& G, int j, bool syn) {
   return worst;
 }
 
+// polls of a grid-barrier wait before it gives up (read at every launch)
+static unsigned int barrier_spin_limit() {
+  const char* e = getenv("UW_BARRIER_SPIN_LIMIT");
+  return e && e[0] ? (unsigned int)strtoul(e, nullptr, 10) : (1u << 22);
+}
+
+// All coarse levels in one cooperative launch (grid barrier between levels);
+// false if that launch is not possible here (then one launch per level).
+template <typename T>
+static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout, T* XS, T* XS2, int batch,
+                                bool fwd, Launcher& L) {
+  const int nl = P.R - 1 - P.J0;
+  if (nl < 2 || !P.d_sync || getenv_flag("UW_COARSE_PER_LEVEL")) return false;
+  size_t sm = 0;
+  int max_tiles = 0;
+  double bytes = 0;
+  for (int it = 0; it < nl; ++it) {
+    const int j = fwd ? P.J0 + it : P.R - 2 - it;
+    const int n0 = 1 << j, n1 = 2 * n0;
+    const int w = coarse_tile_extent(G, j, fwd);
+    if (!fwd && w > 64) return false;
+    if (fwd) {
+      const int TS = syn_tile(n1);
+      sm = std::max(sm, sizeof(T) * (((size_t)4 * G.p + 3) / 4 * 4 + 4 * (size_t)w * w + 2 * (size_t)w * TS));
+      max_tiles = std::max(max_tiles, (n1 / TS) * (n1 / TS));
+    } else {
+      const int TS = ana_tile(n0);
+      sm = std::max(sm, sizeof(T) * (((size_t)4 * G.p + 3) / 4 * 4 + (size_t)w * w + 2 * (size_t)TS * w));
+      max_tiles = std::max(max_tiles, (n0 / TS) * (n0 / TS));
+    }
+    bytes += sizeof(T) * (double)batch * (4.0 * n0 * n0 + (double)n1 * n1);
+  }
+  CoarseIO<T> io{x, xout, XS, XS2, P.M, P.J0, nl, batch};
+  bool ok = false;
+  coarse_dispatch<T>(G.p, [&](auto pc) {
+    constexpr int PP = decltype(pc)::value;
+    auto kern = fwd ? k_syn2d_levels<T, PP> : k_ana2d_levels<T, PP>;
+    set_smem_limit((const void*)kern);
+    int dev = 0, nsm = 0, per = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, sm) != cudaSuccess || per < 1) {
+      cudaGetLastError();
+      return;
+    }
+    const int grid = (int)std::min<int64_t>((int64_t)per * nsm, (int64_t)max_tiles * batch);
+    L.pre(fwd ? "idwt2d_levels" : "dwt2d_levels", bytes);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = L.s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    L.note(cudaLaunchKernelEx(&cfg, kern, io, tabs<T>(P), G, (GridBarrier*)P.d_sync, barrier_spin_limit()));
+    L.check();
+    ok = true;
+  });
+  return ok;
+}
+
 template <typename T>
 static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xout, T* XS, T* XS2, int batch,
                                  bool fwd, Launcher& L) {
+  if (launch_coarse_fused<T>(P, G, x, xout, XS, XS2, batch, fwd, L)) return;
   const int M = P.M, Mh = M / 2;
   const int nl = P.R - 1 - P.J0;
   const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
@@ -1467,6 +1687,31 @@ static int check_call(const uw_plan* P, int prec, const void* x_ptr, const void*
 }
 
 extern "C" {
+
+int uw_plan_device_status(uw_plan* P) {
+  if (!P) {
+    uw::set_error(UW_ERR_INVALID_ARG, "null plan");
+    return UW_ERR_INVALID_ARG;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != P->device) cudaSetDevice(P->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  unsigned int words[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess && P->d_sync) e = cudaMemcpy(words, P->d_sync, sizeof words, cudaMemcpyDeviceToHost);
+  int st = UW_OK;
+  if (e != cudaSuccess) {
+    uw::set_error(UW_ERR_CUDA, std::string("device status: ") + cudaGetErrorString(e));
+    st = UW_ERR_CUDA;
+  } else if (words[2]) {
+    cudaMemset(P->d_sync, 0, sizeof words);   // a fresh barrier for the next launch
+    cudaDeviceSynchronize();
+    uw::set_error(UW_ERR_TIMEOUT, "a grid barrier wait gave up; results of the affected calls are invalid");
+    st = UW_ERR_TIMEOUT;
+  }
+  if (cur != P->device) cudaSetDevice(cur);
+  return st;
+}
 
 int uw_forward(const uw_plan* P, int prec, const void* x, void* y, int batch, void* stream) {
   int st = check_call(P, prec, x, y, batch);

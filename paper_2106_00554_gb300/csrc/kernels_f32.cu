@@ -1,0 +1,720 @@
+// FP32 line operators on the CUDA cores (sm_103a): the hot kernels of the 2D
+// path (Sec. 5, Algorithm 2) for lines of N = 2048 or 4096 samples.
+//
+// forward, one line of M = N / Q coefficients (lo | hi of the last level):
+//   (A) last synthesis level (Sec. 3.2): s = Syn(lo, hi), 16/Q values per
+//       thread from a register window;
+//   (B) v = T s (Sec. 4.1 cell integrals, upsampling by Q = 2^q), 16
+//       consecutive outputs per thread, then the Walsh-Hadamard stages of
+//       bits 0-3 in registers (Sec. 3.1, natural order);
+//   (C) bits 4-7 and bits 8..L-1 as radix-16 (or 8) pencil passes in shared
+//       memory;
+//   then the natural-order line is stored, or the sampled sequency indices
+//   are gathered (P_Omega, Sec. 1.1).
+// adjoint (Sec. 4.2): stage or scatter -> the same Walsh stages -> s = T^T v
+// -> analysis (lo, hi) -> store.
+//
+// Both (A) and (B) use the interior formulas on the whole line with zero
+// padding beyond its ends (periodic plans: wrapped copies in halos).  Near a
+// VMP boundary the exact operator differs from that by C x_edge, where
+// x_edge holds the p lo and p hi coefficients at that end and C reaches only
+// the first / last K outputs of T (built on the host, tc_plan.cpp); warp 0
+// and the last warp compute these corrections while the others run (A), and
+// the owners add them before the bits 0-3 stage.  The adjoint adds C^T
+// applied to the first / last K transformed samples to the 2p edge outputs.
+//
+// CTAs are persistent (N / 16 threads, one 16-output block per thread) and
+// copy the next line (and its sample positions) into shared memory with
+// cp.async while the current line runs.  Shared-memory layouts are padded so
+// that the vector stores of (B), the pencils of (C) and the vector window
+// loads are free of bank conflicts; the Walsh butterflies use the packed
+// FP32x2 add of sm_100+.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+
+#include "line_common.cuh"
+
+namespace uw {
+
+namespace f32k {
+
+// taps as kernel parameters (constant bank), zero-padded to PM >= p, with
+// 2^{-R/2} folded into the cell integrals:
+//   hp[f][d + PM/2] = h_{2d+f}, gp likewise          (d in [-PM/2, PM/2])
+//   tp[f][d + PM-1] = 2^{-R/2} I_q[Q d + f]           (d in [-(PM-1), PM-1])
+template <int PM, int Q>
+struct Taps {
+  float hp[2][PM + 1];
+  float gp[2][PM + 1];
+  float tp[Q][2 * PM - 1];
+};
+
+struct Args {
+  const float* C;   // VMP edge corrections [2][K][CS], null for periodic plans
+  int K, CS, p, per;
+  int L;            // log2 N
+};
+
+// Walsh line: element k at vp(k) (4 words of padding per 16, 16 per 256)
+__host__ __device__ __forceinline__ constexpr int vp(int k) { return k + 4 * (k >> 4) + 16 * (k >> 8); }
+// s line: 4 words of padding per 32
+__host__ __device__ __forceinline__ constexpr int sp(int m) { return m + 4 * (m >> 5); }
+
+__host__ __device__ constexpr int up4(int a) { return (a + 3) / 4 * 4; }
+
+// geometry constants of one instantiation
+template <int PM, int Q, int NT>
+struct Geom {
+  static constexpr int N = 16 * NT;          // samples per line
+  static constexpr int M = N / Q;            // coefficients per line
+  static constexpr int n0 = M / 2;
+  static constexpr int BS = 16 / Q;          // s values per thread
+  static constexpr int BL = BS / 2;          // lo (and hi) values per thread
+  static constexpr int VW = BL >= 4 ? 4 : 2; // vector width of the coefficient window loads
+  static constexpr int HX = 8;               // coefficient halo (per side, per half)
+  static constexpr int XL = 2 * (n0 + 2 * HX);   // one staged coefficient line (lo region, hi region)
+  static constexpr int HS = up4(PM + 3);     // s halo
+  static constexpr int SL = up4(sp(M + 2 * HS - 1) + 1);
+  // (A) synthesis window: lo[a0 - PM/2 + w'], loaded from an aligned start
+  static constexpr int OFFX = ((HX - PM / 2) % VW + VW) % VW;
+  static constexpr int NWX = (OFFX + BL + PM + VW - 1) / VW * VW;
+  // (B) T window: s[i0 - PM + 1 + w']
+  static constexpr int OFFB = ((HS - PM + 1) % 4 + 4) % 4;
+  static constexpr int NWB = up4(OFFB + BS + 2 * PM - 2);
+  // adjoint T^T window: v[Q (m0 - PM + 1) + w']
+  static constexpr int OFFT = ((4 - (Q * (PM - 1)) % 4) % 4);
+  static constexpr int NWT = up4(OFFT + Q * (BS + 2 * PM - 2));
+  // adjoint analysis window: s[2 i0 - PM + w']
+  static constexpr int OFFA = ((HS - PM) % 4 + 4) % 4;
+  static constexpr int NWA = up4(OFFA + 2 * BL + 2 * PM);
+  static constexpr int VH = 256;             // adjoint Walsh halo (keeps the padding pattern)
+  static constexpr int VLf = up4(vp(N - 1) + 1);
+  static constexpr int VLa = up4(vp(N + 2 * VH - 1) + 1);
+  static constexpr int PST = N / 2 + 4;      // sample-position words per buffer
+  static_assert(M % NT == 0 && BS * NT == M, "one block of 16 outputs per thread");
+  static_assert(HX >= PM / 2 + VW - 1, "coefficient halo too small");
+  static_assert(HS >= PM + 3, "s halo too small");
+  static_assert(Q * (PM - 1) + OFFT <= VH, "Walsh halo too small");
+};
+
+// In-register Walsh-Hadamard transform of R values (natural order): the
+// first stage pairs neighbours; the later ones combine aligned pairs with the
+// packed FP32x2 add.
+template <int R>
+__device__ __forceinline__ void wht(float (&a)[R]) {
+#pragma unroll
+  for (int i = 0; i < R; i += 2) {
+    const float x = a[i], y = a[i + 1];
+    a[i] = x + y;
+    a[i + 1] = x - y;
+  }
+  const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+  for (int h = 2; h < R; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < R; i += 2)
+      if (!(i & h)) {
+        const float2 x = make_float2(a[i], a[i + 1]), y = make_float2(a[i + h], a[i + h + 1]);
+        const float2 s = __fadd2_rn(x, y), d = __ffma2_rn(y, m1, x);
+        a[i] = s.x;
+        a[i + 1] = s.y;
+        a[i + h] = d.x;
+        a[i + h + 1] = d.y;
+      }
+}
+
+// one pencil: elements e0 + i * stride (i < R) of the line whose element k
+// sits at V[vp(k + off)]
+template <int R>
+__device__ __forceinline__ void pencil(float* V, int off, int e0, int stride) {
+  float a[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) a[i] = V[vp(e0 + i * stride + off)];
+  wht<R>(a);
+#pragma unroll
+  for (int i = 0; i < R; ++i) V[vp(e0 + i * stride + off)] = a[i];
+}
+
+// the lowest element of pencil c (< 256) of the bits-8.. pass: the two
+// half-warps of a warp take 16-blocks a and a + 4, whose padded addresses
+// differ by 16 banks
+__device__ __forceinline__ int high_pencil(int c) {
+  const int hw = c >> 4, w = hw >> 1;
+  const int a = (w & 3) + 8 * (w >> 2) + 4 * (hw & 1);
+  return 16 * a + (c & 15);
+}
+
+// bits 4-7 (one radix-16 pencil per thread) and bits 8..L-1 (256 pencils)
+template <int NT>
+__device__ __forceinline__ void pass_mid(float* V, int off, int tid) {
+  pencil<16>(V, off, (tid & 15) + 256 * (tid >> 4), 16);
+}
+template <int NT>
+__device__ __forceinline__ void pass_high(float* V, int off, int tid) {
+  constexpr int N = 16 * NT, RH = N / 256;
+#pragma unroll
+  for (int c = tid; c < 256; c += NT) pencil<RH>(V, off, high_pencil(c), 256);
+}
+
+__device__ __forceinline__ void cp16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp4(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// packed-sample range [r0, r1) of mask row mrow
+__device__ __forceinline__ void row_range(const LineIO& io, int mrow, int& r0, int& r1) {
+  r0 = __ldg(io.prefix + (int64_t)mrow * io.wpr);
+  r1 = mrow + 1 < io.mask_rows ? __ldg(io.prefix + (int64_t)(mrow + 1) * io.wpr) : (int)io.m;
+}
+
+// positions (uint16 pairs) of samples [r0, r1) into sP
+__device__ __forceinline__ void issue_pos(const LineIO& io, int r0, int r1, uint32_t* sP, int tid, int nt) {
+  const uint32_t* pw32 = reinterpret_cast<const uint32_t*>(io.pos);
+  for (int w = (r0 >> 1) + tid; w < ((r1 + 1) >> 1); w += nt) cp4(sP + (w - (r0 >> 1)), pw32 + w);
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+template <int PM, int Q, int NT>
+__global__ void __launch_bounds__(NT, 2) k_f32_fwd(const float* __restrict__ in, float* __restrict__ out, Args a,
+                                                   Taps<PM, Q> tp, LineIO io, int total) {
+  using G = Geom<PM, Q, NT>;
+  constexpr int N = G::N, M = G::M, n0 = G::n0, BS = G::BS, BL = G::BL, VW = G::VW, HX = G::HX, XL = G::XL;
+  constexpr int HS = G::HS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool gather = io.mode == 1;
+  float* sV = reinterpret_cast<float*>(smem_raw);
+  float* sS = sV + G::VLf;
+  float* sX = sS + G::SL;                                        // 2 x XL
+  float* sCorr = sX + 2 * XL;                                     // 2K (VMP)
+  uint32_t* sP = reinterpret_cast<uint32_t*>(sCorr + up4(2 * a.K));  // 2 x PST (gather)
+
+  // halos start zero (VMP) and periodic halos are rewritten per line
+  for (int i = tid; i < G::SL; i += NT) sS[i] = 0.f;
+  for (int i = tid; i < 2 * XL; i += NT) sX[i] = 0.f;
+  __syncthreads();
+
+  auto issue_in = [&](int ln, int bi) {
+    const int l = ln % io.lines;
+    const int64_t b = ln / io.lines;
+    const int drow = io.seq_rows ? seqrow(l, a.L) : l;
+    const float* src = in + b * io.in_batch + (int64_t)drow * io.in_stride;
+    float* dst = sX + bi * XL;
+    for (int e4 = tid; e4 < M / 4; e4 += NT) {
+      const int i = 4 * e4, half = i >= n0, ii = i - half * n0;
+      float* reg = dst + half * (n0 + 2 * HX);
+      cp16(reg + HX + ii, src + i);
+      if (a.per) {
+        if (ii < HX) cp16(reg + HX + n0 + ii, src + i);
+        if (ii >= n0 - HX) cp16(reg + ii - (n0 - HX), src + i);
+      }
+    }
+  };
+
+  pdl_trigger();
+  pdl_wait();
+  const int G0 = gridDim.x;
+  int line = blockIdx.x;
+  int cr0 = 0, cr1 = 0, xr0 = 0, xr1 = 0;
+  if (line < total) {
+    issue_in(line, 0);
+    if (gather) {
+      row_range(io, line % io.lines, cr0, cr1);
+      issue_pos(io, cr0, cr1, sP, tid, NT);
+    }
+  }
+  cp_commit();
+  if (gather && line + G0 < total) row_range(io, (line + G0) % io.lines, xr0, xr1);
+
+  for (int buf = 0; line < total; line += G0, buf ^= 1) {
+    const int nxt = line + G0;
+    if (nxt < total) {
+      issue_in(nxt, buf ^ 1);
+      if (gather) issue_pos(io, xr0, xr1, sP + (buf ^ 1) * G::PST, tid, NT);
+    }
+    cp_commit();
+    int yr0 = 0, yr1 = 0;
+    if (gather && nxt + G0 < total) row_range(io, (nxt + G0) % io.lines, yr0, yr1);
+    cp_wait1();
+    __syncthreads();
+    const int l = line % io.lines;
+    const int64_t b = line / io.lines;
+    const float* xl = sX + buf * XL;           // lo[i] at xl[HX + i]
+    const float* xh = xl + n0 + 2 * HX;        // hi[i] at xh[HX + i]
+
+    // (A) s[BS u .. BS u + BS) = Syn(lo, hi), interior formula
+    {
+      const int a0 = BL * tid;
+      const int i0 = HX + a0 - PM / 2 - G::OFFX;     // multiple of VW
+      float wl[G::NWX], wh[G::NWX];
+#pragma unroll
+      for (int w = 0; w < G::NWX; w += VW) {
+        if constexpr (VW == 4) {
+          const float4 u = *reinterpret_cast<const float4*>(xl + i0 + w);
+          const float4 v = *reinterpret_cast<const float4*>(xh + i0 + w);
+          wl[w] = u.x; wl[w + 1] = u.y; wl[w + 2] = u.z; wl[w + 3] = u.w;
+          wh[w] = v.x; wh[w + 1] = v.y; wh[w + 2] = v.z; wh[w + 3] = v.w;
+        } else {
+          const float2 u = *reinterpret_cast<const float2*>(xl + i0 + w);
+          const float2 v = *reinterpret_cast<const float2*>(xh + i0 + w);
+          wl[w] = u.x; wl[w + 1] = u.y;
+          wh[w] = v.x; wh[w + 1] = v.y;
+        }
+      }
+      float s[BS];
+#pragma unroll
+      for (int jj = 0; jj < BL; ++jj)
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          float acc = 0.f;
+#pragma unroll
+          for (int d = -PM / 2; d <= PM / 2; ++d) {
+            const int w = jj - d + PM / 2 + G::OFFX;
+            acc = fmaf(tp.hp[f][d + PM / 2], wl[w], acc);
+            acc = fmaf(tp.gp[f][d + PM / 2], wh[w], acc);
+          }
+          s[2 * jj + f] = acc;
+        }
+      const int m0 = BS * tid;
+#pragma unroll
+      for (int j = 0; j < BS; j += 4)
+        *reinterpret_cast<float4*>(sS + sp(HS + m0 + j)) = make_float4(s[j], s[j + 1], s[j + 2], s[j + 3]);
+      if (a.per) {
+#pragma unroll
+        for (int j = 0; j < BS; ++j) {
+          const int m = m0 + j;
+          if (m < HS) sS[sp(HS + M + m)] = s[j];
+          if (m >= M - HS) sS[sp(HS + m - M)] = s[j];
+        }
+      }
+    }
+    // VMP edge corrections of T (warp 0: left end, last warp: right end)
+    if (a.K && (warp == 0 || warp == NT / 32 - 1)) {
+      const int side = warp == 0 ? 0 : 1;
+      const float* C = a.C + (size_t)side * a.K * a.CS;
+      const int base = side == 0 ? 0 : n0 - a.p;
+      for (int r = lane; r < a.K; r += 32) {
+        const float4* crow = reinterpret_cast<const float4*>(C + (size_t)r * a.CS);
+        float acc = 0.f;
+        for (int c4 = 0; c4 < a.CS / 4; ++c4) {
+          const float4 cw = __ldg(crow + c4);
+          const float cv[4] = {cw.x, cw.y, cw.z, cw.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = 4 * c4 + e;
+            if (c < 2 * a.p) {
+              const int i = base + (c < a.p ? c : c - a.p);
+              acc = fmaf(cv[e], c < a.p ? xl[HX + i] : xh[HX + i], acc);
+            }
+          }
+        }
+        sCorr[side * a.K + r] = acc;
+      }
+    }
+    __syncthreads();
+
+    // (B) v[16 u .. 16 u + 16) = T s, corrections, bits 0-3
+    {
+      constexpr int BI = BS;
+      const int i0 = BI * tid;
+      const int j0 = HS + i0 - PM + 1 - G::OFFB;        // multiple of 4
+      float ws[G::NWB];
+#pragma unroll
+      for (int w = 0; w < G::NWB; w += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(sS + sp(j0 + w));
+        ws[w] = u.x; ws[w + 1] = u.y; ws[w + 2] = u.z; ws[w + 3] = u.w;
+      }
+      float v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        float acc = 0.f;
+#pragma unroll
+        for (int d = -(PM - 1); d <= PM - 1; ++d)
+          acc = fmaf(tp.tp[r % Q][d + PM - 1], ws[r / Q - d + PM - 1 + G::OFFB], acc);
+        v[r] = acc;
+      }
+      if (a.K) {
+        const int kb = a.K / 16;
+        int o = -1;
+        if (tid < kb) o = 16 * tid;
+        else if (tid >= NT - kb) o = a.K + 16 * (tid - (NT - kb));
+        if (o >= 0) {
+#pragma unroll
+          for (int r = 0; r < 16; ++r) v[r] += sCorr[o + r];
+        }
+      }
+      wht<16>(v);
+      float* dst = sV + vp(16 * tid);
+#pragma unroll
+      for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(dst + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
+    }
+    __syncthreads();
+    // (C) bits 4-7, then bits 8..L-1
+    pass_mid<NT>(sV, 0, tid);
+    __syncthreads();
+    if (gather) {
+      pass_high<NT>(sV, 0, tid);
+      __syncthreads();
+      const uint16_t* ps = reinterpret_cast<const uint16_t*>(sP + buf * G::PST) + (cr0 & 1);
+      float* y = out + b * io.m + cr0;
+      const int cnt = cr1 - cr0;
+      for (int j = tid; j < cnt; j += NT) y[j] = sV[vp(ps[j])];
+    } else {
+      // the last pass writes the natural-order line straight to global memory
+      float* dst = out + b * io.out_batch + (int64_t)l * io.out_stride;
+      constexpr int RH = N / 256;
+#pragma unroll
+      for (int c = tid; c < 256; c += NT) {
+        const int e0 = high_pencil(c);
+        float v[RH];
+#pragma unroll
+        for (int i = 0; i < RH; ++i) v[i] = sV[vp(e0 + 256 * i)];
+        wht<RH>(v);
+#pragma unroll
+        for (int i = 0; i < RH; ++i) dst[e0 + 256 * i] = v[i];
+      }
+    }
+    __syncthreads();
+    cr0 = xr0;
+    cr1 = xr1;
+    xr0 = yr0;
+    xr1 = yr1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+template <int PM, int Q, int NT>
+__global__ void __launch_bounds__(NT, 2) k_f32_adj(const float* __restrict__ in, float* __restrict__ out, Args a,
+                                                   Taps<PM, Q> tp, LineIO io, int total) {
+  using G = Geom<PM, Q, NT>;
+  constexpr int N = G::N, M = G::M, n0 = G::n0, BS = G::BS, BL = G::BL, HS = G::HS, VH = G::VH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool scat = io.mode == 1;
+  // mode 0: two staged Walsh lines, transformed in place; mode 1: one Walsh
+  // line, two staged sample buffers and position buffers
+  float* sV0 = reinterpret_cast<float*>(smem_raw);
+  float* sS = sV0 + (scat ? 1 : 2) * G::VLa;
+  float* sCorr = sS + G::SL;                                      // 4p (VMP)
+  float* sY = sCorr + up4(4 * a.p);                               // 2 x N (mode 1)
+  uint32_t* sP = reinterpret_cast<uint32_t*>(sY + (scat ? 2 * N : 0));   // 2 x PST (mode 1)
+
+  for (int i = tid; i < (scat ? 1 : 2) * G::VLa; i += NT) sV0[i] = 0.f;
+  for (int i = tid; i < G::SL; i += NT) sS[i] = 0.f;
+  __syncthreads();
+
+  auto issue_in = [&](int ln, int bi, int r0, int r1) {
+    const int l = ln % io.lines;
+    const int64_t b = ln / io.lines;
+    if (!scat) {
+      const float* src = in + b * io.in_batch + (int64_t)l * io.in_stride;
+      float* dst = sV0 + bi * G::VLa;
+      for (int e4 = tid; e4 < N / 4; e4 += NT) cp16(dst + vp(VH + 4 * e4), src + 4 * e4);
+    } else {
+      const float* y = in + b * io.m;
+      float* dst = sY + bi * N;
+      for (int j = r0 + tid; j < r1; j += NT) cp4(dst + (j - r0), y + j);
+      issue_pos(io, r0, r1, sP + bi * G::PST, tid, NT);
+    }
+  };
+
+  pdl_trigger();
+  pdl_wait();
+  const int G0 = gridDim.x;
+  int line = blockIdx.x;
+  int cr0 = 0, cr1 = 0, xr0 = 0, xr1 = 0;
+  if (line < total) {
+    if (scat) row_range(io, line % io.lines, cr0, cr1);
+    issue_in(line, 0, cr0, cr1);
+  }
+  cp_commit();
+  if (scat && line + G0 < total) row_range(io, (line + G0) % io.lines, xr0, xr1);
+
+  for (int buf = 0; line < total; line += G0, buf ^= 1) {
+    const int nxt = line + G0;
+    if (nxt < total) issue_in(nxt, buf ^ 1, xr0, xr1);
+    cp_commit();
+    int yr0 = 0, yr1 = 0;
+    if (scat && nxt + G0 < total) row_range(io, (nxt + G0) % io.lines, yr0, yr1);
+    cp_wait1();
+    __syncthreads();
+    const int l = line % io.lines;
+    const int64_t b = line / io.lines;
+    float* sV = sV0 + (scat ? 0 : buf * G::VLa);
+    if (scat) {
+      // zero the line, then scatter the staged samples to their natural positions
+      for (int k4 = tid; k4 < N / 4; k4 += NT) *reinterpret_cast<float4*>(sV + vp(VH + 4 * k4)) = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncthreads();
+      const uint16_t* ps = reinterpret_cast<const uint16_t*>(sP + buf * G::PST) + (cr0 & 1);
+      const float* ys = sY + buf * N;
+      const int cnt = cr1 - cr0;
+      for (int j = tid; j < cnt; j += NT) sV[vp(VH + ps[j])] = ys[j];
+      __syncthreads();
+    }
+    // Walsh stages (they commute): bits 8.., bits 4-7, then 0-3 in registers
+    pass_high<NT>(sV, VH, tid);
+    __syncthreads();
+    pass_mid<NT>(sV, VH, tid);
+    __syncthreads();
+    {
+      float v[16];
+      float* src = sV + vp(VH + 16 * tid);
+#pragma unroll
+      for (int r = 0; r < 16; r += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(src + r);
+        v[r] = u.x; v[r + 1] = u.y; v[r + 2] = u.z; v[r + 3] = u.w;
+      }
+      wht<16>(v);
+#pragma unroll
+      for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(src + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
+      if (a.per) {   // wrapped copies in the halos
+        const int k0 = 16 * tid;
+        if (k0 < VH) {
+          float* h = sV + vp(VH + N + k0);
+#pragma unroll
+          for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(h + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
+        }
+        if (k0 >= N - VH) {
+          float* h = sV + vp(VH + k0 - N);
+#pragma unroll
+          for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(h + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
+        }
+      }
+    }
+    __syncthreads();
+    // VMP: C^T on the first / last K transformed samples (warp 0 / last warp)
+    if (a.K && (warp == 0 || warp == NT / 32 - 1)) {
+      const int side = warp == 0 ? 0 : 1;
+      const float* C = a.C + (size_t)side * a.K * a.CS;
+      const int kbase = side == 0 ? 0 : N - a.K;
+      const int half = a.K / 2;
+      // two lanes per output column; every lane runs every round (full-warp shuffle)
+      for (int t0 = 0; t0 < 4 * a.p; t0 += 32) {
+        const int t = t0 + lane;
+        const bool act = t < 4 * a.p;
+        const int c = t >> 1, part = t & 1;
+        float acc = 0.f;
+        if (act)
+          for (int k = part * half; k < (part + 1) * half; ++k)
+            acc = fmaf(__ldg(C + (size_t)k * a.CS + c), sV[vp(VH + kbase + k)], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (act && part == 0) sCorr[side * 2 * a.p + c] = acc;
+      }
+    }
+    // s[BS u .. BS u + BS) = T^T v
+    {
+      const int m0 = BS * tid;
+      const int e0 = Q * m0 - Q * (PM - 1) - G::OFFT;     // multiple of 4
+      float wv[G::NWT];
+#pragma unroll
+      for (int w = 0; w < G::NWT; w += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(sV + vp(VH + e0 + w));
+        wv[w] = u.x; wv[w + 1] = u.y; wv[w + 2] = u.z; wv[w + 3] = u.w;
+      }
+      float s[BS];
+#pragma unroll
+      for (int bb = 0; bb < BS; ++bb) {
+        float acc = 0.f;
+#pragma unroll
+        for (int d = -(PM - 1); d <= PM - 1; ++d)
+#pragma unroll
+          for (int f = 0; f < Q; ++f) acc = fmaf(tp.tp[f][d + PM - 1], wv[Q * (bb + d + PM - 1) + f + G::OFFT], acc);
+        s[bb] = acc;
+      }
+#pragma unroll
+      for (int j = 0; j < BS; j += 4)
+        *reinterpret_cast<float4*>(sS + sp(HS + m0 + j)) = make_float4(s[j], s[j + 1], s[j + 2], s[j + 3]);
+      if (a.per) {
+#pragma unroll
+        for (int j = 0; j < BS; ++j) {
+          const int m = m0 + j;
+          if (m < HS) sS[sp(HS + M + m)] = s[j];
+          if (m >= M - HS) sS[sp(HS + m - M)] = s[j];
+        }
+      }
+    }
+    __syncthreads();
+    // analysis: lo, hi [BL u .. BL u + BL), plus the VMP edge corrections
+    {
+      const int i0 = BL * tid;
+      const int j0 = HS + 2 * i0 - PM - G::OFFA;        // multiple of 4
+      float ws[G::NWA];
+#pragma unroll
+      for (int w = 0; w < G::NWA; w += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(sS + sp(j0 + w));
+        ws[w] = u.x; ws[w + 1] = u.y; ws[w + 2] = u.z; ws[w + 3] = u.w;
+      }
+      float lo[BL], hi[BL];
+#pragma unroll
+      for (int bb = 0; bb < BL; ++bb) {
+        float x = 0.f, y = 0.f;
+#pragma unroll
+        for (int d = -PM / 2; d <= PM / 2; ++d)
+#pragma unroll
+          for (int f = 0; f < 2; ++f) {
+            const float sv = ws[2 * (bb + d) + f + PM + G::OFFA];
+            x = fmaf(tp.hp[f][d + PM / 2], sv, x);
+            y = fmaf(tp.gp[f][d + PM / 2], sv, y);
+          }
+        lo[bb] = x;
+        hi[bb] = y;
+      }
+      if (a.K) {
+#pragma unroll
+        for (int bb = 0; bb < BL; ++bb) {
+          const int i = i0 + bb;
+          if (i < a.p) {
+            lo[bb] += sCorr[i];
+            hi[bb] += sCorr[a.p + i];
+          } else if (i >= n0 - a.p) {
+            const int e = i - (n0 - a.p);
+            lo[bb] += sCorr[2 * a.p + e];
+            hi[bb] += sCorr[3 * a.p + e];
+          }
+        }
+      }
+      const int drow = io.seq_rows ? seqrow(l, a.L) : l;
+      float* dst = out + b * io.out_batch + (int64_t)drow * io.out_stride;
+      if constexpr (BL == 4) {
+        *reinterpret_cast<float4*>(dst + i0) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        *reinterpret_cast<float4*>(dst + n0 + i0) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      } else {
+        *reinterpret_cast<float2*>(dst + i0) = make_float2(lo[0], lo[1]);
+        *reinterpret_cast<float2*>(dst + n0 + i0) = make_float2(hi[0], hi[1]);
+      }
+    }
+    __syncthreads();
+    cr0 = xr0;
+    cr1 = xr1;
+    xr0 = yr0;
+    xr1 = yr1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <int PM, int Q>
+Taps<PM, Q> make_taps(const Plan& P) {
+  Taps<PM, Q> t;
+  std::fill(&t.hp[0][0], &t.hp[0][0] + 2 * (PM + 1), 0.f);
+  std::fill(&t.gp[0][0], &t.gp[0][0] + 2 * (PM + 1), 0.f);
+  std::fill(&t.tp[0][0], &t.tp[0][0] + Q * (2 * PM - 1), 0.f);
+  const int p = P.p;
+  const double sc = std::exp2(-0.5 * P.R);
+  for (int f = 0; f < 2; ++f)
+    for (int d = -PM / 2; d <= PM / 2; ++d) {
+      const int l = 2 * d + f;
+      if (l >= -p + 1 && l <= p) {
+        t.hp[f][d + PM / 2] = (float)P.h[l + p - 1];
+        t.gp[f][d + PM / 2] = (float)P.g[l + p - 1];
+      }
+    }
+  for (int f = 0; f < Q; ++f)
+    for (int d = -(PM - 1); d <= PM - 1; ++d)
+      if (d >= -(p - 1) && d <= p - 1) t.tp[f][d + PM - 1] = (float)(sc * P.taps[Q * d + f + (p - 1) * Q]);
+  return t;
+}
+
+template <int PM, int Q, int NT>
+size_t smem_fwd(const Plan& P, bool gather) {
+  using G = Geom<PM, Q, NT>;
+  return sizeof(float) * ((size_t)G::VLf + G::SL + 2 * G::XL + up4(2 * P.f32.K)) +
+         (gather ? sizeof(uint32_t) * 2 * (size_t)G::PST : 0);
+}
+
+template <int PM, int Q, int NT>
+size_t smem_adj(const Plan& P, bool scat) {
+  using G = Geom<PM, Q, NT>;
+  return sizeof(float) * ((size_t)(scat ? 1 : 2) * G::VLa + G::SL + up4(4 * P.p)) +
+         (scat ? sizeof(float) * 2 * (size_t)G::N + sizeof(uint32_t) * 2 * (size_t)G::PST : 0);
+}
+
+template <typename K>
+int persistent_grid(K kernel, int nt, size_t smem, int total) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, nt, smem);
+  return std::max(1, std::min(total, std::max(per, 1) * nsm));
+}
+
+template <int PM, int Q, int NT>
+cudaError_t go(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total, cudaStream_t s) {
+  Args a{};
+  a.C = (const float*)P.d_f32;
+  a.K = P.f32.K;
+  a.CS = P.f32.CS;
+  a.p = P.p;
+  a.per = P.bd == UW_BOUNDARY_PERIODIC;
+  int L = 0;
+  while ((1 << L) < P.N) ++L;
+  a.L = L;
+  const Taps<PM, Q> t = make_taps<PM, Q>(P);
+  if (fwd) {
+    const size_t sm = smem_fwd<PM, Q, NT>(P, io.mode == 1);
+    auto kern = k_f32_fwd<PM, Q, NT>;
+    set_smem_limit((const void*)kern);
+    return launch_pdl(kern, dim3(persistent_grid(kern, NT, sm, total)), dim3(NT), sm, s, in, out, a, t, io, total);
+  }
+  const size_t sm = smem_adj<PM, Q, NT>(P, io.mode == 1);
+  auto kern = k_f32_adj<PM, Q, NT>;
+  set_smem_limit((const void*)kern);
+  return launch_pdl(kern, dim3(persistent_grid(kern, NT, sm, total)), dim3(NT), sm, s, in, out, a, t, io, total);
+}
+
+template <int PM, int NT>
+cudaError_t go_q(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total, cudaStream_t s) {
+  if (P.Q == 2) return go<PM, 2, NT>(fwd, P, in, out, io, total, s);
+  return go<PM, 4, NT>(fwd, P, in, out, io, total, s);
+}
+
+template <int NT>
+cudaError_t go_nt(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total, cudaStream_t s) {
+  if (P.p <= 4) return go_q<4, NT>(fwd, P, in, out, io, total, s);
+  if (P.p <= 8) return go_q<8, NT>(fwd, P, in, out, io, total, s);
+  return go_q<10, NT>(fwd, P, in, out, io, total, s);
+}
+
+}  // namespace f32k
+
+bool f32_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd) {
+  if (!P.f32.ok || io.jlev != P.R - 1) return false;
+  if (P.N != 2048 && P.N != 4096) return false;
+  if (P.Q != 2 && P.Q != 4) return false;
+  if (P.bd != UW_BOUNDARY_PERIODIC && (!P.d_f32 || P.f32.K == 0)) return false;
+  const int NT = P.N / 16;
+  if (P.f32.K / 16 > NT / 2) return false;
+  if (P.M / 2 < 16) return false;
+  if (io.mode == 1 && !io.pos) return false;
+  auto al16 = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+  if (fwd) {
+    if (!al16(in) || io.in_stride % 4 || io.in_batch % 4) return false;
+    if (io.mode == 0 && (!al16(out) || io.out_stride % 4 || io.out_batch % 4)) return false;
+  } else {
+    if (io.mode == 0 && (!al16(in) || io.in_stride % 4 || io.in_batch % 4)) return false;
+    if (!al16(out) || io.out_stride % 4 || io.out_batch % 4) return false;
+  }
+  return true;
+}
+
+cudaError_t f32_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
+                       cudaStream_t s) {
+  if (P.N == 4096) return f32k::go_nt<256>(fwd, P, in, out, io, total, s);
+  return f32k::go_nt<128>(fwd, P, in, out, io, total, s);
+}
+
+}  // namespace uw

@@ -345,6 +345,11 @@ bool tc_eligible(const Plan& P, const LineIO& io, const void* in, const void* ou
 cudaError_t tc_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
                       cudaStream_t s);
 
+// kernels_f32.cu: persistent FP32 line operators (last level, N = 2048 / 4096)
+bool f32_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd);
+cudaError_t f32_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
+                       cudaStream_t s);
+
 // kernels_line.cu: register-blocked FP32 line operators
 bool line2_eligible(const Plan& P);
 cudaError_t line2_launch(bool fwd, const Plan& P, const Geo& G, const float* in, float* out, const LineIO& io,

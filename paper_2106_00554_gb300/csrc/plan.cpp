@@ -771,6 +771,8 @@ void uw_plan_destroy(uw_plan* P) {
   cudaFree(P->d_work);
   cudaFree(P->d_stage);
   cudaFree(P->d_tc);
+  cudaFree(P->d_f32);
+  cudaFree(P->d_sync);
   cudaFree(P->d_pos);
   delete P;
 }

@@ -150,6 +150,33 @@ struct Exact {
       hi[m] = b;
     }
   }
+  // The interior formulas applied to the whole line with zero padding
+  // beyond its ends (what the FP32 line kernels compute before their edge
+  // corrections): synthesis with h, g for every coefficient index in
+  // [0, n0), T with the taps for every s index in [0, M).
+  void syn_int0(const std::vector<double>& lo, const std::vector<double>& hi, std::vector<double>& s) const {
+    s.assign(M, 0.0);
+    for (int k = 0; k < M; ++k) {
+      double acc = 0;
+      for (int l = -p + 1; l <= p; ++l) {
+        const int km = k - l;
+        if (km & 1) continue;
+        const int i = km / 2;
+        if (i < 0 || i >= n0) continue;
+        acc += P.h[l + p - 1] * lo[i] + P.g[l + p - 1] * hi[i];
+      }
+      s[k] = acc;
+    }
+  }
+  void up_int0(const std::vector<double>& s, std::vector<double>& v) const {
+    v.assign(N, 0.0);
+    for (int k = 0; k < N; ++k) {
+      double acc = 0;
+      for (int m = ceildiv(k - (p * Q - 1), Q); m <= floordiv(k - tmin, Q); ++m)
+        if (m >= 0 && m < M) acc += P.taps[k - Q * m - tmin] * s[m];
+      v[k] = sc * acc;
+    }
+  }
   // interior entry of the line matrix: d v[k] / d lo[i] (hi = false) or
   // d v[k] / d hi[i] (hi = true), any integers k, i (shift invariant)
   double interior(int k, int i, bool hi) const {
@@ -351,6 +378,79 @@ void build_tc(Plan& P, std::vector<uint32_t>& words) {
   }
   G.words = (int64_t)words.size();
   G.ok = 1;
+}
+
+// Edge corrections of the FP32 line operators: C = E_exact - E_int0 on the
+// columns of the p lo and p hi coefficients at each end, where E maps the
+// coefficient line to v = T Syn x.  Every other column of the difference is
+// zero (an interior coefficient reaches only interior s values through the
+// interior filters, Sec. 3.2, and those meet only interior taps, Sec. 4.1);
+// the construction checks that on the next columns and finds the rows K
+// where the difference lives.
+void build_f32(Plan& P, std::vector<float>& out) {
+  out.clear();
+  F32Geo& F = P.f32;
+  F = F32Geo{};
+  const int p = P.p, n0 = P.M / 2, N = P.N;
+  if (P.bd == UW_BOUNDARY_PERIODIC) {
+    F.ok = 1;
+    return;
+  }
+  const int extra = 4;                 // columns past the edge that must show no difference
+  const int Wc = p + extra;
+  if (n0 < 2 * Wc + 8) return;
+  Exact X(P);
+  std::vector<double> lo(n0), hi(n0), s, ve, vi;
+  // D[side][col][k]: col < Wc lo columns, then Wc hi columns
+  std::vector<std::vector<std::vector<double>>> D(2, std::vector<std::vector<double>>(2 * Wc));
+  double dmax = 0;
+  for (int side = 0; side < 2; ++side)
+    for (int c = 0; c < 2 * Wc; ++c) {
+      std::fill(lo.begin(), lo.end(), 0.0);
+      std::fill(hi.begin(), hi.end(), 0.0);
+      const int i = side == 0 ? c % Wc : n0 - 1 - (c % Wc);
+      (c < Wc ? lo : hi)[i] = 1.0;
+      X.syn(lo, hi, s);
+      X.up(s, ve);
+      X.syn_int0(lo, hi, s);
+      X.up_int0(s, vi);
+      auto& d = D[side][c];
+      d.resize(N);
+      for (int k = 0; k < N; ++k) {
+        d[k] = ve[k] - vi[k];
+        dmax = std::max(dmax, std::fabs(d[k]));
+      }
+    }
+  if (dmax == 0) return;
+  const double tol = 1e-12 * dmax;
+  int K = 0;
+  for (int side = 0; side < 2; ++side)
+    for (int c = 0; c < 2 * Wc; ++c) {
+      const bool edge_col = (c % Wc) < p;
+      for (int k = 0; k < N; ++k) {
+        const double a = std::fabs(D[side][c][k]);
+        if (a <= tol) continue;
+        if (!edge_col) return;          // a difference outside the edge columns: not this structure
+        const int r = side == 0 ? k : N - 1 - k;
+        K = std::max(K, r + 1);
+      }
+    }
+  K = (K + 15) / 16 * 16;
+  if (K == 0 || 2 * K > N) return;
+  F.K = K;
+  F.CS = (2 * p + 3) / 4 * 4;
+  out.assign((size_t)2 * K * F.CS, 0.f);
+  for (int side = 0; side < 2; ++side)
+    for (int r = 0; r < K; ++r)
+      for (int c = 0; c < 2 * p; ++c) {
+        // columns: lo[0..p), hi[0..p) on the left; lo[n0-p..n0), hi[n0-p..n0) on the right
+        const int e = c % p, half = c / p;
+        const int col = side == 0 ? half * Wc + e : half * Wc + (p - 1 - e);
+        const int k = side == 0 ? r : N - K + r;
+        out[((size_t)side * K + r) * F.CS + c] = (float)D[side][col][k];
+      }
+  F.words = (int64_t)out.size();
+  F.ok = 1;
 }
 
 }  // namespace uw

@@ -50,6 +50,22 @@ struct TcGeo {
   int64_t oAf = 0, oAa = 0, oEf = 0, oEa = 0, words = 0;
 };
 
+// Edge corrections of the FP32 line operators (kernels_f32.cu).  The kernels
+// apply the interior formulas of the last synthesis level and of T to the
+// whole line with zero padding beyond its ends; near a VMP boundary the exact
+// operator differs from that by a correction that reads only the p lo and p
+// hi coefficients at that end and reaches only the first / last K outputs of
+// T:  v_exact = v_interior + C x_edge.  C is K x 2p per side (rows v[0..K) on
+// the left, v[N-K..N) on the right; columns lo[0..p), hi[0..p) on the left,
+// lo[n0-p..n0), hi[n0-p..n0) on the right), rows padded to CS floats.  The
+// adjoint adds C^T applied to the transformed samples at each end.
+struct F32Geo {
+  int ok = 0;
+  int K = 0;       // corrected outputs of T per side (multiple of 16; 0 = periodic)
+  int CS = 0;      // row stride of C (>= 2p, multiple of 4)
+  int64_t words = 0;
+};
+
 struct Plan {
   int d = 1, R = 0, q = 0, p = 1, bd = 0, J0 = 0;
   int M = 1, N = 1;          // per dimension
@@ -79,6 +95,9 @@ struct Plan {
   Profiler* prof = nullptr;
   TcGeo tc;                      // split-BF16 line operators (tc.ok = 0: not eligible)
   void* d_tc = nullptr;
+  F32Geo f32;                    // FP32 line operators (f32.ok = 0: not eligible)
+  void* d_f32 = nullptr;         // [2][K][CS] floats (left, then right)
+  void* d_sync = nullptr;        // grid barrier of the fused coarse-level kernels
 };
 
 // plan.cpp
@@ -86,6 +105,9 @@ bool build_tables(Plan& P, std::string& err);
 // tc_plan.cpp: block matrices of the tensor-core line operators (host, FP64);
 // fills P.tc and the packed words to upload (empty if not eligible)
 void build_tc(Plan& P, std::vector<uint32_t>& words);
+// tc_plan.cpp: edge corrections of the FP32 line operators (host, FP64);
+// fills P.f32 and the floats to upload (empty if not eligible)
+void build_f32(Plan& P, std::vector<float>& out);
 // kernels.cu
 int upload_tables(Plan& P);
 int launch_forward(const Plan& P, int prec, const void* x, void* y, int batch, void* stream, int* nlaunch);

@@ -13,6 +13,10 @@
   ``checkpoint=True`` every iteration is recomputed during the backward pass
   instead of storing its products.
 * ``half_sq_dist(a, b)``: 1/2 ||a - b||^2 accumulated in FP64 (a loss).
+* ``cg_normal(plan, y, iters)``: generalised sampling (Sec. 1.2), the
+  least-squares fit min_x ||P_Omega U x - y||^2, by conjugate gradients on
+  the normal equations U^* P_Omega^* P_Omega U x = U^* P_Omega^* y (the paper
+  solves its least-squares problems with CG), inner products in FP64.
 
 Every arithmetic step runs in libuw's kernels; torch supplies tensors,
 streams and the autograd tape.
@@ -161,3 +165,44 @@ def fista(plan, y, lam, iters=100, tau=1.0, precision=None, checkpoint=True, x0=
         else:
             x, z = body(z, x, B, lam)
     return x
+
+
+def _axpby(alpha, a, beta, b, out):
+    _lib.uw_axpby(_prec(a), a.numel(), float(alpha), a.data_ptr(), float(beta),
+                  b.data_ptr() if b is not None else None, out.data_ptr(), _stream())
+
+
+def cg_normal(plan, y, iters=50, tol=0.0, precision=None, x0=None):
+    """Conjugate gradients for min_x ||P_Omega U x - y||^2 (generalised
+    sampling, Sec. 1.2): the operator A = U^* P_Omega^* P_Omega U is
+    symmetric positive semi-definite, so CG on A x = U^* P_Omega^* y converges
+    to the least-squares solution (on the range of A^*).  Every product is a
+    library call; the inner products are FP64 device reductions (uw_dot) and
+    the vector updates uw_axpby.  Stops after `iters` iterations or when
+    ||r|| <= tol ||b||.  Returns (x, number of iterations, ||r|| / ||b||)."""
+    shape = (plan.M,) * plan.d
+    b = plan.adjoint(y.contiguous(), precision=precision)
+    x = torch.zeros(shape, dtype=y.dtype, device=y.device) if x0 is None else x0.clone()
+    if x0 is None:
+        r = b.clone()
+    else:
+        r = torch.empty_like(b)
+        _axpby(1.0, b, -1.0, plan.adjoint(plan.forward(x, precision=precision), precision=precision), r)
+    bb = float(dot64(b, b))
+    rr = float(dot64(r, r))
+    p = r.clone()
+    k = 0
+    while k < iters and bb > 0 and rr > (tol * tol) * bb:
+        Ap = plan.adjoint(plan.forward(p, precision=precision), precision=precision)
+        pAp = float(dot64(p, Ap))
+        if pAp <= 0:
+            break
+        alpha = rr / pAp
+        x1, r1, p1 = torch.empty_like(x), torch.empty_like(r), torch.empty_like(p)
+        _axpby(1.0, x, alpha, p, x1)
+        _axpby(1.0, r, -alpha, Ap, r1)
+        rr_new = float(dot64(r1, r1))
+        _axpby(1.0, r1, rr_new / rr, p, p1)
+        x, r, p, rr = x1, r1, p1, rr_new
+        k += 1
+    return x, k, (rr / bb) ** 0.5 if bb > 0 else 0.0

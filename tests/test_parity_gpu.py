@@ -351,3 +351,59 @@ def test_dot_product_2d_fp64():
     a = np.dot(run_fwd(plan, x, F64), y)
     b = np.sum(x * run_adj(plan, y, F64))
     assert abs(a - b) < 1e-12 * abs(a)
+
+
+F32_LINE_CASES = [(1, PERIODIC, 10, 1), (2, VMP, 10, 1), (3, VMP, 9, 2), (5, PERIODIC, 9, 2), (8, VMP, 10, 1),
+                  (9, VMP, 9, 2), (10, PERIODIC, 10, 1), (10, VMP, 10, 1), (4, VMP, 10, 2), (7, PERIODIC, 10, 2)]
+
+
+@pytest.mark.parametrize("p,bd,R,q", F32_LINE_CASES)
+def test_fp32_persistent_line_kernels(p, bd, R, q):
+    """UW_F32 on lines of N = 2048 and 4096 samples: the persistent FP32 line
+    operators (interior formulas with zero or wrapped halos, VMP edges as
+    small corrections) against the dense oracle, both boundary types, q = 1
+    and 2, batch 2, natural-order and sampled passes."""
+    from paper_2106_00554_gb300 import _lib
+    rng = np.random.default_rng(4000 + 10 * p + bd + q)
+    J0 = W.default_J0(p)
+    M, N = 2 ** R, 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.2)
+    plan = Plan(2, R, q, p, bd, omega=omega, max_batch=2)
+    G = dense.G1d(R, q, p, bd)
+    x = np.stack([inputs.coeffs_2d(rng, R, J0, 1.0) for _ in range(2)])
+    y = rng.standard_normal((2, omega.size))
+    want_y = dense.forward2d(x, R, q, p, bd, J0, omega, G=G)
+    want_x = dense.adjoint2d(y, R, q, p, bd, J0, omega, G=G)
+    _lib.uw_plan_profile(plan._h, True)
+    got_y = run_fwd(plan, x, F32)
+    got_x = run_adj(plan, y, F32)
+    names = _kernel_names(plan)
+    _lib.uw_plan_profile(plan._h, False)
+    assert rel(got_y, want_y) < TOL[F32]
+    assert rel(got_x, want_x) < TOL[F32]
+    assert sum(n.endswith("_f32") for n in names) == 4, names
+
+
+def test_coarse_barrier_gives_up_and_reports(monkeypatch):
+    """The coarse 2D levels run as one cooperative launch whose CTAs meet at
+    bounded grid barriers.  With a spin limit of zero every wait gives up at
+    once: the call returns (no hang), uw_plan_device_status reports
+    UW_ERR_TIMEOUT and resets the barrier, and the next call with the default
+    limit is correct again."""
+    from paper_2106_00554_gb300 import _lib
+    UW_OK, UW_ERR_TIMEOUT = 0, 5
+    rng = np.random.default_rng(11)
+    R, q, p = 8, 1, 2
+    N = 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.3)
+    plan = Plan(2, R, q, p, VMP, omega=omega)
+    assert R - 1 - plan.J0 >= 2
+    x = inputs.coeffs_2d(rng, R, plan.J0, 1.0)
+    want = dense.forward2d(x, R, q, p, VMP, plan.J0, omega)
+    assert _lib.uw_plan_device_status(plan._h) == UW_OK
+    monkeypatch.setenv("UW_BARRIER_SPIN_LIMIT", "0")
+    run_fwd(plan, x, F32)
+    assert _lib.uw_plan_device_status(plan._h) == UW_ERR_TIMEOUT
+    monkeypatch.delenv("UW_BARRIER_SPIN_LIMIT")
+    assert rel(run_fwd(plan, x, F32), want) < TOL[F32]
+    assert _lib.uw_plan_device_status(plan._h) == UW_OK

@@ -177,3 +177,46 @@ def test_fista_reduces_the_objective_on_the_benchmark_shape_split_bf16():
     assert objective(x) < objective(torch.zeros_like(xt_d))
     assert torch.isfinite(yv.grad).all() and float(yv.grad.abs().max()) > 0
     assert np.isfinite(float(lt.grad))
+
+
+def test_generalised_sampling_example2_db2():
+    """Generalised sampling of the paper's Example 2 (Sec. 6) on the GPU:
+    f(t1, t2) = cos(3 pi t1 / 2) sin(3 pi t2) from its 32 x 32 first Walsh
+    samples, DB2 with VMP boundaries at M = 16 x 16 (R = 4, q = 1), solved by
+    CG on the normal equations through the library's products.  The solution
+    matches the oracle's least-squares fit, and its relative L2 error matches
+    the 0.0518 the paper prints (the oracle pins the same number on the CPU)."""
+    scipy_integrate = pytest.importorskip("scipy.integrate")
+    from oracle import dense, walsh, wavelets as W
+    from paper_2106_00554_gb300 import F64, VMP, Plan, solvers
+
+    quad = scipy_integrate.quad
+    f1 = lambda t: np.cos(1.5 * np.pi * t)
+    f2 = lambda t: np.sin(3.0 * np.pi * t)
+
+    def cells(f, n):
+        return np.array([quad(f, k / n, (k + 1) / n)[0] for k in range(n)])
+
+    R, q, p = 4, 1, 2
+    N = 2 ** (R + q)
+    c1 = walsh.hadamard(N) @ cells(f1, N)
+    c2 = walsh.hadamard(N) @ cells(f2, N)
+    y = np.outer(c1, c2).reshape(-1)                  # all 32 x 32 samples, row-major sequency order
+    plan = Plan(2, R, q, p, VMP)
+    yd = torch.tensor(y, dtype=torch.float64, device="cuda")
+    x, iters, res = solvers.cg_normal(plan, yd, iters=200, tol=1e-13)
+    x = x.cpu().numpy()
+    # the oracle's least-squares fit in the Mallat wavelet basis
+    A = dense.U1d_scaling(R, q, p, VMP)
+    z1 = np.linalg.lstsq(A, c1, rcond=None)[0]
+    z2 = np.linalg.lstsq(A, c2, rcond=None)[0]
+    want = W.dwt2d(np.outer(z1, z2), plan.J0, p, VMP)
+    assert np.linalg.norm(x - want) < 1e-9 * np.linalg.norm(want), (iters, res)
+    # relative L2 error of the reconstruction: <f, r> from Parseval on 2^12 Walsh functions
+    Af = dense.U1d_scaling(R, 12 - R, p, VMP)
+    fr1 = (walsh.hadamard(4096) @ cells(f1, 4096)) @ Af
+    fr2 = (walsh.hadamard(4096) @ cells(f2, 4096)) @ Af
+    S = W.idwt2d(x, plan.J0, p, VMP)                 # scaling-basis coefficients of the fit
+    n2 = quad(lambda t: f1(t) ** 2, 0, 1)[0] * quad(lambda t: f2(t) ** 2, 0, 1)[0]
+    err = np.sqrt((n2 - 2 * fr1 @ S @ fr2 + np.sum(S ** 2)) / n2)
+    assert abs(err - 0.0518) < 5e-4, err
