@@ -243,9 +243,9 @@ int uw_plan_profile_read(uw_plan* plan, int i, char* name, int cap, double* tota
  * plan's device) and reports whether a bounded device-side wait of the plan
  * gave up since the last query: the 2D products run all coarse wavelet levels
  * in one cooperative launch whose CTAs meet at grid barriers between levels;
- * each wait spins a bounded number of times (environment variable
- * UW_BARRIER_SPIN_LIMIT, default 2^22 polls of about 64 ns) and then records
- * the failure and returns.  Returns UW_OK, UW_ERR_TIMEOUT (the results of the
+ * each wait polls a bounded number of times (environment variable
+ * UW_BARRIER_SPIN_LIMIT, default 2^22 polls with a 32 ns sleep after each)
+ * and then records the failure and returns.  Returns UW_OK, UW_ERR_TIMEOUT (the results of the
  * calls since the last query are invalid; the barrier is reset for the next
  * call) or UW_ERR_CUDA (a CUDA error surfaced while synchronising).  Not part
  * of the paper: failure reporting of this implementation.

@@ -471,7 +471,7 @@ __device__ __forceinline__ void gather_window(T* dst, int rows, int cols, const 
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int r = r0 + a, c = c0 + lane + 32 * h;
-          v[a][h] = (r < rows && c < cols) ? __ldg(addr(r, c)) : T(0);
+          v[a][h] = (r < rows && c < cols) ? *addr(r, c) : T(0);
         }
 #pragma unroll
       for (int a = 0; a < RB; ++a)
@@ -556,7 +556,7 @@ __host__ __device__ inline int ana_tile(int n0) { return n0 >= 128 ? 16 : (n0 >=
 // LL from llsrc (leading dim ldll), details from x; output S_{j+1} to dst.
 // One TS x TS output tile `tile` of instance b; W is the CTA's shared window.
 template <typename T, int P>
-__device__ __forceinline__ void syn2d_tile(int tile, int64_t b, const T* __restrict__ llsrc, int64_t ldll,
+__device__ __forceinline__ void syn2d_tile(int tile, int64_t b, const T* llsrc, int64_t ldll,
                                            int64_t llb, const T* __restrict__ x, int M, T* __restrict__ dst,
                                            int64_t lddst, int64_t dstb, int j, int TS, const SmemTables<T>& st, T* W,
                                            const Geo& G, int tid, int nthr) {
@@ -625,8 +625,8 @@ __global__ void __launch_bounds__(256) k_syn2d_level(const T* __restrict__ llsrc
 // low-pass block to lldst (or to x when lldst is null), details to x.  One
 // tile of TS x TS coefficients per quadrant; S is the CTA's shared window.
 template <typename T, int P>
-__device__ __forceinline__ void ana2d_tile(int tile, int64_t b, const T* __restrict__ src, int64_t ldsrc,
-                                           int64_t srcb, T* __restrict__ x, int M, T* __restrict__ lldst,
+__device__ __forceinline__ void ana2d_tile(int tile, int64_t b, const T* src, int64_t ldsrc,
+                                           int64_t srcb, T* x, int M, T* lldst,
                                            int64_t ldll, int64_t llb, int j, int TS, const SmemTables<T>& st, T* S,
                                            const Geo& G, int tid, int nthr) {
   const int n0 = 1 << j, n1 = 2 * n0;
@@ -713,37 +713,57 @@ struct GridBarrier {
   unsigned int pad;
 };
 
+// relaxed polling load (no L1 invalidation per poll, which would evict the
+// data of the CTAs still working on the same SM); one acquire load after the
+// wait orders (and refreshes) what the CTA reads next
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-// returns false (in every thread of the CTA) if the wait gave up
+__device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;\n" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier: each CTA's thread 0 arrives with an acquire-release
+// increment (after the CTA barrier, so it releases the whole CTA's writes);
+// the last to arrive resets the count and bumps the generation with a
+// release; the others poll the generation with relaxed loads and finish with
+// one acquire load.  Returns false (in every thread of the CTA) if the wait
+// gave up.
 __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int nblocks, unsigned int limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned int g = ld_acquire_u32(&bar->gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+    const unsigned int g = ld_relaxed_u32(&bar->gen);
+    const unsigned int arrived = atom_add_acq_rel_u32(&bar->count, 1u) + 1u;
     if (arrived == nblocks) {
       atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
+      red_add_release_u32(&bar->gen, 1u);
     } else {
       unsigned int it = 0;
-      while (ld_acquire_u32(&bar->gen) == g) {
+      while (ld_relaxed_u32(&bar->gen) == g) {
         if (++it > limit) {
           atomicExch(&bar->err, 1u);
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
+      (void)ld_acquire_u32(&bar->gen);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -761,51 +781,467 @@ struct CoarseIO {
   int M, J0, nl, batch;
 };
 
-template <typename T, int P>
-__global__ void __launch_bounds__(256) k_syn2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, GridBarrier* bar,
+// ---------------------------------------------------------------------------
+// Register-window tiles of one coarse 2D level.  Both passes of a level use
+// the interior formulas (two-scale relations of Sec. 3.2) on windows padded
+// with zeros (VMP) or wrapped (periodic) at the ends; near a VMP boundary the
+// exact level differs from that by a level-independent correction D that
+// reads only the p lo and p hi coefficients at that end and reaches only the
+// first / last Lb outputs (host-built: build_coarse).  The analysis applies
+// the transposes.  Each thread computes several consecutive outputs from a
+// register window.
+// ---------------------------------------------------------------------------
+template <typename T, int PM>
+struct CTaps {
+  T hp[2][PM + 1];   // synthesis, polyphase: hp[f][d + PM/2] = h_{2d+f}
+  T gp[2][PM + 1];
+  T ha[2 * PM];      // analysis: ha[l + PM - 1] = h_l, l in [-PM+1, PM]
+  T ga[2 * PM];
+};
+
+__host__ __device__ constexpr int cup(int a, int b) { return (a + b - 1) / b * b; }
+
+// NW values from a 16-byte aligned shared address, 16-byte loads
+template <typename T, int NW>
+__device__ __forceinline__ void ld16(T (&w)[NW], const T* src) {
+  if constexpr (sizeof(T) == 4) {
+    static_assert(NW % 4 == 0, "float windows are loaded in fours");
+#pragma unroll
+    for (int i = 0; i < NW; i += 4) {
+      const float4 u = *reinterpret_cast<const float4*>(src + i);
+      w[i] = u.x; w[i + 1] = u.y; w[i + 2] = u.z; w[i + 3] = u.w;
+    }
+  } else {
+    static_assert(NW % 2 == 0, "double windows are loaded in pairs");
+#pragma unroll
+    for (int i = 0; i < NW; i += 2) {
+      const double2 u = *reinterpret_cast<const double2*>(src + i);
+      w[i] = u.x; w[i + 1] = u.y;
+    }
+  }
+}
+
+// synthesis tile geometry: TS x TS outputs of level j+1 from NR x NC windows
+// of the four subbands (NR = NC = TS/2 + PM)
+template <typename T, int PM, int TS>
+struct SynGeom {
+  static constexpr int VW = 16 / (int)sizeof(T);
+  static constexpr int NR = TS / 2 + PM;
+  static constexpr int NC = TS / 2 + PM;
+  static constexpr int NCP = 48;                      // row stride (rows 16 banks apart)
+  static constexpr int NWR = cup(4 + PM, VW);         // row-pass window
+  static constexpr int elems = 4 * NR * NCP + 2 * NR * TS;
+  static_assert(4 * (TS / 8 - 1) + NWR <= NCP, "row window exceeds the padded row");
+};
+
+// analysis tile geometry: TSA x TSA coefficients per quadrant from an
+// NR x NR window of level j+1 (NR = 2 TSA + 2 PM - 2)
+template <typename T, int PM, int TSA>
+struct AnaGeom {
+  static constexpr int VW = 16 / (int)sizeof(T);
+  static constexpr int NR = 2 * TSA + 2 * PM - 2;
+  static constexpr int NRP = NR + 1;                  // row stride of the input window
+  static constexpr int NWA = cup(2 * PM + 6, VW);     // row-pass window (2 PM + 6 used)
+  static constexpr int NCH = cup(8 * (TSA / 4 - 1) + NWA, VW);   // row stride of the column-pass result
+  static constexpr int HOFF = cup(NR * NRP, 4);       // the column-pass result starts 16-byte aligned
+  static constexpr int elems = HOFF + 2 * TSA * NCH;
+};
+
+template <typename T, int PM, int TS>
+__device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc, int64_t ldll,
+                                            int64_t llb, const T* __restrict__ x, int M, T* __restrict__ dst,
+                                            int64_t lddst, int64_t dstb, int j, const CTaps<T, PM>& ct, const T* Dl,
+                                            const T* Dr, int p, int Lb, bool per, T* smem, int tid, int nthr) {
+  using SG = SynGeom<T, PM, TS>;
+  constexpr int NR = SG::NR, NC = SG::NC, NCP = SG::NCP, NWR = SG::NWR;
+  const int n0 = 1 << j, n1 = 2 * n0;
+  const int tiles = n1 / TS;
+  const int r0 = (tile / tiles) * TS, c0 = (tile % tiles) * TS;
+  const int ir0 = (r0 >> 1) - PM / 2, ic0 = (c0 >> 1) - PM / 2;
+  T* W = smem;                    // [4][NR][NCP]: LL, D1, D2, D3 windows
+  T* H = W + 4 * NR * NCP;        // [2][NR][TS]: row-synthesised top (LL|D1) and bottom (D2|D3) halves
+  const T* xb = x + b * (int64_t)M * M;
+  const T* lb = llsrc + b * llb;
+  {
+    // every load of the window is issued before the first store (one round
+    // of memory latency); the kernels run 256 threads.  A thread takes the
+    // same (row, column) of the four subbands.
+    constexpr int TOT = NR * NC, CNT = (TOT + 255) / 256;
+    const T* base[4] = {lb, xb + n0, xb + (int64_t)n0 * M, xb + (int64_t)n0 * M + n0};
+    const int64_t ld[4] = {ldll, (int64_t)M, (int64_t)M, (int64_t)M};
+    T v[CNT][4];
+#pragma unroll
+    for (int u = 0; u < CNT; ++u) {
+      const int e = tid + u * 256;
+      const int i = e / NC, m = e - i * NC;
+      int gi = ir0 + i, gm = ic0 + m;
+      bool ok = e < TOT;
+      if (per) {
+        gi &= n0 - 1;
+        gm &= n0 - 1;
+      } else {
+        ok = ok && gi >= 0 && gi < n0 && gm >= 0 && gm < n0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[u][q] = ok ? base[q][gi * ld[q] + gm] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < CNT; ++u) {
+      const int e = tid + u * 256;
+      if (e < TOT) {
+        const int i = e / NC, m = e - i * NC;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) W[(q * NR + i) * NCP + m] = v[u][q];
+      }
+    }
+  }
+  __syncthreads();
+  // rows: H[h][i][8 g + e] from the lo (LL / D2) and hi (D1 / D3) windows
+  {
+    constexpr int GR = TS / 8;
+    for (int t = tid; t < 2 * NR * GR; t += nthr) {
+      const int h = t / (NR * GR), rem = t - h * (NR * GR), i = rem / GR, g = rem - i * GR;
+      const T* rlo = W + ((2 * h) * NR + i) * NCP;
+      const T* rhi = W + ((2 * h + 1) * NR + i) * NCP;
+      T wl[NWR], wh[NWR];
+      ld16(wl, rlo + 4 * g);
+      ld16(wh, rhi + 4 * g);
+      T o[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int f = e & 1, a2 = e >> 1;
+        T acc = T(0);
+#pragma unroll
+        for (int d = -PM / 2; d <= PM / 2; ++d) {
+          acc = fma(ct.hp[f][d + PM / 2], wl[a2 - d + PM / 2], acc);
+          acc = fma(ct.gp[f][d + PM / 2], wh[a2 - d + PM / 2], acc);
+        }
+        o[e] = acc;
+      }
+      if (!per) {
+        if (c0 == 0 && 8 * g < Lb) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int k = 8 * g + e;
+            if (k < Lb)
+              for (int c = 0; c < 2 * p; ++c)
+                o[e] = fma(Dl[k * 2 * p + c], c < p ? rlo[c + PM / 2] : rhi[c - p + PM / 2], o[e]);
+          }
+        }
+        if (c0 + TS == n1 && c0 + 8 * g + 8 > n1 - Lb) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int r = c0 + 8 * g + e - (n1 - Lb);
+            if (r >= 0)
+              for (int c = 0; c < 2 * p; ++c) {
+                const int m = n0 - p + (c < p ? c : c - p) - ic0;
+                o[e] = fma(Dr[r * 2 * p + c], c < p ? rlo[m] : rhi[m], o[e]);
+              }
+          }
+        }
+      }
+      T* hrow = H + (h * NR + i) * TS + 8 * g;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) hrow[e] = o[e];
+    }
+  }
+  __syncthreads();
+  // columns: output rows 4 g4 + e of column cc from the top (lo) and bottom (hi) halves of H
+  {
+    constexpr int GC = TS / 4;
+    for (int t = tid; t < TS * GC; t += nthr) {
+      const int cc = t % TS, g4 = t / TS;
+      T wl[2 + PM], wh[2 + PM];
+#pragma unroll
+      for (int w = 0; w < 2 + PM; ++w) {
+        wl[w] = H[(2 * g4 + w) * TS + cc];
+        wh[w] = H[(NR + 2 * g4 + w) * TS + cc];
+      }
+      T o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int f = e & 1, b2 = e >> 1;
+        T acc = T(0);
+#pragma unroll
+        for (int d = -PM / 2; d <= PM / 2; ++d) {
+          acc = fma(ct.hp[f][d + PM / 2], wl[b2 - d + PM / 2], acc);
+          acc = fma(ct.gp[f][d + PM / 2], wh[b2 - d + PM / 2], acc);
+        }
+        o[e] = acc;
+      }
+      if (!per) {
+        if (r0 == 0 && 4 * g4 < Lb) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = 4 * g4 + e;
+            if (k < Lb)
+              for (int c = 0; c < 2 * p; ++c)
+                o[e] = fma(Dl[k * 2 * p + c], H[((c < p ? 0 : NR) + (c < p ? c : c - p) + PM / 2) * TS + cc], o[e]);
+          }
+        }
+        if (r0 + TS == n1 && r0 + 4 * g4 + 4 > n1 - Lb) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int r = r0 + 4 * g4 + e - (n1 - Lb);
+            if (r >= 0)
+              for (int c = 0; c < 2 * p; ++c) {
+                const int m = n0 - p + (c < p ? c : c - p) - ir0;
+                o[e] = fma(Dr[r * 2 * p + c], H[((c < p ? 0 : NR) + m) * TS + cc], o[e]);
+              }
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) dst[b * dstb + (int64_t)(r0 + 4 * g4 + e) * lddst + c0 + cc] = o[e];
+    }
+  }
+}
+
+template <typename T, int PM, int TSA>
+__device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, int64_t ldsrc,
+                                            int64_t srcb, T* x, int M, T* lldst,
+                                            int64_t ldll, int64_t llb, int j, const CTaps<T, PM>& ct, const T* Dl,
+                                            const T* Dr, int p, int Lb, bool per, T* smem, int tid, int nthr) {
+  using AG = AnaGeom<T, PM, TSA>;
+  constexpr int NR = AG::NR, NRP = AG::NRP, NWA = AG::NWA, NCH = AG::NCH;
+  const int n0 = 1 << j, n1 = 2 * n0;
+  const int tiles = n0 / TSA;
+  const int m0 = (tile / tiles) * TSA, k0 = (tile % tiles) * TSA;
+  const int ir0 = 2 * m0 - PM + 1, ic0 = 2 * k0 - PM + 1;
+  T* S = smem;                    // [NR][NRP] window of level j+1
+  T* Hc = S + AG::HOFF;           // [2][TSA][NCH]: column analysis, lo then hi
+  const T* sb = src + b * srcb;
+  {
+    constexpr int TOT = NR * NR, CNT = (TOT + 255) / 256;
+    T v[CNT];
+#pragma unroll
+    for (int u = 0; u < CNT; ++u) {
+      const int e = tid + u * 256;
+      v[u] = T(0);
+      if (e < TOT) {
+        const int i = e / NR, c = e - i * NR;
+        int gi = ir0 + i, gc = ic0 + c;
+        bool ok = true;
+        if (per) {
+          gi &= n1 - 1;
+          gc &= n1 - 1;
+        } else {
+          ok = gi >= 0 && gi < n1 && gc >= 0 && gc < n1;
+        }
+        if (ok) v[u] = sb[(int64_t)gi * ldsrc + gc];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CNT; ++u) {
+      const int e = tid + u * 256;
+      if (e < TOT) {
+        const int i = e / NR, c = e - i * NR;
+        S[i * NRP + c] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  // columns: lo / hi rows 4 g + e of window column c
+  {
+    constexpr int GC = TSA / 4;
+    for (int t = tid; t < NR * GC; t += nthr) {
+      const int c = t % NR, g = t / NR;
+      T w[2 * PM + 6];
+#pragma unroll
+      for (int k = 0; k < 2 * PM + 6; ++k) w[k] = S[(8 * g + k) * NRP + c];
+      T lo[4], hi[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        T x0 = T(0), x1 = T(0);
+#pragma unroll
+        for (int l = -PM + 1; l <= PM; ++l) {
+          const T v = w[2 * e + l + PM - 1];
+          x0 = fma(ct.ha[l + PM - 1], v, x0);
+          x1 = fma(ct.ga[l + PM - 1], v, x1);
+        }
+        lo[e] = x0;
+        hi[e] = x1;
+      }
+      if (!per) {
+        if (m0 == 0 && 4 * g < p) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int mm = 4 * g + e;
+            if (mm < p)
+              for (int k = 0; k < Lb; ++k) {
+                const T v = S[(k - ir0) * NRP + c];
+                lo[e] = fma(Dl[k * 2 * p + mm], v, lo[e]);
+                hi[e] = fma(Dl[k * 2 * p + p + mm], v, hi[e]);
+              }
+          }
+        }
+        if (m0 + TSA == n0 && m0 + 4 * g + 4 > n0 - p) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int ee = m0 + 4 * g + e - (n0 - p);
+            if (ee >= 0)
+              for (int r = 0; r < Lb; ++r) {
+                const T v = S[(n1 - Lb + r - ir0) * NRP + c];
+                lo[e] = fma(Dr[r * 2 * p + ee], v, lo[e]);
+                hi[e] = fma(Dr[r * 2 * p + p + ee], v, hi[e]);
+              }
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        Hc[(4 * g + e) * NCH + c] = lo[e];
+        Hc[(TSA + 4 * g + e) * NCH + c] = hi[e];
+      }
+    }
+  }
+  __syncthreads();
+  // rows: lo / hi coefficients 4 g + e of each Hc row; quadrants
+  // (col lo, row lo) = LL, (col lo, row hi) = D1, (col hi, row lo) = D2, (col hi, row hi) = D3
+  {
+    constexpr int GR = TSA / 4;
+    T* xb = x + b * (int64_t)M * M;
+    for (int t = tid; t < 2 * TSA * GR; t += nthr) {
+      const int g = t % GR, row = t / GR;      // row < TSA: column-lo rows, else column-hi rows
+      const T* hr = Hc + row * NCH;
+      T w[NWA];
+      ld16(w, hr + 8 * g);
+      T lo[4], hi[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        T x0 = T(0), x1 = T(0);
+#pragma unroll
+        for (int l = -PM + 1; l <= PM; ++l) {
+          const T v = w[2 * e + l + PM - 1];
+          x0 = fma(ct.ha[l + PM - 1], v, x0);
+          x1 = fma(ct.ga[l + PM - 1], v, x1);
+        }
+        lo[e] = x0;
+        hi[e] = x1;
+      }
+      if (!per) {
+        if (k0 == 0 && 4 * g < p) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int kk = 4 * g + e;
+            if (kk < p)
+              for (int k = 0; k < Lb; ++k) {
+                const T v = hr[k - ic0];
+                lo[e] = fma(Dl[k * 2 * p + kk], v, lo[e]);
+                hi[e] = fma(Dl[k * 2 * p + p + kk], v, hi[e]);
+              }
+          }
+        }
+        if (k0 + TSA == n0 && k0 + 4 * g + 4 > n0 - p) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int ee = k0 + 4 * g + e - (n0 - p);
+            if (ee >= 0)
+              for (int r = 0; r < Lb; ++r) {
+                const T v = hr[n1 - Lb + r - ic0];
+                lo[e] = fma(Dr[r * 2 * p + ee], v, lo[e]);
+                hi[e] = fma(Dr[r * 2 * p + p + ee], v, hi[e]);
+              }
+          }
+        }
+      }
+      const int mm = row < TSA ? m0 + row : m0 + row - TSA;
+      const int kq = k0 + 4 * g;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (row < TSA) {
+          if (lldst) lldst[b * llb + (int64_t)mm * ldll + kq + e] = lo[e];
+          else xb[(int64_t)mm * M + kq + e] = lo[e];
+          xb[(int64_t)mm * M + n0 + kq + e] = hi[e];
+        } else {
+          xb[(int64_t)(n0 + mm) * M + kq + e] = lo[e];
+          xb[(int64_t)(n0 + mm) * M + n0 + kq + e] = hi[e];
+        }
+      }
+    }
+  }
+}
+
+// which tile code a level takes: the register-window tiles need TS <= n1
+// (synthesis) and TSA <= n0 (analysis); smaller levels take the generic tiles
+__host__ __device__ inline int syn_rw_ts(int n1) { return n1 >= 32 ? 32 : (n1 >= 16 ? 16 : 0); }
+__host__ __device__ inline int ana_rw_ts(int n0) { return n0 >= 16 ? 16 : (n0 >= 8 ? 8 : 0); }
+
+template <typename T, int PM>
+__global__ void __launch_bounds__(256) k_syn2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, const __grid_constant__ CTaps<T, PM> ct,
+                                                      const T* __restrict__ Dg, int rw, GridBarrier* bar,
                                                       unsigned int limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
-  const int off = stage_filters(tab, G, sm, st, tid, nthr);
+  int off = stage_filters(tab, G, sm, st, tid, nthr);
+  const bool per = G.bd == UW_BOUNDARY_PERIODIC;
+  const int nD = per ? 0 : 4 * G.Lb * G.p;
+  T* Dl = sm + off;
+  for (int i = tid; i < nD; i += nthr) Dl[i] = Dg[i];
+  const T* Dr = Dl + 2 * G.Lb * G.p;
+  off = cup(off + nD, 4);
   const int M = io.M, Mh = M / 2;
   const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
   for (int it = 0; it < io.nl; ++it) {
     const int j = io.J0 + it, n1 = 2 << j;
-    const int TS = syn_tile(n1), tiles = (n1 / TS) * (n1 / TS);
+    const int TR = rw ? syn_rw_ts(n1) : 0;
+    const int TS = TR ? TR : syn_tile(n1), tiles = (n1 / TS) * (n1 / TS);
     const T* src = it == 0 ? io.x : ((io.nl - it) % 2 == 0 ? io.XS : io.XS2);
     const int64_t ld = it == 0 ? M : Mh, sb = it == 0 ? MM : HH;
     T* dst = (io.nl - 1 - it) % 2 == 0 ? io.XS : io.XS2;
     for (int t = blockIdx.x; t < tiles * io.batch; t += gridDim.x) {
       __syncthreads();   // the previous tile's windows are no longer read
-      syn2d_tile<T, P>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, TS, st, sm + off, G, tid,
-                       nthr);
+      if (TR == 32)
+        syn_tile_rw<T, PM, 32>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, ct, Dl, Dr, G.p,
+                               G.Lb, per, sm + off, tid, nthr);
+      else if (TR == 16)
+        syn_tile_rw<T, PM, 16>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, ct, Dl, Dr, G.p,
+                               G.Lb, per, sm + off, tid, nthr);
+      else
+        syn2d_tile<T, 0>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, TS, st, sm + off, G,
+                         tid, nthr);
     }
     if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, limit)) return;
   }
 }
 
-template <typename T, int P>
-__global__ void __launch_bounds__(256) k_ana2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, GridBarrier* bar,
+template <typename T, int PM>
+__global__ void __launch_bounds__(256) k_ana2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, const __grid_constant__ CTaps<T, PM> ct,
+                                                      const T* __restrict__ Dg, int rw, GridBarrier* bar,
                                                       unsigned int limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
-  const int off = stage_filters(tab, G, sm, st, tid, nthr);
+  int off = stage_filters(tab, G, sm, st, tid, nthr);
+  const bool per = G.bd == UW_BOUNDARY_PERIODIC;
+  const int nD = per ? 0 : 4 * G.Lb * G.p;
+  T* Dl = sm + off;
+  for (int i = tid; i < nD; i += nthr) Dl[i] = Dg[i];
+  const T* Dr = Dl + 2 * G.Lb * G.p;
+  off = cup(off + nD, 4);
   const int M = io.M, Mh = M / 2;
   const int64_t HH = (int64_t)Mh * Mh;
   const int R = io.J0 + io.nl + 1;
   for (int it = 0; it < io.nl; ++it) {
     const int j = R - 2 - it, n0 = 1 << j;
-    const int TS = ana_tile(n0), tiles = (n0 / TS) * (n0 / TS);
+    const int TR = rw ? ana_rw_ts(n0) : 0;
+    const int TS = TR ? TR : ana_tile(n0), tiles = (n0 / TS) * (n0 / TS);
     const T* src = it % 2 == 0 ? io.XS : io.XS2;
     T* dst = it == io.nl - 1 ? nullptr : (it % 2 == 0 ? io.XS2 : io.XS);
     for (int t = blockIdx.x; t < tiles * io.batch; t += gridDim.x) {
       __syncthreads();
-      ana2d_tile<T, P>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, TS, st,
-                       sm + off, G, tid, nthr);
+      if (TR == 16)
+        ana_tile_rw<T, PM, 16>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, ct,
+                               Dl, Dr, G.p, G.Lb, per, sm + off, tid, nthr);
+      else if (TR == 8)
+        ana_tile_rw<T, PM, 8>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, ct,
+                              Dl, Dr, G.p, G.Lb, per, sm + off, tid, nthr);
+      else
+        ana2d_tile<T, 0>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, TS, st,
+                         sm + off, G, tid, nthr);
     }
     if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, limit)) return;
   }
@@ -946,6 +1382,25 @@ int upload_tables(Plan& P) {
   if (cudaMemset(P.d_sync, 0, sizeof(GridBarrier)) != cudaSuccess) {
     set_error(UW_ERR_CUDA, "barrier initialisation failed");
     return UW_ERR_CUDA;
+  }
+  {
+    std::vector<double> D;
+    P.coarse_ok = build_coarse(P, D) ? 1 : 0;
+    if (P.coarse_ok && !D.empty()) {
+      std::vector<float> Df(D.begin(), D.end());
+      const size_t bytes = D.size() * (sizeof(double) + sizeof(float));
+      if (cudaMalloc(&P.d_coarse, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error(UW_ERR_OOM, "coarse-level table allocation failed");
+        return UW_ERR_OOM;
+      }
+      if (cudaMemcpy(P.d_coarse, D.data(), D.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy((double*)P.d_coarse + D.size(), Df.data(), Df.size() * sizeof(float),
+                     cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error(UW_ERR_CUDA, "coarse-level table upload failed");
+        return UW_ERR_CUDA;
+      }
+    }
   }
   std::vector<float> f32w;
   build_f32(P, f32w);
@@ -1222,6 +1677,35 @@ static unsigned int barrier_spin_limit() {
   return e && e[0] ? (unsigned int)strtoul(e, nullptr, 10) : (1u << 22);
 }
 
+template <typename T, int PM>
+static CTaps<T, PM> make_ctaps(const Plan& P) {
+  CTaps<T, PM> t;
+  const int p = P.p;
+  for (int f = 0; f < 2; ++f)
+    for (int d = -PM / 2; d <= PM / 2; ++d) {
+      const int l = 2 * d + f;
+      const bool in = l >= -p + 1 && l <= p;
+      t.hp[f][d + PM / 2] = in ? (T)P.h[l + p - 1] : T(0);
+      t.gp[f][d + PM / 2] = in ? (T)P.g[l + p - 1] : T(0);
+    }
+  for (int l = -PM + 1; l <= PM; ++l) {
+    const bool in = l >= -p + 1 && l <= p;
+    t.ha[l + PM - 1] = in ? (T)P.h[l + p - 1] : T(0);
+    t.ga[l + PM - 1] = in ? (T)P.g[l + p - 1] : T(0);
+  }
+  return t;
+}
+
+// filter length rounded up to an even compile-time PM >= p
+template <typename F>
+static void pm_dispatch(int p, F&& f) {
+  if (p <= 2) f(std::integral_constant<int, 2>{});
+  else if (p <= 4) f(std::integral_constant<int, 4>{});
+  else if (p <= 6) f(std::integral_constant<int, 6>{});
+  else if (p <= 8) f(std::integral_constant<int, 8>{});
+  else f(std::integral_constant<int, 10>{});
+}
+
 // All coarse levels in one cooperative launch (grid barrier between levels);
 // false if that launch is not possible here (then one launch per level).
 template <typename T>
@@ -1229,30 +1713,53 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
                                 bool fwd, Launcher& L) {
   const int nl = P.R - 1 - P.J0;
   if (nl < 2 || !P.d_sync || getenv_flag("UW_COARSE_PER_LEVEL")) return false;
-  size_t sm = 0;
-  int max_tiles = 0;
-  double bytes = 0;
-  for (int it = 0; it < nl; ++it) {
-    const int j = fwd ? P.J0 + it : P.R - 2 - it;
-    const int n0 = 1 << j, n1 = 2 * n0;
-    const int w = coarse_tile_extent(G, j, fwd);
-    if (!fwd && w > 64) return false;
-    if (fwd) {
-      const int TS = syn_tile(n1);
-      sm = std::max(sm, sizeof(T) * (((size_t)4 * G.p + 3) / 4 * 4 + 4 * (size_t)w * w + 2 * (size_t)w * TS));
-      max_tiles = std::max(max_tiles, (n1 / TS) * (n1 / TS));
-    } else {
-      const int TS = ana_tile(n0);
-      sm = std::max(sm, sizeof(T) * (((size_t)4 * G.p + 3) / 4 * 4 + (size_t)w * w + 2 * (size_t)TS * w));
-      max_tiles = std::max(max_tiles, (n0 / TS) * (n0 / TS));
-    }
-    bytes += sizeof(T) * (double)batch * (4.0 * n0 * n0 + (double)n1 * n1);
+  const bool rw = P.coarse_ok && !getenv_flag("UW_COARSE_GENERIC");
+  const T* Dg = nullptr;
+  if (P.d_coarse && P.bd != UW_BOUNDARY_PERIODIC) {
+    const size_t nD = (size_t)4 * P.Lb * P.p;
+    Dg = sizeof(T) == 8 ? (const T*)P.d_coarse : (const T*)((const double*)P.d_coarse + nD);
   }
-  CoarseIO<T> io{x, xout, XS, XS2, P.M, P.J0, nl, batch};
+  if (rw && P.bd != UW_BOUNDARY_PERIODIC && !Dg) return false;
   bool ok = false;
-  coarse_dispatch<T>(G.p, [&](auto pc) {
-    constexpr int PP = decltype(pc)::value;
-    auto kern = fwd ? k_syn2d_levels<T, PP> : k_ana2d_levels<T, PP>;
+  pm_dispatch(G.p, [&](auto pc) {
+    constexpr int PM = decltype(pc)::value;
+    const size_t head = (size_t)cup(cup(4 * G.p, 4) + (P.bd == UW_BOUNDARY_PERIODIC ? 0 : 4 * G.Lb * G.p), 4);
+    size_t sm = 0;
+    int max_tiles = 0;
+    double bytes = 0;
+    for (int it = 0; it < nl; ++it) {
+      const int j = fwd ? P.J0 + it : P.R - 2 - it;
+      const int n0 = 1 << j, n1 = 2 * n0;
+      size_t el = 0;
+      int TS = 0;
+      if (fwd) {
+        const int TR = rw ? syn_rw_ts(n1) : 0;
+        if (TR == 32) el = SynGeom<T, PM, 32>::elems;
+        else if (TR == 16) el = SynGeom<T, PM, 16>::elems;
+        else {
+          const int w = coarse_tile_extent(G, j, true);
+          el = 4 * (size_t)w * w + 2 * (size_t)w * syn_tile(n1);
+        }
+        TS = TR ? TR : syn_tile(n1);
+        max_tiles = std::max(max_tiles, (n1 / TS) * (n1 / TS));
+      } else {
+        const int TR = rw ? ana_rw_ts(n0) : 0;
+        if (TR == 16) el = AnaGeom<T, PM, 16>::elems;
+        else if (TR == 8) el = AnaGeom<T, PM, 8>::elems;
+        else {
+          const int w = coarse_tile_extent(G, j, false);
+          if (w > 64) return;
+          el = (size_t)w * w + 2 * (size_t)ana_tile(n0) * w;
+        }
+        TS = TR ? TR : ana_tile(n0);
+        max_tiles = std::max(max_tiles, (n0 / TS) * (n0 / TS));
+      }
+      sm = std::max(sm, sizeof(T) * (head + el));
+      bytes += sizeof(T) * (double)batch * (4.0 * n0 * n0 + (double)n1 * n1);
+    }
+    CoarseIO<T> io{x, xout, XS, XS2, P.M, P.J0, nl, batch};
+    const CTaps<T, PM> ct = make_ctaps<T, PM>(P);
+    auto kern = fwd ? k_syn2d_levels<T, PM> : k_ana2d_levels<T, PM>;
     set_smem_limit((const void*)kern);
     int dev = 0, nsm = 0, per = 0, coop = 0;
     cudaGetDevice(&dev);
@@ -1262,7 +1769,8 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
       cudaGetLastError();
       return;
     }
-    const int grid = (int)std::min<int64_t>((int64_t)per * nsm, (int64_t)max_tiles * batch);
+    // at most two CTAs per SM: fewer arrivals at each grid barrier
+    const int grid = (int)std::min<int64_t>((int64_t)std::min(per, 2) * nsm, (int64_t)max_tiles * batch);
     L.pre(fwd ? "idwt2d_levels" : "dwt2d_levels", bytes);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
@@ -1274,7 +1782,8 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    L.note(cudaLaunchKernelEx(&cfg, kern, io, tabs<T>(P), G, (GridBarrier*)P.d_sync, barrier_spin_limit()));
+    L.note(cudaLaunchKernelEx(&cfg, kern, io, tabs<T>(P), G, ct, Dg, rw ? 1 : 0, (GridBarrier*)P.d_sync,
+                              barrier_spin_limit()));
     L.check();
     ok = true;
   });

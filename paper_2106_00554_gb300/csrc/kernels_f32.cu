@@ -42,14 +42,17 @@ namespace uw {
 namespace f32k {
 
 // taps as kernel parameters (constant bank), zero-padded to PM >= p, with
-// 2^{-R/2} folded into the cell integrals:
-//   hp[f][d + PM/2] = h_{2d+f}, gp likewise          (d in [-PM/2, PM/2])
-//   tp[f][d + PM-1] = 2^{-R/2} I_q[Q d + f]           (d in [-(PM-1), PM-1])
+// 2^{-R/2} folded into the cell integrals, in pairs for the packed FP32x2 FMA:
+//   hp2[d + PM/2] = (h_{2d}, h_{2d+1}), gp2 likewise         (d in [-PM/2, PM/2])
+//   tp2[k][d + PM-1] = 2^{-R/2} (I_q[Q d + 2k], I_q[Q d + 2k + 1])   (d in [-(PM-1), PM-1])
+// The synthesis and T pair two outputs of adjacent phases (same window
+// value, both taps); the analysis and T^T pair two adjacent window values
+// of one output (their two taps) and add the halves at the end.
 template <int PM, int Q>
 struct Taps {
-  float hp[2][PM + 1];
-  float gp[2][PM + 1];
-  float tp[Q][2 * PM - 1];
+  float2 hp2[PM + 1];
+  float2 gp2[PM + 1];
+  float2 tp2[Q / 2][2 * PM - 1];
 };
 
 struct Args {
@@ -126,16 +129,18 @@ __device__ __forceinline__ void wht(float (&a)[R]) {
       }
 }
 
-// one pencil: elements e0 + i * stride (i < R) of the line whose element k
-// sits at V[vp(k + off)]
-template <int R>
-__device__ __forceinline__ void pencil(float* V, int off, int e0, int stride) {
-  float a[R];
+// One pencil of the bits-4..7 pass: elements low4 + 16 i + 256 h (i < 16) of
+// the line whose element k sits at V[vp(k + off)], off a multiple of 256.
+// With low4 < 16 their padded addresses are vp(low4 + 256 h + off) + 20 i.
+template <int NT>
+__device__ __forceinline__ void pass_mid(float* V, int off, int tid) {
+  float* b = V + vp((tid & 15) + 256 * (tid >> 4) + off);
+  float a[16];
 #pragma unroll
-  for (int i = 0; i < R; ++i) a[i] = V[vp(e0 + i * stride + off)];
-  wht<R>(a);
+  for (int i = 0; i < 16; ++i) a[i] = b[20 * i];
+  wht<16>(a);
 #pragma unroll
-  for (int i = 0; i < R; ++i) V[vp(e0 + i * stride + off)] = a[i];
+  for (int i = 0; i < 16; ++i) b[20 * i] = a[i];
 }
 
 // the lowest element of pencil c (< 256) of the bits-8.. pass: the two
@@ -147,16 +152,20 @@ __device__ __forceinline__ int high_pencil(int c) {
   return 16 * a + (c & 15);
 }
 
-// bits 4-7 (one radix-16 pencil per thread) and bits 8..L-1 (256 pencils)
-template <int NT>
-__device__ __forceinline__ void pass_mid(float* V, int off, int tid) {
-  pencil<16>(V, off, (tid & 15) + 256 * (tid >> 4), 16);
-}
+// bits 8..L-1: 256 pencils e0 + 256 i (e0 < 256), at vp(e0 + off) + 336 i
 template <int NT>
 __device__ __forceinline__ void pass_high(float* V, int off, int tid) {
   constexpr int N = 16 * NT, RH = N / 256;
 #pragma unroll
-  for (int c = tid; c < 256; c += NT) pencil<RH>(V, off, high_pencil(c), 256);
+  for (int c = tid; c < 256; c += NT) {
+    float* b = V + vp(high_pencil(c) + off);
+    float a[RH];
+#pragma unroll
+    for (int i = 0; i < RH; ++i) a[i] = b[336 * i];
+    wht<RH>(a);
+#pragma unroll
+    for (int i = 0; i < RH; ++i) b[336 * i] = a[i];
+  }
 }
 
 __device__ __forceinline__ void cp16(void* sdst, const void* gsrc) {
@@ -168,7 +177,34 @@ __device__ __forceinline__ void cp4(void* sdst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc));
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+template <int NPEND>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND)); }
+
+// Position (line l within its instance, instance b) of a CTA's lines, which
+// advance by the grid size: the division happens once per kernel.
+struct LinePos {
+  int l;
+  int64_t b;
+  int lines, dl;
+  int64_t db;
+  __device__ __forceinline__ void init(int line, int step, int nlines) {
+    lines = nlines;
+    l = line % nlines;
+    b = line / nlines;
+    dl = step % nlines;
+    db = step / nlines;
+  }
+  __device__ __forceinline__ LinePos next() const {
+    LinePos q = *this;
+    q.l += dl;
+    q.b += db;
+    if (q.l >= lines) {
+      q.l -= lines;
+      ++q.b;
+    }
+    return q;
+  }
+};
 
 // packed-sample range [r0, r1) of mask row mrow
 __device__ __forceinline__ void row_range(const LineIO& io, int mrow, int& r0, int& r1) {
@@ -186,30 +222,28 @@ __device__ __forceinline__ void issue_pos(const LineIO& io, int r0, int r1, uint
 // forward
 // ---------------------------------------------------------------------------
 template <int PM, int Q, int NT>
-__global__ void __launch_bounds__(NT, 2) k_f32_fwd(const float* __restrict__ in, float* __restrict__ out, Args a,
+__global__ void __launch_bounds__(NT, 3) k_f32_fwd(const float* __restrict__ in, float* __restrict__ out, Args a,
                                                    Taps<PM, Q> tp, LineIO io, int total) {
   using G = Geom<PM, Q, NT>;
   constexpr int N = G::N, M = G::M, n0 = G::n0, BS = G::BS, BL = G::BL, VW = G::VW, HX = G::HX, XL = G::XL;
   constexpr int HS = G::HS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x;
   const bool gather = io.mode == 1;
   float* sV = reinterpret_cast<float*>(smem_raw);
   float* sS = sV + G::VLf;
-  float* sX = sS + G::SL;                                        // 2 x XL
+  float* sX = sS + G::SL;                                         // 2 x XL (this line, next line)
   float* sCorr = sX + 2 * XL;                                     // 2K (VMP)
-  uint32_t* sP = reinterpret_cast<uint32_t*>(sCorr + up4(2 * a.K));  // 2 x PST (gather)
+  uint32_t* sP = reinterpret_cast<uint32_t*>(sCorr + up4(2 * a.K));  // PST (gather)
 
   // halos start zero (VMP) and periodic halos are rewritten per line
   for (int i = tid; i < G::SL; i += NT) sS[i] = 0.f;
   for (int i = tid; i < 2 * XL; i += NT) sX[i] = 0.f;
   __syncthreads();
 
-  auto issue_in = [&](int ln, int bi) {
-    const int l = ln % io.lines;
-    const int64_t b = ln / io.lines;
-    const int drow = io.seq_rows ? seqrow(l, a.L) : l;
-    const float* src = in + b * io.in_batch + (int64_t)drow * io.in_stride;
+  auto issue_in = [&](const LinePos& lp, int bi) {
+    const int drow = io.seq_rows ? seqrow(lp.l, a.L) : lp.l;
+    const float* src = in + lp.b * io.in_batch + (int64_t)drow * io.in_stride;
     float* dst = sX + bi * XL;
     for (int e4 = tid; e4 < M / 4; e4 += NT) {
       const int i = 4 * e4, half = i >= n0, ii = i - half * n0;
@@ -222,34 +256,37 @@ __global__ void __launch_bounds__(NT, 2) k_f32_fwd(const float* __restrict__ in,
     }
   };
 
+  // cp.async groups, oldest first: in(line), pos(line), in(next), ... ; the
+  // sample positions of a line are copied while the previous line's gather
+  // is done, and awaited just before this line's gather
   pdl_trigger();
   pdl_wait();
   const int G0 = gridDim.x;
   int line = blockIdx.x;
+  LinePos cur;
+  cur.init(line, G0, io.lines);
+  LinePos nx = cur.next();
   int cr0 = 0, cr1 = 0, xr0 = 0, xr1 = 0;
-  if (line < total) {
-    issue_in(line, 0);
-    if (gather) {
-      row_range(io, line % io.lines, cr0, cr1);
-      issue_pos(io, cr0, cr1, sP, tid, NT);
-    }
+  if (line < total) issue_in(cur, 0);
+  cp_commit();
+  if (gather && line < total) {
+    row_range(io, cur.l, cr0, cr1);
+    issue_pos(io, cr0, cr1, sP, tid, NT);
   }
   cp_commit();
-  if (gather && line + G0 < total) row_range(io, (line + G0) % io.lines, xr0, xr1);
+  if (gather && line + G0 < total) row_range(io, nx.l, xr0, xr1);
 
   for (int buf = 0; line < total; line += G0, buf ^= 1) {
     const int nxt = line + G0;
-    if (nxt < total) {
-      issue_in(nxt, buf ^ 1);
-      if (gather) issue_pos(io, xr0, xr1, sP + (buf ^ 1) * G::PST, tid, NT);
-    }
+    const LinePos nn = nx.next();
+    if (nxt < total) issue_in(nx, buf ^ 1);
     cp_commit();
     int yr0 = 0, yr1 = 0;
-    if (gather && nxt + G0 < total) row_range(io, (nxt + G0) % io.lines, yr0, yr1);
-    cp_wait1();
+    if (gather && nxt + G0 < total) row_range(io, nn.l, yr0, yr1);
+    cp_wait<2>();
     __syncthreads();
-    const int l = line % io.lines;
-    const int64_t b = line / io.lines;
+    const int l = cur.l;
+    const int64_t b = cur.b;
     const float* xl = sX + buf * XL;           // lo[i] at xl[HX + i]
     const float* xh = xl + n0 + 2 * HX;        // hi[i] at xh[HX + i]
 
@@ -274,18 +311,17 @@ __global__ void __launch_bounds__(NT, 2) k_f32_fwd(const float* __restrict__ in,
       }
       float s[BS];
 #pragma unroll
-      for (int jj = 0; jj < BL; ++jj)
+      for (int jj = 0; jj < BL; ++jj) {
+        float2 acc = make_float2(0.f, 0.f);      // (s[2 a], s[2 a + 1]), a = a0 + jj
 #pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          float acc = 0.f;
-#pragma unroll
-          for (int d = -PM / 2; d <= PM / 2; ++d) {
-            const int w = jj - d + PM / 2 + G::OFFX;
-            acc = fmaf(tp.hp[f][d + PM / 2], wl[w], acc);
-            acc = fmaf(tp.gp[f][d + PM / 2], wh[w], acc);
-          }
-          s[2 * jj + f] = acc;
+        for (int d = -PM / 2; d <= PM / 2; ++d) {
+          const int w = jj - d + PM / 2 + G::OFFX;
+          acc = __ffma2_rn(tp.hp2[d + PM / 2], make_float2(wl[w], wl[w]), acc);
+          acc = __ffma2_rn(tp.gp2[d + PM / 2], make_float2(wh[w], wh[w]), acc);
         }
+        s[2 * jj] = acc.x;
+        s[2 * jj + 1] = acc.y;
+      }
       const int m0 = BS * tid;
 #pragma unroll
       for (int j = 0; j < BS; j += 4)
@@ -299,27 +335,24 @@ __global__ void __launch_bounds__(NT, 2) k_f32_fwd(const float* __restrict__ in,
         }
       }
     }
-    // VMP edge corrections of T (warp 0: left end, last warp: right end)
-    if (a.K && (warp == 0 || warp == NT / 32 - 1)) {
-      const int side = warp == 0 ? 0 : 1;
-      const float* C = a.C + (size_t)side * a.K * a.CS;
-      const int base = side == 0 ? 0 : n0 - a.p;
-      for (int r = lane; r < a.K; r += 32) {
-        const float4* crow = reinterpret_cast<const float4*>(C + (size_t)r * a.CS);
+    // VMP edge corrections of T: one row of C (2p weights) per task, rows of
+    // both ends spread over the CTA
+    if (a.K) {
+      for (int t = tid; t < 2 * a.K; t += NT) {
+        const int side = t >= a.K, r = t - side * a.K;
+        const float4* crow = reinterpret_cast<const float4*>(a.C + ((size_t)side * a.K + r) * a.CS);
+        const int base = HX + (side == 0 ? 0 : n0 - a.p);
         float acc = 0.f;
-        for (int c4 = 0; c4 < a.CS / 4; ++c4) {
+        for (int c4 = 0; 4 * c4 < 2 * a.p; ++c4) {
           const float4 cw = __ldg(crow + c4);
           const float cv[4] = {cw.x, cw.y, cw.z, cw.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int c = 4 * c4 + e;
-            if (c < 2 * a.p) {
-              const int i = base + (c < a.p ? c : c - a.p);
-              acc = fmaf(cv[e], c < a.p ? xl[HX + i] : xh[HX + i], acc);
-            }
+            if (c < 2 * a.p) acc = fmaf(cv[e], c < a.p ? xl[base + c] : xh[base + c - a.p], acc);
           }
         }
-        sCorr[side * a.K + r] = acc;
+        sCorr[t] = acc;
       }
     }
     __syncthreads();
@@ -337,12 +370,15 @@ __global__ void __launch_bounds__(NT, 2) k_f32_fwd(const float* __restrict__ in,
       }
       float v[16];
 #pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        float acc = 0.f;
+      for (int r = 0; r < 16; r += 2) {          // outputs r, r + 1: phases f, f + 1 of one window position
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int d = -(PM - 1); d <= PM - 1; ++d)
-          acc = fmaf(tp.tp[r % Q][d + PM - 1], ws[r / Q - d + PM - 1 + G::OFFB], acc);
-        v[r] = acc;
+        for (int d = -(PM - 1); d <= PM - 1; ++d) {
+          const float x = ws[r / Q - d + PM - 1 + G::OFFB];
+          acc = __ffma2_rn(tp.tp2[(r % Q) / 2][d + PM - 1], make_float2(x, x), acc);
+        }
+        v[r] = acc.x;
+        v[r + 1] = acc.y;
       }
       if (a.K) {
         const int kb = a.K / 16;
@@ -365,11 +401,14 @@ __global__ void __launch_bounds__(NT, 2) k_f32_fwd(const float* __restrict__ in,
     __syncthreads();
     if (gather) {
       pass_high<NT>(sV, 0, tid);
+      cp_wait<1>();              // this line's sample positions
       __syncthreads();
-      const uint16_t* ps = reinterpret_cast<const uint16_t*>(sP + buf * G::PST) + (cr0 & 1);
+      const uint16_t* ps = reinterpret_cast<const uint16_t*>(sP) + (cr0 & 1);
       float* y = out + b * io.m + cr0;
       const int cnt = cr1 - cr0;
       for (int j = tid; j < cnt; j += NT) y[j] = sV[vp(ps[j])];
+      __syncthreads();           // positions consumed: the next line's may land
+      if (nxt < total) issue_pos(io, xr0, xr1, sP, tid, NT);
     } else {
       // the last pass writes the natural-order line straight to global memory
       float* dst = out + b * io.out_batch + (int64_t)l * io.out_stride;
@@ -377,19 +416,22 @@ __global__ void __launch_bounds__(NT, 2) k_f32_fwd(const float* __restrict__ in,
 #pragma unroll
       for (int c = tid; c < 256; c += NT) {
         const int e0 = high_pencil(c);
+        const float* src = sV + vp(e0);
         float v[RH];
 #pragma unroll
-        for (int i = 0; i < RH; ++i) v[i] = sV[vp(e0 + 256 * i)];
+        for (int i = 0; i < RH; ++i) v[i] = src[336 * i];
         wht<RH>(v);
 #pragma unroll
         for (int i = 0; i < RH; ++i) dst[e0 + 256 * i] = v[i];
       }
     }
-    __syncthreads();
+    cp_commit();
     cr0 = xr0;
     cr1 = xr1;
     xr0 = yr0;
     xr1 = yr1;
+    cur = nx;
+    nx = nn;
   }
 }
 
@@ -397,37 +439,36 @@ __global__ void __launch_bounds__(NT, 2) k_f32_fwd(const float* __restrict__ in,
 // adjoint
 // ---------------------------------------------------------------------------
 template <int PM, int Q, int NT>
-__global__ void __launch_bounds__(NT, 2) k_f32_adj(const float* __restrict__ in, float* __restrict__ out, Args a,
+__global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in, float* __restrict__ out, Args a,
                                                    Taps<PM, Q> tp, LineIO io, int total) {
   using G = Geom<PM, Q, NT>;
   constexpr int N = G::N, M = G::M, n0 = G::n0, BS = G::BS, BL = G::BL, HS = G::HS, VH = G::VH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31;
   const bool scat = io.mode == 1;
-  // mode 0: two staged Walsh lines, transformed in place; mode 1: one Walsh
-  // line, two staged sample buffers and position buffers
+  // mode 0: two staged Walsh lines (this one, the next), transformed in
+  // place; mode 1: one Walsh line, the next line's packed samples and positions
   float* sV0 = reinterpret_cast<float*>(smem_raw);
   float* sS = sV0 + (scat ? 1 : 2) * G::VLa;
   float* sCorr = sS + G::SL;                                      // 4p (VMP)
-  float* sY = sCorr + up4(4 * a.p);                               // 2 x N (mode 1)
-  uint32_t* sP = reinterpret_cast<uint32_t*>(sY + (scat ? 2 * N : 0));   // 2 x PST (mode 1)
+  float* sY = sCorr + up4(4 * a.p);                               // N (mode 1)
+  uint32_t* sP = reinterpret_cast<uint32_t*>(sY + (scat ? N : 0));   // PST (mode 1)
 
   for (int i = tid; i < (scat ? 1 : 2) * G::VLa; i += NT) sV0[i] = 0.f;
   for (int i = tid; i < G::SL; i += NT) sS[i] = 0.f;
   __syncthreads();
 
-  auto issue_in = [&](int ln, int bi, int r0, int r1) {
-    const int l = ln % io.lines;
-    const int64_t b = ln / io.lines;
+  auto issue_in = [&](const LinePos& lp, int bi, int r0, int r1) {
+    const int l = lp.l;
+    const int64_t b = lp.b;
     if (!scat) {
       const float* src = in + b * io.in_batch + (int64_t)l * io.in_stride;
       float* dst = sV0 + bi * G::VLa;
       for (int e4 = tid; e4 < N / 4; e4 += NT) cp16(dst + vp(VH + 4 * e4), src + 4 * e4);
     } else {
       const float* y = in + b * io.m;
-      float* dst = sY + bi * N;
-      for (int j = r0 + tid; j < r1; j += NT) cp4(dst + (j - r0), y + j);
-      issue_pos(io, r0, r1, sP + bi * G::PST, tid, NT);
+      for (int j = r0 + tid; j < r1; j += NT) cp4(sY + (j - r0), y + j);
+      issue_pos(io, r0, r1, sP, tid, NT);
     }
   };
 
@@ -435,34 +476,44 @@ __global__ void __launch_bounds__(NT, 2) k_f32_adj(const float* __restrict__ in,
   pdl_wait();
   const int G0 = gridDim.x;
   int line = blockIdx.x;
+  LinePos cur;
+  cur.init(line, G0, io.lines);
+  LinePos nx = cur.next();
   int cr0 = 0, cr1 = 0, xr0 = 0, xr1 = 0;
   if (line < total) {
-    if (scat) row_range(io, line % io.lines, cr0, cr1);
-    issue_in(line, 0, cr0, cr1);
+    if (scat) row_range(io, cur.l, cr0, cr1);
+    issue_in(cur, 0, cr0, cr1);
   }
   cp_commit();
-  if (scat && line + G0 < total) row_range(io, (line + G0) % io.lines, xr0, xr1);
+  if (scat && line + G0 < total) row_range(io, nx.l, xr0, xr1);
 
   for (int buf = 0; line < total; line += G0, buf ^= 1) {
     const int nxt = line + G0;
-    if (nxt < total) issue_in(nxt, buf ^ 1, xr0, xr1);
-    cp_commit();
+    const LinePos nn = nx.next();
     int yr0 = 0, yr1 = 0;
-    if (scat && nxt + G0 < total) row_range(io, (nxt + G0) % io.lines, yr0, yr1);
-    cp_wait1();
+    if (!scat) {
+      if (nxt < total) issue_in(nx, buf ^ 1, 0, 0);
+      cp_commit();
+      cp_wait<1>();
+    } else {
+      if (nxt + G0 < total) row_range(io, nn.l, yr0, yr1);
+      cp_wait<0>();   // this line's samples, copied while the previous line ran
+    }
     __syncthreads();
-    const int l = line % io.lines;
-    const int64_t b = line / io.lines;
+    const int l = cur.l;
+    const int64_t b = cur.b;
     float* sV = sV0 + (scat ? 0 : buf * G::VLa);
     if (scat) {
       // zero the line, then scatter the staged samples to their natural positions
       for (int k4 = tid; k4 < N / 4; k4 += NT) *reinterpret_cast<float4*>(sV + vp(VH + 4 * k4)) = make_float4(0.f, 0.f, 0.f, 0.f);
       __syncthreads();
-      const uint16_t* ps = reinterpret_cast<const uint16_t*>(sP + buf * G::PST) + (cr0 & 1);
-      const float* ys = sY + buf * N;
+      const uint16_t* ps = reinterpret_cast<const uint16_t*>(sP) + (cr0 & 1);
       const int cnt = cr1 - cr0;
-      for (int j = tid; j < cnt; j += NT) sV[vp(VH + ps[j])] = ys[j];
+      for (int j = tid; j < cnt; j += NT) sV[vp(VH + ps[j])] = sY[j];
       __syncthreads();
+      // the staging buffers are free: copy the next line's samples now
+      if (nxt < total) issue_in(nx, 0, xr0, xr1);
+      cp_commit();
     }
     // Walsh stages (they commute): bits 8.., bits 4-7, then 0-3 in registers
     pass_high<NT>(sV, VH, tid);
@@ -495,23 +546,28 @@ __global__ void __launch_bounds__(NT, 2) k_f32_adj(const float* __restrict__ in,
       }
     }
     __syncthreads();
-    // VMP: C^T on the first / last K transformed samples (warp 0 / last warp)
-    if (a.K && (warp == 0 || warp == NT / 32 - 1)) {
-      const int side = warp == 0 ? 0 : 1;
-      const float* C = a.C + (size_t)side * a.K * a.CS;
-      const int kbase = side == 0 ? 0 : N - a.K;
-      const int half = a.K / 2;
-      // two lanes per output column; every lane runs every round (full-warp shuffle)
-      for (int t0 = 0; t0 < 4 * a.p; t0 += 32) {
-        const int t = t0 + lane;
-        const bool act = t < 4 * a.p;
-        const int c = t >> 1, part = t & 1;
+    // VMP: C^T on the first / last K transformed samples.  Output oc (side,
+    // column) is split into 8 parts of K/8 rows on 8 consecutive lanes,
+    // combined with shuffles (every lane of a warp runs every round).
+    if (a.K) {
+      const int ntask = 32 * a.p, kp = a.K / 8;
+      for (int t0 = 0; t0 < ntask; t0 += NT) {
+        if (t0 + (tid & ~31) >= ntask) break;        // warp-uniform: no lane of this warp has a task
+        const int t = t0 + tid;
+        const bool act = t < ntask;
+        const int oc = t >> 3, part = t & 7;
+        const int side = oc >= 2 * a.p, c = oc - side * 2 * a.p;
         float acc = 0.f;
-        if (act)
-          for (int k = part * half; k < (part + 1) * half; ++k)
-            acc = fmaf(__ldg(C + (size_t)k * a.CS + c), sV[vp(VH + kbase + k)], acc);
+        if (act) {
+          const float* C = a.C + (size_t)side * a.K * a.CS + c;
+          const int kbase = (side == 0 ? 0 : N - a.K) + part * kp;
+          for (int k = 0; k < kp; ++k)
+            acc = fmaf(__ldg(C + (size_t)(part * kp + k) * a.CS), sV[vp(VH + kbase + k)], acc);
+        }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        if (act && part == 0) sCorr[side * 2 * a.p + c] = acc;
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (act && (lane & 7) == 0) sCorr[oc] = acc;
       }
     }
     // s[BS u .. BS u + BS) = T^T v
@@ -527,12 +583,15 @@ __global__ void __launch_bounds__(NT, 2) k_f32_adj(const float* __restrict__ in,
       float s[BS];
 #pragma unroll
       for (int bb = 0; bb < BS; ++bb) {
-        float acc = 0.f;
+        float2 acc = make_float2(0.f, 0.f);      // phases (2k, 2k + 1) of each tap position
 #pragma unroll
         for (int d = -(PM - 1); d <= PM - 1; ++d)
 #pragma unroll
-          for (int f = 0; f < Q; ++f) acc = fmaf(tp.tp[f][d + PM - 1], wv[Q * (bb + d + PM - 1) + f + G::OFFT], acc);
-        s[bb] = acc;
+          for (int k = 0; k < Q / 2; ++k) {
+            const int w = Q * (bb + d + PM - 1) + 2 * k + G::OFFT;   // even: an aligned register pair
+            acc = __ffma2_rn(tp.tp2[k][d + PM - 1], make_float2(wv[w], wv[w + 1]), acc);
+          }
+        s[bb] = acc.x + acc.y;
       }
 #pragma unroll
       for (int j = 0; j < BS; j += 4)
@@ -560,17 +619,16 @@ __global__ void __launch_bounds__(NT, 2) k_f32_adj(const float* __restrict__ in,
       float lo[BL], hi[BL];
 #pragma unroll
       for (int bb = 0; bb < BL; ++bb) {
-        float x = 0.f, y = 0.f;
+        float2 x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int d = -PM / 2; d <= PM / 2; ++d)
-#pragma unroll
-          for (int f = 0; f < 2; ++f) {
-            const float sv = ws[2 * (bb + d) + f + PM + G::OFFA];
-            x = fmaf(tp.hp[f][d + PM / 2], sv, x);
-            y = fmaf(tp.gp[f][d + PM / 2], sv, y);
-          }
-        lo[bb] = x;
-        hi[bb] = y;
+        for (int d = -PM / 2; d <= PM / 2; ++d) {
+          const int w = 2 * (bb + d) + PM + G::OFFA;                 // even: an aligned register pair
+          const float2 sv = make_float2(ws[w], ws[w + 1]);
+          x = __ffma2_rn(tp.hp2[d + PM / 2], sv, x);
+          y = __ffma2_rn(tp.gp2[d + PM / 2], sv, y);
+        }
+        lo[bb] = x.x + x.y;
+        hi[bb] = y.x + y.y;
       }
       if (a.K) {
 #pragma unroll
@@ -596,11 +654,12 @@ __global__ void __launch_bounds__(NT, 2) k_f32_adj(const float* __restrict__ in,
         *reinterpret_cast<float2*>(dst + n0 + i0) = make_float2(hi[0], hi[1]);
       }
     }
-    __syncthreads();
     cr0 = xr0;
     cr1 = xr1;
     xr0 = yr0;
     xr1 = yr1;
+    cur = nx;
+    nx = nn;
   }
 }
 
@@ -610,22 +669,19 @@ __global__ void __launch_bounds__(NT, 2) k_f32_adj(const float* __restrict__ in,
 template <int PM, int Q>
 Taps<PM, Q> make_taps(const Plan& P) {
   Taps<PM, Q> t;
-  std::fill(&t.hp[0][0], &t.hp[0][0] + 2 * (PM + 1), 0.f);
-  std::fill(&t.gp[0][0], &t.gp[0][0] + 2 * (PM + 1), 0.f);
-  std::fill(&t.tp[0][0], &t.tp[0][0] + Q * (2 * PM - 1), 0.f);
   const int p = P.p;
   const double sc = std::exp2(-0.5 * P.R);
-  for (int f = 0; f < 2; ++f)
-    for (int d = -PM / 2; d <= PM / 2; ++d) {
-      const int l = 2 * d + f;
-      if (l >= -p + 1 && l <= p) {
-        t.hp[f][d + PM / 2] = (float)P.h[l + p - 1];
-        t.gp[f][d + PM / 2] = (float)P.g[l + p - 1];
-      }
-    }
-  for (int f = 0; f < Q; ++f)
-    for (int d = -(PM - 1); d <= PM - 1; ++d)
-      if (d >= -(p - 1) && d <= p - 1) t.tp[f][d + PM - 1] = (float)(sc * P.taps[Q * d + f + (p - 1) * Q]);
+  auto hf = [&](int l) { return (l >= -p + 1 && l <= p) ? (float)P.h[l + p - 1] : 0.f; };
+  auto gf = [&](int l) { return (l >= -p + 1 && l <= p) ? (float)P.g[l + p - 1] : 0.f; };
+  for (int d = -PM / 2; d <= PM / 2; ++d) {
+    t.hp2[d + PM / 2] = make_float2(hf(2 * d), hf(2 * d + 1));
+    t.gp2[d + PM / 2] = make_float2(gf(2 * d), gf(2 * d + 1));
+  }
+  auto tf = [&](int f, int d) {
+    return (d >= -(p - 1) && d <= p - 1) ? (float)(sc * P.taps[Q * d + f + (p - 1) * Q]) : 0.f;
+  };
+  for (int k = 0; k < Q / 2; ++k)
+    for (int d = -(PM - 1); d <= PM - 1; ++d) t.tp2[k][d + PM - 1] = make_float2(tf(2 * k, d), tf(2 * k + 1, d));
   return t;
 }
 
@@ -633,14 +689,14 @@ template <int PM, int Q, int NT>
 size_t smem_fwd(const Plan& P, bool gather) {
   using G = Geom<PM, Q, NT>;
   return sizeof(float) * ((size_t)G::VLf + G::SL + 2 * G::XL + up4(2 * P.f32.K)) +
-         (gather ? sizeof(uint32_t) * 2 * (size_t)G::PST : 0);
+         (gather ? sizeof(uint32_t) * (size_t)G::PST : 0);
 }
 
 template <int PM, int Q, int NT>
 size_t smem_adj(const Plan& P, bool scat) {
   using G = Geom<PM, Q, NT>;
   return sizeof(float) * ((size_t)(scat ? 1 : 2) * G::VLa + G::SL + up4(4 * P.p)) +
-         (scat ? sizeof(float) * 2 * (size_t)G::N + sizeof(uint32_t) * 2 * (size_t)G::PST : 0);
+         (scat ? sizeof(float) * (size_t)G::N + sizeof(uint32_t) * (size_t)G::PST : 0);
 }
 
 template <typename K>
@@ -668,11 +724,13 @@ cudaError_t go(bool fwd, const Plan& P, const float* in, float* out, const LineI
     const size_t sm = smem_fwd<PM, Q, NT>(P, io.mode == 1);
     auto kern = k_f32_fwd<PM, Q, NT>;
     set_smem_limit((const void*)kern);
+    cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return launch_pdl(kern, dim3(persistent_grid(kern, NT, sm, total)), dim3(NT), sm, s, in, out, a, t, io, total);
   }
   const size_t sm = smem_adj<PM, Q, NT>(P, io.mode == 1);
   auto kern = k_f32_adj<PM, Q, NT>;
   set_smem_limit((const void*)kern);
+  cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   return launch_pdl(kern, dim3(persistent_grid(kern, NT, sm, total)), dim3(NT), sm, s, in, out, a, t, io, total);
 }
 
@@ -695,7 +753,7 @@ bool f32_eligible(const Plan& P, const LineIO& io, const void* in, const void* o
   if (!P.f32.ok || io.jlev != P.R - 1) return false;
   if (P.N != 2048 && P.N != 4096) return false;
   if (P.Q != 2 && P.Q != 4) return false;
-  if (P.bd != UW_BOUNDARY_PERIODIC && (!P.d_f32 || P.f32.K == 0)) return false;
+  if (P.f32.K > 0 && !P.d_f32) return false;
   const int NT = P.N / 16;
   if (P.f32.K / 16 > NT / 2) return false;
   if (P.M / 2 < 16) return false;

@@ -773,6 +773,7 @@ void uw_plan_destroy(uw_plan* P) {
   cudaFree(P->d_tc);
   cudaFree(P->d_f32);
   cudaFree(P->d_sync);
+  cudaFree(P->d_coarse);
   cudaFree(P->d_pos);
   delete P;
 }

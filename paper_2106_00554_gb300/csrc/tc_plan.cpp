@@ -421,7 +421,10 @@ void build_f32(Plan& P, std::vector<float>& out) {
         dmax = std::max(dmax, std::fabs(d[k]));
       }
     }
-  if (dmax == 0) return;
+  if (dmax == 0) {   // the boundary functions are interior ones cut at the ends (p = 1): no correction
+    F.ok = 1;
+    return;
+  }
   const double tol = 1e-12 * dmax;
   int K = 0;
   for (int side = 0; side < 2; ++side)
@@ -451,6 +454,72 @@ void build_f32(Plan& P, std::vector<float>& out) {
       }
   F.words = (int64_t)out.size();
   F.ok = 1;
+}
+
+// Edge corrections of one 2D Mallat level (the coarse-level kernels): the
+// exact VMP synthesis of a level (Sec. 3.2: interior two-scale relations plus
+// the level-independent boundary blocks) differs from the interior formula
+// with zero padding only in the first / last Lb outputs, and only through the
+// p lo and p hi coefficients at that end.  D[side][r][c], r < Lb, c < 2p:
+// left rows k = r, columns lo[c] (c < p) and hi[c - p]; right rows
+// k = n1 - Lb + r, columns lo[n0 - p + c], hi[n0 - p + c - p].  The
+// analysis of a level is the transpose.  Computed at a level with n0 = 4p + 4
+// (the blocks do not depend on the level); returns false if a difference
+// shows up outside that structure.
+bool build_coarse(const Plan& P, std::vector<double>& D) {
+  D.clear();
+  if (P.bd == UW_BOUNDARY_PERIODIC) return true;
+  const int p = P.p, Lb = P.Lb, n0 = 4 * p + 4, n1 = 2 * n0;
+  auto syn_exact = [&](const std::vector<double>& lo, const std::vector<double>& hi, int k) {
+    double acc = 0;
+    const int mlo = std::max(p, ceildiv(k - p, 2)), mhi = std::min(n0 - p - 1, floordiv(k + p - 1, 2));
+    for (int m = mlo; m <= mhi; ++m) acc += P.h[k - 2 * m + p - 1] * lo[m] + P.g[k - 2 * m + p - 1] * hi[m];
+    if (k < Lb)
+      for (int m = 0; m < p; ++m) acc += P.PL[m * Lb + k] * lo[m] + P.QL[m * Lb + k] * hi[m];
+    const int c = n1 - 1 - k;
+    if (c < Lb)
+      for (int r = 0; r < p; ++r) acc += P.PR[r * Lb + c] * lo[n0 - 1 - r] + P.QR[r * Lb + c] * hi[n0 - 1 - r];
+    return acc;
+  };
+  auto syn_int0 = [&](const std::vector<double>& lo, const std::vector<double>& hi, int k) {
+    double acc = 0;
+    for (int l = -p + 1; l <= p; ++l) {
+      const int km = k - l;
+      if (km & 1) continue;
+      const int i = km / 2;
+      if (i < 0 || i >= n0) continue;
+      acc += P.h[l + p - 1] * lo[i] + P.g[l + p - 1] * hi[i];
+    }
+    return acc;
+  };
+  D.assign((size_t)2 * Lb * 2 * p, 0.0);
+  std::vector<double> lo(n0), hi(n0);
+  double dmax = 0, stray = 0;
+  // columns: the p + 2 coefficients nearest each end (the last two must show no difference)
+  for (int side = 0; side < 2; ++side)
+    for (int half = 0; half < 2; ++half)
+      for (int e = 0; e < p + 2; ++e) {
+        std::fill(lo.begin(), lo.end(), 0.0);
+        std::fill(hi.begin(), hi.end(), 0.0);
+        const int i = side == 0 ? e : n0 - 1 - e;
+        (half == 0 ? lo : hi)[i] = 1.0;
+        for (int k = 0; k < n1; ++k) {
+          const double d = syn_exact(lo, hi, k) - syn_int0(lo, hi, k);
+          const int r = side == 0 ? k : k - (n1 - Lb);
+          if (e < p && r >= 0 && r < Lb) {
+            const int c = half * p + (side == 0 ? e : p - 1 - e);
+            D[((size_t)side * Lb + r) * 2 * p + c] = d;
+            dmax = std::max(dmax, std::fabs(d));
+          } else {
+            stray = std::max(stray, std::fabs(d));
+          }
+        }
+      }
+  if (stray > 1e-13 * std::max(dmax, 1.0)) {
+    D.clear();
+    return false;
+  }
+  return true;
 }
 
 }  // namespace uw

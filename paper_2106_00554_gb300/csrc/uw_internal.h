@@ -98,6 +98,8 @@ struct Plan {
   F32Geo f32;                    // FP32 line operators (f32.ok = 0: not eligible)
   void* d_f32 = nullptr;         // [2][K][CS] floats (left, then right)
   void* d_sync = nullptr;        // grid barrier of the fused coarse-level kernels
+  void* d_coarse = nullptr;      // coarse-level edge corrections: [2][Lb][2p] doubles, then floats
+  int coarse_ok = 0;             // 1: the register-window coarse tiles may run
 };
 
 // plan.cpp
@@ -108,6 +110,9 @@ void build_tc(Plan& P, std::vector<uint32_t>& words);
 // tc_plan.cpp: edge corrections of the FP32 line operators (host, FP64);
 // fills P.f32 and the floats to upload (empty if not eligible)
 void build_f32(Plan& P, std::vector<float>& out);
+// tc_plan.cpp: edge corrections of one 2D Mallat level, [2][Lb][2p] (empty
+// for periodic plans); false if the boundary blocks do not have that structure
+bool build_coarse(const Plan& P, std::vector<double>& D);
 // kernels.cu
 int upload_tables(Plan& P);
 int launch_forward(const Plan& P, int prec, const void* x, void* y, int batch, void* stream, int* nlaunch);
