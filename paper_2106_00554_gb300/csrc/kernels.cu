@@ -707,8 +707,8 @@ __global__ void __launch_bounds__(256) k_ana2d_level(const T* __restrict__ src, 
 // reports it as UW_ERR_TIMEOUT).
 // ---------------------------------------------------------------------------
 struct GridBarrier {
-  unsigned int count;   // CTAs arrived at the current barrier
-  unsigned int gen;     // barriers completed (wraps)
+  unsigned int count;   // arrivals since the launch began (barrier k completes at (k + 1) x CTAs)
+  unsigned int exits;   // CTAs that have finished the launch
   unsigned int err;     // set when a wait gave up
   unsigned int pad;
 };
@@ -726,48 +726,54 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-
+__device__ __forceinline__ void red_add_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, unsigned int v) {
   unsigned int old;
   asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;\n" : "=r"(old) : "l"(p), "r"(v) : "memory");
   return old;
 }
-__device__ __forceinline__ void red_add_release_u32(unsigned int* p, unsigned int v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
-}
 
-// Grid barrier: each CTA's thread 0 arrives with an acquire-release
-// increment (after the CTA barrier, so it releases the whole CTA's writes);
-// the last to arrive resets the count and bumps the generation with a
-// release; the others poll the generation with relaxed loads and finish with
-// one acquire load.  Returns false (in every thread of the CTA) if the wait
-// gave up.
-__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int nblocks, unsigned int limit) {
+// Grid barrier number k of a launch: each CTA's thread 0 adds one arrival
+// with a release (after the CTA barrier, so it releases the whole CTA's
+// writes) and polls the count with relaxed loads until all (k + 1) x
+// nblocks arrivals are in, then reads it once with acquire semantics.  The
+// count only grows during a launch; grid_exit resets it.  Returns false (in
+// every thread of the CTA) if the wait gave up.
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int nblocks, int k, unsigned int limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned int g = ld_relaxed_u32(&bar->gen);
-    const unsigned int arrived = atom_add_acq_rel_u32(&bar->count, 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(&bar->count, 0u);
-      red_add_release_u32(&bar->gen, 1u);
-    } else {
-      unsigned int it = 0;
-      while (ld_relaxed_u32(&bar->gen) == g) {
-        if (++it > limit) {
-          atomicExch(&bar->err, 1u);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    const unsigned int target = (unsigned int)(k + 1) * nblocks;
+    red_add_release_u32(&bar->count, 1u);
+    unsigned int it = 0;
+    while (ld_relaxed_u32(&bar->count) < target) {
+      if (++it > limit) {
+        atomicExch(&bar->err, 1u);
+        ok = 0;
+        break;
       }
-      (void)ld_acquire_u32(&bar->gen);
+      __nanosleep(32);
     }
+    (void)ld_acquire_u32(&bar->count);
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Every CTA calls this once at the end of the launch (also after a wait gave
+// up); the last one resets the arrival count for the next launch on the stream.
+__device__ __forceinline__ void grid_exit(GridBarrier* bar, unsigned int nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (atom_add_acq_rel_u32(&bar->exits, 1u) + 1u == nblocks) {
+      atomicExch(&bar->count, 0u);
+      atomicExch(&bar->exits, 0u);
+    }
+  }
 }
 
 // level buffers of the forward synthesis: level it (j = J0 + it) reads
@@ -919,24 +925,31 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
         o[e] = acc;
       }
       if (!per) {
-        if (c0 == 0 && 8 * g < Lb) {
+        // edge corrections: the p lo and p hi inputs at the end into
+        // registers, then unrolled dot products (loads issued up front)
+        const bool left = c0 == 0 && 8 * g < Lb, right = c0 + TS == n1 && c0 + 8 * g + 8 > n1 - Lb;
+        if (left || right) {
+          const int m0e = left ? PM / 2 : n0 - p - ic0;
+          const T* D = left ? Dl : Dr;
+          T xe[2 * PM];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int k = 8 * g + e;
-            if (k < Lb)
-              for (int c = 0; c < 2 * p; ++c)
-                o[e] = fma(Dl[k * 2 * p + c], c < p ? rlo[c + PM / 2] : rhi[c - p + PM / 2], o[e]);
+          for (int e = 0; e < PM; ++e) {
+            xe[e] = rlo[m0e + e];
+            xe[PM + e] = rhi[m0e + e];
           }
-        }
-        if (c0 + TS == n1 && c0 + 8 * g + 8 > n1 - Lb) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const int r = c0 + 8 * g + e - (n1 - Lb);
-            if (r >= 0)
-              for (int c = 0; c < 2 * p; ++c) {
-                const int m = n0 - p + (c < p ? c : c - p) - ic0;
-                o[e] = fma(Dr[r * 2 * p + c], c < p ? rlo[m] : rhi[m], o[e]);
+            const int r = left ? 8 * g + e : c0 + 8 * g + e - (n1 - Lb);
+            if (r >= 0 && r < 3 * PM - 1) {        // rows past Lb and columns past p weigh zero
+              const T* dr = D + r * 2 * PM;
+              T acc = o[e];
+#pragma unroll
+              for (int c = 0; c < PM; ++c) {
+                acc = fma(dr[c], xe[c], acc);
+                acc = fma(dr[PM + c], xe[PM + c], acc);
               }
+              o[e] = acc;
+            }
           }
         }
       }
@@ -970,24 +983,29 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
         o[e] = acc;
       }
       if (!per) {
-        if (r0 == 0 && 4 * g4 < Lb) {
+        const bool top = r0 == 0 && 4 * g4 < Lb, bottom = r0 + TS == n1 && r0 + 4 * g4 + 4 > n1 - Lb;
+        if (top || bottom) {
+          const int m0e = top ? PM / 2 : n0 - p - ir0;
+          const T* D = top ? Dl : Dr;
+          T xe[2 * PM];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int k = 4 * g4 + e;
-            if (k < Lb)
-              for (int c = 0; c < 2 * p; ++c)
-                o[e] = fma(Dl[k * 2 * p + c], H[((c < p ? 0 : NR) + (c < p ? c : c - p) + PM / 2) * TS + cc], o[e]);
+          for (int e = 0; e < PM; ++e) {
+            xe[e] = H[(m0e + e) * TS + cc];
+            xe[PM + e] = H[(NR + m0e + e) * TS + cc];
           }
-        }
-        if (r0 + TS == n1 && r0 + 4 * g4 + 4 > n1 - Lb) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int r = r0 + 4 * g4 + e - (n1 - Lb);
-            if (r >= 0)
-              for (int c = 0; c < 2 * p; ++c) {
-                const int m = n0 - p + (c < p ? c : c - p) - ir0;
-                o[e] = fma(Dr[r * 2 * p + c], H[((c < p ? 0 : NR) + m) * TS + cc], o[e]);
+            const int r = top ? 4 * g4 + e : r0 + 4 * g4 + e - (n1 - Lb);
+            if (r >= 0 && r < 3 * PM - 1) {
+              const T* dr = D + r * 2 * PM;
+              T acc = o[e];
+#pragma unroll
+              for (int c = 0; c < PM; ++c) {
+                acc = fma(dr[c], xe[c], acc);
+                acc = fma(dr[PM + c], xe[PM + c], acc);
               }
+              o[e] = acc;
+            }
           }
         }
       }
@@ -1063,28 +1081,29 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
         hi[e] = x1;
       }
       if (!per) {
-        if (m0 == 0 && 4 * g < p) {
+        // edge corrections (transposed): the Lb inputs at the end into
+        // registers, then unrolled dot products
+        const bool top = m0 == 0 && 4 * g < p, bottom = m0 + TSA == n0 && m0 + 4 * g + 4 > n0 - p;
+        if (top || bottom) {
+          constexpr int LBM = 3 * PM - 1;             // >= Lb = 3p - 1
+          const int k0e = top ? -ir0 : n1 - Lb - ir0;
+          const T* D = top ? Dl : Dr;
+          T xe[LBM];
+#pragma unroll
+          for (int k = 0; k < LBM; ++k) xe[k] = S[min(k0e + k, NR - 1) * NRP + c];   // rows past Lb weigh zero
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int mm = 4 * g + e;
-            if (mm < p)
-              for (int k = 0; k < Lb; ++k) {
-                const T v = S[(k - ir0) * NRP + c];
-                lo[e] = fma(Dl[k * 2 * p + mm], v, lo[e]);
-                hi[e] = fma(Dl[k * 2 * p + p + mm], v, hi[e]);
-              }
-          }
-        }
-        if (m0 + TSA == n0 && m0 + 4 * g + 4 > n0 - p) {
+            const int col = top ? 4 * g + e : m0 + 4 * g + e - (n0 - p);
+            if (col >= 0 && col < PM) {
+              T x0 = lo[e], x1 = hi[e];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int ee = m0 + 4 * g + e - (n0 - p);
-            if (ee >= 0)
-              for (int r = 0; r < Lb; ++r) {
-                const T v = S[(n1 - Lb + r - ir0) * NRP + c];
-                lo[e] = fma(Dr[r * 2 * p + ee], v, lo[e]);
-                hi[e] = fma(Dr[r * 2 * p + p + ee], v, hi[e]);
+              for (int k = 0; k < LBM; ++k) {
+                x0 = fma(D[k * 2 * PM + col], xe[k], x0);
+                x1 = fma(D[k * 2 * PM + PM + col], xe[k], x1);
               }
+              lo[e] = x0;
+              hi[e] = x1;
+            }
           }
         }
       }
@@ -1120,28 +1139,27 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
         hi[e] = x1;
       }
       if (!per) {
-        if (k0 == 0 && 4 * g < p) {
+        const bool left = k0 == 0 && 4 * g < p, right = k0 + TSA == n0 && k0 + 4 * g + 4 > n0 - p;
+        if (left || right) {
+          constexpr int LBM = 3 * PM - 1;
+          const int k0e = left ? -ic0 : n1 - Lb - ic0;
+          const T* D = left ? Dl : Dr;
+          T xe[LBM];
+#pragma unroll
+          for (int k = 0; k < LBM; ++k) xe[k] = hr[min(k0e + k, NR - 1)];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int kk = 4 * g + e;
-            if (kk < p)
-              for (int k = 0; k < Lb; ++k) {
-                const T v = hr[k - ic0];
-                lo[e] = fma(Dl[k * 2 * p + kk], v, lo[e]);
-                hi[e] = fma(Dl[k * 2 * p + p + kk], v, hi[e]);
-              }
-          }
-        }
-        if (k0 + TSA == n0 && k0 + 4 * g + 4 > n0 - p) {
+            const int col = left ? 4 * g + e : k0 + 4 * g + e - (n0 - p);
+            if (col >= 0 && col < PM) {
+              T x0 = lo[e], x1 = hi[e];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int ee = k0 + 4 * g + e - (n0 - p);
-            if (ee >= 0)
-              for (int r = 0; r < Lb; ++r) {
-                const T v = hr[n1 - Lb + r - ic0];
-                lo[e] = fma(Dr[r * 2 * p + ee], v, lo[e]);
-                hi[e] = fma(Dr[r * 2 * p + p + ee], v, hi[e]);
+              for (int k = 0; k < LBM; ++k) {
+                x0 = fma(D[k * 2 * PM + col], xe[k], x0);
+                x1 = fma(D[k * 2 * PM + PM + col], xe[k], x1);
               }
+              lo[e] = x0;
+              hi[e] = x1;
+            }
           }
         }
       }
@@ -1168,7 +1186,7 @@ __host__ __device__ inline int syn_rw_ts(int n1) { return n1 >= 32 ? 32 : (n1 >=
 __host__ __device__ inline int ana_rw_ts(int n0) { return n0 >= 16 ? 16 : (n0 >= 8 ? 8 : 0); }
 
 template <typename T, int PM>
-__global__ void __launch_bounds__(256) k_syn2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, const __grid_constant__ CTaps<T, PM> ct,
+__global__ void __launch_bounds__(256, 2) k_syn2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, const __grid_constant__ CTaps<T, PM> ct,
                                                       const T* __restrict__ Dg, int rw, GridBarrier* bar,
                                                       unsigned int limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1177,10 +1195,16 @@ __global__ void __launch_bounds__(256) k_syn2d_levels(CoarseIO<T> io, Tables<T> 
   SmemTables<T> st;
   int off = stage_filters(tab, G, sm, st, tid, nthr);
   const bool per = G.bd == UW_BOUNDARY_PERIODIC;
-  const int nD = per ? 0 : 4 * G.Lb * G.p;
+  // edge corrections, zero-padded to compile-time bounds: [side][3PM-1 rows][2PM cols]
+  constexpr int LBM = 3 * PM - 1, DW = 2 * PM;
+  const int nD = per ? 0 : 2 * LBM * DW;
   T* Dl = sm + off;
-  for (int i = tid; i < nD; i += nthr) Dl[i] = Dg[i];
-  const T* Dr = Dl + 2 * G.Lb * G.p;
+  for (int i = tid; i < nD; i += nthr) {
+    const int side = i / (LBM * DW), rem = i - side * (LBM * DW), r = rem / DW, c = rem - r * DW;
+    const int e = c < PM ? c : c - PM;
+    Dl[i] = (r < G.Lb && e < G.p) ? Dg[(side * G.Lb + r) * 2 * G.p + (c < PM ? e : G.p + e)] : T(0);
+  }
+  const T* Dr = Dl + LBM * DW;
   off = cup(off + nD, 4);
   const int M = io.M, Mh = M / 2;
   const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
@@ -1203,12 +1227,13 @@ __global__ void __launch_bounds__(256) k_syn2d_levels(CoarseIO<T> io, Tables<T> 
         syn2d_tile<T, 0>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, TS, st, sm + off, G,
                          tid, nthr);
     }
-    if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, limit)) return;
+    if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, it, limit)) break;
   }
+  grid_exit(bar, gridDim.x);
 }
 
 template <typename T, int PM>
-__global__ void __launch_bounds__(256) k_ana2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, const __grid_constant__ CTaps<T, PM> ct,
+__global__ void __launch_bounds__(256, 2) k_ana2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, const __grid_constant__ CTaps<T, PM> ct,
                                                       const T* __restrict__ Dg, int rw, GridBarrier* bar,
                                                       unsigned int limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1217,10 +1242,16 @@ __global__ void __launch_bounds__(256) k_ana2d_levels(CoarseIO<T> io, Tables<T> 
   SmemTables<T> st;
   int off = stage_filters(tab, G, sm, st, tid, nthr);
   const bool per = G.bd == UW_BOUNDARY_PERIODIC;
-  const int nD = per ? 0 : 4 * G.Lb * G.p;
+  // edge corrections, zero-padded to compile-time bounds: [side][3PM-1 rows][2PM cols]
+  constexpr int LBM = 3 * PM - 1, DW = 2 * PM;
+  const int nD = per ? 0 : 2 * LBM * DW;
   T* Dl = sm + off;
-  for (int i = tid; i < nD; i += nthr) Dl[i] = Dg[i];
-  const T* Dr = Dl + 2 * G.Lb * G.p;
+  for (int i = tid; i < nD; i += nthr) {
+    const int side = i / (LBM * DW), rem = i - side * (LBM * DW), r = rem / DW, c = rem - r * DW;
+    const int e = c < PM ? c : c - PM;
+    Dl[i] = (r < G.Lb && e < G.p) ? Dg[(side * G.Lb + r) * 2 * G.p + (c < PM ? e : G.p + e)] : T(0);
+  }
+  const T* Dr = Dl + LBM * DW;
   off = cup(off + nD, 4);
   const int M = io.M, Mh = M / 2;
   const int64_t HH = (int64_t)Mh * Mh;
@@ -1243,8 +1274,9 @@ __global__ void __launch_bounds__(256) k_ana2d_levels(CoarseIO<T> io, Tables<T> 
         ana2d_tile<T, 0>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, TS, st,
                          sm + off, G, tid, nthr);
     }
-    if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, limit)) return;
+    if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, it, limit)) break;
   }
+  grid_exit(bar, gridDim.x);
 }
 
 // FP32 transpose with 64 x 64 tiles and 16-byte global accesses; rows,
@@ -1723,7 +1755,7 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
   bool ok = false;
   pm_dispatch(G.p, [&](auto pc) {
     constexpr int PM = decltype(pc)::value;
-    const size_t head = (size_t)cup(cup(4 * G.p, 4) + (P.bd == UW_BOUNDARY_PERIODIC ? 0 : 4 * G.Lb * G.p), 4);
+    const size_t head = (size_t)cup(cup(4 * G.p, 4) + (P.bd == UW_BOUNDARY_PERIODIC ? 0 : 2 * (3 * PM - 1) * 2 * PM), 4);
     size_t sm = 0;
     int max_tiles = 0;
     double bytes = 0;
