@@ -18,10 +18,11 @@
 // padding beyond its ends (periodic plans: wrapped copies in halos).  Near a
 // VMP boundary the exact operator differs from that by C x_edge, where
 // x_edge holds the p lo and p hi coefficients at that end and C reaches only
-// the first / last K outputs of T (built on the host, tc_plan.cpp); warp 0
-// and the last warp compute these corrections while the others run (A), and
-// the owners add them before the bits 0-3 stage.  The adjoint adds C^T
-// applied to the first / last K transformed samples to the 2p edge outputs.
+// the first / last K outputs of T (built on the host, tc_plan.cpp); the rows
+// of C are spread over the CTA during (A), and the owners of the affected
+// outputs add them before the bits 0-3 stage.  The adjoint adds C^T applied
+// to the first / last K transformed samples to the 2p edge outputs (8 lanes
+// per output, combined with shuffles).
 //
 // CTAs are persistent (N / 16 threads, one 16-output block per thread) and
 // copy the next line (and its sample positions) into shared memory with
@@ -505,7 +506,13 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
     float* sV = sV0 + (scat ? 0 : buf * G::VLa);
     if (scat) {
       // zero the line, then scatter the staged samples to their natural positions
-      for (int k4 = tid; k4 < N / 4; k4 += NT) *reinterpret_cast<float4*>(sV + vp(VH + 4 * k4)) = make_float4(0.f, 0.f, 0.f, 0.f);
+      {
+        // element 4 (tid + NT i) sits at vp(VH + 4 tid) + 4 NT i (1 + 1/4 + 1/16): NT i is a multiple of 256
+        float* z = sV + vp(VH + 4 * tid);
+#pragma unroll
+        for (int i = 0; i < N / (4 * NT); ++i)
+          *reinterpret_cast<float4*>(z + vp(4 * NT * i)) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       __syncthreads();
       const uint16_t* ps = reinterpret_cast<const uint16_t*>(sP) + (cr0 & 1);
       const int cnt = cr1 - cr0;
@@ -559,10 +566,15 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
         const int side = oc >= 2 * a.p, c = oc - side * 2 * a.p;
         float acc = 0.f;
         if (act) {
-          const float* C = a.C + (size_t)side * a.K * a.CS + c;
+          const float* C = a.C + ((size_t)side * a.K + (size_t)part * kp) * a.CS + c;
           const int kbase = (side == 0 ? 0 : N - a.K) + part * kp;
-          for (int k = 0; k < kp; ++k)
-            acc = fmaf(__ldg(C + (size_t)(part * kp + k) * a.CS), sV[vp(VH + kbase + k)], acc);
+          if (kp == 8 && (kbase & 7) == 0) {        // an aligned run of 8 inside one 16-block
+            const float* v = sV + vp(VH + kbase);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc = fmaf(__ldg(C + k * a.CS), v[k], acc);
+          } else {
+            for (int k = 0; k < kp; ++k) acc = fmaf(__ldg(C + (size_t)k * a.CS), sV[vp(VH + kbase + k)], acc);
+          }
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
@@ -575,10 +587,17 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
       const int m0 = BS * tid;
       const int e0 = Q * m0 - Q * (PM - 1) - G::OFFT;     // multiple of 4
       float wv[G::NWT];
+      {
+        // the window starts at 16 tid + (16 - Q (PM - 1) - OFFT) mod 16 inside a
+        // 16-block; the padded address of each 16-block is computed once
+        constexpr int S0 = ((-(Q * (PM - 1) + G::OFFT)) % 16 + 16) % 16;     // offset of e0 in its block
+        const int blk0 = VH + e0 - S0;                                        // multiple of 16
 #pragma unroll
-      for (int w = 0; w < G::NWT; w += 4) {
-        const float4 u = *reinterpret_cast<const float4*>(sV + vp(VH + e0 + w));
-        wv[w] = u.x; wv[w + 1] = u.y; wv[w + 2] = u.z; wv[w + 3] = u.w;
+        for (int w = 0; w < G::NWT; w += 4) {
+          const int rel = S0 + w;                                             // compile-time
+          const float4 u = *reinterpret_cast<const float4*>(sV + vp(blk0 + 16 * (rel >> 4)) + (rel & 15));
+          wv[w] = u.x; wv[w + 1] = u.y; wv[w + 2] = u.z; wv[w + 3] = u.w;
+        }
       }
       float s[BS];
 #pragma unroll
