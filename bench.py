@@ -435,7 +435,7 @@ def run_ours(args):
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
-        cb = oracle_pair_rate(lines=128)
+        cb = oracle_pair_rate(lines=384)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
     if dist:
