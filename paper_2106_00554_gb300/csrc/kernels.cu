@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -784,6 +785,7 @@ struct CoarseIO {
   T* xout;       // adjoint output (Mallat layout)
   T* XS;
   T* XS2;
+  T* XT;         // transposed full-size buffer of the line passes, or null (see tx_share)
   int M, J0, nl, batch;
 };
 
@@ -857,7 +859,8 @@ template <typename T, int PM, int TS>
 __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc, int64_t ldll,
                                             int64_t llb, const T* __restrict__ x, int M, T* __restrict__ dst,
                                             int64_t lddst, int64_t dstb, int j, const CTaps<T, PM>& ct, const T* Dl,
-                                            const T* Dr, int p, int Lb, bool per, T* smem, int tid, int nthr) {
+                                            const T* Dr, int p, int Lb, bool per, T* smem, int tid, int nthr,
+                                            T* xt = nullptr) {
   using SG = SynGeom<T, PM, TS>;
   constexpr int NR = SG::NR, NC = SG::NC, NCP = SG::NCP, NWR = SG::NWR;
   const int n0 = 1 << j, n1 = 2 * n0;
@@ -1009,8 +1012,23 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
           }
         }
       }
+      if (xt) {
+        // transposed output: staged in the (no longer read) subband windows
 #pragma unroll
-      for (int e = 0; e < 4; ++e) dst[b * dstb + (int64_t)(r0 + 4 * g4 + e) * lddst + c0 + cc] = o[e];
+        for (int e = 0; e < 4; ++e) W[cc * (TS + 1) + 4 * g4 + e] = o[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dst[b * dstb + (int64_t)(r0 + 4 * g4 + e) * lddst + c0 + cc] = o[e];
+      }
+    }
+  }
+  if (xt) {
+    // row c0 + rr of the M x M transposed buffer, columns r0 .. r0 + TS - 1
+    __syncthreads();
+    T* xtb = xt + b * (int64_t)M * M;
+    for (int e = tid; e < TS * TS; e += nthr) {
+      const int rr = e / TS, cl = e - rr * TS;
+      xtb[(int64_t)(c0 + rr) * M + r0 + cl] = W[rr * (TS + 1) + cl];
     }
   }
 }
@@ -1019,7 +1037,8 @@ template <typename T, int PM, int TSA>
 __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, int64_t ldsrc,
                                             int64_t srcb, T* x, int M, T* lldst,
                                             int64_t ldll, int64_t llb, int j, const CTaps<T, PM>& ct, const T* Dl,
-                                            const T* Dr, int p, int Lb, bool per, T* smem, int tid, int nthr) {
+                                            const T* Dr, int p, int Lb, bool per, T* smem, int tid, int nthr,
+                                            const T* xt = nullptr) {
   using AG = AnaGeom<T, PM, TSA>;
   constexpr int NR = AG::NR, NRP = AG::NRP, NWA = AG::NWA, NCH = AG::NCH;
   const int n0 = 1 << j, n1 = 2 * n0;
@@ -1030,14 +1049,17 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
   T* Hc = S + AG::HOFF;           // [2][TSA][NCH]: column analysis, lo then hi
   const T* sb = src + b * srcb;
   {
+    // xt: the level is read transposed from the M x M buffer (window rows
+    // run fastest over the threads, so the loads stay coalesced)
     constexpr int TOT = NR * NR, CNT = (TOT + 255) / 256;
+    const T* xtb = xt ? xt + b * (int64_t)M * M : nullptr;
     T v[CNT];
 #pragma unroll
     for (int u = 0; u < CNT; ++u) {
       const int e = tid + u * 256;
       v[u] = T(0);
       if (e < TOT) {
-        const int i = e / NR, c = e - i * NR;
+        const int i = xt ? e % NR : e / NR, c = xt ? e / NR : e % NR;
         int gi = ir0 + i, gc = ic0 + c;
         bool ok = true;
         if (per) {
@@ -1046,14 +1068,14 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
         } else {
           ok = gi >= 0 && gi < n1 && gc >= 0 && gc < n1;
         }
-        if (ok) v[u] = sb[(int64_t)gi * ldsrc + gc];
+        if (ok) v[u] = xt ? xtb[(int64_t)gc * M + gi] : sb[(int64_t)gi * ldsrc + gc];
       }
     }
 #pragma unroll
     for (int u = 0; u < CNT; ++u) {
       const int e = tid + u * 256;
       if (e < TOT) {
-        const int i = e / NR, c = e - i * NR;
+        const int i = xt ? e % NR : e / NR, c = xt ? e / NR : e % NR;
         S[i * NRP + c] = v[u];
       }
     }
@@ -1185,6 +1207,74 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
 __host__ __device__ inline int syn_rw_ts(int n1) { return n1 >= 32 ? 32 : (n1 >= 16 ? 16 : 0); }
 __host__ __device__ inline int ana_rw_ts(int n0) { return n0 >= 16 ? 16 : (n0 >= 8 ? 8 : 0); }
 
+// The line passes work on the transpose XT of the M x M coefficient array
+// (S_{R-1} in the top-left Mh x Mh block, the level R-1 details in the other
+// three quadrants).  The fused coarse-level launches make that layout change
+// themselves: the forward writes its last level transposed into XT and the
+// adjoint reads its first level transposed from XT, and the three detail
+// quadrants move as 64 x 64 tile transposes given to the CTAs that a small
+// level leaves idle.  Steps take at most one item per idle CTA, in order
+// (forward: steps 0 .. nl-2, adjoint: steps 1 .. nl-1); the rest rides with
+// step nl-1.  Step it runs items [q0, q0 + nq) of Q after its level tiles.
+template <typename F>
+__device__ __forceinline__ void tx_share(int it, int nl, bool fwd, int grid, int Q, F&& busy, int& q0, int& nq) {
+  int used = 0;
+  q0 = 0;
+  nq = 0;
+  for (int s = 0; s < nl - 1; ++s) {
+    const int k = fwd ? s : s + 1;
+    const int take = min(Q - used, max(0, grid - busy(k)));
+    if (k == it) {
+      q0 = used;
+      nq = take;
+    }
+    used += take;
+  }
+  if (it == nl - 1) {
+    if (fwd) q0 = used;   // forward: step nl-1 has no share of its own
+    nq += Q - used;       // adjoint: the rest follows its own share
+  }
+}
+
+// dst[(b0 + c) M + a0 + r] = src[(a0 + r) M + b0 + c], r, c < 64 (256 threads)
+template <typename T>
+__device__ __forceinline__ void tx_tile(const T* src, T* dst, int a0, int b0, int M, T* smem, int tid) {
+  constexpr int CNT = 64 * 64 / 256;
+  T v[CNT];
+#pragma unroll
+  for (int u = 0; u < CNT; ++u) {
+    const int e = tid + 256 * u, r = e >> 6, c = e & 63;
+    v[u] = src[(int64_t)(a0 + r) * M + b0 + c];
+  }
+#pragma unroll
+  for (int u = 0; u < CNT; ++u) {
+    const int e = tid + 256 * u;
+    smem[(e >> 6) * 65 + (e & 63)] = v[u];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < CNT; ++u) {
+    const int e = tid + 256 * u, rr = e >> 6, cl = e & 63;
+    dst[(int64_t)(b0 + rr) * M + a0 + cl] = smem[cl * 65 + rr];
+  }
+}
+
+// item q of the detail-quadrant transposes: instance, quadrant (0: rows
+// [0, Mh) x columns [Mh, M), 1: [Mh, M) x [0, Mh), 2: [Mh, M) x [Mh, M)),
+// 64 x 64 tile; forward x -> XT, adjoint XT -> x
+template <typename T>
+__device__ __forceinline__ void tx_item(int q, int M, const T* src, T* dst, bool fwd, T* smem, int tid) {
+  const int Mh = M / 2, nb = Mh / 64, per_b = 3 * nb * nb;
+  const int b = q / per_b;
+  int r = q - b * per_b;
+  const int d = r / (nb * nb);
+  r -= d * nb * nb;
+  const int R0 = (d >= 1 ? Mh : 0) + (r / nb) * 64, C0 = (d != 1 ? Mh : 0) + (r % nb) * 64;
+  const int64_t off = (int64_t)b * M * M;
+  if (fwd) tx_tile(src + off, dst + off, R0, C0, M, smem, tid);
+  else tx_tile(src + off, dst + off, C0, R0, M, smem, tid);
+}
+
 template <typename T, int PM>
 __global__ void __launch_bounds__(256, 2) k_syn2d_levels(CoarseIO<T> io, Tables<T> tab, Geo G, const __grid_constant__ CTaps<T, PM> ct,
                                                       const T* __restrict__ Dg, int rw, GridBarrier* bar,
@@ -1206,8 +1296,18 @@ __global__ void __launch_bounds__(256, 2) k_syn2d_levels(CoarseIO<T> io, Tables<
   }
   const T* Dr = Dl + LBM * DW;
   off = cup(off + nD, 4);
+  // constant tables staged: let the next kernel launch, then wait for the
+  // previous grid (x may be its output)
+  pdl_trigger();
+  pdl_wait();
   const int M = io.M, Mh = M / 2;
   const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
+  const bool tx = io.XT != nullptr;
+  const int Q = tx ? 3 * (Mh / 64) * (Mh / 64) * io.batch : 0;
+  auto busy = [&](int k) {
+    const int n1 = 2 << (io.J0 + k), TR = rw ? syn_rw_ts(n1) : 0, TS = TR ? TR : syn_tile(n1);
+    return (n1 / TS) * (n1 / TS) * io.batch;
+  };
   for (int it = 0; it < io.nl; ++it) {
     const int j = io.J0 + it, n1 = 2 << j;
     const int TR = rw ? syn_rw_ts(n1) : 0;
@@ -1215,14 +1315,20 @@ __global__ void __launch_bounds__(256, 2) k_syn2d_levels(CoarseIO<T> io, Tables<
     const T* src = it == 0 ? io.x : ((io.nl - it) % 2 == 0 ? io.XS : io.XS2);
     const int64_t ld = it == 0 ? M : Mh, sb = it == 0 ? MM : HH;
     T* dst = (io.nl - 1 - it) % 2 == 0 ? io.XS : io.XS2;
-    for (int t = blockIdx.x; t < tiles * io.batch; t += gridDim.x) {
+    T* xt = tx && it == io.nl - 1 ? io.XT : nullptr;
+    const int TB = tiles * io.batch;
+    int q0 = 0, nq = 0;
+    if (tx) tx_share(it, io.nl, true, (int)gridDim.x, Q, busy, q0, nq);
+    for (int t = blockIdx.x; t < TB + nq; t += gridDim.x) {
       __syncthreads();   // the previous tile's windows are no longer read
-      if (TR == 32)
+      if (t >= TB)
+        tx_item(q0 + t - TB, M, io.x, io.XT, true, sm + off, tid);
+      else if (TR == 32)
         syn_tile_rw<T, PM, 32>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, ct, Dl, Dr, G.p,
-                               G.Lb, per, sm + off, tid, nthr);
+                               G.Lb, per, sm + off, tid, nthr, xt);
       else if (TR == 16)
         syn_tile_rw<T, PM, 16>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, ct, Dl, Dr, G.p,
-                               G.Lb, per, sm + off, tid, nthr);
+                               G.Lb, per, sm + off, tid, nthr, xt);
       else
         syn2d_tile<T, 0>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, TS, st, sm + off, G,
                          tid, nthr);
@@ -1253,23 +1359,37 @@ __global__ void __launch_bounds__(256, 2) k_ana2d_levels(CoarseIO<T> io, Tables<
   }
   const T* Dr = Dl + LBM * DW;
   off = cup(off + nD, 4);
+  pdl_trigger();
+  pdl_wait();
   const int M = io.M, Mh = M / 2;
   const int64_t HH = (int64_t)Mh * Mh;
   const int R = io.J0 + io.nl + 1;
+  const bool tx = io.XT != nullptr;
+  const int Q = tx ? 3 * (Mh / 64) * (Mh / 64) * io.batch : 0;
+  auto busy = [&](int k) {
+    const int n0 = 1 << (R - 2 - k), TR = rw ? ana_rw_ts(n0) : 0, TS = TR ? TR : ana_tile(n0);
+    return (n0 / TS) * (n0 / TS) * io.batch;
+  };
   for (int it = 0; it < io.nl; ++it) {
     const int j = R - 2 - it, n0 = 1 << j;
     const int TR = rw ? ana_rw_ts(n0) : 0;
     const int TS = TR ? TR : ana_tile(n0), tiles = (n0 / TS) * (n0 / TS);
     const T* src = it % 2 == 0 ? io.XS : io.XS2;
     T* dst = it == io.nl - 1 ? nullptr : (it % 2 == 0 ? io.XS2 : io.XS);
-    for (int t = blockIdx.x; t < tiles * io.batch; t += gridDim.x) {
+    const T* xt = tx && it == 0 ? io.XT : nullptr;
+    const int TB = tiles * io.batch;
+    int q0 = 0, nq = 0;
+    if (tx) tx_share(it, io.nl, false, (int)gridDim.x, Q, busy, q0, nq);
+    for (int t = blockIdx.x; t < TB + nq; t += gridDim.x) {
       __syncthreads();
-      if (TR == 16)
+      if (t >= TB)
+        tx_item(q0 + t - TB, M, (const T*)io.XT, io.xout, false, sm + off, tid);
+      else if (TR == 16)
         ana_tile_rw<T, PM, 16>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, ct,
-                               Dl, Dr, G.p, G.Lb, per, sm + off, tid, nthr);
+                               Dl, Dr, G.p, G.Lb, per, sm + off, tid, nthr, xt);
       else if (TR == 8)
         ana_tile_rw<T, PM, 8>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, ct,
-                              Dl, Dr, G.p, G.Lb, per, sm + off, tid, nthr);
+                              Dl, Dr, G.p, G.Lb, per, sm + off, tid, nthr, xt);
       else
         ana2d_tile<T, 0>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, TS, st,
                          sm + off, G, tid, nthr);
@@ -1738,10 +1858,22 @@ static void pm_dispatch(int p, F&& f) {
   else f(std::integral_constant<int, 10>{});
 }
 
+// whether the fused coarse-level launch also makes the layout change of the
+// line passes' transposed buffer (needs the register-window tiles at the
+// finest coarse level and 64-aligned quadrants)
+static bool coarse_tx_ok(const Plan& P) {
+  const int nl = P.R - 1 - P.J0;
+  return nl >= 2 && P.d_sync && P.coarse_ok && P.M % 128 == 0 &&
+         (P.bd == UW_BOUNDARY_PERIODIC || P.d_coarse) && !getenv_flag("UW_COARSE_PER_LEVEL") &&
+         !getenv_flag("UW_COARSE_GENERIC") && !getenv_flag("UW_COARSE_SEPARATE_TRANSPOSE");
+}
+
 // All coarse levels in one cooperative launch (grid barrier between levels);
 // false if that launch is not possible here (then one launch per level).
+// XT non-null (only when coarse_tx_ok): the launch also moves the M x M
+// coefficient array between x and its transpose XT.
 template <typename T>
-static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout, T* XS, T* XS2, int batch,
+static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout, T* XS, T* XS2, T* XT, int batch,
                                 bool fwd, Launcher& L) {
   const int nl = P.R - 1 - P.J0;
   if (nl < 2 || !P.d_sync || getenv_flag("UW_COARSE_PER_LEVEL")) return false;
@@ -1789,7 +1921,14 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
       sm = std::max(sm, sizeof(T) * (head + el));
       bytes += sizeof(T) * (double)batch * (4.0 * n0 * n0 + (double)n1 * n1);
     }
-    CoarseIO<T> io{x, xout, XS, XS2, P.M, P.J0, nl, batch};
+    int Q = 0;
+    if (XT) {
+      const int Mh = P.M / 2;
+      Q = 3 * (Mh / 64) * (Mh / 64) * batch;
+      sm = std::max(sm, sizeof(T) * (head + 64 * 65));
+      bytes += sizeof(T) * (double)batch * 6.0 * Mh * Mh;
+    }
+    CoarseIO<T> io{x, xout, XS, XS2, XT, P.M, P.J0, nl, batch};
     const CTaps<T, PM> ct = make_ctaps<T, PM>(P);
     auto kern = fwd ? k_syn2d_levels<T, PM> : k_ana2d_levels<T, PM>;
     set_smem_limit((const void*)kern);
@@ -1802,20 +1941,40 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
       return;
     }
     // at most two CTAs per SM: fewer arrivals at each grid barrier
-    const int grid = (int)std::min<int64_t>((int64_t)std::min(per, 2) * nsm, (int64_t)max_tiles * batch);
+    const int grid = (int)std::min<int64_t>((int64_t)std::min(per, 2) * nsm, (int64_t)max_tiles * batch + Q);
     L.pre(fwd ? "idwt2d_levels" : "dwt2d_levels", bytes);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = L.s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    L.note(cudaLaunchKernelEx(&cfg, kern, io, tabs<T>(P), G, ct, Dg, rw ? 1 : 0, (GridBarrier*)P.d_sync,
-                              barrier_spin_limit()));
+    // cooperative launch with programmatic serialization where the driver
+    // takes it (first decided by a launch outside stream capture)
+    static std::atomic<int> coop_pdl{-1};
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(L.s, &cap);
+    const int known = coop_pdl.load();
+    cfg.numAttrs = known == 1 || (known < 0 && cap == cudaStreamCaptureStatusNone) ? 2 : 1;
+    auto go = [&] {
+      return cudaLaunchKernelEx(&cfg, kern, io, tabs<T>(P), G, ct, Dg, rw ? 1 : 0, (GridBarrier*)P.d_sync,
+                                barrier_spin_limit());
+    };
+    cudaError_t err = go();
+    if (known < 0 && cfg.numAttrs == 2) {
+      coop_pdl.store(err == cudaSuccess ? 1 : 0);
+      if (err != cudaSuccess) {
+        cudaGetLastError();
+        cfg.numAttrs = 1;
+        err = go();
+      }
+    }
+    L.note(err);
     L.check();
     ok = true;
   });
@@ -1823,9 +1982,29 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
 }
 
 template <typename T>
-static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xout, T* XS, T* XS2, int batch,
+static void launch_transpose(const T* in, T* out, int rows, int cols, int64_t in_batch, int64_t out_batch,
+                             const T* alt, int64_t alt_batch, T* altout, int br, int bc, int ldalt, int batch,
+                             Launcher& L);
+
+// the adjoint's layout change XT -> x (top-left Mh x Mh block into XS)
+template <typename T>
+static void transpose_out(const Plan& P, const T* XT, T* x, T* XS, int batch, Launcher& L) {
+  const int M = P.M, Mh = M / 2;
+  const int64_t MM = (int64_t)M * M;
+  L.pre("transpose_out", sizeof(T) * 2.0 * batch * MM);
+  launch_transpose<T>(XT, x, M, M, MM, MM, nullptr, (int64_t)Mh * Mh, XS, Mh, Mh, Mh, batch, L);
+  L.check();
+}
+
+// All coarse levels.  XT non-null: the caller leaves the layout change of the
+// transposed buffer to this call (forward: after the levels, adjoint: before);
+// true when the fused launch made it, false when the forward caller still has
+// to (the adjoint's fallback makes it here, ahead of the per-level launches).
+template <typename T>
+static bool launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xout, T* XS, T* XS2, T* XT, int batch,
                                  bool fwd, Launcher& L) {
-  if (launch_coarse_fused<T>(P, G, x, xout, XS, XS2, batch, fwd, L)) return;
+  if (launch_coarse_fused<T>(P, G, x, xout, XS, XS2, XT, batch, fwd, L)) return XT != nullptr;
+  if (XT && !fwd) transpose_out<T>(P, XT, xout, XS, batch, L);
   const int M = P.M, Mh = M / 2;
   const int nl = P.R - 1 - P.J0;
   const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
@@ -1835,7 +2014,7 @@ static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xou
     const int w = coarse_tile_extent(G, j, fwd);
     if (!fwd && w > 64) {  // the analysis column pass maps window columns to 64 lanes
       L.err = cudaErrorInvalidConfiguration;
-      return;
+      return false;
     }
     if (fwd) {
       const int TS = syn_tile(n1), tiles = n1 / TS;
@@ -1871,6 +2050,7 @@ static void launch_coarse_levels(const Plan& P, const Geo& G, const T* x, T* xou
     }
     L.check();
   }
+  return false;
 }
 
 // transpose dispatcher: the 64 x 64 FP32 kernel where shapes allow
@@ -2024,12 +2204,13 @@ static void fwd2d(const Plan& P, const T* x, T* y, int batch, T* work, Launcher&
   T* VT = XT + (size_t)batch * MM;
   T* V = VT + (size_t)batch * M * N;
   const bool coarse = (P.R - 1 > P.J0);
-  if (coarse) {
-    launch_coarse_levels<T>(P, G, x, nullptr, XS, XS2, batch, true, L);
+  bool moved = false;
+  if (coarse) moved = launch_coarse_levels<T>(P, G, x, nullptr, XS, XS2, coarse_tx_ok(P) ? XT : nullptr, batch, true, L);
+  if (!moved) {
+    L.pre("transpose_in", e * 2.0 * batch * MM);
+    launch_transpose<T>(x, XT, M, M, MM, MM, coarse ? XS : nullptr, (int64_t)Mh * Mh, nullptr, Mh, Mh, Mh, batch, L);
+    L.check();
   }
-  L.pre("transpose_in", e * 2.0 * batch * MM);
-  launch_transpose<T>(x, XT, M, M, MM, MM, coarse ? XS : nullptr, (int64_t)Mh * Mh, nullptr, Mh, Mh, Mh, batch, L);
-  L.check();
   LineIO io{};
   io.in_stride = M; io.out_stride = N; io.lines = M; io.in_batch = MM; io.out_batch = (int64_t)M * N;
   io.seq_rows = 0; io.mode = 0; io.jlev = std::max(P.R - 1, P.J0);
@@ -2076,11 +2257,14 @@ static void adj2d(const Plan& P, const T* y, T* x, int batch, T* work, Launcher&
   L.pre("line_adj_dim1", e * (double)batch * (MM + (double)M * N));
   launch_line<T>(false, P, G, QT, XT, io2, batch * M, L);
   L.check();
-  L.pre("transpose_out", e * 2.0 * batch * MM);
-  launch_transpose<T>(XT, x, M, M, MM, MM, nullptr, (int64_t)Mh * Mh, coarse ? XS : nullptr, Mh, Mh, Mh, batch, L);
-  L.check();
-  if (coarse) {
-    launch_coarse_levels<T>(P, G, nullptr, x, XS, XS2, batch, false, L);
+  if (!coarse) {
+    L.pre("transpose_out", e * 2.0 * batch * MM);
+    launch_transpose<T>(XT, x, M, M, MM, MM, nullptr, (int64_t)Mh * Mh, nullptr, Mh, Mh, Mh, batch, L);
+    L.check();
+  } else {
+    const bool tx = coarse_tx_ok(P);
+    if (!tx) transpose_out<T>(P, XT, x, XS, batch, L);
+    launch_coarse_levels<T>(P, G, nullptr, x, XS, XS2, tx ? XT : nullptr, batch, false, L);
   }
 }
 

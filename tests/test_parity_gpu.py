@@ -145,11 +145,23 @@ def test_2d_sweep_against_dense(p, bd, dR, q):
         assert rel(run_adj(plan, y, prec), want_x) < TOL[prec]
 
 
+COARSE_PATHS = {"fused": None, "separate_transposes": "UW_COARSE_SEPARATE_TRANSPOSE",
+                "generic_tiles": "UW_COARSE_GENERIC", "per_level": "UW_COARSE_PER_LEVEL"}
+
+
+@pytest.mark.parametrize("path", list(COARSE_PATHS))
 @pytest.mark.parametrize("p,bd,R,q", [(5, VMP, 8, 1), (6, PERIODIC, 8, 1), (7, VMP, 7, 2), (8, VMP, 9, 1),
                                        (9, PERIODIC, 9, 1), (10, VMP, 9, 1), (10, PERIODIC, 8, 1)])
-def test_2d_coarse_levels_long_filters(p, bd, R, q):
-    """Several coarse 2D levels with long filters: the per-level kernels'
-    small tiles (8 and 16 samples) meet the boundary blocks of both edges."""
+def test_2d_coarse_levels_long_filters(monkeypatch, path, p, bd, R, q):
+    """Several coarse 2D levels with long filters, through each coarse-level
+    path: one cooperative launch that also moves the coefficient array into
+    (forward) and out of (adjoint) the transposed layout of the line passes,
+    the same launch with separate transpose kernels, the generic tiles, and
+    one launch per level.  Tiles of 8 to 32 samples meet the boundary blocks
+    of both edges."""
+    from paper_2106_00554_gb300 import _lib
+    if COARSE_PATHS[path]:
+        monkeypatch.setenv(COARSE_PATHS[path], "1")
     rng = np.random.default_rng(2000 + 10 * p + bd)
     J0 = W.default_J0(p)
     M, N = 2 ** R, 2 ** (R + q)
@@ -160,9 +172,15 @@ def test_2d_coarse_levels_long_filters(p, bd, R, q):
     y = rng.standard_normal(omega.size)
     want_y = dense.forward2d(x, R, q, p, bd, J0, omega, G=G)
     want_x = dense.adjoint2d(y, R, q, p, bd, J0, omega, G=G)
+    _lib.uw_plan_profile(plan._h, True)
     for prec in (F64, F32):
         assert rel(run_fwd(plan, x, prec), want_y) < TOL[prec]
         assert rel(run_adj(plan, y, prec), want_x) < TOL[prec]
+    names = _kernel_names(plan)
+    _lib.uw_plan_profile(plan._h, False)
+    moved_in_levels = path == "fused" and R - 1 - J0 >= 2
+    assert ("transpose_in" in names) == (not moved_in_levels), names
+    assert ("transpose_out" in names) == (not moved_in_levels), names
 
 
 @pytest.mark.parametrize("generic", [False, True])
