@@ -829,6 +829,60 @@ __device__ __forceinline__ void ld16(T (&w)[NW], const T* src) {
   }
 }
 
+// VMP edge corrections of the register-window tiles, staged in shared memory
+// with zero padding to compile-time bounds (LBM = 3 PM - 1 >= Lb rows):
+//   synthesis: D[LBM + 1][2 PM], row LBM zero (rows outside [0, LBM) read it);
+//   analysis:  D^T[2 PM + 1][LBP], row 2 PM zero (columns outside [0, PM) read it).
+// Rows are 16-byte aligned and loaded as vectors; the dot products of one
+// thread's outputs are independent (no branch per output).  The lanes of a
+// warp read rows 8 apart (synthesis rows) or 4 apart (analysis columns): one
+// 16-byte unit of padding per 8 (4) rows puts those rows in different banks.
+template <typename T, int PM>
+struct EdgeT {
+  static constexpr int VU = 16 / (int)sizeof(T);
+  static constexpr int LBM = 3 * PM - 1;
+  static constexpr int LBP = cup(LBM, VU);
+  __host__ __device__ static constexpr int srow(int r) { return r * 2 * PM + VU * (r >> 3); }
+  __host__ __device__ static constexpr int acol(int c) { return c * LBP + VU * (c >> 2); }
+  static constexpr int syn_side = cup(srow(LBM) + 2 * PM, VU);
+  static constexpr int ana_side = cup(acol(2 * PM) + LBP, VU);
+  static constexpr int syn_words = 2 * syn_side;     // both sides
+  static constexpr int ana_words = 2 * ana_side;
+};
+
+// output r of the synthesis edge band: D row r (zero outside [0, LBM)) . xe
+template <typename T, int PM>
+__device__ __forceinline__ T edge_dot(const T* D, int r, const T (&xe)[2 * PM]) {
+  constexpr int LBM = 3 * PM - 1;
+  T d[2 * PM];
+  ld16(d, D + EdgeT<T, PM>::srow((unsigned)r < (unsigned)LBM ? r : LBM));
+  T a0 = T(0), a1 = T(0);
+#pragma unroll
+  for (int c = 0; c < PM; ++c) {
+    a0 = fma(d[c], xe[c], a0);
+    a1 = fma(d[PM + c], xe[PM + c], a1);
+  }
+  return a0 + a1;
+}
+
+// column col of the analysis edge band: lo += D^T[col] . xe, hi += D^T[PM + col] . xe
+template <typename T, int PM>
+__device__ __forceinline__ void edge_dot_t(const T* DT, int col, const T (&xe)[EdgeT<T, PM>::LBP], T& lo, T& hi) {
+  constexpr int LBP = EdgeT<T, PM>::LBP;
+  const bool ok = (unsigned)col < (unsigned)PM;
+  T dl[LBP], dh[LBP];
+  ld16(dl, DT + EdgeT<T, PM>::acol(ok ? col : 2 * PM));
+  ld16(dh, DT + EdgeT<T, PM>::acol(ok ? PM + col : 2 * PM));
+  T x0 = T(0), x1 = T(0);
+#pragma unroll
+  for (int k = 0; k < LBP; ++k) {
+    x0 = fma(dl[k], xe[k], x0);
+    x1 = fma(dh[k], xe[k], x1);
+  }
+  lo += x0;
+  hi += x1;
+}
+
 // synthesis tile geometry: TS x TS outputs of level j+1 from NR x NC windows
 // of the four subbands (NR = NC = TS/2 + PM)
 template <typename T, int PM, int TS>
@@ -838,7 +892,9 @@ struct SynGeom {
   static constexpr int NC = TS / 2 + PM;
   static constexpr int NCP = 48;                      // row stride (rows 16 banks apart)
   static constexpr int NWR = cup(4 + PM, VW);         // row-pass window
-  static constexpr int elems = 4 * NR * NCP + 2 * NR * TS;
+  static constexpr int TSP = TS + VW;                 // H row stride: an odd number of 16-byte units
+  static constexpr int elems = 4 * NR * NCP + 2 * NR * TSP;
+  static_assert((TSP / VW) % 2 == 1, "H rows must start in alternating bank groups");
   static_assert(4 * (TS / 8 - 1) + NWR <= NCP, "row window exceeds the padded row");
 };
 
@@ -850,7 +906,9 @@ struct AnaGeom {
   static constexpr int NR = 2 * TSA + 2 * PM - 2;
   static constexpr int NRP = NR + 1;                  // row stride of the input window
   static constexpr int NWA = cup(2 * PM + 6, VW);     // row-pass window (2 PM + 6 used)
-  static constexpr int NCH = cup(8 * (TSA / 4 - 1) + NWA, VW);   // row stride of the column-pass result
+  static constexpr int NCH0 = cup(8 * (TSA / 4 - 1) + NWA, VW);
+  // row stride of the column-pass result: an odd number of 16-byte units
+  static constexpr int NCH = (NCH0 / VW) % 2 ? NCH0 : NCH0 + VW;
   static constexpr int HOFF = cup(NR * NRP, 4);       // the column-pass result starts 16-byte aligned
   static constexpr int elems = HOFF + 2 * TSA * NCH;
 };
@@ -862,13 +920,13 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
                                             const T* Dr, int p, int Lb, bool per, T* smem, int tid, int nthr,
                                             T* xt = nullptr) {
   using SG = SynGeom<T, PM, TS>;
-  constexpr int NR = SG::NR, NC = SG::NC, NCP = SG::NCP, NWR = SG::NWR;
+  constexpr int NR = SG::NR, NC = SG::NC, NCP = SG::NCP, NWR = SG::NWR, TSP = SG::TSP;
   const int n0 = 1 << j, n1 = 2 * n0;
   const int tiles = n1 / TS;
   const int r0 = (tile / tiles) * TS, c0 = (tile % tiles) * TS;
   const int ir0 = (r0 >> 1) - PM / 2, ic0 = (c0 >> 1) - PM / 2;
   T* W = smem;                    // [4][NR][NCP]: LL, D1, D2, D3 windows
-  T* H = W + 4 * NR * NCP;        // [2][NR][TS]: row-synthesised top (LL|D1) and bottom (D2|D3) halves
+  T* H = W + 4 * NR * NCP;        // [2][NR][TSP]: row-synthesised top (LL|D1) and bottom (D2|D3) halves
   const T* xb = x + b * (int64_t)M * M;
   const T* lb = llsrc + b * llb;
   {
@@ -940,25 +998,19 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
             xe[e] = rlo[m0e + e];
             xe[PM + e] = rhi[m0e + e];
           }
+          const int rb = left ? 8 * g : c0 + 8 * g - (n1 - Lb);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int r = left ? 8 * g + e : c0 + 8 * g + e - (n1 - Lb);
-            if (r >= 0 && r < 3 * PM - 1) {        // rows past Lb and columns past p weigh zero
-              const T* dr = D + r * 2 * PM;
-              T acc = o[e];
-#pragma unroll
-              for (int c = 0; c < PM; ++c) {
-                acc = fma(dr[c], xe[c], acc);
-                acc = fma(dr[PM + c], xe[PM + c], acc);
-              }
-              o[e] = acc;
-            }
-          }
+          for (int e = 0; e < 8; ++e) o[e] += edge_dot<T, PM>(D, rb + e, xe);
         }
       }
-      T* hrow = H + (h * NR + i) * TS + 8 * g;
+      T* hrow = H + (h * NR + i) * TSP + 8 * g;    // 16-byte aligned
+      if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4*>(hrow)[0] = make_float4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<float4*>(hrow)[1] = make_float4(o[4], o[5], o[6], o[7]);
+      } else {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) hrow[e] = o[e];
+        for (int e = 0; e < 8; e += 2) reinterpret_cast<double2*>(hrow)[e / 2] = make_double2(o[e], o[e + 1]);
+      }
     }
   }
   __syncthreads();
@@ -970,8 +1022,8 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
       T wl[2 + PM], wh[2 + PM];
 #pragma unroll
       for (int w = 0; w < 2 + PM; ++w) {
-        wl[w] = H[(2 * g4 + w) * TS + cc];
-        wh[w] = H[(NR + 2 * g4 + w) * TS + cc];
+        wl[w] = H[(2 * g4 + w) * TSP + cc];
+        wh[w] = H[(NR + 2 * g4 + w) * TSP + cc];
       }
       T o[4];
 #pragma unroll
@@ -993,23 +1045,12 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
           T xe[2 * PM];
 #pragma unroll
           for (int e = 0; e < PM; ++e) {
-            xe[e] = H[(m0e + e) * TS + cc];
-            xe[PM + e] = H[(NR + m0e + e) * TS + cc];
+            xe[e] = H[(m0e + e) * TSP + cc];
+            xe[PM + e] = H[(NR + m0e + e) * TSP + cc];
           }
+          const int rb = top ? 4 * g4 : r0 + 4 * g4 - (n1 - Lb);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int r = top ? 4 * g4 + e : r0 + 4 * g4 + e - (n1 - Lb);
-            if (r >= 0 && r < 3 * PM - 1) {
-              const T* dr = D + r * 2 * PM;
-              T acc = o[e];
-#pragma unroll
-              for (int c = 0; c < PM; ++c) {
-                acc = fma(dr[c], xe[c], acc);
-                acc = fma(dr[PM + c], xe[PM + c], acc);
-              }
-              o[e] = acc;
-            }
-          }
+          for (int e = 0; e < 4; ++e) o[e] += edge_dot<T, PM>(D, rb + e, xe);
         }
       }
       if (xt) {
@@ -1107,26 +1148,15 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
         // registers, then unrolled dot products
         const bool top = m0 == 0 && 4 * g < p, bottom = m0 + TSA == n0 && m0 + 4 * g + 4 > n0 - p;
         if (top || bottom) {
-          constexpr int LBM = 3 * PM - 1;             // >= Lb = 3p - 1
+          constexpr int LBM = 3 * PM - 1, LBP = EdgeT<T, PM>::LBP;
           const int k0e = top ? -ir0 : n1 - Lb - ir0;
           const T* D = top ? Dl : Dr;
-          T xe[LBM];
+          T xe[LBP];
 #pragma unroll
-          for (int k = 0; k < LBM; ++k) xe[k] = S[min(k0e + k, NR - 1) * NRP + c];   // rows past Lb weigh zero
+          for (int k = 0; k < LBP; ++k) xe[k] = k < LBM ? S[min(k0e + k, NR - 1) * NRP + c] : T(0);   // rows past Lb weigh zero
+          const int cb = top ? 4 * g : m0 + 4 * g - (n0 - p);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int col = top ? 4 * g + e : m0 + 4 * g + e - (n0 - p);
-            if (col >= 0 && col < PM) {
-              T x0 = lo[e], x1 = hi[e];
-#pragma unroll
-              for (int k = 0; k < LBM; ++k) {
-                x0 = fma(D[k * 2 * PM + col], xe[k], x0);
-                x1 = fma(D[k * 2 * PM + PM + col], xe[k], x1);
-              }
-              lo[e] = x0;
-              hi[e] = x1;
-            }
-          }
+          for (int e = 0; e < 4; ++e) edge_dot_t<T, PM>(D, cb + e, xe, lo[e], hi[e]);
         }
       }
 #pragma unroll
@@ -1163,26 +1193,15 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
       if (!per) {
         const bool left = k0 == 0 && 4 * g < p, right = k0 + TSA == n0 && k0 + 4 * g + 4 > n0 - p;
         if (left || right) {
-          constexpr int LBM = 3 * PM - 1;
+          constexpr int LBM = 3 * PM - 1, LBP = EdgeT<T, PM>::LBP;
           const int k0e = left ? -ic0 : n1 - Lb - ic0;
           const T* D = left ? Dl : Dr;
-          T xe[LBM];
+          T xe[LBP];
 #pragma unroll
-          for (int k = 0; k < LBM; ++k) xe[k] = hr[min(k0e + k, NR - 1)];
+          for (int k = 0; k < LBP; ++k) xe[k] = k < LBM ? hr[min(k0e + k, NR - 1)] : T(0);
+          const int cb = left ? 4 * g : k0 + 4 * g - (n0 - p);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int col = left ? 4 * g + e : k0 + 4 * g + e - (n0 - p);
-            if (col >= 0 && col < PM) {
-              T x0 = lo[e], x1 = hi[e];
-#pragma unroll
-              for (int k = 0; k < LBM; ++k) {
-                x0 = fma(D[k * 2 * PM + col], xe[k], x0);
-                x1 = fma(D[k * 2 * PM + PM + col], xe[k], x1);
-              }
-              lo[e] = x0;
-              hi[e] = x1;
-            }
-          }
+          for (int e = 0; e < 4; ++e) edge_dot_t<T, PM>(D, cb + e, xe, lo[e], hi[e]);
         }
       }
       const int mm = row < TSA ? m0 + row : m0 + row - TSA;
@@ -1285,17 +1304,18 @@ __global__ void __launch_bounds__(256, 2) k_syn2d_levels(CoarseIO<T> io, Tables<
   SmemTables<T> st;
   int off = stage_filters(tab, G, sm, st, tid, nthr);
   const bool per = G.bd == UW_BOUNDARY_PERIODIC;
-  // edge corrections, zero-padded to compile-time bounds: [side][3PM-1 rows][2PM cols]
+  // edge corrections [side][LBM + 1 rows][2PM cols], zero-padded (EdgeT)
   constexpr int LBM = 3 * PM - 1, DW = 2 * PM;
-  const int nD = per ? 0 : 2 * LBM * DW;
+  const int nD = per ? 0 : 2 * (LBM + 1) * DW;      // entries (padding words are never read)
   T* Dl = sm + off;
   for (int i = tid; i < nD; i += nthr) {
-    const int side = i / (LBM * DW), rem = i - side * (LBM * DW), r = rem / DW, c = rem - r * DW;
+    const int side = i / ((LBM + 1) * DW), rem = i - side * ((LBM + 1) * DW), r = rem / DW, c = rem - r * DW;
     const int e = c < PM ? c : c - PM;
-    Dl[i] = (r < G.Lb && e < G.p) ? Dg[(side * G.Lb + r) * 2 * G.p + (c < PM ? e : G.p + e)] : T(0);
+    Dl[side * EdgeT<T, PM>::syn_side + EdgeT<T, PM>::srow(r) + c] =
+        (r < G.Lb && e < G.p) ? Dg[(side * G.Lb + r) * 2 * G.p + (c < PM ? e : G.p + e)] : T(0);
   }
-  const T* Dr = Dl + LBM * DW;
-  off = cup(off + nD, 4);
+  const T* Dr = Dl + EdgeT<T, PM>::syn_side;
+  off = cup(off + (per ? 0 : EdgeT<T, PM>::syn_words), 4);
   // constant tables staged: let the next kernel launch, then wait for the
   // previous grid (x may be its output)
   pdl_trigger();
@@ -1348,17 +1368,18 @@ __global__ void __launch_bounds__(256, 2) k_ana2d_levels(CoarseIO<T> io, Tables<
   SmemTables<T> st;
   int off = stage_filters(tab, G, sm, st, tid, nthr);
   const bool per = G.bd == UW_BOUNDARY_PERIODIC;
-  // edge corrections, zero-padded to compile-time bounds: [side][3PM-1 rows][2PM cols]
-  constexpr int LBM = 3 * PM - 1, DW = 2 * PM;
-  const int nD = per ? 0 : 2 * LBM * DW;
+  // edge corrections transposed, [side][2PM + 1 columns][LBP rows], zero-padded (EdgeT)
+  constexpr int DW = 2 * PM, LBP = EdgeT<T, PM>::LBP;
+  const int nD = per ? 0 : 2 * (DW + 1) * LBP;      // entries (padding words are never read)
   T* Dl = sm + off;
   for (int i = tid; i < nD; i += nthr) {
-    const int side = i / (LBM * DW), rem = i - side * (LBM * DW), r = rem / DW, c = rem - r * DW;
+    const int side = i / ((DW + 1) * LBP), rem = i - side * ((DW + 1) * LBP), c = rem / LBP, r = rem - c * LBP;
     const int e = c < PM ? c : c - PM;
-    Dl[i] = (r < G.Lb && e < G.p) ? Dg[(side * G.Lb + r) * 2 * G.p + (c < PM ? e : G.p + e)] : T(0);
+    Dl[side * EdgeT<T, PM>::ana_side + EdgeT<T, PM>::acol(c) + r] =
+        (c < DW && r < G.Lb && e < G.p) ? Dg[(side * G.Lb + r) * 2 * G.p + (c < PM ? e : G.p + e)] : T(0);
   }
-  const T* Dr = Dl + LBM * DW;
-  off = cup(off + nD, 4);
+  const T* Dr = Dl + EdgeT<T, PM>::ana_side;
+  off = cup(off + (per ? 0 : EdgeT<T, PM>::ana_words), 4);
   pdl_trigger();
   pdl_wait();
   const int M = io.M, Mh = M / 2;
@@ -1887,7 +1908,8 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
   bool ok = false;
   pm_dispatch(G.p, [&](auto pc) {
     constexpr int PM = decltype(pc)::value;
-    const size_t head = (size_t)cup(cup(4 * G.p, 4) + (P.bd == UW_BOUNDARY_PERIODIC ? 0 : 2 * (3 * PM - 1) * 2 * PM), 4);
+    const int nD = P.bd == UW_BOUNDARY_PERIODIC ? 0 : (fwd ? EdgeT<T, PM>::syn_words : EdgeT<T, PM>::ana_words);
+    const size_t head = (size_t)cup(cup(4 * G.p, 4) + nD, 4);
     size_t sm = 0;
     int max_tiles = 0;
     double bytes = 0;

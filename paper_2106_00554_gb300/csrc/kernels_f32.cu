@@ -96,12 +96,21 @@ struct Geom {
   static constexpr int NWA = up4(OFFA + 2 * BL + 2 * PM);
   static constexpr int VH = 256;             // adjoint Walsh halo (keeps the padding pattern)
   static constexpr int VLf = up4(vp(N - 1) + 1);
-  static constexpr int VLa = up4(vp(N + 2 * VH - 1) + 1);
+  // of the adjoint halo only the 16-blocks that T^T reads are allocated: HL
+  // elements before the line, HR after it; the buffer starts at word VB of
+  // the full padded layout
+  static constexpr int HL = (Q * (PM - 1) + OFFT + 15) / 16 * 16;
+  static constexpr int HR = (Q * (PM - 1) + 3 + 15) / 16 * 16;
+  static constexpr int VB = vp(VH - HL);
+  static constexpr int VLa = up4(vp(VH + N + HR - 1) + 1) - VB;
   static constexpr int PST = N / 2 + 4;      // sample-position words per buffer
   static_assert(M % NT == 0 && BS * NT == M, "one block of 16 outputs per thread");
   static_assert(HX >= PM / 2 + VW - 1, "coefficient halo too small");
   static_assert(HS >= PM + 3, "s halo too small");
   static_assert(Q * (PM - 1) + OFFT <= VH, "Walsh halo too small");
+  static_assert(HL <= VH && HR <= VH && VB % 4 == 0, "trimmed halo outside the padded layout");
+  // T^T window of the last thread: Q (M - BS - PM + 1) - OFFT + NWT - 1 < N + HR
+  static_assert(Q * (M - BS - PM + 1) - OFFT + NWT <= N + HR, "T^T window past the right halo");
 };
 
 // In-register Walsh-Hadamard transform of R values (natural order): the
@@ -448,7 +457,8 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
   const int tid = threadIdx.x, lane = tid & 31;
   const bool scat = io.mode == 1;
   // mode 0: two staged Walsh lines (this one, the next), transformed in
-  // place; mode 1: one Walsh line, the next line's packed samples and positions
+  // place; mode 1: one Walsh line, the next line's packed samples and positions.
+  // Element k of a Walsh line sits at sV[vp(VH + k)], sV = buffer start - VB.
   float* sV0 = reinterpret_cast<float*>(smem_raw);
   float* sS = sV0 + (scat ? 1 : 2) * G::VLa;
   float* sCorr = sS + G::SL;                                      // 4p (VMP)
@@ -464,7 +474,7 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
     const int64_t b = lp.b;
     if (!scat) {
       const float* src = in + b * io.in_batch + (int64_t)l * io.in_stride;
-      float* dst = sV0 + bi * G::VLa;
+      float* dst = sV0 + bi * G::VLa - G::VB;
       for (int e4 = tid; e4 < N / 4; e4 += NT) cp16(dst + vp(VH + 4 * e4), src + 4 * e4);
     } else {
       const float* y = in + b * io.m;
@@ -503,7 +513,7 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
     __syncthreads();
     const int l = cur.l;
     const int64_t b = cur.b;
-    float* sV = sV0 + (scat ? 0 : buf * G::VLa);
+    float* sV = sV0 + (scat ? 0 : buf * G::VLa) - G::VB;
     if (scat) {
       // zero the line, then scatter the staged samples to their natural positions
       {
@@ -538,14 +548,14 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
       wht<16>(v);
 #pragma unroll
       for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(src + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
-      if (a.per) {   // wrapped copies in the halos
+      if (a.per) {   // wrapped copies in the (trimmed) halos
         const int k0 = 16 * tid;
-        if (k0 < VH) {
+        if (k0 < G::HR) {
           float* h = sV + vp(VH + N + k0);
 #pragma unroll
           for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(h + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
         }
-        if (k0 >= N - VH) {
+        if (k0 >= N - G::HL) {
           float* h = sV + vp(VH + k0 - N);
 #pragma unroll
           for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(h + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
@@ -724,6 +734,9 @@ int persistent_grid(K kernel, int nt, size_t smem, int total) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, nt, smem);
+  // UW_F32_CTAS_PER_SM: a lower cap on the CTAs per SM (tuning)
+  const char* cap = getenv("UW_F32_CTAS_PER_SM");
+  if (cap && cap[0] && atoi(cap) > 0) per = std::min(per, atoi(cap));
   return std::max(1, std::min(total, std::max(per, 1) * nsm));
 }
 
