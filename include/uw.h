@@ -164,13 +164,46 @@ int uw_forward_noalloc(const uw_plan* plan, int precision, const void* x_dev, vo
  * uw_forward_host / uw_adjoint_host -- the same products on HOST buffers:
  * the input is copied to the plan's device staging area, the product runs on
  * `stream`, the result is copied back; the call returns once the result is in
- * host memory (it synchronises `stream`).  Staging is part of the reserved
- * workspace.
+ * host memory (it synchronises `stream`, after waiting for the plan's
+ * asynchronous host calls).  Staging is part of the reserved workspace.
  */
 int uw_forward_host(const uw_plan* plan, int precision, const void* x_host, void* y_host,
                     int batch, void* stream);
 int uw_adjoint_host(const uw_plan* plan, int precision, const void* y_host, void* x_host,
                     int batch, void* stream);
+
+/*
+ * uw_forward_host_async / uw_adjoint_host_async -- the host-buffer products,
+ * stream-ordered, for a sequence of instances whose copies overlap the
+ * products.  Each call takes the next of two device staging slots:
+ *   1. the input is copied host -> device on the plan's upload stream (after
+ *      the product that last read that slot is done);
+ *   2. the product runs on `stream` once that copy is done (and once the
+ *      download that last read the slot's output is done);
+ *   3. the result is copied device -> host on the plan's download stream once
+ *      the product is done.
+ * The call returns as soon as this is enqueued.  The upload of call k+1 and
+ * the download of call k-1 therefore run while the product of call k runs.
+ * Products run in call order (they share the plan's workspace).
+ *
+ * Host buffers must be pinned for the copies to be asynchronous.  They must
+ * stay valid until uw_host_wait returns: inputs unchanged, outputs not read.
+ * The same input buffer may be passed to several calls.
+ *
+ * Errors: the same argument checks as uw_forward_host (UW_ERR_INVALID_ARG);
+ * UW_ERR_OOM if the plan's copy streams or events cannot be created;
+ * UW_ERR_CUDA if a copy cannot be enqueued.
+ */
+int uw_forward_host_async(const uw_plan* plan, int precision, const void* x_host, void* y_host,
+                          int batch, void* stream);
+int uw_adjoint_host_async(const uw_plan* plan, int precision, const void* y_host, void* x_host,
+                          int batch, void* stream);
+
+/*
+ * uw_host_wait -- block until every result of the plan's asynchronous host
+ * calls is in host memory.  Returns UW_ERR_CUDA if a copy or product failed.
+ */
+int uw_host_wait(const uw_plan* plan);
 
 /*
  * Solver kernels (element-wise, no plan): the pieces of an l1-regularised

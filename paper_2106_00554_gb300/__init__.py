@@ -126,6 +126,15 @@ class Plan:
     def adjoint_host(self, y, x, precision, batch, stream=None):
         uw_adjoint_host(self._h, precision, y, x, batch, _stream_ptr(stream))
 
+    def forward_host_async(self, x, y, precision, batch, stream=None):
+        _lib.uw_forward_host_async(self._h, precision, x, y, batch, _stream_ptr(stream))
+
+    def adjoint_host_async(self, y, x, precision, batch, stream=None):
+        _lib.uw_adjoint_host_async(self._h, precision, y, x, batch, _stream_ptr(stream))
+
+    def host_wait(self):
+        _lib.uw_host_wait(self._h)
+
     def close(self):
         if getattr(self, "_h", None):
             uw_plan_destroy(self._h)

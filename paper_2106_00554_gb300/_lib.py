@@ -36,6 +36,9 @@ SIGNATURES = {
     "uw_forward_noalloc": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
     "uw_forward_host": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
     "uw_adjoint_host": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
+    "uw_forward_host_async": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
+    "uw_adjoint_host_async": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
+    "uw_host_wait": (_int, [_c_p]),
     "uw_plan_destroy": (None, [_c_p]),
     "uw_plan_table": (_i64, [_c_p, _int, _dp, _i64]),
     "uw_host_table": (_i64, [_int, _int, _int, _dp, _i64]),
@@ -128,6 +131,18 @@ def uw_forward_host(h, precision, x_ptr, y_ptr, batch, stream):
 
 def uw_adjoint_host(h, precision, y_ptr, x_ptr, batch, stream):
     _chk(lib().uw_adjoint_host(h, precision, y_ptr, x_ptr, batch, stream), "uw_adjoint_host")
+
+
+def uw_forward_host_async(h, precision, x_ptr, y_ptr, batch, stream):
+    _chk(lib().uw_forward_host_async(h, precision, x_ptr, y_ptr, batch, stream), "uw_forward_host_async")
+
+
+def uw_adjoint_host_async(h, precision, y_ptr, x_ptr, batch, stream):
+    _chk(lib().uw_adjoint_host_async(h, precision, y_ptr, x_ptr, batch, stream), "uw_adjoint_host_async")
+
+
+def uw_host_wait(h):
+    _chk(lib().uw_host_wait(h), "uw_host_wait")
 
 
 def uw_fista_step(precision, n, z, G, B, x0, tau, lam, beta, x1, z1, stream):

@@ -2495,6 +2495,8 @@ int uw_forward_noalloc(const uw_plan* P, int prec, const void* x, void* y, int b
 static int host_call(const uw_plan* P, int prec, bool fwd, const void* in, void* out, int batch, void* stream) {
   int st = fwd ? check_call(P, prec, in, out, batch) : check_call(P, prec, out, in, batch);
   if (st != UW_OK) return st;
+  // slot 0 may still be in use by an asynchronous host call
+  if (uw_host_wait(P) != UW_OK) return UW_ERR_CUDA;
   const size_t e = prec == UW_F64 ? sizeof(double) : sizeof(float);
   const int64_t coeffs = P->d == 1 ? (int64_t)P->M : (int64_t)P->M * P->M;
   const size_t nin = (size_t)batch * (size_t)(fwd ? coeffs : P->m);
@@ -2525,6 +2527,96 @@ int uw_forward_host(const uw_plan* P, int prec, const void* x, void* y, int batc
 
 int uw_adjoint_host(const uw_plan* P, int prec, const void* y, void* x, int batch, void* stream) {
   return host_call(P, prec, false, y, x, batch, stream);
+}
+
+// copy streams and per-slot events of the asynchronous host calls (created once)
+static int host_async_init(uw_plan* P) {
+  if (P->s_up) return UW_OK;
+  cudaStream_t up = nullptr, down = nullptr;
+  if (cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    if (up) cudaStreamDestroy(up);
+    uw::set_error(UW_ERR_OOM, "copy stream creation failed");
+    return UW_ERR_OOM;
+  }
+  for (auto& slot : P->ev)
+    for (void*& e : slot) {
+      cudaEvent_t ev = nullptr;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        uw::set_error(UW_ERR_OOM, "event creation failed");
+        cudaStreamDestroy(up);
+        cudaStreamDestroy(down);
+        return UW_ERR_OOM;
+      }
+      e = ev;
+    }
+  P->s_up = up;
+  P->s_down = down;
+  return UW_OK;
+}
+
+static int host_call_async(const uw_plan* Pc, int prec, bool fwd, const void* in, void* out, int batch,
+                           void* stream) {
+  int st = fwd ? check_call(Pc, prec, in, out, batch) : check_call(Pc, prec, out, in, batch);
+  if (st != UW_OK) return st;
+  uw_plan* P = const_cast<uw_plan*>(Pc);
+  if ((st = host_async_init(P)) != UW_OK) return st;
+  const size_t e = prec == UW_F64 ? sizeof(double) : sizeof(float);
+  const int64_t coeffs = P->d == 1 ? (int64_t)P->M : (int64_t)P->M * P->M;
+  const size_t nin = (size_t)batch * (size_t)(fwd ? coeffs : P->m);
+  const size_t nout = (size_t)batch * (size_t)(fwd ? P->m : coeffs);
+  auto up256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  const int k = P->slot;
+  P->slot ^= 1;
+  char* din = (char*)P->d_stage + (size_t)k * P->stage_bytes;
+  char* dout = din + up256((size_t)batch * (size_t)(fwd ? coeffs : P->m) * sizeof(double));
+  cudaStream_t s = (cudaStream_t)stream, up = (cudaStream_t)P->s_up, down = (cudaStream_t)P->s_down;
+  cudaEvent_t ev_up = (cudaEvent_t)P->ev[k][0], ev_prod = (cudaEvent_t)P->ev[k][1],
+              ev_down = (cudaEvent_t)P->ev[k][2];
+  // upload once the product that last read this slot is done
+  if (cudaStreamWaitEvent(up, ev_prod, 0) != cudaSuccess ||
+      cudaMemcpyAsync(din, in, nin * e, cudaMemcpyHostToDevice, up) != cudaSuccess ||
+      cudaEventRecord(ev_up, up) != cudaSuccess) {
+    uw::set_error(UW_ERR_CUDA, "host-to-device copy failed");
+    return UW_ERR_CUDA;
+  }
+  // the product: after the upload and after the download that last read this slot's output
+  if (cudaStreamWaitEvent(s, ev_up, 0) != cudaSuccess || cudaStreamWaitEvent(s, ev_down, 0) != cudaSuccess) {
+    uw::set_error(UW_ERR_CUDA, "stream wait failed");
+    return UW_ERR_CUDA;
+  }
+  st = fwd ? uw_forward(P, prec, din, dout, batch, stream) : uw_adjoint(P, prec, din, dout, batch, stream);
+  if (st != UW_OK) return st;
+  if (cudaEventRecord(ev_prod, s) != cudaSuccess || cudaStreamWaitEvent(down, ev_prod, 0) != cudaSuccess ||
+      cudaMemcpyAsync(out, dout, nout * e, cudaMemcpyDeviceToHost, down) != cudaSuccess ||
+      cudaEventRecord(ev_down, down) != cudaSuccess) {
+    uw::set_error(UW_ERR_CUDA, "device-to-host copy failed");
+    return UW_ERR_CUDA;
+  }
+  return UW_OK;
+}
+
+int uw_forward_host_async(const uw_plan* P, int prec, const void* x, void* y, int batch, void* stream) {
+  return host_call_async(P, prec, true, x, y, batch, stream);
+}
+
+int uw_adjoint_host_async(const uw_plan* P, int prec, const void* y, void* x, int batch, void* stream) {
+  return host_call_async(P, prec, false, y, x, batch, stream);
+}
+
+int uw_host_wait(const uw_plan* P) {
+  if (!P) {
+    uw::set_error(UW_ERR_INVALID_ARG, "null plan");
+    return UW_ERR_INVALID_ARG;
+  }
+  // downloads run in call order on one stream, each after its product
+  if (P->s_down && cudaStreamSynchronize((cudaStream_t)P->s_down) != cudaSuccess) {
+    uw::set_error(UW_ERR_CUDA, "asynchronous host call failed");
+    return UW_ERR_CUDA;
+  }
+  return UW_OK;
 }
 
 }  // extern "C"

@@ -734,9 +734,6 @@ int persistent_grid(K kernel, int nt, size_t smem, int total) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, nt, smem);
-  // UW_F32_CTAS_PER_SM: a lower cap on the CTAs per SM (tuning)
-  const char* cap = getenv("UW_F32_CTAS_PER_SM");
-  if (cap && cap[0] && atoi(cap) > 0) per = std::min(per, atoi(cap));
   return std::max(1, std::min(total, std::max(per, 1) * nsm));
 }
 

@@ -707,11 +707,14 @@ int uw_plan_reserve(uw_plan* P, int max_batch) {
   if (!P || max_batch < 1) return fail(UW_ERR_INVALID_ARG, "null plan or max_batch < 1");
   size_t wb = uw::workspace_bytes(*P, max_batch);
   int64_t coeffs = P->d == 1 ? (int64_t)P->M : (int64_t)P->M * P->M;
-  size_t sb = (size_t)max_batch * (size_t)(coeffs + P->m) * sizeof(double) + 512;
+  // bytes per staging slot, a multiple of 256 so that the second slot keeps
+  // the alignment of the first (the line kernels copy 16-byte chunks)
+  size_t sb = ((size_t)max_batch * (size_t)(coeffs + P->m) * sizeof(double) + 512 + 255) & ~(size_t)255;
   void* w = nullptr;
   void* s = nullptr;
   if (wb && cudaMalloc(&w, wb) != cudaSuccess) { cudaGetLastError(); return fail(UW_ERR_OOM, "workspace allocation failed"); }
-  if (sb && cudaMalloc(&s, sb) != cudaSuccess) { cudaFree(w); cudaGetLastError(); return fail(UW_ERR_OOM, "staging allocation failed"); }
+  if (sb && cudaMalloc(&s, 2 * sb) != cudaSuccess) { cudaFree(w); cudaGetLastError(); return fail(UW_ERR_OOM, "staging allocation failed"); }
+  uw_host_wait(P);   // no asynchronous host call may still use the old buffers
   cudaFree(P->d_work);
   cudaFree(P->d_stage);
   P->d_work = w;
@@ -763,6 +766,12 @@ int64_t uw_host_table(int p, int q, int which, double* out, int64_t cap) {
 
 void uw_plan_destroy(uw_plan* P) {
   if (!P) return;
+  uw_host_wait(P);
+  for (auto& slot : P->ev)
+    for (void*& e : slot)
+      if (e) cudaEventDestroy((cudaEvent_t)e);
+  if (P->s_up) cudaStreamDestroy((cudaStream_t)P->s_up);
+  if (P->s_down) cudaStreamDestroy((cudaStream_t)P->s_down);
   uw::profiler_free(*P);
   cudaFree(P->d_tab64);
   cudaFree(P->d_tab32);

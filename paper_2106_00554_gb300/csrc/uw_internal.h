@@ -89,8 +89,14 @@ struct Plan {
   uint16_t* d_pos = nullptr;     // per sample (packed order): its natural FWHT position in the row (N <= 65536)
   void* d_work = nullptr;
   size_t work_bytes = 0;
-  void* d_stage = nullptr;       // host-API staging (input + output)
-  size_t stage_bytes = 0;
+  void* d_stage = nullptr;       // host-API staging: two slots of (input + output)
+  size_t stage_bytes = 0;        // bytes per slot
+  // asynchronous host calls: copy streams, per-slot events (upload done,
+  // product done, download done), next slot
+  void* s_up = nullptr;
+  void* s_down = nullptr;
+  void* ev[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int slot = 0;
   int device = 0;
   Profiler* prof = nullptr;
   TcGeo tc;                      // split-BF16 line operators (tc.ok = 0: not eligible)

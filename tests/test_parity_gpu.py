@@ -358,6 +358,37 @@ def test_host_buffer_api_matches_device():
     assert rel(xb, run_adj(plan, y, F32)) < 1e-6
 
 
+@pytest.mark.parametrize("prec,batch", [(F32, 1), (F64, 2)])
+def test_host_async_pipeline_matches_device(prec, batch):
+    """uw_forward_host_async / uw_adjoint_host_async: five forward and five
+    adjoint calls with different inputs in flight at once (two staging slots,
+    copies on the plan's own streams), then uw_host_wait; every result equals
+    the device API's.  A synchronous host call afterwards still agrees."""
+    rng = np.random.default_rng(7)
+    R, q, p = 8, 1, 4
+    N = 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.2)
+    plan = Plan(2, R, q, p, VMP, omega=omega, max_batch=batch)
+    dt = torch.float64 if prec == F64 else torch.float32
+    shape = (batch, 2 ** R, 2 ** R) if batch > 1 else (2 ** R, 2 ** R)
+    xs = [torch.tensor(rng.standard_normal(shape), dtype=dt).pin_memory() for _ in range(5)]
+    ys = [torch.tensor(rng.standard_normal((batch, plan.m) if batch > 1 else plan.m), dtype=dt).pin_memory()
+          for _ in range(5)]
+    yo = [torch.empty_like(y).pin_memory() for y in ys]
+    xo = [torch.empty_like(x).pin_memory() for x in xs]
+    for k in range(5):
+        plan.forward_host_async(xs[k].data_ptr(), yo[k].data_ptr(), prec, batch)
+        plan.adjoint_host_async(ys[k].data_ptr(), xo[k].data_ptr(), prec, batch)
+    plan.host_wait()
+    tol = 1e-12 if prec == F64 else 1e-6
+    for k in range(5):
+        assert rel(yo[k].numpy(), run_fwd(plan, xs[k].numpy(), prec)) < tol
+        assert rel(xo[k].numpy(), run_adj(plan, ys[k].numpy(), prec)) < tol
+    ysync = torch.empty_like(yo[0]).pin_memory()
+    plan.forward_host(xs[3].data_ptr(), ysync.data_ptr(), prec, batch)
+    assert rel(ysync.numpy(), yo[3].numpy()) < tol
+
+
 def test_dot_product_2d_fp64():
     rng = np.random.default_rng(6)
     R, q, p = 7, 2, 4
