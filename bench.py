@@ -64,10 +64,20 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    h = hashlib.sha256()
+def kernel_source_hash(kernel=""):
+    """First 16 hex digits of the SHA-256 of the sources that define `kernel`
+    and its launch, in name order: for the line operators whose names end in
+    _f32 / _tc, their own file (kernels_f32.cu / kernels_tc.cu) and
+    line_common.cuh; for any other kernel, every file under csrc/."""
     csrc = os.path.join(ROOT, "paper_2106_00554_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    if kernel.endswith("_f32"):
+        files = ["kernels_f32.cu", "line_common.cuh"]
+    elif kernel.endswith("_tc"):
+        files = ["kernels_tc.cu", "line_common.cuh"]
+    else:
+        files = os.listdir(csrc)
+    h = hashlib.sha256()
+    for f in sorted(files):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -75,14 +85,14 @@ def kernel_source_hash():
 def ncu_traffic(kernel):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     of `kernel` from the committed ncu summary profiles/traffic.md, if its
-    counters were taken on the current kernel sources (the summary records
-    the hash of csrc/); None otherwise.  Rows: | name | bytes | hash |."""
+    counters were taken on the current sources of that kernel (the summary
+    records kernel_source_hash(name)); None otherwise.  Rows: | name | bytes | hash |."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     try:
         lines = open(path).read().splitlines()
     except Exception:
         return None
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(kernel)
     for ln in lines:
         f = [c.strip().strip("`") for c in ln.strip().strip("|").split("|")]
         if len(f) >= 3 and f[0] == kernel and f[2] == cur:

@@ -779,6 +779,7 @@ __device__ __forceinline__ void grid_exit(GridBarrier* bar, unsigned int nblocks
 
 // level buffers of the forward synthesis: level it (j = J0 + it) reads
 // S_j (x itself for it = 0) and writes S_{j+1}; S_{R-1} ends in XS
+constexpr int kMaxCoarse = 16;   // coarse levels of one fused launch (R - 1 - J0 <= 15)
 template <typename T>
 struct CoarseIO {
   const T* x;    // forward input (Mallat layout)
@@ -787,6 +788,8 @@ struct CoarseIO {
   T* XS2;
   T* XT;         // transposed full-size buffer of the line passes, or null (see tx_share)
   int M, J0, nl, batch;
+  // transpose items [tq0[it], tq0[it] + tnq[it]) ride with step it (host-computed, tx_share)
+  int tq0[kMaxCoarse], tnq[kMaxCoarse];
 };
 
 // ---------------------------------------------------------------------------
@@ -808,6 +811,7 @@ struct CTaps {
 };
 
 __host__ __device__ constexpr int cup(int a, int b) { return (a + b - 1) / b * b; }
+__host__ __device__ constexpr int ilog2c(int a) { return a <= 1 ? 0 : 1 + ilog2c(a / 2); }
 
 // NW values from a 16-byte aligned shared address, 16-byte loads
 template <typename T, int NW>
@@ -922,8 +926,8 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
   using SG = SynGeom<T, PM, TS>;
   constexpr int NR = SG::NR, NC = SG::NC, NCP = SG::NCP, NWR = SG::NWR, TSP = SG::TSP;
   const int n0 = 1 << j, n1 = 2 * n0;
-  const int tiles = n1 / TS;
-  const int r0 = (tile / tiles) * TS, c0 = (tile % tiles) * TS;
+  const int lt = j + 1 - ilog2c(TS);          // tiles per row: n1 / TS = 2^lt
+  const int r0 = (tile >> lt) * TS, c0 = (tile & ((1 << lt) - 1)) * TS;
   const int ir0 = (r0 >> 1) - PM / 2, ic0 = (c0 >> 1) - PM / 2;
   T* W = smem;                    // [4][NR][NCP]: LL, D1, D2, D3 windows
   T* H = W + 4 * NR * NCP;        // [2][NR][TSP]: row-synthesised top (LL|D1) and bottom (D2|D3) halves
@@ -934,8 +938,9 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
     // of memory latency); the kernels run 256 threads.  A thread takes the
     // same (row, column) of the four subbands.
     constexpr int TOT = NR * NC, CNT = (TOT + 255) / 256;
+    // 32-bit offsets from per-subband bases (2D lines have M <= 2^13)
     const T* base[4] = {lb, xb + n0, xb + (int64_t)n0 * M, xb + (int64_t)n0 * M + n0};
-    const int64_t ld[4] = {ldll, (int64_t)M, (int64_t)M, (int64_t)M};
+    const int ld[4] = {(int)ldll, M, M, M};
     T v[CNT][4];
 #pragma unroll
     for (int u = 0; u < CNT; ++u) {
@@ -1059,17 +1064,17 @@ __device__ __forceinline__ void syn_tile_rw(int tile, int64_t b, const T* llsrc,
         for (int e = 0; e < 4; ++e) W[cc * (TS + 1) + 4 * g4 + e] = o[e];
       } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) dst[b * dstb + (int64_t)(r0 + 4 * g4 + e) * lddst + c0 + cc] = o[e];
+        for (int e = 0; e < 4; ++e) dst[b * dstb + (int64_t)r0 * lddst + c0 + ((4 * g4 + e) * (int)lddst + cc)] = o[e];
       }
     }
   }
   if (xt) {
     // row c0 + rr of the M x M transposed buffer, columns r0 .. r0 + TS - 1
     __syncthreads();
-    T* xtb = xt + b * (int64_t)M * M;
+    T* xtt = xt + b * (int64_t)M * M + (int64_t)c0 * M + r0;
     for (int e = tid; e < TS * TS; e += nthr) {
       const int rr = e / TS, cl = e - rr * TS;
-      xtb[(int64_t)(c0 + rr) * M + r0 + cl] = W[rr * (TS + 1) + cl];
+      xtt[rr * M + cl] = W[rr * (TS + 1) + cl];
     }
   }
 }
@@ -1083,8 +1088,8 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
   using AG = AnaGeom<T, PM, TSA>;
   constexpr int NR = AG::NR, NRP = AG::NRP, NWA = AG::NWA, NCH = AG::NCH;
   const int n0 = 1 << j, n1 = 2 * n0;
-  const int tiles = n0 / TSA;
-  const int m0 = (tile / tiles) * TSA, k0 = (tile % tiles) * TSA;
+  const int lt = j - ilog2c(TSA);             // tiles per row: n0 / TSA = 2^lt
+  const int m0 = (tile >> lt) * TSA, k0 = (tile & ((1 << lt) - 1)) * TSA;
   const int ir0 = 2 * m0 - PM + 1, ic0 = 2 * k0 - PM + 1;
   T* S = smem;                    // [NR][NRP] window of level j+1
   T* Hc = S + AG::HOFF;           // [2][TSA][NCH]: column analysis, lo then hi
@@ -1109,7 +1114,7 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
         } else {
           ok = gi >= 0 && gi < n1 && gc >= 0 && gc < n1;
         }
-        if (ok) v[u] = xt ? xtb[(int64_t)gc * M + gi] : sb[(int64_t)gi * ldsrc + gc];
+        if (ok) v[u] = xt ? xtb[gc * M + gi] : sb[gi * (int)ldsrc + gc];
       }
     }
 #pragma unroll
@@ -1209,12 +1214,12 @@ __device__ __forceinline__ void ana_tile_rw(int tile, int64_t b, const T* src, i
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         if (row < TSA) {
-          if (lldst) lldst[b * llb + (int64_t)mm * ldll + kq + e] = lo[e];
-          else xb[(int64_t)mm * M + kq + e] = lo[e];
-          xb[(int64_t)mm * M + n0 + kq + e] = hi[e];
+          if (lldst) lldst[b * llb + (mm * (int)ldll + kq + e)] = lo[e];
+          else xb[mm * M + kq + e] = lo[e];
+          xb[mm * M + n0 + kq + e] = hi[e];
         } else {
-          xb[(int64_t)(n0 + mm) * M + kq + e] = lo[e];
-          xb[(int64_t)(n0 + mm) * M + n0 + kq + e] = hi[e];
+          xb[(n0 + mm) * M + kq + e] = lo[e];
+          xb[(n0 + mm) * M + n0 + kq + e] = hi[e];
         }
       }
     }
@@ -1236,7 +1241,7 @@ __host__ __device__ inline int ana_rw_ts(int n0) { return n0 >= 16 ? 16 : (n0 >=
 // (forward: steps 0 .. nl-2, adjoint: steps 1 .. nl-1); the rest rides with
 // step nl-1.  Step it runs items [q0, q0 + nq) of Q after its level tiles.
 template <typename F>
-__device__ __forceinline__ void tx_share(int it, int nl, bool fwd, int grid, int Q, F&& busy, int& q0, int& nq) {
+static void tx_share(int it, int nl, bool fwd, int grid, int Q, F&& busy, int& q0, int& nq) {
   int used = 0;
   q0 = 0;
   nq = 0;
@@ -1259,11 +1264,13 @@ __device__ __forceinline__ void tx_share(int it, int nl, bool fwd, int grid, int
 template <typename T>
 __device__ __forceinline__ void tx_tile(const T* src, T* dst, int a0, int b0, int M, T* smem, int tid) {
   constexpr int CNT = 64 * 64 / 256;
+  src += (int64_t)a0 * M + b0;
+  dst += (int64_t)b0 * M + a0;
   T v[CNT];
 #pragma unroll
   for (int u = 0; u < CNT; ++u) {
     const int e = tid + 256 * u, r = e >> 6, c = e & 63;
-    v[u] = src[(int64_t)(a0 + r) * M + b0 + c];
+    v[u] = src[r * M + c];
   }
 #pragma unroll
   for (int u = 0; u < CNT; ++u) {
@@ -1274,7 +1281,7 @@ __device__ __forceinline__ void tx_tile(const T* src, T* dst, int a0, int b0, in
 #pragma unroll
   for (int u = 0; u < CNT; ++u) {
     const int e = tid + 256 * u, rr = e >> 6, cl = e & 63;
-    dst[(int64_t)(b0 + rr) * M + a0 + cl] = smem[cl * 65 + rr];
+    dst[rr * M + cl] = smem[cl * 65 + rr];
   }
 }
 
@@ -1283,12 +1290,10 @@ __device__ __forceinline__ void tx_tile(const T* src, T* dst, int a0, int b0, in
 // 64 x 64 tile; forward x -> XT, adjoint XT -> x
 template <typename T>
 __device__ __forceinline__ void tx_item(int q, int M, const T* src, T* dst, bool fwd, T* smem, int tid) {
-  const int Mh = M / 2, nb = Mh / 64, per_b = 3 * nb * nb;
-  const int b = q / per_b;
-  int r = q - b * per_b;
-  const int d = r / (nb * nb);
-  r -= d * nb * nb;
-  const int R0 = (d >= 1 ? Mh : 0) + (r / nb) * 64, C0 = (d != 1 ? Mh : 0) + (r % nb) * 64;
+  const int Mh = M / 2, lnb = __ffs(Mh) - 7;   // nb = Mh / 64 = 2^lnb tiles per quadrant side
+  const int bd = q >> (2 * lnb), r = q & ((1 << (2 * lnb)) - 1);
+  const int b = bd / 3, d = bd - 3 * b;
+  const int R0 = (d >= 1 ? Mh : 0) + (r >> lnb) * 64, C0 = (d != 1 ? Mh : 0) + (r & ((1 << lnb) - 1)) * 64;
   const int64_t off = (int64_t)b * M * M;
   if (fwd) tx_tile(src + off, dst + off, R0, C0, M, smem, tid);
   else tx_tile(src + off, dst + off, C0, R0, M, smem, tid);
@@ -1323,34 +1328,27 @@ __global__ void __launch_bounds__(256, 2) k_syn2d_levels(CoarseIO<T> io, Tables<
   const int M = io.M, Mh = M / 2;
   const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
   const bool tx = io.XT != nullptr;
-  const int Q = tx ? 3 * (Mh / 64) * (Mh / 64) * io.batch : 0;
-  auto busy = [&](int k) {
-    const int n1 = 2 << (io.J0 + k), TR = rw ? syn_rw_ts(n1) : 0, TS = TR ? TR : syn_tile(n1);
-    return (n1 / TS) * (n1 / TS) * io.batch;
-  };
   for (int it = 0; it < io.nl; ++it) {
     const int j = io.J0 + it, n1 = 2 << j;
     const int TR = rw ? syn_rw_ts(n1) : 0;
-    const int TS = TR ? TR : syn_tile(n1), tiles = (n1 / TS) * (n1 / TS);
+    const int TS = TR ? TR : syn_tile(n1), tiles = (n1 / TS) * (n1 / TS), ltiles = __ffs(tiles) - 1;
     const T* src = it == 0 ? io.x : ((io.nl - it) % 2 == 0 ? io.XS : io.XS2);
     const int64_t ld = it == 0 ? M : Mh, sb = it == 0 ? MM : HH;
     T* dst = (io.nl - 1 - it) % 2 == 0 ? io.XS : io.XS2;
     T* xt = tx && it == io.nl - 1 ? io.XT : nullptr;
-    const int TB = tiles * io.batch;
-    int q0 = 0, nq = 0;
-    if (tx) tx_share(it, io.nl, true, (int)gridDim.x, Q, busy, q0, nq);
+    const int TB = tiles * io.batch, q0 = io.tq0[it], nq = tx ? io.tnq[it] : 0;
     for (int t = blockIdx.x; t < TB + nq; t += gridDim.x) {
       __syncthreads();   // the previous tile's windows are no longer read
       if (t >= TB)
         tx_item(q0 + t - TB, M, io.x, io.XT, true, sm + off, tid);
       else if (TR == 32)
-        syn_tile_rw<T, PM, 32>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, ct, Dl, Dr, G.p,
+        syn_tile_rw<T, PM, 32>(t & (tiles - 1), t >> ltiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, ct, Dl, Dr, G.p,
                                G.Lb, per, sm + off, tid, nthr, xt);
       else if (TR == 16)
-        syn_tile_rw<T, PM, 16>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, ct, Dl, Dr, G.p,
+        syn_tile_rw<T, PM, 16>(t & (tiles - 1), t >> ltiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, ct, Dl, Dr, G.p,
                                G.Lb, per, sm + off, tid, nthr, xt);
       else
-        syn2d_tile<T, 0>(t % tiles, t / tiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, TS, st, sm + off, G,
+        syn2d_tile<T, 0>(t & (tiles - 1), t >> ltiles, src, ld, sb, io.x, M, dst, (int64_t)Mh, HH, j, TS, st, sm + off, G,
                          tid, nthr);
     }
     if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, it, limit)) break;
@@ -1386,33 +1384,26 @@ __global__ void __launch_bounds__(256, 2) k_ana2d_levels(CoarseIO<T> io, Tables<
   const int64_t HH = (int64_t)Mh * Mh;
   const int R = io.J0 + io.nl + 1;
   const bool tx = io.XT != nullptr;
-  const int Q = tx ? 3 * (Mh / 64) * (Mh / 64) * io.batch : 0;
-  auto busy = [&](int k) {
-    const int n0 = 1 << (R - 2 - k), TR = rw ? ana_rw_ts(n0) : 0, TS = TR ? TR : ana_tile(n0);
-    return (n0 / TS) * (n0 / TS) * io.batch;
-  };
   for (int it = 0; it < io.nl; ++it) {
     const int j = R - 2 - it, n0 = 1 << j;
     const int TR = rw ? ana_rw_ts(n0) : 0;
-    const int TS = TR ? TR : ana_tile(n0), tiles = (n0 / TS) * (n0 / TS);
+    const int TS = TR ? TR : ana_tile(n0), tiles = (n0 / TS) * (n0 / TS), ltiles = __ffs(tiles) - 1;
     const T* src = it % 2 == 0 ? io.XS : io.XS2;
     T* dst = it == io.nl - 1 ? nullptr : (it % 2 == 0 ? io.XS2 : io.XS);
     const T* xt = tx && it == 0 ? io.XT : nullptr;
-    const int TB = tiles * io.batch;
-    int q0 = 0, nq = 0;
-    if (tx) tx_share(it, io.nl, false, (int)gridDim.x, Q, busy, q0, nq);
+    const int TB = tiles * io.batch, q0 = io.tq0[it], nq = tx ? io.tnq[it] : 0;
     for (int t = blockIdx.x; t < TB + nq; t += gridDim.x) {
       __syncthreads();
       if (t >= TB)
         tx_item(q0 + t - TB, M, (const T*)io.XT, io.xout, false, sm + off, tid);
       else if (TR == 16)
-        ana_tile_rw<T, PM, 16>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, ct,
+        ana_tile_rw<T, PM, 16>(t & (tiles - 1), t >> ltiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, ct,
                                Dl, Dr, G.p, G.Lb, per, sm + off, tid, nthr, xt);
       else if (TR == 8)
-        ana_tile_rw<T, PM, 8>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, ct,
+        ana_tile_rw<T, PM, 8>(t & (tiles - 1), t >> ltiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, ct,
                               Dl, Dr, G.p, G.Lb, per, sm + off, tid, nthr, xt);
       else
-        ana2d_tile<T, 0>(t % tiles, t / tiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, TS, st,
+        ana2d_tile<T, 0>(t & (tiles - 1), t >> ltiles, src, (int64_t)Mh, HH, io.xout, M, dst, (int64_t)Mh, HH, j, TS, st,
                          sm + off, G, tid, nthr);
     }
     if (it + 1 < io.nl && !grid_barrier(bar, gridDim.x, it, limit)) break;
@@ -1884,7 +1875,7 @@ static void pm_dispatch(int p, F&& f) {
 // finest coarse level and 64-aligned quadrants)
 static bool coarse_tx_ok(const Plan& P) {
   const int nl = P.R - 1 - P.J0;
-  return nl >= 2 && P.d_sync && P.coarse_ok && P.M % 128 == 0 &&
+  return nl >= 2 && nl <= kMaxCoarse && P.d_sync && P.coarse_ok && P.M % 128 == 0 &&
          (P.bd == UW_BOUNDARY_PERIODIC || P.d_coarse) && !getenv_flag("UW_COARSE_PER_LEVEL") &&
          !getenv_flag("UW_COARSE_GENERIC") && !getenv_flag("UW_COARSE_SEPARATE_TRANSPOSE");
 }
@@ -1897,7 +1888,7 @@ template <typename T>
 static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout, T* XS, T* XS2, T* XT, int batch,
                                 bool fwd, Launcher& L) {
   const int nl = P.R - 1 - P.J0;
-  if (nl < 2 || !P.d_sync || getenv_flag("UW_COARSE_PER_LEVEL")) return false;
+  if (nl < 2 || nl > kMaxCoarse || !P.d_sync || getenv_flag("UW_COARSE_PER_LEVEL")) return false;
   const bool rw = P.coarse_ok && !getenv_flag("UW_COARSE_GENERIC");
   const T* Dg = nullptr;
   if (P.d_coarse && P.bd != UW_BOUNDARY_PERIODIC) {
@@ -1950,7 +1941,7 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
       sm = std::max(sm, sizeof(T) * (head + 64 * 65));
       bytes += sizeof(T) * (double)batch * 6.0 * Mh * Mh;
     }
-    CoarseIO<T> io{x, xout, XS, XS2, XT, P.M, P.J0, nl, batch};
+    CoarseIO<T> io{x, xout, XS, XS2, XT, P.M, P.J0, nl, batch, {}, {}};
     const CTaps<T, PM> ct = make_ctaps<T, PM>(P);
     auto kern = fwd ? k_syn2d_levels<T, PM> : k_ana2d_levels<T, PM>;
     set_smem_limit((const void*)kern);
@@ -1964,6 +1955,23 @@ static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout
     }
     // at most two CTAs per SM: fewer arrivals at each grid barrier
     const int grid = (int)std::min<int64_t>((int64_t)std::min(per, 2) * nsm, (int64_t)max_tiles * batch + Q);
+    if (XT) {
+      // the level tiles of step k, as the kernels count them
+      auto busy = [&](int k) {
+        int n, TS;
+        if (fwd) {
+          n = 2 << (P.J0 + k);
+          const int TR = rw ? syn_rw_ts(n) : 0;
+          TS = TR ? TR : syn_tile(n);
+        } else {
+          n = 1 << (P.R - 2 - k);
+          const int TR = rw ? ana_rw_ts(n) : 0;
+          TS = TR ? TR : ana_tile(n);
+        }
+        return (n / TS) * (n / TS) * batch;
+      };
+      for (int it = 0; it < nl; ++it) tx_share(it, nl, fwd, grid, Q, busy, io.tq0[it], io.tnq[it]);
+    }
     L.pre(fwd ? "idwt2d_levels" : "dwt2d_levels", bytes);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
