@@ -471,6 +471,85 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_uneven(args):
+    """The batched uneven workload (instances of R in 6..9, q in 1..2,
+    p in {1,2,4,6,8}, either boundary, alpha in [1, 2], 10-40% masks, seed 3):
+    one plan per instance in a plan group, tuned, its forward + adjoint pair
+    captured as one CUDA graph; pairs/s over all instances, and the same plans
+    issued one after another on one stream for comparison.  One JSON line."""
+    import numpy as np
+    import torch
+    from oracle import wavelets as W
+    from paper_2106_00554_gb300 import F32, PERIODIC, VMP, Plan, PlanGroup, inputs
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(3)
+    t0 = time.perf_counter()
+    plans, xd, yd = [], [], []
+    for _ in range(args.uneven):
+        p = int(rng.choice([1, 2, 4, 6, 8]))
+        R_ = int(rng.choice([r for r in (6, 7, 8, 9) if r >= W.default_J0(p) + 1]))
+        q = int(rng.choice([1, 2]))
+        bd = int(rng.choice([PERIODIC, VMP]))
+        omega = inputs.mask_2d(rng, 2 ** (R_ + q), float(rng.uniform(0.1, 0.4)))
+        pl = Plan(2, R_, q, p, bd, omega=omega)
+        plans.append(pl)
+        xd.append(torch.tensor(inputs.coeffs_2d(rng, R_, pl.J0, float(rng.uniform(1.0, 2.0))),
+                               dtype=torch.float32, device="cuda"))
+        yd.append(torch.tensor(rng.standard_normal(pl.m), dtype=torch.float32, device="cuda"))
+    setup_s = time.perf_counter() - t0
+    yo = [torch.empty_like(y) for y in yd]
+    xo = [torch.empty_like(x) for x in xd]
+    nst = 16
+    group = PlanGroup(plans, nstreams=nst)
+    t0 = time.perf_counter()
+    group.tune([x.clone() for x in xd], [torch.empty_like(y) for y in yd], F32, reps=2)
+    tune_s = time.perf_counter() - t0
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        group.forward(xd, yo, F32, stream=s)
+        group.adjoint(yd, xo, F32, stream=s)
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        group.forward(xd, yo, F32, stream=s)
+        group.adjoint(yd, xo, F32, stream=s)
+
+    def timed(fn, k):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(k):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    k = max(3, min(args.steps, 50))
+    ms_graph = timed(graph.replay, k)
+    group.close()
+
+    def sequential():
+        with torch.cuda.stream(s):
+            for pl, x, y, a, b in zip(plans, xd, yd, yo, xo):
+                pl.forward(x, a, precision=F32, stream=s)
+                pl.adjoint(y, b, precision=F32, stream=s)
+
+    ms_seq = timed(sequential, max(3, k // 5))
+    n = len(plans)
+    print(json.dumps({
+        "metric": f"batched uneven 2D U x + U* y pairs/s ({n} instances)", "value": n * 1000.0 / ms_graph,
+        "unit": "pairs/s", "higher_is_better": True, "ms_per_step": ms_graph, "steps": k, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{n} instances: R in 6..9, q in 1..2, p in {{1,2,4,6,8}}, periodic or VMP, "
+                               "alpha in [1,2], 10-40% radial multilevel masks, seed 3",
+                   "launch": f"plan group over {nst} streams, tuned, pair captured as one CUDA graph",
+                   "setup_s": round(setup_s, 2), "tune_s": round(tune_s, 2)},
+        "sequential": {"value": n * 1000.0 / ms_seq, "unit": "pairs/s", "ms_per_step": ms_seq,
+                       "how": "each plan's forward and adjoint issued in turn on one stream, eager"}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,7 +565,12 @@ def main():
                     help="level per dimension (default 11 = the benchmark workload; smaller only for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--uneven", type=int, default=0,
+                    help="instead of the benchmark workload: the batched uneven workload with this many instances")
     args = ap.parse_args()
+    if args.uneven:
+        run_uneven(args)
+        return
     globals()["R"] = args.R
     if args.R != 11:
         n = 2 ** (args.R + 1)

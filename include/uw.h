@@ -206,6 +206,38 @@ int uw_adjoint_host_async(const uw_plan* plan, int precision, const void* y_host
 int uw_host_wait(const uw_plan* plan);
 
 /*
+ * Plan groups -- many independent products (any mix of d, R, q, p, boundary
+ * and masks) issued as one unit, e.g. to be captured into one CUDA graph.
+ *
+ * uw_group_create(plans, n, nstreams): a group over n existing plans (still
+ *   owned by the caller; they must outlive the group).  While the group
+ *   exists, its plans run their coarse 2D levels as one launch per level
+ *   (kernels of different instances may then run at the same time; no grid-
+ *   wide barrier is shared between them); uw_group_destroy restores the plans'
+ *   launch choices.  nstreams in [1, 64]: internal streams.  NULL on error.
+ * uw_group_forward / uw_group_adjoint(g, precision, in, out, stream): the
+ *   product of instance i on device buffers in[i] -> out[i] (batch 1 each,
+ *   layouts as uw_forward / uw_adjoint).  The instances are spread round-robin
+ *   over the group's streams, forked from `stream` by an event and joined
+ *   back into it, so work later on `stream` sees every result and a capture of
+ *   `stream` records one graph with nstreams parallel branches.
+ * uw_group_tune(g, precision, x, y, reps, stream): for every instance, times
+ *   reps forward + adjoint pairs (on x[i] -> y[i] -> x[i], which it
+ *   overwrites) with each line-operator variant the plan supports -- the
+ *   specialised kernels that apply to its sizes, or the generic ones -- and
+ *   keeps the fastest for that plan.  Synchronises `stream`.
+ * Errors: UW_ERR_INVALID_ARG (null pointers, n < 1, nstreams out of range,
+ *   precision, a plan's own argument checks), UW_ERR_OOM (streams or events),
+ *   UW_ERR_CUDA; a failing instance stops the call with its status.
+ */
+typedef struct uw_group uw_group;
+uw_group* uw_group_create(uw_plan* const* plans, int n, int nstreams);
+int uw_group_forward(uw_group* group, int precision, const void* const* x, void* const* y, void* stream);
+int uw_group_adjoint(uw_group* group, int precision, const void* const* y, void* const* x, void* stream);
+int uw_group_tune(uw_group* group, int precision, void* const* x, void* const* y, int reps, void* stream);
+void uw_group_destroy(uw_group* group);
+
+/*
  * Solver kernels (element-wise, no plan): the pieces of an l1-regularised
  * recovery  min_x 1/2 ||P_Omega U x - y||^2 + lam ||x||_1  (the
  * compressive-sensing use of the products, Sec. 1.2 and Remark 4.2) that are

@@ -145,3 +145,39 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class PlanGroup:
+    """uw_group over existing Plans (uneven sizes allowed): one call issues
+    every instance's product, spread over `nstreams` internal streams forked
+    from and joined back into the caller's stream (capturable as one graph).
+    While the group exists its plans run their coarse 2D levels one launch
+    per level.  tune() keeps, per plan, the faster line-operator variant."""
+
+    def __init__(self, plans, nstreams=8):
+        self.plans = list(plans)
+        self._g = _lib.uw_group_create([pl._h for pl in self.plans], nstreams)
+
+    def forward(self, xs, ys, precision, stream=None):
+        _lib.uw_group_forward(self._g, precision, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys],
+                              _stream_ptr(stream))
+
+    def adjoint(self, ys, xs, precision, stream=None):
+        _lib.uw_group_adjoint(self._g, precision, [y.data_ptr() for y in ys], [x.data_ptr() for x in xs],
+                              _stream_ptr(stream))
+
+    def tune(self, xs, ys, precision, reps=3, stream=None):
+        """Overwrites xs and ys (each pair maps x -> y -> x)."""
+        _lib.uw_group_tune(self._g, precision, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys], reps,
+                           _stream_ptr(stream))
+
+    def close(self):
+        if self._g:
+            _lib.uw_group_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

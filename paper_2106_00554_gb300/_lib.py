@@ -39,6 +39,11 @@ SIGNATURES = {
     "uw_forward_host_async": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
     "uw_adjoint_host_async": (_int, [_c_p, _int, _c_p, _c_p, _int, _c_p]),
     "uw_host_wait": (_int, [_c_p]),
+    "uw_group_create": (_c_p, [ctypes.POINTER(_c_p), _int, _int]),
+    "uw_group_forward": (_int, [_c_p, _int, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p), _c_p]),
+    "uw_group_adjoint": (_int, [_c_p, _int, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p), _c_p]),
+    "uw_group_tune": (_int, [_c_p, _int, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p), _int, _c_p]),
+    "uw_group_destroy": (None, [_c_p]),
     "uw_plan_destroy": (None, [_c_p]),
     "uw_plan_table": (_i64, [_c_p, _int, _dp, _i64]),
     "uw_host_table": (_i64, [_int, _int, _int, _dp, _i64]),
@@ -143,6 +148,33 @@ def uw_adjoint_host_async(h, precision, y_ptr, x_ptr, batch, stream):
 
 def uw_host_wait(h):
     _chk(lib().uw_host_wait(h), "uw_host_wait")
+
+
+def _ptrs(ptrs):
+    return (_c_p * len(ptrs))(*ptrs)
+
+
+def uw_group_create(plan_handles, nstreams):
+    g = lib().uw_group_create(_ptrs(plan_handles), len(plan_handles), nstreams)
+    if not g:
+        raise UWError(lib().uw_last_error(), "uw_group_create")
+    return g
+
+
+def uw_group_forward(g, precision, x_ptrs, y_ptrs, stream):
+    _chk(lib().uw_group_forward(g, precision, _ptrs(x_ptrs), _ptrs(y_ptrs), stream), "uw_group_forward")
+
+
+def uw_group_adjoint(g, precision, y_ptrs, x_ptrs, stream):
+    _chk(lib().uw_group_adjoint(g, precision, _ptrs(y_ptrs), _ptrs(x_ptrs), stream), "uw_group_adjoint")
+
+
+def uw_group_tune(g, precision, x_ptrs, y_ptrs, reps, stream):
+    _chk(lib().uw_group_tune(g, precision, _ptrs(x_ptrs), _ptrs(y_ptrs), reps, stream), "uw_group_tune")
+
+
+def uw_group_destroy(g):
+    lib().uw_group_destroy(g)
 
 
 def uw_fista_step(precision, n, z, G, B, x0, tau, lam, beta, x1, z1, stream):

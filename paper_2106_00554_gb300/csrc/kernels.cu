@@ -1769,17 +1769,18 @@ static void launch_line(bool fwd, const Plan& P, const Geo& G, const T* in, T* o
 template <>
 void launch_line<float>(bool fwd, const Plan& P, const Geo& G, const float* in, float* out, const LineIO& io,
                         int nblocks, Launcher& L) {
-  if (L.split && tc_eligible(P, io, in, out, fwd)) {
+  if (L.split && P.line_variant == 0 && tc_eligible(P, io, in, out, fwd)) {
     if (L.armed) L.retag(P.prof->names[L.cur.id] + "_tc");
     L.note(tc_launch(fwd, P, in, out, io, nblocks, L.s));
     return;
   }
-  if (!L.split && f32_eligible(P, io, in, out, fwd) && !getenv_flag("UW_GENERIC_LINES")) {
+  const bool generic = P.line_variant == 1 || getenv_flag("UW_GENERIC_LINES");
+  if (!L.split && !generic && f32_eligible(P, io, in, out, fwd)) {
     if (L.armed) L.retag(P.prof->names[L.cur.id] + "_f32");
     L.note(f32_launch(fwd, P, in, out, io, nblocks, L.s));
     return;
   }
-  if (line2_eligible(P) && !getenv_flag("UW_GENERIC_LINES")) {
+  if (!generic && line2_eligible(P)) {
     L.note(line2_launch(fwd, P, G, in, out, io, nblocks, L.s));
     return;
   }
@@ -1876,7 +1877,7 @@ static void pm_dispatch(int p, F&& f) {
 static bool coarse_tx_ok(const Plan& P) {
   const int nl = P.R - 1 - P.J0;
   return nl >= 2 && nl <= kMaxCoarse && P.d_sync && P.coarse_ok && P.M % 128 == 0 &&
-         (P.bd == UW_BOUNDARY_PERIODIC || P.d_coarse) && !getenv_flag("UW_COARSE_PER_LEVEL") &&
+         (P.bd == UW_BOUNDARY_PERIODIC || P.d_coarse) && P.coarse_mode == 0 && !getenv_flag("UW_COARSE_PER_LEVEL") &&
          !getenv_flag("UW_COARSE_GENERIC") && !getenv_flag("UW_COARSE_SEPARATE_TRANSPOSE");
 }
 
@@ -1888,7 +1889,7 @@ template <typename T>
 static bool launch_coarse_fused(const Plan& P, const Geo& G, const T* x, T* xout, T* XS, T* XS2, T* XT, int batch,
                                 bool fwd, Launcher& L) {
   const int nl = P.R - 1 - P.J0;
-  if (nl < 2 || nl > kMaxCoarse || !P.d_sync || getenv_flag("UW_COARSE_PER_LEVEL")) return false;
+  if (nl < 2 || nl > kMaxCoarse || !P.d_sync || P.coarse_mode == 1 || getenv_flag("UW_COARSE_PER_LEVEL")) return false;
   const bool rw = P.coarse_ok && !getenv_flag("UW_COARSE_GENERIC");
   const T* Dg = nullptr;
   if (P.d_coarse && P.bd != UW_BOUNDARY_PERIODIC) {

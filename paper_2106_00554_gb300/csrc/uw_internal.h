@@ -97,6 +97,11 @@ struct Plan {
   void* s_down = nullptr;
   void* ev[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   int slot = 0;
+  // launch choices (a plan group and its tuner set them): line operators
+  // 0 = the fastest specialised kernel that applies, 1 = the generic kernels;
+  // coarse 2D levels 0 = one cooperative launch, 1 = one launch per level
+  int line_variant = 0;
+  int coarse_mode = 0;
   int device = 0;
   Profiler* prof = nullptr;
   TcGeo tc;                      // split-BF16 line operators (tc.ok = 0: not eligible)
