@@ -55,6 +55,10 @@ extern "C" {
 typedef struct uw_plan uw_plan;
 
 enum { UW_BOUNDARY_PERIODIC = 0, UW_BOUNDARY_VMP = 1 };
+/* OR'd into p (uw_plan_create, uw_host_table): the least-asymmetric
+ * Daubechies filter (symlet) with p vanishing moments instead of the
+ * extremal-phase one (Table 1's sym rows) */
+enum { UW_FILTER_SYMLET = 0x100 };
 enum { UW_F64 = 0, UW_F32 = 1, UW_F32_SPLIT_BF16 = 2 };
 enum {
   UW_OK = 0,
@@ -72,7 +76,13 @@ enum {
  *   d        dimension, 1 or 2 (Sec. 4 / Sec. 5)
  *   R        level of the reconstruction space, M = 2^R per dimension
  *   q        oversampling, N = 2^{R+q} per dimension (Remark 4.1), 0..6
- *   p        vanishing moments of the Daubechies wavelet (nu), 1..10
+ *   p        vanishing moments of the Daubechies wavelet (nu), 1..10;
+ *            p | UW_FILTER_SYMLET selects the least-asymmetric filter
+ *            (symlet): among the choices of one zero per reciprocal pair
+ *            of m0 (Daubechies' construction), the one whose unwrapped
+ *            phase is closest to linear in mean square on 256 points of
+ *            (0, pi), oriented with its energy in the first half of the
+ *            taps (equal to the extremal-phase filter for p <= 3)
  *   boundary UW_BOUNDARY_PERIODIC or UW_BOUNDARY_VMP (Sec. 3.2)
  * Tables (Sec. 4.1 "computed a priori", Sec. 4.3, Prop. 4.4): the filter h,
  * the (2p-1) 2^q cell integrals of phi, the boundary cell-integral rows and

@@ -26,34 +26,122 @@ def _mp():
 
 
 # ----------------------------------------------------------------------------
-# Daubechies filter (Sec. 3.2: orthonormal, compactly supported, p vanishing
-# moments, minimal support; "Daubechies wavelet" = extremal phase).
+# Daubechies filters (Sec. 3.2: orthonormal, compactly supported, p vanishing
+# moments, minimal support).  "Daubechies wavelet" = extremal phase; the
+# symlets of Table 1 are the least-asymmetric choice among the same family.
 # ----------------------------------------------------------------------------
-@lru_cache(maxsize=None)
-def daubechies_mp(p):
-    """Extremal-phase Daubechies filter h_k, k = -p+1..p, as mpf list.
+class Sym(int):
+    """p for the least-asymmetric Daubechies filter (symlet) with p vanishing
+    moments.  It behaves as the integer p everywhere; the table caches are
+    typed, so its tables are kept apart from the extremal-phase ones."""
 
-    Daubechies' construction: |m0(xi)|^2 = cos^{2p}(xi/2) P(sin^2(xi/2)) with
-    P(y) = sum_{k<p} C(p-1+k, k) y^k.  Each root y of P gives a reciprocal
-    pair z, 1/z of z^2 - (2 - 4y) z + 1; the classical table (h_0 largest
-    first) keeps the root of modulus > 1 in m0(z) = sum h_k z^{k+p-1}.
-    """
-    m = _mp()
+    def __repr__(self):
+        return f"Sym({int(self)})"
+
+
+def _reciprocal_roots(m, p):
+    """Daubechies' construction: |m0(xi)|^2 = cos^{2p}(xi/2) P(sin^2(xi/2))
+    with P(y) = sum_{k<p} C(p-1+k, k) y^k.  Each root y of P gives a
+    reciprocal pair z, 1/z of z^2 - (2 - 4y) z + 1.  Returns the pairs as
+    (z outside the unit circle, its reciprocal), one per root of P."""
+    if p == 1:
+        return []
+    coeffs = [m.mpf(comb(p - 1 + k, k)) for k in range(p)][::-1]
+    out = []
+    for y in m.polyroots(coeffs, maxsteps=400, extraprec=4 * DPS):
+        b = 2 - 4 * y
+        d = m.sqrt(b * b - 4)
+        z1, z2 = (b + d) / 2, (b - d) / 2
+        out.append((z1, z2) if abs(z1) > 1 else (z2, z1))
+    return out
+
+
+def _filter_from_zeros(m, p, zeros):
+    """h_k, k = -p+1..p (mpf list), of m0(z) = sum h_k z^{k+p-1} with a zero
+    of order p at z = -1 and the given other zeros, normalised to sum h = sqrt2."""
     Q = [m.mpc(1)]
     for _ in range(p):
         Q = _polymul(Q, [m.mpc(1), m.mpc(1)])
-    if p > 1:
-        coeffs = [m.mpf(comb(p - 1 + k, k)) for k in range(p)][::-1]
-        ys = m.polyroots(coeffs, maxsteps=400, extraprec=4 * DPS)
-        for y in ys:
-            b = 2 - 4 * y
-            d = m.sqrt(b * b - 4)
-            z1, z2 = (b + d) / 2, (b - d) / 2
-            z = z1 if abs(z1) > 1 else z2
-            Q = _polymul(Q, [-z, m.mpc(1)])
+    for z in zeros:
+        Q = _polymul(Q, [-z, m.mpc(1)])
     re = [c.real for c in Q]
     s = sum(re)
     return [m.sqrt(2) * c / s for c in re]
+
+
+ASYM_GRID = 256
+
+
+def phase_asymmetry(zeros):
+    """Asymmetry of the filter whose m0 has zeros of order p at -1 and the
+    given other zeros: m0(e^{-iw}) = c (1 + e^{-iw})^p R(e^{-iw}) with
+    R(z) = prod (z - z_k).  On (0, pi) the first factor has the exactly linear
+    phase -p w / 2, so the deviation of the phase of m0 from a line through
+    the origin is that of psi(w) = arg R(e^{-iw}) - arg R(1) (unwrapped); this
+    is the mean squared distance of psi from its least-squares line through
+    the origin on w_k = pi (k + 1/2) / 256, k < 256.  (Evaluating m0 itself
+    there is ill-conditioned near w = pi, where it has a zero of order p.)"""
+    z = np.asarray([complex(v) for v in zeros])
+    w = np.pi * (np.arange(ASYM_GRID) + 0.5) / ASYM_GRID
+    e = np.exp(-1j * w)
+    Rw = np.prod(e[:, None] - z[None, :], axis=1) if z.size else np.ones_like(e)
+    psi = np.unwrap(np.angle(Rw))
+    psi = psi - np.angle(np.prod(1 - z)) if z.size else psi
+    # psi(0+) must be near 0 after the shift; take the branch nearest 0
+    psi = psi - 2 * np.pi * np.round(psi[0] / (2 * np.pi))
+    b = (psi @ w) / (w @ w)
+    return float(np.mean((psi - b * w) ** 2))
+
+
+def _front_loaded(h):
+    """True if the energy centre sum n h_n^2 lies in the first half of 0..2p-1."""
+    e = [float(v) ** 2 for v in h]
+    return sum(i * v for i, v in enumerate(e)) < (len(e) - 1) / 2 * sum(e)
+
+
+@lru_cache(maxsize=None, typed=True)
+def daubechies_mp(p):
+    """Daubechies filter h_k, k = -p+1..p, as mpf list.
+
+    Extremal phase (p an int): every zero of m0 other than z = -1 is the
+    member of its reciprocal pair outside the unit circle (the classical
+    table, h_0 largest first).  Least asymmetric (p a ``Sym``): among the
+    choices of one member per pair (a complex pair of P's roots chosen
+    together, so that h is real), the one whose phase_asymmetry is smallest;
+    a choice and its complement give mirror-image filters with the same
+    asymmetry, and the one whose energy lies in the first half is kept (for
+    p <= 3 this is the extremal-phase filter again, as Table 1's equal
+    DB2/sym2 and DB3/sym3 rows say)."""
+    m = _mp()
+    pairs = _reciprocal_roots(m, int(p))
+    if not isinstance(p, Sym):
+        return _filter_from_zeros(m, int(p), [zo for zo, _ in pairs])
+    # groups: a real root of P, or a root with positive imaginary part together
+    # with its conjugate
+    tol = m.mpf(10) ** (-DPS // 2)
+    groups, used = [], [False] * len(pairs)
+    ys = [(2 - (zo + zi)) / 4 for zo, zi in pairs]      # back to the root y of P
+    for i in range(len(pairs)):
+        if used[i]:
+            continue
+        used[i] = True
+        if abs(ys[i].imag) < tol:
+            groups.append([i])
+            continue
+        j = min((k for k in range(len(pairs)) if not used[k]), key=lambda k: abs(ys[k] - m.conj(ys[i])))
+        used[j] = True
+        groups.append([i, j])
+    best = None
+    for mask in range(1 << max(len(groups) - 1, 0)):     # group 0 fixed: one of each mirror pair
+        zeros = []
+        for g, idx in enumerate(groups):
+            inside = g > 0 and (mask >> (g - 1)) & 1
+            zeros += [pairs[i][1] if inside else pairs[i][0] for i in idx]
+        a = phase_asymmetry(zeros)
+        if best is None or a < best[0]:
+            best = (a, zeros)
+    h = _filter_from_zeros(m, int(p), best[1])
+    return h if _front_loaded(h) else h[::-1]
 
 
 def _polymul(a, b):
@@ -84,7 +172,7 @@ def wavelet_filter(p):
 # Exact cell integrals of phi.  I_q[t] = int_{t/2^q}^{(t+1)/2^q} phi, the
 # "precomputed integrals" behind the taps W phi_{0,-l}(s) of Sec. 4.1.
 # ----------------------------------------------------------------------------
-@lru_cache(maxsize=None)
+@lru_cache(maxsize=None, typed=True)
 def _cells_mp(p, q):
     m = _mp()
     h = daubechies_mp(p)
@@ -127,7 +215,7 @@ def cell_integrals(p, q):
 # with G = delta when a translate lies in [0, inf) and G = 0 when one lies in
 # (-inf, 0].
 # ----------------------------------------------------------------------------
-@lru_cache(maxsize=None)
+@lru_cache(maxsize=None, typed=True)
 def _gram_left_mp(p):
     m = _mp()
     h = daubechies_mp(p)
@@ -209,7 +297,7 @@ def _gs(vectors, G):
     return out
 
 
-@lru_cache(maxsize=None)
+@lru_cache(maxsize=None, typed=True)
 def _edges_mp(p):
     m = _mp()
     trL = list(range(-p + 1, p))
@@ -223,7 +311,7 @@ def _edges_mp(p):
     return A, trL, B, trR
 
 
-@lru_cache(maxsize=None)
+@lru_cache(maxsize=None, typed=True)
 def _edge_cells_mp(p, q):
     m = _mp()
     A, trL, B, trR = _edges_mp(p)
@@ -311,7 +399,7 @@ def _side_rows(p, side):
     return rows_edge, rows_int, K, W
 
 
-@lru_cache(maxsize=None)
+@lru_cache(maxsize=None, typed=True)
 def _wavelets_mp(p, side):
     m = _mp()
     h = daubechies_mp(p)

@@ -62,7 +62,7 @@ def cell_matrix(R, q, p, bd):
     return T * 2.0 ** (-R / 2)
 
 
-@lru_cache(maxsize=None)
+@lru_cache(maxsize=None, typed=True)
 def synthesis_matrix(j, p, bd):
     """S_j (2^{j+1} x 2^{j+1}): column c holds the B_{phi,j+1} coordinates of
     phi^rep_{j,c} (c < 2^j) or psi^rep_{j,c-2^j}; s_{j+1} = S_j [s_j; d_j]."""

@@ -29,9 +29,11 @@ def _stream_ptr(stream):
 class Plan:
     """Owns one uw_plan (tables, mask and workspace on the current device)."""
 
-    def __init__(self, d, R, q, p, boundary=VMP, J0=None, omega=None, max_batch=1):
-        self.d, self.R, self.q, self.p, self.boundary = d, R, q, p, boundary
-        self._h = uw_plan_create(d, R, q, p, boundary)
+    def __init__(self, d, R, q, p, boundary=VMP, J0=None, omega=None, max_batch=1, symlet=False):
+        """symlet: the least-asymmetric Daubechies filter with p vanishing
+        moments (UW_FILTER_SYMLET) instead of the extremal-phase one."""
+        self.d, self.R, self.q, self.p, self.boundary, self.symlet = d, R, q, p, boundary, symlet
+        self._h = uw_plan_create(d, R, q, p | (_lib.UW_FILTER_SYMLET if symlet else 0), boundary)
         if J0 is not None:
             uw_plan_set_coarsest(self._h, J0)
         if omega is not None:

@@ -11,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libuw.so")
 
 UW_BOUNDARY_PERIODIC, UW_BOUNDARY_VMP = 0, 1
+UW_FILTER_SYMLET = 0x100
 UW_F64, UW_F32, UW_F32_SPLIT_BF16 = 0, 1, 2
 STATUS = {0: "UW_OK", 1: "UW_ERR_INVALID_ARG", 2: "UW_ERR_UNSUPPORTED", 3: "UW_ERR_OOM",
           4: "UW_ERR_CUDA", 5: "UW_ERR_TIMEOUT", 6: "UW_ERR_INTERNAL"}

@@ -131,7 +131,9 @@ static std::vector<CLD> poly_roots(const std::vector<LD>& c /* increasing */) {
   return z;
 }
 
-static std::vector<LD> daubechies(int p) {
+// Filter of m0(z) with a zero of order p at z = -1 and the given zeros,
+// normalised to sum h = sqrt 2 (h_k, k = -p+1..p).
+static std::vector<LD> filter_from_zeros(int p, const std::vector<CLD>& zeros) {
   std::vector<CLD> Q(1, CLD(1, 0));
   auto mul = [&](CLD a0, CLD a1) {  // Q *= (a0 + a1 z)
     std::vector<CLD> out(Q.size() + 1, CLD(0, 0));
@@ -142,26 +144,125 @@ static std::vector<LD> daubechies(int p) {
     Q.swap(out);
   };
   for (int i = 0; i < p; ++i) mul(1, 1);
-  if (p > 1) {
-    std::vector<LD> P(p);
-    LD binom = 1;  // C(p-1+k, k)
-    for (int k = 0; k < p; ++k) {
-      P[k] = binom;
-      binom = binom * (LD)(p + k) / (LD)(k + 1);
-    }
-    for (CLD y : poly_roots(P)) {
-      CLD b = (LD)2 - (LD)4 * y;
-      CLD d = std::sqrt(b * b - (LD)4);
-      CLD z1 = (b + d) / (LD)2, z2 = (b - d) / (LD)2;
-      CLD z = std::abs(z1) > 1 ? z1 : z2;
-      mul(-z, 1);
-    }
-  }
+  for (CLD z : zeros) mul(-z, 1);
   std::vector<LD> h(2 * p);
   LD s = 0;
   for (int i = 0; i < 2 * p; ++i) s += Q[i].real();
   for (int i = 0; i < 2 * p; ++i) h[i] = std::sqrt((LD)2) * Q[i].real() / s;
   return h;
+}
+
+// Least-asymmetric measure of the filter whose m0 has zeros of order p at -1
+// and the given other zeros: m0(e^{-iw}) = c (1 + e^{-iw})^p R(e^{-iw}),
+// R(z) = prod (z - z_k).  On (0, pi) the first factor has the linear phase
+// -p w / 2, so the measure is the mean squared distance of
+// psi(w) = arg R(e^{-iw}) - arg R(1) (unwrapped) from its least-squares line
+// through the origin on w_k = pi (k + 1/2) / 256, k < 256.  (m0 itself is
+// ill-conditioned near w = pi, where it has a zero of order p.)
+static LD phase_asymmetry(const std::vector<CLD>& zeros) {
+  const int K = 256;
+  const LD pi = 3.141592653589793238462643383279502884L;
+  CLD R1(1, 0);
+  for (CLD z : zeros) R1 *= CLD(1, 0) - z;
+  const LD a1 = std::atan2(R1.imag(), R1.real());
+  std::vector<LD> ph(K), w(K);
+  LD prev = 0, off = 0;
+  for (int k = 0; k < K; ++k) {
+    w[k] = pi * ((LD)k + 0.5L) / (LD)K;
+    const CLD e = std::polar((LD)1, -w[k]);
+    CLD Rw(1, 0);
+    for (CLD z : zeros) Rw *= e - z;
+    LD a = std::atan2(Rw.imag(), Rw.real()) - a1;
+    if (k == 0) {
+      a -= 2 * pi * std::nearbyint(a / (2 * pi));   // the branch nearest 0 at w -> 0
+    } else {
+      LD d = a + off - prev;                         // unwrap
+      while (d > pi) { off -= 2 * pi; d -= 2 * pi; }
+      while (d < -pi) { off += 2 * pi; d += 2 * pi; }
+    }
+    ph[k] = a + off;
+    prev = ph[k];
+  }
+  LD sw = 0, sp = 0;
+  for (int k = 0; k < K; ++k) {
+    sw += w[k] * w[k];
+    sp += ph[k] * w[k];
+  }
+  const LD b = sp / sw;
+  LD e = 0;
+  for (int k = 0; k < K; ++k) e += (ph[k] - b * w[k]) * (ph[k] - b * w[k]);
+  return e / (LD)K;
+}
+
+// Daubechies filters with p vanishing moments.  Each root y of
+// P(y) = sum_{k<p} C(p-1+k,k) y^k gives a reciprocal pair of zeros of m0.
+// Extremal phase keeps every member outside the unit circle.  The symlet
+// (least asymmetric) takes one member per pair -- a complex conjugate pair of
+// roots of P chosen together so that h stays real -- minimising
+// phase_asymmetry; a choice and its complement are mirror images, and the
+// one whose energy centre lies in the first half of the taps is kept.
+static std::vector<LD> daubechies(int p, bool symlet = false) {
+  if (p == 1) return filter_from_zeros(1, {});
+  std::vector<LD> P(p);
+  LD binom = 1;  // C(p-1+k, k)
+  for (int k = 0; k < p; ++k) {
+    P[k] = binom;
+    binom = binom * (LD)(p + k) / (LD)(k + 1);
+  }
+  const std::vector<CLD> ys = poly_roots(P);
+  std::vector<CLD> zo, zi;   // member outside / inside the unit circle
+  for (CLD y : ys) {
+    CLD b = (LD)2 - (LD)4 * y;
+    CLD d = std::sqrt(b * b - (LD)4);
+    CLD z1 = (b + d) / (LD)2, z2 = (b - d) / (LD)2;
+    zo.push_back(std::abs(z1) > 1 ? z1 : z2);
+    zi.push_back(std::abs(z1) > 1 ? z2 : z1);
+  }
+  if (!symlet) return filter_from_zeros(p, zo);
+  // groups of roots of P chosen together
+  const int n = (int)ys.size();
+  std::vector<std::vector<int>> groups;
+  std::vector<bool> used(n, false);
+  const LD tol = 1e-12L;
+  for (int i = 0; i < n; ++i) {
+    if (used[i]) continue;
+    used[i] = true;
+    if (std::abs(ys[i].imag()) < tol) {
+      groups.push_back({i});
+      continue;
+    }
+    int j = -1;
+    LD best = 0;
+    for (int k = 0; k < n; ++k)
+      if (!used[k] && (j < 0 || std::abs(ys[k] - std::conj(ys[i])) < best)) {
+        j = k;
+        best = std::abs(ys[k] - std::conj(ys[i]));
+      }
+    used[j] = true;
+    groups.push_back({i, j});
+  }
+  const int G = (int)groups.size();
+  std::vector<LD> best_h;
+  LD best_a = 0;
+  for (int mask = 0; mask < (1 << (G - 1)); ++mask) {   // group 0 fixed: one of each mirror pair
+    std::vector<CLD> zeros;
+    for (int g = 0; g < G; ++g) {
+      const bool inside = g > 0 && ((mask >> (g - 1)) & 1);
+      for (int i : groups[g]) zeros.push_back(inside ? zi[i] : zo[i]);
+    }
+    const LD a = phase_asymmetry(zeros);
+    if (best_h.empty() || a < best_a) {
+      best_a = a;
+      best_h = filter_from_zeros(p, zeros);
+    }
+  }
+  LD c = 0, e = 0;
+  for (int i = 0; i < 2 * p; ++i) {
+    c += (LD)i * best_h[i] * best_h[i];
+    e += best_h[i] * best_h[i];
+  }
+  if (!(c < (LD)(2 * p - 1) / 2 * e)) std::reverse(best_h.begin(), best_h.end());
+  return best_h;
 }
 
 // ---------------------------------------------------------------------------
@@ -496,7 +597,7 @@ bool build_tables(Plan& P, std::string& err) {
   P.Q = Q;
   P.Lb = 3 * p - 1;
   P.ntap = (2 * p - 1) * Q;
-  std::vector<LD> h = daubechies(p);
+  std::vector<LD> h = daubechies(p, P.family == 1);
   std::vector<LD> I = cell_integrals(h, p, q);
   if ((int)I.size() != P.ntap) { err = "cell integral table size"; return false; }
   P.h.resize(2 * p);
@@ -653,6 +754,8 @@ static int upload_mask(uw_plan* P, const int64_t* omega, int64_t m) {
 extern "C" {
 
 uw_plan* uw_plan_create(int d, int R, int q, int p, int boundary) {
+  const int family = (p & UW_FILTER_SYMLET) ? 1 : 0;
+  p &= ~UW_FILTER_SYMLET;
   if (d != 1 && d != 2) { fail(UW_ERR_INVALID_ARG, "d must be 1 or 2"); return nullptr; }
   if (p < 1 || p > 10) { fail(UW_ERR_INVALID_ARG, "p must be in 1..10"); return nullptr; }
   if (q < 0 || q > 6) { fail(UW_ERR_INVALID_ARG, "q must be in 0..6"); return nullptr; }
@@ -664,7 +767,7 @@ uw_plan* uw_plan_create(int d, int R, int q, int p, int boundary) {
   if (R < J0 || d * (R + q) > 26) { fail(UW_ERR_INVALID_ARG, "need J0(p) <= R and d (R + q) <= 26"); return nullptr; }
   uw_plan* P = new (std::nothrow) uw_plan();
   if (!P) { fail(UW_ERR_OOM, "host allocation failed"); return nullptr; }
-  P->d = d; P->R = R; P->q = q; P->p = p; P->bd = boundary; P->J0 = J0;
+  P->d = d; P->R = R; P->q = q; P->p = p; P->bd = boundary; P->J0 = J0; P->family = family;
   P->M = 1 << R;
   P->N = 1 << (R + q);
   cudaGetDevice(&P->device);
@@ -751,9 +854,12 @@ int64_t uw_plan_table(const uw_plan* P, int which, double* out, int64_t cap) {
 }
 
 int64_t uw_host_table(int p, int q, int which, double* out, int64_t cap) {
+  const int family = (p & UW_FILTER_SYMLET) ? 1 : 0;
+  p &= ~UW_FILTER_SYMLET;
   if (p < 1 || p > 10 || q < 0 || q > 6) return -1;
   uw_plan T;
   T.p = p;
+  T.family = family;
   T.q = q;
   std::string err;
   try {

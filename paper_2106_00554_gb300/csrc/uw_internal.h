@@ -68,6 +68,7 @@ struct F32Geo {
 
 struct Plan {
   int d = 1, R = 0, q = 0, p = 1, bd = 0, J0 = 0;
+  int family = 0;            // 0: extremal-phase Daubechies, 1: least asymmetric (symlet)
   int M = 1, N = 1;          // per dimension
   int Q = 1, Lb = 2, ntap = 1;
   int64_t m = 0;             // samples

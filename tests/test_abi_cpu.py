@@ -48,13 +48,19 @@ def test_argument_validation_without_gpu():
     L.uw_plan_destroy(None)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 8])
+SYMLET = 0x100   # UW_FILTER_SYMLET
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 8, tables.Sym(4), tables.Sym(6), tables.Sym(8)])
 @pytest.mark.parametrize("q", [0, 1, 2, 4])
 def test_host_tables_match_oracle(p, q):
+    """The planner's tables (its own long-double routes) against the oracle's,
+    for extremal-phase filters and for symlets (p | UW_FILTER_SYMLET)."""
     tol = 1e-14 if p <= 4 else (1e-12 if p <= 6 else 5e-9)
-    h = _lib.uw_host_table(p, q, 0)
+    pc = int(p) | (SYMLET if isinstance(p, tables.Sym) else 0)
+    h = _lib.uw_host_table(pc, q, 0)
     assert np.abs(h - tables.daubechies(p)).max() < 1e-15
-    I = _lib.uw_host_table(p, q, 1)
+    I = _lib.uw_host_table(pc, q, 1)
     Io = tables.cell_integrals(p, q)
     assert np.abs(I - np.array([Io[t] for t in sorted(Io)])).max() < 1e-15
     Q = 2 ** q
@@ -62,13 +68,13 @@ def test_host_tables_match_oracle(p, q):
     R = W.default_J0(p) + 1
     T = W.cell_matrix(R, q, p, W.VMP) * 2 ** (R / 2)
     N, M = T.shape
-    EL = _lib.uw_host_table(p, q, 2).reshape(p, ntap)
-    ER = _lib.uw_host_table(p, q, 3).reshape(p, ntap)
+    EL = _lib.uw_host_table(pc, q, 2).reshape(p, ntap)
+    ER = _lib.uw_host_table(pc, q, 3).reshape(p, ntap)
     for m in range(p):
         assert np.abs(EL[m] - T[:ntap, m]).max() < tol
         assert np.abs(ER[m] - T[N - 1 - np.arange(ntap), M - 1 - m]).max() < tol
     Lb = 3 * p - 1
     for side, (wp, wq) in (("L", (4, 5)), ("R", (6, 7))):
         Po, Qo = tables.edge_blocks(p, side)
-        assert np.abs(_lib.uw_host_table(p, q, wp).reshape(p, Lb) - Po[:, :Lb]).max() < tol
-        assert np.abs(_lib.uw_host_table(p, q, wq).reshape(p, Lb) - Qo[:, :Lb]).max() < 100 * tol
+        assert np.abs(_lib.uw_host_table(pc, q, wp).reshape(p, Lb) - Po[:, :Lb]).max() < tol
+        assert np.abs(_lib.uw_host_table(pc, q, wq).reshape(p, Lb) - Qo[:, :Lb]).max() < 100 * tol

@@ -6,6 +6,7 @@ import pytest
 from oracle import tables, wavelets as W
 
 PER, VMP = W.PER, W.VMP
+Sym = tables.Sym
 
 
 def _cellint_poly(k, N):
@@ -13,7 +14,7 @@ def _cellint_poly(k, N):
     return (e[1:] ** (k + 1) - e[:-1] ** (k + 1)) / (k + 1)
 
 
-@pytest.mark.parametrize("p", [2, 3, 4, 6, 8])
+@pytest.mark.parametrize("p", [2, 3, 4, 6, 8, Sym(4), Sym(6)])
 def test_vmp_space_reproduces_polynomials(p):
     """Sec. 3.2: VMP boundary functions keep x^k, k < p, in V_j: the cell
     integrals of x^k lie in the range of T (exactly, not approximately)."""
@@ -32,7 +33,7 @@ def test_vmp_space_reproduces_polynomials(p):
     assert np.linalg.norm(T @ sol - c) > 1e-9 * np.linalg.norm(c)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8, Sym(4), Sym(6)])
 @pytest.mark.parametrize("bd", [PER, VMP])
 def test_scaling_basis_orthonormal(p, bd):
     """B_{phi,j} is orthonormal: as q grows, N T^T T -> I (the projection onto
@@ -48,7 +49,7 @@ def test_scaling_basis_orthonormal(p, bd):
     assert errs[-1] < 0.2 * errs[0] + 1e-12 and errs[-1] < 5e-3
 
 
-@pytest.mark.parametrize("p", [2, 3, 4, 6, 8])
+@pytest.mark.parametrize("p", [2, 3, 4, 6, 8, Sym(4), Sym(6)])
 def test_edge_functions_exact_orthonormality_and_support(p):
     # exact orthonormality, evaluated at the tables' working precision (the
     # float64 product cancels: translate coefficients are large where the
@@ -77,7 +78,7 @@ def test_edge_functions_exact_orthonormality_and_support(p):
         assert np.all(T[: N - 2 ** q * (p + m), M - 1 - m] == 0)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 8, Sym(4), Sym(5)])
 @pytest.mark.parametrize("bd", [PER, VMP])
 def test_dwt_orthogonal(p, bd):
     J0 = W.default_J0(p)
@@ -86,7 +87,7 @@ def test_dwt_orthogonal(p, bd):
         assert np.abs(Wi @ Wi.T - np.eye(2 ** R)).max() < 1e-13
 
 
-@pytest.mark.parametrize("p", [2, 3, 4, 6])
+@pytest.mark.parametrize("p", [2, 3, 4, 6, Sym(4), Sym(6)])
 def test_vmp_wavelets_have_vanishing_moments_at_edges(p):
     """VMP (Sec. 3.2): detail coefficients of x^k (k < p) vanish, including
     the boundary wavelets; the periodic basis loses this at the edges."""
@@ -106,7 +107,7 @@ def test_vmp_wavelets_have_vanishing_moments_at_edges(p):
             assert worst > 1e-4
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8, Sym(4), Sym(8)])
 def test_boundary_wavelet_supports(p):
     """psi^left_m uses level-1 coordinates up to p + 2m only (supp [0, p+m]);
     same mirrored on the right; p = 1 reduces to the Haar wavelet."""

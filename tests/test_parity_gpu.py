@@ -6,7 +6,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import dense, fast, wavelets as W
+from oracle import dense, fast, tables, wavelets as W
 from paper_2106_00554_gb300 import F32, F32_SPLIT_BF16, F64, PERIODIC, VMP, Plan, UWError, build, inputs
 
 pytestmark = pytest.mark.gpu
@@ -431,6 +431,43 @@ def test_fp32_persistent_line_kernels(p, bd, R, q):
     assert rel(got_y, want_y) < TOL[F32]
     assert rel(got_x, want_x) < TOL[F32]
     assert sum(n.endswith("_f32") for n in names) == 4, names
+
+
+SYM_CASES = [(2, 4, VMP, 7, 1), (2, 6, PERIODIC, 7, 2), (2, 5, VMP, 8, 1), (2, 8, VMP, 10, 1),
+             (1, 4, VMP, 10, 2), (1, 7, PERIODIC, 11, 1)]
+
+
+@pytest.mark.parametrize("d,p,bd,R,q", SYM_CASES)
+def test_symlets_against_dense_oracle(d, p, bd, R, q):
+    """Least-asymmetric filters (UW_FILTER_SYMLET; Table 1's sym rows) through
+    every kernel family: coarse 2D levels and line operators (the persistent
+    FP32 kernels at N = 2048), 1D lines; FP64 and FP32 against the dense
+    oracle built on the oracle's own symlet tables."""
+    Sp = tables.Sym(p)
+    rng = np.random.default_rng(6000 + 10 * p + bd + d)
+    J0 = W.default_J0(p)
+    M, N = 2 ** R, 2 ** (R + q)
+    if d == 2:
+        omega = inputs.mask_2d(rng, N, 0.2)
+        x = inputs.coeffs_2d(rng, R, J0, 1.0)
+    else:
+        omega = inputs.mask_1d(rng, N, 0.3)
+        x = inputs.coeffs_1d(rng, R, J0, 1.0)
+    plan = Plan(d, R, q, p, bd, omega=omega, symlet=True)
+    y = rng.standard_normal(omega.size)
+    if d == 2:
+        G = dense.G1d(R, q, Sp, bd)
+        want_y = dense.forward2d(x, R, q, Sp, bd, J0, omega, G=G)
+        want_x = dense.adjoint2d(y, R, q, Sp, bd, J0, omega, G=G)
+    else:
+        want_y = dense.forward1d(x, R, q, Sp, bd, J0, omega)
+        want_x = dense.adjoint1d(y, R, q, Sp, bd, J0, omega)
+    for prec in (F64, F32):
+        assert rel(run_fwd(plan, x, prec), want_y) < TOL[prec]
+        assert rel(run_adj(plan, y, prec), want_x) < TOL[prec]
+    # the extremal-phase plan of the same p gives a different product
+    db = Plan(d, R, q, p, bd, omega=omega)
+    assert rel(run_fwd(db, x, F64), want_y) > 1e-3
 
 
 def test_coarse_barrier_gives_up_and_reports(monkeypatch):
