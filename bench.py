@@ -479,15 +479,23 @@ def run_uneven(args):
     issued one after another on one stream for comparison.  One JSON line."""
     import numpy as np
     import torch
-    from oracle import wavelets as W
-    from paper_2106_00554_gb300 import F32, PERIODIC, VMP, Plan, PlanGroup, inputs
+    from paper_2106_00554_gb300 import F32, F32_SPLIT_BF16, PERIODIC, VMP, Plan, PlanGroup, inputs
+    if args.precision not in ("f32", "split_bf16"):
+        raise SystemExit("--uneven runs FP32 or split-BF16 (float buffers)")
+    prec = F32 if args.precision == "f32" else F32_SPLIT_BF16
     torch.cuda.set_device(0)
     rng = np.random.default_rng(3)
     t0 = time.perf_counter()
+    # the library's default coarsest level per p (levels below J0 + 1 have no detail level)
+    j0 = {}
+    for p in (1, 2, 4, 6, 8):
+        probe = Plan(1, 10, 0, p, VMP)
+        j0[p] = probe.J0
+        probe.close()
     plans, xd, yd = [], [], []
     for _ in range(args.uneven):
         p = int(rng.choice([1, 2, 4, 6, 8]))
-        R_ = int(rng.choice([r for r in (6, 7, 8, 9) if r >= W.default_J0(p) + 1]))
+        R_ = int(rng.choice([r for r in (6, 7, 8, 9) if r >= j0[p] + 1]))
         q = int(rng.choice([1, 2]))
         bd = int(rng.choice([PERIODIC, VMP]))
         omega = inputs.mask_2d(rng, 2 ** (R_ + q), float(rng.uniform(0.1, 0.4)))
@@ -502,17 +510,17 @@ def run_uneven(args):
     nst = 16
     group = PlanGroup(plans, nstreams=nst)
     t0 = time.perf_counter()
-    group.tune([x.clone() for x in xd], [torch.empty_like(y) for y in yd], F32, reps=2)
+    group.tune([x.clone() for x in xd], [torch.empty_like(y) for y in yd], prec, reps=2)
     tune_s = time.perf_counter() - t0
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        group.forward(xd, yo, F32, stream=s)
-        group.adjoint(yd, xo, F32, stream=s)
+        group.forward(xd, yo, prec, stream=s)
+        group.adjoint(yd, xo, prec, stream=s)
     s.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=s):
-        group.forward(xd, yo, F32, stream=s)
-        group.adjoint(yd, xo, F32, stream=s)
+        group.forward(xd, yo, prec, stream=s)
+        group.adjoint(yd, xo, prec, stream=s)
 
     def timed(fn, k):
         for _ in range(max(3, args.warmup)):
@@ -533,14 +541,15 @@ def run_uneven(args):
     def sequential():
         with torch.cuda.stream(s):
             for pl, x, y, a, b in zip(plans, xd, yd, yo, xo):
-                pl.forward(x, a, precision=F32, stream=s)
-                pl.adjoint(y, b, precision=F32, stream=s)
+                pl.forward(x, a, precision=prec, stream=s)
+                pl.adjoint(y, b, precision=prec, stream=s)
 
     ms_seq = timed(sequential, max(3, k // 5))
     n = len(plans)
     print(json.dumps({
         "metric": f"batched uneven 2D U x + U* y pairs/s ({n} instances)", "value": n * 1000.0 / ms_graph,
-        "unit": "pairs/s", "higher_is_better": True, "ms_per_step": ms_graph, "steps": k, "dtype": "f32",
+        "unit": "pairs/s", "higher_is_better": True, "ms_per_step": ms_graph, "steps": k,
+        "dtype": "f32" if prec == F32 else "bf16 split (3 parts per operand), f32 accumulate",
         "data": "synthetic",
         "config": {"workload": f"{n} instances: R in 6..9, q in 1..2, p in {{1,2,4,6,8}}, periodic or VMP, "
                                "alpha in [1,2], 10-40% radial multilevel masks, seed 3",

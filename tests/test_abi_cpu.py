@@ -78,3 +78,21 @@ def test_host_tables_match_oracle(p, q):
         Po, Qo = tables.edge_blocks(p, side)
         assert np.abs(_lib.uw_host_table(pc, q, wp).reshape(p, Lb) - Po[:, :Lb]).max() < tol
         assert np.abs(_lib.uw_host_table(pc, q, wq).reshape(p, Lb) - Qo[:, :Lb]).max() < 100 * tol
+
+
+def test_group_and_async_argument_validation_without_gpu():
+    """Plan groups and the asynchronous host calls reject bad arguments with
+    UW_ERR_INVALID_ARG before touching the device."""
+    import ctypes
+    L = _lib.lib()
+    assert not L.uw_group_create(None, 0, 1)
+    assert L.uw_last_error() == 1
+    one = (ctypes.c_void_p * 1)(None)
+    assert not L.uw_group_create(one, 1, 1)          # a null plan in the list
+    assert not L.uw_group_create(one, 1, 65)         # nstreams outside [1, 64]
+    assert L.uw_group_forward(None, 1, one, one, None) == 1
+    assert L.uw_group_adjoint(None, 1, one, one, None) == 1
+    assert L.uw_group_tune(None, 1, one, one, 1, None) == 1
+    L.uw_group_destroy(None)
+    assert L.uw_host_wait(None) == 1
+    assert L.uw_forward_host_async(None, 1, None, None, 1, None) == 1
