@@ -1328,6 +1328,16 @@ __global__ void __launch_bounds__(256, 2) k_syn2d_levels(CoarseIO<T> io, Tables<
   const int M = io.M, Mh = M / 2;
   const int64_t HH = (int64_t)Mh * Mh, MM = (int64_t)M * M;
   const bool tx = io.XT != nullptr;
+  {
+    // the coarse levels read the top-left Mh x Mh block of x; bring it into
+    // L2 now (one 128-byte line per prefetch, all threads of the grid)
+    const int lpr = (int)((Mh * sizeof(T) + 127) / 128), total = Mh * lpr * io.batch;
+    for (int i = blockIdx.x * nthr + tid; i < total; i += gridDim.x * nthr) {
+      const int b = i / (Mh * lpr), r = (i / lpr) % Mh, l = i % lpr;
+      const char* a = reinterpret_cast<const char*>(io.x + (int64_t)b * MM + (int64_t)r * M) + 128 * l;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+  }
   for (int it = 0; it < io.nl; ++it) {
     const int j = io.J0 + it, n1 = 2 << j;
     const int TR = rw ? syn_rw_ts(n1) : 0;
