@@ -96,3 +96,12 @@ def test_group_and_async_argument_validation_without_gpu():
     L.uw_group_destroy(None)
     assert L.uw_host_wait(None) == 1
     assert L.uw_forward_host_async(None, 1, None, None, 1, None) == 1
+
+
+@pytest.mark.parametrize("p", range(1, 11))
+def test_planner_picks_the_oracles_symlet(p):
+    """The planner restates the least-asymmetric selection in long double; for
+    every p it must pick the same filter (same zeros, same orientation) as the
+    oracle's 60-digit selection."""
+    h = _lib.uw_host_table(p | SYMLET, 1, 0)
+    assert np.abs(h - tables.daubechies(tables.Sym(p))).max() < 1e-15
