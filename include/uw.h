@@ -22,7 +22,10 @@
  *    the last failing call on the calling thread is kept in uw_last_error()
  *    and a message in uw_last_message().  No C++ exception crosses the ABI.
  *  - Device pointers are CUDA device addresses on the device that was
- *    current when the plan was created; the caller owns them.  Host pointers
+ *    current when the plan was created; the caller owns them.  Every call
+ *    that runs a plan's product must be made with that device current: with
+ *    another device current it returns UW_ERR_INVALID_ARG before any lookup
+ *    or launch.  Host pointers
  *    are ordinary CPU memory (pinned memory is faster, pageable works).
  *  - Calls are asynchronous and ordered on the given stream (a cudaStream_t
  *    passed as void*; NULL = legacy default stream).  A plan may be used by
@@ -158,9 +161,11 @@ int uw_adjoint(const uw_plan* plan, int precision, const void* y_dev, void* x_de
  *              M = 512, N = 1024 in FP32: batch 1), else UW_ERR_INVALID_ARG
  *              and nothing is launched
  *   stream     cudaStream_t as void*
- * Errors: UW_ERR_UNSUPPORTED for 1D plans; UW_ERR_CUDA if the scratch's
- * device address cannot be found (looked up once per device, on the device
- * that is current at the call).
+ * Errors: UW_ERR_UNSUPPORTED for 1D plans; UW_ERR_INVALID_ARG if the
+ * current device is not the plan's device (nothing is looked up or launched);
+ * UW_ERR_CUDA if the scratch's device address cannot be found.  The address
+ * is looked up once per device and CUDA context (after a device reset the
+ * next call looks it up again).
  * All calls on one device share the one scratch array: two calls whose
  * kernels can overlap (different streams, or different host threads without
  * ordering) race on it and give wrong results; order them on one stream.
@@ -220,7 +225,10 @@ int uw_host_wait(const uw_plan* plan);
  * and masks) issued as one unit, e.g. to be captured into one CUDA graph.
  *
  * uw_group_create(plans, n, nstreams): a group over n existing plans (still
- *   owned by the caller; they must outlive the group).  While the group
+ *   owned by the caller; they must outlive the group).  A plan owns one
+ *   workspace, so it may appear at most once in a group and belong to at
+ *   most one live group: a repeated plan, or one already in another group,
+ *   gives NULL with UW_ERR_INVALID_ARG.  While the group
  *   exists, its plans run their coarse 2D levels as one launch per level
  *   (kernels of different instances may then run at the same time; no grid-
  *   wide barrier is shared between them); uw_group_destroy restores the plans'
@@ -238,7 +246,9 @@ int uw_host_wait(const uw_plan* plan);
  *   keeps the fastest for that plan.  Synchronises `stream`.
  * Errors: UW_ERR_INVALID_ARG (null pointers, n < 1, nstreams out of range,
  *   precision, a plan's own argument checks), UW_ERR_OOM (streams or events),
- *   UW_ERR_CUDA; a failing instance stops the call with its status.
+ *   UW_ERR_CUDA; a failing instance stops the call with its status (the
+ *   internal streams are still joined back into `stream`, so a capture of
+ *   `stream` can end).
  */
 typedef struct uw_group uw_group;
 uw_group* uw_group_create(uw_plan* const* plans, int n, int nstreams);

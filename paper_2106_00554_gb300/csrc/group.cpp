@@ -5,6 +5,7 @@
 // fastest on that plan's sizes.
 #include <cuda_runtime.h>
 
+#include <set>
 #include <vector>
 
 #include "uw_internal.h"
@@ -40,11 +41,23 @@ uw_group* uw_group_create(uw_plan* const* plans, int n, int nstreams) {
     uw::set_error(UW_ERR_INVALID_ARG, "null plans, n < 1 or nstreams outside [1, 64]");
     return nullptr;
   }
-  for (int i = 0; i < n; ++i)
+  // one plan owns one workspace, so it may appear once in one live group:
+  // two streams running the same plan would race on it
+  std::set<const uw_plan*> seen;
+  for (int i = 0; i < n; ++i) {
     if (!plans[i]) {
       uw::set_error(UW_ERR_INVALID_ARG, "null plan in the group");
       return nullptr;
     }
+    if (!seen.insert(plans[i]).second) {
+      uw::set_error(UW_ERR_INVALID_ARG, "a plan appears twice in the group");
+      return nullptr;
+    }
+    if (plans[i]->group) {
+      uw::set_error(UW_ERR_INVALID_ARG, "a plan already belongs to another live group");
+      return nullptr;
+    }
+  }
   uw_group* g = new uw_group();
   g->plans.assign(plans, plans + n);
   const int ns = nstreams < n ? nstreams : n;
@@ -63,6 +76,7 @@ uw_group* uw_group_create(uw_plan* const* plans, int n, int nstreams) {
   for (uw_plan* P : g->plans) {
     g->saved_coarse.push_back(P->coarse_mode);
     P->coarse_mode = 1;
+    P->group = g;
   }
   return g;
 }
@@ -76,16 +90,19 @@ static int group_run(uw_group* g, int prec, bool fwd, const void* const* in, voi
   if (cudaEventRecord(g->fork, s) != cudaSuccess) return group_fail(UW_ERR_CUDA, "fork event failed");
   for (int k = 0; k < ns; ++k)
     if (cudaStreamWaitEvent(g->streams[k], g->fork, 0) != cudaSuccess) return group_fail(UW_ERR_CUDA, "fork wait failed");
-  for (size_t i = 0; i < g->plans.size(); ++i) {
+  int st = UW_OK;
+  for (size_t i = 0; i < g->plans.size() && st == UW_OK; ++i) {
     void* si = g->streams[i % ns];
-    const int st = fwd ? uw_forward(g->plans[i], prec, in[i], out[i], 1, si)
-                       : uw_adjoint(g->plans[i], prec, in[i], out[i], 1, si);
-    if (st != UW_OK) return st;
+    st = fwd ? uw_forward(g->plans[i], prec, in[i], out[i], 1, si)
+             : uw_adjoint(g->plans[i], prec, in[i], out[i], 1, si);
   }
+  // join every internal stream back into the caller's stream even after a
+  // failing instance, so that a capture of `stream` can still end; the first
+  // error is returned
   for (int k = 0; k < ns; ++k)
     if (cudaEventRecord(g->join[k], g->streams[k]) != cudaSuccess || cudaStreamWaitEvent(s, g->join[k], 0) != cudaSuccess)
-      return group_fail(UW_ERR_CUDA, "join failed");
-  return UW_OK;
+      if (st == UW_OK) st = group_fail(UW_ERR_CUDA, "join failed");
+  return st;
 }
 
 int uw_group_forward(uw_group* g, int prec, const void* const* x, void* const* y, void* stream) {
@@ -140,7 +157,10 @@ int uw_group_tune(uw_group* g, int prec, void* const* x, void* const* y, int rep
 void uw_group_destroy(uw_group* g) {
   if (!g) return;
   for (cudaStream_t s : g->streams) cudaStreamSynchronize(s);
-  for (size_t i = 0; i < g->plans.size(); ++i) g->plans[i]->coarse_mode = g->saved_coarse[i];
+  for (size_t i = 0; i < g->plans.size(); ++i) {
+    g->plans[i]->coarse_mode = g->saved_coarse[i];
+    g->plans[i]->group = nullptr;
+  }
   group_free(g);
 }
 

@@ -2366,28 +2366,64 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 namespace uw {
 
-// device address of g_noalloc_scratch on the current device, looked up once
-// per device (the first call on a device should come before any stream
-// capture: the lookup may load the library's module)
+// Unique id of the current CUDA context, 0 if it cannot be read.  The
+// driver entry points come through the runtime, so the library needs no
+// link against the driver library.
+static unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f;
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of g_noalloc_scratch on the current device.  It is looked up
+// once per device and context: a reset of the device (cudaDeviceReset) makes
+// a new context, which loads the module again at a new address, and the next
+// call looks the address up again.  The first call on a device (or after a
+// reset) should come before any stream capture: the lookup may load the
+// library's module.
 static int noalloc_scratch(void** out) {
   static std::mutex mu;
   static void* addr[128] = {};
+  static unsigned long long ctx_of[128] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
     cudaGetLastError();
     set_error(UW_ERR_CUDA, "no usable current CUDA device");
     return UW_ERR_CUDA;
   }
+  // make sure the primary context exists before its id is read
+  cudaFree(nullptr);
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  if (!addr[dev] || ctx == 0 || ctx != ctx_of[dev]) {
     void* a = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
     if (e != cudaSuccess || !a) {
       cudaGetLastError();
+      addr[dev] = nullptr;
       set_error(UW_ERR_CUDA, std::string("cudaGetSymbolAddress of the fixed scratch failed: ") + cudaGetErrorString(e));
       return UW_ERR_CUDA;
     }
     addr[dev] = a;
+    ctx_of[dev] = ctx;
   }
   *out = addr[dev];
   return UW_OK;
@@ -2436,6 +2472,24 @@ int launch_forward_noalloc(const Plan& P, int prec, const void* x, void* y, int 
 // ===========================================================================
 struct uw_plan : public uw::Plan {};
 
+// The plan's tables, mask and workspace live on the device that was current
+// when it was created; a call made with another device current would launch
+// there and read them across devices.  Rejected before any lookup or launch.
+static int check_device(const uw_plan* P) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    uw::set_error(UW_ERR_CUDA, "no usable current CUDA device");
+    return UW_ERR_CUDA;
+  }
+  if (cur != P->device) {
+    uw::set_error(UW_ERR_INVALID_ARG, "the current CUDA device (" + std::to_string(cur) +
+                                          ") is not the plan's device (" + std::to_string(P->device) + ")");
+    return UW_ERR_INVALID_ARG;
+  }
+  return UW_OK;
+}
+
 // x_ptr: the coefficient side, y_ptr: the sample side (may be NULL when the
 // plan samples nothing, m == 0)
 static int check_call(const uw_plan* P, int prec, const void* x_ptr, const void* y_ptr, int batch) {
@@ -2449,7 +2503,7 @@ static int check_call(const uw_plan* P, int prec, const void* x_ptr, const void*
     return UW_ERR_INVALID_ARG;
   }
   if (!x_ptr || (!y_ptr && P->m > 0)) { uw::set_error(UW_ERR_INVALID_ARG, "null buffer"); return UW_ERR_INVALID_ARG; }
-  return UW_OK;
+  return check_device(P);
 }
 
 extern "C" {
@@ -2505,6 +2559,8 @@ int uw_forward_noalloc(const uw_plan* P, int prec, const void* x, void* y, int b
   }
   if (batch < 1) { uw::set_error(UW_ERR_INVALID_ARG, "batch must be >= 1"); return UW_ERR_INVALID_ARG; }
   if (!x || (!y && P->m > 0)) { uw::set_error(UW_ERR_INVALID_ARG, "null buffer"); return UW_ERR_INVALID_ARG; }
+  const int dst = check_device(P);
+  if (dst != UW_OK) return dst;
   int nl = 0;
   int st = uw::launch_forward_noalloc(*P, prec, x, y, batch, stream, &nl);
   const_cast<uw_plan*>(P)->last_launches = nl;

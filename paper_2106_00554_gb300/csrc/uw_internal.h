@@ -103,6 +103,7 @@ struct Plan {
   // coarse 2D levels 0 = one cooperative launch, 1 = one launch per level
   int line_variant = 0;
   int coarse_mode = 0;
+  void* group = nullptr;         // the live plan group that holds this plan (at most one)
   int device = 0;
   Profiler* prof = nullptr;
   TcGeo tc;                      // split-BF16 line operators (tc.ok = 0: not eligible)

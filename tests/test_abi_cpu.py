@@ -56,7 +56,17 @@ SYMLET = 0x100   # UW_FILTER_SYMLET
 def test_host_tables_match_oracle(p, q):
     """The planner's tables (its own long-double routes) against the oracle's,
     for extremal-phase filters and for symlets (p | UW_FILTER_SYMLET)."""
-    tol = 1e-14 if p <= 4 else (1e-12 if p <= 6 else 5e-9)
+    # bounds about 10x above the errors observed with the 80-bit long double
+    # of x86 (the quad-precision build on Arm is tighter): extremal phase
+    # p = 8: 4e-14 (cell rows), 8e-14 (P), 3e-13 (Q); symlet 8: 7e-11, 1e-10,
+    # 1.2e-9 (its filter comes out of a less well conditioned root choice)
+    sym = isinstance(p, tables.Sym)
+    if int(p) <= 5:
+        tol = 1e-14
+    elif int(p) <= 6:
+        tol = 1e-13 if sym else 1e-14
+    else:
+        tol = 5e-10 if sym else 5e-13
     pc = int(p) | (SYMLET if isinstance(p, tables.Sym) else 0)
     h = _lib.uw_host_table(pc, q, 0)
     assert np.abs(h - tables.daubechies(p)).max() < 1e-15
@@ -77,7 +87,7 @@ def test_host_tables_match_oracle(p, q):
     for side, (wp, wq) in (("L", (4, 5)), ("R", (6, 7))):
         Po, Qo = tables.edge_blocks(p, side)
         assert np.abs(_lib.uw_host_table(pc, q, wp).reshape(p, Lb) - Po[:, :Lb]).max() < tol
-        assert np.abs(_lib.uw_host_table(pc, q, wq).reshape(p, Lb) - Qo[:, :Lb]).max() < 100 * tol
+        assert np.abs(_lib.uw_host_table(pc, q, wq).reshape(p, Lb) - Qo[:, :Lb]).max() < 10 * tol
 
 
 def test_group_and_async_argument_validation_without_gpu():

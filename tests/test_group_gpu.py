@@ -122,3 +122,24 @@ def test_group_graph_capture_matches_plain_calls():
     again = plans[-1].forward(xd[-1], precision=F32)
     torch.cuda.synchronize()
     assert rel(again.cpu().numpy(), ref_y[-1].cpu().numpy()) == 0.0
+
+
+def test_group_rejects_a_plan_twice_and_a_plan_in_two_groups():
+    """A plan owns one workspace: the same plan on two internal streams, or in
+    two live groups, would race on it.  Both are refused at creation; after
+    the first group is destroyed the plan may join another."""
+    from paper_2106_00554_gb300 import UWError
+    a = Plan(2, 6, 1, 2, VMP)
+    b = Plan(2, 6, 1, 4, PERIODIC)
+    with pytest.raises(UWError) as e:
+        PlanGroup([a, b, a], nstreams=2)
+    assert e.value.status == 1
+    g = PlanGroup([a, b], nstreams=2)
+    with pytest.raises(UWError) as e:
+        PlanGroup([b], nstreams=1)
+    assert e.value.status == 1
+    g.close()
+    g2 = PlanGroup([b], nstreams=1)
+    g2.close()
+    a.close()
+    b.close()

@@ -493,3 +493,26 @@ def test_coarse_barrier_gives_up_and_reports(monkeypatch):
     monkeypatch.delenv("UW_BARRIER_SPIN_LIMIT")
     assert rel(run_fwd(plan, x, F32), want) < TOL[F32]
     assert _lib.uw_plan_device_status(plan._h) == UW_OK
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs two visible CUDA devices")
+def test_call_with_another_device_current_is_rejected():
+    """A plan's tables and workspace live on its own device.  A call made with
+    another device current is refused before any lookup or launch (only the
+    argument checks run), for the device products and the no-allocation one."""
+    from paper_2106_00554_gb300 import UWError
+    torch.cuda.set_device(0)
+    plan = Plan(2, 6, 1, 2, VMP)
+    x = torch.zeros((64, 64), dtype=torch.float32, device="cuda:0")
+    y = torch.zeros(plan.m, dtype=torch.float32, device="cuda:0")
+    try:
+        torch.cuda.set_device(1)
+        for call in (lambda: plan.forward(x, y, precision=F32), lambda: plan.adjoint(y, x, precision=F32),
+                     lambda: plan.forward_noalloc(x, y, precision=F32)):
+            with pytest.raises(UWError) as e:
+                call()
+            assert e.value.status == 1
+    finally:
+        torch.cuda.set_device(0)
+    plan.close()
