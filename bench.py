@@ -158,101 +158,275 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# the CPU oracle (reference arm and cpu_baseline)
+# the CPU oracle (reference arm, cpu_baseline, oracle timings)
+#
+# Everything here runs in a child process (`bench.py --cpu-oracle ...`) with
+# no GPU visible and one BLAS thread per process; the all-core measurements
+# spread Algorithm 1's lines over a process pool started with `spawn`.  The
+# oracle's own functions do every step; nothing here changes its arithmetic.
 # ----------------------------------------------------------------------------
-def oracle_pair_rate(lines=64):
-    """Time the oracle's Algorithm 2 on a bounded sample of the workload and
-    scale to one full pair: the Mallat IDWT and DWT on the full 2048^2 array,
-    and Algorithm 1 (sum_l D_l H_l plus Prop. 4.4 edges) forward and adjoint
-    on `lines` lines of each pass; a full pair applies Algorithm 1 to
-    M + N lines in each direction.  Single thread (BLAS pinned to 1)."""
-    code = f"""
-import time, json, numpy as np
-from oracle import fast, wavelets as W
-from paper_2106_00554_gb300 import inputs
-R, q, p = {R}, {Q}, {P}
-M, N = 2 ** R, 2 ** (R + q)
-J0 = W.default_J0(p)
-rng = np.random.default_rng({SEED})
-x = inputs.coeffs_2d(rng, R, J0, 1.5)
-fast.alg1_forward(np.zeros((1, M)), R, q, p, W.VMP)       # build the oracle tables first
-t0 = time.perf_counter(); S = fast.idwt2d(x, J0, p, W.VMP); t_idwt = time.perf_counter() - t0
-t0 = time.perf_counter(); fast.dwt2d(S, J0, p, W.VMP); t_dwt = time.perf_counter() - t0
-L = {lines}
-xi = rng.standard_normal((L, M)); al = rng.standard_normal((L, N))
-t0 = time.perf_counter(); fast.alg1_forward(xi, R, q, p, W.VMP); t_f = (time.perf_counter() - t0) / L
-t0 = time.perf_counter(); fast.alg1_adjoint(al, R, q, p, W.VMP); t_a = (time.perf_counter() - t0) / L
-pair = t_idwt + t_dwt + (M + N) * (t_f + t_a)
-print(json.dumps({{"pair_s": pair, "idwt_s": t_idwt, "dwt_s": t_dwt, "line_fwd_s": t_f, "line_adj_s": t_a}}))
-"""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+CPU_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+           "CUDA_VISIBLE_DEVICES": ""}
+
+
+def host_cpu():
+    """(cores usable by this process, CPU model name from lscpu)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model
+
+
+def _alg1_lines(args):
+    """Pool worker: the oracle's Algorithm 1 on a block of lines."""
+    direction, lines, R_, q, p = args
+    from oracle import fast, wavelets as W
+    f = fast.alg1_forward if direction == "fwd" else fast.alg1_adjoint
+    return f(lines, R_, q, p, W.VMP)
+
+
+def _vector_pair(args):
+    """Pool worker: one 1D forward and adjoint product of the oracle."""
+    x, y, R_, q, p, J0, omega = args
+    from oracle import fast, wavelets as W
+    return fast.forward1d(x, R_, q, p, W.VMP, J0, omega), fast.adjoint1d(y, R_, q, p, W.VMP, J0, omega)
+
+
+def _map_lines(pool, direction, A, R_, q, p, workers):
+    import numpy as np
+    if pool is None:
+        return _alg1_lines((direction, A, R_, q, p))
+    chunks = np.array_split(A, 4 * workers, axis=0)
+    return np.concatenate(pool.map(_alg1_lines, [(direction, c, R_, q, p) for c in chunks]), axis=0)
+
+
+def oracle_pair_2d(pool, workers, x, y, R_, q, p, J0, omega):
+    """One forward and one adjoint product of Algorithm 2 (the Mallat IDWT /
+    DWT in this process, Algorithm 1 on every line of both passes, in the
+    pool when there is one).  Returns (y, x) of the pair."""
+    import numpy as np
+    from oracle import fast, wavelets as W
+    N = 2 ** (R_ + q)
+    xi = fast.idwt2d(x, J0, p, W.VMP)
+    t = _map_lines(pool, "fwd", xi, R_, q, p, workers)                         # rows: M x N
+    a = _map_lines(pool, "fwd", np.ascontiguousarray(t.T), R_, q, p, workers).T  # columns: N x N
+    y_out = a.reshape(N * N)[omega]
+    A = np.zeros(N * N)
+    A[omega] = y
+    t = _map_lines(pool, "adj", A.reshape(N, N), R_, q, p, workers)             # rows: N x M
+    xi = _map_lines(pool, "adj", np.ascontiguousarray(t.T), R_, q, p, workers).T  # columns: M x M
+    return y_out, fast.dwt2d(xi, J0, p, W.VMP)
+
+
+def _spawn_pool(workers):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(workers)
+
+
+def cpu_oracle_reference(steps, warmup, budget_s=300.0):
+    """The reference arm: every step one whole pair of Algorithm 2 at the
+    benchmark workload on all host cores.  If whole pairs would not fit the
+    time budget, each step takes Algorithm 1 on a sample of lines instead and
+    says so."""
+    import numpy as np
+    from oracle import fast, wavelets as W
+    from paper_2106_00554_gb300 import inputs
+    cores, model = host_cpu()
+    rng = np.random.default_rng(SEED)
+    N = 2 ** (R + Q)
+    omega = inputs.mask_2d(rng, N, FRAC)
+    J0 = W.default_J0(P)
+    x = inputs.coeffs_2d(rng, R, J0, 1.5)
+    y = rng.standard_normal(omega.size)
+    fast.alg1_forward(np.zeros((1, 2 ** R)), R, Q, P, W.VMP)          # oracle tables
+    pool = _spawn_pool(cores)
+    try:
+        pool.map(_alg1_lines, [("fwd", np.zeros((1, 2 ** R)), R, Q, P)] * cores)   # workers' tables
+        t0 = time.perf_counter()
+        oracle_pair_2d(pool, cores, x, y, R, Q, P, J0, omega)
+        first = time.perf_counter() - t0
+        times = []
+        if first * (steps + warmup) <= budget_s:
+            for s in range(1, steps + warmup):
+                t0 = time.perf_counter()
+                oracle_pair_2d(pool, cores, x, y, R, Q, P, J0, omega)
+                if s >= warmup:
+                    times.append(time.perf_counter() - t0)
+            if warmup == 0:
+                times.insert(0, first)
+            how = "whole pairs"
+            sample = (f"every step one whole pair of the oracle's Algorithm 2 at N=4096^2 (Mallat IDWT + "
+                      f"DWT in one process, Algorithm 1 on all 6144 lines of both passes spread over "
+                      f"{cores} processes); CPU {model}")
+        else:
+            M = 2 ** R
+            L = 2 * cores
+            t_ana = 0.0
+            t0 = time.perf_counter()
+            S = fast.idwt2d(x, J0, P, W.VMP)
+            fast.dwt2d(S, J0, P, W.VMP)
+            t_ana = time.perf_counter() - t0
+            for s in range(steps + warmup):
+                xi = rng.standard_normal((L, M))
+                al = rng.standard_normal((L, N))
+                t0 = time.perf_counter()
+                _map_lines(pool, "fwd", xi, R, Q, P, cores)
+                _map_lines(pool, "adj", al, R, Q, P, cores)
+                t = time.perf_counter() - t0
+                if s >= warmup:
+                    times.append(t_ana + (M + N) / L * t)
+            how = "sampled"
+            sample = (f"whole pairs would exceed {budget_s:.0f} s: the Mallat IDWT + DWT once, then per step "
+                      f"Algorithm 1 forward and adjoint on {L} lines over {cores} processes, scaled to the "
+                      f"6144 lines of a pair (extrapolated); CPU {model}")
+    finally:
+        pool.close()
+        pool.join()
+    return {"pair_s": statistics.median(times), "step_s": times, "cores": cores, "model": model,
+            "how": how, "sample": sample}
+
+
+def cpu_oracle_baseline():
+    """cpu_baseline (two whole pairs of Algorithm 2 at the benchmark workload
+    on all host cores) and the oracle timings: the dense oracle at the 1D
+    configuration of 2048 x 1024 (forming U, then the products, one thread),
+    and the O(N log N) oracle (Algorithm 1 / 2) on one thread and on all
+    cores at that configuration, at the batched 1D configuration and at the
+    benchmark workload."""
+    import numpy as np
+    from oracle import dense, fast, wavelets as W
+    from paper_2106_00554_gb300 import inputs
+    cores, model = host_cpu()
+    out = {"cores": cores, "cpu_model": model}
+    # dense, configuration 1: p = 2 VMP, M = 2^10, q = 1, J0 = 3, all 2048 Walsh rows
+    rng = np.random.default_rng(0)
     t0 = time.perf_counter()
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
-    wall = time.perf_counter() - t0
+    U = dense.U1d(10, 1, 2, W.VMP, 3)
+    t_form = time.perf_counter() - t0
+    x1 = inputs.coeffs_1d(rng, 10, 3, 1.0)
+    y1 = inputs.gaussian(rng, 2048)
+    reps = 200
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        U @ x1
+        U.T @ y1
+    t_dense = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(20):
+        fast.forward1d(x1, 10, 1, 2, W.VMP, 3)
+        fast.adjoint1d(y1, 10, 1, 2, W.VMP, 3)
+    t_fast1 = (time.perf_counter() - t0) / 20
+    out["config1_dense"] = {"formation_s": t_form, "pair_s": t_dense, "pairs_per_s": 1.0 / t_dense, "threads": 1,
+                            "what": "U = H_N T W^{-1} formed from the definitions (2048 x 1024, FP64), then "
+                                    "U x and U^T y"}
+    out["config1_fast"] = {"pairs_per_s_1thread": 1.0 / t_fast1, "pair_s": t_fast1,
+                           "all_cores": "not applicable: one vector of one line"}
+    # configuration 2: p = 4, M = 2^16, q = 2, 15% multilevel mask, batch 64 (seed 1)
+    rng = np.random.default_rng(1)
+    R2, q2, p2 = 16, 2, 4
+    om2 = inputs.mask_1d(rng, 2 ** (R2 + q2), 0.15)
+    J2 = W.default_J0(p2)
+    xs = inputs.coeffs_1d(rng, R2, J2, 1.5, batch=64)
+    ys = rng.standard_normal((64, om2.size))
+    fast.forward1d(xs[:1], R2, q2, p2, W.VMP, J2, om2)
+    t0 = time.perf_counter()
+    for b in range(2):
+        fast.forward1d(xs[b], R2, q2, p2, W.VMP, J2, om2)
+        fast.adjoint1d(ys[b], R2, q2, p2, W.VMP, J2, om2)
+    t_c2 = (time.perf_counter() - t0) / 2
+    pool = _spawn_pool(cores)
+    try:
+        pool.map(_vector_pair, [(xs[0], ys[0], R2, q2, p2, J2, om2)] * cores)     # workers' tables
+        nv = min(64, cores)
+        t0 = time.perf_counter()
+        pool.map(_vector_pair, [(xs[b], ys[b], R2, q2, p2, J2, om2) for b in range(nv)])
+        t_c2p = time.perf_counter() - t0
+        out["config2_fast"] = {"pairs_per_s_1thread": 1.0 / t_c2,
+                               "pairs_per_s_all_cores": nv / t_c2p, "cores": cores,
+                               "sample": f"1 thread: 2 of the 64 vector pairs; all cores: {nv} vector pairs, one "
+                                         f"per process"}
+        # configuration 5 / the benchmark workload
+        rng = np.random.default_rng(SEED)
+        N = 2 ** (R + Q)
+        omega = inputs.mask_2d(rng, N, FRAC)
+        J0 = W.default_J0(P)
+        x = inputs.coeffs_2d(rng, R, J0, 1.5)
+        y = rng.standard_normal(omega.size)
+        pool.map(_alg1_lines, [("fwd", np.zeros((1, 2 ** R)), R, Q, P)] * cores)
+        times = []
+        for _ in range(2):
+            t0 = time.perf_counter()
+            oracle_pair_2d(pool, cores, x, y, R, Q, P, J0, omega)
+            times.append(time.perf_counter() - t0)
+    finally:
+        pool.close()
+        pool.join()
+    t_all = statistics.median(times)
+    # one thread: the Mallat IDWT + DWT once, Algorithm 1 on 64 lines per direction, scaled
+    M = 2 ** R
+    t0 = time.perf_counter()
+    S = fast.idwt2d(x, J0, P, W.VMP)
+    fast.dwt2d(S, J0, P, W.VMP)
+    t_ana = time.perf_counter() - t0
+    L = 64
+    xi = rng.standard_normal((L, M))
+    al = rng.standard_normal((L, N))
+    t0 = time.perf_counter()
+    fast.alg1_forward(xi, R, Q, P, W.VMP)
+    fast.alg1_adjoint(al, R, Q, P, W.VMP)
+    t_l = (time.perf_counter() - t0) / L
+    t_one = t_ana + (M + N) * t_l
+    out["config5_fast"] = {"pairs_per_s_1thread": 1.0 / t_one, "pairs_per_s_all_cores": 1.0 / t_all,
+                           "cores": cores,
+                           "sample": "all cores: two whole pairs of Algorithm 2 (median); 1 thread: the Mallat "
+                                     "IDWT + DWT once and Algorithm 1 on 64 lines per direction, scaled to "
+                                     "the 6144 lines of a pair"}
+    baseline = {"value": 1.0 / t_all, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                "sample": (f"two whole pairs of the oracle's Algorithm 2 at N=4096^2 (median of {len(times)}): "
+                           f"Mallat IDWT + DWT in one process, Algorithm 1 on all 6144 lines of both passes "
+                           f"over {cores} processes; CPU {model}")}
+    return {"cpu_baseline": baseline, "oracle_timings": out}
+
+
+def run_cpu_oracle(what, steps, warmup):
+    """Run one CPU oracle measurement in a child process with no GPU visible
+    and one BLAS thread per process; returns its JSON result."""
+    env = dict(os.environ, **CPU_ENV)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-oracle", what,
+                        "--steps", str(steps), "--warmup", str(warmup)],
+                       cwd=ROOT, env=env, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": 1.0 / d["pair_s"], "unit": "pairs/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle Algorithm 2 at N=4096^2: full 2048^2 Mallat IDWT + DWT, Algorithm 1 "
-                       f"forward and adjoint timed on {lines} lines each and scaled to the M+N=6144 "
-                       f"lines of one pair; single thread; {wall:.1f} s of CPU work"),
-            "detail": d}
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args):
-    """The oracle on the host cores: one-time Mallat IDWT + DWT of the full
-    array, then per step Algorithm 1 forward and adjoint on a bounded number
-    of lines (sized so the whole run stays within a few minutes), each step
-    scaled to one full pair."""
+    """The reference arm: the CPU oracle on the host cores (rank 0 only)."""
     rank, _, world = env_rank()
     if rank != 0:
         return
-    total = args.steps + args.warmup
-    code = f"""
-import time, json, statistics, numpy as np
-from oracle import fast, wavelets as W
-from paper_2106_00554_gb300 import inputs
-R, q, p = {R}, {Q}, {P}
-M, N = 2 ** R, 2 ** (R + q)
-J0 = W.default_J0(p)
-rng = np.random.default_rng({SEED})
-x = inputs.coeffs_2d(rng, R, J0, 1.5)
-fast.alg1_forward(np.zeros((1, M)), R, q, p, W.VMP)
-t0 = time.perf_counter(); S = fast.idwt2d(x, J0, p, W.VMP); t_idwt = time.perf_counter() - t0
-t0 = time.perf_counter(); fast.dwt2d(S, J0, p, W.VMP); t_dwt = time.perf_counter() - t0
-budget = 120.0 / {total}
-t0 = time.perf_counter(); fast.alg1_forward(rng.standard_normal((1, M)), R, q, p, W.VMP)
-fast.alg1_adjoint(rng.standard_normal((1, N)), R, q, p, W.VMP); t1 = time.perf_counter() - t0
-L = max(1, min(32, int(budget / max(t1, 1e-6))))
-pairs = []
-for s in range({total}):
-    xi = rng.standard_normal((L, M)); al = rng.standard_normal((L, N))
-    t0 = time.perf_counter(); fast.alg1_forward(xi, R, q, p, W.VMP); tf = (time.perf_counter() - t0) / L
-    t0 = time.perf_counter(); fast.alg1_adjoint(al, R, q, p, W.VMP); ta = (time.perf_counter() - t0) / L
-    if s >= {args.warmup}:
-        pairs.append(t_idwt + t_dwt + (M + N) * (tf + ta))
-print(json.dumps({{"pair_s": statistics.median(pairs), "lines": L, "steps": len(pairs), "idwt_s": t_idwt,
-                  "dwt_s": t_dwt}}))
-"""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
     t0 = time.perf_counter()
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+    d = run_cpu_oracle("reference", args.steps, args.warmup)
     wall = time.perf_counter() - t0
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
     v = 1.0 / d["pair_s"]
-    sample = (f"oracle Algorithm 2 at N=4096^2: the full 2048^2 Mallat IDWT + DWT timed once "
-              f"({d['idwt_s'] + d['dwt_s']:.1f} s), then per step Algorithm 1 forward and adjoint on "
-              f"{d['lines']} line(s) each, scaled to the M+N=6144 lines of one pair; median over "
-              f"{d['steps']} steps; single thread; {wall:.1f} s wall")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "f64 (CPU oracle)"},
-            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * d["pair_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "f64 (CPU oracle)", "steps_timed": d["how"],
+                       "timed_region_s": round(sum(d["step_s"]), 2), "wall_s": round(wall, 1)},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": d["cores"], "kind": "oracle",
+                             "sample": d["sample"]},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -260,6 +434,145 @@ print(json.dumps({{"pair_s": statistics.median(pairs), "lines": L, "steps": len(
 # ----------------------------------------------------------------------------
 # the CUDA path
 # ----------------------------------------------------------------------------
+def _graph_of(fn, stream):
+    """fn captured as a CUDA graph (after one eager call on a side stream)."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        fn()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    torch.cuda.synchronize()
+    return g
+
+
+def _time_replays(g, k, stream, flush):
+    """Mean ms of one replay over k replays, each bracketed by CUDA events on
+    `stream`, with an L2 flush between replays outside the events."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for _ in range(3):
+        g.replay()
+        flush.fill_(0)
+    torch.cuda.synchronize()
+    for i, (a, b) in enumerate(ev):
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        flush.fill_(i)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / k
+
+
+def measure_workload_1d(steps, flush, peak):
+    """The batched 1D workload: Daubechies p = 4 VMP, M = 2^16, q = 2
+    (N = 2^18), multilevel 15% mask (m = 39322), a batch of 64 level-decaying
+    x (alpha = 1.5) and 64 y ~ N(0,1), seed 1.  One step is the forward and
+    adjoint product of the whole batch (64 vector pairs), captured as one CUDA
+    graph; FP32 (headline) and FP64.  Roofline of the dominant kernel and of
+    the batch against the compulsory bytes (x, y and the mask, both ways)."""
+    import numpy as np
+    import torch
+    from paper_2106_00554_gb300 import F32, F64, VMP, Plan, _lib, inputs
+    rng = np.random.default_rng(1)
+    R1, q1, p1, B = 16, 2, 4, 64
+    N1 = 2 ** (R1 + q1)
+    om = inputs.mask_1d(rng, N1, 0.15)
+    plan = Plan(1, R1, q1, p1, VMP, omega=om, max_batch=B)
+    x_np = inputs.coeffs_1d(rng, R1, plan.J0, 1.5, batch=B)
+    y_np = rng.standard_normal((B, om.size))
+    stream = torch.cuda.current_stream()
+    out = {"workload": ("1D Daubechies p=4 VMP, M=2^16 -> N=2^18 (R=16, q=2), multilevel 15% mask (m=39322), "
+                        "batch 64, x level-decaying alpha=1.5, y ~ N(0,1), seed 1"),
+           "unit": "pairs/s", "batch": B, "launch": "cuda graph of the batch's pair",
+           "l2": "flushed between timed steps"}
+    for prec, name in ((F32, "f32"), (F64, "f64")):
+        dt = torch.float64 if prec == F64 else torch.float32
+        esize = 8 if prec == F64 else 4
+        x = torch.tensor(x_np, dtype=dt, device="cuda")
+        yin = torch.tensor(y_np, dtype=dt, device="cuda")
+        y = torch.empty((B, plan.m), dtype=dt, device="cuda")
+        xo = torch.empty_like(x)
+
+        def step():
+            plan.forward(x, y, precision=prec)
+            plan.adjoint(yin, xo, precision=prec)
+
+        g = _graph_of(step, stream)
+        k = max(5, min(steps, 100))
+        ms = _time_replays(g, k, stream, flush)
+        _lib.uw_plan_profile(plan._h, True)
+        for i in range(5):
+            step()
+            flush.fill_(i)
+        torch.cuda.synchronize()
+        prof = [e for e in _lib.uw_plan_profile_read(plan._h) if e["launches"] > 0]
+        _lib.uw_plan_profile(plan._h, False)
+        dom = max(prof, key=lambda e: e["total_ms"])
+        avg_ms = dom["total_ms"] / dom["launches"]
+        words = (N1 + 31) // 32
+        comp = 2 * B * (plan.coeffs * esize + plan.m * esize) + 2 * 8 * words
+        out[name] = {"value": B * 1000.0 / ms, "ms_per_step": ms, "compulsory_bytes_per_step": comp,
+                     "frac_compulsory": comp / (ms / 1000.0) / 1e9 / peak,
+                     "dominant_kernel": {"name": dom["name"], "avg_us": 1000.0 * avg_ms,
+                                         "achieved_GBps": dom["bytes_per_launch"] / (avg_ms / 1000.0) / 1e9,
+                                         "frac": dom["bytes_per_launch"] / (avg_ms / 1000.0) / 1e9 / peak},
+                     "kernels": {e["name"]: round(1000.0 * e["total_ms"] / e["launches"], 2) for e in prof}}
+    out["value"] = out["f32"]["value"]
+    plan.close()
+    return out
+
+
+def measure_fista(plan, flush):
+    """The reconstruction of the benchmark workload: 100 FISTA iterations of
+    min ||P_Omega U x - y||^2 / 2 + lam ||x||_1 (lam = 1e-3) from
+    y = P_Omega U x_true + 1e-3 noise, x_true level-decaying (alpha = 1.5) with
+    5% nonzeros (seed 4).  Timed without gradients, and with the gradient of
+    1/2 ||x_100 - x_true||^2 with respect to lam and y through checkpointed
+    iterations; split-BF16 and FP32 products."""
+    import numpy as np
+    import torch
+    from paper_2106_00554_gb300 import F32, F32_SPLIT_BF16, inputs, solvers
+    rng = np.random.default_rng(SEED + 100)
+    xt = torch.tensor(inputs.sparse_coeffs_2d(rng, R, plan.J0, 1.5, 0.05), dtype=torch.float32, device="cuda")
+    y = plan.forward(xt, precision=F32) + 1e-3 * torch.tensor(rng.standard_normal(plan.m), dtype=torch.float32,
+                                                              device="cuda")
+    iters = 100
+    out = {"iterations": iters, "lam": 1e-3, "unit": "iterations/s",
+           "what": "one iteration = U z, U^* of it, and the fused proximal step with momentum"}
+    for prec, name in ((F32_SPLIT_BF16, "split_bf16"), (F32, "f32")):
+        with torch.no_grad():
+            solvers.fista(plan, y, 1e-3, iters=2, precision=prec, checkpoint=False)
+            torch.cuda.synchronize()
+            flush.fill_(0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x = solvers.fista(plan, y, 1e-3, iters=iters, precision=prec, checkpoint=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        yv = y.clone().requires_grad_(True)
+        lt = torch.tensor(1e-3, dtype=torch.float64, device="cuda", requires_grad=True)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0.record()
+        xg = solvers.fista(plan, yv, lt, iters=iters, precision=prec, checkpoint=True)
+        loss = solvers.half_sq_dist(xg, xt)
+        loss.backward()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_g = e0.elapsed_time(e1)
+        rel = float(torch.linalg.norm((x - xt).double()) / torch.linalg.norm(xt.double()))
+        out[name] = {"value": iters * 1000.0 / ms, "ms_solve": ms, "ms_solve_and_gradient": ms_g,
+                     "gradient_iterations_per_s": iters * 1000.0 / ms_g, "rel_error_to_x_true": rel}
+    out["value"] = out["split_bf16"]["value"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -463,9 +776,13 @@ def run_ours(args):
                               "launch": comp_m["launch"], "speedup_of_main": value / comp_m["value"]}
     if e2e:
         line["e2e"] = e2e
+    if not args.no_extra:
+        line["fista"] = measure_fista(plan, flush)
+        line["workload_1d"] = measure_workload_1d(args.steps, flush, peak)
     if not args.no_cpu_baseline:
-        cb = oracle_pair_rate(lines=384)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cb = run_cpu_oracle("baseline", 0, 0)
+        line["cpu_baseline"] = cb["cpu_baseline"]
+        line["oracle_timings"] = cb["oracle_timings"]
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -574,9 +891,18 @@ def main():
                     help="level per dimension (default 11 = the benchmark workload; smaller only for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the FISTA and 1D workload measurements that ride along the main line")
     ap.add_argument("--uneven", type=int, default=0,
                     help="instead of the benchmark workload: the batched uneven workload with this many instances")
+    ap.add_argument("--cpu-oracle", default="", choices=["", "reference", "baseline"],
+                    help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_oracle:
+        res = (cpu_oracle_reference(args.steps, args.warmup) if args.cpu_oracle == "reference"
+               else cpu_oracle_baseline())
+        print(json.dumps(res), flush=True)
+        return
     if args.uneven:
         run_uneven(args)
         return

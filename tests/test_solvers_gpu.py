@@ -220,3 +220,34 @@ def test_generalised_sampling_example2_db2():
     n2 = quad(lambda t: f1(t) ** 2, 0, 1)[0] * quad(lambda t: f2(t) ** 2, 0, 1)[0]
     err = np.sqrt((n2 - 2 * fr1 @ S @ fr2 + np.sum(S ** 2)) / n2)
     assert abs(err - 0.0518) < 5e-4, err
+
+
+@pytest.mark.parametrize("prec", [F32_SPLIT_BF16, F32])
+def test_fista_iterate_against_the_fp64_gpu_solve(prec):
+    """The 100-iteration solve in split-BF16 (and FP32) against the same solve
+    with the FP64 products, at the size of config 3 (p = 4, 256^2 -> 512^2,
+    25% radial mask, x_true level-decaying with 5% nonzeros, noise 1e-3,
+    lam = 1e-3).  Bound: each iteration's proximal-gradient map is
+    nonexpansive, so the per-iteration product errors (<= 1e-5 of ||x||)
+    add up to at most 100 * 1e-5 = 1e-3 of ||x_100||; the difference is
+    printed (pytest -s) and is far below that in practice."""
+    rng = np.random.default_rng(2)
+    R, q, p = 8, 1, 4
+    N = 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.25)
+    plan = Plan(2, R, q, p, VMP, omega=omega)
+    xt = inputs.sparse_coeffs_2d(rng, R, plan.J0, 1.5, 0.05)
+    xt64 = torch.tensor(xt, dtype=torch.float64, device="cuda")
+    y64 = plan.forward(xt64, precision=F64) + 1e-3 * torch.tensor(rng.standard_normal(omega.size),
+                                                                  dtype=torch.float64, device="cuda")
+    with torch.no_grad():
+        ref = S.fista(plan, y64, 1e-3, iters=100, precision=F64, checkpoint=False)
+        got = S.fista(plan, y64.float(), 1e-3, iters=100, precision=prec, checkpoint=False)
+    torch.cuda.synchronize()
+    d = float(torch.linalg.norm(got.double() - ref) / torch.linalg.norm(ref))
+    print(f"FISTA x_100, precision {prec} against FP64: relative difference {d:.2e}")
+    assert d < 1e-3
+    # and the FP64 solve itself reduced the objective
+    r = plan.forward(ref, precision=F64) - y64
+    obj = 0.5 * float(r @ r) + 1e-3 * float(ref.abs().sum())
+    assert obj < 0.5 * float(y64 @ y64)
