@@ -1548,6 +1548,19 @@ int upload_tables(Plan& P) {
       return UW_ERR_CUDA;
     }
   }
+  std::vector<unsigned char> uw5;
+  build_umma(P, uw5);
+  if (P.umma.ok) {
+    if (cudaMalloc(&P.d_umma, uw5.size()) != cudaSuccess) {
+      cudaGetLastError();
+      set_error(UW_ERR_OOM, "tensor-core operator allocation failed");
+      return UW_ERR_OOM;
+    }
+    if (cudaMemcpy(P.d_umma, uw5.data(), uw5.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error(UW_ERR_CUDA, "tensor-core operator upload failed");
+      return UW_ERR_CUDA;
+    }
+  }
   if (cudaMalloc(&P.d_sync, sizeof(GridBarrier)) != cudaSuccess) {
     cudaGetLastError();
     set_error(UW_ERR_OOM, "barrier allocation failed");
@@ -1779,6 +1792,11 @@ static void launch_line(bool fwd, const Plan& P, const Geo& G, const T* in, T* o
 template <>
 void launch_line<float>(bool fwd, const Plan& P, const Geo& G, const float* in, float* out, const LineIO& io,
                         int nblocks, Launcher& L) {
+  if (L.split && P.line_variant == 0 && !getenv_flag("UW_NO_UMMA") && umma_eligible(P, io, in, out, fwd, nblocks)) {
+    if (L.armed) L.retag(P.prof->names[L.cur.id] + "_umma");
+    L.note(umma_launch(fwd, P, in, out, io, nblocks, L.s));
+    return;
+  }
   if (L.split && P.line_variant == 0 && tc_eligible(P, io, in, out, fwd)) {
     if (L.armed) L.retag(P.prof->names[L.cur.id] + "_tc");
     L.note(tc_launch(fwd, P, in, out, io, nblocks, L.s));

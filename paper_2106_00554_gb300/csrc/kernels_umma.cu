@@ -1,0 +1,785 @@
+// Split-BF16 line operators on the 5th-generation tensor cores (sm_103a):
+// tcgen05.mma with FP32 accumulators in tensor memory, operands in shared
+// memory described by matrix descriptors, lines staged by bulk copies (the
+// TMA engine's 1D form).  They serve the 2D path (Sec. 5, Algorithm 2) for
+// lines of N = 4096 samples with q = 1 (M = 2048 coefficients per line).
+//
+// A line's outputs are 128 blocks of 32, k = 32 b + r.  Forward:
+//   GEMM1  D1[b][r] = sum_j W[b][j] B1[r][j]           (M = 128, N = 32, K = 48)
+//          W[b][j] = lo[8 b - 8 + j] (j < 24), hi[8 b - 32 + j] (j >= 24): the
+//          window of coefficients that block b reads, never materialised --
+//          consecutive rows of a K-major operand without swizzling are 16
+//          bytes (8 BF16 values) apart, exactly the shift of the window per
+//          block, so a descriptor over the plain coefficient array is W
+//          itself.  B1 = the last synthesis level (Sec. 3.2), T (Sec. 4.1)
+//          and the Walsh-Hadamard stages of bits 0-4 (Sec. 3.1) of one block.
+//   GEMM2  D2[b'][r] = sum_b H128[b'][b] D1[b][r]      (M = 128, N = 32, K = 128)
+//          the Walsh-Hadamard stages of bits 5-11 as an exact +-1 contraction
+//   D2 is the natural-order line: stored, or gathered at the sampled
+//   sequency indices (P_Omega, Sec. 1.1).
+// Adjoint (Sec. 4.2): stage or scatter the natural line, GEMM2 (H128 is
+// symmetric), then Z[b][j] = sum_r D2[b][r] B1[r][j] (M = 128, N = 48, K = 32)
+// and lo[i], hi[i] = the sum of the three entries of Z whose window position
+// is i.
+//
+// Precision: every FP32 operand is split into three BF16 parts
+// (x = x1 + x2 + x3 + O(2^-24 |x|)); B1 likewise on the host.  GEMM1 and the
+// adjoint's third product keep the six part products of order <= 2; the
+// Walsh matrix is exact in BF16, so GEMM2 takes the three data parts.  The
+// products are exact in FP32 and accumulate in FP32: as accurate as the FP32
+// CUDA-core kernels.
+//
+// VMP boundaries: the windows read zero beyond the coefficient range; the
+// exact operator differs from that by a host-built correction that reads the
+// p lo and p hi coefficients at an end and reaches only the first / last KB
+// blocks (added to D1 before GEMM2; the adjoint adds its transpose).
+// Periodic plans wrap the windows instead (halo copies), which is exact.
+//
+// Organisation: one persistent CTA per SM with two warpgroups; each
+// warpgroup runs its own sequence of lines (its own buffers, tensor-memory
+// columns and mbarriers) so that one group's CUDA-core work overlaps the
+// other's tensor-core work.  One thread per group issues its MMAs.  Every
+// wait is bounded: when one gives up, the group records it in the plan's
+// error word, drains its copies and MMAs in flight (again bounded), and
+// leaves; the tensor memory is freed before the CTA exits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+
+#include "line_common.cuh"
+#include "umma.cuh"
+
+namespace uw {
+namespace ummak {
+
+using namespace umma;
+
+constexpr int NB = 128;            // blocks per line
+constexpr int NL = 4096;           // samples per line
+constexpr int ML = 2048;           // coefficients per line
+constexpr int N0 = 1024;           // lo (and hi) coefficients per line
+constexpr int WG = 2;              // warpgroups per CTA
+constexpr int NTH = 128 * WG;
+
+// shared memory (bytes); operand regions 1024-byte aligned
+constexpr int HANK_LEN = 1056;                       // bf16 per window array: e in [-8, 1048)
+constexpr int HANK_BYTES = HANK_LEN * 2;             // 2112
+constexpr int OFF_H = 0;                             // H128, K-major: 32768
+constexpr int OFF_B1 = 32768;                        // 3 x 3072 (forward: B1, adjoint: B1^T)
+constexpr int OFF_G = 32768 + 9216;                  // per-group regions
+// forward group region
+constexpr int F_STAGE = 0;                           // 2 x 8192 FP32 input lines
+constexpr int F_HANK = 16384;                        // 6 x 2112 (L1 H1 L2 H2 L3 H3)
+constexpr int F_B2 = F_HANK + 6 * HANK_BYTES;        // 3 x 8192 (Y parts, MN-major) = 29056
+constexpr int F_OUT = F_B2 + 3 * 8192;               // FP32 line, 36 floats per 32: 4608 x 4 = 18432
+constexpr int POS_LEN = 4112;                        // uint16 positions per buffer (a row plus alignment)
+constexpr int F_POS = F_OUT + 18432;                 // 2 x POS_LEN uint16
+constexpr int F_CORR = F_POS + 2 * POS_LEN * 2;      // up to 512 floats
+constexpr int F_BYTES = (F_CORR + 2048 + 1023) / 1024 * 1024;
+constexpr int F_SMEM = OFF_G + WG * F_BYTES + 1024;  // + barriers
+static_assert(F_B2 % 16 == 0 && F_OUT % 16 == 0 && F_POS % 16 == 0, "alignment");
+// adjoint group region
+constexpr int A_STAGE = 0;                           // 2 x (4096 + 4) FP32: natural line or packed samples
+constexpr int A_STAGE_LEN = 4100;
+constexpr int A_SV = 2 * A_STAGE_LEN * 4;            // scatter target: the natural line (4096 FP32)
+constexpr int A_POS = A_SV + NL * 4;                 // 2 x POS_LEN uint16
+constexpr int A_OPS = A_POS + 2 * POS_LEN * 2;       // 3 x 8192: V parts (GEMM2 B), then Ybar parts (GEMM3 A)
+constexpr int A_EDGE = A_OPS + 3 * 8192;             // warp-boundary rows of Z: 4 warps x 2 x 16 floats
+constexpr int A_YE = A_EDGE + 4 * 2 * 16 * 4;        // Ybar rows of the edge blocks: up to 2 x 4 x 32 floats
+constexpr int A_CO = A_YE + 256 * 4;                 // corrections of the 4p edge outputs
+constexpr int A_BYTES = (A_CO + 64 * 4 + 1023) / 1024 * 1024;
+constexpr int A_SMEM = OFF_G + WG * A_BYTES + 1024;
+static_assert(A_SV % 16 == 0 && A_POS % 16 == 0 && A_OPS % 16 == 0 && A_EDGE % 16 == 0, "alignment");
+
+__host__ __device__ constexpr int opad(int k) { return k + 4 * (k >> 5); }
+
+struct Args {
+  const uint16_t* ops;    // d_umma: B1 parts (forward), B1^T parts (adjoint)
+  const float* corr;      // C'[2][KB*32][2p] or null
+  int KB, p, per;
+  int L;                  // log2 N
+  unsigned* err;          // plan error word (set when a wait gives up)
+  unsigned spin;          // polls per wait
+};
+
+// Everything one group keeps across its line loop.
+struct GroupBars {
+  uint64_t load[2];
+  uint64_t mma;
+  uint32_t status;        // broadcast of the polling thread's result
+  uint32_t pad;
+};
+
+// H128 (natural-order Walsh-Hadamard, +-1) in the K-major canonical layout:
+// element (row, k) at ((row / 8) 16 + k / 8) 64 + (row % 8) 8 + k % 8
+__device__ __forceinline__ void fill_h128(uint16_t* sH, int tid, int nth) {
+  for (int e = tid; e < 128 * 128 / 8; e += nth) {     // 16-byte chunks
+    const int core = e >> 3, rr = e & 7;
+    const int rg = core >> 4, kg = core & 15;
+    const int row = 8 * rg + rr;
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k0 = 8 * kg + 2 * q;
+      const uint16_t a = (__popc(row & k0) & 1) ? 0xBF80 : 0x3F80;
+      const uint16_t b = (__popc(row & (k0 + 1)) & 1) ? 0xBF80 : 0x3F80;
+      w[q] = (uint32_t)a | ((uint32_t)b << 16);
+    }
+    *reinterpret_cast<uint4*>(sH + 8 * e) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// one thread of the group polls; the group learns the result at the barrier
+__device__ __forceinline__ bool group_wait(GroupBars& gb, uint64_t* bar, uint32_t parity, unsigned spin, int wtid,
+                                           int barid) {
+  if (wtid == 0) gb.status = mbar_wait(bar, parity, spin) ? 1u : 0u;
+  bar_sync(barid, 128);
+  return gb.status != 0;
+}
+
+// Position of a group's lines: line index, instance, sequency / natural row.
+struct LineAt {
+  int l;
+  int64_t b;
+};
+__device__ __forceinline__ LineAt line_at(int line, int lines) { return LineAt{line % lines, line / lines}; }
+
+// packed-sample range [r0, r1) of mask row mrow
+__device__ __forceinline__ void sample_range(const LineIO& io, int mrow, int& r0, int& r1) {
+  r0 = __ldg(io.prefix + (int64_t)mrow * io.wpr);
+  r1 = mrow + 1 < io.mask_rows ? __ldg(io.prefix + (int64_t)(mrow + 1) * io.wpr) : (int)io.m;
+}
+
+
+// ---------------------------------------------------------------------------
+// forward: lines of M = 2048 coefficients (lo | hi) -> N = 4096 outputs
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NTH, 1) k_umma_fwd(const float* __restrict__ in, float* __restrict__ out, Args a,
+                                                     LineIO io, int total) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, g = tid >> 7, wtid = tid & 127, wq = wtid >> 5;
+  const int barid = 1 + g;
+  uint16_t* sH = reinterpret_cast<uint16_t*>(sm + OFF_H);
+  uint16_t* sB1 = reinterpret_cast<uint16_t*>(sm + OFF_B1);
+  unsigned char* G = sm + OFF_G + g * F_BYTES;
+  float* stage = reinterpret_cast<float*>(G + F_STAGE);
+  uint16_t* hank = reinterpret_cast<uint16_t*>(G + F_HANK);
+  unsigned char* b2 = G + F_B2;
+  float* sout = reinterpret_cast<float*>(G + F_OUT);
+  uint16_t* spos = reinterpret_cast<uint16_t*>(G + F_POS);
+  float* scorr = reinterpret_cast<float*>(G + F_CORR);
+  GroupBars* bars = reinterpret_cast<GroupBars*>(sm + OFF_G + WG * F_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + WG);
+  GroupBars& gb = bars[g];
+  const bool gather = io.mode == 1;
+
+  if (tid < 32) tmem_alloc(tslot, 256);
+  if (tid == 0) {
+    for (int k = 0; k < WG; ++k) {
+      mbar_init(&bars[k].load[0], 1);
+      mbar_init(&bars[k].load[1], 1);
+      mbar_init(&bars[k].mma, 1);
+    }
+    mbar_fence_init();
+  }
+  fill_h128(sH, tid, NTH);
+  for (int e = tid; e < 3 * 1536 / 8; e += NTH)
+    reinterpret_cast<uint4*>(sB1)[e] = __ldg(reinterpret_cast<const uint4*>(a.ops) + e);
+  // window halos start zero (VMP: zero padding); periodic halos are rewritten per line
+  for (int e = tid; e < WG * 6 * HANK_BYTES / 16; e += NTH) {
+    const int k = e / (6 * HANK_BYTES / 16), r = e % (6 * HANK_BYTES / 16);
+    reinterpret_cast<uint4*>(sm + OFF_G + k * F_BYTES + F_HANK)[r] = make_uint4(0, 0, 0, 0);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot + 128u * g;
+  const uint32_t D1 = tbase, D2 = tbase + 32;
+  const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
+
+  pdl_trigger();
+  pdl_wait();
+
+  const int step = WG * gridDim.x;
+  int line = WG * blockIdx.x + g;
+  bool ok = true;
+  uint32_t pend = 0, mma_pend = 0, ph_load[2] = {0, 0}, ph_mma = 0;
+
+  // one thread of the group: the input line and (gather) its sample positions
+  auto issue = [&](int ln, int bi) {
+    const LineAt at = line_at(ln, io.lines);
+    const int drow = io.seq_rows ? seqrow(at.l, a.L) : at.l;
+    const float* src = in + at.b * io.in_batch + (int64_t)drow * io.in_stride;
+    uint32_t pbytes = 0;
+    int p0 = 0;
+    if (gather) {
+      int r0, r1;
+      sample_range(io, at.l, r0, r1);
+      p0 = r0 & ~7;
+      pbytes = (uint32_t)(2 * (((r1 + 7) & ~7) - p0));
+    }
+    fence_async_smem();
+    mbar_expect_tx(&gb.load[bi], ML * 4 + pbytes);
+    bulk_g2s(stage + bi * ML, src, ML * 4, &gb.load[bi]);
+    if (pbytes) bulk_g2s(spos + bi * POS_LEN, io.pos + p0, pbytes, &gb.load[bi]);
+  };
+
+  if (line < total) {
+    if (wtid == 0) issue(line, 0);
+    pend = 1;
+  }
+  for (int it = 0; line < total; line += step, ++it) {
+    const int buf = it & 1;
+    const int nxt = line + step;
+    if (nxt < total) {
+      if (wtid == 0) issue(nxt, buf ^ 1);
+      pend |= 1u << (buf ^ 1);
+    }
+    if (!group_wait(gb, &gb.load[buf], ph_load[buf], a.spin, wtid, barid)) {
+      ok = false;
+      break;
+    }
+    ph_load[buf] ^= 1;
+    pend &= ~(1u << buf);
+    const LineAt at = line_at(line, io.lines);
+    const float* xin = stage + buf * ML;
+
+    // split lo[8t, 8t + 8) and hi[8t, 8t + 8) into three BF16 parts
+    {
+      const float4* s4 = reinterpret_cast<const float4*>(xin);
+      const float4 l0 = s4[2 * wtid], l1 = s4[2 * wtid + 1];
+      const float4 h0 = s4[N0 / 4 + 2 * wtid], h1 = s4[N0 / 4 + 2 * wtid + 1];
+      uint32_t pl[3][4], ph[3][4];
+      split3x2(l0.x, l0.y, pl[0][0], pl[1][0], pl[2][0]);
+      split3x2(l0.z, l0.w, pl[0][1], pl[1][1], pl[2][1]);
+      split3x2(l1.x, l1.y, pl[0][2], pl[1][2], pl[2][2]);
+      split3x2(l1.z, l1.w, pl[0][3], pl[1][3], pl[2][3]);
+      split3x2(h0.x, h0.y, ph[0][0], ph[1][0], ph[2][0]);
+      split3x2(h0.z, h0.w, ph[0][1], ph[1][1], ph[2][1]);
+      split3x2(h1.x, h1.y, ph[0][2], ph[1][2], ph[2][2]);
+      split3x2(h1.z, h1.w, ph[0][3], ph[1][3], ph[2][3]);
+#pragma unroll
+      for (int P = 0; P < 3; ++P) {
+        uint16_t* L = hank + (2 * P) * HANK_LEN;
+        uint16_t* H = L + HANK_LEN;
+        const uint4 vl = make_uint4(pl[P][0], pl[P][1], pl[P][2], pl[P][3]);
+        const uint4 vh = make_uint4(ph[P][0], ph[P][1], ph[P][2], ph[P][3]);
+        *reinterpret_cast<uint4*>(L + 8 + 8 * wtid) = vl;
+        *reinterpret_cast<uint4*>(H + 8 + 8 * wtid) = vh;
+        if (a.per) {   // window positions -8..-1 and 1024..1031 wrap around
+          if (wtid == 0) {
+            *reinterpret_cast<uint4*>(L + 8 + N0) = vl;
+            *reinterpret_cast<uint4*>(H + 8 + N0) = vh;
+          }
+          if (wtid == 127) {
+            *reinterpret_cast<uint4*>(L) = vl;
+            *reinterpret_cast<uint4*>(H) = vh;
+          }
+        }
+      }
+    }
+    // VMP: the corrections of the first / last KB blocks, one value per thread
+    if (a.KB) {
+      for (int c = wtid; c < 2 * a.KB * 32; c += 128) {
+        const int side = c >= a.KB * 32;
+        const float* C = a.corr + (size_t)c * 2 * a.p;
+        float acc = 0.f;
+        for (int e = 0; e < 2 * a.p; ++e) {
+          const int half = e >= a.p, ee = e - half * a.p;
+          acc = fmaf(__ldg(C + e), xin[half * N0 + (side ? N0 - a.p + ee : ee)], acc);
+        }
+        scorr[c] = acc;
+      }
+    }
+    fence_async_smem();
+    bar_sync(barid, 128);
+    // GEMM1: the six part products, three K steps each
+    if (wtid == 0) {
+      tc_fence_after();
+      const uint32_t id1 = idesc_bf16(128, 32, 0, 0);
+      const uint32_t hk = smem_u32(hank), bb = smem_u32(sB1);
+      uint32_t acc = 0;
+#pragma unroll
+      for (int dp = 0; dp < 3; ++dp)
+#pragma unroll
+        for (int op = 0; op + dp < 3; ++op) {
+          const uint32_t L = hk + 2 * dp * HANK_BYTES, H = L + HANK_BYTES, Bp = bb + op * 3072;
+          umma_bf16(D1, sdesc(L, 16, 128), sdesc(Bp, 128, 768), id1, acc);
+          umma_bf16(D1, sdesc(L + 32, HANK_BYTES - 32, 128), sdesc(Bp + 256, 128, 768), id1, 1);
+          umma_bf16(D1, sdesc(H + 16, 16, 128), sdesc(Bp + 512, 128, 768), id1, 1);
+          acc = 1;
+        }
+      umma_commit(&gb.mma);
+    }
+    mma_pend = 1;
+    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
+      ok = false;
+      break;
+    }
+    ph_mma ^= 1;
+    mma_pend = 0;
+    tc_fence_after();
+    {
+      float y[32];
+      tmem_ld32(D1 + lane_off, y);
+      const int b = wtid;
+      if (a.KB) {
+        int row = -1;
+        if (b < a.KB) row = b;
+        else if (b >= NB - a.KB) row = a.KB + b - (NB - a.KB);
+        if (row >= 0) {
+#pragma unroll
+          for (int r = 0; r < 32; ++r) y[r] += scorr[32 * row + r];
+        }
+      }
+      // MN-major B operand of GEMM2: element (r, b) of part P at
+      // P 8192 + (r % 8) 2 + (r / 8) 128 + (b % 8) 16 + (b / 8) 512
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t w[3][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split3x2(y[8 * q + 2 * e], y[8 * q + 2 * e + 1], w[0][e], w[1][e], w[2][e]);
+#pragma unroll
+        for (int P = 0; P < 3; ++P)
+          *reinterpret_cast<uint4*>(b2 + P * 8192 + q * 128 + (b & 7) * 16 + (b >> 3) * 512) =
+              make_uint4(w[P][0], w[P][1], w[P][2], w[P][3]);
+      }
+    }
+    tc_fence_before();
+    fence_async_smem();
+    bar_sync(barid, 128);
+    // GEMM2: H128 against the three parts, eight K steps each
+    if (wtid == 0) {
+      tc_fence_after();
+      const uint32_t id2 = idesc_bf16(128, 32, 0, 1);
+      const uint32_t hs = smem_u32(sH), bq = smem_u32(b2);
+#pragma unroll
+      for (int P = 0; P < 3; ++P)
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+          umma_bf16(D2, sdesc(hs + 256 * s, 128, 2048), sdesc(bq + P * 8192 + 1024 * s, 512, 128), id2,
+                    (P | s) != 0);
+      umma_commit(&gb.mma);
+    }
+    mma_pend = 1;
+    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
+      ok = false;
+      break;
+    }
+    ph_mma ^= 1;
+    mma_pend = 0;
+    tc_fence_after();
+    {
+      float o[32];
+      tmem_ld32(D2 + lane_off, o);
+      float* row = sout + opad(32 * wtid);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4*>(row + 4 * q) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    }
+    tc_fence_before();
+    bar_sync(barid, 128);
+    if (gather) {
+      int r0, r1;
+      sample_range(io, at.l, r0, r1);
+      const uint16_t* ps = spos + buf * POS_LEN + (r0 & 7);
+      float* y = out + at.b * io.m + r0;
+      for (int j = wtid; j < r1 - r0; j += 128) y[j] = sout[opad(ps[j])];
+    } else {
+      float* dst = out + at.b * io.out_batch + (int64_t)at.l * io.out_stride;
+#pragma unroll 4
+      for (int c = wtid; c < NL / 4; c += 128)
+        *reinterpret_cast<float4*>(dst + 4 * c) = *reinterpret_cast<const float4*>(sout + opad(4 * c));
+    }
+    // the staging buffers of this line are read: the next copies may land
+    bar_sync(barid, 128);
+  }
+  if (!ok && wtid == 0) atomicExch(a.err, 1u);
+  // drain what is still in flight (bounded), then free the tensor memory
+  if (wtid == 0) {
+    for (int bi = 0; bi < 2; ++bi)
+      if (pend & (1u << bi)) mbar_wait(&gb.load[bi], ph_load[bi], 1u << 22);
+    if (mma_pend) mbar_wait(&gb.mma, ph_mma, 1u << 22);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid < 32) tmem_dealloc(*tslot, 256);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint: natural lines of N = 4096 (mode 0) or the sampled entries of a
+// sequency row (mode 1) -> M = 2048 coefficients (lo | hi)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NTH, 1) k_umma_adj(const float* __restrict__ in, float* __restrict__ out, Args a,
+                                                     LineIO io, int total) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, g = tid >> 7, wtid = tid & 127, wq = wtid >> 5, lane = tid & 31;
+  const int barid = 1 + g;
+  uint16_t* sH = reinterpret_cast<uint16_t*>(sm + OFF_H);
+  uint16_t* sBt = reinterpret_cast<uint16_t*>(sm + OFF_B1);
+  unsigned char* G = sm + OFF_G + g * A_BYTES;
+  float* stage = reinterpret_cast<float*>(G + A_STAGE);
+  float* sv = reinterpret_cast<float*>(G + A_SV);
+  uint16_t* spos = reinterpret_cast<uint16_t*>(G + A_POS);
+  unsigned char* ops = G + A_OPS;
+  float* sedge = reinterpret_cast<float*>(G + A_EDGE);
+  float* sye = reinterpret_cast<float*>(G + A_YE);
+  float* sco = reinterpret_cast<float*>(G + A_CO);
+  GroupBars* bars = reinterpret_cast<GroupBars*>(sm + OFF_G + WG * A_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + WG);
+  GroupBars& gb = bars[g];
+  const bool scat = io.mode == 1;
+
+  if (tid < 32) tmem_alloc(tslot, 256);
+  if (tid == 0) {
+    for (int k = 0; k < WG; ++k) {
+      mbar_init(&bars[k].load[0], 1);
+      mbar_init(&bars[k].load[1], 1);
+      mbar_init(&bars[k].mma, 1);
+    }
+    mbar_fence_init();
+  }
+  fill_h128(sH, tid, NTH);
+  for (int e = tid; e < 3 * 1536 / 8; e += NTH)
+    reinterpret_cast<uint4*>(sBt)[e] = __ldg(reinterpret_cast<const uint4*>(a.ops) + 3 * 1536 / 8 + e);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot + 128u * g;
+  const uint32_t D2 = tbase, D3 = tbase + 32;
+  const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
+
+  pdl_trigger();
+  pdl_wait();
+
+  const int step = WG * gridDim.x;
+  int line = WG * blockIdx.x + g;
+  bool ok = true;
+  uint32_t pend = 0, mma_pend = 0, ph_load[2] = {0, 0}, ph_mma = 0;
+
+  // one thread of the group: the natural line, or the aligned span of the
+  // row's packed samples (whole 16-byte units inside [r0, r1)) and positions
+  auto issue = [&](int ln, int bi) {
+    const LineAt at = line_at(ln, io.lines);
+    fence_async_smem();
+    if (!scat) {
+      const float* src = in + at.b * io.in_batch + (int64_t)at.l * io.in_stride;
+      mbar_expect_tx(&gb.load[bi], NL * 4);
+      bulk_g2s(stage + bi * A_STAGE_LEN, src, NL * 4, &gb.load[bi]);
+      return;
+    }
+    int r0, r1;
+    sample_range(io, at.l, r0, r1);
+    const int64_t base = at.b * io.m;             // a multiple of 4: checked on the host
+    const int a0 = (r0 + 3) & ~3, a1 = r1 & ~3;   // aligned interior span of the samples
+    const uint32_t ybytes = a1 > a0 ? (uint32_t)(4 * (a1 - a0)) : 0u;
+    const int p0 = r0 & ~7;
+    const uint32_t pbytes = (uint32_t)(2 * (((r1 + 7) & ~7) - p0));
+    // sample k of the row sits at stage[k - (r0 & ~3)]: the aligned span lands 16-byte aligned
+    // (an arrival with nothing to copy completes the phase at once)
+    mbar_expect_tx(&gb.load[bi], ybytes + pbytes);
+    if (ybytes) bulk_g2s(stage + bi * A_STAGE_LEN + (a0 - (r0 & ~3)), in + base + a0, ybytes, &gb.load[bi]);
+    if (pbytes) bulk_g2s(spos + bi * POS_LEN, io.pos + p0, pbytes, &gb.load[bi]);
+  };
+
+  if (line < total) {
+    if (wtid == 0) issue(line, 0);
+    pend = 1;
+  }
+  for (int it = 0; line < total; line += step, ++it) {
+    const int buf = it & 1;
+    const int nxt = line + step;
+    if (nxt < total) {
+      if (wtid == 0) issue(nxt, buf ^ 1);
+      pend |= 1u << (buf ^ 1);
+    }
+    if (!group_wait(gb, &gb.load[buf], ph_load[buf], a.spin, wtid, barid)) {
+      ok = false;
+      break;
+    }
+    ph_load[buf] ^= 1;
+    pend &= ~(1u << buf);
+    const LineAt at = line_at(line, io.lines);
+    const float* v = stage + buf * A_STAGE_LEN;
+    if (scat) {
+      int r0, r1;
+      sample_range(io, at.l, r0, r1);
+      float* st = stage + buf * A_STAGE_LEN + (r0 & 3);   // relative sample j at st[j]
+      const float* ysrc = in + at.b * io.m;
+      // the unaligned head and tail of the samples with plain loads
+      const int a0 = (r0 + 3) & ~3, a1 = r1 & ~3;
+      if (a1 > a0) {
+        if (wtid < a0 - r0) st[wtid] = __ldg(ysrc + r0 + wtid);
+        if (wtid < r1 - a1) st[a1 - r0 + wtid] = __ldg(ysrc + a1 + wtid);
+      } else {
+        if (wtid < r1 - r0) st[wtid] = __ldg(ysrc + r0 + wtid);
+      }
+#pragma unroll
+      for (int i = 0; i < NL / 4 / 128; ++i)
+        reinterpret_cast<float4*>(sv)[wtid + 128 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      bar_sync(barid, 128);
+      const uint16_t* ps = spos + buf * POS_LEN + (r0 & 7);
+      for (int j = wtid; j < r1 - r0; j += 128) sv[ps[j]] = st[j];
+      bar_sync(barid, 128);
+      v = sv;
+    }
+    // V parts as the MN-major B operand of GEMM2: chunk c = (b, q) holds
+    // v[32 b + 8 q, + 8) at P 8192 + q 128 + (b % 8) 16 + (b / 8) 512
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int c = wtid + 128 * i, b = c >> 2, q = c & 3;
+      const float4 u0 = reinterpret_cast<const float4*>(v)[2 * c];
+      const float4 u1 = reinterpret_cast<const float4*>(v)[2 * c + 1];
+      uint32_t w[3][4];
+      split3x2(u0.x, u0.y, w[0][0], w[1][0], w[2][0]);
+      split3x2(u0.z, u0.w, w[0][1], w[1][1], w[2][1]);
+      split3x2(u1.x, u1.y, w[0][2], w[1][2], w[2][2]);
+      split3x2(u1.z, u1.w, w[0][3], w[1][3], w[2][3]);
+#pragma unroll
+      for (int P = 0; P < 3; ++P)
+        *reinterpret_cast<uint4*>(ops + P * 8192 + q * 128 + (b & 7) * 16 + (b >> 3) * 512) =
+            make_uint4(w[P][0], w[P][1], w[P][2], w[P][3]);
+    }
+    fence_async_smem();
+    bar_sync(barid, 128);
+    if (wtid == 0) {
+      tc_fence_after();
+      const uint32_t id2 = idesc_bf16(128, 32, 0, 1);
+      const uint32_t hs = smem_u32(sH), bq = smem_u32(ops);
+#pragma unroll
+      for (int P = 0; P < 3; ++P)
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+          umma_bf16(D2, sdesc(hs + 256 * s, 128, 2048), sdesc(bq + P * 8192 + 1024 * s, 512, 128), id2,
+                    (P | s) != 0);
+      umma_commit(&gb.mma);
+    }
+    mma_pend = 1;
+    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
+      ok = false;
+      break;
+    }
+    ph_mma ^= 1;
+    mma_pend = 0;
+    tc_fence_after();
+    {
+      float y[32];
+      tmem_ld32(D2 + lane_off, y);
+      const int b = wtid;
+      if (a.KB) {   // keep the edge blocks' rows for the corrections
+        int row = -1;
+        if (b < a.KB) row = b;
+        else if (b >= NB - a.KB) row = a.KB + b - (NB - a.KB);
+        if (row >= 0) {
+#pragma unroll
+          for (int r = 0; r < 32; r += 4)
+            *reinterpret_cast<float4*>(sye + 32 * row + r) = make_float4(y[r], y[r + 1], y[r + 2], y[r + 3]);
+        }
+      }
+      // K-major A operand of GEMM3: element (b, r) of part P at
+      // P 8192 + (b % 8) 16 + (b / 8) 512 + (r % 8) 2 + (r / 8) 128
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t w[3][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split3x2(y[8 * q + 2 * e], y[8 * q + 2 * e + 1], w[0][e], w[1][e], w[2][e]);
+#pragma unroll
+        for (int P = 0; P < 3; ++P)
+          *reinterpret_cast<uint4*>(ops + P * 8192 + q * 128 + (b & 7) * 16 + (b >> 3) * 512) =
+              make_uint4(w[P][0], w[P][1], w[P][2], w[P][3]);
+      }
+    }
+    tc_fence_before();
+    fence_async_smem();
+    bar_sync(barid, 128);
+    if (wtid == 0) {
+      tc_fence_after();
+      const uint32_t id3 = idesc_bf16(128, 48, 0, 0);
+      const uint32_t aq = smem_u32(ops), bb = smem_u32(sBt);
+      uint32_t acc = 0;
+#pragma unroll
+      for (int dp = 0; dp < 3; ++dp)
+#pragma unroll
+        for (int op = 0; op + dp < 3; ++op)
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            umma_bf16(D3, sdesc(aq + dp * 8192 + 256 * s, 128, 512), sdesc(bb + op * 3072 + 256 * s, 128, 512), id3,
+                      acc);
+            acc = 1;
+          }
+      umma_commit(&gb.mma);
+    }
+    // VMP: corrections of the 4p edge outputs from the edge blocks' rows
+    if (a.KB && wtid < 4 * a.p) {
+      const int side = wtid >= 2 * a.p, c = wtid - side * 2 * a.p;
+      const float* C = a.corr + (size_t)side * a.KB * 32 * 2 * a.p + c;
+      const float* ye = sye + side * a.KB * 32;
+      float acc = 0.f;
+      for (int k = 0; k < a.KB * 32; ++k) acc = fmaf(__ldg(C + (size_t)k * 2 * a.p), ye[k], acc);
+      sco[wtid] = acc;
+    }
+    mma_pend = 1;
+    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
+      ok = false;
+      break;
+    }
+    ph_mma ^= 1;
+    mma_pend = 0;
+    tc_fence_after();
+    {
+      // Z row b: 48 values; lo[8c + e] = Z[c+1][e] + Z[c][8+e] + Z[c-1][16+e],
+      // hi[8c + e] = Z[c+1][24+e] + Z[c][32+e] + Z[c-1][40+e]
+      float z[48];
+      {
+        float t32[32];
+        float t16[16];
+        tmem_ld32(D3 + lane_off, t32);
+        tmem_ld16(D3 + lane_off + 32, t16);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) z[i] = t32[i];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[32 + i] = t16[i];
+      }
+      // rows that cross a warp boundary go through shared memory
+      if (lane == 0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          sedge[(wq * 2 + 0) * 16 + e] = z[e];
+          sedge[(wq * 2 + 0) * 16 + 8 + e] = z[24 + e];
+        }
+      }
+      if (lane == 31) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          sedge[(wq * 2 + 1) * 16 + e] = z[16 + e];
+          sedge[(wq * 2 + 1) * 16 + 8 + e] = z[40 + e];
+        }
+      }
+      tc_fence_before();
+      bar_sync(barid, 128);
+      const int c = wtid;
+      const bool has_next = a.per || c + 1 < NB, has_prev = a.per || c > 0;
+      float lo[8], hi[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        float nl = __shfl_down_sync(0xffffffffu, z[e], 1);
+        float nh = __shfl_down_sync(0xffffffffu, z[24 + e], 1);
+        float pl = __shfl_up_sync(0xffffffffu, z[16 + e], 1);
+        float ph = __shfl_up_sync(0xffffffffu, z[40 + e], 1);
+        if (lane == 31) {   // row c + 1 is lane 0 of the next warp (wrapping for periodic plans)
+          const int w2 = (wq + 1) & 3;
+          nl = sedge[(w2 * 2 + 0) * 16 + e];
+          nh = sedge[(w2 * 2 + 0) * 16 + 8 + e];
+        }
+        if (lane == 0) {
+          const int w0 = (wq + 3) & 3;
+          pl = sedge[(w0 * 2 + 1) * 16 + e];
+          ph = sedge[(w0 * 2 + 1) * 16 + 8 + e];
+        }
+        lo[e] = z[8 + e] + (has_next ? nl : 0.f) + (has_prev ? pl : 0.f);
+        hi[e] = z[32 + e] + (has_next ? nh : 0.f) + (has_prev ? ph : 0.f);
+      }
+      if (a.KB) {
+        if (c == 0) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (e < a.p) {
+              lo[e] += sco[e];
+              hi[e] += sco[a.p + e];
+            }
+        }
+        if (c == NB - 1) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int k = e - (8 - a.p);   // lo[n0 - p + k] sits at e = 8 - p + k
+            if (k >= 0) {
+              lo[e] += sco[2 * a.p + k];
+              hi[e] += sco[3 * a.p + k];
+            }
+          }
+        }
+      }
+      const int drow = io.seq_rows ? seqrow(at.l, a.L) : at.l;
+      float* dst = out + at.b * io.out_batch + (int64_t)drow * io.out_stride;
+      *reinterpret_cast<float4*>(dst + 8 * c) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<float4*>(dst + 8 * c + 4) = make_float4(lo[4], lo[5], lo[6], lo[7]);
+      *reinterpret_cast<float4*>(dst + N0 + 8 * c) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<float4*>(dst + N0 + 8 * c + 4) = make_float4(hi[4], hi[5], hi[6], hi[7]);
+    }
+    // shared buffers of this line are read: the next copies may land
+    bar_sync(barid, 128);
+  }
+  if (!ok && wtid == 0) atomicExch(a.err, 1u);
+  if (wtid == 0) {
+    for (int bi = 0; bi < 2; ++bi)
+      if (pend & (1u << bi)) mbar_wait(&gb.load[bi], ph_load[bi], 1u << 22);
+    if (mma_pend) mbar_wait(&gb.mma, ph_mma, 1u << 22);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid < 32) tmem_dealloc(*tslot, 256);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static unsigned spin_limit() {
+  const char* e = getenv("UW_TC_SPIN_LIMIT");
+  if (e && *e) return (unsigned)strtoul(e, nullptr, 10);
+  return 1u << 22;
+}
+
+}  // namespace ummak
+
+bool umma_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd, int total) {
+  if (!P.umma.ok || !P.d_umma || io.jlev != P.R - 1) return false;
+  if (P.N != ummak::NL || P.Q != 2 || P.M != ummak::ML || P.p > 8) return false;
+  if (P.umma.KB > 4 || !P.d_sync) return false;
+  if (io.mode == 1 && P.m > 0 && !io.pos) return false;
+  auto al16 = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+  if (fwd) {
+    if (!al16(in) || io.in_stride % 4 || io.in_batch % 4) return false;
+    if (io.mode == 0 && (io.out_stride % 4 || io.out_batch % 4 || !al16(out))) return false;
+  } else {
+    if (io.mode == 0 && (!al16(in) || io.in_stride % 4 || io.in_batch % 4)) return false;
+    // the aligned copies of a row's samples need every instance's samples to
+    // start 16-byte aligned
+    if (io.mode == 1 && (!al16(in) || (total > io.lines && io.m % 4))) return false;
+    if (!al16(out) || io.out_stride % 4 || io.out_batch % 4) return false;
+  }
+  return true;
+}
+
+cudaError_t umma_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
+                        cudaStream_t s) {
+  using namespace ummak;
+  Args a{};
+  a.ops = (const uint16_t*)P.d_umma;
+  a.KB = P.umma.KB;
+  a.corr = a.KB ? (const float*)P.d_umma + P.umma.oC : nullptr;
+  a.p = P.p;
+  a.per = P.bd == UW_BOUNDARY_PERIODIC;
+  int L = 0;
+  while ((1 << L) < P.N) ++L;
+  a.L = L;
+  a.err = (unsigned*)P.d_sync + 2;
+  a.spin = spin_limit();
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(nsm, (total + WG - 1) / WG));
+  if (fwd) {
+    cudaFuncSetAttribute((const void*)k_umma_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
+    return launch_pdl(k_umma_fwd, dim3(grid), dim3(NTH), (size_t)F_SMEM, s, in, out, a, io, total);
+  }
+  cudaFuncSetAttribute((const void*)k_umma_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, A_SMEM);
+  return launch_pdl(k_umma_adj, dim3(grid), dim3(NTH), (size_t)A_SMEM, s, in, out, a, io, total);
+}
+
+}  // namespace uw

@@ -345,6 +345,11 @@ bool tc_eligible(const Plan& P, const LineIO& io, const void* in, const void* ou
 cudaError_t tc_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
                       cudaStream_t s);
 
+// kernels_umma.cu: split-BF16 line operators on tcgen05 (last level, N = 4096, q = 1)
+bool umma_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd, int total);
+cudaError_t umma_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
+                        cudaStream_t s);
+
 // kernels_f32.cu: persistent FP32 line operators (last level, N = 2048 / 4096)
 bool f32_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd);
 cudaError_t f32_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,

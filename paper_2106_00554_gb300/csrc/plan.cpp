@@ -712,8 +712,9 @@ static int upload_mask(uw_plan* P, const int64_t* omega, int64_t m) {
   }
   uint16_t* dpos = nullptr;
   if (!pos.empty()) {
-    pos.push_back(0);   // padding: positions are also read in 32-bit pairs
-    pos.push_back(0);
+    // padding: positions are also read in 32-bit pairs and copied in whole
+    // 16-byte units (up to 7 entries past a row's last sample)
+    pos.resize((pos.size() + 7) / 8 * 8 + 8, 0);
     if (cudaMalloc(&dpos, pos.size() * sizeof(uint16_t)) != cudaSuccess) {
       cudaGetLastError();
       return fail(UW_ERR_OOM, "sample position allocation failed");
@@ -886,6 +887,7 @@ void uw_plan_destroy(uw_plan* P) {
   cudaFree(P->d_work);
   cudaFree(P->d_stage);
   cudaFree(P->d_tc);
+  cudaFree(P->d_umma);
   cudaFree(P->d_f32);
   cudaFree(P->d_sync);
   cudaFree(P->d_coarse);

@@ -456,6 +456,129 @@ void build_f32(Plan& P, std::vector<float>& out) {
   F.ok = 1;
 }
 
+// Operators of the tcgen05 line kernels (UmmaGeo in uw_internal.h).  With
+// q = 1 the interior map from the coefficients to the outputs of T is shift
+// invariant under (k, i) -> (k + 32, i + 8), so one 32 x 48 matrix B1 serves
+// every block of 32 outputs: B1[r][j] = sum_r' H32[r][r'] d v[r'] / d x[i_j],
+// i_j = j - 8 (lo) or j - 32 (hi), folding the Walsh-Hadamard stages of bits
+// 0-4 (natural order, Sec. 3.1) into the last synthesis level and T (Sec. 3.2,
+// 4.1).  The window [-8, 16) must hold every i the interior map reaches
+// (p <= 9); this is checked.
+namespace {
+
+// K-major canonical layout of a rows x K BF16 operand without swizzling:
+// core matrix (row / 8, k / 8) at ((row / 8) (K / 8) + k / 8) 64 elements,
+// inside it row % 8 then k % 8
+void pack_kmajor3(const std::vector<double>& A, int rows, int K, uint16_t* out) {
+  for (int part = 0; part < 3; ++part)
+    for (int r = 0; r < rows; ++r)
+      for (int k = 0; k < K; ++k) {
+        double x = A[(size_t)r * K + k];
+        uint16_t b1 = bf16_rn((float)x);
+        double r1 = x - (double)bf16_f(b1);
+        uint16_t b2 = bf16_rn((float)r1);
+        double r2 = r1 - (double)bf16_f(b2);
+        uint16_t b3 = bf16_rn((float)r2);
+        const uint16_t b = part == 0 ? b1 : (part == 1 ? b2 : b3);
+        out[(size_t)part * rows * K + ((size_t)(r / 8) * (K / 8) + k / 8) * 64 + (r % 8) * 8 + k % 8] = b;
+      }
+}
+
+}  // namespace
+
+void build_umma(Plan& P, std::vector<unsigned char>& bytes) {
+  bytes.clear();
+  UmmaGeo& U = P.umma;
+  U = UmmaGeo{};
+  if (P.Q != 2 || P.N != 4096 || P.p > 9) return;
+  const int p = P.p, n0 = P.M / 2, N = P.N;
+  Exact X(P);
+  // window coverage: every interior entry of the first block lies in the window
+  for (int r = 0; r < 32; ++r)
+    for (int i = -3 * p - 8; i < 3 * p + 24; ++i) {
+      if (i >= -8 && i < 16) continue;
+      if (X.interior(r, i, false) != 0.0 || X.interior(r, i, true) != 0.0) return;
+    }
+  auto hs = [](int a, int b) { return (__builtin_popcount((unsigned)(a & b)) & 1) ? -1.0 : 1.0; };
+  std::vector<double> B1(32 * 48), B1t(48 * 32);
+  for (int r = 0; r < 32; ++r)
+    for (int j = 0; j < 48; ++j) {
+      const bool hi = j >= 24;
+      const int i = hi ? j - 32 : j - 8;
+      double acc = 0;
+      for (int r2 = 0; r2 < 32; ++r2) acc += hs(r, r2) * X.interior(r2, i, hi);
+      B1[(size_t)r * 48 + j] = acc;
+      B1t[(size_t)j * 32 + r] = acc;
+    }
+  // VMP corrections: exact minus the windowed interior map (zero padding
+  // beyond the coefficient range), for unit vectors at the edge columns; a
+  // few columns past the edge must show no difference
+  int KB = 0;
+  std::vector<std::vector<std::vector<double>>> D;
+  if (P.bd != UW_BOUNDARY_PERIODIC) {
+    const int Wc = p + 4;
+    if (n0 < 2 * Wc + 16) return;
+    D.assign(2, std::vector<std::vector<double>>(2 * Wc, std::vector<double>(N, 0.0)));
+    std::vector<double> lo(n0), hi(n0), s, ve;
+    double dmax = 0;
+    for (int side = 0; side < 2; ++side)
+      for (int c = 0; c < 2 * Wc; ++c) {
+        std::fill(lo.begin(), lo.end(), 0.0);
+        std::fill(hi.begin(), hi.end(), 0.0);
+        const int i = side == 0 ? c % Wc : n0 - 1 - (c % Wc);
+        const bool h = c >= Wc;
+        (h ? hi : lo)[i] = 1.0;
+        X.syn(lo, hi, s);
+        X.up(s, ve);
+        for (int k = 0; k < N; ++k) {
+          const double d = ve[k] - X.interior(k, i, h);
+          D[side][c][k] = d;
+          dmax = std::max(dmax, std::fabs(d));
+        }
+      }
+    const double tol = 1e-12 * std::max(dmax, 1e-300);
+    int K = 0;
+    for (int side = 0; side < 2; ++side)
+      for (int c = 0; c < 2 * Wc; ++c)
+        for (int k = 0; k < N; ++k) {
+          if (std::fabs(D[side][c][k]) <= tol) continue;
+          if ((c % Wc) >= p) return;            // a difference outside the edge columns
+          K = std::max(K, (side == 0 ? k : N - 1 - k) + 1);
+        }
+    KB = (K + 31) / 32;
+    if (2 * KB > 128) return;
+  }
+  U.KB = KB;
+  const size_t nb = 3 * 1536;                   // bf16 values per operator
+  U.oF = 0;
+  U.oA = (int64_t)nb;
+  const size_t corr_floats = (size_t)2 * KB * 32 * 2 * p;
+  U.oC = (int64_t)(2 * nb * sizeof(uint16_t) / sizeof(float));
+  U.bytes = (int64_t)(2 * nb * sizeof(uint16_t) + corr_floats * sizeof(float));
+  bytes.assign((size_t)U.bytes, 0);
+  uint16_t* w = reinterpret_cast<uint16_t*>(bytes.data());
+  pack_kmajor3(B1, 32, 48, w + U.oF);
+  pack_kmajor3(B1t, 48, 32, w + U.oA);
+  if (KB) {
+    float* C = reinterpret_cast<float*>(bytes.data()) + U.oC;
+    const int Wc = p + 4;
+    for (int side = 0; side < 2; ++side)
+      for (int row = 0; row < KB * 32; ++row) {
+        const int bb = row / 32, r = row % 32;
+        for (int c = 0; c < 2 * p; ++c) {
+          // columns: lo[0..p), hi[0..p) on the left; lo[n0-p..n0), hi[n0-p..n0) on the right
+          const int e = c % p, half = c / p;
+          const int col = side == 0 ? half * Wc + e : half * Wc + (p - 1 - e);
+          const int k0 = side == 0 ? 32 * bb : N - 32 * KB + 32 * bb;
+          double acc = 0;
+          for (int r2 = 0; r2 < 32; ++r2) acc += hs(r, r2) * D[side][col][k0 + r2];
+          C[((size_t)side * KB * 32 + row) * 2 * p + c] = (float)acc;
+        }
+      }
+  }
+  U.ok = 1;
+}
+
 // Edge corrections of one 2D Mallat level (the coarse-level kernels): the
 // exact VMP synthesis of a level (Sec. 3.2: interior two-scale relations plus
 // the level-independent boundary blocks) differs from the interior formula

@@ -66,6 +66,27 @@ struct F32Geo {
   int64_t words = 0;
 };
 
+// Geometry of the tcgen05 split-BF16 line operators (kernels_umma.cu), for
+// lines of N = 4096 samples with q = 1.  A line is 128 blocks of 32 outputs,
+// k = 32 b + r.  Forward: D1[b][r] = sum_j W[b][j] B1[r][j] with the window
+// W[b][j] = lo[8 b - 8 + j] (j < 24), hi[8 b - 32 + j] (j >= 24), and B1 the
+// last synthesis level, T and the Walsh-Hadamard stages of bits 0-4 of one
+// block; then D2 = H_128 D1 (bits 5-11).  The adjoint applies the
+// transposes.  Near a VMP boundary the exact operator differs from the
+// windowed interior one by a correction that reads only the p lo and p hi
+// coefficients at that end and reaches only the first / last KB blocks.
+// Device buffer d_umma: three BF16 parts of B1 (forward B operand, K-major,
+// 32 x 48), three BF16 parts of B1^T (adjoint B operand, K-major, 48 x 32),
+// then the corrections C'[2][KB * 32][2p] (FP32, the Walsh stages of bits
+// 0-4 applied to each row block).
+struct UmmaGeo {
+  int ok = 0;
+  int KB = 0;                  // corrected blocks per side (0: periodic or none)
+  int64_t oF = 0, oA = 0;      // bf16 offsets of the operator parts (each 3 x 1536 values)
+  int64_t oC = 0;              // float offset of the corrections
+  int64_t bytes = 0;
+};
+
 struct Plan {
   int d = 1, R = 0, q = 0, p = 1, bd = 0, J0 = 0;
   int family = 0;            // 0: extremal-phase Daubechies, 1: least asymmetric (symlet)
@@ -108,6 +129,8 @@ struct Plan {
   Profiler* prof = nullptr;
   TcGeo tc;                      // split-BF16 line operators (tc.ok = 0: not eligible)
   void* d_tc = nullptr;
+  UmmaGeo umma;                  // tcgen05 line operators (umma.ok = 0: not eligible)
+  void* d_umma = nullptr;
   F32Geo f32;                    // FP32 line operators (f32.ok = 0: not eligible)
   void* d_f32 = nullptr;         // [2][K][CS] floats (left, then right)
   void* d_sync = nullptr;        // grid barrier of the fused coarse-level kernels
@@ -120,6 +143,10 @@ bool build_tables(Plan& P, std::string& err);
 // tc_plan.cpp: block matrices of the tensor-core line operators (host, FP64);
 // fills P.tc and the packed words to upload (empty if not eligible)
 void build_tc(Plan& P, std::vector<uint32_t>& words);
+// tc_plan.cpp: operator matrices and edge corrections of the tcgen05 line
+// operators (host, FP64); fills P.umma and the bytes to upload (empty if not
+// eligible)
+void build_umma(Plan& P, std::vector<unsigned char>& bytes);
 // tc_plan.cpp: edge corrections of the FP32 line operators (host, FP64);
 // fills P.f32 and the floats to upload (empty if not eligible)
 void build_f32(Plan& P, std::vector<float>& out);

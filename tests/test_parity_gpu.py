@@ -296,8 +296,8 @@ def test_config5_full_size_split_bf16():
     _lib.uw_plan_profile(plan._h, True)
     assert rel(run_fwd(plan, x, F32_SPLIT_BF16), dense.forward2d(x, R, q, p, VMP, plan.J0, omega, G=G)) < 1e-5
     assert rel(run_adj(plan, y, F32_SPLIT_BF16), dense.adjoint2d(y, R, q, p, VMP, plan.J0, omega, G=G)) < 1e-5
-    # all four line passes of the benchmark workload run on the tensor cores
-    assert sum(n.endswith("_tc") for n in _kernel_names(plan)) == 4
+    # all four line passes of the benchmark workload run on the tcgen05 kernels
+    assert sum(n.endswith("_umma") for n in _kernel_names(plan)) == 4
 
 
 def test_config5_full_size_fp32():
