@@ -12,36 +12,42 @@
 //          bytes (8 BF16 values) apart, exactly the shift of the window per
 //          block, so a descriptor over the plain coefficient array is W
 //          itself.  B1 = the last synthesis level (Sec. 3.2), T (Sec. 4.1)
-//          and the Walsh-Hadamard stages of bits 0-4 (Sec. 3.1) of one block.
-//   GEMM2  D2[b'][r] = sum_b H128[b'][b] D1[b][r]      (M = 128, N = 32, K = 128)
-//          the Walsh-Hadamard stages of bits 5-11 as an exact +-1 contraction
-//   D2 is the natural-order line: stored, or gathered at the sampled
-//   sequency indices (P_Omega, Sec. 1.1).
-// Adjoint (Sec. 4.2): stage or scatter the natural line, GEMM2 (H128 is
-// symmetric), then Z[b][j] = sum_r D2[b][r] B1[r][j] (M = 128, N = 48, K = 32)
-// and lo[i], hi[i] = the sum of the three entries of Z whose window position
-// is i.
+//          and the Walsh-Hadamard stages of bits 0-4 (Sec. 3.1) of one block:
+//          all of the line's multiply-adds.
+//   bits 5-11 of the Walsh-Hadamard transform (the +-1 stages across blocks)
+//          as two radix-16 / radix-8 passes in shared memory, then the line is
+//          stored, or gathered at the sampled sequency indices (P_Omega,
+//          Sec. 1.1).
+// Adjoint (Sec. 4.2): stage or scatter the natural line, the same two passes
+// (H is symmetric), then Z[b][j] = sum_r D[b][r] B1[r][j] (M = 128, N = 48,
+// K = 32) on the tensor cores and lo[i], hi[i] = the sum of the three entries
+// of Z whose window position is i.
 //
-// Precision: every FP32 operand is split into three BF16 parts
-// (x = x1 + x2 + x3 + O(2^-24 |x|)); B1 likewise on the host.  GEMM1 and the
-// adjoint's third product keep the six part products of order <= 2; the
-// Walsh matrix is exact in BF16, so GEMM2 takes the three data parts.  The
-// products are exact in FP32 and accumulate in FP32: as accurate as the FP32
+// Why the +-1 stages are not a tensor-core contraction here: an MMA of
+// M = 128, K = 16 costs about 50 cycles for any N <= 64 (measured on GB300),
+// a line offers N = 32, and the contraction over 128 blocks would need the
+// line's 4096 values in three BF16 parts (24 KB of shared memory per line in
+// flight).  Folded into GEMM1 the stages of bits 0-4 cost nothing extra.
+//
+// Precision: every FP32 operand of an MMA is split into three BF16 parts
+// (x = x1 + x2 + x3 + O(2^-24 |x|)); B1 likewise on the host, and the six part
+// products of order <= 2 are kept.  The products are exact in FP32 and
+// accumulate in FP32, and the +-1 passes run in FP32: as accurate as the FP32
 // CUDA-core kernels.
 //
 // VMP boundaries: the windows read zero beyond the coefficient range; the
 // exact operator differs from that by a host-built correction that reads the
 // p lo and p hi coefficients at an end and reaches only the first / last KB
-// blocks (added to D1 before GEMM2; the adjoint adds its transpose).
-// Periodic plans wrap the windows instead (halo copies), which is exact.
+// blocks (added to D1; the adjoint adds its transpose).  Periodic plans wrap
+// the windows instead (halo copies), which is exact.
 //
-// Organisation: one persistent CTA per SM with two warpgroups; each
+// Organisation: one persistent CTA per SM with several warpgroups; each
 // warpgroup runs its own sequence of lines (its own buffers, tensor-memory
-// columns and mbarriers) so that one group's CUDA-core work overlaps the
-// other's tensor-core work.  One thread per group issues its MMAs.  Every
-// wait is bounded: when one gives up, the group records it in the plan's
-// error word, drains its copies and MMAs in flight (again bounded), and
-// leaves; the tensor memory is freed before the CTA exits.
+// columns and mbarriers), so that the groups' CUDA-core work overlaps the
+// tensor cores and each other's MMA latency.  One thread per group issues
+// its MMAs.  Every wait is bounded: when one gives up, the group records it
+// in the plan's error word, drains its copies and MMAs in flight (again
+// bounded), and leaves; the tensor memory is freed before the CTA exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,38 +66,34 @@ constexpr int NB = 128;            // blocks per line
 constexpr int NL = 4096;           // samples per line
 constexpr int ML = 2048;           // coefficients per line
 constexpr int N0 = 1024;           // lo (and hi) coefficients per line
-constexpr int WG = 2;              // warpgroups per CTA
-constexpr int NTH = 128 * WG;
+constexpr int GF = 4;              // warpgroups per CTA, forward
+constexpr int GA = 3;              // warpgroups per CTA, adjoint
 
-// shared memory (bytes); operand regions 1024-byte aligned
+// shared memory (bytes)
 constexpr int HANK_LEN = 1056;                       // bf16 per window array: e in [-8, 1048)
 constexpr int HANK_BYTES = HANK_LEN * 2;             // 2112
-constexpr int OFF_H = 0;                             // H128, K-major: 32768
-constexpr int OFF_B1 = 32768;                        // 3 x 3072 (forward: B1, adjoint: B1^T)
-constexpr int OFF_G = 32768 + 9216;                  // per-group regions
+constexpr int OFF_B1 = 0;                            // 3 x 3072 (forward: B1, adjoint: B1^T)
+constexpr int OFF_G = 9216;                          // per-group regions
+constexpr int LINE_FLOATS = 4608;                    // a padded FP32 line: element k at opad(k)
 // forward group region
-constexpr int F_STAGE = 0;                           // 2 x 8192 FP32 input lines
-constexpr int F_HANK = 16384;                        // 6 x 2112 (L1 H1 L2 H2 L3 H3)
-constexpr int F_B2 = F_HANK + 6 * HANK_BYTES;        // 3 x 8192 (Y parts, MN-major) = 29056
-constexpr int F_OUT = F_B2 + 3 * 8192;               // FP32 line, 36 floats per 32: 4608 x 4 = 18432
-constexpr int POS_LEN = 4112;                        // uint16 positions per buffer (a row plus alignment)
-constexpr int F_POS = F_OUT + 18432;                 // 2 x POS_LEN uint16
-constexpr int F_CORR = F_POS + 2 * POS_LEN * 2;      // up to 512 floats
+constexpr int F_STAGE = 0;                           // 8192: the FP32 input line
+constexpr int F_HANK = 8192;                         // 6 x 2112 (L1 H1 L2 H2 L3 H3)
+constexpr int F_LINE = F_HANK + 6 * HANK_BYTES;      // padded FP32 line
+constexpr int F_CORR = F_LINE + LINE_FLOATS * 4;     // up to 512 floats
 constexpr int F_BYTES = (F_CORR + 2048 + 1023) / 1024 * 1024;
-constexpr int F_SMEM = OFF_G + WG * F_BYTES + 1024;  // + barriers
-static_assert(F_B2 % 16 == 0 && F_OUT % 16 == 0 && F_POS % 16 == 0, "alignment");
+constexpr int F_SMEM = OFF_G + GF * F_BYTES + 1024;  // + barriers
+static_assert(F_LINE % 16 == 0 && F_CORR % 16 == 0, "alignment");
 // adjoint group region
-constexpr int A_STAGE = 0;                           // 2 x (4096 + 4) FP32: natural line or packed samples
+constexpr int A_STAGE = 0;                           // (4096 + 4) FP32: natural line or packed samples
 constexpr int A_STAGE_LEN = 4100;
-constexpr int A_SV = 2 * A_STAGE_LEN * 4;            // scatter target: the natural line (4096 FP32)
-constexpr int A_POS = A_SV + NL * 4;                 // 2 x POS_LEN uint16
-constexpr int A_OPS = A_POS + 2 * POS_LEN * 2;       // 3 x 8192: V parts (GEMM2 B), then Ybar parts (GEMM3 A)
+constexpr int A_LINE = A_STAGE_LEN * 4;              // padded FP32 line
+constexpr int A_OPS = A_LINE + LINE_FLOATS * 4;      // 3 x 8192: the A operand parts of GEMM3
 constexpr int A_EDGE = A_OPS + 3 * 8192;             // warp-boundary rows of Z: 4 warps x 2 x 16 floats
-constexpr int A_YE = A_EDGE + 4 * 2 * 16 * 4;        // Ybar rows of the edge blocks: up to 2 x 4 x 32 floats
+constexpr int A_YE = A_EDGE + 4 * 2 * 16 * 4;        // rows of the edge blocks: up to 2 x 4 x 32 floats
 constexpr int A_CO = A_YE + 256 * 4;                 // corrections of the 4p edge outputs
 constexpr int A_BYTES = (A_CO + 64 * 4 + 1023) / 1024 * 1024;
-constexpr int A_SMEM = OFF_G + WG * A_BYTES + 1024;
-static_assert(A_SV % 16 == 0 && A_POS % 16 == 0 && A_OPS % 16 == 0 && A_EDGE % 16 == 0, "alignment");
+constexpr int A_SMEM = OFF_G + GA * A_BYTES + 1024;
+static_assert(A_LINE % 16 == 0 && A_OPS % 16 == 0 && A_EDGE % 16 == 0, "alignment");
 
 __host__ __device__ constexpr int opad(int k) { return k + 4 * (k >> 5); }
 
@@ -111,25 +113,6 @@ struct GroupBars {
   uint32_t status;        // broadcast of the polling thread's result
   uint32_t pad;
 };
-
-// H128 (natural-order Walsh-Hadamard, +-1) in the K-major canonical layout:
-// element (row, k) at ((row / 8) 16 + k / 8) 64 + (row % 8) 8 + k % 8
-__device__ __forceinline__ void fill_h128(uint16_t* sH, int tid, int nth) {
-  for (int e = tid; e < 128 * 128 / 8; e += nth) {     // 16-byte chunks
-    const int core = e >> 3, rr = e & 7;
-    const int rg = core >> 4, kg = core & 15;
-    const int row = 8 * rg + rr;
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k0 = 8 * kg + 2 * q;
-      const uint16_t a = (__popc(row & k0) & 1) ? 0xBF80 : 0x3F80;
-      const uint16_t b = (__popc(row & (k0 + 1)) & 1) ? 0xBF80 : 0x3F80;
-      w[q] = (uint32_t)a | ((uint32_t)b << 16);
-    }
-    *reinterpret_cast<uint4*>(sH + 8 * e) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
 
 // one thread of the group polls; the group learns the result at the barrier
 __device__ __forceinline__ bool group_wait(GroupBars& gb, uint64_t* bar, uint32_t parity, unsigned spin, int wtid,
@@ -153,42 +136,101 @@ __device__ __forceinline__ void sample_range(const LineIO& io, int mrow, int& r0
 }
 
 
+
+// Walsh-Hadamard transform of R values in registers, natural order: the first
+// stage pairs neighbours, the later ones combine aligned pairs with the
+// packed FP32x2 add.
+template <int R>
+__device__ __forceinline__ void wht_regs(float (&a)[R]) {
+#pragma unroll
+  for (int i = 0; i < R; i += 2) {
+    const float x = a[i], y = a[i + 1];
+    a[i] = x + y;
+    a[i + 1] = x - y;
+  }
+  const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+  for (int h = 2; h < R; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < R; i += 2)
+      if (!(i & h)) {
+        const float2 x = make_float2(a[i], a[i + 1]), y = make_float2(a[i + h], a[i + h + 1]);
+        const float2 s = __fadd2_rn(x, y), d = __ffma2_rn(y, m1, x);
+        a[i] = s.x;
+        a[i + 1] = s.y;
+        a[i + h] = d.x;
+        a[i + h + 1] = d.y;
+      }
+}
+
+// The Walsh-Hadamard stages of bits 5-8 of k = 32 b + r (b = 16 bh + bl):
+// pencils of fixed (r, bh) over bl.  Thread t takes r = t % 32 and
+// bh = t / 32, t / 32 + 4; for a fixed step the 32 lanes read 32 consecutive
+// words (conflict-free in the padded layout and in the plain one).
+// src: element k at src[k] (plain = true) or src[opad(k)]; dst padded.
+template <bool PLAIN_SRC>
+__device__ __forceinline__ void pass_bits5_8(const float* src, float* dst, int wtid) {
+  const int r = wtid & 31;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int bh = (wtid >> 5) + 4 * h;
+    float a[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int k = 32 * (16 * bh + i) + r;
+      a[i] = src[PLAIN_SRC ? k : opad(k)];
+    }
+    wht_regs<16>(a);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dst[opad(32 * (16 * bh + i) + r)] = a[i];
+  }
+}
+// bits 9-11: pencils of fixed (r, bl) over bh, in place on a padded line
+__device__ __forceinline__ void pass_bits9_11(float* line, int wtid) {
+  const int r = wtid & 31;
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const int bl = (wtid >> 5) + 4 * h;
+    float a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = line[opad(32 * (bl + 16 * i) + r)];
+    wht_regs<8>(a);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) line[opad(32 * (bl + 16 * i) + r)] = a[i];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // forward: lines of M = 2048 coefficients (lo | hi) -> N = 4096 outputs
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NTH, 1) k_umma_fwd(const float* __restrict__ in, float* __restrict__ out, Args a,
-                                                     LineIO io, int total) {
+__global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restrict__ in, float* __restrict__ out, Args a,
+                                                          LineIO io, int total) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, g = tid >> 7, wtid = tid & 127, wq = wtid >> 5;
   const int barid = 1 + g;
-  uint16_t* sH = reinterpret_cast<uint16_t*>(sm + OFF_H);
   uint16_t* sB1 = reinterpret_cast<uint16_t*>(sm + OFF_B1);
   unsigned char* G = sm + OFF_G + g * F_BYTES;
   float* stage = reinterpret_cast<float*>(G + F_STAGE);
   uint16_t* hank = reinterpret_cast<uint16_t*>(G + F_HANK);
-  unsigned char* b2 = G + F_B2;
-  float* sout = reinterpret_cast<float*>(G + F_OUT);
-  uint16_t* spos = reinterpret_cast<uint16_t*>(G + F_POS);
+  float* line_s = reinterpret_cast<float*>(G + F_LINE);
   float* scorr = reinterpret_cast<float*>(G + F_CORR);
-  GroupBars* bars = reinterpret_cast<GroupBars*>(sm + OFF_G + WG * F_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + WG);
+  GroupBars* bars = reinterpret_cast<GroupBars*>(sm + OFF_G + GF * F_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + GF);
   GroupBars& gb = bars[g];
   const bool gather = io.mode == 1;
 
-  if (tid < 32) tmem_alloc(tslot, 256);
+  if (tid < 32) tmem_alloc(tslot, 128);
   if (tid == 0) {
-    for (int k = 0; k < WG; ++k) {
+    for (int k = 0; k < GF; ++k) {
       mbar_init(&bars[k].load[0], 1);
-      mbar_init(&bars[k].load[1], 1);
       mbar_init(&bars[k].mma, 1);
     }
     mbar_fence_init();
   }
-  fill_h128(sH, tid, NTH);
-  for (int e = tid; e < 3 * 1536 / 8; e += NTH)
+  for (int e = tid; e < 3 * 1536 / 8; e += 128 * GF)
     reinterpret_cast<uint4*>(sB1)[e] = __ldg(reinterpret_cast<const uint4*>(a.ops) + e);
   // window halos start zero (VMP: zero padding); periodic halos are rewritten per line
-  for (int e = tid; e < WG * 6 * HANK_BYTES / 16; e += NTH) {
+  for (int e = tid; e < GF * 6 * HANK_BYTES / 16; e += 128 * GF) {
     const int k = e / (6 * HANK_BYTES / 16), r = e % (6 * HANK_BYTES / 16);
     reinterpret_cast<uint4*>(sm + OFF_G + k * F_BYTES + F_HANK)[r] = make_uint4(0, 0, 0, 0);
   }
@@ -196,60 +238,42 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_fwd(const float* __restrict__ i
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tbase = *tslot + 128u * g;
-  const uint32_t D1 = tbase, D2 = tbase + 32;
+  const uint32_t D1 = *tslot + 32u * g;
   const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
 
   pdl_trigger();
   pdl_wait();
 
-  const int step = WG * gridDim.x;
-  int line = WG * blockIdx.x + g;
+  const int step = GF * gridDim.x;
+  int line = GF * blockIdx.x + g;
   bool ok = true;
-  uint32_t pend = 0, mma_pend = 0, ph_load[2] = {0, 0}, ph_mma = 0;
+  uint32_t load_pend = 0, mma_pend = 0, ph_load = 0, ph_mma = 0;
 
-  // one thread of the group: the input line and (gather) its sample positions
-  auto issue = [&](int ln, int bi) {
+  // one thread of the group: the input line, once the previous one is consumed
+  auto issue = [&](int ln) {
     const LineAt at = line_at(ln, io.lines);
     const int drow = io.seq_rows ? seqrow(at.l, a.L) : at.l;
-    const float* src = in + at.b * io.in_batch + (int64_t)drow * io.in_stride;
-    uint32_t pbytes = 0;
-    int p0 = 0;
-    if (gather) {
-      int r0, r1;
-      sample_range(io, at.l, r0, r1);
-      p0 = r0 & ~7;
-      pbytes = (uint32_t)(2 * (((r1 + 7) & ~7) - p0));
-    }
     fence_async_smem();
-    mbar_expect_tx(&gb.load[bi], ML * 4 + pbytes);
-    bulk_g2s(stage + bi * ML, src, ML * 4, &gb.load[bi]);
-    if (pbytes) bulk_g2s(spos + bi * POS_LEN, io.pos + p0, pbytes, &gb.load[bi]);
+    mbar_expect_tx(&gb.load[0], ML * 4);
+    bulk_g2s(stage, in + at.b * io.in_batch + (int64_t)drow * io.in_stride, ML * 4, &gb.load[0]);
   };
 
   if (line < total) {
-    if (wtid == 0) issue(line, 0);
-    pend = 1;
+    if (wtid == 0) issue(line);
+    load_pend = 1;
   }
-  for (int it = 0; line < total; line += step, ++it) {
-    const int buf = it & 1;
-    const int nxt = line + step;
-    if (nxt < total) {
-      if (wtid == 0) issue(nxt, buf ^ 1);
-      pend |= 1u << (buf ^ 1);
-    }
-    if (!group_wait(gb, &gb.load[buf], ph_load[buf], a.spin, wtid, barid)) {
+  for (; line < total; line += step) {
+    if (!group_wait(gb, &gb.load[0], ph_load, a.spin, wtid, barid)) {
       ok = false;
       break;
     }
-    ph_load[buf] ^= 1;
-    pend &= ~(1u << buf);
+    ph_load ^= 1;
+    load_pend = 0;
     const LineAt at = line_at(line, io.lines);
-    const float* xin = stage + buf * ML;
 
     // split lo[8t, 8t + 8) and hi[8t, 8t + 8) into three BF16 parts
     {
-      const float4* s4 = reinterpret_cast<const float4*>(xin);
+      const float4* s4 = reinterpret_cast<const float4*>(stage);
       const float4 l0 = s4[2 * wtid], l1 = s4[2 * wtid + 1];
       const float4 h0 = s4[N0 / 4 + 2 * wtid], h1 = s4[N0 / 4 + 2 * wtid + 1];
       uint32_t pl[3][4], ph[3][4];
@@ -289,15 +313,17 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_fwd(const float* __restrict__ i
         float acc = 0.f;
         for (int e = 0; e < 2 * a.p; ++e) {
           const int half = e >= a.p, ee = e - half * a.p;
-          acc = fmaf(__ldg(C + e), xin[half * N0 + (side ? N0 - a.p + ee : ee)], acc);
+          acc = fmaf(__ldg(C + e), stage[half * N0 + (side ? N0 - a.p + ee : ee)], acc);
         }
         scorr[c] = acc;
       }
     }
     fence_async_smem();
     bar_sync(barid, 128);
-    // GEMM1: the six part products, three K steps each
     if (wtid == 0) {
+      // the staged line is consumed: the next one may land
+      if (line + step < total) issue(line + step);
+      // GEMM1: the six part products, three K steps each
       tc_fence_after();
       const uint32_t id1 = idesc_bf16(128, 32, 0, 0);
       const uint32_t hk = smem_u32(hank), bb = smem_u32(sB1);
@@ -314,6 +340,7 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_fwd(const float* __restrict__ i
         }
       umma_commit(&gb.mma);
     }
+    if (line + step < total) load_pend = 1;
     mma_pend = 1;
     if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
       ok = false;
@@ -335,181 +362,127 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_fwd(const float* __restrict__ i
           for (int r = 0; r < 32; ++r) y[r] += scorr[32 * row + r];
         }
       }
-      // MN-major B operand of GEMM2: element (r, b) of part P at
-      // P 8192 + (r % 8) 2 + (r / 8) 128 + (b % 8) 16 + (b / 8) 512
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t w[3][4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) split3x2(y[8 * q + 2 * e], y[8 * q + 2 * e + 1], w[0][e], w[1][e], w[2][e]);
-#pragma unroll
-        for (int P = 0; P < 3; ++P)
-          *reinterpret_cast<uint4*>(b2 + P * 8192 + q * 128 + (b & 7) * 16 + (b >> 3) * 512) =
-              make_uint4(w[P][0], w[P][1], w[P][2], w[P][3]);
-      }
-    }
-    tc_fence_before();
-    fence_async_smem();
-    bar_sync(barid, 128);
-    // GEMM2: H128 against the three parts, eight K steps each
-    if (wtid == 0) {
-      tc_fence_after();
-      const uint32_t id2 = idesc_bf16(128, 32, 0, 1);
-      const uint32_t hs = smem_u32(sH), bq = smem_u32(b2);
-#pragma unroll
-      for (int P = 0; P < 3; ++P)
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-          umma_bf16(D2, sdesc(hs + 256 * s, 128, 2048), sdesc(bq + P * 8192 + 1024 * s, 512, 128), id2,
-                    (P | s) != 0);
-      umma_commit(&gb.mma);
-    }
-    mma_pend = 1;
-    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
-      ok = false;
-      break;
-    }
-    ph_mma ^= 1;
-    mma_pend = 0;
-    tc_fence_after();
-    {
-      float o[32];
-      tmem_ld32(D2 + lane_off, o);
-      float* row = sout + opad(32 * wtid);
+      float* rowp = line_s + opad(32 * b);
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        *reinterpret_cast<float4*>(row + 4 * q) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        *reinterpret_cast<float4*>(rowp + 4 * q) = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
     }
     tc_fence_before();
+    bar_sync(barid, 128);
+    pass_bits5_8<false>(line_s, line_s, wtid);
+    bar_sync(barid, 128);
+    pass_bits9_11(line_s, wtid);
     bar_sync(barid, 128);
     if (gather) {
       int r0, r1;
       sample_range(io, at.l, r0, r1);
-      const uint16_t* ps = spos + buf * POS_LEN + (r0 & 7);
+      const uint16_t* ps = io.pos + r0;
       float* y = out + at.b * io.m + r0;
-      for (int j = wtid; j < r1 - r0; j += 128) y[j] = sout[opad(ps[j])];
+      for (int j = wtid; j < r1 - r0; j += 128) y[j] = line_s[opad(__ldg(ps + j))];
     } else {
       float* dst = out + at.b * io.out_batch + (int64_t)at.l * io.out_stride;
 #pragma unroll 4
       for (int c = wtid; c < NL / 4; c += 128)
-        *reinterpret_cast<float4*>(dst + 4 * c) = *reinterpret_cast<const float4*>(sout + opad(4 * c));
+        *reinterpret_cast<float4*>(dst + 4 * c) = *reinterpret_cast<const float4*>(line_s + opad(4 * c));
     }
-    // the staging buffers of this line are read: the next copies may land
-    bar_sync(barid, 128);
+    // (the next line's first wait is a group barrier: these reads finish
+    // before the line buffer is written again)
   }
   if (!ok && wtid == 0) atomicExch(a.err, 1u);
   // drain what is still in flight (bounded), then free the tensor memory
   if (wtid == 0) {
-    for (int bi = 0; bi < 2; ++bi)
-      if (pend & (1u << bi)) mbar_wait(&gb.load[bi], ph_load[bi], 1u << 22);
+    if (load_pend) mbar_wait(&gb.load[0], ph_load, 1u << 22);
     if (mma_pend) mbar_wait(&gb.mma, ph_mma, 1u << 22);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (tid < 32) tmem_dealloc(*tslot, 256);
+  if (tid < 32) tmem_dealloc(*tslot, 128);
 }
 
 // ---------------------------------------------------------------------------
 // adjoint: natural lines of N = 4096 (mode 0) or the sampled entries of a
 // sequency row (mode 1) -> M = 2048 coefficients (lo | hi)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NTH, 1) k_umma_adj(const float* __restrict__ in, float* __restrict__ out, Args a,
-                                                     LineIO io, int total) {
+__global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restrict__ in, float* __restrict__ out, Args a,
+                                                          LineIO io, int total) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, g = tid >> 7, wtid = tid & 127, wq = wtid >> 5, lane = tid & 31;
   const int barid = 1 + g;
-  uint16_t* sH = reinterpret_cast<uint16_t*>(sm + OFF_H);
   uint16_t* sBt = reinterpret_cast<uint16_t*>(sm + OFF_B1);
   unsigned char* G = sm + OFF_G + g * A_BYTES;
   float* stage = reinterpret_cast<float*>(G + A_STAGE);
-  float* sv = reinterpret_cast<float*>(G + A_SV);
-  uint16_t* spos = reinterpret_cast<uint16_t*>(G + A_POS);
+  float* line_s = reinterpret_cast<float*>(G + A_LINE);
   unsigned char* ops = G + A_OPS;
   float* sedge = reinterpret_cast<float*>(G + A_EDGE);
   float* sye = reinterpret_cast<float*>(G + A_YE);
   float* sco = reinterpret_cast<float*>(G + A_CO);
-  GroupBars* bars = reinterpret_cast<GroupBars*>(sm + OFF_G + WG * A_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + WG);
+  GroupBars* bars = reinterpret_cast<GroupBars*>(sm + OFF_G + GA * A_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + GA);
   GroupBars& gb = bars[g];
   const bool scat = io.mode == 1;
 
   if (tid < 32) tmem_alloc(tslot, 256);
   if (tid == 0) {
-    for (int k = 0; k < WG; ++k) {
+    for (int k = 0; k < GA; ++k) {
       mbar_init(&bars[k].load[0], 1);
-      mbar_init(&bars[k].load[1], 1);
       mbar_init(&bars[k].mma, 1);
     }
     mbar_fence_init();
   }
-  fill_h128(sH, tid, NTH);
-  for (int e = tid; e < 3 * 1536 / 8; e += NTH)
+  for (int e = tid; e < 3 * 1536 / 8; e += 128 * GA)
     reinterpret_cast<uint4*>(sBt)[e] = __ldg(reinterpret_cast<const uint4*>(a.ops) + 3 * 1536 / 8 + e);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tbase = *tslot + 128u * g;
-  const uint32_t D2 = tbase, D3 = tbase + 32;
+  const uint32_t D3 = *tslot + 64u * g;
   const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
 
   pdl_trigger();
   pdl_wait();
 
-  const int step = WG * gridDim.x;
-  int line = WG * blockIdx.x + g;
+  const int step = GA * gridDim.x;
+  int line = GA * blockIdx.x + g;
   bool ok = true;
-  uint32_t pend = 0, mma_pend = 0, ph_load[2] = {0, 0}, ph_mma = 0;
+  uint32_t load_pend = 0, mma_pend = 0, ph_load = 0, ph_mma = 0;
 
   // one thread of the group: the natural line, or the aligned span of the
-  // row's packed samples (whole 16-byte units inside [r0, r1)) and positions
-  auto issue = [&](int ln, int bi) {
+  // row's packed samples (whole 16-byte units inside [r0, r1)); sample k of
+  // the row lands at stage[k - (r0 & ~3)], 16-byte aligned
+  auto issue = [&](int ln) {
     const LineAt at = line_at(ln, io.lines);
     fence_async_smem();
     if (!scat) {
-      const float* src = in + at.b * io.in_batch + (int64_t)at.l * io.in_stride;
-      mbar_expect_tx(&gb.load[bi], NL * 4);
-      bulk_g2s(stage + bi * A_STAGE_LEN, src, NL * 4, &gb.load[bi]);
+      mbar_expect_tx(&gb.load[0], NL * 4);
+      bulk_g2s(stage, in + at.b * io.in_batch + (int64_t)at.l * io.in_stride, NL * 4, &gb.load[0]);
       return;
     }
     int r0, r1;
     sample_range(io, at.l, r0, r1);
-    const int64_t base = at.b * io.m;             // a multiple of 4: checked on the host
-    const int a0 = (r0 + 3) & ~3, a1 = r1 & ~3;   // aligned interior span of the samples
+    const int a0 = (r0 + 3) & ~3, a1 = r1 & ~3;
     const uint32_t ybytes = a1 > a0 ? (uint32_t)(4 * (a1 - a0)) : 0u;
-    const int p0 = r0 & ~7;
-    const uint32_t pbytes = (uint32_t)(2 * (((r1 + 7) & ~7) - p0));
-    // sample k of the row sits at stage[k - (r0 & ~3)]: the aligned span lands 16-byte aligned
-    // (an arrival with nothing to copy completes the phase at once)
-    mbar_expect_tx(&gb.load[bi], ybytes + pbytes);
-    if (ybytes) bulk_g2s(stage + bi * A_STAGE_LEN + (a0 - (r0 & ~3)), in + base + a0, ybytes, &gb.load[bi]);
-    if (pbytes) bulk_g2s(spos + bi * POS_LEN, io.pos + p0, pbytes, &gb.load[bi]);
+    // an arrival with nothing to copy completes the phase at once
+    mbar_expect_tx(&gb.load[0], ybytes);
+    if (ybytes) bulk_g2s(stage + (a0 - (r0 & ~3)), in + at.b * io.m + a0, ybytes, &gb.load[0]);
   };
 
   if (line < total) {
-    if (wtid == 0) issue(line, 0);
-    pend = 1;
+    if (wtid == 0) issue(line);
+    load_pend = 1;
   }
-  for (int it = 0; line < total; line += step, ++it) {
-    const int buf = it & 1;
-    const int nxt = line + step;
-    if (nxt < total) {
-      if (wtid == 0) issue(nxt, buf ^ 1);
-      pend |= 1u << (buf ^ 1);
-    }
-    if (!group_wait(gb, &gb.load[buf], ph_load[buf], a.spin, wtid, barid)) {
+  for (; line < total; line += step) {
+    if (!group_wait(gb, &gb.load[0], ph_load, a.spin, wtid, barid)) {
       ok = false;
       break;
     }
-    ph_load[buf] ^= 1;
-    pend &= ~(1u << buf);
+    ph_load ^= 1;
+    load_pend = 0;
     const LineAt at = line_at(line, io.lines);
-    const float* v = stage + buf * A_STAGE_LEN;
     if (scat) {
       int r0, r1;
       sample_range(io, at.l, r0, r1);
-      float* st = stage + buf * A_STAGE_LEN + (r0 & 3);   // relative sample j at st[j]
+      float* st = stage + (r0 & 3);   // relative sample j at st[j]
       const float* ysrc = in + at.b * io.m;
       // the unaligned head and tail of the samples with plain loads
       const int a0 = (r0 + 3) & ~3, a1 = r1 & ~3;
@@ -520,56 +493,32 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_adj(const float* __restrict__ i
         if (wtid < r1 - r0) st[wtid] = __ldg(ysrc + r0 + wtid);
       }
 #pragma unroll
-      for (int i = 0; i < NL / 4 / 128; ++i)
-        reinterpret_cast<float4*>(sv)[wtid + 128 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < LINE_FLOATS / 4 / 128; ++i)
+        reinterpret_cast<float4*>(line_s)[wtid + 128 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
       bar_sync(barid, 128);
-      const uint16_t* ps = spos + buf * POS_LEN + (r0 & 7);
-      for (int j = wtid; j < r1 - r0; j += 128) sv[ps[j]] = st[j];
+      const uint16_t* ps = io.pos + r0;
+      for (int j = wtid; j < r1 - r0; j += 128) line_s[opad(__ldg(ps + j))] = st[j];
       bar_sync(barid, 128);
-      v = sv;
+      if (wtid == 0 && line + step < total) issue(line + step);
+      pass_bits5_8<false>(line_s, line_s, wtid);
+    } else {
+      pass_bits5_8<true>(stage, line_s, wtid);
+      bar_sync(barid, 128);
+      if (wtid == 0 && line + step < total) issue(line + step);
     }
-    // V parts as the MN-major B operand of GEMM2: chunk c = (b, q) holds
-    // v[32 b + 8 q, + 8) at P 8192 + q 128 + (b % 8) 16 + (b / 8) 512
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int c = wtid + 128 * i, b = c >> 2, q = c & 3;
-      const float4 u0 = reinterpret_cast<const float4*>(v)[2 * c];
-      const float4 u1 = reinterpret_cast<const float4*>(v)[2 * c + 1];
-      uint32_t w[3][4];
-      split3x2(u0.x, u0.y, w[0][0], w[1][0], w[2][0]);
-      split3x2(u0.z, u0.w, w[0][1], w[1][1], w[2][1]);
-      split3x2(u1.x, u1.y, w[0][2], w[1][2], w[2][2]);
-      split3x2(u1.z, u1.w, w[0][3], w[1][3], w[2][3]);
-#pragma unroll
-      for (int P = 0; P < 3; ++P)
-        *reinterpret_cast<uint4*>(ops + P * 8192 + q * 128 + (b & 7) * 16 + (b >> 3) * 512) =
-            make_uint4(w[P][0], w[P][1], w[P][2], w[P][3]);
-    }
-    fence_async_smem();
+    if (line + step < total) load_pend = 1;
     bar_sync(barid, 128);
-    if (wtid == 0) {
-      tc_fence_after();
-      const uint32_t id2 = idesc_bf16(128, 32, 0, 1);
-      const uint32_t hs = smem_u32(sH), bq = smem_u32(ops);
-#pragma unroll
-      for (int P = 0; P < 3; ++P)
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-          umma_bf16(D2, sdesc(hs + 256 * s, 128, 2048), sdesc(bq + P * 8192 + 1024 * s, 512, 128), id2,
-                    (P | s) != 0);
-      umma_commit(&gb.mma);
-    }
-    mma_pend = 1;
-    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
-      ok = false;
-      break;
-    }
-    ph_mma ^= 1;
-    mma_pend = 0;
-    tc_fence_after();
+    pass_bits9_11(line_s, wtid);
+    bar_sync(barid, 128);
     {
+      // row b: D[b][r] = the line after bits 5-11, k = 32 b + r
       float y[32];
-      tmem_ld32(D2 + lane_off, y);
+      const float* rowp = line_s + opad(32 * wtid);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 u = *reinterpret_cast<const float4*>(rowp + 4 * q);
+        y[4 * q] = u.x; y[4 * q + 1] = u.y; y[4 * q + 2] = u.z; y[4 * q + 3] = u.w;
+      }
       const int b = wtid;
       if (a.KB) {   // keep the edge blocks' rows for the corrections
         int row = -1;
@@ -594,7 +543,6 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_adj(const float* __restrict__ i
               make_uint4(w[P][0], w[P][1], w[P][2], w[P][3]);
       }
     }
-    tc_fence_before();
     fence_async_smem();
     bar_sync(barid, 128);
     if (wtid == 0) {
@@ -614,6 +562,7 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_adj(const float* __restrict__ i
           }
       umma_commit(&gb.mma);
     }
+    mma_pend = 1;
     // VMP: corrections of the 4p edge outputs from the edge blocks' rows
     if (a.KB && wtid < 4 * a.p) {
       const int side = wtid >= 2 * a.p, c = wtid - side * 2 * a.p;
@@ -623,7 +572,6 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_adj(const float* __restrict__ i
       for (int k = 0; k < a.KB * 32; ++k) acc = fmaf(__ldg(C + (size_t)k * 2 * a.p), ye[k], acc);
       sco[wtid] = acc;
     }
-    mma_pend = 1;
     if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
       ok = false;
       break;
@@ -711,13 +659,10 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_adj(const float* __restrict__ i
       *reinterpret_cast<float4*>(dst + N0 + 8 * c) = make_float4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<float4*>(dst + N0 + 8 * c + 4) = make_float4(hi[4], hi[5], hi[6], hi[7]);
     }
-    // shared buffers of this line are read: the next copies may land
-    bar_sync(barid, 128);
   }
   if (!ok && wtid == 0) atomicExch(a.err, 1u);
   if (wtid == 0) {
-    for (int bi = 0; bi < 2; ++bi)
-      if (pend & (1u << bi)) mbar_wait(&gb.load[bi], ph_load[bi], 1u << 22);
+    if (load_pend) mbar_wait(&gb.load[0], ph_load, 1u << 22);
     if (mma_pend) mbar_wait(&gb.mma, ph_mma, 1u << 22);
   }
   tc_fence_before();
@@ -726,16 +671,16 @@ __global__ void __launch_bounds__(NTH, 1) k_umma_adj(const float* __restrict__ i
   if (tid < 32) tmem_dealloc(*tslot, 256);
 }
 
+}  // namespace ummak
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-static unsigned spin_limit() {
+static unsigned umma_spin_limit() {
   const char* e = getenv("UW_TC_SPIN_LIMIT");
   if (e && *e) return (unsigned)strtoul(e, nullptr, 10);
   return 1u << 22;
 }
-
-}  // namespace ummak
 
 bool umma_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd, int total) {
   if (!P.umma.ok || !P.d_umma || io.jlev != P.R - 1) return false;
@@ -769,17 +714,18 @@ cudaError_t umma_launch(bool fwd, const Plan& P, const float* in, float* out, co
   while ((1 << L) < P.N) ++L;
   a.L = L;
   a.err = (unsigned*)P.d_sync + 2;
-  a.spin = spin_limit();
+  a.spin = umma_spin_limit();
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(nsm, (total + WG - 1) / WG));
   if (fwd) {
+    const int grid = std::max(1, std::min(nsm, (total + GF - 1) / GF));
     cudaFuncSetAttribute((const void*)k_umma_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
-    return launch_pdl(k_umma_fwd, dim3(grid), dim3(NTH), (size_t)F_SMEM, s, in, out, a, io, total);
+    return launch_pdl(k_umma_fwd, dim3(grid), dim3(128 * GF), (size_t)F_SMEM, s, in, out, a, io, total);
   }
+  const int grid = std::max(1, std::min(nsm, (total + GA - 1) / GA));
   cudaFuncSetAttribute((const void*)k_umma_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, A_SMEM);
-  return launch_pdl(k_umma_adj, dim3(grid), dim3(NTH), (size_t)A_SMEM, s, in, out, a, io, total);
+  return launch_pdl(k_umma_adj, dim3(grid), dim3(128 * GA), (size_t)A_SMEM, s, in, out, a, io, total);
 }
 
 }  // namespace uw
