@@ -79,7 +79,7 @@ constexpr int LINE_FLOATS = 4608;                    // a padded FP32 line: elem
 constexpr int F_STAGE = 0;                           // 8192: the FP32 input line
 constexpr int F_HANK = 8192;                         // 6 x 2112 (L1 H1 L2 H2 L3 H3)
 constexpr int F_LINE = F_HANK + 6 * HANK_BYTES;      // padded FP32 line
-constexpr int F_CORR = F_LINE + LINE_FLOATS * 4;     // up to 512 floats
+constexpr int F_CORR = F_LINE + LINE_FLOATS * 4;     // 2 x up to 256 floats (two lines in flight)
 constexpr int F_BYTES = (F_CORR + 2048 + 1023) / 1024 * 1024;
 constexpr int F_SMEM = OFF_G + GF * F_BYTES + 1024;  // + barriers
 static_assert(F_LINE % 16 == 0 && F_CORR % 16 == 0, "alignment");
@@ -90,8 +90,8 @@ constexpr int A_LINE = A_STAGE_LEN * 4;              // padded FP32 line
 constexpr int A_OPS = A_LINE + LINE_FLOATS * 4;      // 3 x 8192: the A operand parts of GEMM3
 constexpr int A_EDGE = A_OPS + 3 * 8192;             // warp-boundary rows of Z: 4 warps x 2 x 16 floats
 constexpr int A_YE = A_EDGE + 4 * 2 * 16 * 4;        // rows of the edge blocks: up to 2 x 4 x 32 floats
-constexpr int A_CO = A_YE + 256 * 4;                 // corrections of the 4p edge outputs
-constexpr int A_BYTES = (A_CO + 64 * 4 + 1023) / 1024 * 1024;
+constexpr int A_CO = A_YE + 256 * 4;                 // corrections of the 4p edge outputs, two lines
+constexpr int A_BYTES = (A_CO + 2 * 64 * 4 + 1023) / 1024 * 1024;
 constexpr int A_SMEM = OFF_G + GA * A_BYTES + 1024;
 static_assert(A_LINE % 16 == 0 && A_OPS % 16 == 0 && A_EDGE % 16 == 0, "alignment");
 
@@ -201,8 +201,45 @@ __device__ __forceinline__ void pass_bits9_11(float* line, int wtid) {
 }
 
 // ---------------------------------------------------------------------------
-// forward: lines of M = 2048 coefficients (lo | hi) -> N = 4096 outputs
+// forward: lines of M = 2048 coefficients (lo | hi) -> N = 4096 outputs.
+// Each group works on two lines at a time: it splits line i and issues its
+// GEMM1, then, while those MMAs run, finishes line i - 1 from the other
+// tensor-memory accumulator (Walsh stages of bits 5-11, store or gather).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void fwd_split(const float* stage, uint16_t* hank, int wtid, bool per) {
+  const float4* s4 = reinterpret_cast<const float4*>(stage);
+  const float4 l0 = s4[2 * wtid], l1 = s4[2 * wtid + 1];
+  const float4 h0 = s4[N0 / 4 + 2 * wtid], h1 = s4[N0 / 4 + 2 * wtid + 1];
+  uint32_t pl[3][4], ph[3][4];
+  split3x2(l0.x, l0.y, pl[0][0], pl[1][0], pl[2][0]);
+  split3x2(l0.z, l0.w, pl[0][1], pl[1][1], pl[2][1]);
+  split3x2(l1.x, l1.y, pl[0][2], pl[1][2], pl[2][2]);
+  split3x2(l1.z, l1.w, pl[0][3], pl[1][3], pl[2][3]);
+  split3x2(h0.x, h0.y, ph[0][0], ph[1][0], ph[2][0]);
+  split3x2(h0.z, h0.w, ph[0][1], ph[1][1], ph[2][1]);
+  split3x2(h1.x, h1.y, ph[0][2], ph[1][2], ph[2][2]);
+  split3x2(h1.z, h1.w, ph[0][3], ph[1][3], ph[2][3]);
+#pragma unroll
+  for (int P = 0; P < 3; ++P) {
+    uint16_t* L = hank + (2 * P) * HANK_LEN;
+    uint16_t* H = L + HANK_LEN;
+    const uint4 vl = make_uint4(pl[P][0], pl[P][1], pl[P][2], pl[P][3]);
+    const uint4 vh = make_uint4(ph[P][0], ph[P][1], ph[P][2], ph[P][3]);
+    *reinterpret_cast<uint4*>(L + 8 + 8 * wtid) = vl;
+    *reinterpret_cast<uint4*>(H + 8 + 8 * wtid) = vh;
+    if (per) {   // window positions -8..-1 and 1024..1031 wrap around
+      if (wtid == 0) {
+        *reinterpret_cast<uint4*>(L + 8 + N0) = vl;
+        *reinterpret_cast<uint4*>(H + 8 + N0) = vh;
+      }
+      if (wtid == 127) {
+        *reinterpret_cast<uint4*>(L) = vl;
+        *reinterpret_cast<uint4*>(H) = vh;
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restrict__ in, float* __restrict__ out, Args a,
                                                           LineIO io, int total) {
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -213,13 +250,13 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
   float* stage = reinterpret_cast<float*>(G + F_STAGE);
   uint16_t* hank = reinterpret_cast<uint16_t*>(G + F_HANK);
   float* line_s = reinterpret_cast<float*>(G + F_LINE);
-  float* scorr = reinterpret_cast<float*>(G + F_CORR);
+  float* scorr = reinterpret_cast<float*>(G + F_CORR);   // [2][256]
   GroupBars* bars = reinterpret_cast<GroupBars*>(sm + OFF_G + GF * F_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + GF);
   GroupBars& gb = bars[g];
   const bool gather = io.mode == 1;
 
-  if (tid < 32) tmem_alloc(tslot, 128);
+  if (tid < 32) tmem_alloc(tslot, 256);
   if (tid == 0) {
     for (int k = 0; k < GF; ++k) {
       mbar_init(&bars[k].load[0], 1);
@@ -238,7 +275,7 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t D1 = *tslot + 32u * g;
+  const uint32_t D1 = *tslot + 64u * g;          // two accumulators of 32 columns
   const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
 
   pdl_trigger();
@@ -249,144 +286,138 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
   bool ok = true;
   uint32_t load_pend = 0, mma_pend = 0, ph_load = 0, ph_mma = 0;
 
-  // one thread of the group: the input line, once the previous one is consumed
-  auto issue = [&](int ln) {
+  auto issue = [&](int ln) {   // one thread: the input line, once the previous one is consumed
     const LineAt at = line_at(ln, io.lines);
     const int drow = io.seq_rows ? seqrow(at.l, a.L) : at.l;
     fence_async_smem();
     mbar_expect_tx(&gb.load[0], ML * 4);
     bulk_g2s(stage, in + at.b * io.in_batch + (int64_t)drow * io.in_stride, ML * 4, &gb.load[0]);
   };
+  auto wait_mma = [&]() -> bool {
+    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) return false;
+    ph_mma ^= 1;
+    mma_pend = 0;
+    return true;
+  };
 
   if (line < total) {
     if (wtid == 0) issue(line);
     load_pend = 1;
   }
-  for (; line < total; line += step) {
-    if (!group_wait(gb, &gb.load[0], ph_load, a.spin, wtid, barid)) {
-      ok = false;
-      break;
-    }
-    ph_load ^= 1;
-    load_pend = 0;
-    const LineAt at = line_at(line, io.lines);
-
-    // split lo[8t, 8t + 8) and hi[8t, 8t + 8) into three BF16 parts
-    {
-      const float4* s4 = reinterpret_cast<const float4*>(stage);
-      const float4 l0 = s4[2 * wtid], l1 = s4[2 * wtid + 1];
-      const float4 h0 = s4[N0 / 4 + 2 * wtid], h1 = s4[N0 / 4 + 2 * wtid + 1];
-      uint32_t pl[3][4], ph[3][4];
-      split3x2(l0.x, l0.y, pl[0][0], pl[1][0], pl[2][0]);
-      split3x2(l0.z, l0.w, pl[0][1], pl[1][1], pl[2][1]);
-      split3x2(l1.x, l1.y, pl[0][2], pl[1][2], pl[2][2]);
-      split3x2(l1.z, l1.w, pl[0][3], pl[1][3], pl[2][3]);
-      split3x2(h0.x, h0.y, ph[0][0], ph[1][0], ph[2][0]);
-      split3x2(h0.z, h0.w, ph[0][1], ph[1][1], ph[2][1]);
-      split3x2(h1.x, h1.y, ph[0][2], ph[1][2], ph[2][2]);
-      split3x2(h1.z, h1.w, ph[0][3], ph[1][3], ph[2][3]);
-#pragma unroll
-      for (int P = 0; P < 3; ++P) {
-        uint16_t* L = hank + (2 * P) * HANK_LEN;
-        uint16_t* H = L + HANK_LEN;
-        const uint4 vl = make_uint4(pl[P][0], pl[P][1], pl[P][2], pl[P][3]);
-        const uint4 vh = make_uint4(ph[P][0], ph[P][1], ph[P][2], ph[P][3]);
-        *reinterpret_cast<uint4*>(L + 8 + 8 * wtid) = vl;
-        *reinterpret_cast<uint4*>(H + 8 + 8 * wtid) = vh;
-        if (a.per) {   // window positions -8..-1 and 1024..1031 wrap around
-          if (wtid == 0) {
-            *reinterpret_cast<uint4*>(L + 8 + N0) = vl;
-            *reinterpret_cast<uint4*>(H + 8 + N0) = vh;
-          }
-          if (wtid == 127) {
-            *reinterpret_cast<uint4*>(L) = vl;
-            *reinterpret_cast<uint4*>(H) = vh;
-          }
-        }
+  int prev = -1;                                   // the line whose GEMM1 is in flight
+  for (int it = 0;; ++it) {
+    const bool have = line < total;
+    if (have) {
+      if (!group_wait(gb, &gb.load[0], ph_load, a.spin, wtid, barid)) {
+        ok = false;
+        break;
       }
-    }
-    // VMP: the corrections of the first / last KB blocks, one value per thread
-    if (a.KB) {
-      for (int c = wtid; c < 2 * a.KB * 32; c += 128) {
-        const int side = c >= a.KB * 32;
-        const float* C = a.corr + (size_t)c * 2 * a.p;
-        float acc = 0.f;
-        for (int e = 0; e < 2 * a.p; ++e) {
-          const int half = e >= a.p, ee = e - half * a.p;
-          acc = fmaf(__ldg(C + e), stage[half * N0 + (side ? N0 - a.p + ee : ee)], acc);
-        }
-        scorr[c] = acc;
+      ph_load ^= 1;
+      load_pend = 0;
+      // the previous GEMM1 has finished reading the windows
+      if (mma_pend && !wait_mma()) {
+        ok = false;
+        break;
       }
-    }
-    fence_async_smem();
-    bar_sync(barid, 128);
-    if (wtid == 0) {
-      // the staged line is consumed: the next one may land
-      if (line + step < total) issue(line + step);
-      // GEMM1: the six part products, three K steps each
-      tc_fence_after();
-      const uint32_t id1 = idesc_bf16(128, 32, 0, 0);
-      const uint32_t hk = smem_u32(hank), bb = smem_u32(sB1);
-      uint32_t acc = 0;
-#pragma unroll
-      for (int dp = 0; dp < 3; ++dp)
-#pragma unroll
-        for (int op = 0; op + dp < 3; ++op) {
-          const uint32_t L = hk + 2 * dp * HANK_BYTES, H = L + HANK_BYTES, Bp = bb + op * 3072;
-          umma_bf16(D1, sdesc(L, 16, 128), sdesc(Bp, 128, 768), id1, acc);
-          umma_bf16(D1, sdesc(L + 32, HANK_BYTES - 32, 128), sdesc(Bp + 256, 128, 768), id1, 1);
-          umma_bf16(D1, sdesc(H + 16, 16, 128), sdesc(Bp + 512, 128, 768), id1, 1);
-          acc = 1;
-        }
-      umma_commit(&gb.mma);
-    }
-    if (line + step < total) load_pend = 1;
-    mma_pend = 1;
-    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
-      ok = false;
-      break;
-    }
-    ph_mma ^= 1;
-    mma_pend = 0;
-    tc_fence_after();
-    {
-      float y[32];
-      tmem_ld32(D1 + lane_off, y);
-      const int b = wtid;
+      fwd_split(stage, hank, wtid, a.per);
+      // VMP: the corrections of the first / last KB blocks, one value per thread
       if (a.KB) {
-        int row = -1;
-        if (b < a.KB) row = b;
-        else if (b >= NB - a.KB) row = a.KB + b - (NB - a.KB);
-        if (row >= 0) {
-#pragma unroll
-          for (int r = 0; r < 32; ++r) y[r] += scorr[32 * row + r];
+        float* sc = scorr + 256 * (it & 1);
+        for (int c = wtid; c < 2 * a.KB * 32; c += 128) {
+          const int side = c >= a.KB * 32;
+          const float* C = a.corr + (size_t)c * 2 * a.p;
+          float acc = 0.f;
+          for (int e = 0; e < 2 * a.p; ++e) {
+            const int half = e >= a.p, ee = e - half * a.p;
+            acc = fmaf(__ldg(C + e), stage[half * N0 + (side ? N0 - a.p + ee : ee)], acc);
+          }
+          sc[c] = acc;
         }
       }
-      float* rowp = line_s + opad(32 * b);
+      fence_async_smem();
+      bar_sync(barid, 128);
+      if (wtid == 0) {
+        if (line + step < total) issue(line + step);
+        tc_fence_after();
+        const uint32_t d = D1 + 32u * (it & 1);
+        const uint32_t id1 = idesc_bf16(128, 32, 0, 0);
+        const uint32_t hk = smem_u32(hank), bb = smem_u32(sB1);
+        uint32_t acc = 0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        *reinterpret_cast<float4*>(rowp + 4 * q) = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+        for (int dp = 0; dp < 3; ++dp)
+#pragma unroll
+          for (int op = 0; op + dp < 3; ++op) {
+            const uint32_t L = hk + 2 * dp * HANK_BYTES, H = L + HANK_BYTES, Bp = bb + op * 3072;
+            umma_bf16(d, sdesc(L, 16, 128), sdesc(Bp, 128, 768), id1, acc);
+            umma_bf16(d, sdesc(L + 32, HANK_BYTES - 32, 128), sdesc(Bp + 256, 128, 768), id1, 1);
+            umma_bf16(d, sdesc(H + 16, 16, 128), sdesc(Bp + 512, 128, 768), id1, 1);
+            acc = 1;
+          }
+        umma_commit(&gb.mma);
+      }
+      if (line + step < total) load_pend = 1;
+      mma_pend = 1;
     }
-    tc_fence_before();
-    bar_sync(barid, 128);
-    pass_bits5_8<false>(line_s, line_s, wtid);
-    bar_sync(barid, 128);
-    pass_bits9_11(line_s, wtid);
-    bar_sync(barid, 128);
-    if (gather) {
-      int r0, r1;
-      sample_range(io, at.l, r0, r1);
-      const uint16_t* ps = io.pos + r0;
-      float* y = out + at.b * io.m + r0;
-      for (int j = wtid; j < r1 - r0; j += 128) y[j] = line_s[opad(__ldg(ps + j))];
-    } else {
-      float* dst = out + at.b * io.out_batch + (int64_t)at.l * io.out_stride;
+    // the previous line: its accumulator is complete once the GEMM1 issued
+    // after it started (the waits are in order), or once its own commit is seen
+    if (prev >= 0) {
+      if (!have && mma_pend && !wait_mma()) {
+        ok = false;
+        break;
+      }
+      const int ps_slot = (it - 1) & 1;
+      const LineAt at = line_at(prev, io.lines);
+      int r0 = 0, r1 = 0;
+      uint16_t pp[4] = {0, 0, 0, 0};
+      if (gather) {   // positions of the first samples, loaded while the passes run
+        sample_range(io, at.l, r0, r1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (wtid + 128 * k < r1 - r0) pp[k] = __ldg(io.pos + r0 + wtid + 128 * k);
+      }
+      tc_fence_after();
+      {
+        float y[32];
+        tmem_ld32(D1 + 32u * ps_slot + lane_off, y);
+        const int b = wtid;
+        if (a.KB) {
+          int row = -1;
+          if (b < a.KB) row = b;
+          else if (b >= NB - a.KB) row = a.KB + b - (NB - a.KB);
+          if (row >= 0) {
+            const float* sc = scorr + 256 * ps_slot + 32 * row;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) y[r] += sc[r];
+          }
+        }
+        float* rowp = line_s + opad(32 * b);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(rowp + 4 * q) = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+      }
+      tc_fence_before();
+      bar_sync(barid, 128);
+      pass_bits5_8<false>(line_s, line_s, wtid);
+      bar_sync(barid, 128);
+      pass_bits9_11(line_s, wtid);
+      bar_sync(barid, 128);
+      if (gather) {
+        float* y = out + at.b * io.m + r0;
+        const int cnt = r1 - r0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (wtid + 128 * k < cnt) y[wtid + 128 * k] = line_s[opad(pp[k])];
+        for (int j = wtid + 512; j < cnt; j += 128) y[j] = line_s[opad(__ldg(io.pos + r0 + j))];
+      } else {
+        float* dst = out + at.b * io.out_batch + (int64_t)at.l * io.out_stride;
 #pragma unroll 4
-      for (int c = wtid; c < NL / 4; c += 128)
-        *reinterpret_cast<float4*>(dst + 4 * c) = *reinterpret_cast<const float4*>(line_s + opad(4 * c));
+        for (int c = wtid; c < NL / 4; c += 128)
+          *reinterpret_cast<float4*>(dst + 4 * c) = *reinterpret_cast<const float4*>(line_s + opad(4 * c));
+      }
     }
-    // (the next line's first wait is a group barrier: these reads finish
-    // before the line buffer is written again)
+    if (!have) break;
+    prev = line;
+    line += step;
   }
   if (!ok && wtid == 0) atomicExch(a.err, 1u);
   // drain what is still in flight (bounded), then free the tensor memory
@@ -397,12 +428,14 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (tid < 32) tmem_dealloc(*tslot, 128);
+  if (tid < 32) tmem_dealloc(*tslot, 256);
 }
 
 // ---------------------------------------------------------------------------
 // adjoint: natural lines of N = 4096 (mode 0) or the sampled entries of a
-// sequency row (mode 1) -> M = 2048 coefficients (lo | hi)
+// sequency row (mode 1) -> M = 2048 coefficients (lo | hi).  Each group
+// prepares line i (scatter, Walsh stages of bits 5-11, split) and issues its
+// MMAs, then finishes line i - 1 from the other accumulator.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restrict__ in, float* __restrict__ out, Args a,
                                                           LineIO io, int total) {
@@ -416,13 +449,13 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
   unsigned char* ops = G + A_OPS;
   float* sedge = reinterpret_cast<float*>(G + A_EDGE);
   float* sye = reinterpret_cast<float*>(G + A_YE);
-  float* sco = reinterpret_cast<float*>(G + A_CO);
+  float* sco = reinterpret_cast<float*>(G + A_CO);   // [2][64]
   GroupBars* bars = reinterpret_cast<GroupBars*>(sm + OFF_G + GA * A_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + GA);
   GroupBars& gb = bars[g];
   const bool scat = io.mode == 1;
 
-  if (tid < 32) tmem_alloc(tslot, 256);
+  if (tid < 32) tmem_alloc(tslot, 512);
   if (tid == 0) {
     for (int k = 0; k < GA; ++k) {
       mbar_init(&bars[k].load[0], 1);
@@ -436,7 +469,7 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t D3 = *tslot + 64u * g;
+  const uint32_t D3 = *tslot + 128u * g;         // two accumulators of 64 columns
   const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
 
   pdl_trigger();
@@ -466,128 +499,154 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
     mbar_expect_tx(&gb.load[0], ybytes);
     if (ybytes) bulk_g2s(stage + (a0 - (r0 & ~3)), in + at.b * io.m + a0, ybytes, &gb.load[0]);
   };
+  auto wait_mma = [&]() -> bool {
+    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) return false;
+    ph_mma ^= 1;
+    mma_pend = 0;
+    return true;
+  };
 
   if (line < total) {
     if (wtid == 0) issue(line);
     load_pend = 1;
   }
-  for (; line < total; line += step) {
-    if (!group_wait(gb, &gb.load[0], ph_load, a.spin, wtid, barid)) {
-      ok = false;
-      break;
-    }
-    ph_load ^= 1;
-    load_pend = 0;
-    const LineAt at = line_at(line, io.lines);
-    if (scat) {
-      int r0, r1;
-      sample_range(io, at.l, r0, r1);
-      float* st = stage + (r0 & 3);   // relative sample j at st[j]
-      const float* ysrc = in + at.b * io.m;
-      // the unaligned head and tail of the samples with plain loads
-      const int a0 = (r0 + 3) & ~3, a1 = r1 & ~3;
-      if (a1 > a0) {
-        if (wtid < a0 - r0) st[wtid] = __ldg(ysrc + r0 + wtid);
-        if (wtid < r1 - a1) st[a1 - r0 + wtid] = __ldg(ysrc + a1 + wtid);
+  int prev = -1;
+  for (int it = 0;; ++it) {
+    const bool have = line < total;
+    if (have) {
+      const LineAt at = line_at(line, io.lines);
+      int r0 = 0, r1 = 0;
+      uint16_t pp[4] = {0, 0, 0, 0};
+      if (scat) {   // positions of the first samples, loaded while the copy lands
+        sample_range(io, at.l, r0, r1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (wtid + 128 * k < r1 - r0) pp[k] = __ldg(io.pos + r0 + wtid + 128 * k);
+      }
+      if (!group_wait(gb, &gb.load[0], ph_load, a.spin, wtid, barid)) {
+        ok = false;
+        break;
+      }
+      ph_load ^= 1;
+      load_pend = 0;
+      if (scat) {
+        float* st = stage + (r0 & 3);   // relative sample j at st[j]
+        const float* ysrc = in + at.b * io.m;
+        // the unaligned head and tail of the samples with plain loads
+        const int a0 = (r0 + 3) & ~3, a1 = r1 & ~3;
+        if (a1 > a0) {
+          if (wtid < a0 - r0) st[wtid] = __ldg(ysrc + r0 + wtid);
+          if (wtid < r1 - a1) st[a1 - r0 + wtid] = __ldg(ysrc + a1 + wtid);
+        } else {
+          if (wtid < r1 - r0) st[wtid] = __ldg(ysrc + r0 + wtid);
+        }
+#pragma unroll
+        for (int i = 0; i < LINE_FLOATS / 4 / 128; ++i)
+          reinterpret_cast<float4*>(line_s)[wtid + 128 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        bar_sync(barid, 128);
+        const int cnt = r1 - r0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (wtid + 128 * k < cnt) line_s[opad(pp[k])] = st[wtid + 128 * k];
+        for (int j = wtid + 512; j < cnt; j += 128) line_s[opad(__ldg(io.pos + r0 + j))] = st[j];
+        bar_sync(barid, 128);
+        if (wtid == 0 && line + step < total) issue(line + step);
+        pass_bits5_8<false>(line_s, line_s, wtid);
       } else {
-        if (wtid < r1 - r0) st[wtid] = __ldg(ysrc + r0 + wtid);
+        pass_bits5_8<true>(stage, line_s, wtid);
+        bar_sync(barid, 128);
+        if (wtid == 0 && line + step < total) issue(line + step);
       }
-#pragma unroll
-      for (int i = 0; i < LINE_FLOATS / 4 / 128; ++i)
-        reinterpret_cast<float4*>(line_s)[wtid + 128 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (line + step < total) load_pend = 1;
       bar_sync(barid, 128);
-      const uint16_t* ps = io.pos + r0;
-      for (int j = wtid; j < r1 - r0; j += 128) line_s[opad(__ldg(ps + j))] = st[j];
+      pass_bits9_11(line_s, wtid);
       bar_sync(barid, 128);
-      if (wtid == 0 && line + step < total) issue(line + step);
-      pass_bits5_8<false>(line_s, line_s, wtid);
-    } else {
-      pass_bits5_8<true>(stage, line_s, wtid);
-      bar_sync(barid, 128);
-      if (wtid == 0 && line + step < total) issue(line + step);
-    }
-    if (line + step < total) load_pend = 1;
-    bar_sync(barid, 128);
-    pass_bits9_11(line_s, wtid);
-    bar_sync(barid, 128);
-    {
-      // row b: D[b][r] = the line after bits 5-11, k = 32 b + r
       float y[32];
-      const float* rowp = line_s + opad(32 * wtid);
+      {
+        const float* rowp = line_s + opad(32 * wtid);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 u = *reinterpret_cast<const float4*>(rowp + 4 * q);
-        y[4 * q] = u.x; y[4 * q + 1] = u.y; y[4 * q + 2] = u.z; y[4 * q + 3] = u.w;
-      }
-      const int b = wtid;
-      if (a.KB) {   // keep the edge blocks' rows for the corrections
-        int row = -1;
-        if (b < a.KB) row = b;
-        else if (b >= NB - a.KB) row = a.KB + b - (NB - a.KB);
-        if (row >= 0) {
-#pragma unroll
-          for (int r = 0; r < 32; r += 4)
-            *reinterpret_cast<float4*>(sye + 32 * row + r) = make_float4(y[r], y[r + 1], y[r + 2], y[r + 3]);
+        for (int q = 0; q < 8; ++q) {
+          const float4 u = *reinterpret_cast<const float4*>(rowp + 4 * q);
+          y[4 * q] = u.x; y[4 * q + 1] = u.y; y[4 * q + 2] = u.z; y[4 * q + 3] = u.w;
         }
       }
-      // K-major A operand of GEMM3: element (b, r) of part P at
-      // P 8192 + (b % 8) 16 + (b / 8) 512 + (r % 8) 2 + (r / 8) 128
+      // the previous line's MMAs have finished reading the operand
+      if (mma_pend && !wait_mma()) {
+        ok = false;
+        break;
+      }
+      {
+        const int b = wtid;
+        if (a.KB) {   // keep the edge blocks' rows for the corrections
+          int row = -1;
+          if (b < a.KB) row = b;
+          else if (b >= NB - a.KB) row = a.KB + b - (NB - a.KB);
+          if (row >= 0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t w[3][4];
+            for (int r = 0; r < 32; r += 4)
+              *reinterpret_cast<float4*>(sye + 32 * row + r) = make_float4(y[r], y[r + 1], y[r + 2], y[r + 3]);
+          }
+        }
+        // K-major A operand of GEMM3: element (b, r) of part P at
+        // P 8192 + (b % 8) 16 + (b / 8) 512 + (r % 8) 2 + (r / 8) 128
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split3x2(y[8 * q + 2 * e], y[8 * q + 2 * e + 1], w[0][e], w[1][e], w[2][e]);
+        for (int q = 0; q < 4; ++q) {
+          uint32_t w[3][4];
 #pragma unroll
-        for (int P = 0; P < 3; ++P)
-          *reinterpret_cast<uint4*>(ops + P * 8192 + q * 128 + (b & 7) * 16 + (b >> 3) * 512) =
-              make_uint4(w[P][0], w[P][1], w[P][2], w[P][3]);
+          for (int e = 0; e < 4; ++e) split3x2(y[8 * q + 2 * e], y[8 * q + 2 * e + 1], w[0][e], w[1][e], w[2][e]);
+#pragma unroll
+          for (int P = 0; P < 3; ++P)
+            *reinterpret_cast<uint4*>(ops + P * 8192 + q * 128 + (b & 7) * 16 + (b >> 3) * 512) =
+                make_uint4(w[P][0], w[P][1], w[P][2], w[P][3]);
+        }
+      }
+      fence_async_smem();
+      bar_sync(barid, 128);
+      if (wtid == 0) {
+        tc_fence_after();
+        const uint32_t d = D3 + 64u * (it & 1);
+        const uint32_t id3 = idesc_bf16(128, 48, 0, 0);
+        const uint32_t aq = smem_u32(ops), bb = smem_u32(sBt);
+        uint32_t acc = 0;
+#pragma unroll
+        for (int dp = 0; dp < 3; ++dp)
+#pragma unroll
+          for (int op = 0; op + dp < 3; ++op)
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+              umma_bf16(d, sdesc(aq + dp * 8192 + 256 * s, 128, 512), sdesc(bb + op * 3072 + 256 * s, 128, 512), id3,
+                        acc);
+              acc = 1;
+            }
+        umma_commit(&gb.mma);
+      }
+      mma_pend = 1;
+      // VMP: corrections of this line's 4p edge outputs from its edge blocks' rows
+      if (a.KB && wtid < 4 * a.p) {
+        const int side = wtid >= 2 * a.p, c = wtid - side * 2 * a.p;
+        const float* C = a.corr + (size_t)side * a.KB * 32 * 2 * a.p + c;
+        const float* ye = sye + side * a.KB * 32;
+        float acc = 0.f;
+        for (int k = 0; k < a.KB * 32; ++k) acc = fmaf(__ldg(C + (size_t)k * 2 * a.p), ye[k], acc);
+        sco[64 * (it & 1) + wtid] = acc;
       }
     }
-    fence_async_smem();
-    bar_sync(barid, 128);
-    if (wtid == 0) {
+    if (prev >= 0) {
+      if (!have && mma_pend && !wait_mma()) {
+        ok = false;
+        break;
+      }
+      const int ps_slot = (it - 1) & 1;
+      const LineAt at = line_at(prev, io.lines);
       tc_fence_after();
-      const uint32_t id3 = idesc_bf16(128, 48, 0, 0);
-      const uint32_t aq = smem_u32(ops), bb = smem_u32(sBt);
-      uint32_t acc = 0;
-#pragma unroll
-      for (int dp = 0; dp < 3; ++dp)
-#pragma unroll
-        for (int op = 0; op + dp < 3; ++op)
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            umma_bf16(D3, sdesc(aq + dp * 8192 + 256 * s, 128, 512), sdesc(bb + op * 3072 + 256 * s, 128, 512), id3,
-                      acc);
-            acc = 1;
-          }
-      umma_commit(&gb.mma);
-    }
-    mma_pend = 1;
-    // VMP: corrections of the 4p edge outputs from the edge blocks' rows
-    if (a.KB && wtid < 4 * a.p) {
-      const int side = wtid >= 2 * a.p, c = wtid - side * 2 * a.p;
-      const float* C = a.corr + (size_t)side * a.KB * 32 * 2 * a.p + c;
-      const float* ye = sye + side * a.KB * 32;
-      float acc = 0.f;
-      for (int k = 0; k < a.KB * 32; ++k) acc = fmaf(__ldg(C + (size_t)k * 2 * a.p), ye[k], acc);
-      sco[wtid] = acc;
-    }
-    if (!group_wait(gb, &gb.mma, ph_mma, a.spin, wtid, barid)) {
-      ok = false;
-      break;
-    }
-    ph_mma ^= 1;
-    mma_pend = 0;
-    tc_fence_after();
-    {
       // Z row b: 48 values; lo[8c + e] = Z[c+1][e] + Z[c][8+e] + Z[c-1][16+e],
       // hi[8c + e] = Z[c+1][24+e] + Z[c][32+e] + Z[c-1][40+e]
       float z[48];
       {
         float t32[32];
         float t16[16];
-        tmem_ld32(D3 + lane_off, t32);
-        tmem_ld16(D3 + lane_off + 32, t16);
+        tmem_ld32(D3 + 64u * ps_slot + lane_off, t32);
+        tmem_ld16(D3 + 64u * ps_slot + lane_off + 32, t16);
 #pragma unroll
         for (int i = 0; i < 32; ++i) z[i] = t32[i];
 #pragma unroll
@@ -633,12 +692,13 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
         hi[e] = z[32 + e] + (has_next ? nh : 0.f) + (has_prev ? ph : 0.f);
       }
       if (a.KB) {
+        const float* co = sco + 64 * ps_slot;
         if (c == 0) {
 #pragma unroll
           for (int e = 0; e < 8; ++e)
             if (e < a.p) {
-              lo[e] += sco[e];
-              hi[e] += sco[a.p + e];
+              lo[e] += co[e];
+              hi[e] += co[a.p + e];
             }
         }
         if (c == NB - 1) {
@@ -646,8 +706,8 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
           for (int e = 0; e < 8; ++e) {
             const int k = e - (8 - a.p);   // lo[n0 - p + k] sits at e = 8 - p + k
             if (k >= 0) {
-              lo[e] += sco[2 * a.p + k];
-              hi[e] += sco[3 * a.p + k];
+              lo[e] += co[2 * a.p + k];
+              hi[e] += co[3 * a.p + k];
             }
           }
         }
@@ -659,6 +719,9 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
       *reinterpret_cast<float4*>(dst + N0 + 8 * c) = make_float4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<float4*>(dst + N0 + 8 * c + 4) = make_float4(hi[4], hi[5], hi[6], hi[7]);
     }
+    if (!have) break;
+    prev = line;
+    line += step;
   }
   if (!ok && wtid == 0) atomicExch(a.err, 1u);
   if (wtid == 0) {
@@ -668,7 +731,7 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (tid < 32) tmem_dealloc(*tslot, 256);
+  if (tid < 32) tmem_dealloc(*tslot, 512);
 }
 
 }  // namespace ummak
