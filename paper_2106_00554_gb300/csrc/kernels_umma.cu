@@ -73,7 +73,9 @@ constexpr int GA = 3;              // warpgroups per CTA, adjoint
 constexpr int HANK_LEN = 1056;                       // bf16 per window array: e in [-8, 1048)
 constexpr int HANK_BYTES = HANK_LEN * 2;             // 2112
 constexpr int OFF_B1 = 0;                            // 3 x 3072 (forward: B1, adjoint: B1^T)
-constexpr int OFF_G = 9216;                          // per-group regions
+constexpr int OFF_C = 9216;                          // corrections C'[2][KB*32][2p], KB <= 4, p <= 8
+constexpr int C_MAX = 2 * 4 * 32 * 16;               // floats
+constexpr int OFF_G = OFF_C + C_MAX * 4;             // per-group regions
 constexpr int LINE_FLOATS = 4608;                    // a padded FP32 line: element k at opad(k)
 // forward group region
 constexpr int F_STAGE = 0;                           // 8192: the FP32 input line
@@ -266,6 +268,8 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
   }
   for (int e = tid; e < 3 * 1536 / 8; e += 128 * GF)
     reinterpret_cast<uint4*>(sB1)[e] = __ldg(reinterpret_cast<const uint4*>(a.ops) + e);
+  float* sC = reinterpret_cast<float*>(sm + OFF_C);
+  for (int e = tid; e < 2 * a.KB * 32 * 2 * a.p; e += 128 * GF) sC[e] = __ldg(a.corr + e);
   // window halos start zero (VMP: zero padding); periodic halos are rewritten per line
   for (int e = tid; e < GF * 6 * HANK_BYTES / 16; e += 128 * GF) {
     const int k = e / (6 * HANK_BYTES / 16), r = e % (6 * HANK_BYTES / 16);
@@ -325,13 +329,15 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
         float* sc = scorr + 256 * (it & 1);
         for (int c = wtid; c < 2 * a.KB * 32; c += 128) {
           const int side = c >= a.KB * 32;
-          const float* C = a.corr + (size_t)c * 2 * a.p;
-          float acc = 0.f;
-          for (int e = 0; e < 2 * a.p; ++e) {
-            const int half = e >= a.p, ee = e - half * a.p;
-            acc = fmaf(__ldg(C + e), stage[half * N0 + (side ? N0 - a.p + ee : ee)], acc);
+          const float* C = sC + c * 2 * a.p;
+          const float* xl = stage + (side ? N0 - a.p : 0);
+          float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll 8
+          for (int e = 0; e < a.p; ++e) {
+            acc0 = fmaf(C[e], xl[e], acc0);
+            acc1 = fmaf(C[a.p + e], xl[N0 + e], acc1);
           }
-          sc[c] = acc;
+          sc[c] = acc0 + acc1;
         }
       }
       fence_async_smem();
@@ -465,6 +471,8 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
   }
   for (int e = tid; e < 3 * 1536 / 8; e += 128 * GA)
     reinterpret_cast<uint4*>(sBt)[e] = __ldg(reinterpret_cast<const uint4*>(a.ops) + 3 * 1536 / 8 + e);
+  float* sC = reinterpret_cast<float*>(sm + OFF_C);
+  for (int e = tid; e < 2 * a.KB * 32 * 2 * a.p; e += 128 * GA) sC[e] = __ldg(a.corr + e);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -622,13 +630,26 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
       }
       mma_pend = 1;
       // VMP: corrections of this line's 4p edge outputs from its edge blocks' rows
-      if (a.KB && wtid < 4 * a.p) {
-        const int side = wtid >= 2 * a.p, c = wtid - side * 2 * a.p;
-        const float* C = a.corr + (size_t)side * a.KB * 32 * 2 * a.p + c;
-        const float* ye = sye + side * a.KB * 32;
-        float acc = 0.f;
-        for (int k = 0; k < a.KB * 32; ++k) acc = fmaf(__ldg(C + (size_t)k * 2 * a.p), ye[k], acc);
-        sco[64 * (it & 1) + wtid] = acc;
+      // (8 lanes per output, combined with shuffles; every lane of a warp runs
+      // every round)
+      if (a.KB) {
+        for (int t0 = 0; t0 < 32 * a.p; t0 += 128) {
+          if (t0 + (wtid & ~31) >= 32 * a.p) break;     // warp-uniform: no lane of this warp has a task
+          const int t = t0 + wtid, oc = t >> 3, part = t & 7;
+          const bool act = t < 32 * a.p;
+          float acc = 0.f;
+          if (act) {
+            const int side = oc >= 2 * a.p, c = oc - side * 2 * a.p;
+            const int kp = a.KB * 4;                     // rows per lane
+            const float* C = sC + ((size_t)side * a.KB * 32 + part * kp) * 2 * a.p + c;
+            const float* ye = sye + side * a.KB * 32 + part * kp;
+            for (int k = 0; k < kp; ++k) acc = fmaf(C[k * 2 * a.p], ye[k], acc);
+          }
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+          if (act && part == 0) sco[64 * (it & 1) + oc] = acc;
+        }
       }
     }
     if (prev >= 0) {
