@@ -309,6 +309,10 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
     load_pend = 1;
   }
   int prev = -1;                                   // the line whose GEMM1 is in flight
+  // sample range and first positions of the line in flight, loaded while its
+  // MMAs run (gather)
+  int nr0 = 0, nr1 = 0;
+  uint16_t npp[4] = {0, 0, 0, 0};
   for (int it = 0;; ++it) {
     const bool have = line < total;
     if (have) {
@@ -364,6 +368,17 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
       if (line + step < total) load_pend = 1;
       mma_pend = 1;
     }
+    // this line's sample range and first positions (consumed after the next
+    // line's MMAs are issued)
+    int tr0 = 0, tr1 = 0;
+    uint16_t tpp[4] = {0, 0, 0, 0};
+    if (have && gather) {
+      sample_range(io, line_at(line, io.lines).l, tr0, tr1);
+      if (io.m > 0) {   // clamped to the last sample: no wait on the row's count here
+#pragma unroll
+        for (int k = 0; k < 4; ++k) tpp[k] = __ldg(io.pos + min((int64_t)tr0 + wtid + 128 * k, io.m - 1));
+      }
+    }
     // the previous line: its accumulator is complete once the GEMM1 issued
     // after it started (the waits are in order), or once its own commit is seen
     if (prev >= 0) {
@@ -373,14 +388,7 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
       }
       const int ps_slot = (it - 1) & 1;
       const LineAt at = line_at(prev, io.lines);
-      int r0 = 0, r1 = 0;
-      uint16_t pp[4] = {0, 0, 0, 0};
-      if (gather) {   // positions of the first samples, loaded while the passes run
-        sample_range(io, at.l, r0, r1);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (wtid + 128 * k < r1 - r0) pp[k] = __ldg(io.pos + r0 + wtid + 128 * k);
-      }
+      const int r0 = nr0, r1 = nr1;
       tc_fence_after();
       {
         float y[32];
@@ -412,7 +420,7 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
         const int cnt = r1 - r0;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          if (wtid + 128 * k < cnt) y[wtid + 128 * k] = line_s[opad(pp[k])];
+          if (wtid + 128 * k < cnt) y[wtid + 128 * k] = line_s[opad(npp[k])];
         for (int j = wtid + 512; j < cnt; j += 128) y[j] = line_s[opad(__ldg(io.pos + r0 + j))];
       } else {
         float* dst = out + at.b * io.out_batch + (int64_t)at.l * io.out_stride;
@@ -424,6 +432,10 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
     if (!have) break;
     prev = line;
     line += step;
+    nr0 = tr0;
+    nr1 = tr1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) npp[k] = tpp[k];
   }
   if (!ok && wtid == 0) atomicExch(a.err, 1u);
   // drain what is still in flight (bounded), then free the tensor memory
@@ -518,19 +530,27 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
     if (wtid == 0) issue(line);
     load_pend = 1;
   }
+  // sample range and first positions of a row (scatter), loaded one line ahead
+  auto row_info = [&](int ln, int& r0, int& r1, uint16_t (&pp)[4]) {
+    sample_range(io, line_at(ln, io.lines).l, r0, r1);
+    if (io.m > 0) {   // clamped to the last sample: no wait on the row's count here
+#pragma unroll
+      for (int k = 0; k < 4; ++k) pp[k] = __ldg(io.pos + min((int64_t)r0 + wtid + 128 * k, io.m - 1));
+    }
+  };
+  int nr0 = 0, nr1 = 0;
+  uint16_t npp[4] = {0, 0, 0, 0};
+  if (scat && line < total) row_info(line, nr0, nr1, npp);
   int prev = -1;
   for (int it = 0;; ++it) {
     const bool have = line < total;
     if (have) {
       const LineAt at = line_at(line, io.lines);
-      int r0 = 0, r1 = 0;
-      uint16_t pp[4] = {0, 0, 0, 0};
-      if (scat) {   // positions of the first samples, loaded while the copy lands
-        sample_range(io, at.l, r0, r1);
+      const int r0 = nr0, r1 = nr1;
+      uint16_t pp[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (wtid + 128 * k < r1 - r0) pp[k] = __ldg(io.pos + r0 + wtid + 128 * k);
-      }
+      for (int k = 0; k < 4; ++k) pp[k] = npp[k];
+      if (scat && line + step < total) row_info(line + step, nr0, nr1, npp);
       if (!group_wait(gb, &gb.load[0], ph_load, a.spin, wtid, barid)) {
         ok = false;
         break;
