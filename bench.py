@@ -829,15 +829,19 @@ def run_uneven(args):
     t0 = time.perf_counter()
     group.tune([x.clone() for x in xd], [torch.empty_like(y) for y in yd], prec, reps=2)
     tune_s = time.perf_counter() - t0
+    prm = group.params()
     s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        group.forward(xd, yo, prec, stream=s)
-        group.adjoint(yd, xo, prec, stream=s)
-    s.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=s):
-        group.forward(xd, yo, prec, stream=s)
-        group.adjoint(yd, xo, prec, stream=s)
+
+    def capture():
+        with torch.cuda.stream(s):
+            group.forward(xd, yo, prec, stream=s)
+            group.adjoint(yd, xo, prec, stream=s)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            group.forward(xd, yo, prec, stream=s)
+            group.adjoint(yd, xo, prec, stream=s)
+        return g
 
     def timed(fn, k):
         for _ in range(max(3, args.warmup)):
@@ -852,7 +856,16 @@ def run_uneven(args):
         return e0.elapsed_time(e1) / k
 
     k = max(3, min(args.steps, 50))
+    graph = capture()
     ms_graph = timed(graph.replay, k)
+    assert group.device_status() == 0
+    in_use = prec == F32 and prm["persistent_in_use"] == 1
+    ms_streams = None
+    if in_use:   # the same pair through the forked streams, for comparison
+        os.environ["UW_GROUP_STREAMS"] = "1"
+        g2 = capture()
+        ms_streams = timed(g2.replay, k)
+        del os.environ["UW_GROUP_STREAMS"]
     group.close()
 
     def sequential():
@@ -863,17 +876,31 @@ def run_uneven(args):
 
     ms_seq = timed(sequential, max(3, k // 5))
     n = len(plans)
-    print(json.dumps({
+    # compulsory bytes of one step: x, the packed y, the mask bits and prefix, both directions
+    comp = sum(2 * (4 * pl.coeffs + 4 * pl.m + 8 * pl.N * ((pl.N + 31) // 32)) for pl in plans)
+    peak, peak_kind = peaks()
+    launch = ("one persistent launch per direction (tasks of (instance, phase, items) drained by one grid), "
+              "captured with its counter reset as one CUDA graph" if in_use else
+              f"plan group forked over {nst} streams, captured as one CUDA graph")
+    line = {
         "metric": f"batched uneven 2D U x + U* y pairs/s ({n} instances)", "value": n * 1000.0 / ms_graph,
         "unit": "pairs/s", "higher_is_better": True, "ms_per_step": ms_graph, "steps": k,
         "dtype": "f32" if prec == F32 else "bf16 split (3 parts per operand), f32 accumulate",
         "data": "synthetic",
         "config": {"workload": f"{n} instances: R in 6..9, q in 1..2, p in {{1,2,4,6,8}}, periodic or VMP, "
                                "alpha in [1,2], 10-40% radial multilevel masks, seed 3",
-                   "launch": f"plan group over {nst} streams, tuned, pair captured as one CUDA graph",
+                   "launch": launch, "tuned": {k2: v for k2, v in prm.items()},
                    "setup_s": round(setup_s, 2), "tune_s": round(tune_s, 2)},
+        "roofline": {"bound": "hbm", "achieved": comp / (ms_graph / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": comp / (ms_graph / 1000.0) / 1e9 / peak, "bytes_per_step": comp,
+                     "model": "compulsory: x, packed y, mask bits and row prefix of every instance, both directions",
+                     "peak_kind": peak_kind},
         "sequential": {"value": n * 1000.0 / ms_seq, "unit": "pairs/s", "ms_per_step": ms_seq,
-                       "how": "each plan's forward and adjoint issued in turn on one stream, eager"}}))
+                       "how": "each plan's forward and adjoint issued in turn on one stream, eager"}}
+    if ms_streams is not None:
+        line["forked_streams"] = {"value": n * 1000.0 / ms_streams, "unit": "pairs/s", "ms_per_step": ms_streams,
+                                  "how": f"the same group forked over {nst} streams, captured as one CUDA graph"}
+    print(json.dumps(line))
 
 
 def main():

@@ -244,6 +244,30 @@ int uw_host_wait(const uw_plan* plan);
  *   overwrites) with each line-operator variant the plan supports -- the
  *   specialised kernels that apply to its sizes, or the generic ones -- and
  *   keeps the fastest for that plan.  Synchronises `stream`.
+ * FP32 products of a group of 2D plans (M >= 64, at most 1024 instances) run
+ *   as ONE persistent launch: a grid of CTAs drains a device-side queue of
+ *   tasks (instance, phase, run of items), phase by phase across all
+ *   instances; the phases of one instance are the coarse Mallat levels (rows,
+ *   then columns, one line per item), the transposes (32 x 32 tiles) and the
+ *   two line passes (one line per item).  A task waits, bounded, until the
+ *   previous phase of its instance has counted all its items; a wait that gives
+ *   up is reported by uw_group_device_status.  Other precisions, or groups that
+ *   do not qualify, use the forked streams.
+ * uw_group_tune_cached(g, precision, x, y, reps, cache_path, stream): as
+ *   uw_group_tune, and for FP32 groups on the persistent launch it also times
+ *   the launch's parameters (items per task of the line, coarse-level and
+ *   transpose phases; largest radix of the shared-memory Walsh-Hadamard
+ *   passes, 16 or 8; CTAs per SM) and the forked streams, and keeps the
+ *   fastest.  cache_path (may be NULL): a JSON file of choices keyed by GPU
+ *   name, dimension, the instances' N values and precision; a hit skips the
+ *   timing, a miss adds the entry.
+ * uw_group_params(g, out7): out7[0] 1 if the persistent launch is available,
+ *   out7[1] 1 if it is in use for FP32, out7[2..6] its parameters (items per
+ *   task of line / coarse / transpose phases, radix, CTAs per SM, 0 = as many
+ *   as fit).
+ * uw_group_device_status(g): waits for the device and returns
+ *   UW_ERR_TIMEOUT (and clears it) if a bounded wait of the persistent launch
+ *   gave up since the last query; the affected results are invalid.
  * Errors: UW_ERR_INVALID_ARG (null pointers, n < 1, nstreams out of range,
  *   precision, a plan's own argument checks), UW_ERR_OOM (streams or events),
  *   UW_ERR_CUDA; a failing instance stops the call with its status (the
@@ -255,6 +279,10 @@ uw_group* uw_group_create(uw_plan* const* plans, int n, int nstreams);
 int uw_group_forward(uw_group* group, int precision, const void* const* x, void* const* y, void* stream);
 int uw_group_adjoint(uw_group* group, int precision, const void* const* y, void* const* x, void* stream);
 int uw_group_tune(uw_group* group, int precision, void* const* x, void* const* y, int reps, void* stream);
+int uw_group_tune_cached(uw_group* group, int precision, void* const* x, void* const* y, int reps,
+                         const char* cache_path, void* stream);
+int uw_group_params(const uw_group* group, int* out7);
+int uw_group_device_status(uw_group* group);
 void uw_group_destroy(uw_group* group);
 
 /*

@@ -168,10 +168,26 @@ class PlanGroup:
         _lib.uw_group_adjoint(self._g, precision, [y.data_ptr() for y in ys], [x.data_ptr() for x in xs],
                               _stream_ptr(stream))
 
-    def tune(self, xs, ys, precision, reps=3, stream=None):
-        """Overwrites xs and ys (each pair maps x -> y -> x)."""
-        _lib.uw_group_tune(self._g, precision, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys], reps,
-                           _stream_ptr(stream))
+    def tune(self, xs, ys, precision, reps=3, stream=None, cache=None):
+        """Overwrites xs and ys (each pair maps x -> y -> x).  For FP32 groups
+        on the persistent launch, also picks its parameters and the faster of
+        the persistent launch and the forked streams; `cache`: JSON file of
+        choices (read first, written after a miss)."""
+        _lib.uw_group_tune_cached(self._g, precision, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys], reps,
+                                  cache, _stream_ptr(stream))
+
+    def params(self):
+        """{'persistent_available', 'persistent_in_use', 'lines_per_task',
+        'cols_per_task', 'tiles_per_task', 'radix', 'ctas_per_sm'}"""
+        v = _lib.uw_group_params(self._g)
+        keys = ("persistent_available", "persistent_in_use", "lines_per_task", "cols_per_task", "tiles_per_task",
+                "radix", "ctas_per_sm")
+        return dict(zip(keys, v))
+
+    def device_status(self):
+        """UW_OK, or UW_ERR_TIMEOUT if a bounded wait of the persistent launch
+        gave up since the last query (synchronises the device)."""
+        return _lib.uw_group_device_status(self._g)
 
     def close(self):
         if self._g:

@@ -44,6 +44,10 @@ SIGNATURES = {
     "uw_group_forward": (_int, [_c_p, _int, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p), _c_p]),
     "uw_group_adjoint": (_int, [_c_p, _int, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p), _c_p]),
     "uw_group_tune": (_int, [_c_p, _int, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p), _int, _c_p]),
+    "uw_group_tune_cached": (_int, [_c_p, _int, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p), _int, ctypes.c_char_p,
+                                    _c_p]),
+    "uw_group_params": (_int, [_c_p, ctypes.POINTER(_int)]),
+    "uw_group_device_status": (_int, [_c_p]),
     "uw_group_destroy": (None, [_c_p]),
     "uw_plan_destroy": (None, [_c_p]),
     "uw_plan_table": (_i64, [_c_p, _int, _dp, _i64]),
@@ -172,6 +176,22 @@ def uw_group_adjoint(g, precision, y_ptrs, x_ptrs, stream):
 
 def uw_group_tune(g, precision, x_ptrs, y_ptrs, reps, stream):
     _chk(lib().uw_group_tune(g, precision, _ptrs(x_ptrs), _ptrs(y_ptrs), reps, stream), "uw_group_tune")
+
+
+def uw_group_tune_cached(g, precision, x_ptrs, y_ptrs, reps, cache_path, stream):
+    path = cache_path.encode() if cache_path else None
+    _chk(lib().uw_group_tune_cached(g, precision, _ptrs(x_ptrs), _ptrs(y_ptrs), reps, path, stream),
+         "uw_group_tune_cached")
+
+
+def uw_group_params(g):
+    out = (_int * 7)()
+    _chk(lib().uw_group_params(g, out), "uw_group_params")
+    return list(out)
+
+
+def uw_group_device_status(g):
+    return lib().uw_group_device_status(g)
 
 
 def uw_group_destroy(g):

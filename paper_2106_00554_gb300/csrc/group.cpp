@@ -5,7 +5,14 @@
 // fastest on that plan's sizes.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
 #include <set>
+#include <sstream>
+#include <string>
 #include <vector>
 
 #include "uw_internal.h"
@@ -18,6 +25,9 @@ struct uw_group {
   std::vector<cudaStream_t> streams;
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
+  uw::PersistentGroup* pg = nullptr;   // one persistent launch for FP32 (null: not eligible)
+  int use_pg = 1;                      // the tuner may prefer the forked streams
+  unsigned* derr = nullptr;            // device word: a bounded wait of the persistent launch gave up
 };
 
 static int group_fail(int code, const char* msg) {
@@ -26,6 +36,8 @@ static int group_fail(int code, const char* msg) {
 }
 
 static void group_free(uw_group* g) {
+  uw::pgroup_destroy(g->pg);
+  if (g->derr) cudaFree(g->derr);
   for (cudaStream_t s : g->streams)
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : g->join)
@@ -78,6 +90,23 @@ uw_group* uw_group_create(uw_plan* const* plans, int n, int nstreams) {
     P->coarse_mode = 1;
     P->group = g;
   }
+  if (cudaMalloc(&g->derr, sizeof(unsigned)) != cudaSuccess || cudaMemset(g->derr, 0, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    for (size_t i = 0; i < g->plans.size(); ++i) {
+      g->plans[i]->coarse_mode = g->saved_coarse[i];
+      g->plans[i]->group = nullptr;
+    }
+    group_free(g);
+    uw::set_error(UW_ERR_OOM, "group status word allocation failed");
+    return nullptr;
+  }
+  {
+    std::string why;
+    std::vector<const uw::Plan*> pl(g->plans.begin(), g->plans.end());
+    g->pg = uw::pgroup_create(pl.data(), n, why);
+    cudaGetLastError();
+  }
+  uw::set_error(UW_OK, "");
   return g;
 }
 
@@ -86,6 +115,16 @@ static int group_run(uw_group* g, int prec, bool fwd, const void* const* in, voi
   if (prec != UW_F64 && prec != UW_F32 && prec != UW_F32_SPLIT_BF16)
     return group_fail(UW_ERR_INVALID_ARG, "unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
+  if (prec == UW_F32 && g->pg && g->use_pg && !getenv("UW_GROUP_STREAMS")) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != g->plans[0]->device)
+      return group_fail(UW_ERR_INVALID_ARG, "the current CUDA device is not the group's device");
+    for (size_t i = 0; i < g->plans.size(); ++i) {
+      const bool need_in = fwd || g->plans[i]->m > 0, need_out = !fwd || g->plans[i]->m > 0;
+      if ((need_in && !in[i]) || (need_out && !out[i])) return group_fail(UW_ERR_INVALID_ARG, "null buffer");
+    }
+    return uw::pgroup_run(g->pg, fwd, in, out, g->derr, stream);
+  }
   const int ns = (int)g->streams.size();
   if (cudaEventRecord(g->fork, s) != cudaSuccess) return group_fail(UW_ERR_CUDA, "fork event failed");
   for (int k = 0; k < ns; ++k)
@@ -113,7 +152,7 @@ int uw_group_adjoint(uw_group* g, int prec, const void* const* y, void* const* x
   return group_run(g, prec, false, y, x, stream);
 }
 
-int uw_group_tune(uw_group* g, int prec, void* const* x, void* const* y, int reps, void* stream) {
+static int group_tune_variants(uw_group* g, int prec, void* const* x, void* const* y, int reps, void* stream) {
   if (!g || !x || !y || reps < 1) return group_fail(UW_ERR_INVALID_ARG, "null group or buffers, or reps < 1");
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -152,6 +191,169 @@ int uw_group_tune(uw_group* g, int prec, void* const* x, void* const* y, int rep
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
+}
+
+
+// ---------------------------------------------------------------------------
+// tuner of the persistent launch, with a JSON cache
+// ---------------------------------------------------------------------------
+// ms per forward + adjoint pair of the whole group on the current settings
+static int time_group_pairs(uw_group* g, int prec, void* const* x, void* const* y, int reps, void* stream, float* ms) {
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return group_fail(UW_ERR_OOM, "event creation failed");
+  }
+  int st = UW_OK;
+  for (int r = 0; r <= reps && st == UW_OK; ++r) {
+    if (r == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = group_fail(UW_ERR_CUDA, "event record failed");
+    if (st == UW_OK) st = group_run(g, prec, true, (const void* const*)x, y, stream);
+    if (st == UW_OK) st = group_run(g, prec, false, (const void* const*)y, x, stream);
+  }
+  if (st == UW_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                      cudaEventElapsedTime(ms, e0, e1) != cudaSuccess))
+    st = group_fail(UW_ERR_CUDA, "timing failed");
+  if (st == UW_OK) *ms /= (float)reps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+// cache key: GPU, dimension, the multiset of N over the instances, precision
+static std::string tune_key(const uw_group* g, int prec) {
+  cudaDeviceProp prop{};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  std::map<int, int> ns;
+  for (const uw_plan* P : g->plans) ns[P->N]++;
+  std::ostringstream k;
+  k << prop.name << "|d2|n" << g->plans.size() << "|N";
+  for (auto& kv : ns) k << kv.first << "x" << kv.second << ",";
+  k << "|prec" << prec;
+  std::string out = k.str();
+  for (char& c : out)
+    if (c == '"' || c == '\\') c = '_';
+  return out;
+}
+
+// the cache file: one JSON object, "key": [lines, cols, tiles, rad, ctas, persistent]
+static std::map<std::string, std::vector<int>> read_cache(const char* path) {
+  std::map<std::string, std::vector<int>> m;
+  std::ifstream f(path);
+  if (!f) return m;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string t = ss.str();
+  size_t i = 0;
+  while ((i = t.find('"', i)) != std::string::npos) {
+    const size_t j = t.find('"', i + 1);
+    if (j == std::string::npos) break;
+    const std::string key = t.substr(i + 1, j - i - 1);
+    const size_t a = t.find('[', j), b = t.find(']', j);
+    if (a == std::string::npos || b == std::string::npos || b < a) break;
+    std::vector<int> v;
+    std::stringstream vs(t.substr(a + 1, b - a - 1));
+    std::string tok;
+    while (std::getline(vs, tok, ',')) v.push_back(atoi(tok.c_str()));
+    m[key] = v;
+    i = b + 1;
+  }
+  return m;
+}
+static void write_cache(const char* path, const std::map<std::string, std::vector<int>>& m) {
+  std::ofstream f(path, std::ios::trunc);
+  if (!f) return;
+  f << "{\n";
+  size_t n = 0;
+  for (auto& kv : m) {
+    f << "  \"" << kv.first << "\": [";
+    for (size_t i = 0; i < kv.second.size(); ++i) f << (i ? ", " : "") << kv.second[i];
+    f << "]" << (++n < m.size() ? "," : "") << "\n";
+  }
+  f << "}\n";
+}
+
+static int group_tune_persistent(uw_group* g, int prec, void* const* x, void* const* y, int reps, const char* cache,
+                                 void* stream) {
+  const std::string key = tune_key(g, prec);
+  if (cache) {
+    auto m = read_cache(cache);
+    auto it = m.find(key);
+    if (it != m.end() && it->second.size() == 6) {
+      const auto& v = it->second;
+      const int st = uw::pgroup_set_params(g->pg, v[0], v[1], v[2], v[3], v[4]);
+      g->use_pg = v[5];
+      return st;
+    }
+  }
+  float t_streams = 0.f;
+  g->use_pg = 0;
+  int st = time_group_pairs(g, prec, x, y, reps, stream, &t_streams);
+  g->use_pg = 1;
+  if (st != UW_OK) return st;
+  float best = 0.f;
+  int bp[5] = {1, 4, 4, 16, 0};
+  bool first = true;
+  for (int lines : {1, 2, 4})
+    for (int cols : {4, 16})
+      for (int tiles : {2, 8})
+        for (int rad : {16, 8})
+          for (int ctas : {0, 2}) {
+            if ((st = uw::pgroup_set_params(g->pg, lines, cols, tiles, rad, ctas)) != UW_OK) return st;
+            float t = 0.f;
+            if ((st = time_group_pairs(g, prec, x, y, reps, stream, &t)) != UW_OK) return st;
+            if (first || t < best) {
+              best = t;
+              const int v[5] = {lines, cols, tiles, rad, ctas};
+              std::memcpy(bp, v, sizeof bp);
+              first = false;
+            }
+          }
+  if ((st = uw::pgroup_set_params(g->pg, bp[0], bp[1], bp[2], bp[3], bp[4])) != UW_OK) return st;
+  g->use_pg = best <= t_streams ? 1 : 0;
+  if (cache) {
+    auto m = read_cache(cache);
+    m[key] = {bp[0], bp[1], bp[2], bp[3], bp[4], g->use_pg};
+    write_cache(cache, m);
+  }
+  return UW_OK;
+}
+
+int uw_group_tune_cached(uw_group* g, int prec, void* const* x, void* const* y, int reps, const char* cache,
+                         void* stream) {
+  int st = group_tune_variants(g, prec, x, y, reps, stream);
+  if (st != UW_OK || prec != UW_F32 || !g->pg) return st;
+  return group_tune_persistent(g, prec, x, y, reps, cache, stream);
+}
+
+int uw_group_tune(uw_group* g, int prec, void* const* x, void* const* y, int reps, void* stream) {
+  return uw_group_tune_cached(g, prec, x, y, reps, nullptr, stream);
+}
+
+int uw_group_params(const uw_group* g, int* out7) {
+  if (!g || !out7) return group_fail(UW_ERR_INVALID_ARG, "null group or output");
+  out7[0] = g->pg ? 1 : 0;
+  out7[1] = g->use_pg;
+  if (g->pg) uw::pgroup_params(g->pg, out7 + 2);
+  else
+    for (int i = 2; i < 7; ++i) out7[i] = 0;
+  return UW_OK;
+}
+
+int uw_group_device_status(uw_group* g) {
+  if (!g) return group_fail(UW_ERR_INVALID_ARG, "null group");
+  unsigned w = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&w, g->derr, sizeof w, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return group_fail(UW_ERR_CUDA, "group status: device error");
+  if (w) {
+    cudaMemset(g->derr, 0, sizeof(unsigned));
+    cudaDeviceSynchronize();
+    return group_fail(UW_ERR_TIMEOUT, "a bounded wait of the persistent group launch gave up; results invalid");
+  }
+  return UW_OK;
 }
 
 void uw_group_destroy(uw_group* g) {

@@ -44,64 +44,10 @@ __global__ void __launch_bounds__(256) k_line_fwd(const T* __restrict__ in, T* _
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
-  int off = stage_tables(tab, G, sm, st, tid, nthr);
+  const int off = stage_tables(tab, G, sm, st, tid, nthr);
   pdl_trigger();
   pdl_wait();
-  T* s0 = sm + off;
-  T* s1 = s0 + G.M;
-  T* v = s1 + G.M;
-  const int line = blockIdx.x % io.lines;
-  const int64_t b = blockIdx.x / io.lines;
-  const int drow = io.seq_rows ? seqrow(line, G.L) : line;
-  const T* src = in + b * io.in_batch + (int64_t)drow * io.in_stride;
-  for (int i = tid; i < G.M; i += nthr) s0[i] = src[i];
-  __syncthreads();
-  // (a) synthesis levels jlev .. R-1; the last output must land in s1
-  const int nlev = G.R - io.jlev;
-  T* A = s0;
-  T* Bf = (nlev & 1) ? s1 : v;
-  for (int j = io.jlev; j < G.R; ++j) {
-    const int n0 = 1 << j;
-    Plain<T> lo{A}, hi{s0 + n0};
-    for (int k = tid; k < 2 * n0; k += nthr) Bf[k] = syn_one<T>(k, n0, lo, hi, st, G);
-    __syncthreads();
-    T* nb = (A == s0) ? ((Bf == s1) ? v : s1) : A;
-    A = Bf;
-    Bf = nb;
-  }
-  if (nlev == 0) {
-    for (int i = tid; i < G.M; i += nthr) s1[i] = s0[i];
-    __syncthreads();
-  }
-  // (b) v = T s, scaled by 2^{-R/2}
-  const T sc = (T)exp2(-0.5 * (double)G.R);
-  {
-    Plain<T> s{s1};
-    for (int k = tid; k < G.N; k += nthr) v[padi(k)] = sc * up_one<T>(k, s, st, G);
-  }
-  __syncthreads();
-  // (c) natural-order FWHT
-  fwht_smem<T>(v, G.L, tid, nthr);
-  // (d) store natural order, or gather the sampled sequency indices
-  if (io.mode == 0) {
-    T* dst = out + b * io.out_batch + (int64_t)line * io.out_stride;
-    for (int k = tid; k < G.N; k += nthr) dst[k] = v[padi(k)];
-  } else {
-    const int mrow = io.mask_rows == 1 ? 0 : line;
-    const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
-    const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
-    T* y = out + b * io.m;
-    for (int w = tid; w < io.wpr; w += nthr) {
-      uint32_t bits = mk[w];
-      int64_t pos = pf[w];
-      while (bits) {
-        int bb = __ffs(bits) - 1;
-        bits &= bits - 1;
-        int n = w * 32 + bb;
-        y[pos++] = v[padi(seqrow(n, G.L))];
-      }
-    }
-  }
+  line_fwd_one<T>(in, out, st, G, io, blockIdx.x, sm + off, tid, nthr);
 }
 
 template <typename T>
@@ -111,68 +57,10 @@ __global__ void __launch_bounds__(256) k_line_adj(const T* __restrict__ in, T* _
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   SmemTables<T> st;
-  int off = stage_tables(tab, G, sm, st, tid, nthr);
+  const int off = stage_tables(tab, G, sm, st, tid, nthr);
   pdl_trigger();
   pdl_wait();
-  T* s0 = sm + off;
-  T* s1 = s0 + G.M;
-  T* v = s1 + G.M;
-  const int line = blockIdx.x % io.lines;
-  const int64_t b = blockIdx.x / io.lines;
-  if (io.mode == 0) {
-    const T* src = in + b * io.in_batch + (int64_t)line * io.in_stride;
-    for (int k = tid; k < G.N; k += nthr) v[padi(k)] = src[k];
-  } else {
-    for (int k = tid; k < padlen(G.N); k += nthr) v[k] = 0;
-    __syncthreads();
-    const int mrow = io.mask_rows == 1 ? 0 : line;
-    const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
-    const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
-    const T* y = in + b * io.m;
-    for (int w = tid; w < io.wpr; w += nthr) {
-      uint32_t bits = mk[w];
-      int64_t pos = pf[w];
-      while (bits) {
-        int bb = __ffs(bits) - 1;
-        bits &= bits - 1;
-        int n = w * 32 + bb;
-        v[padi(seqrow(n, G.L))] = y[pos++];
-      }
-    }
-  }
-  __syncthreads();
-  // (c^T) the Hadamard matrix is symmetric: same transform
-  fwht_smem<T>(v, G.L, tid, nthr);
-  // (b^T) s = T^T v
-  const T sc = (T)exp2(-0.5 * (double)G.R);
-  {
-    Padded<T> vv{v};
-    for (int m = tid; m < G.M; m += nthr) s1[m] = sc * upT_one<T>(m, vv, st, G);
-  }
-  __syncthreads();
-  // (a^T) analysis levels R-1 .. jlev; details go straight to s0
-  T* A = s1;
-  T* Bf = v;
-  for (int j = G.R - 1; j >= io.jlev; --j) {
-    const int n0 = 1 << j;
-    Plain<T> s{A};
-    for (int m = tid; m < n0; m += nthr) {
-      T lo, hi;
-      ana_one<T>(m, n0, s, st, G, lo, hi);
-      Bf[m] = lo;
-      s0[n0 + m] = hi;
-    }
-    __syncthreads();
-    T* t = A;
-    A = Bf;
-    Bf = t;
-  }
-  const int nlo = 1 << io.jlev;
-  for (int i = tid; i < nlo; i += nthr) s0[i] = A[i];
-  __syncthreads();
-  const int drow = io.seq_rows ? seqrow(line, G.L) : line;
-  T* dst = out + b * io.out_batch + (int64_t)drow * io.out_stride;
-  for (int i = tid; i < G.M; i += nthr) dst[i] = s0[i];
+  line_adj_one<T>(in, out, st, G, io, blockIdx.x, sm + off, tid, nthr);
 }
 
 // ---------------------------------------------------------------------------

@@ -28,6 +28,7 @@ struct SmemTables {  // tables staged in shared memory for one CTA
 
 struct Geo {  // geometry of one plan, passed by value
   int p, q, Q, R, M, N, L, bd, ntap, Lb;
+  int rad = 16;  // largest radix of the shared-memory FWHT passes (16, 8 or 4)
 };
 
 __host__ __device__ inline int table_count(const Geo& G) {
@@ -241,10 +242,11 @@ __device__ __forceinline__ void fwht_pass(T* v, int L, int done, int tid, int nt
 }
 
 template <typename T>
-__device__ void fwht_smem(T* v, int L, int tid, int nthr) {
+__device__ void fwht_smem(T* v, int L, int tid, int nthr, int rad = 16) {
+  const int rb = rad >= 16 ? 4 : (rad >= 8 ? 3 : 2);
   int done = 0;
   while (done < L) {
-    int r = min(4, L - done);
+    int r = min(rb, L - done);
     if (r == 4) fwht_pass<T, 16>(v, L, done, tid, nthr);
     else if (r == 3) fwht_pass<T, 8>(v, L, done, tid, nthr);
     else if (r == 2) fwht_pass<T, 4>(v, L, done, tid, nthr);
@@ -274,6 +276,137 @@ struct LineIO {
   int mask_rows;         // 1 for d = 1 (all lines use row 0), else = lines
   const uint16_t* pos;   // per sample: natural FWHT position in its row (or null)
 };
+
+// One line of the generic line operators, one CTA (any size), the whole
+// line in shared memory at sm (2 M + padlen(N) values of T).  `item` is the
+// line's index over all batch instances (line = item % io.lines).
+// Forward: synthesis levels jlev .. R-1 of one line, T, natural-order FWHT,
+// then the natural line is stored or the sampled sequency indices gathered.
+template <typename T>
+__device__ void line_fwd_one(const T* __restrict__ in, T* __restrict__ out, const SmemTables<T>& st, const Geo& G,
+                             const LineIO& io, int item, T* sm, int tid, int nthr) {
+  T* s0 = sm;
+  T* s1 = s0 + G.M;
+  T* v = s1 + G.M;
+  const int line = item % io.lines;
+  const int64_t b = item / io.lines;
+  const int drow = io.seq_rows ? seqrow(line, G.L) : line;
+  const T* src = in + b * io.in_batch + (int64_t)drow * io.in_stride;
+  for (int i = tid; i < G.M; i += nthr) s0[i] = src[i];
+  __syncthreads();
+  // (a) synthesis levels jlev .. R-1; the last output must land in s1
+  const int nlev = G.R - io.jlev;
+  T* A = s0;
+  T* Bf = (nlev & 1) ? s1 : v;
+  for (int j = io.jlev; j < G.R; ++j) {
+    const int n0 = 1 << j;
+    Plain<T> lo{A}, hi{s0 + n0};
+    for (int k = tid; k < 2 * n0; k += nthr) Bf[k] = syn_one<T>(k, n0, lo, hi, st, G);
+    __syncthreads();
+    T* nb = (A == s0) ? ((Bf == s1) ? v : s1) : A;
+    A = Bf;
+    Bf = nb;
+  }
+  if (nlev == 0) {
+    for (int i = tid; i < G.M; i += nthr) s1[i] = s0[i];
+    __syncthreads();
+  }
+  // (b) v = T s, scaled by 2^{-R/2}
+  const T sc = (T)exp2(-0.5 * (double)G.R);
+  {
+    Plain<T> s{s1};
+    for (int k = tid; k < G.N; k += nthr) v[padi(k)] = sc * up_one<T>(k, s, st, G);
+  }
+  __syncthreads();
+  // (c) natural-order FWHT
+  fwht_smem<T>(v, G.L, tid, nthr, G.rad);
+  // (d) store natural order, or gather the sampled sequency indices
+  if (io.mode == 0) {
+    T* dst = out + b * io.out_batch + (int64_t)line * io.out_stride;
+    for (int k = tid; k < G.N; k += nthr) dst[k] = v[padi(k)];
+  } else {
+    const int mrow = io.mask_rows == 1 ? 0 : line;
+    const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
+    const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
+    T* y = out + b * io.m;
+    for (int w = tid; w < io.wpr; w += nthr) {
+      uint32_t bits = mk[w];
+      int64_t pos = pf[w];
+      while (bits) {
+        int bb = __ffs(bits) - 1;
+        bits &= bits - 1;
+        int n = w * 32 + bb;
+        y[pos++] = v[padi(seqrow(n, G.L))];
+      }
+    }
+  }
+}
+
+// Adjoint of line_fwd_one: load the natural line or scatter the samples,
+// FWHT (H is symmetric), T^T, analysis levels R-1 .. jlev.
+template <typename T>
+__device__ void line_adj_one(const T* __restrict__ in, T* __restrict__ out, const SmemTables<T>& st, const Geo& G,
+                             const LineIO& io, int item, T* sm, int tid, int nthr) {
+  T* s0 = sm;
+  T* s1 = s0 + G.M;
+  T* v = s1 + G.M;
+  const int line = item % io.lines;
+  const int64_t b = item / io.lines;
+  if (io.mode == 0) {
+    const T* src = in + b * io.in_batch + (int64_t)line * io.in_stride;
+    for (int k = tid; k < G.N; k += nthr) v[padi(k)] = src[k];
+  } else {
+    for (int k = tid; k < padlen(G.N); k += nthr) v[k] = 0;
+    __syncthreads();
+    const int mrow = io.mask_rows == 1 ? 0 : line;
+    const uint32_t* mk = io.mask + (int64_t)mrow * io.wpr;
+    const int32_t* pf = io.prefix + (int64_t)mrow * io.wpr;
+    const T* y = in + b * io.m;
+    for (int w = tid; w < io.wpr; w += nthr) {
+      uint32_t bits = mk[w];
+      int64_t pos = pf[w];
+      while (bits) {
+        int bb = __ffs(bits) - 1;
+        bits &= bits - 1;
+        int n = w * 32 + bb;
+        v[padi(seqrow(n, G.L))] = y[pos++];
+      }
+    }
+  }
+  __syncthreads();
+  // (c^T) the Hadamard matrix is symmetric: same transform
+  fwht_smem<T>(v, G.L, tid, nthr, G.rad);
+  // (b^T) s = T^T v
+  const T sc = (T)exp2(-0.5 * (double)G.R);
+  {
+    Padded<T> vv{v};
+    for (int m = tid; m < G.M; m += nthr) s1[m] = sc * upT_one<T>(m, vv, st, G);
+  }
+  __syncthreads();
+  // (a^T) analysis levels R-1 .. jlev; details go straight to s0
+  T* A = s1;
+  T* Bf = v;
+  for (int j = G.R - 1; j >= io.jlev; --j) {
+    const int n0 = 1 << j;
+    Plain<T> s{A};
+    for (int m = tid; m < n0; m += nthr) {
+      T lo, hi;
+      ana_one<T>(m, n0, s, st, G, lo, hi);
+      Bf[m] = lo;
+      s0[n0 + m] = hi;
+    }
+    __syncthreads();
+    T* t = A;
+    A = Bf;
+    Bf = t;
+  }
+  const int nlo = 1 << io.jlev;
+  for (int i = tid; i < nlo; i += nthr) s0[i] = A[i];
+  __syncthreads();
+  const int drow = io.seq_rows ? seqrow(line, G.L) : line;
+  T* dst = out + b * io.out_batch + (int64_t)drow * io.out_stride;
+  for (int i = tid; i < G.M; i += nthr) dst[i] = s0[i];
+}
 
 // position of the (r+1)-th set bit of x (0 <= r < popc(x)), branch-free
 __device__ __forceinline__ int select_bit(unsigned x, int r) {

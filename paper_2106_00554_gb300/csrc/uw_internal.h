@@ -153,6 +153,15 @@ void build_f32(Plan& P, std::vector<float>& out);
 // tc_plan.cpp: edge corrections of one 2D Mallat level, [2][Lb][2p] (empty
 // for periodic plans); false if the boundary blocks do not have that structure
 bool build_coarse(const Plan& P, std::vector<double>& D);
+// group_kernel.cu: one persistent launch for the FP32 products of a plan
+// group (NULL from pgroup_create, with the reason, if the group does not
+// qualify); err: a device word set when a bounded wait gives up
+struct PersistentGroup;
+PersistentGroup* pgroup_create(const Plan* const* plans, int n, std::string& why);
+int pgroup_run(PersistentGroup* g, bool fwd, const void* const* in, void* const* out, unsigned* err, void* stream);
+int pgroup_set_params(PersistentGroup* g, int lines, int cols, int tiles, int rad, int ctas);
+void pgroup_params(const PersistentGroup* g, int* p5);
+void pgroup_destroy(PersistentGroup* g);
 // kernels.cu
 int upload_tables(Plan& P);
 int launch_forward(const Plan& P, int prec, const void* x, void* y, int batch, void* stream, int* nlaunch);

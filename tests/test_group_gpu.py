@@ -143,3 +143,97 @@ def test_group_rejects_a_plan_twice_and_a_plan_in_two_groups():
     g2.close()
     a.close()
     b.close()
+
+
+def _group_case(seed, n):
+    rng = np.random.default_rng(seed)
+    inst = uneven_instances(rng, n, Rs=(6, 7, 8), qs=(1, 2), ps=(1, 2, 4, 6, 8))
+    plans = [Plan(2, R, q, p, bd, omega=om) for R, q, p, bd, om, _ in inst]
+    xs = [x for *_, x in inst]
+    ys = [rng.standard_normal(pl.m) for pl in plans]
+    return inst, plans, xs, ys
+
+
+def test_persistent_group_launch_matches_the_forked_streams(monkeypatch):
+    """FP32 products of a group of 2D plans run as one persistent launch (a
+    grid draining a queue of (instance, phase, items) tasks).  The results
+    equal the forked-stream path within FP32 rounding and the dense oracle
+    within 1e-5; the launch is in use before any tuning."""
+    inst, plans, xs, ys = _group_case(41, 24)
+    xd, yd, yo, xo = tensors(plans, xs, ys, torch.float32)
+    group = PlanGroup(plans, nstreams=4)
+    prm = group.params()
+    assert prm["persistent_available"] == 1 and prm["persistent_in_use"] == 1, prm
+    group.forward(xd, yo, F32)
+    group.adjoint(yd, xo, F32)
+    torch.cuda.synchronize()
+    got_y = [t.cpu().numpy() for t in yo]
+    got_x = [t.cpu().numpy() for t in xo]
+    monkeypatch.setenv("UW_GROUP_STREAMS", "1")
+    group.forward(xd, yo, F32)
+    group.adjoint(yd, xo, F32)
+    torch.cuda.synchronize()
+    monkeypatch.delenv("UW_GROUP_STREAMS")
+    for i, (R, q, p, bd, om, x) in enumerate(inst):
+        assert rel(got_y[i], yo[i].cpu().numpy()) < 1e-6, i
+        assert rel(got_x[i], xo[i].cpu().numpy()) < 1e-6, i
+        G = dense.G1d(R, q, p, bd)
+        J0 = W.default_J0(p)
+        assert rel(got_y[i], dense.forward2d(x, R, q, p, bd, J0, om, G=G)) < 1e-5, i
+        assert rel(got_x[i], dense.adjoint2d(ys[i], R, q, p, bd, J0, om, G=G)) < 1e-5, i
+    assert group.device_status() == 0
+    group.close()
+
+
+def test_persistent_group_wait_gives_up_and_reports(monkeypatch):
+    """With a spin limit of zero every task whose previous phase is not yet
+    complete gives up at once: the launch returns (no hang), the group reports
+    UW_ERR_TIMEOUT and clears it, and the next call with the default limit is
+    right."""
+    inst, plans, xs, ys = _group_case(42, 12)
+    xd, yd, yo, xo = tensors(plans, xs, ys, torch.float32)
+    group = PlanGroup(plans, nstreams=2)
+    group.forward(xd, yo, F32)
+    torch.cuda.synchronize()
+    want = [t.cpu().numpy().copy() for t in yo]
+    monkeypatch.setenv("UW_GROUP_SPIN_LIMIT", "0")
+    for t in yo:
+        t.zero_()
+    group.forward(xd, yo, F32)
+    assert group.device_status() == 5
+    monkeypatch.delenv("UW_GROUP_SPIN_LIMIT")
+    group.forward(xd, yo, F32)
+    assert group.device_status() == 0
+    for i in range(len(plans)):
+        assert rel(yo[i].cpu().numpy(), want[i]) == 0.0, i
+    group.close()
+
+
+def test_group_tuner_writes_and_reads_its_cache(tmp_path):
+    """The tuner times the persistent launch's parameters and the forked
+    streams, keeps the fastest, and records the choice in a JSON cache keyed by
+    GPU, dimension, the instances' N and precision; a second tuning of a group
+    of the same shape reads it back without timing."""
+    import json
+    inst, plans, xs, ys = _group_case(43, 8)
+    xd, yd, yo, xo = tensors(plans, xs, ys, torch.float32)
+    cache = str(tmp_path / "tune.json")
+    group = PlanGroup(plans, nstreams=2)
+    group.tune([x.clone() for x in xd], [torch.empty_like(y) for y in yo], F32, reps=1, cache=cache)
+    first = group.params()
+    group.close()
+    entries = json.load(open(cache))
+    assert len(entries) == 1
+    (key, val), = entries.items()
+    assert "|d2|" in key and len(val) == 6
+    assert val[:5] == [first[k] for k in ("lines_per_task", "cols_per_task", "tiles_per_task", "radix",
+                                          "ctas_per_sm")]
+    group2 = PlanGroup(plans, nstreams=2)
+    group2.tune([x.clone() for x in xd], [torch.empty_like(y) for y in yo], F32, reps=1, cache=cache)
+    assert group2.params() == first
+    group2.forward(xd, yo, F32)
+    torch.cuda.synchronize()
+    for i, (R, q, p, bd, om, x) in enumerate(inst):
+        G = dense.G1d(R, q, p, bd)
+        assert rel(yo[i].cpu().numpy(), dense.forward2d(x, R, q, p, bd, W.default_J0(p), om, G=G)) < 1e-5, i
+    group2.close()
