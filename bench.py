@@ -860,12 +860,14 @@ def run_uneven(args):
     ms_graph = timed(graph.replay, k)
     assert group.device_status() == 0
     in_use = prec == F32 and prm["persistent_in_use"] == 1
-    ms_streams = None
-    if in_use:   # the same pair through the forked streams, for comparison
-        os.environ["UW_GROUP_STREAMS"] = "1"
+    other = None
+    if prec == F32 and prm["persistent_available"] == 1:   # the path the tuner did not keep, for comparison
+        var = "UW_GROUP_STREAMS" if in_use else "UW_GROUP_PERSISTENT"
+        os.environ[var] = "1"
         g2 = capture()
-        ms_streams = timed(g2.replay, k)
-        del os.environ["UW_GROUP_STREAMS"]
+        other = timed(g2.replay, k)
+        del os.environ[var]
+        assert group.device_status() == 0
     group.close()
 
     def sequential():
@@ -897,9 +899,11 @@ def run_uneven(args):
                      "peak_kind": peak_kind},
         "sequential": {"value": n * 1000.0 / ms_seq, "unit": "pairs/s", "ms_per_step": ms_seq,
                        "how": "each plan's forward and adjoint issued in turn on one stream, eager"}}
-    if ms_streams is not None:
-        line["forked_streams"] = {"value": n * 1000.0 / ms_streams, "unit": "pairs/s", "ms_per_step": ms_streams,
-                                  "how": f"the same group forked over {nst} streams, captured as one CUDA graph"}
+    if other is not None:
+        name = "forked_streams" if in_use else "persistent"
+        how = (f"the same group forked over {nst} streams, captured as one CUDA graph" if in_use else
+               "the same group as one persistent launch per direction with the tuned parameters, captured")
+        line[name] = {"value": n * 1000.0 / other, "unit": "pairs/s", "ms_per_step": other, "how": how}
     print(json.dumps(line))
 
 

@@ -115,7 +115,7 @@ static int group_run(uw_group* g, int prec, bool fwd, const void* const* in, voi
   if (prec != UW_F64 && prec != UW_F32 && prec != UW_F32_SPLIT_BF16)
     return group_fail(UW_ERR_INVALID_ARG, "unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
-  if (prec == UW_F32 && g->pg && g->use_pg && !getenv("UW_GROUP_STREAMS")) {
+  if (prec == UW_F32 && g->pg && (g->use_pg || getenv("UW_GROUP_PERSISTENT")) && !getenv("UW_GROUP_STREAMS")) {
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess || cur != g->plans[0]->device)
       return group_fail(UW_ERR_INVALID_ARG, "the current CUDA device is not the group's device");
@@ -297,9 +297,9 @@ static int group_tune_persistent(uw_group* g, int prec, void* const* x, void* co
   float best = 0.f;
   int bp[5] = {1, 4, 4, 16, 0};
   bool first = true;
-  for (int lines : {1, 2, 4})
-    for (int cols : {4, 16})
-      for (int tiles : {2, 8})
+  for (int lines : {1, 4, 16})
+    for (int cols : {4, 16, 64})
+      for (int tiles : {4, 16})
         for (int rad : {16, 8})
           for (int ctas : {0, 2}) {
             if ((st = uw::pgroup_set_params(g->pg, lines, cols, tiles, rad, ctas)) != UW_OK) return st;

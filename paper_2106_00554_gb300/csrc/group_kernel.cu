@@ -282,6 +282,9 @@ __global__ void __launch_bounds__(NTH) k_group(const Inst* __restrict__ insts, c
   float* sm = reinterpret_cast<float*>(smem_raw);
   __shared__ int s_t, s_ok;
   const int tid = threadIdx.x;
+  int staged = -1;                 // instance whose tables are in shared memory
+  SmemTables<float> st{};
+  int off = 0;
   for (;;) {
     if (tid == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
@@ -311,10 +314,12 @@ __global__ void __launch_bounds__(NTH) k_group(const Inst* __restrict__ insts, c
       if (tid == 0) atomicExch(err, 1u);
       break;
     }
-    SmemTables<float> st;
     Geo G = I.G;
-    const int off = stage_tables(I.tab, G, sm, st, tid, NTH);
-    __syncthreads();
+    if (tk.inst != staged) {       // consecutive tasks of one instance keep its tables
+      off = stage_tables(I.tab, G, sm, st, tid, NTH);
+      staged = tk.inst;
+      __syncthreads();
+    }
     G.rad = rad;
     Inst J = I;
     J.G = G;
