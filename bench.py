@@ -844,14 +844,17 @@ def run_uneven(args):
         return g
 
     def timed(fn, k):
-        for _ in range(max(3, args.warmup)):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(k):
-            fn()
-        e1.record(s)
+        # everything on stream s: graph replays launch on the current stream,
+        # and the events must bracket them on the same stream
+        with torch.cuda.stream(s):
+            for _ in range(max(3, args.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(k):
+                fn()
+            e1.record(s)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
 
