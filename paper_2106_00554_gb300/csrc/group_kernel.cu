@@ -80,25 +80,25 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
 // relations with the boundary blocks, via syn_one / ana_one)
 // ---------------------------------------------------------------------------
 // synthesis, level j: row r of [[LL, HL], [LH, HH]] (LL = S_j) -> T[r][0, 2n0)
-__device__ void syn_row(const Inst& I, const float* x, const float* S, int ldS, float* Tm, int j, int r,
+__device__ void syn_row(const Geo& G, const float* x, const float* S, int ldS, float* Tm, int j, int r,
                         const SmemTables<float>& st, float* sm, int tid) {
-  const int n0 = 1 << j, n1 = 2 * n0, M = I.G.M;
+  const int n0 = 1 << j, n1 = 2 * n0, M = G.M;
   for (int c = tid; c < n1; c += NTH) sm[c] = (r < n0 && c < n0) ? S[(int64_t)r * ldS + c] : x[(int64_t)r * M + c];
   __syncthreads();
   Plain<float> lo{sm}, hi{sm + n0};
-  for (int k = tid; k < n1; k += NTH) Tm[(int64_t)r * n1 + k] = syn_one<float>(k, n0, lo, hi, st, I.G);
+  for (int k = tid; k < n1; k += NTH) Tm[(int64_t)r * n1 + k] = syn_one<float>(k, n0, lo, hi, st, G);
 }
 // synthesis, level j: column c of T -> S_{j+1}[0, 2n0)[c]
-__device__ void syn_col(const Inst& I, const float* Tm, float* Sout, int ldO, int j, int c, const SmemTables<float>& st,
+__device__ void syn_col(const Geo& G, const float* Tm, float* Sout, int ldO, int j, int c, const SmemTables<float>& st,
                         float* sm, int tid) {
   const int n0 = 1 << j, n1 = 2 * n0;
   for (int k = tid; k < n1; k += NTH) sm[k] = Tm[(int64_t)k * n1 + c];
   __syncthreads();
   Plain<float> lo{sm}, hi{sm + n0};
-  for (int k = tid; k < n1; k += NTH) Sout[(int64_t)k * ldO + c] = syn_one<float>(k, n0, lo, hi, st, I.G);
+  for (int k = tid; k < n1; k += NTH) Sout[(int64_t)k * ldO + c] = syn_one<float>(k, n0, lo, hi, st, G);
 }
 // analysis, level j: column c of S_{j+1} -> T[0, n0)[c] (lo), T[n0, 2n0)[c] (hi)
-__device__ void ana_col(const Inst& I, const float* S, int ldS, float* Tm, int j, int c, const SmemTables<float>& st,
+__device__ void ana_col(const Geo& G, const float* S, int ldS, float* Tm, int j, int c, const SmemTables<float>& st,
                         float* sm, int tid) {
   const int n0 = 1 << j, n1 = 2 * n0;
   for (int k = tid; k < n1; k += NTH) sm[k] = S[(int64_t)k * ldS + c];
@@ -106,22 +106,22 @@ __device__ void ana_col(const Inst& I, const float* S, int ldS, float* Tm, int j
   Plain<float> s{sm};
   for (int m = tid; m < n0; m += NTH) {
     float lo, hi;
-    ana_one<float>(m, n0, s, st, I.G, lo, hi);
+    ana_one<float>(m, n0, s, st, G, lo, hi);
     Tm[(int64_t)m * n1 + c] = lo;
     Tm[(int64_t)(n0 + m) * n1 + c] = hi;
   }
 }
 // analysis, level j: row r of T -> [lo | hi]; the LL quarter to S_j (or x at
 // the coarsest level), the rest to x
-__device__ void ana_row(const Inst& I, const float* Tm, float* x, float* Snext, int ldN, int j, int r,
+__device__ void ana_row(const Geo& G, const float* Tm, float* x, float* Snext, int ldN, int j, int r,
                         const SmemTables<float>& st, float* sm, int tid) {
-  const int n0 = 1 << j, n1 = 2 * n0, M = I.G.M;
+  const int n0 = 1 << j, n1 = 2 * n0, M = G.M;
   for (int k = tid; k < n1; k += NTH) sm[k] = Tm[(int64_t)r * n1 + k];
   __syncthreads();
   Plain<float> s{sm};
   for (int m = tid; m < n0; m += NTH) {
     float lo, hi;
-    ana_one<float>(m, n0, s, st, I.G, lo, hi);
+    ana_one<float>(m, n0, s, st, G, lo, hi);
     if (r < n0) Snext[(int64_t)r * ldN + m] = lo;
     else x[(int64_t)r * M + m] = lo;
     x[(int64_t)r * M + n0 + m] = hi;
@@ -184,16 +184,16 @@ __host__ __device__ inline int kind_of(const Inst& I, int ph, int fwd) {
   return ph < 4 ? 0 : 1;
 }
 
-__device__ void run_item(const Inst& I, int ph, int it, int fwd, const float* in, float* out,
+__device__ void run_item(const Inst& I, const Geo& G, int ph, int it, int fwd, const float* in, float* out,
                          const SmemTables<float>& st, float* sm, int tid) {
-  const int M = I.G.M, N = I.G.N, Mh = M / 2, L = I.nl;
+  const int M = G.M, N = G.N, Mh = M / 2, L = I.nl;
   if (fwd) {
     if (ph < 2 * L) {
       const int k = ph / 2, j = I.J0 + k;
       const float* S = k == 0 ? in : (((k - 1) & 1) == 0 ? I.XS : I.XS2);
       const int ldS = k == 0 ? M : Mh;
-      if ((ph & 1) == 0) syn_row(I, in, S, ldS, I.VT, j, it, st, sm, tid);
-      else syn_col(I, I.VT, (k & 1) == 0 ? I.XS : I.XS2, Mh, j, it, st, sm, tid);
+      if ((ph & 1) == 0) syn_row(G, in, S, ldS, I.VT, j, it, st, sm, tid);
+      else syn_col(G, I.VT, (k & 1) == 0 ? I.XS : I.XS2, Mh, j, it, st, sm, tid);
       return;
     }
     const int k = ph - 2 * L;
@@ -214,30 +214,30 @@ __device__ void run_item(const Inst& I, int ph, int it, int fwd, const float* in
       return;
     }
     LineIO io{};
-    io.jlev = I.G.R - 1;
+    io.jlev = G.R - 1;
     if (k == 1) {
       io.in_stride = M; io.out_stride = N; io.lines = M; io.in_batch = (int64_t)M * M;
       io.out_batch = (int64_t)M * N; io.seq_rows = 0; io.mode = 0;
-      line_fwd_one<float>(I.XT, I.VT, st, I.G, io, it, sm, tid, NTH);
+      line_fwd_one<float>(I.XT, I.VT, st, G, io, it, sm, tid, NTH);
     } else {
       io.in_stride = M; io.lines = N; io.in_batch = (int64_t)N * M; io.out_batch = I.m; io.seq_rows = 1;
       io.mode = 1; io.mask = I.mask; io.prefix = I.prefix; io.pos = I.pos; io.wpr = I.wpr; io.m = I.m;
       io.mask_rows = N;
-      line_fwd_one<float>(I.V, out, st, I.G, io, it, sm, tid, NTH);
+      line_fwd_one<float>(I.V, out, st, G, io, it, sm, tid, NTH);
     }
     return;
   }
   if (ph == 0 || ph == 2) {
     LineIO io{};
-    io.jlev = I.G.R - 1;
+    io.jlev = G.R - 1;
     if (ph == 0) {
       io.out_stride = M; io.lines = N; io.out_batch = (int64_t)N * M; io.seq_rows = 1; io.mode = 1;
       io.mask = I.mask; io.prefix = I.prefix; io.pos = I.pos; io.wpr = I.wpr; io.m = I.m; io.mask_rows = N;
-      line_adj_one<float>(in, I.V, st, I.G, io, it, sm, tid, NTH);
+      line_adj_one<float>(in, I.V, st, G, io, it, sm, tid, NTH);
     } else {
       io.in_stride = N; io.out_stride = M; io.lines = M; io.in_batch = (int64_t)M * N; io.out_batch = (int64_t)M * M;
       io.seq_rows = 0; io.mode = 0;
-      line_adj_one<float>(I.VT, I.XT, st, I.G, io, it, sm, tid, NTH);
+      line_adj_one<float>(I.VT, I.XT, st, G, io, it, sm, tid, NTH);
     }
     return;
   }
@@ -259,13 +259,13 @@ __device__ void run_item(const Inst& I, int ph, int it, int fwd, const float* in
         sm, tid);
     return;
   }
-  const int k = (ph - 4) / 2, j = I.G.R - 2 - k;
+  const int k = (ph - 4) / 2, j = G.R - 2 - k;
   const float* S = k == 0 ? I.XS : (((k - 1) & 1) == 0 ? I.XS2 : I.XS);
   if (((ph - 4) & 1) == 0) {
-    ana_col(I, S, Mh, I.V, j, it, st, sm, tid);
+    ana_col(G, S, Mh, I.V, j, it, st, sm, tid);
   } else {
     float* Sn = k == L - 1 ? out : ((k & 1) == 0 ? I.XS2 : I.XS);
-    ana_row(I, I.V, out, Sn, k == L - 1 ? M : Mh, j, it, st, sm, tid);
+    ana_row(G, I.V, out, Sn, k == L - 1 ? M : Mh, j, it, st, sm, tid);
   }
 }
 
@@ -275,7 +275,10 @@ __host__ __device__ inline int item_floats(const Inst& I) {
   return line > 32 * 33 ? line : 32 * 33;
 }
 
-__global__ void __launch_bounds__(NTH) k_group(const Inst* __restrict__ insts, const Task* __restrict__ tasks,
+// MINB: CTAs per SM the register budget is sized for (2: no spills; 3: a
+// few spilled values, more lines in flight); the tuner picks
+template <int MINB>
+__global__ void __launch_bounds__(NTH, MINB) k_group(const Inst* __restrict__ insts, const Task* __restrict__ tasks,
                                                int ntasks, int* done, int* ticket, unsigned* err, unsigned spin,
                                                int fwd, int rad, const __grid_constant__ Ptrs ptrs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -321,10 +324,8 @@ __global__ void __launch_bounds__(NTH) k_group(const Inst* __restrict__ insts, c
       __syncthreads();
     }
     G.rad = rad;
-    Inst J = I;
-    J.G = G;
     for (int k = 0; k < tk.nitems; ++k) {
-      run_item(J, tk.phase, tk.item0 + k, fwd, ptrs.in[tk.inst], ptrs.out[tk.inst], st, sm + off, tid);
+      run_item(I, G, tk.phase, tk.item0 + k, fwd, ptrs.in[tk.inst], ptrs.out[tk.inst], st, sm + off, tid);
       __syncthreads();
     }
     if (tid == 0) {
@@ -382,8 +383,9 @@ static int pgroup_layout(PersistentGroup* g) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute((const void*)gk::k_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gk::k_group, gk::NTH, g->smem);
+  const void* fn = g->prm.ctas_per_sm == 2 ? (const void*)gk::k_group<2> : (const void*)gk::k_group<3>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, gk::NTH, g->smem);
   per = std::max(1, per);
   if (g->prm.ctas_per_sm > 0) per = std::min(per, g->prm.ctas_per_sm);
   g->grid = per * nsm;
@@ -473,8 +475,12 @@ int pgroup_run(PersistentGroup* g, bool fwd, const void* const* in, void* const*
     return UW_ERR_CUDA;
   }
   const int f = fwd ? 1 : 0;
-  gk::k_group<<<g->grid, gk::NTH, g->smem, s>>>(g->dinst, g->dtasks[f], g->ntasks[f], g->ddone, g->ddone + g->ncount, err,
-                                                group_spin_limit(), f, g->prm.rad, ptrs);
+  if (g->prm.ctas_per_sm == 2)
+    gk::k_group<2><<<g->grid, gk::NTH, g->smem, s>>>(g->dinst, g->dtasks[f], g->ntasks[f], g->ddone,
+                                                     g->ddone + g->ncount, err, group_spin_limit(), f, g->prm.rad, ptrs);
+  else
+    gk::k_group<3><<<g->grid, gk::NTH, g->smem, s>>>(g->dinst, g->dtasks[f], g->ntasks[f], g->ddone,
+                                                     g->ddone + g->ncount, err, group_spin_limit(), f, g->prm.rad, ptrs);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(UW_ERR_CUDA, std::string("persistent group launch failed: ") + cudaGetErrorString(e));

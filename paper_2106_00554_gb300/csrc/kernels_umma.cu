@@ -268,8 +268,13 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
   }
   for (int e = tid; e < 3 * 1536 / 8; e += 128 * GF)
     reinterpret_cast<uint4*>(sB1)[e] = __ldg(reinterpret_cast<const uint4*>(a.ops) + e);
+  // corrections transposed, sC[e][row]: the 32 lanes that compute 32 rows
+  // read consecutive words for each column e
   float* sC = reinterpret_cast<float*>(sm + OFF_C);
-  for (int e = tid; e < 2 * a.KB * 32 * 2 * a.p; e += 128 * GF) sC[e] = __ldg(a.corr + e);
+  {
+    const int rows = 2 * a.KB * 32, cols = 2 * a.p;
+    for (int e = tid; e < rows * cols; e += 128 * GF) sC[(e % cols) * rows + e / cols] = __ldg(a.corr + e);
+  }
   // window halos start zero (VMP: zero padding); periodic halos are rewritten per line
   for (int e = tid; e < GF * 6 * HANK_BYTES / 16; e += 128 * GF) {
     const int k = e / (6 * HANK_BYTES / 16), r = e % (6 * HANK_BYTES / 16);
@@ -333,13 +338,14 @@ __global__ void __launch_bounds__(128 * GF, 1) k_umma_fwd(const float* __restric
         float* sc = scorr + 256 * (it & 1);
         for (int c = wtid; c < 2 * a.KB * 32; c += 128) {
           const int side = c >= a.KB * 32;
-          const float* C = sC + c * 2 * a.p;
+          const int rows = 2 * a.KB * 32;
+          const float* C = sC + c;                   // column e at C[e * rows]
           const float* xl = stage + (side ? N0 - a.p : 0);
           float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll 8
           for (int e = 0; e < a.p; ++e) {
-            acc0 = fmaf(C[e], xl[e], acc0);
-            acc1 = fmaf(C[a.p + e], xl[N0 + e], acc1);
+            acc0 = fmaf(C[e * rows], xl[e], acc0);
+            acc1 = fmaf(C[(a.p + e) * rows], xl[N0 + e], acc1);
           }
           sc[c] = acc0 + acc1;
         }
@@ -650,26 +656,17 @@ __global__ void __launch_bounds__(128 * GA, 1) k_umma_adj(const float* __restric
       }
       mma_pend = 1;
       // VMP: corrections of this line's 4p edge outputs from its edge blocks' rows
-      // (8 lanes per output, combined with shuffles; every lane of a warp runs
-      // every round)
-      if (a.KB) {
-        for (int t0 = 0; t0 < 32 * a.p; t0 += 128) {
-          if (t0 + (wtid & ~31) >= 32 * a.p) break;     // warp-uniform: no lane of this warp has a task
-          const int t = t0 + wtid, oc = t >> 3, part = t & 7;
-          const bool act = t < 32 * a.p;
-          float acc = 0.f;
-          if (act) {
-            const int side = oc >= 2 * a.p, c = oc - side * 2 * a.p;
-            const int kp = a.KB * 4;                     // rows per lane
-            const float* C = sC + ((size_t)side * a.KB * 32 + part * kp) * 2 * a.p + c;
-            const float* ye = sye + side * a.KB * 32 + part * kp;
-            for (int k = 0; k < kp; ++k) acc = fmaf(C[k * 2 * a.p], ye[k], acc);
-          }
-          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-          acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-          if (act && part == 0) sco[64 * (it & 1) + oc] = acc;
+      // (one lane per output: for each row the lanes read consecutive columns)
+      if (a.KB && wtid < 4 * a.p) {
+        const int side = wtid >= 2 * a.p, c = wtid - side * 2 * a.p;
+        const float* C = sC + (size_t)side * a.KB * 32 * 2 * a.p + c;
+        const float* ye = sye + side * a.KB * 32;
+        float acc0 = 0.f, acc1 = 0.f;
+        for (int k = 0; k < a.KB * 32; k += 2) {
+          acc0 = fmaf(C[k * 2 * a.p], ye[k], acc0);
+          acc1 = fmaf(C[(k + 1) * 2 * a.p], ye[k + 1], acc1);
         }
+        sco[64 * (it & 1) + wtid] = acc0 + acc1;
       }
     }
     if (prev >= 0) {
