@@ -26,10 +26,11 @@
 //
 // CTAs are persistent (N / 16 threads, one 16-output block per thread) and
 // copy the next line (and its sample positions) into shared memory with
-// cp.async while the current line runs.  Shared-memory layouts are padded so
-// that the vector stores of (B), the pencils of (C) and the vector window
-// loads are free of bank conflicts; the Walsh butterflies use the packed
-// FP32x2 add of sm_100+.
+// cp.async while the current line runs.  The shared-memory layouts (padded
+// Walsh line, swizzled s line) and the lane orders keep every access but the
+// data-dependent gather / scatter free of bank conflicts: the vector stores
+// of (B), the pencils of (C), the vector window loads and the zeroing; the
+// Walsh butterflies use the packed FP32x2 add of sm_100+.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,10 +63,19 @@ struct Args {
   int L;            // log2 N
 };
 
-// Walsh line: element k at vp(k) (4 words of padding per 16, 16 per 256)
-__host__ __device__ __forceinline__ constexpr int vp(int k) { return k + 4 * (k >> 4) + 16 * (k >> 8); }
-// s line: 4 words of padding per 32
-__host__ __device__ __forceinline__ constexpr int sp(int m) { return m + 4 * (m >> 5); }
+// Walsh line: element k at vp(k), 4 words of padding per 16.  Consecutive
+// 16-blocks are 20 words apart, so any 8 consecutive blocks start in 8
+// different 4-bank groups (16-byte accesses of a quarter-warp never
+// conflict); 256-blocks are VCH = 320 words apart, 0 mod 32 banks.
+__host__ __device__ __forceinline__ constexpr int vp(int k) { return k + 4 * (k >> 4); }
+constexpr int VCH = 320;
+// s line.  Q = 2: every lane owns 8 consecutive s values, so a quarter-warp
+// reads or writes 16 bytes at a stride of 8 words; swapping the 4-word
+// groups of odd 32-word rows in pairs makes those 8 lanes cover all 32 banks
+// wherever the first lane starts.  Q = 4: 4 values per lane, the plain line
+// already spreads them over all banks.
+template <int Q>
+__host__ __device__ __forceinline__ constexpr int sp(int m) { return Q == 2 ? (m ^ (((m >> 5) & 1) << 2)) : m; }
 
 __host__ __device__ constexpr int up4(int a) { return (a + 3) / 4 * 4; }
 
@@ -81,7 +91,7 @@ struct Geom {
   static constexpr int HX = 8;               // coefficient halo (per side, per half)
   static constexpr int XL = 2 * (n0 + 2 * HX);   // one staged coefficient line (lo region, hi region)
   static constexpr int HS = up4(PM + 3);     // s halo
-  static constexpr int SL = up4(sp(M + 2 * HS - 1) + 1);
+  static constexpr int SL = up4(M + 2 * HS + 4);   // sp(m) <= m + 4
   // (A) synthesis window: lo[a0 - PM/2 + w'], loaded from an aligned start
   static constexpr int OFFX = ((HX - PM / 2) % VW + VW) % VW;
   static constexpr int NWX = (OFFX + BL + PM + VW - 1) / VW * VW;
@@ -94,7 +104,7 @@ struct Geom {
   // adjoint analysis window: s[2 i0 - PM + w']
   static constexpr int OFFA = ((HS - PM) % 4 + 4) % 4;
   static constexpr int NWA = up4(OFFA + 2 * BL + 2 * PM);
-  static constexpr int VH = 256;             // adjoint Walsh halo (keeps the padding pattern)
+  static constexpr int VH = 256;             // adjoint Walsh halo (whole 256-blocks)
   static constexpr int VLf = up4(vp(N - 1) + 1);
   // of the adjoint halo only the 16-blocks that T^T reads are allocated: HL
   // elements before the line, HR after it; the buffer starts at word VB of
@@ -139,18 +149,55 @@ __device__ __forceinline__ void wht(float (&a)[R]) {
       }
 }
 
+// wht<16> with the stage of bit 2 written as (a[k], a[k + 4]) <-
+// (sa a[k] + a[k + 4], a[k] - sa a[k + 4]) for k with bit 2 clear: sa = 1 is
+// the plain butterfly.  With sa = -1 and a[i] loaded from element i ^ 4 of
+// the pencil, register k ends holding output k ^ 4, bit for bit what the
+// plain transform of the natural order leaves in register k ^ 4 (the stage
+// only exchanges the two halves and negates one, both exact).
+__device__ __forceinline__ void wht16_x4(float (&a)[16], float sa) {
+#pragma unroll
+  for (int i = 0; i < 16; i += 2) {
+    const float x = a[i], y = a[i + 1];
+    a[i] = x + y;
+    a[i + 1] = x - y;
+  }
+  const float2 m1 = make_float2(-1.f, -1.f), s2 = make_float2(sa, sa), n2 = make_float2(-sa, -sa);
+#pragma unroll
+  for (int h = 2; h < 16; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < 16; i += 2)
+      if (!(i & h)) {
+        const float2 x = make_float2(a[i], a[i + 1]), y = make_float2(a[i + h], a[i + h + 1]);
+        const float2 lo = h == 4 ? __ffma2_rn(s2, x, y) : __fadd2_rn(x, y);
+        const float2 hi = h == 4 ? __ffma2_rn(n2, y, x) : __ffma2_rn(y, m1, x);
+        a[i] = lo.x;
+        a[i + 1] = lo.y;
+        a[i + h] = hi.x;
+        a[i + h + 1] = hi.y;
+      }
+}
+
 // One pencil of the bits-4..7 pass: elements low4 + 16 i + 256 h (i < 16) of
 // the line whose element k sits at V[vp(k + off)], off a multiple of 256.
 // With low4 < 16 their padded addresses are vp(low4 + 256 h + off) + 20 i.
+// Lanes 0-15 of a warp take the 16 pencils of one 256-block and lanes 16-31
+// those of the next, VCH = 0 mod 32 banks further: so the upper half-warp
+// visits its elements in the order i ^ 4 (80 words = 16 banks away) and
+// transforms them with wht16_x4, which hands back output i ^ 4 in register i
+// for the same store order.
 template <int NT>
 __device__ __forceinline__ void pass_mid(float* V, int off, int tid) {
+  const int up = (tid >> 4) & 1;
   float* b = V + vp((tid & 15) + 256 * (tid >> 4) + off);
+  float* bp = b + 80 * up;   // i with bit 2 clear: element i + 4 for the upper half-warp
+  float* bm = b - 80 * up;   // bit 2 set: element i - 4
   float a[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) a[i] = b[20 * i];
-  wht<16>(a);
+  for (int i = 0; i < 16; ++i) a[i] = ((i & 4) ? bm : bp)[20 * i];
+  wht16_x4(a, up ? -1.f : 1.f);
 #pragma unroll
-  for (int i = 0; i < 16; ++i) b[20 * i] = a[i];
+  for (int i = 0; i < 16; ++i) ((i & 4) ? bm : bp)[20 * i] = a[i];
 }
 
 // the lowest element of pencil c (< 256) of the bits-8.. pass: the two
@@ -162,7 +209,7 @@ __device__ __forceinline__ int high_pencil(int c) {
   return 16 * a + (c & 15);
 }
 
-// bits 8..L-1: 256 pencils e0 + 256 i (e0 < 256), at vp(e0 + off) + 336 i
+// bits 8..L-1: 256 pencils e0 + 256 i (e0 < 256), at vp(e0 + off) + VCH i
 template <int NT>
 __device__ __forceinline__ void pass_high(float* V, int off, int tid) {
   constexpr int N = 16 * NT, RH = N / 256;
@@ -171,10 +218,10 @@ __device__ __forceinline__ void pass_high(float* V, int off, int tid) {
     float* b = V + vp(high_pencil(c) + off);
     float a[RH];
 #pragma unroll
-    for (int i = 0; i < RH; ++i) a[i] = b[336 * i];
+    for (int i = 0; i < RH; ++i) a[i] = b[VCH * i];
     wht<RH>(a);
 #pragma unroll
-    for (int i = 0; i < RH; ++i) b[336 * i] = a[i];
+    for (int i = 0; i < RH; ++i) b[VCH * i] = a[i];
   }
 }
 
@@ -335,13 +382,13 @@ __global__ void __launch_bounds__(NT, 3) k_f32_fwd(const float* __restrict__ in,
       const int m0 = BS * tid;
 #pragma unroll
       for (int j = 0; j < BS; j += 4)
-        *reinterpret_cast<float4*>(sS + sp(HS + m0 + j)) = make_float4(s[j], s[j + 1], s[j + 2], s[j + 3]);
+        *reinterpret_cast<float4*>(sS + sp<Q>(HS + m0 + j)) = make_float4(s[j], s[j + 1], s[j + 2], s[j + 3]);
       if (a.per) {
 #pragma unroll
         for (int j = 0; j < BS; ++j) {
           const int m = m0 + j;
-          if (m < HS) sS[sp(HS + M + m)] = s[j];
-          if (m >= M - HS) sS[sp(HS + m - M)] = s[j];
+          if (m < HS) sS[sp<Q>(HS + M + m)] = s[j];
+          if (m >= M - HS) sS[sp<Q>(HS + m - M)] = s[j];
         }
       }
     }
@@ -375,7 +422,7 @@ __global__ void __launch_bounds__(NT, 3) k_f32_fwd(const float* __restrict__ in,
       float ws[G::NWB];
 #pragma unroll
       for (int w = 0; w < G::NWB; w += 4) {
-        const float4 u = *reinterpret_cast<const float4*>(sS + sp(j0 + w));
+        const float4 u = *reinterpret_cast<const float4*>(sS + sp<Q>(j0 + w));
         ws[w] = u.x; ws[w + 1] = u.y; ws[w + 2] = u.z; ws[w + 3] = u.w;
       }
       float v[16];
@@ -429,7 +476,7 @@ __global__ void __launch_bounds__(NT, 3) k_f32_fwd(const float* __restrict__ in,
         const float* src = sV + vp(e0);
         float v[RH];
 #pragma unroll
-        for (int i = 0; i < RH; ++i) v[i] = src[336 * i];
+        for (int i = 0; i < RH; ++i) v[i] = src[VCH * i];
         wht<RH>(v);
 #pragma unroll
         for (int i = 0; i < RH; ++i) dst[e0 + 256 * i] = v[i];
@@ -516,12 +563,12 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
     float* sV = sV0 + (scat ? 0 : buf * G::VLa) - G::VB;
     if (scat) {
       // zero the line, then scatter the staged samples to their natural positions
-      {
-        // element 4 (tid + NT i) sits at vp(VH + 4 tid) + 4 NT i (1 + 1/4 + 1/16): NT i is a multiple of 256
-        float* z = sV + vp(VH + 4 * tid);
+      // 4-word chunk c = r-th of 16-block (c & 7) + 8 (c >> 5), r = (c >> 3) & 3:
+      // the 8 lanes of a quarter-warp write 8 consecutive blocks
 #pragma unroll
-        for (int i = 0; i < N / (4 * NT); ++i)
-          *reinterpret_cast<float4*>(z + vp(4 * NT * i)) = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < N / (4 * NT); ++i) {
+        const int c = NT * i + tid, blk = (c & 7) + 8 * (c >> 5), r = (c >> 3) & 3;
+        *reinterpret_cast<float4*>(sV + vp(VH + 16 * blk + 4 * r)) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncthreads();
       const uint16_t* ps = reinterpret_cast<const uint16_t*>(sP) + (cr0 & 1);
@@ -624,13 +671,13 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
       }
 #pragma unroll
       for (int j = 0; j < BS; j += 4)
-        *reinterpret_cast<float4*>(sS + sp(HS + m0 + j)) = make_float4(s[j], s[j + 1], s[j + 2], s[j + 3]);
+        *reinterpret_cast<float4*>(sS + sp<Q>(HS + m0 + j)) = make_float4(s[j], s[j + 1], s[j + 2], s[j + 3]);
       if (a.per) {
 #pragma unroll
         for (int j = 0; j < BS; ++j) {
           const int m = m0 + j;
-          if (m < HS) sS[sp(HS + M + m)] = s[j];
-          if (m >= M - HS) sS[sp(HS + m - M)] = s[j];
+          if (m < HS) sS[sp<Q>(HS + M + m)] = s[j];
+          if (m >= M - HS) sS[sp<Q>(HS + m - M)] = s[j];
         }
       }
     }
@@ -642,7 +689,7 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
       float ws[G::NWA];
 #pragma unroll
       for (int w = 0; w < G::NWA; w += 4) {
-        const float4 u = *reinterpret_cast<const float4*>(sS + sp(j0 + w));
+        const float4 u = *reinterpret_cast<const float4*>(sS + sp<Q>(j0 + w));
         ws[w] = u.x; ws[w + 1] = u.y; ws[w + 2] = u.z; ws[w + 3] = u.w;
       }
       float lo[BL], hi[BL];

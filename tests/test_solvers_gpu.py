@@ -179,6 +179,45 @@ def test_fista_reduces_the_objective_on_the_benchmark_shape_split_bf16():
     assert np.isfinite(float(lt.grad))
 
 
+@pytest.mark.parametrize("bd_name", ["periodic", "vmp"])
+def test_periodic_vs_vmp_reconstructions_fig4(bd_name):
+    """The periodic-versus-boundary comparison of Sec. 3.2 (Fig. 4) on the
+    GPU: f(t) = cos(2 pi t) and g(t) = cos(2 pi t) + t from their first 32
+    Walsh samples, generalised sampling in M = 16 DB4 functions (R = 4, q = 1)
+    with the plan's boundary extension, solved by CG on the normal equations
+    through the library's 1D products.  Each solution matches the oracle's
+    least-squares fit, and the errors of the GPU solutions show what the
+    figure's caption states (the oracle pins the same in
+    tests/test_oracle_fig4.py): periodic wavelets fit the periodic f and leave
+    boundary artefacts on g; VMP wavelets fit g, with the same error as f
+    since g - f = t lies in their span."""
+    from oracle import dense, wavelets as W
+    from paper_2106_00554_gb300 import F64, PERIODIC, VMP, Plan, solvers
+    import test_oracle_fig4 as fig4
+
+    bd = PERIODIC if bd_name == "periodic" else VMP
+    R, q, p = fig4.R, fig4.Q, fig4.P
+    plan = Plan(1, R, q, p, bd)
+    A = dense.U1d_scaling(R, q, p, bd)
+    out = {}
+    for name in ("f", "g"):
+        c = fig4.samples(name)
+        x, iters, res = solvers.cg_normal(plan, torch.tensor(c, dtype=torch.float64, device="cuda"), iters=100,
+                                          tol=1e-14)
+        x = x.cpu().numpy()
+        want = W.dwt1d(np.linalg.lstsq(A, c, rcond=None)[0], plan.J0, p, bd)   # wavelet-basis coefficients
+        assert np.linalg.norm(x - want) < 1e-10 * np.linalg.norm(want), (name, iters, res)
+        z = W.idwt1d(x, plan.J0, p, bd)                                           # scaling-basis coefficients
+        out[name] = fig4.errors(name, z, bd)
+    (rel_f, d_f, eb_f, ei_f), (rel_g, d_g, eb_g, ei_g) = out["f"], out["g"]
+    if bd == PERIODIC:
+        assert rel_f < 2e-3 and eb_f < 2 * ei_f, (rel_f, eb_f, ei_f)
+        assert rel_g > 2e-2 and eb_g > 5 * ei_g, (rel_g, eb_g, ei_g)
+    else:
+        assert rel_g < 5e-3 and eb_g < 3 * ei_g, (rel_g, eb_g, ei_g)
+        assert np.max(np.abs(d_g - d_f)) < 1e-9, np.max(np.abs(d_g - d_f))
+
+
 def test_generalised_sampling_example2_db2():
     """Generalised sampling of the paper's Example 2 (Sec. 6) on the GPU:
     f(t1, t2) = cos(3 pi t1 / 2) sin(3 pi t2) from its 32 x 32 first Walsh
