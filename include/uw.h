@@ -201,13 +201,24 @@ int uw_adjoint_host(const uw_plan* plan, int precision, const void* y_host, void
  * the download of call k-1 therefore run while the product of call k runs.
  * Products run in call order (they share the plan's workspace).
  *
+ * The product of step 2 is launched as a CUDA graph: the first call for a
+ * (direction, precision, slot) captures it on a stream of the plan's own and
+ * later calls replay it.  A call captures anew when anything the graph was
+ * built from differs: the batch, the mask, the coarsest level, the reserved
+ * buffers, membership of a plan group, the group tuner's kernel choice, or
+ * the UW_* launch switches in the environment.  While the per-kernel
+ * profiler is on (uw_plan_profile), or if the driver refuses the capture,
+ * the kernels are launched one by one as by uw_forward / uw_adjoint.  The
+ * first call of each kind therefore costs a capture: make it before
+ * timing, and not while another capture is active on this thread.
+ *
  * Host buffers must be pinned for the copies to be asynchronous.  They must
  * stay valid until uw_host_wait returns: inputs unchanged, outputs not read.
  * The same input buffer may be passed to several calls.
  *
  * Errors: the same argument checks as uw_forward_host (UW_ERR_INVALID_ARG);
- * UW_ERR_OOM if the plan's copy streams or events cannot be created;
- * UW_ERR_CUDA if a copy cannot be enqueued.
+ * UW_ERR_OOM if the plan's copy or capture streams or events cannot be
+ * created; UW_ERR_CUDA if a copy or the graph launch cannot be enqueued.
  */
 int uw_forward_host_async(const uw_plan* plan, int precision, const void* x_host, void* y_host,
                           int batch, void* stream);

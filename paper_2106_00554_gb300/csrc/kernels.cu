@@ -2513,11 +2513,13 @@ int uw_adjoint_host(const uw_plan* P, int prec, const void* y, void* x, int batc
 // copy streams and per-slot events of the asynchronous host calls (created once)
 static int host_async_init(uw_plan* P) {
   if (P->s_up) return UW_OK;
-  cudaStream_t up = nullptr, down = nullptr;
+  cudaStream_t up = nullptr, down = nullptr, cap = nullptr;
   if (cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     if (up) cudaStreamDestroy(up);
+    if (down) cudaStreamDestroy(down);
     uw::set_error(UW_ERR_OOM, "copy stream creation failed");
     return UW_ERR_OOM;
   }
@@ -2529,12 +2531,78 @@ static int host_async_init(uw_plan* P) {
         uw::set_error(UW_ERR_OOM, "event creation failed");
         cudaStreamDestroy(up);
         cudaStreamDestroy(down);
+        cudaStreamDestroy(cap);
         return UW_ERR_OOM;
       }
       e = ev;
     }
   P->s_up = up;
   P->s_down = down;
+  P->s_cap = cap;
+  return UW_OK;
+}
+
+// the UW_* switches that change which kernels a product launches or their
+// parameters
+static std::string launch_env() {
+  static const char* const names[] = {"UW_BARRIER_SPIN_LIMIT", "UW_COARSE_GENERIC", "UW_COARSE_PER_LEVEL",
+                                      "UW_COARSE_SEPARATE_TRANSPOSE", "UW_GENERIC_LINES", "UW_NO_UMMA",
+                                      "UW_TC_SPIN_LIMIT", "UW_TC_THREADS"};
+  std::string sig;
+  for (const char* n : names) {
+    const char* v = getenv(n);
+    sig += v ? v : "\x01";
+    sig += '\x02';
+  }
+  return sig;
+}
+
+// The product of an asynchronous host call on stream s.  Replayed as a CUDA
+// graph captured at the first call with the same signature (a graph's
+// launches are fixed: new buffers, mask, coarsest level, group membership,
+// line variant or launch switches capture anew); eager while the profiler
+// is on or if the capture failed.
+static int host_product(uw_plan* P, int prec, bool fwd, const void* din, void* dout, int batch, int slot,
+                        cudaStream_t s) {
+  auto eager = [&]() {
+    return fwd ? uw_forward(P, prec, din, dout, batch, s) : uw_adjoint(P, prec, din, dout, batch, s);
+  };
+  if (P->prof && P->prof->on) return eager();
+  uw::HostGraph key;
+  key.fwd = fwd; key.prec = prec; key.slot = slot; key.batch = batch; key.J0 = P->J0;
+  key.line_variant = P->line_variant; key.coarse_mode = P->coarse_mode; key.grouped = P->group != nullptr;
+  key.m = P->m; key.work = P->d_work; key.stage = P->d_stage; key.mask = P->d_mask; key.pos = P->d_pos;
+  key.env = launch_env();
+  uw::HostGraph* g = nullptr;
+  for (auto& h : P->hgraphs)
+    if (h.fwd == key.fwd && h.prec == key.prec && h.slot == key.slot) g = &h;
+  if (!g) {
+    P->hgraphs.push_back(key);
+    g = &P->hgraphs.back();
+  } else if (!g->same(key)) {
+    if (g->exec) cudaGraphExecDestroy((cudaGraphExec_t)g->exec);
+    *g = key;
+  }
+  if (!g->tried) {
+    // capture once, on the plan's own stream
+    g->tried = true;
+    cudaStream_t cs = (cudaStream_t)P->s_cap;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int st = fwd ? uw_forward(P, prec, din, dout, batch, cs) : uw_adjoint(P, prec, din, dout, batch, cs);
+      const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+      if (st == UW_OK && ce == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
+        g->exec = exec;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();   // a refused capture leaves the eager path
+  }
+  if (!g->exec) return eager();
+  if (cudaGraphLaunch((cudaGraphExec_t)g->exec, s) != cudaSuccess) {
+    uw::set_error(UW_ERR_CUDA, "graph launch failed");
+    return UW_ERR_CUDA;
+  }
   return UW_OK;
 }
 
@@ -2568,7 +2636,7 @@ static int host_call_async(const uw_plan* Pc, int prec, bool fwd, const void* in
     uw::set_error(UW_ERR_CUDA, "stream wait failed");
     return UW_ERR_CUDA;
   }
-  st = fwd ? uw_forward(P, prec, din, dout, batch, stream) : uw_adjoint(P, prec, din, dout, batch, stream);
+  st = host_product(P, prec, fwd, din, dout, batch, k, s);
   if (st != UW_OK) return st;
   if (cudaEventRecord(ev_prod, s) != cudaSuccess || cudaStreamWaitEvent(down, ev_prod, 0) != cudaSuccess ||
       cudaMemcpyAsync(out, dout, nout * e, cudaMemcpyDeviceToHost, down) != cudaSuccess ||

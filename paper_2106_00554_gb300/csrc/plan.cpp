@@ -879,6 +879,9 @@ void uw_plan_destroy(uw_plan* P) {
       if (e) cudaEventDestroy((cudaEvent_t)e);
   if (P->s_up) cudaStreamDestroy((cudaStream_t)P->s_up);
   if (P->s_down) cudaStreamDestroy((cudaStream_t)P->s_down);
+  for (auto& g : P->hgraphs)
+    if (g.exec) cudaGraphExecDestroy((cudaGraphExec_t)g.exec);
+  if (P->s_cap) cudaStreamDestroy((cudaStream_t)P->s_cap);
   uw::profiler_free(*P);
   cudaFree(P->d_tab64);
   cudaFree(P->d_tab32);

@@ -9,6 +9,22 @@
 
 namespace uw {
 
+// A captured product of an asynchronous host call, and everything its
+// launches were built from: a call whose signature differs captures anew.
+struct HostGraph {
+  int fwd = 0, prec = 0, slot = 0, batch = 0, J0 = 0, line_variant = 0, coarse_mode = 0, grouped = 0;
+  int64_t m = 0;
+  const void *work = nullptr, *stage = nullptr, *mask = nullptr, *pos = nullptr;
+  std::string env;        // the UW_* launch switches in force at capture
+  bool tried = false;     // captured (or the capture was refused) for this signature
+  void* exec = nullptr;   // cudaGraphExec_t; null after a refused capture: run eagerly
+  bool same(const HostGraph& o) const {
+    return fwd == o.fwd && prec == o.prec && slot == o.slot && batch == o.batch && J0 == o.J0 &&
+           line_variant == o.line_variant && coarse_mode == o.coarse_mode && grouped == o.grouped && m == o.m &&
+           work == o.work && stage == o.stage && mask == o.mask && pos == o.pos && env == o.env;
+  }
+};
+
 // Device-side view of the input-independent tables, one copy per precision.
 // Everything is indexed exactly like the host vectors of Plan below.
 template <typename T>
@@ -71,8 +87,8 @@ struct F32Geo {
 // k = 32 b + r.  Forward: D1[b][r] = sum_j W[b][j] B1[r][j] with the window
 // W[b][j] = lo[8 b - 8 + j] (j < 24), hi[8 b - 32 + j] (j >= 24), and B1 the
 // last synthesis level, T and the Walsh-Hadamard stages of bits 0-4 of one
-// block; then D2 = H_128 D1 (bits 5-11).  The adjoint applies the
-// transposes.  Near a VMP boundary the exact operator differs from the
+// block; the stages of bits 5-11 across the blocks follow on the CUDA
+// cores.  The adjoint applies the transposes.  Near a VMP boundary the exact operator differs from the
 // windowed interior one by a correction that reads only the p lo and p hi
 // coefficients at that end and reaches only the first / last KB blocks.
 // Device buffer d_umma: three BF16 parts of B1 (forward B operand, K-major,
@@ -119,6 +135,10 @@ struct Plan {
   void* s_down = nullptr;
   void* ev[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   int slot = 0;
+  // the products of the asynchronous host calls as CUDA graphs, captured on
+  // s_cap at first use and replayed while nothing they depend on changed
+  void* s_cap = nullptr;
+  std::vector<HostGraph> hgraphs;
   // launch choices (a plan group and its tuner set them): line operators
   // 0 = the fastest specialised kernel that applies, 1 = the generic kernels;
   // coarse 2D levels 0 = one cooperative launch, 1 = one launch per level

@@ -389,6 +389,46 @@ def test_host_async_pipeline_matches_device(prec, batch):
     assert rel(ysync.numpy(), yo[3].numpy()) < tol
 
 
+def test_host_async_graphs_follow_plan_changes(monkeypatch):
+    """The asynchronous host calls replay their products as CUDA graphs
+    captured at first use; a change of anything a graph was built from
+    (mask, reserved buffers, coarsest level, launch switches) must capture
+    anew.  After each change the asynchronous result equals the device API's
+    for the changed plan (and the FP64 oracle's)."""
+    rng = np.random.default_rng(11)
+    R, q, p = 7, 1, 4
+    N = 2 ** (R + q)
+    omega = inputs.mask_2d(rng, N, 0.2)
+    plan = Plan(2, R, q, p, VMP, omega=omega)
+    x = torch.tensor(rng.standard_normal((2 ** R, 2 ** R)), dtype=torch.float32).pin_memory()
+
+    def check(batch=1, xin=None):
+        xin = x if xin is None else xin
+        out = torch.empty((batch, plan.m) if batch > 1 else plan.m, dtype=torch.float32).pin_memory()
+        for _ in range(3):                       # first call captures, the next ones replay
+            plan.forward_host_async(xin.data_ptr(), out.data_ptr(), F32, batch)
+        plan.host_wait()
+        want = dense.forward2d(xin.double().numpy(), R, q, p, VMP, plan.J0, plan_omega[0])
+        assert rel(out.numpy(), run_fwd(plan, xin.numpy(), F32)) < 1e-6
+        assert rel(out.numpy(), want) < 1e-5
+
+    plan_omega = [omega]
+    check()
+    omega2 = inputs.mask_2d(rng, N, 0.35)        # another mask: another m, positions, prefix
+    plan.set_mask(omega2)
+    plan_omega[0] = omega2
+    check()
+    plan.reserve(2)                              # new workspace and staging buffers
+    xb = torch.tensor(rng.standard_normal((2, 2 ** R, 2 ** R)), dtype=torch.float32).pin_memory()
+    check(batch=2, xin=xb)
+    check()
+    from paper_2106_00554_gb300 import _lib
+    _lib.uw_plan_set_coarsest(plan._h, plan.J0 + 1)   # one coarse level fewer
+    check()
+    monkeypatch.setenv("UW_GENERIC_LINES", "1")        # other line kernels
+    check()
+
+
 def test_dot_product_2d_fp64():
     rng = np.random.default_rng(6)
     R, q, p = 7, 2, 4
