@@ -18,6 +18,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "uw_internal.h"
@@ -592,7 +593,7 @@ static void side_blocks(int p, bool left, const std::vector<LD>& h, const Gram& 
     }
 }
 
-bool build_tables(Plan& P, std::string& err) {
+static bool build_tables_uncached(Plan& P, std::string& err) {
   const int p = P.p, q = P.q, Q = 1 << q;
   P.Q = Q;
   P.Lb = 3 * p - 1;
@@ -642,6 +643,35 @@ bool build_tables(Plan& P, std::string& err) {
   P.QL.assign(ql.begin(), ql.end());
   P.PR.assign(pr.begin(), pr.end());
   P.QR.assign(qr.begin(), qr.end());
+  return true;
+}
+
+// The tables depend on (p, q, filter family) only and take up to ~0.1 s to
+// build at p = 10: they are built once per process and copied into every
+// later plan with the same three.
+bool build_tables(Plan& P, std::string& err) {
+  struct Set {
+    std::vector<double> h, g, taps, EL, ER, PL, QL, PR, QR;
+  };
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, Set> cache;
+  const auto key = std::make_tuple(P.p, P.q, P.family);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      const Set& c = it->second;
+      P.Q = 1 << P.q;
+      P.Lb = 3 * P.p - 1;
+      P.ntap = (2 * P.p - 1) * P.Q;
+      P.h = c.h; P.g = c.g; P.taps = c.taps; P.EL = c.EL; P.ER = c.ER;
+      P.PL = c.PL; P.QL = c.QL; P.PR = c.PR; P.QR = c.QR;
+      return true;
+    }
+  }
+  if (!build_tables_uncached(P, err)) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  cache.emplace(key, Set{P.h, P.g, P.taps, P.EL, P.ER, P.PL, P.QL, P.PR, P.QR});
   return true;
 }
 
@@ -814,6 +844,12 @@ int uw_plan_reserve(uw_plan* P, int max_batch) {
   // bytes per staging slot, a multiple of 256 so that the second slot keeps
   // the alignment of the first (the line kernels copy 16-byte chunks)
   size_t sb = ((size_t)max_batch * (size_t)(coeffs + P->m) * sizeof(double) + 512 + 255) & ~(size_t)255;
+  if (P->d_stage && wb <= P->work_bytes && sb <= P->stage_bytes) {
+    // the buffers already hold this batch (a smaller mask after the default
+    // one, or a smaller batch): keep them, and their slot stride
+    P->max_batch = max_batch;
+    return UW_OK;
+  }
   void* w = nullptr;
   void* s = nullptr;
   if (wb && cudaMalloc(&w, wb) != cudaSuccess) { cudaGetLastError(); return fail(UW_ERR_OOM, "workspace allocation failed"); }
