@@ -766,6 +766,11 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": ("profiles/traffic.md: dram__bytes_read.sum + dram__bytes_write.sum of this "
+                                        "kernel from a committed ncu capture of the same bench workload, taken on "
+                                        "the kernel's current sources (source hash " + kernel_source_hash(dom["name"])
+                                        + "); not measured in this run" if traffic is not None else
+                                        "no committed ncu capture of this kernel's current sources"),
                      "peak_kind": (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                                    else "fallback 6.8 TB/s")},
         "pipeline_roofline": {"compulsory_bytes_per_pair": comp, "two_pass_bytes_per_pair": twopass,
