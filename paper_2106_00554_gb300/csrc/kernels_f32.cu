@@ -313,6 +313,26 @@ __global__ void __launch_bounds__(NT, 3) k_f32_fwd(const float* __restrict__ in,
     }
   };
 
+  // VMP edge corrections of T with their weights in registers (they are the
+  // same for every line; read per line from global memory they put an L2
+  // round trip between two barriers of every line): thread t < 4K takes the
+  // lo (t even) or hi (t odd) half of row t / 2 of C, p weights, and the two
+  // halves of a row meet on adjacent lanes.  Other shapes read C per line.
+  const bool creg = a.K && PM <= 8 && 4 * a.K <= NT;
+  float cw[PM <= 8 ? PM : 1];
+  int coff = 0, crow = 0;
+  bool cact = false;
+  if (creg) {
+    cact = tid < 4 * a.K;
+    crow = tid >> 1;
+    const int half = tid & 1, side = crow >= a.K, r = crow - side * a.K;
+    // offset of this half's first edge coefficient from lo[-HX] of a staged line
+    coff = half * (n0 + 2 * HX) + HX + (side == 0 ? 0 : n0 - a.p);
+#pragma unroll
+    for (int k = 0; k < (PM <= 8 ? PM : 1); ++k)
+      cw[k] = (cact && k < a.p) ? __ldg(a.C + (size_t)(side * a.K + r) * a.CS + half * a.p + k) : 0.f;
+  }
+
   // cp.async groups, oldest first: in(line), pos(line), in(next), ... ; the
   // sample positions of a line are copied while the previous line's gather
   // is done, and awaited just before this line's gather
@@ -394,7 +414,15 @@ __global__ void __launch_bounds__(NT, 3) k_f32_fwd(const float* __restrict__ in,
     }
     // VMP edge corrections of T: one row of C (2p weights) per task, rows of
     // both ends spread over the CTA
-    if (a.K) {
+    if (creg) {
+      if (tid < ((4 * a.K + 31) & ~31)) {      // warp-uniform: the warps that hold weights
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < (PM <= 8 ? PM : 1); ++k) acc = fmaf(cw[k], xl[coff + k], acc);   // cw = 0 past p
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (cact && !(tid & 1)) sCorr[crow] = acc;
+      }
+    } else if (a.K) {
       for (int t = tid; t < 2 * a.K; t += NT) {
         const int side = t >= a.K, r = t - side * a.K;
         const float4* crow = reinterpret_cast<const float4*>(a.C + ((size_t)side * a.K + r) * a.CS);
@@ -530,6 +558,27 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
     }
   };
 
+  // VMP: C^T on the first / last K transformed samples, with the weights in
+  // registers (the same for every line; read per line from global memory
+  // they put an L2 round trip between two barriers of every line).  Output
+  // oc (side, column) is split into 8 parts of K/8 rows on 8 consecutive
+  // lanes; thread t < 32p holds part t & 7 of output t >> 3.  Other shapes
+  // read C per line.
+  const bool creg = a.K && 32 * PM <= NT && a.K <= 64;
+  float cw[8];
+  int cv0 = 0, coc = 0;
+  bool cact = false;
+  if (creg) {
+    const int kp = a.K / 8, part = tid & 7;
+    cact = tid < 32 * a.p;
+    coc = tid >> 3;
+    const int side = coc >= 2 * a.p, c = coc - side * 2 * a.p;
+    cv0 = (side == 0 ? 0 : N - a.K) + part * kp;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      cw[k] = (cact && k < kp) ? __ldg(a.C + ((size_t)side * a.K + (size_t)part * kp + k) * a.CS + c) : 0.f;
+  }
+
   pdl_trigger();
   pdl_wait();
   const int G0 = gridDim.x;
@@ -613,7 +662,24 @@ __global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in,
     // VMP: C^T on the first / last K transformed samples.  Output oc (side,
     // column) is split into 8 parts of K/8 rows on 8 consecutive lanes,
     // combined with shuffles (every lane of a warp runs every round).
-    if (a.K) {
+    if (creg) {
+      if (tid < ((32 * a.p + 31) & ~31)) {      // warp-uniform: the warps that hold weights
+        float acc = 0.f;
+        if (a.K == 64 && (cv0 & 7) == 0) {        // 8 rows, an aligned run inside one 16-block
+          const float* v = sV + vp(VH + cv0);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc = fmaf(cw[k], v[k], acc);
+        } else {
+          // cw = 0 past K/8 rows; those reads stay in the line or its zero halo
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc = fmaf(cw[k], sV[vp(VH + cv0 + k)], acc);
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (cact && (lane & 7) == 0) sCorr[coc] = acc;
+      }
+    } else if (a.K) {
       const int ntask = 32 * a.p, kp = a.K / 8;
       for (int t0 = 0; t0 < ntask; t0 += NT) {
         if (t0 + (tid & ~31) >= ntask) break;        // warp-uniform: no lane of this warp has a task
