@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(NT, 3) k_f32_fwd(const float* __restrict__ in,
 // adjoint
 // ---------------------------------------------------------------------------
 template <int PM, int Q, int NT>
-__global__ void __launch_bounds__(NT, 3) k_f32_adj(const float* __restrict__ in, float* __restrict__ out, Args a,
+__global__ void __launch_bounds__(NT, 4) k_f32_adj(const float* __restrict__ in, float* __restrict__ out, Args a,
                                                    Taps<PM, Q> tp, LineIO io, int total) {
   using G = Geom<PM, Q, NT>;
   constexpr int N = G::N, M = G::M, n0 = G::n0, BS = G::BS, BL = G::BL, HS = G::HS, VH = G::VH;
