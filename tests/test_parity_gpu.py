@@ -443,7 +443,8 @@ def test_dot_product_2d_fp64():
 
 
 F32_LINE_CASES = [(1, PERIODIC, 10, 1), (2, VMP, 10, 1), (3, VMP, 9, 2), (5, PERIODIC, 9, 2), (8, VMP, 10, 1),
-                  (9, VMP, 9, 2), (10, PERIODIC, 10, 1), (10, VMP, 10, 1), (4, VMP, 10, 2), (7, PERIODIC, 10, 2)]
+                  (9, VMP, 9, 2), (10, PERIODIC, 10, 1), (10, VMP, 10, 1), (4, VMP, 10, 2), (7, PERIODIC, 10, 2),
+                  (8, VMP, 10, 2), (6, VMP, 10, 2)]
 
 
 @pytest.mark.parametrize("p,bd,R,q", F32_LINE_CASES)
@@ -451,7 +452,10 @@ def test_fp32_persistent_line_kernels(p, bd, R, q):
     """UW_F32 on lines of N = 2048 and 4096 samples: the persistent FP32 line
     operators (interior formulas with zero or wrapped halos, VMP edges as
     small corrections) against the dense oracle, both boundary types, q = 1
-    and 2, batch 2, natural-order and sampled passes."""
+    and 2, batch 2, natural-order and sampled passes.  The VMP cases take
+    both ways of applying the edge corrections: weights held in registers
+    (p <= 4 at N = 2048; p <= 8 at N = 4096) and weights read per line
+    (p >= 5 at N = 2048, p = 9, 10)."""
     from paper_2106_00554_gb300 import _lib
     rng = np.random.default_rng(4000 + 10 * p + bd + q)
     J0 = W.default_J0(p)
