@@ -129,6 +129,111 @@ __global__ void k_ana_level(const T* __restrict__ in, T* __restrict__ out, int n
   }
 }
 
+// 1D lines longer than one CTA's shared memory, batched along blockIdx.x
+// (one line per CTA): the coarse synthesis levels J0 .. jto-1 of a line in
+// shared memory (Sec. 3.2, the Mallat IDWT), ping-ponging between two
+// buffers of 2^(jto-1).  Level j reads s_j from shared memory (the
+// coarsest block from x) and the details d_j = x[2^j, 2^(j+1)) from global
+// memory; the last of these levels writes s_jto to out[0, 2^jto) of the line.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_syn1d_levels(const T* __restrict__ x, T* __restrict__ out, int64_t out_bs,
+                                                       Tables<T> tab, Geo G, int J0, int jto, int64_t in_bs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<T> st;
+  const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
+  const T* xb = x + (int64_t)blockIdx.x * in_bs;
+  T* ob = out + (int64_t)blockIdx.x * out_bs;
+  T* P0 = sm + ((off + 3) & ~3);
+  T* P1 = P0 + (1 << (jto - 1));
+  for (int k = tid; k < (1 << J0); k += nthr) P0[k] = xb[k];
+  __syncthreads();
+  T* src = P0;
+  T* dst = P1;
+  for (int j = J0; j < jto; ++j) {
+    const int n0 = 1 << j;
+    Plain<T> lo{src}, hi{xb + n0};
+    T* o = j + 1 == jto ? ob : dst;
+    for (int k = tid; k < 2 * n0; k += nthr) o[k] = syn_one<T>(k, n0, lo, hi, st, G);
+    __syncthreads();
+    T* t = src;
+    src = dst;
+    dst = t;
+  }
+}
+
+// The transposed steps: the analysis levels jfrom-1 .. J0 of a line.  The
+// first reads s_jfrom from in[0, 2^jfrom) of the line; every level writes
+// its details d_j to x[2^j, 2^(j+1)) and its s_j to shared memory, the last
+// one s_J0 to x[0, 2^J0).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_ana1d_levels(const T* __restrict__ in, int64_t in_bs, T* __restrict__ x,
+                                                       Tables<T> tab, Geo G, int J0, int jfrom, int64_t out_bs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<T> st;
+  const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
+  const T* ib = in + (int64_t)blockIdx.x * in_bs;
+  T* xb = x + (int64_t)blockIdx.x * out_bs;
+  T* P0 = sm + ((off + 3) & ~3);
+  T* P1 = P0 + (1 << (jfrom - 1));
+  const T* src = ib;
+  T* dst = P0;
+  for (int j = jfrom - 1; j >= J0; --j) {
+    const int n0 = 1 << j;
+    Plain<T> s{src};
+    T* lo_out = j == J0 ? xb : dst;
+    for (int m = tid; m < n0; m += nthr) {
+      T lo, hi;
+      ana_one<T>(m, n0, s, st, G, lo, hi);
+      lo_out[m] = lo;
+      xb[n0 + m] = hi;
+    }
+    __syncthreads();
+    src = dst;
+    dst = dst == P0 ? P1 : P0;
+  }
+}
+
+// One synthesis level of a batch of 1D lines with the low-pass and detail
+// inputs in separate arrays: out[k] = Syn(lo, hi)[k], k < 2 n0.
+template <typename T>
+__global__ void k_syn1d_level(const T* __restrict__ lo, int64_t lo_bs, const T* __restrict__ hi, int64_t hi_bs,
+                              T* __restrict__ out, int64_t out_bs, int n0, Tables<T> t, Geo G, int batch) {
+  const int64_t total = (int64_t)batch * 2 * n0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % (2 * n0));
+    const int64_t b = idx / (2 * n0);
+    Plain<T> l{lo + b * lo_bs}, h{hi + b * hi_bs};
+    out[b * out_bs + k] = syn_one<T>(k, n0, l, h, t, G);
+  }
+}
+
+// One analysis level of a batch of 1D lines: lo to one array, the details
+// hi to another.
+template <typename T>
+__global__ void k_ana1d_level(const T* __restrict__ in, int64_t in_bs, T* __restrict__ lo, int64_t lo_bs,
+                              T* __restrict__ hi, int64_t hi_bs, int n0, Tables<T> t, Geo G, int batch) {
+  const int64_t total = (int64_t)batch * n0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(idx % n0);
+    const int64_t b = idx / n0;
+    Plain<T> s{in + b * in_bs};
+    T l, h;
+    ana_one<T>(m, n0, s, t, G, l, h);
+    lo[b * lo_bs + m] = l;
+    hi[b * hi_bs + m] = h;
+  }
+}
+
 template <typename T>
 __global__ void k_up(const T* __restrict__ s, T* __restrict__ v, Tables<T> t, Geo G, int batch) {
   const T sc = (T)exp2(-0.5 * (double)G.R);
@@ -203,6 +308,55 @@ __global__ void __launch_bounds__(256) k_fwht_cols(T* __restrict__ x, int L1, in
   for (int i = threadIdx.x; i < n1 * COLS; i += blockDim.x) {
     int r = i / COLS, cc = i % COLS;
     base[(int64_t)r * n2 + cc] = v[cc * pl + padi(r)];
+  }
+}
+
+// FWHT across segments for 3 <= L1 <= 6 (2^L1 rows of stride 2^L2): a CTA
+// of 256 threads takes 32 adjacent columns, so every row is read and written
+// as one 128-byte run (FP32).  Thread (g = tid / 32, c = tid % 32) first holds
+// rows g + 8 i of column c and applies the stages of row bits 3 .. L1-1 in
+// registers; one padded shared-memory exchange gives it rows 8 g + i, and the
+// stages of bits 0-2 follow in registers.  Natural order throughout.
+template <typename T, int L1>
+__global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2) {
+  constexpr int n1 = 1 << L1, NR = n1 / 8;
+  __shared__ T S[n1][33];
+  const int tid = threadIdx.x, c = tid & 31, g = tid >> 5;
+  const int64_t n2 = (int64_t)1 << L2;
+  const int tiles = (int)(n2 / 32);
+  const int64_t b = blockIdx.x / tiles;
+  T* base = x + b * ((int64_t)n1 << L2) + (int64_t)(blockIdx.x % tiles) * 32 + c;
+  T v[8];
+  if (g < 8) {
+#pragma unroll
+    for (int i = 0; i < NR; ++i) v[i] = base[(int64_t)(g + 8 * i) * n2];
+#pragma unroll
+    for (int h = 1; h < NR; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < NR; ++i)
+        if (!(i & h)) {
+          const T a = v[i], d = v[i + h];
+          v[i] = a + d;
+          v[i + h] = a - d;
+        }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) S[g + 8 * i][c] = v[i];
+  }
+  __syncthreads();
+  if (g < NR) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = S[8 * g + i][c];
+#pragma unroll
+    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (!(i & h)) {
+          const T a = v[i], d = v[i + h];
+          v[i] = a + d;
+          v[i + h] = a - d;
+        }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) base[(int64_t)(8 * g + i) * n2] = v[i];
   }
 }
 
@@ -2069,7 +2223,15 @@ static void fwht_big(T* v, int L, int batch, Launcher& Lc) {
   Lc.pre("fwht_seg", 2.0 * sizeof(T) * (double)batch * (double)(1LL << L));
   k_fwht_seg<T><<<(int64_t)batch << L1, 256, sm2, Lc.s>>>(v, L2);
   Lc.check();
-  if (L1 > 0) {
+  if (L1 >= 3 && L1 <= 6 && L2 >= 5) {
+    Lc.pre("fwht_cols", 2.0 * sizeof(T) * (double)batch * (double)(1LL << L));
+    const dim3 grid((unsigned)(batch * ((1 << L2) / 32)));
+    if (L1 == 3) k_fwht_cols32<T, 3><<<grid, 256, 0, Lc.s>>>(v, L2);
+    else if (L1 == 4) k_fwht_cols32<T, 4><<<grid, 256, 0, Lc.s>>>(v, L2);
+    else if (L1 == 5) k_fwht_cols32<T, 5><<<grid, 256, 0, Lc.s>>>(v, L2);
+    else k_fwht_cols32<T, 6><<<grid, 256, 0, Lc.s>>>(v, L2);
+    Lc.check();
+  } else if (L1 > 0) {
     const int COLS = 8;
     size_t sm1 = sizeof(T) * COLS * padlen(1 << L1);
     set_smem<T>((const void*)k_fwht_cols<T, COLS>, sm1);
@@ -2079,6 +2241,25 @@ static void fwht_big(T* v, int L, int batch, Launcher& Lc) {
   }
 }
 
+// Largest level jto <= R - 1 whose synthesis (analysis) levels below it fit
+// one CTA's shared memory (the tables and two buffers of 2^(jto-1)); 0 if
+// no level above J0 does.
+template <typename T>
+static int fused1d_top(const Plan& P) {
+  const Geo G = geo_of(P);
+  int jto = 0;
+  for (int j = P.J0 + 1; j <= P.R - 1; ++j)
+    if (sizeof(T) * ((size_t)table_count(G) + 4 + 2 * ((size_t)1 << (j - 1))) <= kSmemMax) jto = j;
+  return jto;
+}
+
+template <typename T>
+static size_t fused1d_smem(const Plan& P, int jto) {
+  return sizeof(T) * ((size_t)table_count(geo_of(P)) + 4 + 2 * ((size_t)1 << (jto - 1)));
+}
+
+// 1D, lines larger than shared memory: the coarse levels of each line in one
+// CTA, the levels above them one launch each, T, the two-pass FWHT, gather.
 template <typename T>
 static void fwd1d_big(const Plan& P, const T* x, T* y, int batch, T* work, Launcher& L) {
   const double e = sizeof(T);
@@ -2087,21 +2268,30 @@ static void fwd1d_big(const Plan& P, const T* x, T* y, int batch, T* work, Launc
   T* sA = work;
   T* sB = sA + (size_t)batch * M;
   T* v = sB + (size_t)batch * M;
-  cudaMemcpyAsync(sA, x, sizeof(T) * (size_t)batch * M, cudaMemcpyDeviceToDevice, L.s);
-  for (int j = P.J0; j < P.R; ++j) {
-    int n0 = 1 << j;
-    LineGeom gi{M, 1, M, 1, 0}, go{M, 1, M, 1, 0};
-    // lo from sA (synthesised so far), hi = details of x at [n0, 2n0): copied in sA
+  const int jto = fused1d_top<T>(P);
+  const T* cur = x;          // s_j of every line at cur + b M (the coarsest block of x to start)
+  int j = P.J0;
+  if (jto) {
+    const size_t sm = fused1d_smem<T>(P, jto);
+    set_smem<T>((const void*)k_syn1d_levels<T>, sm);
+    L.pre("syn_levels_1d", e * 2.0 * batch * (double)(1 << jto));
+    L.note(launch_pdl(k_syn1d_levels<T>, dim3(batch), dim3(1024), sm, L.s, x, sA, (int64_t)M, tabs<T>(P), G, P.J0, jto,
+                      (int64_t)M));
+    L.check();
+    cur = sA;
+    j = jto;
+  }
+  for (; j < P.R; ++j) {
+    const int n0 = 1 << j;
+    T* o = cur == sB ? sA : sB;
     L.pre("syn_level_1d", e * 4.0 * batch * n0);
-    k_syn_level<T><<<grid_for((int64_t)batch * 2 * n0), 256, 0, L.s>>>(sA, sB, n0, tabs<T>(P), G, gi, go, batch);
+    k_syn1d_level<T><<<grid_for((int64_t)batch * 2 * n0), 256, 0, L.s>>>(cur, M, x + n0, M, o, M, n0, tabs<T>(P), G,
+                                                                          batch);
     L.check();
-    // keep the untouched details of higher levels: copy the new prefix back
-    L.pre("copy_prefix_1d", e * 4.0 * batch * n0);
-    k_copy_block<T><<<grid_for((int64_t)batch * 2 * n0), 256, 0, L.s>>>(sB, M, M, sA, M, M, 1, 2 * n0, batch);
-    L.check();
+    cur = o;
   }
   L.pre("upconv_1d", e * (double)batch * (M + N));
-  k_up<T><<<grid_for((int64_t)batch * N), 256, 0, L.s>>>(sA, v, tabs<T>(P), G, batch);
+  k_up<T><<<grid_for((int64_t)batch * N), 256, 0, L.s>>>(cur, v, tabs<T>(P), G, batch);
   L.check();
   fwht_big<T>(v, G.L, batch, L);
   L.pre("gather_1d", e * 2.0 * batch * P.m + 8.0 * P.words);
@@ -2125,17 +2315,25 @@ static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launc
   L.pre("upconvT_1d", e * (double)batch * (M + N));
   k_upT<T><<<grid_for((int64_t)batch * M), 256, 0, L.s>>>(v, sA, tabs<T>(P), G, batch);
   L.check();
-  for (int j = P.R - 1; j >= P.J0; --j) {
-    int n0 = 1 << j;
-    LineGeom gi{M, 1, M, 1, 0}, go{M, 1, M, 1, 0};
+  const int jfrom = fused1d_top<T>(P);
+  const int jlow = jfrom ? jfrom : P.J0;
+  T* cur = sA;               // s_(j+1) of every line at cur + b M
+  for (int j = P.R - 1; j >= jlow; --j) {
+    const int n0 = 1 << j;
+    T* lo = (!jfrom && j == P.J0) ? x : (cur == sA ? sB : sA);
     L.pre("ana_level_1d", e * 4.0 * batch * n0);
-    k_ana_level<T><<<grid_for((int64_t)batch * n0), 256, 0, L.s>>>(sA, sB, n0, tabs<T>(P), G, gi, go, batch);
+    k_ana1d_level<T><<<grid_for((int64_t)batch * n0), 256, 0, L.s>>>(cur, M, lo, M, x + n0, M, n0, tabs<T>(P), G, batch);
     L.check();
-    L.pre("copy_prefix_1d", e * 4.0 * batch * n0);
-    k_copy_block<T><<<grid_for((int64_t)batch * 2 * n0), 256, 0, L.s>>>(sB, M, M, sA, M, M, 1, 2 * n0, batch);
+    cur = lo;
+  }
+  if (jfrom) {
+    const size_t sm = fused1d_smem<T>(P, jfrom);
+    set_smem<T>((const void*)k_ana1d_levels<T>, sm);
+    L.pre("ana_levels_1d", e * 2.0 * batch * (double)(1 << jfrom));
+    L.note(launch_pdl(k_ana1d_levels<T>, dim3(batch), dim3(1024), sm, L.s, (const T*)cur, (int64_t)M, x, tabs<T>(P), G,
+                      P.J0, jfrom, (int64_t)M));
     L.check();
   }
-  cudaMemcpyAsync(x, sA, sizeof(T) * (size_t)batch * M, cudaMemcpyDeviceToDevice, L.s);
 }
 
 // 2D (Algorithm 2 with the Mallat IDWT in front).

@@ -82,18 +82,22 @@ def test_1d_sweep_against_dense(p, bd, dR, q):
         assert rel(run_adj(plan, y, prec), y @ U) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec,R,q,p", [(F64, 13, 2, 3), (F32, 14, 2, 2), (F64, 12, 4, 4)])
-def test_1d_large_lines_against_algorithm1(prec, R, q, p):
-    """Lines longer than one CTA's shared memory take the multi-kernel path."""
-    rng = np.random.default_rng(R + q)
+@pytest.mark.parametrize("prec,R,q,p,bd", [(F64, 13, 2, 3, VMP), (F32, 14, 2, 2, VMP), (F64, 12, 4, 4, VMP),
+                                            (F32, 14, 2, 3, PERIODIC), (F64, 14, 1, 5, PERIODIC),
+                                            (F32, 15, 1, 8, VMP)])
+def test_1d_large_lines_against_algorithm1(prec, R, q, p, bd):
+    """Lines longer than one CTA's shared memory take the multi-kernel path:
+    the coarse levels of each line in one CTA's shared memory (as many as
+    fit), the levels above them one launch each, T, the two-pass FWHT."""
+    rng = np.random.default_rng(R + q + 10 * bd)
     J0 = W.default_J0(p)
     N = 2 ** (R + q)
     omega = inputs.mask_1d(rng, N, 0.2)
-    plan = Plan(1, R, q, p, VMP, omega=omega, max_batch=2)
+    plan = Plan(1, R, q, p, bd, omega=omega, max_batch=2)
     x = inputs.coeffs_1d(rng, R, J0, 1.5, batch=2)
     y = rng.standard_normal((2, omega.size))
-    assert rel(run_fwd(plan, x, prec), fast.forward1d(x, R, q, p, VMP, J0, omega)) < TOL[prec]
-    assert rel(run_adj(plan, y, prec), fast.adjoint1d(y, R, q, p, VMP, J0, omega)) < TOL[prec]
+    assert rel(run_fwd(plan, x, prec), fast.forward1d(x, R, q, p, bd, J0, omega)) < TOL[prec]
+    assert rel(run_adj(plan, y, prec), fast.adjoint1d(y, R, q, p, bd, J0, omega)) < TOL[prec]
 
 
 @pytest.mark.parametrize("prec", [F32, F64])
