@@ -2216,13 +2216,15 @@ static void adj1d_smem(const Plan& P, const T* y, T* x, int batch, Launcher& L) 
 
 // 1D, lines larger than shared memory: level kernels + T + two-pass FWHT.
 template <typename T>
-static void fwht_big(T* v, int L, int batch, Launcher& Lc) {
+static void fwht_big(T* v, int L, int batch, Launcher& Lc, bool segments = true) {
   int L2 = std::min(L, 12), L1 = L - L2;
-  size_t sm2 = sizeof(T) * padlen(1 << L2);
-  set_smem<T>((const void*)k_fwht_seg<T>, sm2);
-  Lc.pre("fwht_seg", 2.0 * sizeof(T) * (double)batch * (double)(1LL << L));
-  k_fwht_seg<T><<<(int64_t)batch << L1, 256, sm2, Lc.s>>>(v, L2);
-  Lc.check();
+  if (segments) {
+    size_t sm2 = sizeof(T) * padlen(1 << L2);
+    set_smem<T>((const void*)k_fwht_seg<T>, sm2);
+    Lc.pre("fwht_seg", 2.0 * sizeof(T) * (double)batch * (double)(1LL << L));
+    k_fwht_seg<T><<<(int64_t)batch << L1, 256, sm2, Lc.s>>>(v, L2);
+    Lc.check();
+  }
   if (L1 >= 3 && L1 <= 6 && L2 >= 5) {
     Lc.pre("fwht_cols", 2.0 * sizeof(T) * (double)batch * (double)(1LL << L));
     const dim3 grid((unsigned)(batch * ((1 << L2) / 32)));
@@ -2290,6 +2292,20 @@ static void fwd1d_big(const Plan& P, const T* x, T* y, int batch, T* work, Launc
     L.check();
     cur = o;
   }
+  if constexpr (std::is_same<T, float>::value) {
+    if (f32_seg_eligible(P)) {
+      // T and the stages of bits 0-11 per segment of 4096, then bits 12..
+      L.pre("upconv_fwht_seg_1d", e * (double)batch * (M + N));
+      L.note(f32_seg_up(P, G, cur, v, batch, L.s));
+      L.check();
+      fwht_big<T>(v, G.L, batch, L, false);
+      L.pre("gather_1d", e * 2.0 * batch * P.m + 8.0 * P.words);
+      k_gather<T><<<grid_for((int64_t)batch * P.words), 256, 0, L.s>>>(v, y, P.d_mask, P.d_prefix, P.words, G.L, N, P.m,
+                                                                        batch);
+      L.check();
+      return;
+    }
+  }
   L.pre("upconv_1d", e * (double)batch * (M + N));
   k_up<T><<<grid_for((int64_t)batch * N), 256, 0, L.s>>>(cur, v, tabs<T>(P), G, batch);
   L.check();
@@ -2311,10 +2327,26 @@ static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launc
   L.pre("scatter_1d", e * 2.0 * batch * P.m + 8.0 * P.words);
   k_scatter<T><<<grid_for((int64_t)batch * P.words), 256, 0, L.s>>>(y, v, P.d_mask, P.d_prefix, P.words, G.L, N, P.m, batch);
   L.check();
-  fwht_big<T>(v, G.L, batch, L);
-  L.pre("upconvT_1d", e * (double)batch * (M + N));
-  k_upT<T><<<grid_for((int64_t)batch * M), 256, 0, L.s>>>(v, sA, tabs<T>(P), G, batch);
-  L.check();
+  bool done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (f32_seg_eligible(P)) {
+      // the stages of bits 12.., then bits 0-11 per segment of 4096, then T^T
+      fwht_big<T>(v, G.L, batch, L, false);
+      L.pre("fwht_seg", 2.0 * e * (double)batch * N);
+      L.note(f32_seg_fwht(P, v, batch, L.s));
+      L.check();
+      L.pre("upconvT_1d", e * (double)batch * (M + N));
+      L.note(f32_upT_lines(P, G, v, sA, batch, L.s));
+      L.check();
+      done = true;
+    }
+  }
+  if (!done) {
+    fwht_big<T>(v, G.L, batch, L);
+    L.pre("upconvT_1d", e * (double)batch * (M + N));
+    k_upT<T><<<grid_for((int64_t)batch * M), 256, 0, L.s>>>(v, sA, tabs<T>(P), G, batch);
+    L.check();
+  }
   const int jfrom = fused1d_top<T>(P);
   const int jlow = jfrom ? jfrom : P.J0;
   T* cur = sA;               // s_(j+1) of every line at cur + b M

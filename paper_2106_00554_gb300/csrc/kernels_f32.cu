@@ -33,6 +33,8 @@
 // Walsh butterflies use the packed FP32x2 add of sm_100+.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -889,6 +891,154 @@ cudaError_t go_nt(bool fwd, const Plan& P, const float* in, float* out, const Li
   return go_q<10, NT>(fwd, P, in, out, io, total, s);
 }
 
+// ---------------------------------------------------------------------------
+// long 1D lines (N = 2^L, L > 12): segments of 4096 outputs
+// ---------------------------------------------------------------------------
+constexpr int SEGN = 4096, SEGNT = 256;
+constexpr int SEGV = up4(vp(SEGN - 1) + 1);
+
+// the rest of a segment after its 16-blocks are in V (natural order, bits
+// 0-3 done): bits 4-7 in place, bits 8-11 on the way to out[0, 4096)
+__device__ __forceinline__ void seg_finish(float* V, float* __restrict__ out, int tid) {
+  __syncthreads();
+  pass_mid<SEGNT>(V, 0, tid);
+  __syncthreads();
+  const int e0 = high_pencil(tid);
+  const float* src = V + vp(e0);
+  float v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = src[VCH * i];
+  wht<16>(v);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) out[e0 + 256 * i] = v[i];
+}
+
+// v = T s on segment `seg` of line b, then the Walsh-Hadamard stages of bits
+// 0-11 (Sec. 4.1, Sec. 3.1); the stages of bits 12.. across segments follow
+// in another kernel.  Thread t computes outputs 16 t .. 16 t + 15 of the
+// segment from a register window of s (interior formula, taps with
+// 2^{-R/2} folded in; periodic plans wrap the window).  Outputs within ntap
+// of a VMP end take the exact formula (boundary rows of T).
+template <int PM, int Q>
+__global__ void __launch_bounds__(SEGNT) k_up_seg(const float* __restrict__ s, float* __restrict__ v, Taps<PM, Q> tp,
+                                                  Tables<float> tab, Geo G, int segs) {
+  constexpr int BS = 16 / Q, NW = BS + 2 * PM - 2;
+  __shared__ __align__(16) float sV[SEGV];
+  const int tid = threadIdx.x;
+  const int64_t b = blockIdx.x / segs;
+  const int seg = blockIdx.x - (int)(b * segs);
+  const int M = G.M, N = G.N;
+  const float* sb = s + b * M;
+  const int K0 = seg * SEGN + 16 * tid;
+  float o[16];
+  if (G.bd == UW_BOUNDARY_VMP && (K0 < G.ntap || K0 + 16 > N - G.ntap)) {
+    const float sc = exp2f(-0.5f * (float)G.R);
+    Plain<float> sa{sb};
+#pragma unroll 1
+    for (int r = 0; r < 16; ++r) o[r] = sc * up_one<float>(K0 + r, sa, tab, G);
+  } else {
+    const int m0 = K0 / Q - PM + 1;
+    float ws[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      int m = m0 + w;
+      if (G.bd == UW_BOUNDARY_PERIODIC) m &= M - 1;
+      ws[w] = (m >= 0 && m < M) ? __ldg(sb + m) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 16; r += 2) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int d = -(PM - 1); d <= PM - 1; ++d) {
+        const float x = ws[r / Q - d + PM - 1];
+        acc = __ffma2_rn(tp.tp2[(r % Q) / 2][d + PM - 1], make_float2(x, x), acc);
+      }
+      o[r] = acc.x;
+      o[r + 1] = acc.y;
+    }
+  }
+  wht<16>(o);
+  float* dst = sV + vp(16 * tid);
+#pragma unroll
+  for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(dst + r) = make_float4(o[r], o[r + 1], o[r + 2], o[r + 3]);
+  seg_finish(sV, v + b * N + (int64_t)seg * SEGN, tid);
+}
+
+// the Walsh-Hadamard stages of bits 0-11 of every segment of 4096, in place
+__global__ void __launch_bounds__(SEGNT) k_fwht_seg4096(float* __restrict__ v) {
+  __shared__ __align__(16) float sV[SEGV];
+  const int tid = threadIdx.x;
+  float* seg = v + (int64_t)blockIdx.x * SEGN;
+  float o[16];
+#pragma unroll
+  for (int r = 0; r < 16; r += 4) {
+    const float4 u = *reinterpret_cast<const float4*>(seg + 16 * tid + r);
+    o[r] = u.x; o[r + 1] = u.y; o[r + 2] = u.z; o[r + 3] = u.w;
+  }
+  wht<16>(o);
+  float* dst = sV + vp(16 * tid);
+#pragma unroll
+  for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(dst + r) = make_float4(o[r], o[r + 1], o[r + 2], o[r + 3]);
+  seg_finish(sV, seg, tid);
+}
+
+// taps of T^T, 2^{-R/2} folded in, zero-padded to (2 PM - 1) Q entries:
+// entry i multiplies v[Q m + (1 - PM) Q + i] for output s[m]
+template <int PM, int Q>
+struct TapsT {
+  float2 t2[(2 * PM - 1) * Q / 2];
+};
+
+// s = T^T v on every line (Sec. 4.2): thread t computes outputs 4 t .. 4 t + 3
+// of its line from a register window of v (interior formula; periodic plans
+// wrap the window); outputs within p of a VMP end take the exact formula.
+template <int PM, int Q>
+__global__ void __launch_bounds__(256) k_upT_lines(const float* __restrict__ v, float* __restrict__ s, TapsT<PM, Q> tp,
+                                                   Tables<float> tab, Geo G, int batch) {
+  constexpr int BO = 4, NWV = Q * (BO + 2 * PM - 2), NT2 = (2 * PM - 1) * Q / 2;
+  const int per = G.M / BO;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)batch * per) return;
+  const int64_t b = idx / per;
+  const int m0 = (int)(idx - b * per) * BO;
+  const int M = G.M, N = G.N;
+  const float* vb = v + b * N;
+  float* sb = s + b * M;
+  if (G.bd == UW_BOUNDARY_VMP && (m0 < G.p || m0 + BO > M - G.p)) {
+    const float sc = exp2f(-0.5f * (float)G.R);
+    Plain<float> va{vb};
+#pragma unroll 1
+    for (int u = 0; u < BO; ++u) sb[m0 + u] = sc * upT_one<float>(m0 + u, va, tab, G);
+    return;
+  }
+  const int k0 = Q * m0 + (1 - PM) * Q;      // even
+  float ws[NWV];
+  if (k0 >= 0 && k0 + NWV <= N) {
+#pragma unroll
+    for (int w = 0; w < NWV; w += 2) {
+      const float2 u = __ldg(reinterpret_cast<const float2*>(vb + k0 + w));
+      ws[w] = u.x;
+      ws[w + 1] = u.y;
+    }
+  } else {
+#pragma unroll
+    for (int w = 0; w < NWV; ++w) {
+      int k = k0 + w;
+      if (G.bd == UW_BOUNDARY_PERIODIC) k &= N - 1;
+      ws[w] = (k >= 0 && k < N) ? __ldg(vb + k) : 0.f;
+    }
+  }
+  float o[BO];
+#pragma unroll
+  for (int u = 0; u < BO; ++u) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < NT2; ++i) acc = __ffma2_rn(tp.t2[i], make_float2(ws[Q * u + 2 * i], ws[Q * u + 2 * i + 1]), acc);
+    o[u] = acc.x + acc.y;
+  }
+  *reinterpret_cast<float4*>(sb + m0) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
 }  // namespace f32k
 
 bool f32_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd) {
@@ -909,6 +1059,55 @@ bool f32_eligible(const Plan& P, const LineIO& io, const void* in, const void* o
     if (!al16(out) || io.out_stride % 4 || io.out_batch % 4) return false;
   }
   return true;
+}
+
+// long 1D lines on FP32: T with the Walsh-Hadamard stages of bits 0-11 per
+// segment of 4096 (forward), those stages alone (adjoint), and T^T
+bool f32_seg_eligible(const Plan& P) {
+  return (P.Q == 2 || P.Q == 4) && P.N >= 2 * f32k::SEGN && P.M >= 16 && P.M % 4 == 0;
+}
+
+template <typename F>
+static cudaError_t f32_pm_dispatch(const Plan& P, F&& f) {
+  if (P.p <= 4) return P.Q == 2 ? f(std::integral_constant<int, 4>{}, std::integral_constant<int, 2>{})
+                                 : f(std::integral_constant<int, 4>{}, std::integral_constant<int, 4>{});
+  if (P.p <= 8) return P.Q == 2 ? f(std::integral_constant<int, 8>{}, std::integral_constant<int, 2>{})
+                                 : f(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{});
+  return P.Q == 2 ? f(std::integral_constant<int, 10>{}, std::integral_constant<int, 2>{})
+                  : f(std::integral_constant<int, 10>{}, std::integral_constant<int, 4>{});
+}
+
+cudaError_t f32_seg_up(const Plan& P, const Geo& G, const float* s, float* v, int batch, cudaStream_t st) {
+  const int segs = P.N / f32k::SEGN;
+  return f32_pm_dispatch(P, [&](auto pm, auto q) {
+    constexpr int PM = decltype(pm)::value, Q = decltype(q)::value;
+    f32k::k_up_seg<PM, Q><<<(unsigned)(batch * segs), f32k::SEGNT, 0, st>>>(s, v, f32k::make_taps<PM, Q>(P), P.t32, G,
+                                                                            segs);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t f32_seg_fwht(const Plan& P, float* v, int batch, cudaStream_t st) {
+  f32k::k_fwht_seg4096<<<(unsigned)((int64_t)batch * (P.N / f32k::SEGN)), f32k::SEGNT, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t f32_upT_lines(const Plan& P, const Geo& G, const float* v, float* s, int batch, cudaStream_t st) {
+  const int64_t threads = (int64_t)batch * (P.M / 4);
+  return f32_pm_dispatch(P, [&](auto pm, auto q) {
+    constexpr int PM = decltype(pm)::value, Q = decltype(q)::value;
+    f32k::TapsT<PM, Q> t;
+    float* tv = reinterpret_cast<float*>(t.t2);
+    const int p = P.p;
+    const double sc = std::exp2(-0.5 * P.R);
+    for (int i = 0; i < (2 * PM - 1) * Q; ++i) {
+      const int tt = (1 - PM) * Q + i;                    // tap position
+      const bool in = tt >= (1 - p) * Q && tt < p * Q;
+      tv[i] = in ? (float)(sc * P.taps[tt + (p - 1) * Q]) : 0.f;
+    }
+    f32k::k_upT_lines<PM, Q><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(v, s, t, P.t32, G, batch);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t f32_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,

@@ -485,6 +485,11 @@ cudaError_t umma_launch(bool fwd, const Plan& P, const float* in, float* out, co
 
 // kernels_f32.cu: persistent FP32 line operators (last level, N = 2048 / 4096)
 bool f32_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd);
+// long 1D lines on FP32 (kernels_f32.cu)
+bool f32_seg_eligible(const Plan& P);
+cudaError_t f32_seg_up(const Plan& P, const Geo& G, const float* s, float* v, int batch, cudaStream_t st);
+cudaError_t f32_seg_fwht(const Plan& P, float* v, int batch, cudaStream_t st);
+cudaError_t f32_upT_lines(const Plan& P, const Geo& G, const float* v, float* s, int batch, cudaStream_t st);
 cudaError_t f32_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
                        cudaStream_t s);
 
