@@ -317,19 +317,33 @@ __global__ void __launch_bounds__(256) k_fwht_cols(T* __restrict__ x, int L1, in
 // rows g + 8 i of column c and applies the stages of row bits 3 .. L1-1 in
 // registers; one padded shared-memory exchange gives it rows 8 g + i, and the
 // stages of bits 0-2 follow in registers.  Natural order throughout.
-template <typename T, int L1>
-__global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2) {
+//
+// MODE 1 (forward) writes only the sampled outputs, straight into y (n2y:
+// natural position -> index in y, or -1); MODE 2 (adjoint) reads its input
+// from y through the same table (zero where nothing is sampled).
+template <typename T, int L1, int MODE = 0>
+__global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2, const int32_t* __restrict__ n2y = nullptr,
+                                                     const T* __restrict__ yin = nullptr, T* __restrict__ yout = nullptr,
+                                                     int64_t m = 0) {
   constexpr int n1 = 1 << L1, NR = n1 / 8;
   __shared__ T S[n1][33];
   const int tid = threadIdx.x, c = tid & 31, g = tid >> 5;
   const int64_t n2 = (int64_t)1 << L2;
   const int tiles = (int)(n2 / 32);
   const int64_t b = blockIdx.x / tiles;
-  T* base = x + b * ((int64_t)n1 << L2) + (int64_t)(blockIdx.x % tiles) * 32 + c;
+  const int64_t col = (int64_t)(blockIdx.x % tiles) * 32 + c;
+  T* base = x + b * ((int64_t)n1 << L2) + col;
   T v[8];
   if (g < 8) {
 #pragma unroll
-    for (int i = 0; i < NR; ++i) v[i] = base[(int64_t)(g + 8 * i) * n2];
+    for (int i = 0; i < NR; ++i) {
+      if (MODE == 2) {
+        const int yi = __ldg(n2y + (int64_t)(g + 8 * i) * n2 + col);
+        v[i] = yi >= 0 ? __ldg(yin + b * m + yi) : T(0);
+      } else {
+        v[i] = base[(int64_t)(g + 8 * i) * n2];
+      }
+    }
 #pragma unroll
     for (int h = 1; h < NR; h <<= 1)
 #pragma unroll
@@ -356,9 +370,18 @@ __global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2) 
           v[i + h] = a - d;
         }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) base[(int64_t)(8 * g + i) * n2] = v[i];
+    for (int i = 0; i < 8; ++i) {
+      if (MODE == 1) {
+        const int yi = __ldg(n2y + (int64_t)(8 * g + i) * n2 + col);
+        if (yi >= 0) yout[b * m + yi] = v[i];
+      } else {
+        base[(int64_t)(8 * g + i) * n2] = v[i];
+      }
+    }
   }
 }
+
+
 
 template <typename T>
 __global__ void k_gather(const T* __restrict__ beta, T* __restrict__ y, const uint32_t* __restrict__ mask,
@@ -2215,6 +2238,28 @@ static void adj1d_smem(const Plan& P, const T* y, T* x, int batch, Launcher& L) 
 }
 
 // 1D, lines larger than shared memory: level kernels + T + two-pass FWHT.
+// the stages across segments of 4096 (L1 = L - 12 in 3..6) with the gather
+// (mode 1) or the scatter (mode 2) folded in; false if not applicable
+template <typename T>
+static bool cols_with_samples(const Plan& P, T* v, const T* yin, T* yout, int batch, int mode, Launcher& Lc) {
+  const int L = geo_of(P).L, L2 = 12, L1 = L - L2;
+  if (!P.d_nat2y || L1 < 3 || L1 > 6) return false;
+  const dim3 grid((unsigned)(batch * ((1 << L2) / 32)));
+  Lc.pre(mode == 1 ? "fwht_cols_gather_1d" : "fwht_cols_scatter_1d",
+         sizeof(T) * (double)batch * ((double)(1LL << L) + 2.0 * P.m) + 4.0 * (double)(1LL << L));
+  auto go = [&](auto l1) {
+    constexpr int LL = decltype(l1)::value;
+    if (mode == 1) k_fwht_cols32<T, LL, 1><<<grid, 256, 0, Lc.s>>>(v, L2, P.d_nat2y, nullptr, yout, P.m);
+    else k_fwht_cols32<T, LL, 2><<<grid, 256, 0, Lc.s>>>(v, L2, P.d_nat2y, yin, nullptr, P.m);
+  };
+  if (L1 == 3) go(std::integral_constant<int, 3>{});
+  else if (L1 == 4) go(std::integral_constant<int, 4>{});
+  else if (L1 == 5) go(std::integral_constant<int, 5>{});
+  else go(std::integral_constant<int, 6>{});
+  Lc.check();
+  return true;
+}
+
 template <typename T>
 static void fwht_big(T* v, int L, int batch, Launcher& Lc, bool segments = true) {
   int L2 = std::min(L, 12), L1 = L - L2;
@@ -2273,12 +2318,17 @@ static void fwd1d_big(const Plan& P, const T* x, T* y, int batch, T* work, Launc
   const int jto = fused1d_top<T>(P);
   const T* cur = x;          // s_j of every line at cur + b M (the coarsest block of x to start)
   int j = P.J0;
+  constexpr bool f32 = std::is_same<T, float>::value;
   if (jto) {
     const size_t sm = fused1d_smem<T>(P, jto);
-    set_smem<T>((const void*)k_syn1d_levels<T>, sm);
     L.pre("syn_levels_1d", e * 2.0 * batch * (double)(1 << jto));
-    L.note(launch_pdl(k_syn1d_levels<T>, dim3(batch), dim3(1024), sm, L.s, x, sA, (int64_t)M, tabs<T>(P), G, P.J0, jto,
-                      (int64_t)M));
+    if constexpr (f32) {
+      L.note(f32_syn1d_levels(P, G, x, sA, jto, sm, batch, L.s));
+    } else {
+      set_smem<T>((const void*)k_syn1d_levels<T>, sm);
+      L.note(launch_pdl(k_syn1d_levels<T>, dim3(batch), dim3(1024), sm, L.s, x, sA, (int64_t)M, tabs<T>(P), G, P.J0,
+                        jto, (int64_t)M));
+    }
     L.check();
     cur = sA;
     j = jto;
@@ -2287,8 +2337,12 @@ static void fwd1d_big(const Plan& P, const T* x, T* y, int batch, T* work, Launc
     const int n0 = 1 << j;
     T* o = cur == sB ? sA : sB;
     L.pre("syn_level_1d", e * 4.0 * batch * n0);
-    k_syn1d_level<T><<<grid_for((int64_t)batch * 2 * n0), 256, 0, L.s>>>(cur, M, x + n0, M, o, M, n0, tabs<T>(P), G,
-                                                                          batch);
+    if (f32 && n0 >= 4) {
+      if constexpr (f32) L.note(f32_syn1d_level(P, G, cur, x + n0, o, n0, batch, L.s));
+    } else {
+      k_syn1d_level<T><<<grid_for((int64_t)batch * 2 * n0), 256, 0, L.s>>>(cur, M, x + n0, M, o, M, n0, tabs<T>(P), G,
+                                                                            batch);
+    }
     L.check();
     cur = o;
   }
@@ -2298,6 +2352,7 @@ static void fwd1d_big(const Plan& P, const T* x, T* y, int batch, T* work, Launc
       L.pre("upconv_fwht_seg_1d", e * (double)batch * (M + N));
       L.note(f32_seg_up(P, G, cur, v, batch, L.s));
       L.check();
+      if (cols_with_samples<T>(P, v, nullptr, y, batch, 1, L)) return;
       fwht_big<T>(v, G.L, batch, L, false);
       L.pre("gather_1d", e * 2.0 * batch * P.m + 8.0 * P.words);
       k_gather<T><<<grid_for((int64_t)batch * P.words), 256, 0, L.s>>>(v, y, P.d_mask, P.d_prefix, P.words, G.L, N, P.m,
@@ -2323,15 +2378,24 @@ static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launc
   T* sA = work;
   T* sB = sA + (size_t)batch * M;
   T* v = sB + (size_t)batch * M;
-  cudaMemsetAsync(v, 0, sizeof(T) * (size_t)batch * N, L.s);
-  L.pre("scatter_1d", e * 2.0 * batch * P.m + 8.0 * P.words);
-  k_scatter<T><<<grid_for((int64_t)batch * P.words), 256, 0, L.s>>>(y, v, P.d_mask, P.d_prefix, P.words, G.L, N, P.m, batch);
-  L.check();
+  bool scattered = false;
+  auto scatter = [&]() {
+    cudaMemsetAsync(v, 0, sizeof(T) * (size_t)batch * N, L.s);
+    L.pre("scatter_1d", e * 2.0 * batch * P.m + 8.0 * P.words);
+    k_scatter<T><<<grid_for((int64_t)batch * P.words), 256, 0, L.s>>>(y, v, P.d_mask, P.d_prefix, P.words, G.L, N, P.m,
+                                                                       batch);
+    L.check();
+  };
   bool done = false;
   if constexpr (std::is_same<T, float>::value) {
     if (f32_seg_eligible(P)) {
-      // the stages of bits 12.., then bits 0-11 per segment of 4096, then T^T
-      fwht_big<T>(v, G.L, batch, L, false);
+      // the stages of bits 12.. (reading the samples from y where the table
+      // allows), then bits 0-11 per segment of 4096, then T^T
+      scattered = cols_with_samples<T>(P, v, y, nullptr, batch, 2, L);
+      if (!scattered) {
+        scatter();
+        fwht_big<T>(v, G.L, batch, L, false);
+      }
       L.pre("fwht_seg", 2.0 * e * (double)batch * N);
       L.note(f32_seg_fwht(P, v, batch, L.s));
       L.check();
@@ -2342,6 +2406,7 @@ static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launc
     }
   }
   if (!done) {
+    scatter();
     fwht_big<T>(v, G.L, batch, L);
     L.pre("upconvT_1d", e * (double)batch * (M + N));
     k_upT<T><<<grid_for((int64_t)batch * M), 256, 0, L.s>>>(v, sA, tabs<T>(P), G, batch);
@@ -2350,18 +2415,26 @@ static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launc
   const int jfrom = fused1d_top<T>(P);
   const int jlow = jfrom ? jfrom : P.J0;
   T* cur = sA;               // s_(j+1) of every line at cur + b M
+  // the FP32 level kernels store 16 bytes at a time into x
+  const bool f32 = std::is_same<T, float>::value && ((uintptr_t)x & 15u) == 0;
   for (int j = P.R - 1; j >= jlow; --j) {
     const int n0 = 1 << j;
     T* lo = (!jfrom && j == P.J0) ? x : (cur == sA ? sB : sA);
     L.pre("ana_level_1d", e * 4.0 * batch * n0);
-    k_ana1d_level<T><<<grid_for((int64_t)batch * n0), 256, 0, L.s>>>(cur, M, lo, M, x + n0, M, n0, tabs<T>(P), G, batch);
+    if (f32 && n0 >= 4) {
+      if constexpr (std::is_same<T, float>::value) L.note(f32_ana1d_level(P, G, cur, lo, x + n0, n0, batch, L.s));
+    } else {
+      k_ana1d_level<T><<<grid_for((int64_t)batch * n0), 256, 0, L.s>>>(cur, M, lo, M, x + n0, M, n0, tabs<T>(P), G,
+                                                                         batch);
+    }
     L.check();
     cur = lo;
   }
   if (jfrom) {
     const size_t sm = fused1d_smem<T>(P, jfrom);
-    set_smem<T>((const void*)k_ana1d_levels<T>, sm);
     L.pre("ana_levels_1d", e * 2.0 * batch * (double)(1 << jfrom));
+    // (the per-pair formula: windows of groups would read shared memory 8 words apart per lane)
+    set_smem<T>((const void*)k_ana1d_levels<T>, sm);
     L.note(launch_pdl(k_ana1d_levels<T>, dim3(batch), dim3(1024), sm, L.s, (const T*)cur, (int64_t)M, x, tabs<T>(P), G,
                       P.J0, jfrom, (int64_t)M));
     L.check();

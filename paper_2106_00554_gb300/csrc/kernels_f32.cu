@@ -1039,6 +1039,178 @@ __global__ void __launch_bounds__(256) k_upT_lines(const float* __restrict__ v, 
   *reinterpret_cast<float4*>(sb + m0) = make_float4(o[0], o[1], o[2], o[3]);
 }
 
+// ---------------------------------------------------------------------------
+// 1D wavelet levels (Sec. 3.2) with register windows: a thread makes 8
+// synthesis outputs, or 4 analysis (lo, hi) pairs, by the interior formula;
+// the outputs whose formula involves an edge function take the exact one
+// (VMP); periodic plans wrap the windows, which is exact.
+// ---------------------------------------------------------------------------
+template <int PM>
+struct HGTaps {
+  float2 hp2[PM + 1];   // (h_{2d}, h_{2d+1}), d in [-PM/2, PM/2]
+  float2 gp2[PM + 1];
+};
+
+// s_{j+1}[8 g .. 8 g + 8) from lo = s_j, hi = d_j (n0 values each)
+template <int PM>
+__device__ __forceinline__ void syn8(const float* lo, const float* hi, int n0, int g, bool per, const HGTaps<PM>& tp,
+                                     float (&o)[8]) {
+  constexpr int NW = 4 + PM;
+  const int i0 = 4 * g - PM / 2;
+  float wl[NW], wh[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    int m = i0 + w;
+    if (per) m &= n0 - 1;
+    const bool ok = m >= 0 && m < n0;
+    wl[w] = ok ? lo[m] : 0.f;
+    wh[w] = ok ? hi[m] : 0.f;
+  }
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int d = -PM / 2; d <= PM / 2; ++d) {
+      const int w = jj - d + PM / 2;
+      acc = __ffma2_rn(tp.hp2[d + PM / 2], make_float2(wl[w], wl[w]), acc);
+      acc = __ffma2_rn(tp.gp2[d + PM / 2], make_float2(wh[w], wh[w]), acc);
+    }
+    o[2 * jj] = acc.x;
+    o[2 * jj + 1] = acc.y;
+  }
+}
+
+// (lo, hi)[4 g .. 4 g + 4) of level j from s = s_{j+1} (n1 = 2 n0 values)
+template <int PM>
+__device__ __forceinline__ void ana4(const float* s, int n1, int g, bool per, const HGTaps<PM>& tp, float (&lo)[4],
+                                     float (&hi)[4]) {
+  constexpr int NW = 8 + 2 * PM;
+  const int i0 = 8 * g - PM;
+  float ws[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    int k = i0 + w;
+    if (per) k &= n1 - 1;
+    ws[w] = (k >= 0 && k < n1) ? s[k] : 0.f;
+  }
+#pragma unroll
+  for (int bb = 0; bb < 4; ++bb) {
+    float2 x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int d = -PM / 2; d <= PM / 2; ++d) {
+      const int w = 2 * (bb + d) + PM;
+      const float2 sv = make_float2(ws[w], ws[w + 1]);
+      x = __ffma2_rn(tp.hp2[d + PM / 2], sv, x);
+      y = __ffma2_rn(tp.gp2[d + PM / 2], sv, y);
+    }
+    lo[bb] = x.x + x.y;
+    hi[bb] = y.x + y.y;
+  }
+}
+
+// one synthesis level: the 8 outputs of group g into o[8 g ..)
+template <int PM, typename TB>
+__device__ __forceinline__ void syn_group(const float* lo, const float* hi, float* o, int n0, int g,
+                                          const HGTaps<PM>& tp, const TB& tab, const Geo& G) {
+  const int n1 = 2 * n0, k0 = 8 * g;
+  const bool per = G.bd == UW_BOUNDARY_PERIODIC;
+  if (!per && (k0 < G.Lb || k0 + 8 > n1 - G.Lb)) {
+    Plain<float> l{lo}, h{hi};
+#pragma unroll 1
+    for (int r = 0; r < 8; ++r) o[k0 + r] = syn_one<float>(k0 + r, n0, l, h, tab, G);
+    return;
+  }
+  float v[8];
+  syn8<PM>(lo, hi, n0, g, per, tp, v);
+  *reinterpret_cast<float4*>(o + k0) = make_float4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<float4*>(o + k0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// one analysis level: the 4 pairs of group g
+template <int PM, typename TB>
+__device__ __forceinline__ void ana_group(const float* s, float* lo, float* hi, int n0, int g, const HGTaps<PM>& tp,
+                                          const TB& tab, const Geo& G) {
+  const int m0 = 4 * g;
+  const bool per = G.bd == UW_BOUNDARY_PERIODIC;
+  if (!per && (m0 < G.p || m0 + 4 > n0 - G.p)) {
+    Plain<float> sa{s};
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+      float a, b;
+      ana_one<float>(m0 + r, n0, sa, tab, G, a, b);
+      lo[m0 + r] = a;
+      hi[m0 + r] = b;
+    }
+    return;
+  }
+  float a[4], b[4];
+  ana4<PM>(s, 2 * n0, g, per, tp, a, b);
+  *reinterpret_cast<float4*>(lo + m0) = make_float4(a[0], a[1], a[2], a[3]);
+  *reinterpret_cast<float4*>(hi + m0) = make_float4(b[0], b[1], b[2], b[3]);
+}
+
+// the coarse synthesis levels J0 .. jto-1 of one line per CTA in shared
+// memory (two buffers of 2^(jto-1)); details from x, s_jto to out
+template <int PM>
+__global__ void __launch_bounds__(1024) k_syn1d_levels_f32(const float* __restrict__ x, float* __restrict__ out,
+                                                           int64_t out_bs, HGTaps<PM> tp, Tables<float> tab, Geo G,
+                                                           int J0, int jto, int64_t in_bs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<float> st;
+  const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
+  const float* xb = x + (int64_t)blockIdx.x * in_bs;
+  float* ob = out + (int64_t)blockIdx.x * out_bs;
+  float* P0 = sm + ((off + 3) & ~3);
+  float* P1 = P0 + (1 << (jto - 1));
+  for (int k = tid; k < (1 << J0); k += nthr) P0[k] = xb[k];
+  __syncthreads();
+  float* src = P0;
+  float* dst = P1;
+  for (int j = J0; j < jto; ++j) {
+    const int n0 = 1 << j, n1 = 2 * n0;
+    float* o = j + 1 == jto ? ob : dst;
+    if (n1 / 8 >= nthr) {   // groups of 8 once they fill the CTA; small levels are latency-bound
+      for (int g = tid; g < n1 / 8; g += nthr) syn_group<PM>(src, xb + n0, o, n0, g, tp, st, G);
+    } else {
+      Plain<float> lo{src}, hi{xb + n0};
+      for (int k = tid; k < n1; k += nthr) o[k] = syn_one<float>(k, n0, lo, hi, st, G);
+    }
+    __syncthreads();
+    float* t = src;
+    src = dst;
+    dst = t;
+  }
+}
+
+// one level over a batch of lines, a group of outputs per thread
+template <int PM>
+__global__ void __launch_bounds__(256) k_syn1d_level_f32(const float* __restrict__ lo, int64_t lo_bs,
+                                                         const float* __restrict__ hi, int64_t hi_bs,
+                                                         float* __restrict__ out, int64_t out_bs, int n0, HGTaps<PM> tp,
+                                                         Tables<float> tab, Geo G, int batch) {
+  const int per = (2 * n0) / 8;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)batch * per) return;
+  const int64_t b = idx / per;
+  syn_group<PM>(lo + b * lo_bs, hi + b * hi_bs, out + b * out_bs, n0, (int)(idx - b * per), tp, tab, G);
+}
+
+template <int PM>
+__global__ void __launch_bounds__(256) k_ana1d_level_f32(const float* __restrict__ in, int64_t in_bs,
+                                                         float* __restrict__ lo, int64_t lo_bs, float* __restrict__ hi,
+                                                         int64_t hi_bs, int n0, HGTaps<PM> tp, Tables<float> tab, Geo G,
+                                                         int batch) {
+  const int per = n0 / 4;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)batch * per) return;
+  const int64_t b = idx / per;
+  ana_group<PM>(in + b * in_bs, lo + b * lo_bs, hi + b * hi_bs, n0, (int)(idx - b * per), tp, tab, G);
+}
+
 }  // namespace f32k
 
 bool f32_eligible(const Plan& P, const LineIO& io, const void* in, const void* out, bool fwd) {
@@ -1106,6 +1278,59 @@ cudaError_t f32_upT_lines(const Plan& P, const Geo& G, const float* v, float* s,
       tv[i] = in ? (float)(sc * P.taps[tt + (p - 1) * Q]) : 0.f;
     }
     f32k::k_upT_lines<PM, Q><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(v, s, t, P.t32, G, batch);
+    return cudaGetLastError();
+  });
+}
+
+template <int PM>
+static f32k::HGTaps<PM> make_hg(const Plan& P) {
+  f32k::HGTaps<PM> t;
+  const int p = P.p;
+  auto hf = [&](int l) { return (l >= -p + 1 && l <= p) ? (float)P.h[l + p - 1] : 0.f; };
+  auto gf = [&](int l) { return (l >= -p + 1 && l <= p) ? (float)P.g[l + p - 1] : 0.f; };
+  for (int d = -PM / 2; d <= PM / 2; ++d) {
+    t.hp2[d + PM / 2] = make_float2(hf(2 * d), hf(2 * d + 1));
+    t.gp2[d + PM / 2] = make_float2(gf(2 * d), gf(2 * d + 1));
+  }
+  return t;
+}
+
+template <typename F>
+static cudaError_t hg_dispatch(const Plan& P, F&& f) {
+  if (P.p <= 4) return f(std::integral_constant<int, 4>{});
+  if (P.p <= 8) return f(std::integral_constant<int, 8>{});
+  return f(std::integral_constant<int, 10>{});
+}
+
+cudaError_t f32_syn1d_levels(const Plan& P, const Geo& G, const float* x, float* out, int jto, size_t smem, int batch,
+                             cudaStream_t st) {
+  return hg_dispatch(P, [&](auto pm) {
+    constexpr int PM = decltype(pm)::value;
+    auto kern = f32k::k_syn1d_levels_f32<PM>;
+    cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch_pdl(kern, dim3(batch), dim3(1024), smem, st, x, out, (int64_t)P.M, make_hg<PM>(P), P.t32, G, P.J0,
+                      jto, (int64_t)P.M);
+  });
+}
+
+cudaError_t f32_syn1d_level(const Plan& P, const Geo& G, const float* lo, const float* hi, float* out, int n0, int batch,
+                            cudaStream_t st) {
+  const int64_t threads = (int64_t)batch * (2 * n0 / 8);
+  return hg_dispatch(P, [&](auto pm) {
+    constexpr int PM = decltype(pm)::value;
+    f32k::k_syn1d_level_f32<PM><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(lo, P.M, hi, P.M, out, P.M, n0,
+                                                                                   make_hg<PM>(P), P.t32, G, batch);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t f32_ana1d_level(const Plan& P, const Geo& G, const float* in, float* lo, float* hi, int n0, int batch,
+                            cudaStream_t st) {
+  const int64_t threads = (int64_t)batch * (n0 / 4);
+  return hg_dispatch(P, [&](auto pm) {
+    constexpr int PM = decltype(pm)::value;
+    f32k::k_ana1d_level_f32<PM><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(in, P.M, lo, P.M, hi, P.M, n0,
+                                                                                   make_hg<PM>(P), P.t32, G, batch);
     return cudaGetLastError();
   });
 }

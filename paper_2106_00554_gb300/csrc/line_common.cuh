@@ -490,6 +490,12 @@ bool f32_seg_eligible(const Plan& P);
 cudaError_t f32_seg_up(const Plan& P, const Geo& G, const float* s, float* v, int batch, cudaStream_t st);
 cudaError_t f32_seg_fwht(const Plan& P, float* v, int batch, cudaStream_t st);
 cudaError_t f32_upT_lines(const Plan& P, const Geo& G, const float* v, float* s, int batch, cudaStream_t st);
+cudaError_t f32_syn1d_levels(const Plan& P, const Geo& G, const float* x, float* out, int jto, size_t smem, int batch,
+                             cudaStream_t st);
+cudaError_t f32_syn1d_level(const Plan& P, const Geo& G, const float* lo, const float* hi, float* out, int n0, int batch,
+                            cudaStream_t st);
+cudaError_t f32_ana1d_level(const Plan& P, const Geo& G, const float* in, float* lo, float* hi, int n0, int batch,
+                            cudaStream_t st);
 cudaError_t f32_launch(bool fwd, const Plan& P, const float* in, float* out, const LineIO& io, int total,
                        cudaStream_t s);
 

@@ -754,12 +754,40 @@ static int upload_mask(uw_plan* P, const int64_t* omega, int64_t m) {
       return fail(UW_ERR_CUDA, "sample position upload failed");
     }
   }
+  // 1D long lines: the sample of every natural FWHT position (the products
+  // gather and scatter in the kernel that applies the last Walsh stages)
+  int32_t* dn2y = nullptr;
+  if (P->d == 1 && N >= 8192 && N <= (int64_t(1) << 22)) {
+    int L = 0;
+    while ((int64_t(1) << L) < N) ++L;
+    std::vector<int32_t> n2y((size_t)N, -1);
+    int32_t rank = 0;
+    for (int64_t w = 0; w < wpr; ++w)
+      for (uint32_t bits = mask[w]; bits; bits &= bits - 1) {
+        const uint32_t n = (uint32_t)(w * 32 + __builtin_ctz(bits));
+        const uint32_t gry = n ^ (n >> 1);
+        uint32_t rev = 0;
+        for (int b = 0; b < L; ++b) rev |= ((gry >> b) & 1u) << (L - 1 - b);
+        n2y[rev] = rank++;
+      }
+    if (cudaMalloc(&dn2y, n2y.size() * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(dpos);
+      return fail(UW_ERR_OOM, "sample table allocation failed");
+    }
+    if (cudaMemcpy(dn2y, n2y.data(), n2y.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(dn2y);
+      cudaFree(dpos);
+      return fail(UW_ERR_CUDA, "sample table upload failed");
+    }
+  }
   uint32_t* dm = nullptr;
   int32_t* dp = nullptr;
   if (cudaMalloc(&dm, words * sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&dp, words * sizeof(int32_t)) != cudaSuccess) {
     cudaFree(dm);
     cudaFree(dpos);
+    cudaFree(dn2y);
     cudaGetLastError();
     return fail(UW_ERR_OOM, "mask allocation failed");
   }
@@ -768,14 +796,17 @@ static int upload_mask(uw_plan* P, const int64_t* omega, int64_t m) {
     cudaFree(dm);
     cudaFree(dp);
     cudaFree(dpos);
+    cudaFree(dn2y);
     return fail(UW_ERR_CUDA, "mask upload failed");
   }
   cudaFree(P->d_mask);
   cudaFree(P->d_prefix);
   cudaFree(P->d_pos);
+  cudaFree(P->d_nat2y);
   P->d_mask = dm;
   P->d_prefix = dp;
   P->d_pos = dpos;
+  P->d_nat2y = dn2y;
   P->m = m;
   P->words = words;
   P->wpr = wpr;
@@ -931,6 +962,7 @@ void uw_plan_destroy(uw_plan* P) {
   cudaFree(P->d_sync);
   cudaFree(P->d_coarse);
   cudaFree(P->d_pos);
+  cudaFree(P->d_nat2y);
   delete P;
 }
 

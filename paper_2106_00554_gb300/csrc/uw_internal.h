@@ -125,6 +125,7 @@ struct Plan {
   uint32_t* d_mask = nullptr;    // words
   int32_t* d_prefix = nullptr;   // exclusive prefix count per word
   uint16_t* d_pos = nullptr;     // per sample (packed order): its natural FWHT position in the row (N <= 65536)
+  int32_t* d_nat2y = nullptr;    // 1D, 2^13 <= N <= 2^22: natural FWHT position -> index of its sample in y, or -1
   void* d_work = nullptr;
   size_t work_bytes = 0;
   void* d_stage = nullptr;       // host-API staging: two slots of (input + output)
