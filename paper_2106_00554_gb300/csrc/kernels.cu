@@ -2396,11 +2396,8 @@ static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launc
         scatter();
         fwht_big<T>(v, G.L, batch, L, false);
       }
-      L.pre("fwht_seg", 2.0 * e * (double)batch * N);
-      L.note(f32_seg_fwht(P, v, batch, L.s));
-      L.check();
-      L.pre("upconvT_1d", e * (double)batch * (M + N));
-      L.note(f32_upT_lines(P, G, v, sA, batch, L.s));
+      L.pre("fwht_seg_upT_1d", e * (double)batch * (M + N));
+      L.note(f32_seg_fwht_upT(P, G, v, sA, batch, L.s));
       L.check();
       done = true;
     }

@@ -964,23 +964,6 @@ __global__ void __launch_bounds__(SEGNT) k_up_seg(const float* __restrict__ s, f
   seg_finish(sV, v + b * N + (int64_t)seg * SEGN, tid);
 }
 
-// the Walsh-Hadamard stages of bits 0-11 of every segment of 4096, in place
-__global__ void __launch_bounds__(SEGNT) k_fwht_seg4096(float* __restrict__ v) {
-  __shared__ __align__(16) float sV[SEGV];
-  const int tid = threadIdx.x;
-  float* seg = v + (int64_t)blockIdx.x * SEGN;
-  float o[16];
-#pragma unroll
-  for (int r = 0; r < 16; r += 4) {
-    const float4 u = *reinterpret_cast<const float4*>(seg + 16 * tid + r);
-    o[r] = u.x; o[r + 1] = u.y; o[r + 2] = u.z; o[r + 3] = u.w;
-  }
-  wht<16>(o);
-  float* dst = sV + vp(16 * tid);
-#pragma unroll
-  for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(dst + r) = make_float4(o[r], o[r + 1], o[r + 2], o[r + 3]);
-  seg_finish(sV, seg, tid);
-}
 
 // taps of T^T, 2^{-R/2} folded in, zero-padded to (2 PM - 1) Q entries:
 // entry i multiplies v[Q m + (1 - PM) Q + i] for output s[m]
@@ -989,55 +972,101 @@ struct TapsT {
   float2 t2[(2 * PM - 1) * Q / 2];
 };
 
-// s = T^T v on every line (Sec. 4.2): thread t computes outputs 4 t .. 4 t + 3
-// of its line from a register window of v (interior formula; periodic plans
-// wrap the window); outputs within p of a VMP end take the exact formula.
+// outputs of T^T at each side of a segment that the fused kernel below
+// leaves to seg_upT_fix (their window reaches the neighbouring segment, or a
+// VMP end): NB, and the segment values those read, H at each end
 template <int PM, int Q>
-__global__ void __launch_bounds__(256) k_upT_lines(const float* __restrict__ v, float* __restrict__ s, TapsT<PM, Q> tp,
-                                                   Tables<float> tab, Geo G, int batch) {
-  constexpr int BO = 4, NWV = Q * (BO + 2 * PM - 2), NT2 = (2 * PM - 1) * Q / 2;
-  const int per = G.M / BO;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)batch * per) return;
-  const int64_t b = idx / per;
-  const int m0 = (int)(idx - b * per) * BO;
-  const int M = G.M, N = G.N;
-  const float* vb = v + b * N;
-  float* sb = s + b * M;
-  if (G.bd == UW_BOUNDARY_VMP && (m0 < G.p || m0 + BO > M - G.p)) {
-    const float sc = exp2f(-0.5f * (float)G.R);
-    Plain<float> va{vb};
-#pragma unroll 1
-    for (int u = 0; u < BO; ++u) sb[m0 + u] = sc * upT_one<float>(m0 + u, va, tab, G);
-    return;
-  }
-  const int k0 = Q * m0 + (1 - PM) * Q;      // even
-  float ws[NWV];
-  if (k0 >= 0 && k0 + NWV <= N) {
+struct SegUT {
+  static constexpr int BO = SEGN / Q / SEGNT;                // outputs per thread
+  static constexpr int NB = (2 * PM + BO - 1) / BO * BO;     // >= max(PM - 1, p), whole threads
+  static constexpr int H = ((NB + PM) * Q + 15) / 16 * 16;   // >= (NB + p) Q and >= (p - 1) Q
+};
+
+// the adjoint on segment `seg` of line b, after the stages across segments:
+// the Walsh-Hadamard stages of bits 0-11 in shared memory, then s = T^T v
+// for the segment's interior outputs (windows read from shared memory), and
+// the H values at each end of the transformed segment back to v for the
+// boundary outputs (seg_upT_fix)
+template <int PM, int Q>
+__global__ void __launch_bounds__(SEGNT) k_fwht_seg_upT(float* __restrict__ v, float* __restrict__ s, TapsT<PM, Q> tp,
+                                                        Geo G, int segs) {
+  using U = SegUT<PM, Q>;
+  constexpr int BO = U::BO, NT2 = (2 * PM - 1) * Q / 2;
+  constexpr int OFF = (((1 - PM) * Q) % 4 + 4) % 4;          // window start below a 4-aligned index
+  constexpr int NWV = (OFF + Q * (BO + 2 * PM - 2) + 3) / 4 * 4;
+  static_assert(BO >= 1 && (Q * BO) % 16 == 0, "outputs per thread");
+  __shared__ __align__(16) float sV[SEGV];
+  const int tid = threadIdx.x;
+  const int64_t b = blockIdx.x / segs;
+  const int seg = blockIdx.x - (int)(b * segs);
+  float* vs = v + b * G.N + (int64_t)seg * SEGN;
+  float o[16];
 #pragma unroll
-    for (int w = 0; w < NWV; w += 2) {
-      const float2 u = __ldg(reinterpret_cast<const float2*>(vb + k0 + w));
-      ws[w] = u.x;
-      ws[w + 1] = u.y;
+  for (int r = 0; r < 16; r += 4) {
+    const float4 u = *reinterpret_cast<const float4*>(vs + 16 * tid + r);
+    o[r] = u.x; o[r + 1] = u.y; o[r + 2] = u.z; o[r + 3] = u.w;
+  }
+  wht<16>(o);
+  {
+    float* dst = sV + vp(16 * tid);
+#pragma unroll
+    for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(dst + r) = make_float4(o[r], o[r + 1], o[r + 2], o[r + 3]);
+  }
+  __syncthreads();
+  pass_mid<SEGNT>(sV, 0, tid);
+  __syncthreads();
+  pass_high<SEGNT>(sV, 0, tid);
+  __syncthreads();
+  // the ends of the transformed segment, for the boundary outputs
+  for (int i = tid; i < 2 * U::H; i += SEGNT) {
+    const int k = i < U::H ? i : SEGN - 2 * U::H + i;
+    vs[k] = sV[vp(k)];
+  }
+  // interior outputs: local m in [NB, SEGN / Q - NB)
+  const int ml = BO * tid;                    // local output index of this thread's first output
+  if (ml >= U::NB && ml + BO <= SEGN / Q - U::NB) {
+    // local v index of the window start (Q ml + (1 - PM) Q), rounded down to a
+    // multiple of 4; it and the window's end stay inside the segment
+    const int k0 = Q * ml + (1 - PM) * Q - OFF;
+    float ws[NWV];
+#pragma unroll
+    for (int w = 0; w < NWV; w += 4) {
+      const float4 u = *reinterpret_cast<const float4*>(sV + vp(k0 + w));   // 4 values inside one 16-block
+      ws[w] = u.x; ws[w + 1] = u.y; ws[w + 2] = u.z; ws[w + 3] = u.w;
     }
-  } else {
+    float out[BO];
 #pragma unroll
-    for (int w = 0; w < NWV; ++w) {
-      int k = k0 + w;
-      if (G.bd == UW_BOUNDARY_PERIODIC) k &= N - 1;
-      ws[w] = (k >= 0 && k < N) ? __ldg(vb + k) : 0.f;
+    for (int u = 0; u < BO; ++u) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < NT2; ++i)
+        acc = __ffma2_rn(tp.t2[i], make_float2(ws[OFF + Q * u + 2 * i], ws[OFF + Q * u + 2 * i + 1]), acc);
+      out[u] = acc.x + acc.y;
     }
-  }
-  float o[BO];
+    float* sb = s + b * G.M + (int64_t)seg * (SEGN / Q) + ml;
 #pragma unroll
-  for (int u = 0; u < BO; ++u) {
-    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < NT2; ++i) acc = __ffma2_rn(tp.t2[i], make_float2(ws[Q * u + 2 * i], ws[Q * u + 2 * i + 1]), acc);
-    o[u] = acc.x + acc.y;
+    for (int u = 0; u < BO; ++u) sb[u] = out[u];
   }
-  *reinterpret_cast<float4*>(sb + m0) = make_float4(o[0], o[1], o[2], o[3]);
 }
+
+// the boundary outputs of T^T that k_fwht_seg_upT left: NB at each side of
+// every segment, by the exact formula (reads v only inside the ends written)
+template <int PM, int Q>
+__global__ void __launch_bounds__(256) k_seg_upT_fix(const float* __restrict__ v, float* __restrict__ s,
+                                                     Tables<float> tab, Geo G, int segs, int batch) {
+  using U = SegUT<PM, Q>;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per_line = (int64_t)segs * 2 * U::NB;
+  if (idx >= (int64_t)batch * per_line) return;
+  const int64_t b = idx / per_line;
+  const int r = (int)(idx - b * per_line);
+  const int seg = r / (2 * U::NB), j = r - seg * (2 * U::NB);
+  const int m = seg * (SEGN / Q) + (j < U::NB ? j : SEGN / Q - 2 * U::NB + j);
+  const float sc = exp2f(-0.5f * (float)G.R);
+  Plain<float> va{v + b * G.N};
+  s[b * G.M + m] = sc * upT_one<float>(m, va, tab, G);
+}
+
 
 // ---------------------------------------------------------------------------
 // 1D wavelet levels (Sec. 3.2) with register windows: a thread makes 8
@@ -1259,28 +1288,36 @@ cudaError_t f32_seg_up(const Plan& P, const Geo& G, const float* s, float* v, in
   });
 }
 
-cudaError_t f32_seg_fwht(const Plan& P, float* v, int batch, cudaStream_t st) {
-  f32k::k_fwht_seg4096<<<(unsigned)((int64_t)batch * (P.N / f32k::SEGN)), f32k::SEGNT, 0, st>>>(v);
-  return cudaGetLastError();
+
+template <int PM, int Q>
+static f32k::TapsT<PM, Q> make_tapsT(const Plan& P) {
+  f32k::TapsT<PM, Q> t;
+  float* tv = reinterpret_cast<float*>(t.t2);
+  const int p = P.p;
+  const double sc = std::exp2(-0.5 * P.R);
+  for (int i = 0; i < (2 * PM - 1) * Q; ++i) {
+    const int tt = (1 - PM) * Q + i;                    // tap position
+    const bool in = tt >= (1 - p) * Q && tt < p * Q;
+    tv[i] = in ? (float)(sc * P.taps[tt + (p - 1) * Q]) : 0.f;
+  }
+  return t;
 }
 
-cudaError_t f32_upT_lines(const Plan& P, const Geo& G, const float* v, float* s, int batch, cudaStream_t st) {
-  const int64_t threads = (int64_t)batch * (P.M / 4);
+// the adjoint's segment stages (bits 0-11) fused with T^T for every
+// segment's interior outputs, then the boundary outputs
+cudaError_t f32_seg_fwht_upT(const Plan& P, const Geo& G, float* v, float* s, int batch, cudaStream_t st) {
+  const int segs = P.N / f32k::SEGN;
   return f32_pm_dispatch(P, [&](auto pm, auto q) {
     constexpr int PM = decltype(pm)::value, Q = decltype(q)::value;
-    f32k::TapsT<PM, Q> t;
-    float* tv = reinterpret_cast<float*>(t.t2);
-    const int p = P.p;
-    const double sc = std::exp2(-0.5 * P.R);
-    for (int i = 0; i < (2 * PM - 1) * Q; ++i) {
-      const int tt = (1 - PM) * Q + i;                    // tap position
-      const bool in = tt >= (1 - p) * Q && tt < p * Q;
-      tv[i] = in ? (float)(sc * P.taps[tt + (p - 1) * Q]) : 0.f;
-    }
-    f32k::k_upT_lines<PM, Q><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(v, s, t, P.t32, G, batch);
+    f32k::k_fwht_seg_upT<PM, Q><<<(unsigned)(batch * segs), f32k::SEGNT, 0, st>>>(v, s, make_tapsT<PM, Q>(P), G, segs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t n = (int64_t)batch * segs * 2 * f32k::SegUT<PM, Q>::NB;
+    f32k::k_seg_upT_fix<PM, Q><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, s, P.t32, G, segs, batch);
     return cudaGetLastError();
   });
 }
+
 
 template <int PM>
 static f32k::HGTaps<PM> make_hg(const Plan& P) {

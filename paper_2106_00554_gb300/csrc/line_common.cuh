@@ -488,8 +488,7 @@ bool f32_eligible(const Plan& P, const LineIO& io, const void* in, const void* o
 // long 1D lines on FP32 (kernels_f32.cu)
 bool f32_seg_eligible(const Plan& P);
 cudaError_t f32_seg_up(const Plan& P, const Geo& G, const float* s, float* v, int batch, cudaStream_t st);
-cudaError_t f32_seg_fwht(const Plan& P, float* v, int batch, cudaStream_t st);
-cudaError_t f32_upT_lines(const Plan& P, const Geo& G, const float* v, float* s, int batch, cudaStream_t st);
+cudaError_t f32_seg_fwht_upT(const Plan& P, const Geo& G, float* v, float* s, int batch, cudaStream_t st);
 cudaError_t f32_syn1d_levels(const Plan& P, const Geo& G, const float* x, float* out, int jto, size_t smem, int batch,
                              cudaStream_t st);
 cudaError_t f32_syn1d_level(const Plan& P, const Geo& G, const float* lo, const float* hi, float* out, int n0, int batch,
