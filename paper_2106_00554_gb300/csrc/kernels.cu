@@ -147,6 +147,9 @@ __global__ void __launch_bounds__(1024) k_syn1d_levels(const T* __restrict__ x, 
   pdl_wait();
   const T* xb = x + (int64_t)blockIdx.x * in_bs;
   T* ob = out + (int64_t)blockIdx.x * out_bs;
+  // the whole line of coefficients into L2: each level here and the level
+  // kernels after this one read their details from there instead of DRAM
+  if (tid == 0) prefetch_l2_bulk(xb, (int64_t)sizeof(T) * in_bs);
   T* P0 = sm + ((off + 3) & ~3);
   T* P1 = P0 + (1 << (jto - 1));
   for (int k = tid; k < (1 << J0); k += nthr) P0[k] = xb[k];
@@ -327,6 +330,8 @@ __global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2, 
                                                      int64_t m = 0) {
   constexpr int n1 = 1 << L1, NR = n1 / 8;
   __shared__ T S[n1][33];
+  pdl_trigger();
+  pdl_wait();
   const int tid = threadIdx.x, c = tid & 31, g = tid >> 5;
   const int64_t n2 = (int64_t)1 << L2;
   const int tiles = (int)(n2 / 32);
@@ -2249,8 +2254,12 @@ static bool cols_with_samples(const Plan& P, T* v, const T* yin, T* yout, int ba
          sizeof(T) * (double)batch * ((double)(1LL << L) + 2.0 * P.m) + 4.0 * (double)(1LL << L));
   auto go = [&](auto l1) {
     constexpr int LL = decltype(l1)::value;
-    if (mode == 1) k_fwht_cols32<T, LL, 1><<<grid, 256, 0, Lc.s>>>(v, L2, P.d_nat2y, nullptr, yout, P.m);
-    else k_fwht_cols32<T, LL, 2><<<grid, 256, 0, Lc.s>>>(v, L2, P.d_nat2y, yin, nullptr, P.m);
+    if (mode == 1)
+      Lc.note(launch_pdl(k_fwht_cols32<T, LL, 1>, grid, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y,
+                         (const T*)nullptr, yout, (int64_t)P.m));
+    else
+      Lc.note(launch_pdl(k_fwht_cols32<T, LL, 2>, grid, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y, yin,
+                         (T*)nullptr, (int64_t)P.m));
   };
   if (L1 == 3) go(std::integral_constant<int, 3>{});
   else if (L1 == 4) go(std::integral_constant<int, 4>{});

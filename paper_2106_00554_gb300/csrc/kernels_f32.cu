@@ -924,6 +924,8 @@ __global__ void __launch_bounds__(SEGNT) k_up_seg(const float* __restrict__ s, f
                                                   Tables<float> tab, Geo G, int segs) {
   constexpr int BS = 16 / Q, NW = BS + 2 * PM - 2;
   __shared__ __align__(16) float sV[SEGV];
+  pdl_trigger();
+  pdl_wait();
   const int tid = threadIdx.x;
   const int64_t b = blockIdx.x / segs;
   const int seg = blockIdx.x - (int)(b * segs);
@@ -991,6 +993,8 @@ template <int PM, int Q>
 __global__ void __launch_bounds__(SEGNT) k_fwht_seg_upT(float* __restrict__ v, float* __restrict__ s, TapsT<PM, Q> tp,
                                                         Geo G, int segs) {
   using U = SegUT<PM, Q>;
+  pdl_trigger();
+  pdl_wait();
   constexpr int BO = U::BO, NT2 = (2 * PM - 1) * Q / 2;
   constexpr int OFF = (((1 - PM) * Q) % 4 + 4) % 4;          // window start below a 4-aligned index
   constexpr int NWV = (OFF + Q * (BO + 2 * PM - 2) + 3) / 4 * 4;
@@ -1055,6 +1059,8 @@ template <int PM, int Q>
 __global__ void __launch_bounds__(256) k_seg_upT_fix(const float* __restrict__ v, float* __restrict__ s,
                                                      Tables<float> tab, Geo G, int segs, int batch) {
   using U = SegUT<PM, Q>;
+  pdl_trigger();
+  pdl_wait();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t per_line = (int64_t)segs * 2 * U::NB;
   if (idx >= (int64_t)batch * per_line) return;
@@ -1193,6 +1199,9 @@ __global__ void __launch_bounds__(1024) k_syn1d_levels_f32(const float* __restri
   pdl_wait();
   const float* xb = x + (int64_t)blockIdx.x * in_bs;
   float* ob = out + (int64_t)blockIdx.x * out_bs;
+  // the whole line of coefficients into L2: each level here and the level
+  // kernels after this one read their details from there instead of DRAM
+  if (tid == 0) prefetch_l2_bulk(xb, 4 * in_bs);
   float* P0 = sm + ((off + 3) & ~3);
   float* P1 = P0 + (1 << (jto - 1));
   for (int k = tid; k < (1 << J0); k += nthr) P0[k] = xb[k];
@@ -1221,6 +1230,8 @@ __global__ void __launch_bounds__(256) k_syn1d_level_f32(const float* __restrict
                                                          const float* __restrict__ hi, int64_t hi_bs,
                                                          float* __restrict__ out, int64_t out_bs, int n0, HGTaps<PM> tp,
                                                          Tables<float> tab, Geo G, int batch) {
+  pdl_trigger();
+  pdl_wait();
   const int per = (2 * n0) / 8;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)batch * per) return;
@@ -1233,6 +1244,8 @@ __global__ void __launch_bounds__(256) k_ana1d_level_f32(const float* __restrict
                                                          float* __restrict__ lo, int64_t lo_bs, float* __restrict__ hi,
                                                          int64_t hi_bs, int n0, HGTaps<PM> tp, Tables<float> tab, Geo G,
                                                          int batch) {
+  pdl_trigger();
+  pdl_wait();
   const int per = n0 / 4;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)batch * per) return;
@@ -1282,9 +1295,8 @@ cudaError_t f32_seg_up(const Plan& P, const Geo& G, const float* s, float* v, in
   const int segs = P.N / f32k::SEGN;
   return f32_pm_dispatch(P, [&](auto pm, auto q) {
     constexpr int PM = decltype(pm)::value, Q = decltype(q)::value;
-    f32k::k_up_seg<PM, Q><<<(unsigned)(batch * segs), f32k::SEGNT, 0, st>>>(s, v, f32k::make_taps<PM, Q>(P), P.t32, G,
-                                                                            segs);
-    return cudaGetLastError();
+    return launch_pdl(f32k::k_up_seg<PM, Q>, dim3((unsigned)(batch * segs)), dim3(f32k::SEGNT), 0, st, s, v,
+                      f32k::make_taps<PM, Q>(P), P.t32, G, segs);
   });
 }
 
@@ -1309,12 +1321,12 @@ cudaError_t f32_seg_fwht_upT(const Plan& P, const Geo& G, float* v, float* s, in
   const int segs = P.N / f32k::SEGN;
   return f32_pm_dispatch(P, [&](auto pm, auto q) {
     constexpr int PM = decltype(pm)::value, Q = decltype(q)::value;
-    f32k::k_fwht_seg_upT<PM, Q><<<(unsigned)(batch * segs), f32k::SEGNT, 0, st>>>(v, s, make_tapsT<PM, Q>(P), G, segs);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(f32k::k_fwht_seg_upT<PM, Q>, dim3((unsigned)(batch * segs)), dim3(f32k::SEGNT), 0, st,
+                               v, s, make_tapsT<PM, Q>(P), G, segs);
     if (e != cudaSuccess) return e;
     const int64_t n = (int64_t)batch * segs * 2 * f32k::SegUT<PM, Q>::NB;
-    f32k::k_seg_upT_fix<PM, Q><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, s, P.t32, G, segs, batch);
-    return cudaGetLastError();
+    return launch_pdl(f32k::k_seg_upT_fix<PM, Q>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st,
+                      (const float*)v, s, P.t32, G, segs, batch);
   });
 }
 
@@ -1355,9 +1367,8 @@ cudaError_t f32_syn1d_level(const Plan& P, const Geo& G, const float* lo, const 
   const int64_t threads = (int64_t)batch * (2 * n0 / 8);
   return hg_dispatch(P, [&](auto pm) {
     constexpr int PM = decltype(pm)::value;
-    f32k::k_syn1d_level_f32<PM><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(lo, P.M, hi, P.M, out, P.M, n0,
-                                                                                   make_hg<PM>(P), P.t32, G, batch);
-    return cudaGetLastError();
+    return launch_pdl(f32k::k_syn1d_level_f32<PM>, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, st, lo,
+                      (int64_t)P.M, hi, (int64_t)P.M, out, (int64_t)P.M, n0, make_hg<PM>(P), P.t32, G, batch);
   });
 }
 
@@ -1366,9 +1377,8 @@ cudaError_t f32_ana1d_level(const Plan& P, const Geo& G, const float* in, float*
   const int64_t threads = (int64_t)batch * (n0 / 4);
   return hg_dispatch(P, [&](auto pm) {
     constexpr int PM = decltype(pm)::value;
-    f32k::k_ana1d_level_f32<PM><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(in, P.M, lo, P.M, hi, P.M, n0,
-                                                                                   make_hg<PM>(P), P.t32, G, batch);
-    return cudaGetLastError();
+    return launch_pdl(f32k::k_ana1d_level_f32<PM>, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, st, in,
+                      (int64_t)P.M, lo, (int64_t)P.M, hi, (int64_t)P.M, n0, make_hg<PM>(P), P.t32, G, batch);
   });
 }
 

@@ -454,6 +454,17 @@ __device__ __forceinline__ int sample_index(const uint32_t* smask, const int* sp
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
+// [p, p + bytes) into L2 by bulk prefetches of up to 64 KB (one thread);
+// skipped unless p and bytes are multiples of 16
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, int64_t bytes) {
+  if ((reinterpret_cast<uintptr_t>(p) & 15) || (bytes & 15)) return;
+  const char* a = reinterpret_cast<const char*>(p);
+  for (int64_t o = 0; o < bytes; o += 65536) {
+    const uint32_t n = (uint32_t)(bytes - o < 65536 ? bytes - o : 65536);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a + o), "r"(n) : "memory");
+  }
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args) {
