@@ -1143,45 +1143,142 @@ __device__ __forceinline__ void ana4(const float* s, int n1, int g, bool per, co
   }
 }
 
-// one synthesis level: the 8 outputs of group g into o[8 g ..)
+// One output of a VMP synthesis level by the exact formula (Sec. 3.2
+// boundary functions), the same sums in the same order as syn_one, with the
+// loops unrolled to the compile-time filter bound so that all loads of the
+// output are issued together.
 template <int PM, typename TB>
-__device__ __forceinline__ void syn_group(const float* lo, const float* hi, float* o, int n0, int g,
+__device__ __forceinline__ float syn_one_u(int k, int n0, const float* lo, const float* hi, const TB& t, const Geo& G) {
+  const int p = G.p, n1 = 2 * n0, Lb = G.Lb;
+  const int mlo = max(p, (k - p + 1) >> 1), mhi = min(n0 - p - 1, (k + p - 1) >> 1);   // at most p terms
+  float acc = 0.f;
+#pragma unroll
+  for (int d = 0; d < PM; ++d) {
+    const int m = mlo + d;
+    if (m <= mhi) {
+      const int l = k - 2 * m + p - 1;
+      acc += t.h[l] * lo[m] + t.g[l] * hi[m];
+    }
+  }
+  if (k < Lb) {
+#pragma unroll
+    for (int m = 0; m < PM; ++m)
+      if (m < p) acc += t.PL[m * Lb + k] * lo[m] + t.QL[m * Lb + k] * hi[m];
+  }
+  const int c = n1 - 1 - k;
+  if (c < Lb) {
+#pragma unroll
+    for (int r = 0; r < PM; ++r)
+      if (r < p) acc += t.PR[r * Lb + c] * lo[n0 - 1 - r] + t.QR[r * Lb + c] * hi[n0 - 1 - r];
+  }
+  return acc;
+}
+
+// One output pair of a VMP analysis level by the exact formula, as ana_one
+// (same sums, same order), unrolled to the compile-time filter bound.
+template <int PM, typename TB>
+__device__ __forceinline__ void ana_one_u(int m, int n0, const float* s, const TB& t, const Geo& G, float& lo,
+                                          float& hi) {
+  const int p = G.p, n1 = 2 * n0, Lb = G.Lb;   // Lb = 3p - 1 < 3 PM
+  float a = 0.f, b = 0.f;
+  if (m < p) {
+#pragma unroll
+    for (int c = 0; c < 3 * PM; ++c)
+      if (c < Lb) {
+        const float v = s[c];
+        a += t.PL[m * Lb + c] * v;
+        b += t.QL[m * Lb + c] * v;
+      }
+  } else if (m >= n0 - p) {
+    const int r = n0 - 1 - m;
+#pragma unroll
+    for (int c = 0; c < 3 * PM; ++c)
+      if (c < Lb) {
+        const float v = s[n1 - 1 - c];
+        a += t.PR[r * Lb + c] * v;
+        b += t.QR[r * Lb + c] * v;
+      }
+  } else {
+#pragma unroll
+    for (int d = 0; d < 2 * PM; ++d)
+      if (d < 2 * p) {
+        const float v = s[2 * m + d - p + 1];
+        a += t.h[d] * v;
+        b += t.g[d] * v;
+      }
+  }
+  lo = a;
+  hi = b;
+}
+
+// the lane of warp-mask `em` that holds the j-th set bit (lane 0 if none)
+__device__ __forceinline__ int nth_lane(unsigned em, int j) {
+  for (int i = 0; i < j && em; ++i) em &= em - 1;
+  return em ? __ffs(em) - 1 : 0;
+}
+
+// One synthesis level, groups of 8 outputs; every lane of the warp calls it
+// (valid: the lane has a group).  Interior groups by the register-window
+// formula.  The outputs of the groups near a VMP end are then shared out
+// over the warp, one per lane, 4 groups per round: computed one after
+// another by the group's own thread they put a chain of memory round trips
+// on the critical path of the level.
+template <int PM, typename TB>
+__device__ __forceinline__ void syn_group(const float* lo, const float* hi, float* o, int n0, int g, bool valid,
                                           const HGTaps<PM>& tp, const TB& tab, const Geo& G) {
   const int n1 = 2 * n0, k0 = 8 * g;
   const bool per = G.bd == UW_BOUNDARY_PERIODIC;
-  if (!per && (k0 < G.Lb || k0 + 8 > n1 - G.Lb)) {
-    Plain<float> l{lo}, h{hi};
-#pragma unroll 1
-    for (int r = 0; r < 8; ++r) o[k0 + r] = syn_one<float>(k0 + r, n0, l, h, tab, G);
-    return;
+  const bool edge = valid && !per && (k0 < G.Lb || k0 + 8 > n1 - G.Lb);
+  if (valid && !edge) {
+    float v[8];
+    syn8<PM>(lo, hi, n0, g, per, tp, v);
+    *reinterpret_cast<float4*>(o + k0) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(o + k0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
   }
-  float v[8];
-  syn8<PM>(lo, hi, n0, g, per, tp, v);
-  *reinterpret_cast<float4*>(o + k0) = make_float4(v[0], v[1], v[2], v[3]);
-  *reinterpret_cast<float4*>(o + k0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  const unsigned em = __ballot_sync(0xffffffffu, edge);
+  if (!em) return;
+  const int lane = threadIdx.x & 31, ne = __popc(em);
+  for (int base = 0; base < ne; base += 4) {
+    const int j = base + (lane >> 3), src = nth_lane(em, j);
+    const int ks = __shfl_sync(0xffffffffu, k0, src) + (lane & 7);
+    const float* ls = reinterpret_cast<const float*>(__shfl_sync(0xffffffffu, (unsigned long long)lo, src));
+    const float* hs = reinterpret_cast<const float*>(__shfl_sync(0xffffffffu, (unsigned long long)hi, src));
+    float* os = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, (unsigned long long)o, src));
+    if (j < ne) os[ks] = syn_one_u<PM>(ks, n0, ls, hs, tab, G);
+  }
 }
 
-// one analysis level: the 4 pairs of group g
+// One analysis level, groups of 4 pairs; every lane of the warp calls it.
+// Interior groups by the register-window formula, the pairs of the groups
+// near a VMP end shared out over the warp, one per lane, 8 groups per round.
 template <int PM, typename TB>
-__device__ __forceinline__ void ana_group(const float* s, float* lo, float* hi, int n0, int g, const HGTaps<PM>& tp,
-                                          const TB& tab, const Geo& G) {
+__device__ __forceinline__ void ana_group(const float* s, float* lo, float* hi, int n0, int g, bool valid,
+                                          const HGTaps<PM>& tp, const TB& tab, const Geo& G) {
   const int m0 = 4 * g;
   const bool per = G.bd == UW_BOUNDARY_PERIODIC;
-  if (!per && (m0 < G.p || m0 + 4 > n0 - G.p)) {
-    Plain<float> sa{s};
-#pragma unroll 1
-    for (int r = 0; r < 4; ++r) {
-      float a, b;
-      ana_one<float>(m0 + r, n0, sa, tab, G, a, b);
-      lo[m0 + r] = a;
-      hi[m0 + r] = b;
-    }
-    return;
+  const bool edge = valid && !per && (m0 < G.p || m0 + 4 > n0 - G.p);
+  if (valid && !edge) {
+    float a[4], b[4];
+    ana4<PM>(s, 2 * n0, g, per, tp, a, b);
+    *reinterpret_cast<float4*>(lo + m0) = make_float4(a[0], a[1], a[2], a[3]);
+    *reinterpret_cast<float4*>(hi + m0) = make_float4(b[0], b[1], b[2], b[3]);
   }
-  float a[4], b[4];
-  ana4<PM>(s, 2 * n0, g, per, tp, a, b);
-  *reinterpret_cast<float4*>(lo + m0) = make_float4(a[0], a[1], a[2], a[3]);
-  *reinterpret_cast<float4*>(hi + m0) = make_float4(b[0], b[1], b[2], b[3]);
+  const unsigned em = __ballot_sync(0xffffffffu, edge);
+  if (!em) return;
+  const int lane = threadIdx.x & 31, ne = __popc(em);
+  for (int base = 0; base < ne; base += 8) {
+    const int j = base + (lane >> 2), src = nth_lane(em, j);
+    const int ms = __shfl_sync(0xffffffffu, m0, src) + (lane & 3);
+    const float* ss = reinterpret_cast<const float*>(__shfl_sync(0xffffffffu, (unsigned long long)s, src));
+    float* los = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, (unsigned long long)lo, src));
+    float* his = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, (unsigned long long)hi, src));
+    if (j < ne) {
+      float a, b;
+      ana_one_u<PM>(ms, n0, ss, tab, G, a, b);
+      los[ms] = a;
+      his[ms] = b;
+    }
+  }
 }
 
 // the coarse synthesis levels J0 .. jto-1 of one line per CTA in shared
@@ -1212,7 +1309,7 @@ __global__ void __launch_bounds__(1024) k_syn1d_levels_f32(const float* __restri
     const int n0 = 1 << j, n1 = 2 * n0;
     float* o = j + 1 == jto ? ob : dst;
     if (n1 / 8 >= nthr) {   // groups of 8 once they fill the CTA; small levels are latency-bound
-      for (int g = tid; g < n1 / 8; g += nthr) syn_group<PM>(src, xb + n0, o, n0, g, tp, st, G);
+      for (int g = tid; g < n1 / 8; g += nthr) syn_group<PM>(src, xb + n0, o, n0, g, true, tp, st, G);
     } else {
       Plain<float> lo{src}, hi{xb + n0};
       for (int k = tid; k < n1; k += nthr) o[k] = syn_one<float>(k, n0, lo, hi, st, G);
@@ -1234,9 +1331,10 @@ __global__ void __launch_bounds__(256) k_syn1d_level_f32(const float* __restrict
   pdl_wait();
   const int per = (2 * n0) / 8;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)batch * per) return;
-  const int64_t b = idx / per;
-  syn_group<PM>(lo + b * lo_bs, hi + b * hi_bs, out + b * out_bs, n0, (int)(idx - b * per), tp, tab, G);
+  const bool valid = idx < (int64_t)batch * per;     // whole warps take part in the edge rounds
+  const int64_t b = valid ? idx / per : 0;
+  syn_group<PM>(lo + b * lo_bs, hi + b * hi_bs, out + b * out_bs, n0, valid ? (int)(idx - b * per) : 0, valid, tp, tab,
+                G);
 }
 
 template <int PM>
@@ -1248,9 +1346,10 @@ __global__ void __launch_bounds__(256) k_ana1d_level_f32(const float* __restrict
   pdl_wait();
   const int per = n0 / 4;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)batch * per) return;
-  const int64_t b = idx / per;
-  ana_group<PM>(in + b * in_bs, lo + b * lo_bs, hi + b * hi_bs, n0, (int)(idx - b * per), tp, tab, G);
+  const bool valid = idx < (int64_t)batch * per;     // whole warps take part in the edge rounds
+  const int64_t b = valid ? idx / per : 0;
+  ana_group<PM>(in + b * in_bs, lo + b * lo_bs, hi + b * hi_bs, n0, valid ? (int)(idx - b * per) : 0, valid, tp, tab,
+                G);
 }
 
 }  // namespace f32k
