@@ -2440,9 +2440,13 @@ static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launc
     const size_t sm = fused1d_smem<T>(P, jfrom);
     L.pre("ana_levels_1d", e * 2.0 * batch * (double)(1 << jfrom));
     // (the per-pair formula: windows of groups would read shared memory 8 words apart per lane)
-    set_smem<T>((const void*)k_ana1d_levels<T>, sm);
-    L.note(launch_pdl(k_ana1d_levels<T>, dim3(batch), dim3(1024), sm, L.s, (const T*)cur, (int64_t)M, x, tabs<T>(P), G,
-                      P.J0, jfrom, (int64_t)M));
+    if (f32) {   // FP32, x 16-byte aligned (the groups store 16 bytes at a time into x)
+      if constexpr (std::is_same<T, float>::value) L.note(f32_ana1d_levels(P, G, cur, x, jfrom, sm, batch, L.s));
+    } else {
+      set_smem<T>((const void*)k_ana1d_levels<T>, sm);
+      L.note(launch_pdl(k_ana1d_levels<T>, dim3(batch), dim3(1024), sm, L.s, (const T*)cur, (int64_t)M, x, tabs<T>(P),
+                        G, P.J0, jfrom, (int64_t)M));
+    }
     L.check();
   }
 }

@@ -1093,13 +1093,35 @@ __device__ __forceinline__ void syn8(const float* lo, const float* hi, int n0, i
   constexpr int NW = 4 + PM;
   const int i0 = 4 * g - PM / 2;
   float wl[NW], wh[NW];
+  // inside the line and 16-byte aligned: the window as aligned 16-byte
+  // vectors from a0 = 4 g - S (lanes 16 bytes apart: no shared-memory bank
+  // conflicts, a quarter of the load instructions)
+  constexpr int S = (PM / 2 + 3) / 4 * 4, NV = (S + 4 + PM / 2 + 3) / 4;
+  const int a0 = 4 * g - S;
+  if (a0 >= 0 && a0 + 4 * NV <= n0 &&
+      !((reinterpret_cast<uintptr_t>(lo + a0) | reinterpret_cast<uintptr_t>(hi + a0)) & 15)) {
+    float vl[4 * NV], vh[4 * NV];
 #pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    int m = i0 + w;
-    if (per) m &= n0 - 1;
-    const bool ok = m >= 0 && m < n0;
-    wl[w] = ok ? lo[m] : 0.f;
-    wh[w] = ok ? hi[m] : 0.f;
+    for (int v = 0; v < NV; ++v) {
+      const float4 a = reinterpret_cast<const float4*>(lo + a0)[v];
+      const float4 b = reinterpret_cast<const float4*>(hi + a0)[v];
+      vl[4 * v] = a.x; vl[4 * v + 1] = a.y; vl[4 * v + 2] = a.z; vl[4 * v + 3] = a.w;
+      vh[4 * v] = b.x; vh[4 * v + 1] = b.y; vh[4 * v + 2] = b.z; vh[4 * v + 3] = b.w;
+    }
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      wl[w] = vl[w + S - PM / 2];
+      wh[w] = vh[w + S - PM / 2];
+    }
+  } else {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      int m = i0 + w;
+      if (per) m &= n0 - 1;
+      const bool ok = m >= 0 && m < n0;
+      wl[w] = ok ? lo[m] : 0.f;
+      wh[w] = ok ? hi[m] : 0.f;
+    }
   }
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) {
@@ -1122,11 +1144,26 @@ __device__ __forceinline__ void ana4(const float* s, int n1, int g, bool per, co
   constexpr int NW = 8 + 2 * PM;
   const int i0 = 8 * g - PM;
   float ws[NW];
+  // inside the line and 16-byte aligned: aligned 16-byte vectors from
+  // a0 = 8 g - S (as in syn8)
+  constexpr int S = (PM + 3) / 4 * 4, NV = (S + 8 + PM + 3) / 4;
+  const int a0 = 8 * g - S;
+  if (a0 >= 0 && a0 + 4 * NV <= n1 && !(reinterpret_cast<uintptr_t>(s + a0) & 15)) {
+    float vs[4 * NV];
 #pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    int k = i0 + w;
-    if (per) k &= n1 - 1;
-    ws[w] = (k >= 0 && k < n1) ? s[k] : 0.f;
+    for (int v = 0; v < NV; ++v) {
+      const float4 a = reinterpret_cast<const float4*>(s + a0)[v];
+      vs[4 * v] = a.x; vs[4 * v + 1] = a.y; vs[4 * v + 2] = a.z; vs[4 * v + 3] = a.w;
+    }
+#pragma unroll
+    for (int w = 0; w < NW; ++w) ws[w] = vs[w + S - PM];
+  } else {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      int k = i0 + w;
+      if (per) k &= n1 - 1;
+      ws[w] = (k >= 0 && k < n1) ? s[k] : 0.f;
+    }
   }
 #pragma unroll
   for (int bb = 0; bb < 4; ++bb) {
@@ -1286,7 +1323,7 @@ __device__ __forceinline__ void ana_group(const float* s, float* lo, float* hi, 
 template <int PM>
 __global__ void __launch_bounds__(1024) k_syn1d_levels_f32(const float* __restrict__ x, float* __restrict__ out,
                                                            int64_t out_bs, HGTaps<PM> tp, Tables<float> tab, Geo G,
-                                                           int J0, int jto, int64_t in_bs) {
+                                                           int J0, int jto, int64_t in_bs, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1301,6 +1338,13 @@ __global__ void __launch_bounds__(1024) k_syn1d_levels_f32(const float* __restri
   if (tid == 0) prefetch_l2_bulk(xb, 4 * in_bs);
   float* P0 = sm + ((off + 3) & ~3);
   float* P1 = P0 + (1 << (jto - 1));
+  // stage: the last level's details (2^(jto-1) values, the largest level)
+  // are copied into shared memory while the lower levels run, so that level
+  // does not wait on global memory once per group
+  float* D = P1 + (1 << (jto - 1));
+  if (stage)
+    for (int i = 4 * tid; i < (1 << (jto - 1)); i += 4 * nthr) cp16(D + i, xb + (1 << (jto - 1)) + i);
+  cp_commit();
   for (int k = tid; k < (1 << J0); k += nthr) P0[k] = xb[k];
   __syncthreads();
   float* src = P0;
@@ -1308,16 +1352,75 @@ __global__ void __launch_bounds__(1024) k_syn1d_levels_f32(const float* __restri
   for (int j = J0; j < jto; ++j) {
     const int n0 = 1 << j, n1 = 2 * n0;
     float* o = j + 1 == jto ? ob : dst;
+    const bool staged = stage && j + 1 == jto;
+    if (staged) {
+      cp_wait<0>();
+      __syncthreads();
+    }
+    const float* hd = staged ? D : xb + n0;
     if (n1 / 8 >= nthr) {   // groups of 8 once they fill the CTA; small levels are latency-bound
-      for (int g = tid; g < n1 / 8; g += nthr) syn_group<PM>(src, xb + n0, o, n0, g, true, tp, st, G);
-    } else {
-      Plain<float> lo{src}, hi{xb + n0};
+      for (int g = tid; g < n1 / 8; g += nthr) syn_group<PM>(src, hd, o, n0, g, true, tp, st, G);
+    } else if (G.bd == UW_BOUNDARY_PERIODIC) {
+      Plain<float> lo{src}, hi{hd};
       for (int k = tid; k < n1; k += nthr) o[k] = syn_one<float>(k, n0, lo, hi, st, G);
+    } else {
+      for (int k = tid; k < n1; k += nthr) o[k] = syn_one_u<PM>(k, n0, src, hd, st, G);
     }
     __syncthreads();
     float* t = src;
     src = dst;
     dst = t;
+  }
+}
+
+// The transposed steps: the analysis levels jfrom-1 .. J0 of one line per
+// CTA.  Every level writes its details to x[2^j, 2^(j+1)) and its low-pass
+// half to shared memory (the last one to x[0, 2^J0)); groups of 4 pairs
+// once they fill the CTA, the per-pair formula below that.  stage: the
+// input s_jfrom (2^jfrom values, the previous kernel's output) is first
+// copied into the second buffer and the room after it, so the first level,
+// the largest, reads shared memory rather than global memory pair by pair.
+template <int PM>
+__global__ void __launch_bounds__(1024) k_ana1d_levels_f32(const float* __restrict__ in, int64_t in_bs,
+                                                           float* __restrict__ x, HGTaps<PM> tp, Tables<float> tab,
+                                                           Geo G, int J0, int jfrom, int64_t out_bs, int stage) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  SmemTables<float> st;
+  const int off = stage_tables(tab, G, sm, st, tid, nthr);
+  pdl_trigger();
+  pdl_wait();
+  const float* ib = in + (int64_t)blockIdx.x * in_bs;
+  float* xb = x + (int64_t)blockIdx.x * out_bs;
+  float* P0 = sm + ((off + 3) & ~3);
+  float* P1 = P0 + (1 << (jfrom - 1));
+  const float* src = ib;
+  if (stage) {
+    for (int i = 4 * tid; i < (1 << jfrom); i += 4 * nthr) cp16(P1 + i, ib + i);
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+    src = P1;
+  }
+  float* dst = P0;
+  for (int j = jfrom - 1; j >= J0; --j) {
+    const int n0 = 1 << j;
+    float* lo_out = j == J0 ? xb : dst;
+    if (n0 / 4 >= nthr && j > J0) {   // groups of 4 pairs once they fill the CTA
+      for (int g = tid; g < n0 / 4; g += nthr) ana_group<PM>(src, lo_out, xb + n0, n0, g, true, tp, st, G);
+    } else {
+      Plain<float> sa{src};
+      for (int m = tid; m < n0; m += nthr) {
+        float lo, hi;
+        ana_one<float>(m, n0, sa, st, G, lo, hi);
+        lo_out[m] = lo;
+        xb[n0 + m] = hi;
+      }
+    }
+    __syncthreads();
+    src = dst;
+    dst = dst == P0 ? P1 : P0;
   }
 }
 
@@ -1455,9 +1558,34 @@ cudaError_t f32_syn1d_levels(const Plan& P, const Geo& G, const float* x, float*
   return hg_dispatch(P, [&](auto pm) {
     constexpr int PM = decltype(pm)::value;
     auto kern = f32k::k_syn1d_levels_f32<PM>;
-    cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return launch_pdl(kern, dim3(batch), dim3(1024), smem, st, x, out, (int64_t)P.M, make_hg<PM>(P), P.t32, G, P.J0,
-                      jto, (int64_t)P.M);
+    // room for the last level's details as well: stage them in shared memory
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t add = sizeof(float) << (jto - 1);
+    const int stage = smem + add <= (size_t)optin && ((uintptr_t)x & 15u) == 0 && P.M % 4 == 0 && jto >= 3;
+    const size_t sm = stage ? smem + add : smem;
+    cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return launch_pdl(kern, dim3(batch), dim3(1024), sm, st, x, out, (int64_t)P.M, make_hg<PM>(P), P.t32, G, P.J0,
+                      jto, (int64_t)P.M, stage);
+  });
+}
+
+cudaError_t f32_ana1d_levels(const Plan& P, const Geo& G, const float* in, float* x, int jfrom, size_t smem,
+                             int batch, cudaStream_t st) {
+  return hg_dispatch(P, [&](auto pm) {
+    constexpr int PM = decltype(pm)::value;
+    auto kern = f32k::k_ana1d_levels_f32<PM>;
+    // room for the whole input line: stage it in shared memory
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t add = sizeof(float) << (jfrom - 1);
+    const int stage = smem + add <= (size_t)optin && ((uintptr_t)in & 15u) == 0 && P.M % 4 == 0 && jfrom >= 2;
+    const size_t sm = stage ? smem + add : smem;
+    cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return launch_pdl(kern, dim3(batch), dim3(1024), sm, st, in, (int64_t)P.M, x, make_hg<PM>(P), P.t32, G, P.J0,
+                      jfrom, (int64_t)P.M, stage);
   });
 }
 

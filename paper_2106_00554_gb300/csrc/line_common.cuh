@@ -502,6 +502,8 @@ cudaError_t f32_seg_up(const Plan& P, const Geo& G, const float* s, float* v, in
 cudaError_t f32_seg_fwht_upT(const Plan& P, const Geo& G, float* v, float* s, int batch, cudaStream_t st);
 cudaError_t f32_syn1d_levels(const Plan& P, const Geo& G, const float* x, float* out, int jto, size_t smem, int batch,
                              cudaStream_t st);
+cudaError_t f32_ana1d_levels(const Plan& P, const Geo& G, const float* in, float* x, int jfrom, size_t smem,
+                             int batch, cudaStream_t st);
 cudaError_t f32_syn1d_level(const Plan& P, const Geo& G, const float* lo, const float* hi, float* out, int n0, int batch,
                             cudaStream_t st);
 cudaError_t f32_ana1d_level(const Plan& P, const Geo& G, const float* in, float* lo, float* hi, int n0, int batch,

@@ -100,6 +100,43 @@ def test_1d_large_lines_against_algorithm1(prec, R, q, p, bd):
     assert rel(run_adj(plan, y, prec), fast.adjoint1d(y, R, q, p, bd, J0, omega)) < TOL[prec]
 
 
+@pytest.mark.parametrize("bd", [VMP, PERIODIC])
+def test_1d_large_lines_unaligned_buffers(bd):
+    """FP32 lines longer than shared memory with x and y buffers 4 bytes off
+    a 16-byte boundary (views one element into larger tensors): the kernels
+    that move 16 bytes at a time fall back to their scalar forms.  The
+    forward matches the aligned call bit for bit (same arithmetic); the
+    adjoint's levels take the generic per-pair kernels, so it matches to
+    rounding; both match Algorithm 1."""
+    import torch
+    rng = np.random.default_rng(77 + bd)
+    R, q, p = 14, 2, 4
+    J0 = W.default_J0(p)
+    M, N = 2 ** R, 2 ** (R + q)
+    omega = inputs.mask_1d(rng, N, 0.2)
+    plan = Plan(1, R, q, p, bd, omega=omega, max_batch=2)
+    x = inputs.coeffs_1d(rng, R, J0, 1.5, batch=2)
+    y = rng.standard_normal((2, omega.size))
+    xa, ya = dev(x, F32), dev(y, F32)
+    bx = torch.zeros(2 * M + 1, dtype=torch.float32, device="cuda")
+    by = torch.zeros(2 * omega.size + 1, dtype=torch.float32, device="cuda")
+    xu, yu = bx[1:].view(2, M), by[1:].view(2, omega.size)
+    xu.copy_(xa)
+    yu.copy_(ya)
+    assert xu.data_ptr() % 16 and yu.data_ptr() % 16
+    got_y = torch.zeros(2 * omega.size + 1, dtype=torch.float32, device="cuda")[1:].view(2, omega.size)
+    got_x = torch.zeros(2 * M + 1, dtype=torch.float32, device="cuda")[1:].view(2, M)
+    plan.forward(xu, got_y, precision=F32)
+    plan.adjoint(yu, got_x, precision=F32)
+    want_y = plan.forward(xa, precision=F32)
+    want_x = plan.adjoint(ya, precision=F32)
+    torch.cuda.synchronize()
+    assert torch.equal(got_y, want_y)
+    assert rel(got_x.double().cpu().numpy(), want_x.double().cpu().numpy()) < 1e-6
+    assert rel(got_y.double().cpu().numpy(), fast.forward1d(x, R, q, p, bd, J0, omega)) < TOL[F32]
+    assert rel(got_x.double().cpu().numpy(), fast.adjoint1d(y, R, q, p, bd, J0, omega)) < TOL[F32]
+
+
 @pytest.mark.parametrize("prec", [F32, F64])
 def test_config2_full_size(prec):
     """p = 4, M = 2^16, q = 2 (N = 2^18), multilevel 15% mask, batch 64 with
