@@ -388,6 +388,86 @@ __global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2, 
 
 
 
+// FP32 butterfly of 4 adjacent columns: (a, d) <- (a + d, a - d), as two
+// packed FP32x2 operations each (a - d = fma(d, -1, a), exact like the plain
+// difference)
+__device__ __forceinline__ void bfly_x4(float4& a, float4& d) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+  const float2 d0 = make_float2(d.x, d.y), d1 = make_float2(d.z, d.w);
+  const float2 s0 = __fadd2_rn(a0, d0), s1 = __fadd2_rn(a1, d1);
+  const float2 t0 = __ffma2_rn(d0, m1, a0), t1 = __ffma2_rn(d1, m1, a1);
+  a = make_float4(s0.x, s0.y, s1.x, s1.y);
+  d = make_float4(t0.x, t0.y, t1.x, t1.y);
+}
+
+// k_fwht_cols32 for FP32 with 4 adjacent columns per thread (128 per CTA):
+// the line is read and written as 16-byte vectors, the sample table 4
+// entries at a time, and the butterflies run as packed FP32x2 operations;
+// the same stages in the same order, so the results are those of
+// k_fwht_cols32 bit for bit.  The kernel is bound by instruction issue, and
+// this cuts its loads, stores and address arithmetic by 4 and its adds by 2.
+template <int L1, int MODE>
+__global__ void __launch_bounds__(256) k_fwht_cols128(float* __restrict__ x, int L2, const int32_t* __restrict__ n2y,
+                                                      const float* __restrict__ yin, float* __restrict__ yout,
+                                                      int64_t m) {
+  constexpr int n1 = 1 << L1, NR = n1 / 8;
+  __shared__ __align__(16) float4 S[n1][32];
+  pdl_trigger();
+  pdl_wait();
+  const int tid = threadIdx.x, c4 = tid & 31, g = tid >> 5;
+  const int64_t n2 = (int64_t)1 << L2;
+  const int tiles = (int)(n2 / 128);
+  const int64_t b = blockIdx.x / tiles;
+  const int64_t col = (int64_t)(blockIdx.x % tiles) * 128 + 4 * c4;
+  float* base = x + b * ((int64_t)n1 << L2) + col;
+  const int32_t* tb = n2y + col;
+  const float* yb = yin + b * m;
+  float4 v[8];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const int64_t r = g + 8 * i;
+    if constexpr (MODE == 2) {
+      const int4 t = __ldg(reinterpret_cast<const int4*>(tb + r * n2));
+      v[i] = make_float4(t.x >= 0 ? __ldg(yb + t.x) : 0.f, t.y >= 0 ? __ldg(yb + t.y) : 0.f,
+                         t.z >= 0 ? __ldg(yb + t.z) : 0.f, t.w >= 0 ? __ldg(yb + t.w) : 0.f);
+    } else {
+      v[i] = *reinterpret_cast<const float4*>(base + r * n2);
+    }
+  }
+#pragma unroll
+  for (int h = 1; h < NR; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < NR; ++i)
+      if (!(i & h)) bfly_x4(v[i], v[i + h]);
+#pragma unroll
+  for (int i = 0; i < NR; ++i) S[g + 8 * i][c4] = v[i];
+  __syncthreads();
+  if (g < NR) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = S[8 * g + i][c4];
+#pragma unroll
+    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (!(i & h)) bfly_x4(v[i], v[i + h]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t r = 8 * g + i;
+      if constexpr (MODE == 1) {
+        const int4 t = __ldg(reinterpret_cast<const int4*>(tb + r * n2));
+        float* yo = yout + b * m;
+        if (t.x >= 0) yo[t.x] = v[i].x;
+        if (t.y >= 0) yo[t.y] = v[i].y;
+        if (t.z >= 0) yo[t.z] = v[i].z;
+        if (t.w >= 0) yo[t.w] = v[i].w;
+      } else {
+        *reinterpret_cast<float4*>(base + r * n2) = v[i];
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_gather(const T* __restrict__ beta, T* __restrict__ y, const uint32_t* __restrict__ mask,
                          const int32_t* __restrict__ prefix, int64_t words, int L, int64_t N, int64_t m, int batch) {
@@ -2254,6 +2334,18 @@ static bool cols_with_samples(const Plan& P, T* v, const T* yin, T* yout, int ba
          sizeof(T) * (double)batch * ((double)(1LL << L) + 2.0 * P.m) + 4.0 * (double)(1LL << L));
   auto go = [&](auto l1) {
     constexpr int LL = decltype(l1)::value;
+    if constexpr (std::is_same<T, float>::value) {
+      // 4 columns per thread: 16-byte accesses to the line (its base and the
+      // table are 256-byte aligned; rows are 2^12 floats apart)
+      const dim3 g4((unsigned)(batch * ((1 << L2) / 128)));
+      if (mode == 1)
+        Lc.note(launch_pdl(k_fwht_cols128<LL, 1>, g4, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y,
+                           (const float*)nullptr, yout, (int64_t)P.m));
+      else
+        Lc.note(launch_pdl(k_fwht_cols128<LL, 2>, g4, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y, yin,
+                           (float*)nullptr, (int64_t)P.m));
+      return;
+    }
     if (mode == 1)
       Lc.note(launch_pdl(k_fwht_cols32<T, LL, 1>, grid, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y,
                          (const T*)nullptr, yout, (int64_t)P.m));
