@@ -937,6 +937,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the FISTA and 1D workload measurements that ride along the main line")
+    ap.add_argument("--workload-1d", action="store_true",
+                    help="instead of the benchmark workload: only the batched 1D workload's measurement, one JSON line")
     ap.add_argument("--uneven", type=int, default=0,
                     help="instead of the benchmark workload: the batched uneven workload with this many instances")
     ap.add_argument("--cpu-oracle", default="", choices=["", "reference", "baseline"],
@@ -949,6 +951,11 @@ def main():
         return
     if args.uneven:
         run_uneven(args)
+        return
+    if args.workload_1d:
+        import torch
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+        print(json.dumps(measure_workload_1d(args.steps, flush, peaks()[0])), flush=True)
         return
     globals()["R"] = args.R
     if args.R != 11:
