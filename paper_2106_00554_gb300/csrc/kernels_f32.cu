@@ -979,82 +979,131 @@ struct TapsT {
 // VMP end): NB, and the segment values those read, H at each end
 template <int PM, int Q>
 struct SegUT {
-  static constexpr int BO = SEGN / Q / SEGNT;                // outputs per thread
-  static constexpr int NB = (2 * PM + BO - 1) / BO * BO;     // >= max(PM - 1, p), whole threads
+  static constexpr int CK = 4;                               // outputs per window step
+  static constexpr int NB = (2 * PM + CK - 1) / CK * CK;     // >= max(PM - 1, p), whole steps
   static constexpr int H = ((NB + PM) * Q + 15) / 16 * 16;   // >= (NB + p) Q and >= (p - 1) Q
 };
 
+// The adjoint's segment kernel with 64 threads per segment of 4096: thread t
+// loads the pencil t + 64 i (coalesced) and applies the stages of bits 6-11
+// in registers; one exchange through shared memory (4 words of padding per
+// 64, conflict-free both ways) gives it the 64 consecutive values 64 t + i,
+// and the stages of bits 0-5 follow in registers (the stages commute).
+// Shared-memory traffic per value: one store, one load and one store, and
+// about 1.4 loads for the T^T windows, which slide through registers 4
+// outputs at a time.  (With 256 threads, 16 values
+// each and three passes of 4 stages, each value went through shared memory
+// about 7.5 times, and the kernel was bound by it.)
+constexpr int SEG64 = 64;
+__host__ __device__ __forceinline__ constexpr int vq(int k) { return k + 4 * (k >> 6); }
+constexpr int SEGV64 = up4(vq(SEGN - 1) + 1);
+
 // the adjoint on segment `seg` of line b, after the stages across segments:
-// the Walsh-Hadamard stages of bits 0-11 in shared memory, then s = T^T v
-// for the segment's interior outputs (windows read from shared memory), and
-// the H values at each end of the transformed segment back to v for the
-// boundary outputs (seg_upT_fix)
+// the Walsh-Hadamard stages of bits 0-11, then s = T^T v for the segment's
+// interior outputs (windows from shared memory), and the H values at each
+// end of the transformed segment back to v for the boundary outputs
+// (seg_upT_fix)
 template <int PM, int Q>
-__global__ void __launch_bounds__(SEGNT) k_fwht_seg_upT(float* __restrict__ v, float* __restrict__ s, TapsT<PM, Q> tp,
-                                                        Geo G, int segs) {
+__global__ void __launch_bounds__(SEG64) k_fwht_seg64_upT(float* __restrict__ v, float* __restrict__ s,
+                                                          TapsT<PM, Q> tp, Geo G, int segs) {
   using U = SegUT<PM, Q>;
   pdl_trigger();
   pdl_wait();
-  constexpr int BO = U::BO, NT2 = (2 * PM - 1) * Q / 2;
+  constexpr int BO = SEGN / Q / SEG64, NT2 = (2 * PM - 1) * Q / 2;   // outputs per thread: 16 or 32
   constexpr int OFF = (((1 - PM) * Q) % 4 + 4) % 4;          // window start below a 4-aligned index
-  constexpr int NWV = (OFF + Q * (BO + 2 * PM - 2) + 3) / 4 * 4;
-  static_assert(BO >= 1 && (Q * BO) % 16 == 0, "outputs per thread");
-  __shared__ __align__(16) float sV[SEGV];
+  constexpr int CK = U::CK, ST = Q * CK;                     // outputs per window step, window advance
+  constexpr int W = (OFF + Q * (CK + 2 * PM - 2) + 3) / 4 * 4;
+  static_assert(BO % CK == 0 && W > ST && ST % 4 == 0, "window steps");
+  __shared__ __align__(16) float sV[SEGV64];
   const int tid = threadIdx.x;
   const int64_t b = blockIdx.x / segs;
   const int seg = blockIdx.x - (int)(b * segs);
   float* vs = v + b * G.N + (int64_t)seg * SEGN;
-  float o[16];
-#pragma unroll
-  for (int r = 0; r < 16; r += 4) {
-    const float4 u = *reinterpret_cast<const float4*>(vs + 16 * tid + r);
-    o[r] = u.x; o[r + 1] = u.y; o[r + 2] = u.z; o[r + 3] = u.w;
-  }
-  wht<16>(o);
   {
-    float* dst = sV + vp(16 * tid);
+    float a[64];
 #pragma unroll
-    for (int r = 0; r < 16; r += 4) *reinterpret_cast<float4*>(dst + r) = make_float4(o[r], o[r + 1], o[r + 2], o[r + 3]);
+    for (int i = 0; i < 64; ++i) a[i] = vs[tid + 64 * i];
+    wht<64>(a);
+#pragma unroll
+    for (int i = 0; i < 64; ++i) sV[vq(tid + 64 * i)] = a[i];
   }
   __syncthreads();
-  pass_mid<SEGNT>(sV, 0, tid);
-  __syncthreads();
-  pass_high<SEGNT>(sV, 0, tid);
+  {
+    float a[64];
+    float* row = sV + vq(64 * tid);
+#pragma unroll
+    for (int r = 0; r < 64; r += 4) {
+      const float4 u = *reinterpret_cast<const float4*>(row + r);
+      a[r] = u.x; a[r + 1] = u.y; a[r + 2] = u.z; a[r + 3] = u.w;
+    }
+    wht<64>(a);
+#pragma unroll
+    for (int r = 0; r < 64; r += 4) *reinterpret_cast<float4*>(row + r) = make_float4(a[r], a[r + 1], a[r + 2], a[r + 3]);
+  }
   __syncthreads();
   // the ends of the transformed segment, for the boundary outputs
-  for (int i = tid; i < 2 * U::H; i += SEGNT) {
+  for (int i = tid; i < 2 * U::H; i += SEG64) {
     const int k = i < U::H ? i : SEGN - 2 * U::H + i;
-    vs[k] = sV[vp(k)];
+    vs[k] = sV[vq(k)];
   }
-  // interior outputs: local m in [NB, SEGN / Q - NB)
-  const int ml = BO * tid;                    // local output index of this thread's first output
-  if (ml >= U::NB && ml + BO <= SEGN / Q - U::NB) {
-    // local v index of the window start (Q ml + (1 - PM) Q), rounded down to a
-    // multiple of 4; it and the window's end stay inside the segment
-    const int k0 = Q * ml + (1 - PM) * Q - OFF;
-    float ws[NWV];
+  // interior outputs: local m in [NB, SEGN / Q - NB), CK at a time
+  const int ml = BO * tid;
+  float* sb = s + b * G.M + (int64_t)seg * (SEGN / Q) + ml;
+  auto step = [&](const float (&win)[W], int c) {
+    float out[CK];
 #pragma unroll
-    for (int w = 0; w < NWV; w += 4) {
-      const float4 u = *reinterpret_cast<const float4*>(sV + vp(k0 + w));   // 4 values inside one 16-block
-      ws[w] = u.x; ws[w + 1] = u.y; ws[w + 2] = u.z; ws[w + 3] = u.w;
-    }
-    float out[BO];
-#pragma unroll
-    for (int u = 0; u < BO; ++u) {
+    for (int u = 0; u < CK; ++u) {
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < NT2; ++i)
-        acc = __ffma2_rn(tp.t2[i], make_float2(ws[OFF + Q * u + 2 * i], ws[OFF + Q * u + 2 * i + 1]), acc);
+        acc = __ffma2_rn(tp.t2[i], make_float2(win[OFF + Q * u + 2 * i], win[OFF + Q * u + 2 * i + 1]), acc);
       out[u] = acc.x + acc.y;
     }
-    float* sb = s + b * G.M + (int64_t)seg * (SEGN / Q) + ml;
+    *reinterpret_cast<float4*>(sb + CK * c) = make_float4(out[0], out[1], out[2], out[3]);
+  };
+  // window of step c: v[Q (ml + CK c) + (1 - PM) Q - OFF ..) (a multiple of 4; inside the
+  // segment whenever the step's outputs are interior)
+  const int k0 = Q * ml + (1 - PM) * Q - OFF;
+  float win[W];
+  if (ml >= U::NB && ml + BO <= SEGN / Q - U::NB) {
+    // every step interior: the window slides through registers
 #pragma unroll
-    for (int u = 0; u < BO; ++u) sb[u] = out[u];
+    for (int w = 0; w < W; w += 4) {
+      const float4 u = *reinterpret_cast<const float4*>(sV + vq(k0 + w));   // 4 values inside one 64-block
+      win[w] = u.x; win[w + 1] = u.y; win[w + 2] = u.z; win[w + 3] = u.w;
+    }
+#pragma unroll
+    for (int c = 0; c < BO / CK; ++c) {
+      step(win, c);
+      if (c + 1 < BO / CK) {
+#pragma unroll
+        for (int w = 0; w < W - ST; ++w) win[w] = win[w + ST];
+#pragma unroll
+        for (int w = W - ST; w < W; w += 4) {
+          const float4 u = *reinterpret_cast<const float4*>(sV + vq(k0 + ST * (c + 1) + w));
+          win[w] = u.x; win[w + 1] = u.y; win[w + 2] = u.z; win[w + 3] = u.w;
+        }
+      }
+    }
+  } else {
+    // the first and last thread: only the interior steps, each with its own window
+#pragma unroll 1
+    for (int c = 0; c < BO / CK; ++c) {
+      const int m = ml + CK * c;
+      if (m < U::NB || m + CK > SEGN / Q - U::NB) continue;
+#pragma unroll
+      for (int w = 0; w < W; w += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(sV + vq(k0 + ST * c + w));
+        win[w] = u.x; win[w + 1] = u.y; win[w + 2] = u.z; win[w + 3] = u.w;
+      }
+      step(win, c);
+    }
   }
 }
 
-// the boundary outputs of T^T that k_fwht_seg_upT left: NB at each side of
-// every segment, by the exact formula (reads v only inside the ends written)
+// the boundary outputs of T^T that the fused segment kernel left: NB at
+// each side of every segment, by the exact formula (reads v only inside the
+// ends written)
 template <int PM, int Q>
 __global__ void __launch_bounds__(256) k_seg_upT_fix(const float* __restrict__ v, float* __restrict__ s,
                                                      Tables<float> tab, Geo G, int segs, int batch) {
@@ -1523,8 +1572,9 @@ cudaError_t f32_seg_fwht_upT(const Plan& P, const Geo& G, float* v, float* s, in
   const int segs = P.N / f32k::SEGN;
   return f32_pm_dispatch(P, [&](auto pm, auto q) {
     constexpr int PM = decltype(pm)::value, Q = decltype(q)::value;
-    cudaError_t e = launch_pdl(f32k::k_fwht_seg_upT<PM, Q>, dim3((unsigned)(batch * segs)), dim3(f32k::SEGNT), 0, st,
-                               v, s, make_tapsT<PM, Q>(P), G, segs);
+    constexpr int NTS = f32k::SEG64;
+    cudaError_t e = launch_pdl(f32k::k_fwht_seg64_upT<PM, Q>, dim3((unsigned)(batch * segs)), dim3(NTS), 0, st, v,
+                               s, make_tapsT<PM, Q>(P), G, segs);
     if (e != cudaSuccess) return e;
     const int64_t n = (int64_t)batch * segs * 2 * f32k::SegUT<PM, Q>::NB;
     return launch_pdl(f32k::k_seg_upT_fix<PM, Q>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st,
