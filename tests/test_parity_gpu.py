@@ -84,11 +84,14 @@ def test_1d_sweep_against_dense(p, bd, dR, q):
 
 @pytest.mark.parametrize("prec,R,q,p,bd", [(F64, 13, 2, 3, VMP), (F32, 14, 2, 2, VMP), (F64, 12, 4, 4, VMP),
                                             (F32, 14, 2, 3, PERIODIC), (F64, 14, 1, 5, PERIODIC),
-                                            (F32, 15, 1, 8, VMP), (F32, 14, 1, 10, VMP), (F32, 13, 2, 9, PERIODIC)])
+                                            (F32, 15, 1, 8, VMP), (F32, 14, 1, 10, VMP), (F32, 13, 2, 9, PERIODIC),
+                                            (F32, 17, 2, 4, VMP)])
 def test_1d_large_lines_against_algorithm1(prec, R, q, p, bd):
     """Lines longer than one CTA's shared memory take the multi-kernel path:
     the coarse levels of each line in one CTA's shared memory (as many as
-    fit), the levels above them one launch each, T, the two-pass FWHT."""
+    fit), the levels above them one launch each, T, the two-pass FWHT.  At
+    N = 2^19 (FP32) the stages across segments exceed one CTA's columns and
+    the separate gather / scatter run."""
     rng = np.random.default_rng(R + q + 10 * bd)
     J0 = W.default_J0(p)
     N = 2 ** (R + q)
