@@ -1,4 +1,5 @@
-"""Shared-memory bank model of the FP32 line operators (kernels_f32.cu).
+"""Shared-memory bank model of the FP32 line operators (kernels_f32.cu) and
+of the adjoint's 64-thread segment kernel for long 1D lines.
 
 The address of every shared-memory access of k_f32_fwd / k_f32_adj is
 restated here from the kernel (layouts vp, sp<Q>, the lane orders of the
@@ -126,3 +127,49 @@ def test_model_counts_conflicts():
     # the swapped half-warp visits the same pencil elements, only reordered
     for i in range(16):
         assert sorted({i ^ 4 * h for h in (0, 1)}) == sorted({i, i ^ 4})
+
+
+# --- the adjoint's segment kernel for long 1D lines (k_fwht_seg64_upT) ---
+def vq(k):                      # segment of 4096: 4 words of padding per 64
+    return k + 4 * (k >> 6)
+
+
+def seg64_accesses(PM, Q):
+    """(site, width, lane addresses) of the shared-memory accesses of one
+    segment: 64 threads, thread t first holds the pencil t + 64 i, then the
+    64 consecutive values 64 t + r, then reads its T^T windows (Sec. 4.2)
+    4 outputs at a time."""
+    BO = 4096 // Q // 64
+    NB = (2 * PM + 3) // 4 * 4
+    OFF = ((1 - PM) * Q % 4 + 4) % 4
+    CK, ST = 4, 4 * Q
+    W = (OFF + Q * (CK + 2 * PM - 2) + 3) // 4 * 4
+    out = []
+    for warp in range(2):
+        lanes = range(32 * warp, 32 * warp + 32)
+        for i in range(64):                                    # pencil stores
+            out.append(("seg64 pencil", 1, [vq(t + 64 * i) for t in lanes]))
+        for r in range(0, 64, 4):                              # rows of 64, 16-byte vectors
+            out.append(("seg64 rows", 4, [vq(64 * t + r) for t in lanes]))
+        act = [t for t in lanes if BO * t >= NB and BO * t + BO <= 4096 // Q - NB]
+        for c in range(BO // CK):                              # sliding T^T windows
+            for w in range(0 if c == 0 else W - ST, W, 4):
+                out.append(("seg64 window", 4, [vq(Q * BO * t + (1 - PM) * Q - OFF + ST * c + w) for t in act]))
+    return out
+
+
+@pytest.mark.parametrize("PM", [4, 8, 10])
+@pytest.mark.parametrize("Q", [2, 4])
+def test_seg64_layout_conflict_free(PM, Q):
+    """Every access of the 64-thread segment kernel, in its padded layout,
+    needs no more wavefronts than its bytes demand; the plain layout (no
+    padding) does not, which checks the model."""
+    bad = {}
+    for site, width, addrs in seg64_accesses(PM, Q):
+        if addrs:
+            extra = _wavefronts(addrs, width) - _ideal(addrs, width)
+            if extra:
+                bad[site] = bad.get(site, 0) + extra
+    assert not bad, bad
+    plain = [64 * t for t in range(32)]
+    assert _wavefronts(plain, 4) > _ideal(plain, 4)
