@@ -319,15 +319,10 @@ __global__ void __launch_bounds__(256) k_fwht_cols(T* __restrict__ x, int L1, in
 // as one 128-byte run (FP32).  Thread (g = tid / 32, c = tid % 32) first holds
 // rows g + 8 i of column c and applies the stages of row bits 3 .. L1-1 in
 // registers; one padded shared-memory exchange gives it rows 8 g + i, and the
-// stages of bits 0-2 follow in registers.  Natural order throughout.
-//
-// MODE 1 (forward) writes only the sampled outputs, straight into y (n2y:
-// natural position -> index in y, or -1); MODE 2 (adjoint) reads its input
-// from y through the same table (zero where nothing is sampled).
-template <typename T, int L1, int MODE = 0>
-__global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2, const int32_t* __restrict__ n2y = nullptr,
-                                                     const T* __restrict__ yin = nullptr, T* __restrict__ yout = nullptr,
-                                                     int64_t m = 0) {
+// stages of bits 0-2 follow in registers.  Natural order throughout.  (The
+// FP32 1D products use k_fwht_cols128 below, which also samples.)
+template <typename T, int L1>
+__global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2) {
   constexpr int n1 = 1 << L1, NR = n1 / 8;
   __shared__ T S[n1][33];
   pdl_trigger();
@@ -341,14 +336,7 @@ __global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2, 
   T v[8];
   if (g < 8) {
 #pragma unroll
-    for (int i = 0; i < NR; ++i) {
-      if (MODE == 2) {
-        const int yi = __ldg(n2y + (int64_t)(g + 8 * i) * n2 + col);
-        v[i] = yi >= 0 ? __ldg(yin + b * m + yi) : T(0);
-      } else {
-        v[i] = base[(int64_t)(g + 8 * i) * n2];
-      }
-    }
+    for (int i = 0; i < NR; ++i) v[i] = base[(int64_t)(g + 8 * i) * n2];
 #pragma unroll
     for (int h = 1; h < NR; h <<= 1)
 #pragma unroll
@@ -375,14 +363,7 @@ __global__ void __launch_bounds__(256) k_fwht_cols32(T* __restrict__ x, int L2, 
           v[i + h] = a - d;
         }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (MODE == 1) {
-        const int yi = __ldg(n2y + (int64_t)(8 * g + i) * n2 + col);
-        if (yi >= 0) yout[b * m + yi] = v[i];
-      } else {
-        base[(int64_t)(8 * g + i) * n2] = v[i];
-      }
-    }
+    for (int i = 0; i < 8; ++i) base[(int64_t)(8 * g + i) * n2] = v[i];
   }
 }
 
@@ -2325,33 +2306,28 @@ static void adj1d_smem(const Plan& P, const T* y, T* x, int batch, Launcher& L) 
 // 1D, lines larger than shared memory: level kernels + T + two-pass FWHT.
 // the stages across segments of 4096 (L1 = L - 12 in 3..6) with the gather
 // (mode 1) or the scatter (mode 2) folded in; false if not applicable
-template <typename T>
-static bool cols_with_samples(const Plan& P, T* v, const T* yin, T* yout, int batch, int mode, Launcher& Lc) {
+// The stages of bits 12.. of FP32 1D lines across their segments of 4096,
+// writing the sampled outputs straight into yout (mode 1) or reading the
+// input from yin (mode 2) through the natural-position-to-sample table;
+// false if the shape does not suit (the caller then runs the plain stages
+// and a separate gather / scatter).
+static bool cols_with_samples(const Plan& P, float* v, const float* yin, float* yout, int batch, int mode,
+                              Launcher& Lc) {
   const int L = geo_of(P).L, L2 = 12, L1 = L - L2;
   if (!P.d_nat2y || L1 < 3 || L1 > 6) return false;
-  const dim3 grid((unsigned)(batch * ((1 << L2) / 32)));
   Lc.pre(mode == 1 ? "fwht_cols_gather_1d" : "fwht_cols_scatter_1d",
-         sizeof(T) * (double)batch * ((double)(1LL << L) + 2.0 * P.m) + 4.0 * (double)(1LL << L));
+         sizeof(float) * (double)batch * ((double)(1LL << L) + 2.0 * P.m) + 4.0 * (double)(1LL << L));
   auto go = [&](auto l1) {
     constexpr int LL = decltype(l1)::value;
-    if constexpr (std::is_same<T, float>::value) {
-      // 4 columns per thread: 16-byte accesses to the line (its base and the
-      // table are 256-byte aligned; rows are 2^12 floats apart)
-      const dim3 g4((unsigned)(batch * ((1 << L2) / 128)));
-      if (mode == 1)
-        Lc.note(launch_pdl(k_fwht_cols128<LL, 1>, g4, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y,
-                           (const float*)nullptr, yout, (int64_t)P.m));
-      else
-        Lc.note(launch_pdl(k_fwht_cols128<LL, 2>, g4, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y, yin,
-                           (float*)nullptr, (int64_t)P.m));
-      return;
-    }
+    // 4 columns per thread: 16-byte accesses to the line (its base and the
+    // table are 256-byte aligned; rows are 2^12 floats apart)
+    const dim3 g4((unsigned)(batch * ((1 << L2) / 128)));
     if (mode == 1)
-      Lc.note(launch_pdl(k_fwht_cols32<T, LL, 1>, grid, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y,
-                         (const T*)nullptr, yout, (int64_t)P.m));
+      Lc.note(launch_pdl(k_fwht_cols128<LL, 1>, g4, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y,
+                         (const float*)nullptr, yout, (int64_t)P.m));
     else
-      Lc.note(launch_pdl(k_fwht_cols32<T, LL, 2>, grid, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y, yin,
-                         (T*)nullptr, (int64_t)P.m));
+      Lc.note(launch_pdl(k_fwht_cols128<LL, 2>, g4, dim3(256), 0, Lc.s, v, L2, (const int32_t*)P.d_nat2y, yin,
+                         (float*)nullptr, (int64_t)P.m));
   };
   if (L1 == 3) go(std::integral_constant<int, 3>{});
   else if (L1 == 4) go(std::integral_constant<int, 4>{});
@@ -2453,7 +2429,7 @@ static void fwd1d_big(const Plan& P, const T* x, T* y, int batch, T* work, Launc
       L.pre("upconv_fwht_seg_1d", e * (double)batch * (M + N));
       L.note(f32_seg_up(P, G, cur, v, batch, L.s));
       L.check();
-      if (cols_with_samples<T>(P, v, nullptr, y, batch, 1, L)) return;
+      if (cols_with_samples(P, v, nullptr, y, batch, 1, L)) return;
       fwht_big<T>(v, G.L, batch, L, false);
       L.pre("gather_1d", e * 2.0 * batch * P.m + 8.0 * P.words);
       k_gather<T><<<grid_for((int64_t)batch * P.words), 256, 0, L.s>>>(v, y, P.d_mask, P.d_prefix, P.words, G.L, N, P.m,
@@ -2492,7 +2468,7 @@ static void adj1d_big(const Plan& P, const T* y, T* x, int batch, T* work, Launc
     if (f32_seg_eligible(P)) {
       // the stages of bits 12.. (reading the samples from y where the table
       // allows), then bits 0-11 per segment of 4096, then T^T
-      scattered = cols_with_samples<T>(P, v, y, nullptr, batch, 2, L);
+      scattered = cols_with_samples(P, v, y, nullptr, batch, 2, L);
       if (!scattered) {
         scatter();
         fwht_big<T>(v, G.L, batch, L, false);
